@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the PTSBE hot path on one GB300 (or N, one process each).
+
+Workload: the 17-qubit syndrome-extraction circuit (9 data + 8 ancilla qubits, 3 rounds, amplitude
+damping 5e-4 + depolarising 1e-3 after every gate on every touched qubit, 390 noise sites), the
+10^4 most likely Kraus sets (top-K pre-trajectory sampling), 10^8 shots recorded with their
+Kraus-set labels. One step = register the circuit, run PTS on the host, prepare all 10^4 states
+with prefix reuse (10.5 GB of complex64 states, larger than L2), draw the 10^8 shots.
+
+Output: one JSON line (rank 0) with shots/s, the roofline of the dominant kernel (algorithmic
+bytes per launch over CUDA-event time, against the measured HBM copy peak), the end-to-end figure
+through host buffers, the CPU oracle timed on a bounded sample, and the clocks seen meanwhile.
+`--impl reference` times the CPU oracle (the reference arm of this build) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "syndrome17_3rounds_top1e4_1e8shots"
+METRIC = "shots/s & gate-apply HBM GB/s, PTSBE batched vs per-shot trajectories, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--k", type=int, default=10_000)
+    ap.add_argument("--shots", type=int, default=100_000_000)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": num(rows[0][2]),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_sha") == source_sha(e["sources"]):
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------------------------
+def oracle_estimate(budget_s: float, k: int, shots: int, seed: int):
+    """Times the oracle on a bounded sample of the workload and extrapolates the whole job:
+    top-K PTS once, state preparation of a few sets (each costs a full 17-qubit evolution), CDF
+    construction and per-shot inverse-CDF draws. Returns (shots/s, description)."""
+    from oracle import oracle as orc
+    from workloads import config
+    c = config(1)
+    circ = c["circuit"]
+    n = circ.n_qubits
+    t0 = time.perf_counter()
+    o = orc.Oracle(circ)
+    sets = o.pts_topk(k, shots)
+    t_pts = time.perf_counter() - t0
+    picks = [0, 1, sets.count // 2, sets.count - 1]
+    t_ev, n_ev = 0.0, 0
+    psi0 = None
+    while n_ev < len(picks) or (t_ev < 0.5 * budget_s and n_ev < 64):
+        i = picks[n_ev % len(picks)] if n_ev < len(picks) else (n_ev * 7919) % sets.count
+        t0 = time.perf_counter()
+        psi, w, st = o.evolve(sets, i)
+        t_ev += time.perf_counter() - t0
+        if psi0 is None:
+            psi0 = psi
+        n_ev += 1
+    t0 = time.perf_counter()
+    orc.cdf(n, psi0)
+    t_cdf = time.perf_counter() - t0
+    m = 200_000
+    t0 = time.perf_counter()
+    while True:
+        orc.sample(n, psi0, m, seed, 0)
+        el = time.perf_counter() - t0
+        if el > 0.2 * budget_s or m >= 4_000_000:
+            break
+        m *= 2
+    t_shot = el / m   # includes one CDF build per call, negligible at this m
+    total = t_pts + sets.count * (t_ev / n_ev + t_cdf) + shots * t_shot
+    desc = (f"complex128 C oracle, 1 thread: top-{k} PTS once ({t_pts:.1f}s), {n_ev} of {sets.count} state "
+            f"preparations ({t_ev / n_ev:.3f}s each), CDF build {t_cdf * 1e3:.1f} ms, {m} shots "
+            f"({t_shot * 1e9:.0f} ns each); extrapolated to {sets.count} states + {shots} shots = {total:.0f}s")
+    return shots / total, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    desc = ""
+    for step in range(args.warmup + args.steps):
+        v, desc = oracle_estimate(max(5.0, args.cpu_budget / 2), args.k, args.shots, 2001)
+        if step >= args.warmup:
+            vals.append(v)
+    val = float(np.median(vals))
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shots/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "dtype": "f64", "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": WORKLOAD, "kraus_sets": args.k, "shots": args.shots, "qubits": 17},
+           "cpu_baseline": {"value": val, "unit": "shots/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": val, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2504_16297_gb300 import build, capi
+    from paper_2504_16297_gb300.runtime import Ptsbe
+    from workloads import config
+    build()
+
+    cfg = config(1)
+    circ = cfg["circuit"]
+    n = circ.n_qubits
+    K, M = args.k, args.shots
+    seed = cfg["seed"] + rank          # weak scaling: every rank collects its own 1e8 shots
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    P = Ptsbe(device=local, stream=stream.cuda_stream)
+    states = torch.empty((K, 1 << n), dtype=torch.complex64, device=dev)
+    weights = torch.empty(K, dtype=torch.float64, device=dev)
+    status = torch.empty(K, dtype=torch.uint8, device=dev)
+    bits = torch.empty(M, dtype=torch.int32, device=dev)
+    host_bits = torch.empty(M, dtype=torch.int32, pin_memory=True)
+    host_w = torch.empty(K, dtype=torch.float64, pin_memory=True)
+    host_s = torch.empty(K, dtype=torch.uint8, pin_memory=True)
+    h2d_bytes = [0]
+
+    def step(e2e: bool):
+        cid = P.register(circ)
+        info = P.sample_kraus(cid, "topk", k=K, total_shots=M, export=False)
+        assert info.count == K and info.total_shots == M
+        P.evolve(info, 0, K, states, weights, status, prefix_reuse=True)
+        P.sample(info, 0, K, states, status, seed, bits)
+        if e2e:
+            host_bits.copy_(bits, non_blocking=True)
+            host_w.copy_(weights, non_blocking=True)
+            host_s.copy_(status, non_blocking=True)
+        P.release_set(info)
+        P.release_circuit(cid)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(e2e: bool, steps: int, instrument: bool):
+        barrier()
+        if instrument:
+            P.set_timing(True)
+            for cls in range(4):
+                P.timing(cls, reset=True)
+        l0 = capi.ptsbe_kernel_launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step(e2e)
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = capi.ptsbe_kernel_launches() - l0
+        kern = {}
+        if instrument:
+            for cls, name in enumerate(["evolve_stage", "evolve_finalize", "sample", "pershot"]):
+                kms, kl, kb = P.timing(cls, reset=True)
+                if kl:
+                    kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
+            P.set_timing(False)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), launches, kern
+
+    for _ in range(args.warmup):
+        step(False)
+    clocks = Clocks(local)
+    clocks.start()
+    ms, launches, kern = timed(False, args.steps, True)
+    clk = clocks.stop()
+    steps_e2e = max(1, args.steps // 2)
+    hb0 = capi.ptsbe_h2d_bytes()
+    ms_e2e, _, _ = timed(True, steps_e2e, False)
+    h2d_bytes[0] = (capi.ptsbe_h2d_bytes() - hb0) // steps_e2e
+
+    ms_step = ms / args.steps
+    value = world * M / (ms_step / 1e3)
+    e2e_value = world * M / (ms_e2e / steps_e2e / 1e3)
+    peak, peak_kind = peaks()
+    dom = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
+    roof = None
+    if dom:
+        d = kern[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic_for(dom), "bytes_per_launch": d["bytes"] / d["launches"],
+                "ms_per_launch": d["ms"] / d["launches"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc = oracle_estimate(args.cpu_budget, K, M, seed)
+        cpu = {"value": v, "unit": "shots/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        gate_ms = kern.get("evolve_stage", {}).get("ms")
+        out = {
+            "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "qubits": n, "kraus_sets": K, "shots": M, "pts": "topk",
+                       "prefix_reuse": True, "amplitudes": "complex64, FP64 norms and CDF",
+                       "l2": "inputs larger than L2 (10.5 GB of states per step)",
+                       "parallelism": f"{world} independent replicas (weak scaling)"},
+            "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,
+            "kernels": kern,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": h2d_bytes[0],
+                    "d2h_bytes_per_step": M * 4 + K * 9},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,308 @@
+/*
+ * ptsbe.h -- C ABI of libptsbe: Pre-Trajectory Sampling with Batched Execution (PTSBE) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Patti, Nguyen, Lietz, McCaskey, Khailany, "Augmenting Simulated Noisy Quantum Data
+ * Collection by Orders of Magnitude Using Pre-Trajectory Sampling with Batched Execution"
+ * (SC'25). A noisy circuit is registered (Fig. 1), a PTS algorithm picks Kraus-operator sets
+ * alpha and their shot counts m_alpha up front (Sec. 3.1, Algorithm 2), each unique noisy state
+ * is prepared once and all m_alpha shots are drawn from it at once (Sec. 3, batched execution).
+ * The traditional per-operator trajectory loop (Algorithm 1) is provided as a comparison path.
+ *
+ * Conventions for every call:
+ *   - Every function returns a ptsbe_status; nothing throws or aborts across the ABI. On error
+ *     the outputs are unspecified, the context stays usable and ptsbe_last_error() describes
+ *     the failure.
+ *   - Host buffers are owned by the caller. Device buffers passed in (states, weights, shot
+ *     bitstrings) are owned by the caller (e.g. PyTorch tensors); the library never frees them.
+ *     The library owns its own device tables and workspace and frees them in ptsbe_destroy.
+ *   - Device work is enqueued on the context's CUDA stream and is asynchronous unless stated.
+ *   - Qubit q is bit q of a basis-state index. States are complex64, interleaved (re, im), one
+ *     state of 2^n amplitudes after another.
+ *   - Noise sites are the NOISE operations numbered 0..S-1 in circuit order. A Kraus set alpha
+ *     is a list of (site, k) with k != 0, sites strictly increasing; a site not listed uses
+ *     Kraus operator 0 ("no error").
+ *   - Counter-based randomness is Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed
+ *     (key = {seed_lo, seed_hi}); a 53-bit uniform is ((x0 << 21) | (x1 >> 11)) * 2^-53 of the
+ *     first two output words. Every draw is a pure function of (seed, counter), so any slice of a
+ *     job can be recomputed bit-identically.
+ */
+#ifndef PTSBE_H
+#define PTSBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PTSBE_API __attribute__((visibility("default")))
+#else
+#define PTSBE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptsbe_ctx ptsbe_ctx;
+
+typedef enum {
+    PTSBE_OK = 0,
+    PTSBE_ERR_INVALID = 1,          /* malformed argument (bad id, qubit >= n, unsorted set ...) */
+    PTSBE_ERR_NOT_CPTP = 2,         /* a channel violates sum_k K_k^dag K_k = I (Sec. 2.2)      */
+    PTSBE_ERR_OOM = 3,              /* host or device allocation failed; nothing was written     */
+    PTSBE_ERR_CUDA = 4,             /* a CUDA runtime call failed                                */
+    PTSBE_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up                        */
+    PTSBE_ERR_BUFFER_TOO_SMALL = 6, /* a caller buffer is smaller than the result                */
+    PTSBE_ERR_UNSUPPORTED = 7,      /* well-formed request outside what the library handles      */
+    PTSBE_ERR_NO_DEVICE = 8         /* a device entry point was called on a host-only context    */
+} ptsbe_status;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Context                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` that enqueues work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream). device = -1 creates a host-only context: registration, PTS
+ * and set export work, device entry points return PTSBE_ERR_NO_DEVICE. *out receives the handle. */
+PTSBE_API int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream);
+
+/* Waits for the context's stream, frees every library-owned host and device resource. */
+PTSBE_API int ptsbe_destroy(ptsbe_ctx* ctx);
+
+/* Replaces the stream later calls enqueue on. */
+PTSBE_API int ptsbe_set_stream(ptsbe_ctx* ctx, void* cuda_stream);
+
+/* Message of the last failed call on this context (owned by the library, valid until the next
+ * call on the context). Never NULL. */
+PTSBE_API const char* ptsbe_last_error(const ptsbe_ctx* ctx);
+
+/* Blocks until all work enqueued by the context has finished; returns PTSBE_ERR_CUDA (with the
+ * CUDA error text) if an asynchronous kernel failed, PTSBE_ERR_TIMEOUT if a bounded device wait
+ * gave up. */
+PTSBE_API int ptsbe_synchronize(ptsbe_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Circuit registration (Fig. 1: "an arbitrary noisy circuit is registered"; Sec. 2.2)        */
+/* ---------------------------------------------------------------------------------------- */
+
+enum { PTSBE_OP_GATE = 0, PTSBE_OP_NOISE = 1 };
+
+/* Gate codes. Matrices: OpenQASM U3(theta, phi, lambda) = [[cos t/2, -e^{i l} sin t/2],
+ * [e^{i p} sin t/2, e^{i(p+l)} cos t/2]]; RX/RY/RZ(theta) = exp(-i theta P/2). Two-qubit gates act
+ * on the local index 2*bit(targets[0]) + bit(targets[1]); CX has control targets[0]. U1/U2 take
+ * their matrix from the custom-gate table, row params[0]. */
+enum {
+    PTSBE_G_I = 0, PTSBE_G_X, PTSBE_G_Y, PTSBE_G_Z, PTSBE_G_H, PTSBE_G_S, PTSBE_G_SDG, PTSBE_G_T,
+    PTSBE_G_TDG, PTSBE_G_RX, PTSBE_G_RY, PTSBE_G_RZ, PTSBE_G_U3, PTSBE_G_CX, PTSBE_G_CZ,
+    PTSBE_G_SWAP, PTSBE_G_U1, PTSBE_G_U2
+};
+
+/* Channel kinds (Sec. 2.2: channels given as CPTP Kraus sets). With strength p (or gamma):
+ *   DEPOL1    {sqrt(1-p) I, sqrt(p/3) X, Y, Z}
+ *   DEPOL2    {sqrt(1-p) I(x)I, sqrt(p/15) P_a (x) P_b}, k = 4a + b, P_a on targets[0]
+ *   AMPDAMP   {[[1,0],[0,sqrt(1-g)]], [[0,sqrt(g)],[0,0]]}
+ *   BITFLIP   {sqrt(1-p) I, sqrt(p) X};  PHASEFLIP {sqrt(1-p) I, sqrt(p) Z}
+ *   CUSTOM    n_kraus <= 16 caller matrices of size 2^arity.
+ * Kraus operator 0 is "no error". Nominal probabilities q_k = tr(K_k^dag K_k)/d (closed forms
+ * 1-p, p/3 ... for the named kinds). A channel with K_k^dag K_k = q_k I for every k is a unitary
+ * mixture (Sec. 2.2 item 2): it is applied as U_k = K_k/sqrt(q_k) and needs no norm. */
+enum {
+    PTSBE_CH_DEPOL1 = 0, PTSBE_CH_DEPOL2, PTSBE_CH_AMPDAMP, PTSBE_CH_BITFLIP, PTSBE_CH_PHASEFLIP,
+    PTSBE_CH_CUSTOM
+};
+
+typedef struct {
+    uint32_t kind;        /* PTSBE_OP_GATE or PTSBE_OP_NOISE                                 */
+    uint32_t id;          /* gate code, or channel index into the channel array              */
+    uint32_t n_targets;   /* 1 or 2; must equal the gate's or channel's arity                */
+    uint32_t targets[2];  /* distinct qubits < n_qubits                                      */
+    double params[3];     /* angles (U3: theta, phi, lambda; RX/RY/RZ: theta)                */
+} ptsbe_op;
+
+typedef struct {
+    uint32_t kind;        /* PTSBE_CH_*                                                      */
+    uint32_t arity;       /* 1 or 2                                                          */
+    uint32_t n_kraus;     /* 4 / 16 / 2 / 2 / 2 for the named kinds; <= 16 for CUSTOM         */
+    double param;         /* p or gamma in [0, 1] for the named kinds                        */
+    const double* kraus;  /* CUSTOM only: n_kraus row-major (2^arity x 2^arity) complex128
+                             matrices as (re, im) pairs; copied during the call                */
+} ptsbe_channel;
+
+/* Validates and copies a noisy circuit; builds its device tables (gate matrices and Kraus
+ * operators rounded once to complex64, unitary-mixture flags, the tiling plan). n_qubits in
+ * [1, 32]. custom_gates: n_custom rows of 4x4 complex128 (re, im) (a 1-qubit custom gate uses the
+ * top-left 2x2). *circuit_id receives the handle.
+ * Errors: PTSBE_ERR_INVALID (bad op or channel), PTSBE_ERR_NOT_CPTP (|sum K^dag K - I| > 1e-10). */
+PTSBE_API int ptsbe_register_circuit(ptsbe_ctx* ctx, uint32_t n_qubits, const ptsbe_op* ops, uint64_t n_ops,
+                           const ptsbe_channel* channels, uint32_t n_channels,
+                           const double* custom_gates, uint32_t n_custom, uint32_t* circuit_id);
+
+/* Number of noise sites S and gates of a registered circuit. */
+PTSBE_API int ptsbe_circuit_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* n_qubits, uint64_t* n_sites,
+                       uint64_t* n_gates);
+
+PTSBE_API int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Pre-trajectory sampling (Sec. 3.1, Algorithm 2). Host-synchronous.                        */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef enum {
+    /* Algorithm 2 with one categorical draw per noise site (reading of "sampled ... in much the
+     * same way as they would be at state preparation runtime"): sample i at site s draws
+     * u = U53(Philox(seed; s, i_lo, i_hi, 1)) and takes the smallest k with u < q_0 + ... + q_k
+     * (FP64, listed order; the last k if rounding leaves u above the sum). */
+    PTSBE_PTS_PROPORTIONAL = 0,
+    /* The k most likely sets (Sec. 3.1, "most common errors ... above a given cutoff"): key of a
+     * set = product of its ratios q_{s,k}/q_{s,0} multiplied in descending order; order = key
+     * descending, then canonical order. Needs q_{s,0} > q_{s,k} at every site. */
+    PTSBE_PTS_TOPK = 1,
+    /* Every set with p_min <= q_alpha <= p_max (probability band; cutoff = band with p_max = 1). */
+    PTSBE_PTS_BAND = 2,
+    /* Caller-given sets (targeted errors; Sec. 3.1 "selection criteria"). */
+    PTSBE_PTS_TARGETED = 3,
+    /* Algorithm 2 as printed: each (site, k != 0) draws r = U53(Philox(seed; s, i_lo, i_hi,
+     * 4 | k << 8)) and is appended when r <= q_{s,k} and its site is still free (compatible). */
+    PTSBE_PTS_LITERAL = 4
+} ptsbe_pts_mode;
+
+typedef enum {
+    PTSBE_SHOTS_BY_COUNT = 0, /* largest-remainder apportionment of total_shots by multiplicity  */
+    PTSBE_SHOTS_UNIFORM = 1,  /* shots_per_set for every set (Algorithm 2's nshots)             */
+    PTSBE_SHOTS_BY_PROB = 2,  /* largest-remainder apportionment of total_shots by q_alpha      */
+    PTSBE_SHOTS_GIVEN = 3     /* TARGETED only: t_shots[i] per given set                        */
+} ptsbe_shot_alloc;
+
+typedef struct {
+    uint32_t mode;              /* ptsbe_pts_mode                                             */
+    uint32_t shot_alloc;        /* ptsbe_shot_alloc                                           */
+    uint64_t nsamples;          /* PROPORTIONAL, LITERAL                                      */
+    uint64_t k;                 /* TOPK                                                       */
+    double p_min, p_max;        /* BAND                                                       */
+    uint64_t total_shots;       /* BY_COUNT, BY_PROB                                          */
+    uint64_t shots_per_set;     /* UNIFORM                                                    */
+    uint32_t t_count;           /* TARGETED: number of sets                                   */
+    const uint32_t* t_offsets;  /* TARGETED: [t_count + 1] CSR offsets into t_sites/t_kidx    */
+    const uint32_t* t_sites;    /* TARGETED: strictly increasing per set                      */
+    const uint8_t* t_kidx;      /* TARGETED: 0 < k < n_kraus                                  */
+    const uint64_t* t_shots;    /* TARGETED with SHOTS_GIVEN: [t_count]                       */
+} ptsbe_pts_params;
+
+/* Runs a PTS algorithm and stores the resulting Kraus sets in the context. Sets are returned in
+ * canonical order (lexicographic over the (site, k) list, a prefix before its extensions, so the
+ * empty set comes first) with duplicates merged (uniqueKraus); mult = how many samples produced
+ * the set; q_alpha = (prod_s q_{s,0}) * key. Largest-remainder apportionment gives the extra
+ * shots to the largest remainders, ties to the lower index. The shot layout of the set is the
+ * exclusive prefix of m_alpha ("shot offsets"): shot j of set a is global shot offset[a] + j.
+ * Outputs (any may be NULL): *set_id, *count (unique sets), *n_entries (total (site, k) entries),
+ * *total_shots. Errors: PTSBE_ERR_INVALID, PTSBE_ERR_UNSUPPORTED (TOPK/BAND with a site whose
+ * q_0 is not the strict maximum), PTSBE_ERR_OOM. */
+PTSBE_API int ptsbe_sample_kraus(ptsbe_ctx* ctx, uint32_t circuit_id, const ptsbe_pts_params* params, uint64_t seed,
+                       uint32_t* set_id, uint32_t* count, uint64_t* n_entries, uint64_t* total_shots);
+
+/* Caller buffers for a set export; any pointer may be NULL. Sizes: offsets/shot_offsets
+ * [count+1], sites/kidx [n_entries], mult/q/shots [count]. These are the error-provenance labels
+ * of Sec. 3 ("lightweight metadata"): shot g belongs to the set a with
+ * shot_offsets[a] <= g < shot_offsets[a+1]. */
+typedef struct {
+    uint32_t* offsets;
+    uint32_t* sites;
+    uint8_t* kidx;
+    uint64_t* mult;
+    double* q;
+    uint64_t* shots;
+    uint64_t* shot_offsets;
+} ptsbe_set_view;
+
+PTSBE_API int ptsbe_set_export(ptsbe_ctx* ctx, uint32_t set_id, const ptsbe_set_view* out);
+PTSBE_API int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched execution (Sec. 3)                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+enum {
+    /* Prefix reuse: a set whose (site, k) list extends another set of the same call starts from
+     * that set's state at the first differing site instead of from |0...0>. The parent writes
+     * its state into the child's output slot when it reaches the branch site. */
+    PTSBE_EVOLVE_PREFIX_REUSE = 1u
+};
+
+/* Prepares the states of sets [first, first + count) of set_id (each once, Sec. 3):
+ *   psi_alpha = normalise( prod_ops (K_{s,k_s} or U_{s,k_s}) G ... |0...0> ),
+ * the Kraus operators of alpha inserted at their sites; unitary-mixture sites apply U_k, other
+ * sites apply K_k, and the state is renormalised at the end (Sec. 2.2 renormalisation; deferred
+ * renormalisation gives the same normalised state). Outputs (device, caller-owned):
+ *   d_states  complex64 [count][2^n], 16-byte aligned; written completely
+ *   d_weights float64 [count]: w_alpha = prod_{mixture sites} q_{s,k_s} * ||unnormalised psi||^2,
+ *             the Born probability of the Kraus branch (may be NULL)
+ *   d_status  uint8 [count]: 0 ok, 1 null (w_alpha < 1e-6 q_alpha: a branch the state cannot take,
+ *             e.g. damping a qubit with no |1> population; its state is zeroed) (may be NULL).
+ * Asynchronous on the context stream. Errors: PTSBE_ERR_INVALID (range, null pointer, alignment),
+ * PTSBE_ERR_OOM (workspace), PTSBE_ERR_CUDA (launch). */
+PTSBE_API int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
+                       double* d_weights, uint8_t* d_status, uint32_t flags);
+
+/* Draws all m_alpha shots of sets [first, first + count) from their prepared states (Sec. 3,
+ * "sampling all m_alpha desired quantum bitstrings at once"). For state alpha with
+ * P_i = |psi_i|^2 and C its FP64 inclusive prefix, T = C[2^n - 1]: shot j uses
+ * u = U53(Philox(seed; j_lo, j_hi, alpha, 2)) (alpha = index of the set within set_id) and returns
+ * the smallest i with u*T < C[i] (2^n - 1 if none). Outputs:
+ *   d_bits  uint32 [sum of m_alpha over the range], set-major: shot j of set first+a lands at
+ *           shot_offsets[first+a] - shot_offsets[first] + j. Null states (d_status 1) yield
+ *           0xFFFFFFFF. d_bits_capacity = number of uint32 slots available.
+ * d_states as written by ptsbe_evolve_batch for the same range; d_status may be NULL.
+ * Asynchronous. Errors: PTSBE_ERR_BUFFER_TOO_SMALL, PTSBE_ERR_INVALID, PTSBE_ERR_OOM. */
+PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
+                       const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Traditional trajectories (Algorithm 1), one prepared state per shot, for comparison        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Simulates shots [first_shot, first_shot + n_shots) of the traditional trajectory loop: at
+ * noise site s shot j draws u = U53(Philox(seed; s, j_lo, j_hi, 3)); a unitary mixture picks
+ * k = index(u, {q}) and applies U_k; a general channel computes p_i = <psi|K_i^dag K_i|psi> (FP64
+ * accumulation), picks k = index(u, {p}) and applies K_k / sqrt(p_k). The final state is read out
+ * once with u = U53(Philox(seed; j_lo, j_hi, 0, 5)) by the inverse-CDF rule of
+ * ptsbe_sample_shots. Outputs: d_bits uint32 [n_shots]; d_kraus uint8 [n_shots][S] chosen k per
+ * site (may be NULL). Uses library workspace for the states in flight. Asynchronous. */
+PTSBE_API int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64_t first_shot,
+                      uint64_t n_shots, uint32_t* d_bits, uint8_t* d_kraus);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Instrumentation                                                                           */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Number of CUDA kernels the library has enqueued since it was loaded (all contexts). */
+PTSBE_API int ptsbe_kernel_launches(uint64_t* count);
+
+/* Host-to-device bytes the library has copied since it was loaded (circuit tables, Kraus-set
+ * entries, per-call schedules). */
+PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
+
+/* Kernel classes of the timing counters. */
+enum {
+    PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
+    PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* renormalisation pass of ptsbe_evolve_batch (n > 14)      */
+    PTSBE_TIMER_SAMPLE = 2,           /* ptsbe_sample_shots                                       */
+    PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
+    PTSBE_TIMER_CLASSES = 4
+};
+
+/* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and
+ * its algorithmic bytes are added up per kernel class (state bytes read and written by a pass,
+ * checkpoint writes, 4 bytes per shot ...). Adds two event records per launch. */
+PTSBE_API int ptsbe_set_timing(ptsbe_ctx* ctx, int enable);
+
+/* Waits for the timed launches and returns, for one kernel class, the summed event time in
+ * milliseconds, the number of launches and the algorithmic bytes (any pointer may be NULL);
+ * reset != 0 clears the counters afterwards. */
+PTSBE_API int ptsbe_get_timing(ptsbe_ctx* ctx, int kernel_class, double* ms, uint64_t* launches, double* bytes,
+                               int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTSBE_H */

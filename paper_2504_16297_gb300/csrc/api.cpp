@@ -1,0 +1,582 @@
+// C ABI of libptsbe: contexts, registries, workspace and the host-side scheduling of the kernels.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace ptsbe {
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    const int st = (e == cudaErrorMemoryAllocation) ? PTSBE_ERR_OOM : PTSBE_ERR_CUDA;
+    fail(st, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t sample_global_scratch_doubles(int n);
+
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_h2d{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void count_h2d(uint64_t bytes) { g_h2d.fetch_add(bytes, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Optional per-kernel-class timing: CUDA events recorded on the context stream around each
+// launch, plus the algorithmic bytes of that launch.
+struct ClassTimer {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms = 0;
+    uint64_t launches = 0;
+    double bytes = 0;
+};
+
+}  // namespace ptsbe
+
+using namespace ptsbe;
+
+struct ptsbe_ctx {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+    std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
+    std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
+    uint32_t next_circuit = 1, next_set = 1;
+    DevBuf nodes, part, scale, items, scratch, pershot;
+    std::vector<unsigned char> host_blob;
+    bool timing = false;
+    ClassTimer timers[PTSBE_TIMER_CLASSES];
+
+    cudaEvent_t take_event(ClassTimer& t) {
+        if (!t.pool.empty()) { cudaEvent_t e = t.pool.back(); t.pool.pop_back(); return e; }
+        cudaEvent_t e;
+        PTSBE_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    // Brackets a launch of kernel class `cls` (no-op when timing is off).
+    template <class F>
+    void timed(int cls, double bytes, F&& launch) {
+        if (!timing) { launch(); return; }
+        ClassTimer& t = timers[cls];
+        cudaEvent_t a = take_event(t), b = take_event(t);
+        PTSBE_CUDA(cudaEventRecord(a, stream));
+        launch();
+        PTSBE_CUDA(cudaEventRecord(b, stream));
+        t.pending.push_back({a, b});
+        t.launches += 1;
+        t.bytes += bytes;
+    }
+    void collect_timers() {
+        for (ClassTimer& t : timers) {
+            for (auto& ab : t.pending) {
+                PTSBE_CUDA(cudaEventSynchronize(ab.second));
+                float ms = 0;
+                PTSBE_CUDA(cudaEventElapsedTime(&ms, ab.first, ab.second));
+                t.ms += ms;
+                t.pool.push_back(ab.first);
+                t.pool.push_back(ab.second);
+            }
+            t.pending.clear();
+        }
+    }
+    void free_timers() {
+        for (ClassTimer& t : timers) {
+            for (auto& ab : t.pending) { cudaEventDestroy(ab.first); cudaEventDestroy(ab.second); }
+            for (cudaEvent_t e : t.pool) cudaEventDestroy(e);
+            t = ClassTimer{};
+        }
+    }
+
+    bool has_device() const { return device >= 0; }
+    void need_device() const {
+        if (!has_device()) fail(PTSBE_ERR_NO_DEVICE, "device entry point on a host-only context");
+    }
+    void use_device() const { PTSBE_CUDA(cudaSetDevice(device)); }
+
+    // Grows a workspace buffer; waits for in-flight work that may still use the old one.
+    void* ws(DevBuf& b, size_t bytes) {
+        if (bytes <= b.cap && b.p) return b.p;
+        PTSBE_CUDA(cudaStreamSynchronize(stream));
+        if (b.p) { PTSBE_CUDA(cudaFree(b.p)); b.p = nullptr; b.cap = 0; }
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+        void* p = nullptr;
+        const cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "workspace allocation of " + std::to_string(want) + " bytes failed"); }
+        b.p = p; b.cap = want;
+        return p;
+    }
+    void free_buf(DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; b.cap = 0; }
+
+    Circuit& circuit(uint32_t id) {
+        auto it = circuits.find(id);
+        if (it == circuits.end()) fail(PTSBE_ERR_INVALID, "unknown circuit id " + std::to_string(id));
+        return *it->second;
+    }
+    KSet& set(uint32_t id) {
+        auto it = sets.find(id);
+        if (it == sets.end()) fail(PTSBE_ERR_INVALID, "unknown set id " + std::to_string(id));
+        return *it->second;
+    }
+};
+
+namespace {
+
+template <class F>
+int guarded(ptsbe_ctx* ctx, F&& f) {
+    if (!ctx) return PTSBE_ERR_INVALID;
+    try {
+        f();
+        return PTSBE_OK;
+    } catch (const Error& e) {
+        ctx->err = e.what();
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        ctx->err = "host allocation failed";
+        return PTSBE_ERR_OOM;
+    } catch (const std::exception& e) {
+        ctx->err = e.what();
+        return PTSBE_ERR_INVALID;
+    }
+}
+
+template <class T>
+T* dev_upload(const std::vector<T>& v) {
+    if (v.empty()) return nullptr;
+    T* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+    if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "device table allocation failed"); }
+    PTSBE_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    count_h2d(v.size() * sizeof(T));
+    return p;
+}
+
+void free_device_circuit(DeviceCircuit& d) {
+    cudaFree(d.ops); cudaFree(d.micro); cudaFree(d.mats); cudaFree(d.chans);
+    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.hi);
+    d = DeviceCircuit{};
+}
+
+void upload_circuit(const Circuit& c, const Plan& P, DeviceCircuit& d) {
+    d.ops = dev_upload(c.dops);
+    d.micro = dev_upload(c.dmicro);
+    d.mats = dev_upload(c.dmats);
+    d.chans = dev_upload(c.dchans);
+    d.site_op = dev_upload(c.site_op);
+    d.stages = dev_upload(P.stages);
+    d.hi = dev_upload(P.hi);
+}
+
+// Builds a blob of aligned arrays on the host and returns the device pointers after one upload.
+struct Blob {
+    std::vector<unsigned char>& buf;
+    explicit Blob(std::vector<unsigned char>& b) : buf(b) { buf.clear(); }
+    template <class T>
+    size_t add(const std::vector<T>& v) {
+        size_t off = (buf.size() + 255) & ~size_t(255);
+        buf.resize(off + std::max<size_t>(v.size() * sizeof(T), 1));
+        if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+void ensure_set_on_device(KSet& s) {
+    if (s.d_site || s.site.empty()) return;
+    s.d_site = dev_upload(s.site);
+    s.d_k = dev_upload(s.k);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
+    if (!out) return PTSBE_ERR_INVALID;
+    *out = nullptr;
+    std::unique_ptr<ptsbe_ctx> ctx;
+    try {
+        ctx.reset(new ptsbe_ctx());
+    } catch (...) {
+        return PTSBE_ERR_OOM;
+    }
+    ctx->device = device < 0 ? -1 : device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (device >= 0) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
+            (void)cudaGetLastError();
+            return PTSBE_ERR_NO_DEVICE;
+        }
+        if (cudaSetDevice(device) != cudaSuccess) { (void)cudaGetLastError(); return PTSBE_ERR_CUDA; }
+    }
+    *out = ctx.release();
+    return PTSBE_OK;
+}
+
+int ptsbe_destroy(ptsbe_ctx* ctx) {
+    if (!ctx) return PTSBE_ERR_INVALID;
+    if (ctx->has_device()) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (auto& kv : ctx->circuits) { free_device_circuit(kv.second->dev); free_device_circuit(kv.second->dev_pershot); }
+        for (auto& kv : ctx->sets) { cudaFree(kv.second->d_site); cudaFree(kv.second->d_k); }
+        ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
+        ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
+        ctx->free_timers();
+    }
+    delete ctx;
+    return PTSBE_OK;
+}
+
+int ptsbe_set_stream(ptsbe_ctx* ctx, void* cuda_stream) {
+    return guarded(ctx, [&] { ctx->stream = (cudaStream_t)cuda_stream; });
+}
+
+const char* ptsbe_last_error(const ptsbe_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+int ptsbe_synchronize(ptsbe_ctx* ctx) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        ctx->use_device();
+        PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
+        PTSBE_CUDA(cudaGetLastError());
+    });
+}
+
+int ptsbe_register_circuit(ptsbe_ctx* ctx, uint32_t n_qubits, const ptsbe_op* ops, uint64_t n_ops,
+                           const ptsbe_channel* channels, uint32_t n_channels, const double* custom_gates,
+                           uint32_t n_custom, uint32_t* circuit_id) {
+    return guarded(ctx, [&] {
+        if (!circuit_id) fail(PTSBE_ERR_INVALID, "circuit_id is NULL");
+        if (n_qubits < 1 || n_qubits > (uint32_t)kMaxQubits) fail(PTSBE_ERR_INVALID, "n_qubits must be in [1, 32]");
+        if (n_ops && !ops) fail(PTSBE_ERR_INVALID, "ops is NULL");
+        if (n_channels && !channels) fail(PTSBE_ERR_INVALID, "channels is NULL");
+        auto c = std::make_unique<Circuit>();
+        c->n = n_qubits;
+        c->ch.resize(n_channels);
+        for (uint32_t j = 0; j < n_channels; ++j) build_channel(channels[j], c->ch[j]);
+        register_ops(*c, ops, n_ops, custom_gates, n_custom);
+        build_device_ops(*c);
+        c->plan = make_plan(*c, kTileMax, false);
+        if (ctx->has_device()) {
+            ctx->use_device();
+            upload_circuit(*c, c->plan, c->dev);
+        }
+        const uint32_t id = ctx->next_circuit++;
+        ctx->circuits[id] = std::move(c);
+        *circuit_id = id;
+    });
+}
+
+int ptsbe_circuit_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* n_qubits, uint64_t* n_sites, uint64_t* n_gates) {
+    return guarded(ctx, [&] {
+        Circuit& c = ctx->circuit(circuit_id);
+        if (n_qubits) *n_qubits = c.n;
+        if (n_sites) *n_sites = c.site_op.size();
+        if (n_gates) *n_gates = c.n_gates;
+    });
+}
+
+int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
+    return guarded(ctx, [&] {
+        Circuit& c = ctx->circuit(circuit_id);
+        if (ctx->has_device()) {
+            ctx->use_device();
+            PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
+            free_device_circuit(c.dev);
+            free_device_circuit(c.dev_pershot);
+        }
+        ctx->circuits.erase(circuit_id);
+    });
+}
+
+int ptsbe_sample_kraus(ptsbe_ctx* ctx, uint32_t circuit_id, const ptsbe_pts_params* params, uint64_t seed,
+                       uint32_t* set_id, uint32_t* count, uint64_t* n_entries, uint64_t* total_shots) {
+    return guarded(ctx, [&] {
+        if (!params) fail(PTSBE_ERR_INVALID, "params is NULL");
+        Circuit& c = ctx->circuit(circuit_id);
+        auto s = std::make_unique<KSet>();
+        s->circuit = circuit_id;
+        pts_run(c, *params, seed, *s);
+        if (s->count() > 0xFFFFFFF0u) fail(PTSBE_ERR_UNSUPPORTED, "too many sets");
+        const uint32_t id = ctx->next_set++;
+        if (count) *count = s->count();
+        if (n_entries) *n_entries = s->site.size();
+        if (total_shots) *total_shots = s->shot_off.back();
+        ctx->sets[id] = std::move(s);
+        if (set_id) *set_id = id;
+    });
+}
+
+int ptsbe_set_export(ptsbe_ctx* ctx, uint32_t set_id, const ptsbe_set_view* out) {
+    return guarded(ctx, [&] {
+        if (!out) fail(PTSBE_ERR_INVALID, "out is NULL");
+        const KSet& s = ctx->set(set_id);
+        const uint32_t n = s.count();
+        if (out->offsets) std::memcpy(out->offsets, s.off.data(), (n + 1) * sizeof(uint32_t));
+        if (out->sites && !s.site.empty()) std::memcpy(out->sites, s.site.data(), s.site.size() * sizeof(uint32_t));
+        if (out->kidx && !s.k.empty()) std::memcpy(out->kidx, s.k.data(), s.k.size());
+        if (out->mult && n) std::memcpy(out->mult, s.mult.data(), n * sizeof(uint64_t));
+        if (out->q && n) std::memcpy(out->q, s.q.data(), n * sizeof(double));
+        if (out->shots && n) std::memcpy(out->shots, s.shots.data(), n * sizeof(uint64_t));
+        if (out->shot_offsets) std::memcpy(out->shot_offsets, s.shot_off.data(), (n + 1) * sizeof(uint64_t));
+    });
+}
+
+int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id) {
+    return guarded(ctx, [&] {
+        KSet& s = ctx->set(set_id);
+        if (ctx->has_device() && s.d_site) {
+            ctx->use_device();
+            PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
+            cudaFree(s.d_site); cudaFree(s.d_k);
+        }
+        ctx->sets.erase(set_id);
+    });
+}
+
+int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
+                       double* d_weights, uint8_t* d_status, uint32_t flags) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        KSet& s = ctx->set(set_id);
+        Circuit& c = ctx->circuit(s.circuit);
+        if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (count == 0) return;
+        if (!d_states) fail(PTSBE_ERR_INVALID, "d_states is NULL");
+        if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
+        if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
+        ctx->use_device();
+        ensure_set_on_device(s);
+        const Plan& P = c.plan;
+        const uint32_t S = (uint32_t)c.site_op.size();
+        const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
+
+        // --- node tables ---
+        std::vector<uint32_t> ebeg(count), eend(count), start(count), depth(count), parent(count, UINT32_MAX);
+        std::vector<uint8_t> fresh(count);
+        std::vector<double> wmix(count), qa(count);
+        std::unordered_map<std::string, uint32_t> index;
+        auto key_of = [&](uint32_t alpha, uint32_t len) {
+            std::string k;
+            k.resize(len * 5);
+            for (uint32_t i = 0; i < len; ++i) {
+                std::memcpy(&k[5 * i], &s.site[s.off[alpha] + i], 4);
+                k[5 * i + 4] = (char)s.k[s.off[alpha] + i];
+            }
+            return k;
+        };
+        uint32_t max_depth = 0;
+        for (uint32_t a = 0; a < count; ++a) {
+            const uint32_t alpha = first + a;
+            const uint32_t len = s.off[alpha + 1] - s.off[alpha];
+            ebeg[a] = s.off[alpha]; eend[a] = s.off[alpha + 1];
+            qa[a] = s.q[alpha];
+            if (reuse) {
+                for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
+                    auto it = index.find(key_of(alpha, (uint32_t)p));
+                    if (it != index.end()) { parent[a] = it->second; break; }
+                }
+                index.emplace(key_of(alpha, len), a);
+            }
+            if (parent[a] != UINT32_MAX) {
+                const uint32_t plen = s.off[first + parent[a] + 1] - s.off[first + parent[a]];
+                start[a] = c.site_op[s.site[s.off[alpha] + plen]];
+                fresh[a] = 0;
+                depth[a] = depth[parent[a]] + 1;
+            } else {
+                start[a] = 0; fresh[a] = 1; depth[a] = 0;
+            }
+            max_depth = std::max(max_depth, depth[a]);
+            // prod over unitary-mixture sites of q_{s,k_s}
+            double w = 1.0;
+            uint32_t e = s.off[alpha];
+            for (uint32_t site = 0; site < S; ++site) {
+                uint32_t k = 0;
+                if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
+                const HostChannel& ch = c.ch[c.site_ch[site]];
+                if (ch.mixture) w *= ch.q[k];
+            }
+            wmix[a] = w;
+        }
+        // children grouped by parent, ascending branch op
+        std::vector<uint32_t> cbeg(count, 0), cend(count, 0), child_op, child_node;
+        {
+            std::vector<std::vector<std::pair<uint32_t, uint32_t>>> kids(count);
+            for (uint32_t a = 0; a < count; ++a)
+                if (parent[a] != UINT32_MAX) kids[parent[a]].push_back({start[a], a});
+            for (uint32_t a = 0; a < count; ++a) {
+                std::sort(kids[a].begin(), kids[a].end());
+                cbeg[a] = (uint32_t)child_op.size();
+                for (auto& kv : kids[a]) { child_op.push_back(kv.first); child_node.push_back(kv.second); }
+                cend[a] = (uint32_t)child_op.size();
+            }
+        }
+        // launch lists: generation g, stage j -> nodes of depth g whose start stage <= j
+        const uint32_t J = (uint32_t)P.stages.size();
+        std::vector<uint32_t> lists;
+        std::vector<std::pair<size_t, uint32_t>> launches;  // (offset, count) per (g, j)
+        std::vector<uint32_t> sstage(count);
+        for (uint32_t a = 0; a < count; ++a) sstage[a] = fresh[a] ? 0 : (uint32_t)P.op_stage[start[a]];
+        for (uint32_t g = 0; g <= max_depth; ++g)
+            for (uint32_t j = 0; j < J; ++j) {
+                const size_t off = lists.size();
+                for (uint32_t a = 0; a < count; ++a)
+                    if (depth[a] == g && sstage[a] <= j) lists.push_back(a);
+                launches.push_back({off, (uint32_t)(lists.size() - off)});
+            }
+        Blob blob(ctx->host_blob);
+        const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_start = blob.add(start);
+        const size_t o_fresh = blob.add(fresh), o_cbeg = blob.add(cbeg), o_cend = blob.add(cend);
+        const size_t o_cop = blob.add(child_op), o_cnode = blob.add(child_node);
+        const size_t o_wmix = blob.add(wmix), o_q = blob.add(qa), o_lists = blob.add(lists);
+        unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
+        PTSBE_CUDA(cudaMemcpyAsync(dblob, ctx->host_blob.data(), ctx->host_blob.size(), cudaMemcpyHostToDevice, ctx->stream));
+        count_h2d(ctx->host_blob.size());
+
+        EvolveArgs A{};
+        A.ops = c.dev.ops; A.micro = c.dev.micro; A.mats = c.dev.mats; A.chans = c.dev.chans;
+        A.site_op = c.dev.site_op; A.stages = c.dev.stages; A.hi = c.dev.hi;
+        A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
+        A.ent_site = s.d_site; A.ent_k = s.d_k;
+        A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
+        A.node_start = (const uint32_t*)(dblob + o_start); A.node_fresh = (const uint8_t*)(dblob + o_fresh);
+        A.node_cbeg = (const uint32_t*)(dblob + o_cbeg); A.node_cend = (const uint32_t*)(dblob + o_cend);
+        A.child_op = (const uint32_t*)(dblob + o_cop); A.child_node = (const uint32_t*)(dblob + o_cnode);
+        A.wmix = (const double*)(dblob + o_wmix); A.qalpha = (const double*)(dblob + o_q);
+        A.states = (float2*)d_states;
+        A.weights = d_weights; A.status = d_status;
+        const int ob = (int)c.n - P.tb;
+        float* d_scale = nullptr;
+        if (ob > 0) {
+            A.part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
+            d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
+        }
+        const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
+        const double sbytes = 8.0 * (double)(1ull << c.n);
+        std::vector<uint32_t> kids_in_stage;
+        size_t li = 0;
+        for (uint32_t g = 0; g <= max_depth; ++g)
+            for (uint32_t j = 0; j < J; ++j, ++li) {
+                const auto& L = launches[li];
+                if (L.second == 0) continue;
+                // algorithmic bytes: read (unless started from |0>), write, checkpoints for children
+                double bytes = 0;
+                for (size_t t = L.first; t < L.first + L.second; ++t) {
+                    const uint32_t a = lists[t];
+                    bytes += (fresh[a] && j == 0) ? sbytes : 2 * sbytes;
+                    for (uint32_t ci = cbeg[a]; ci < cend[a]; ++ci)
+                        if ((uint32_t)P.op_stage[child_op[ci]] == j) bytes += sbytes;
+                }
+                ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
+                    launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream);
+                });
+            }
+        if (ob > 0)
+            ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
+    });
+}
+
+int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
+                       const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        KSet& s = ctx->set(set_id);
+        Circuit& c = ctx->circuit(s.circuit);
+        if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (count == 0) return;
+        const uint64_t base = s.shot_off[first];
+        const uint64_t total = s.shot_off[first + count] - base;
+        if (total == 0) return;
+        if (!d_states || !d_bits) fail(PTSBE_ERR_INVALID, "null device pointer");
+        if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
+        if (d_bits_capacity < total) fail(PTSBE_ERR_BUFFER_TOO_SMALL, "d_bits holds " + std::to_string(d_bits_capacity) +
+                                                                          " shots, the range needs " + std::to_string(total));
+        if (c.n > 32) fail(PTSBE_ERR_UNSUPPORTED, "outcomes are 32-bit");
+        ctx->use_device();
+        SampleArgs A{};
+        A.n = (int)c.n;
+        A.states = (const float2*)d_states;
+        A.status = d_status;
+        A.seed = seed;
+        A.bits = d_bits;
+        if ((int)c.n <= sample_cluster_max_qubits()) {
+            // split heavy states so the clusters stay busy; every item rebuilds its state's CDF
+            const uint64_t chunk = std::max<uint64_t>(1u << 14, (total + 1023) / 1024);
+            std::vector<SampleItem> items;
+            for (uint32_t a = 0; a < count; ++a) {
+                const uint32_t alpha = first + a;
+                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+                for (uint64_t j0 = 0; j0 < m; j0 += chunk)
+                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0});
+            }
+            SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
+            PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
+            count_h2d(items.size() * sizeof(SampleItem));
+            const double bytes = 8.0 * (double)(1ull << c.n) * (double)items.size() + 4.0 * (double)total;
+            ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream); });
+        } else {
+            A.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles((int)c.n) * sizeof(double));
+            for (uint32_t a = 0; a < count; ++a) {
+                const uint32_t alpha = first + a;
+                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+                const double sb = 8.0 * (double)(1ull << c.n);
+                if (m) ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
+            }
+        }
+    });
+}
+
+int ptsbe_set_timing(ptsbe_ctx* ctx, int enable) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        ctx->timing = enable != 0;
+    });
+}
+
+int ptsbe_get_timing(ptsbe_ctx* ctx, int kernel_class, double* ms, uint64_t* launches, double* bytes, int reset) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        if (kernel_class < 0 || kernel_class >= PTSBE_TIMER_CLASSES) fail(PTSBE_ERR_INVALID, "unknown kernel class");
+        ctx->use_device();
+        ctx->collect_timers();
+        ClassTimer& t = ctx->timers[kernel_class];
+        if (ms) *ms = t.ms;
+        if (launches) *launches = t.launches;
+        if (bytes) *bytes = t.bytes;
+        if (reset) { t.ms = 0; t.launches = 0; t.bytes = 0; }
+    });
+}
+
+int ptsbe_kernel_launches(uint64_t* count) {
+    if (!count) return PTSBE_ERR_INVALID;
+    *count = launches_so_far();
+    return PTSBE_OK;
+}
+
+int ptsbe_h2d_bytes(uint64_t* bytes) {
+    if (!bytes) return PTSBE_ERR_INVALID;
+    *bytes = g_h2d.load(std::memory_order_relaxed);
+    return PTSBE_OK;
+}
+
+int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64_t first_shot, uint64_t n_shots,
+                      uint32_t* d_bits, uint8_t* d_kraus) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        (void)circuit_id; (void)seed; (void)first_shot; (void)n_shots; (void)d_bits; (void)d_kraus;
+        fail(PTSBE_ERR_UNSUPPORTED, "per-shot trajectories are not built yet");
+    });
+}
+
+}  // extern "C"

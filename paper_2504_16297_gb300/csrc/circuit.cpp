@@ -1,0 +1,436 @@
+// Circuit registration (Fig. 1) and evolution planning.
+//
+// Channels are CPTP Kraus sets (Sec. 2.2). A channel whose every operator satisfies
+// K_k^dag K_k = q_k I is a unitary mixture (Sec. 2.2, item 2): its branch probabilities do not
+// depend on the state, it is applied as U_k = K_k / sqrt(q_k) and needs no norm.
+//
+// Evolution plan: a state of n qubits is processed in tiles of 2^tb amplitudes held in shared
+// memory. When n <= tb one tile is the whole state and the whole circuit runs in one pass.
+// Otherwise the op sequence is cut greedily into stages whose ops all act inside one set of tb
+// qubits; the set always contains the lb lowest qubits so each tile is made of contiguous
+// 2^lb-amplitude segments (coalesced loads).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace ptsbe {
+
+namespace {
+
+const double kSqrtHalf = 0.70710678118654752440;
+
+void gate_matrix(uint32_t g, const double* p, const double* custom, cd* m, int& dim) {
+    const cd I(0, 1);
+    for (int i = 0; i < 16; ++i) m[i] = 0;
+    const double th = p[0], ph = p[1], la = p[2];
+    dim = 2;
+    switch (g) {
+    case PTSBE_G_I: m[0] = 1; m[3] = 1; break;
+    case PTSBE_G_X: m[1] = 1; m[2] = 1; break;
+    case PTSBE_G_Y: m[1] = -I; m[2] = I; break;
+    case PTSBE_G_Z: m[0] = 1; m[3] = -1; break;
+    case PTSBE_G_H: m[0] = kSqrtHalf; m[1] = kSqrtHalf; m[2] = kSqrtHalf; m[3] = -kSqrtHalf; break;
+    case PTSBE_G_S: m[0] = 1; m[3] = I; break;
+    case PTSBE_G_SDG: m[0] = 1; m[3] = -I; break;
+    case PTSBE_G_T: m[0] = 1; m[3] = std::polar(1.0, M_PI / 4); break;
+    case PTSBE_G_TDG: m[0] = 1; m[3] = std::polar(1.0, -M_PI / 4); break;
+    case PTSBE_G_RX: m[0] = std::cos(th / 2); m[1] = -I * std::sin(th / 2); m[2] = m[1]; m[3] = m[0]; break;
+    case PTSBE_G_RY: m[0] = std::cos(th / 2); m[1] = -std::sin(th / 2); m[2] = std::sin(th / 2); m[3] = m[0]; break;
+    case PTSBE_G_RZ: m[0] = std::polar(1.0, -th / 2); m[3] = std::polar(1.0, th / 2); break;
+    case PTSBE_G_U3:
+        m[0] = std::cos(th / 2);
+        m[1] = -std::polar(1.0, la) * std::sin(th / 2);
+        m[2] = std::polar(1.0, ph) * std::sin(th / 2);
+        m[3] = std::polar(1.0, ph + la) * std::cos(th / 2);
+        break;
+    case PTSBE_G_U1:
+        m[0] = cd(custom[0], custom[1]); m[1] = cd(custom[2], custom[3]);
+        m[2] = cd(custom[8], custom[9]); m[3] = cd(custom[10], custom[11]);
+        break;
+    case PTSBE_G_CX: dim = 4; m[0] = 1; m[5] = 1; m[11] = 1; m[14] = 1; break;
+    case PTSBE_G_CZ: dim = 4; m[0] = 1; m[5] = 1; m[10] = 1; m[15] = -1; break;
+    case PTSBE_G_SWAP: dim = 4; m[0] = 1; m[6] = 1; m[9] = 1; m[15] = 1; break;
+    case PTSBE_G_U2: dim = 4; for (int i = 0; i < 16; ++i) m[i] = cd(custom[2 * i], custom[2 * i + 1]); break;
+    default: fail(PTSBE_ERR_INVALID, "unknown gate code " + std::to_string(g));
+    }
+}
+
+uint32_t gate_arity(uint32_t g) {
+    return (g == PTSBE_G_CX || g == PTSBE_G_CZ || g == PTSBE_G_SWAP || g == PTSBE_G_U2) ? 2 : 1;
+}
+
+void pauli(int a, cd* m) {
+    const cd I(0, 1);
+    m[0] = m[1] = m[2] = m[3] = 0;
+    if (a == 0) { m[0] = 1; m[3] = 1; }
+    if (a == 1) { m[1] = 1; m[2] = 1; }
+    if (a == 2) { m[1] = -I; m[2] = I; }
+    if (a == 3) { m[0] = 1; m[3] = -1; }
+}
+
+}  // namespace
+
+// Builds the Kraus operators, nominal probabilities and unitary-mixture data of one channel.
+void build_channel(const ptsbe_channel& in, HostChannel& c) {
+    c.kind = in.kind; c.arity = in.arity; c.nk = in.n_kraus; c.param = in.param;
+    if (in.arity < 1 || in.arity > 2) fail(PTSBE_ERR_INVALID, "channel arity must be 1 or 2");
+    if (in.n_kraus < 1 || in.n_kraus > (uint32_t)kMaxKraus) fail(PTSBE_ERR_INVALID, "channel needs 1..16 Kraus operators");
+    c.dim = 1u << in.arity;
+    const uint32_t d = c.dim, dd = d * d;
+    const double p = in.param;
+    c.K.assign((size_t)c.nk * dd, 0.0);
+    c.q.assign(c.nk, 0.0);
+    c.U.clear();
+    auto need = [&](uint32_t ar, uint32_t nk) {
+        if (in.arity != ar || in.n_kraus != nk) fail(PTSBE_ERR_INVALID, "channel arity/n_kraus mismatch for its kind");
+        if (!(p >= 0 && p <= 1)) fail(PTSBE_ERR_INVALID, "channel strength must lie in [0, 1]");
+    };
+    cd P[4][4];
+    for (int a = 0; a < 4; ++a) pauli(a, P[a]);
+    bool pauli_mixture = false;
+    switch (in.kind) {
+    case PTSBE_CH_DEPOL1:
+        need(1, 4);
+        for (int a = 0; a < 4; ++a) {
+            const double s = a == 0 ? std::sqrt(1 - p) : std::sqrt(p / 3);
+            for (int i = 0; i < 4; ++i) c.K[a * 4 + i] = s * P[a][i];
+            c.q[a] = a == 0 ? 1 - p : p / 3;
+        }
+        pauli_mixture = true;
+        break;
+    case PTSBE_CH_DEPOL2:
+        need(2, 16);
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const int k = 4 * a + b;
+                const double s = k == 0 ? std::sqrt(1 - p) : std::sqrt(p / 15);
+                for (int r = 0; r < 4; ++r)
+                    for (int col = 0; col < 4; ++col)
+                        c.K[k * 16 + r * 4 + col] = s * P[a][(r >> 1) * 2 + (col >> 1)] * P[b][(r & 1) * 2 + (col & 1)];
+                c.q[k] = k == 0 ? 1 - p : p / 15;
+            }
+        pauli_mixture = true;
+        break;
+    case PTSBE_CH_AMPDAMP:
+        need(1, 2);
+        c.K[0] = 1; c.K[3] = std::sqrt(1 - p);
+        c.K[5] = std::sqrt(p);
+        c.q[0] = 1 - p / 2; c.q[1] = p / 2;
+        break;
+    case PTSBE_CH_BITFLIP:
+    case PTSBE_CH_PHASEFLIP: {
+        need(1, 2);
+        const int e = in.kind == PTSBE_CH_BITFLIP ? 1 : 3;
+        for (int i = 0; i < 4; ++i) { c.K[i] = std::sqrt(1 - p) * P[0][i]; c.K[4 + i] = std::sqrt(p) * P[e][i]; }
+        c.q[0] = 1 - p; c.q[1] = p;
+        pauli_mixture = true;
+        break;
+    }
+    case PTSBE_CH_CUSTOM:
+        if (!in.kraus) fail(PTSBE_ERR_INVALID, "CUSTOM channel needs Kraus matrices");
+        for (uint32_t k = 0; k < c.nk; ++k) {
+            double s = 0;
+            for (uint32_t i = 0; i < dd; ++i) {
+                const double re = in.kraus[2 * (k * dd + i)], im = in.kraus[2 * (k * dd + i) + 1];
+                if (!std::isfinite(re) || !std::isfinite(im)) fail(PTSBE_ERR_INVALID, "non-finite Kraus entry");
+                c.K[k * dd + i] = cd(re, im);
+                s += re * re + im * im;
+            }
+            c.q[k] = s / d;
+        }
+        break;
+    default:
+        fail(PTSBE_ERR_INVALID, "unknown channel kind");
+    }
+    // CPTP: sum_k K_k^dag K_k = I
+    double worst = 0;
+    for (uint32_t r = 0; r < d; ++r)
+        for (uint32_t col = 0; col < d; ++col) {
+            cd s = 0;
+            for (uint32_t k = 0; k < c.nk; ++k)
+                for (uint32_t i = 0; i < d; ++i) s += std::conj(c.K[k * dd + i * d + r]) * c.K[k * dd + i * d + col];
+            worst = std::max(worst, std::abs(s - (r == col ? 1.0 : 0.0)));
+        }
+    if (worst > 1e-10) fail(PTSBE_ERR_NOT_CPTP, "channel is not trace preserving (|sum K^dag K - I| = " + std::to_string(worst) + ")");
+    // unitary mixture: K_k^dag K_k = q_k I
+    c.mixture = true;
+    for (uint32_t k = 0; k < c.nk && c.mixture; ++k)
+        for (uint32_t r = 0; r < d; ++r)
+            for (uint32_t col = 0; col < d; ++col) {
+                cd s = 0;
+                for (uint32_t i = 0; i < d; ++i) s += std::conj(c.K[k * dd + i * d + r]) * c.K[k * dd + i * d + col];
+                if (std::abs(s - (r == col ? c.q[k] : 0.0)) > 1e-12) c.mixture = false;
+            }
+    if (c.mixture) {
+        c.U.assign((size_t)c.nk * dd, 0.0);
+        for (uint32_t k = 0; k < c.nk; ++k) {
+            if (pauli_mixture) {
+                // exact Pauli products
+                if (c.arity == 1) {
+                    int a = in.kind == PTSBE_CH_DEPOL1 ? (int)k : (k == 0 ? 0 : (in.kind == PTSBE_CH_BITFLIP ? 1 : 3));
+                    for (int i = 0; i < 4; ++i) c.U[k * 4 + i] = P[a][i];
+                } else {
+                    const int a = (int)k / 4, b = (int)k % 4;
+                    for (int r = 0; r < 4; ++r)
+                        for (int col = 0; col < 4; ++col)
+                            c.U[k * 16 + r * 4 + col] = P[a][(r >> 1) * 2 + (col >> 1)] * P[b][(r & 1) * 2 + (col & 1)];
+                }
+            } else if (c.q[k] > 0) {
+                const double s = 1.0 / std::sqrt(c.q[k]);
+                for (uint32_t i = 0; i < dd; ++i) c.U[k * dd + i] = c.K[k * dd + i] * s;
+            }
+        }
+    }
+}
+
+void register_ops(Circuit& c, const ptsbe_op* ops, uint64_t n_ops, const double* custom, uint32_t n_custom) {
+    const uint32_t n = c.n;
+    c.ops.assign(ops, ops + n_ops);
+    c.custom.assign(custom ? custom : nullptr, custom ? custom + 32 * (size_t)n_custom : nullptr);
+    c.site_op.clear(); c.site_ch.clear();
+    c.n_gates = 0;
+    for (uint64_t i = 0; i < n_ops; ++i) {
+        const ptsbe_op& o = ops[i];
+        if (o.n_targets < 1 || o.n_targets > 2) fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": n_targets must be 1 or 2");
+        if (o.targets[0] >= n || (o.n_targets == 2 && (o.targets[1] >= n || o.targets[1] == o.targets[0])))
+            fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": bad target qubits");
+        if (o.kind == PTSBE_OP_GATE) {
+            if (o.id > PTSBE_G_U2 || gate_arity(o.id) != o.n_targets) fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": bad gate");
+            if (o.id == PTSBE_G_U1 || o.id == PTSBE_G_U2) {
+                const double r = o.params[0];
+                if (!(r >= 0 && r < n_custom) || r != std::floor(r) || !custom) fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": bad custom gate row");
+            }
+            ++c.n_gates;
+        } else if (o.kind == PTSBE_OP_NOISE) {
+            if (o.id >= c.ch.size() || c.ch[o.id].arity != o.n_targets) fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": bad channel");
+            c.site_op.push_back((uint32_t)i);
+            c.site_ch.push_back(o.id);
+        } else {
+            fail(PTSBE_ERR_INVALID, "op " + std::to_string(i) + ": kind must be GATE or NOISE");
+        }
+    }
+    if (c.site_op.size() >= (1ull << 32) || n_ops >= (1ull << 32)) fail(PTSBE_ERR_UNSUPPORTED, "too many ops");
+    c.Q0 = 1.0;
+    c.k0_strict_mode = true;
+    for (uint32_t s : c.site_ch) {
+        const HostChannel& ch = c.ch[s];
+        c.Q0 *= ch.q[0];
+        if (!(ch.q[0] > 0)) c.k0_strict_mode = false;
+        for (uint32_t k = 1; k < ch.nk; ++k) if (!(ch.q[k] < ch.q[0])) c.k0_strict_mode = false;
+    }
+}
+
+namespace {
+
+uint32_t push_mat(Circuit& c, const cd* m, int count) {
+    const uint32_t off = (uint32_t)c.dmats.size();
+    for (int i = 0; i < count; ++i) c.dmats.push_back(make_float2((float)m[i].real(), (float)m[i].imag()));
+    return off;
+}
+
+// Classifies a 2x2 operator (after rounding to complex64) into a micro-op.
+DevMicro micro1(Circuit& c, const cd* m, uint8_t operand) {
+    DevMicro u{};
+    u.operand = operand;
+    auto f0 = [](cd z) { return (float)z.real() == 0.0f && (float)z.imag() == 0.0f; };
+    auto f1 = [](cd z) { return (float)z.real() == 1.0f && (float)z.imag() == 0.0f; };
+    if (f0(m[1]) && f0(m[2])) {
+        if (f1(m[0]) && f1(m[3])) { u.kind = DOP_NOP; return u; }
+        cd d[2] = {m[0], m[3]};
+        u.kind = DOP_D1; u.mat = push_mat(c, d, 2);
+    } else if (f0(m[0]) && f0(m[3])) {
+        cd d[2] = {m[1], m[2]};
+        u.kind = DOP_X1; u.mat = push_mat(c, d, 2);
+    } else {
+        u.kind = DOP_G1; u.mat = push_mat(c, m, 4);
+    }
+    return u;
+}
+
+// Splits a 4x4 operator into a product of single-qubit factors when it is a Kronecker product
+// A (x) B (true for the Pauli products of two-qubit depolarising noise); otherwise keeps G2.
+bool kron_split(const cd* m, cd* A, cd* B) {
+    // find the largest entry to anchor the factorisation
+    int br = 0, bc = 0;
+    double best = -1;
+    for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 4; ++col)
+            if (std::abs(m[r * 4 + col]) > best) { best = std::abs(m[r * 4 + col]); br = r; bc = col; }
+    if (best <= 0) return false;
+    const int ar = br >> 1, ac = bc >> 1, b_r = br & 1, b_c = bc & 1;
+    // B = m[block (ar, ac)] / m[br][bc] * scale, A[i][j] = m[(i, b_r), (j, b_c)]
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            A[i * 2 + j] = m[(i * 2 + b_r) * 4 + (j * 2 + b_c)];
+            B[i * 2 + j] = m[(ar * 2 + i) * 4 + (ac * 2 + j)] / m[br * 4 + bc];
+        }
+    for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 4; ++col) {
+            const cd want = A[(r >> 1) * 2 + (col >> 1)] * B[(r & 1) * 2 + (col & 1)];
+            if (std::abs(want - m[r * 4 + col]) > 1e-14) return false;
+        }
+    return true;
+}
+
+}  // namespace
+
+void build_device_ops(Circuit& c) {
+    c.dops.clear(); c.dmicro.clear(); c.dmats.clear(); c.dchans.clear();
+    // channels: micro ops of every Kraus operator
+    for (const HostChannel& ch : c.ch) {
+        DevChannel dc{};
+        dc.nk = (uint8_t)ch.nk; dc.arity = (uint8_t)ch.arity; dc.mixture = ch.mixture ? 1 : 0;
+        const uint32_t dd = ch.dim * ch.dim;
+        for (uint32_t k = 0; k < ch.nk; ++k) {
+            dc.micro_off[k] = (uint32_t)c.dmicro.size();
+            dc.q[k] = ch.q[k];
+            const cd* m = ch.mixture ? &ch.U[k * dd] : &ch.K[k * dd];
+            if (ch.arity == 1) {
+                DevMicro u = micro1(c, m, 0);
+                if (u.kind != DOP_NOP) c.dmicro.push_back(u);
+            } else {
+                cd A[4], B[4];
+                if (kron_split(m, A, B)) {
+                    DevMicro ua = micro1(c, A, 0), ub = micro1(c, B, 1);
+                    if (ua.kind != DOP_NOP) c.dmicro.push_back(ua);
+                    if (ub.kind != DOP_NOP) c.dmicro.push_back(ub);
+                } else {
+                    DevMicro u{};
+                    u.kind = DOP_G2; u.operand = 2; u.mat = push_mat(c, m, 16);
+                    c.dmicro.push_back(u);
+                }
+            }
+            // K_k^dag K_k for Algorithm 1 probabilities
+            std::vector<cd> h(dd, 0.0);
+            for (uint32_t r = 0; r < ch.dim; ++r)
+                for (uint32_t col = 0; col < ch.dim; ++col)
+                    for (uint32_t i = 0; i < ch.dim; ++i)
+                        h[r * ch.dim + col] += std::conj(ch.K[k * dd + i * ch.dim + r]) * ch.K[k * dd + i * ch.dim + col];
+            dc.herm_mat[k] = push_mat(c, h.data(), (int)dd);
+        }
+        dc.micro_off[ch.nk] = (uint32_t)c.dmicro.size();
+        c.dchans.push_back(dc);
+    }
+    // ops
+    for (size_t i = 0; i < c.ops.size(); ++i) {
+        const ptsbe_op& o = c.ops[i];
+        DevOp d{};
+        d.q0 = (uint8_t)o.targets[0];
+        d.q1 = (uint8_t)(o.n_targets == 2 ? o.targets[1] : o.targets[0]);
+        d.nt = (uint8_t)o.n_targets;
+        if (o.kind == PTSBE_OP_NOISE) {
+            d.kind = DOP_NOISE; d.ch = o.id;
+            d.site = (uint32_t)(std::lower_bound(c.site_op.begin(), c.site_op.end(), (uint32_t)i) - c.site_op.begin());
+        } else if (o.id == PTSBE_G_CX) {
+            d.kind = DOP_CX;
+        } else if (o.id == PTSBE_G_CZ) {
+            d.kind = DOP_CZ;
+        } else if (o.id == PTSBE_G_SWAP) {
+            d.kind = DOP_SWAP;
+        } else {
+            cd m[16];
+            int dim;
+            const double* custom = nullptr;
+            if (o.id == PTSBE_G_U1 || o.id == PTSBE_G_U2) custom = c.custom.data() + 32 * (size_t)o.params[0];
+            gate_matrix(o.id, o.params, custom, m, dim);
+            if (dim == 2) {
+                DevMicro u = micro1(c, m, 0);
+                d.kind = u.kind; d.mat = u.mat;
+            } else {
+                d.kind = DOP_G2; d.mat = push_mat(c, m, 16);
+            }
+        }
+        c.dops.push_back(d);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+uint64_t op_mask(const Circuit& c, size_t i) {
+    const ptsbe_op& o = c.ops[i];
+    uint64_t m = 1ull << o.targets[0];
+    if (o.n_targets == 2) m |= 1ull << o.targets[1];
+    return m;
+}
+
+bool general_noise(const Circuit& c, size_t i) {
+    const ptsbe_op& o = c.ops[i];
+    return o.kind == PTSBE_OP_NOISE && !c.ch[o.id].mixture;
+}
+
+void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, bool probe, uint32_t probe_op) {
+    const int n = (int)c.n, tb = P.tb, lb = P.lb;
+    // fill the qubit set up to tb with the lowest unused qubits
+    for (int q = 0; q < n && __builtin_popcountll(Q) < tb; ++q) Q |= 1ull << q;
+    DevStage st{};
+    st.op_begin = b; st.op_end = e;
+    st.flags = probe ? 1u : 0u;
+    st.probe_op = probe_op;
+    std::memset(st.pos, 0xFF, sizeof(st.pos));
+    std::memset(st.outer_q, 0xFF, sizeof(st.outer_q));
+    int tq[kMaxQubits];
+    int t = 0;
+    for (int q = 0; q < lb; ++q) tq[t++] = q;
+    for (int q = lb; q < n; ++q) if (Q & (1ull << q)) tq[t++] = q;
+    int ob = 0;
+    for (int q = 0; q < n; ++q) if (!(Q & (1ull << q))) st.outer_q[ob++] = (uint8_t)q;
+    for (int i = 0; i < tb; ++i) st.pos[tq[i]] = (uint8_t)i;
+    st.hi_off = (uint32_t)P.hi.size();
+    for (uint32_t h = 0; h < (1u << (tb - lb)); ++h) {
+        uint32_t g = 0;
+        for (int bit = 0; bit < tb - lb; ++bit) if (h & (1u << bit)) g |= 1u << tq[lb + bit];
+        P.hi.push_back(g);
+    }
+    for (uint32_t i = b; i < e; ++i) P.op_stage[i] = (int32_t)P.stages.size();
+    P.stages.push_back(st);
+}
+
+}  // namespace
+
+Plan make_plan(const Circuit& c, int tile_bits, bool pershot) {
+    Plan P;
+    const int n = (int)c.n;
+    P.tb = std::min(n, tile_bits);
+    P.lb = std::min(P.tb, kLowBits);
+    const size_t nops = c.ops.size();
+    P.op_stage.assign(nops, 0);
+    const uint64_t low = (P.lb >= 64) ? ~0ull : ((1ull << P.lb) - 1);
+    if (n <= tile_bits) {
+        close_stage(P, c, (n >= 64 ? ~0ull : ((1ull << n) - 1)), 0, (uint32_t)nops, false, 0);
+        return P;
+    }
+    if (P.tb < P.lb + 4) fail(PTSBE_ERR_UNSUPPORTED, "tile too small for the planner");
+    uint64_t Q = low;
+    uint32_t begin = 0;
+    for (size_t i = 0; i < nops; ++i) {
+        if (pershot && general_noise(c, i)) {
+            // Algorithm 1: the branch probabilities of this site are accumulated by the epilogue
+            // of the stage that ends here, so the site's qubits belong to that stage.
+            const uint64_t need = Q | op_mask(c, i);
+            if (__builtin_popcountll(need) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "planner invariant violated");
+            close_stage(P, c, need, begin, (uint32_t)i, true, (uint32_t)i);
+            begin = (uint32_t)i;
+            Q = low | op_mask(c, i);
+            if (i + 1 < nops && general_noise(c, i + 1)) Q |= op_mask(c, i + 1);
+            continue;
+        }
+        uint64_t need = Q | op_mask(c, i);
+        if (pershot && i + 1 < nops && general_noise(c, i + 1)) need |= op_mask(c, i + 1);
+        if (__builtin_popcountll(need) > P.tb) {
+            close_stage(P, c, Q, begin, (uint32_t)i, false, 0);
+            begin = (uint32_t)i;
+            need = low | op_mask(c, i);
+            if (pershot && i + 1 < nops && general_noise(c, i + 1)) need |= op_mask(c, i + 1);
+        }
+        Q = need;
+    }
+    close_stage(P, c, Q, begin, (uint32_t)nops, false, 0);
+    return P;
+}
+
+}  // namespace ptsbe

@@ -1,0 +1,227 @@
+// Internal data structures of libptsbe shared by the host code and the CUDA kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <complex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ptsbe.h"
+
+namespace ptsbe {
+
+constexpr int kMaxKraus = 16;
+constexpr int kMaxQubits = 32;
+constexpr int kTileMax = 14;      // largest tile: 2^14 complex64 = 128 KiB of shared memory
+constexpr int kLowBits = 4;       // low qubits every tile keeps contiguous (16 amplitudes = 128 B)
+
+// ---------------------------------------------------------------------------------------------
+// Errors: thrown inside the library, turned into a status at the ABI boundary.
+// ---------------------------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    int status;
+    Error(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+[[noreturn]] inline void fail(int status, const std::string& msg) { throw Error(status, msg); }
+
+void cuda_check(cudaError_t e, const char* what);
+void count_launch(uint64_t n = 1);   // kernels enqueued by the library (all contexts)
+void count_h2d(uint64_t bytes);      // host-to-device bytes copied by the library
+uint64_t launches_so_far();
+#define PTSBE_CUDA(call) ::ptsbe::cuda_check((call), #call)
+
+// ---------------------------------------------------------------------------------------------
+// Device op tables. A circuit becomes a list of DevOp; a gate is one micro-kernel, a noise site
+// selects the micro-op list of its chosen Kraus operator at run time.
+// ---------------------------------------------------------------------------------------------
+enum : uint8_t {
+    DOP_G1 = 0,    // general 2x2: mat[0..3]
+    DOP_D1 = 1,    // diagonal 2x2: mat[0], mat[1]
+    DOP_X1 = 2,    // anti-diagonal [[0, a], [b, 0]]: mat[0] = a, mat[1] = b
+    DOP_CX = 3,    // controlled-X, control q0, target q1
+    DOP_CZ = 4,    // diag(1, 1, 1, -1)
+    DOP_SWAP = 5,
+    DOP_G2 = 6,    // general 4x4 on local index 2*bit(q0) + bit(q1): mat[0..15]
+    DOP_NOISE = 7, // noise site: ch, site
+    DOP_NOP = 8    // identity
+};
+
+struct DevOp {
+    uint8_t kind;
+    uint8_t q0, q1;
+    uint8_t nt;
+    uint32_t mat;    // offset into the complex64 matrix pool
+    uint32_t site;   // DOP_NOISE: site index
+    uint32_t ch;     // DOP_NOISE: channel index
+};
+
+struct DevMicro {
+    uint8_t kind;     // DOP_G1 / D1 / X1 / G2 / NOP
+    uint8_t operand;  // 0: first target, 1: second target, 2: both (G2)
+    uint16_t pad;
+    uint32_t mat;
+};
+
+struct DevChannel {
+    uint32_t micro_off[kMaxKraus + 1];  // micro ops of Kraus k: [micro_off[k], micro_off[k+1])
+    uint32_t herm_mat[kMaxKraus];       // K_k^dag K_k (for Algorithm 1 probabilities), pool offset
+    double q[kMaxKraus];                // nominal probabilities (unitary mixture: exact mixing weights)
+    uint8_t nk, arity, mixture, pad;
+};
+
+// One pass of the tiled evolution: ops [op_begin, op_end) all act inside the qubit set of the
+// tile. Tile index l (tb bits): bits [0, lb) are global qubits [0, lb) (contiguous in memory),
+// bits [lb, tb) are the global qubits listed in tile_q[lb..tb); the remaining n - tb qubits
+// (outer_q) enumerate the 2^(n-tb) tiles of a state.
+struct DevStage {
+    uint32_t op_begin, op_end;
+    uint32_t hi_off;                 // offset of this stage's hi table (2^(tb-lb) uint32)
+    uint32_t flags;                  // bit 0: ends right before a general noise site (Algorithm 1 mode)
+    uint32_t probe_op;               // Algorithm 1 mode: the general noise op whose probabilities
+                                     // the epilogue accumulates
+    uint8_t pos[kMaxQubits];         // global qubit -> tile bit, 0xFF if outer
+    uint8_t outer_q[kMaxQubits];     // outer bit b -> global qubit
+};
+
+struct Plan {
+    int tb = 0, lb = 0;              // tile bits, contiguous low bits
+    std::vector<DevStage> stages;
+    std::vector<uint32_t> hi;        // concatenated hi tables: global offset of tile bits [lb, tb)
+    std::vector<int32_t> op_stage;   // op index -> stage
+};
+
+// ---------------------------------------------------------------------------------------------
+// Host-side circuit and Kraus-set records.
+// ---------------------------------------------------------------------------------------------
+using cd = std::complex<double>;
+
+struct HostChannel {
+    uint32_t kind = 0, arity = 1, nk = 0, dim = 2;
+    double param = 0;
+    std::vector<cd> K;       // nk * dim * dim, row-major
+    std::vector<double> q;   // nominal probabilities
+    std::vector<cd> U;       // unitary-mixture: K_k / sqrt(q_k)
+    bool mixture = false;
+};
+
+struct DeviceCircuit {
+    DevOp* ops = nullptr;
+    DevMicro* micro = nullptr;
+    float2* mats = nullptr;
+    DevChannel* chans = nullptr;
+    uint32_t* site_op = nullptr;
+    DevStage* stages = nullptr;
+    uint32_t* hi = nullptr;
+    size_t bytes = 0;
+};
+
+struct Circuit {
+    uint32_t n = 0;
+    std::vector<ptsbe_op> ops;
+    std::vector<double> custom;      // custom gate rows, 4x4 complex128 as (re, im)
+    std::vector<HostChannel> ch;
+    std::vector<uint32_t> site_op, site_ch;
+    uint64_t n_gates = 0;
+    double Q0 = 1.0;                 // prod_s q_{s,0}, site order
+    bool k0_strict_mode = true;      // q_{s,0} > q_{s,k} for all k at every site
+    // device form
+    std::vector<DevOp> dops;
+    std::vector<DevMicro> dmicro;
+    std::vector<float2> dmats;
+    std::vector<DevChannel> dchans;
+    Plan plan;                       // PTSBE evolution plan
+    Plan plan_pershot;               // Algorithm 1 plan (stage break before every general site)
+    bool pershot_planned = false;
+    DeviceCircuit dev;
+    DeviceCircuit dev_pershot;
+};
+
+struct KSet {
+    uint32_t circuit = 0;
+    std::vector<uint32_t> off;       // [count + 1]
+    std::vector<uint32_t> site;
+    std::vector<uint8_t> k;
+    std::vector<uint64_t> mult, shots, shot_off;
+    std::vector<double> q, key;
+    // device copies of the entries (uploaded on first use)
+    uint32_t* d_site = nullptr;
+    uint8_t* d_k = nullptr;
+    uint32_t count() const { return (uint32_t)(off.size() - 1); }
+};
+
+// PTS (host) ----------------------------------------------------------------------------------
+void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& out);
+void apportion_counts(const std::vector<uint64_t>& c, uint64_t M, std::vector<uint64_t>& out);
+void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uint64_t>& out);
+double set_key(const Circuit& c, const uint32_t* sites, const uint8_t* ks, uint32_t len);
+
+// Registration and planning (host) -----------------------------------------------------------------
+void build_channel(const ptsbe_channel& in, HostChannel& c);
+void register_ops(Circuit& c, const ptsbe_op* ops, uint64_t n_ops, const double* custom, uint32_t n_custom);
+void build_device_ops(Circuit& c);
+Plan make_plan(const Circuit& c, int tile_bits, bool pershot);
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launch interface (evolve.cu / sample.cu / pershot.cu).
+// ---------------------------------------------------------------------------------------------
+struct EvolveArgs {
+    // circuit
+    const DevOp* ops;
+    const DevMicro* micro;
+    const float2* mats;
+    const DevChannel* chans;
+    const uint32_t* site_op;
+    const DevStage* stages;
+    const uint32_t* hi;
+    int n, tb, lb;
+    // Kraus-set entries (whole set, on device)
+    const uint32_t* ent_site;
+    const uint8_t* ent_k;
+    // per-node tables (range-local node index)
+    const uint32_t* node_ebeg;
+    const uint32_t* node_eend;
+    const uint32_t* node_start;      // first op to apply
+    const uint8_t* node_fresh;       // 1: start from |0...0>
+    const uint32_t* node_cbeg;
+    const uint32_t* node_cend;
+    const uint32_t* child_op;        // branch op of each child, ascending per parent
+    const uint32_t* child_node;
+    const double* wmix;              // prod of unitary-mixture q over all sites
+    const double* qalpha;
+    // outputs
+    float2* states;                  // [count][2^n]
+    double* part;                    // [count][2^(n-tb)] last-stage partial norms
+    double* weights;
+    uint8_t* status;
+};
+
+void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
+                         cudaStream_t s);
+void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
+
+struct SampleItem {                  // one cluster's share of one state's shots
+    uint32_t state;                  // range-local state index
+    uint32_t alpha;                  // global set index (Philox counter word 2)
+    uint64_t j0, j1;                 // shot interval within the set
+    uint64_t out0;                   // output slot of shot j0
+};
+
+struct SampleArgs {
+    int n;
+    const float2* states;
+    const uint8_t* status;
+    uint64_t seed;
+    uint32_t* bits;
+    double* scratch;                 // n > 17: per-state global CDF workspace
+    double* scratch_tot;             // n > 17: per-block totals / offsets
+};
+
+void launch_sample_cluster(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);
+void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1,
+                          uint64_t out0, cudaStream_t s);
+int sample_cluster_max_qubits();
+
+}  // namespace ptsbe

@@ -1,0 +1,366 @@
+// Pre-trajectory sampling on the host (Sec. 3.1, Algorithm 2).
+//
+// Every mode ends in the same bookkeeping: sets sorted into canonical order (lexicographic over
+// the (site, k) list, a prefix before its extensions), duplicates merged (uniqueKraus of
+// Algorithm 2, multiplicity = number of samples that produced the set), nominal probability
+// q_alpha = Q0 * key(alpha) with Q0 = prod_s q_{s,0} and key = product of the set's ratios
+// q_{s,k}/q_{s,0} taken in descending order, and shots allocated by largest remainders
+// ("redistributing ... according to the relative populations", Sec. 3.1).
+//
+// Compiled without floating-point contraction so the FP64 decisions (categorical draws,
+// keys, quotas) are reproducible on every host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.h"
+#include "philox.h"
+
+namespace ptsbe {
+
+namespace {
+
+struct Entry {
+    uint32_t site;
+    uint8_t k;
+    bool operator<(const Entry& o) const { return site != o.site ? site < o.site : k < o.k; }
+    bool operator==(const Entry& o) const { return site == o.site && k == o.k; }
+};
+using List = std::vector<Entry>;
+
+bool canon_less(const List& a, const List& b) {
+    return std::lexicographical_compare(a.begin(), a.end(), b.begin(), b.end());
+}
+
+// Smallest k with u < q_0 + ... + q_k, summed in listed order; the last index otherwise.
+inline int categorical(double u, const double* q, int nk) {
+    double acc = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        acc += q[k];
+        if (u < acc) return k;
+    }
+    return nk - 1;
+}
+
+double ratio(const Circuit& c, uint32_t site, int k) {
+    const HostChannel& ch = c.ch[c.site_ch[site]];
+    return ch.q[k] / ch.q[0];
+}
+
+// Sorts, merges duplicates, fills key/q and the CSR arrays of `out`.
+void finish(const Circuit& c, std::vector<std::pair<List, uint64_t>>& sets, std::vector<uint64_t>* given_shots,
+            KSet& out) {
+    std::vector<size_t> idx(sets.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return canon_less(sets[a].first, sets[b].first); });
+    out.off.assign(1, 0);
+    out.site.clear(); out.k.clear(); out.mult.clear(); out.q.clear(); out.key.clear(); out.shots.clear();
+    std::vector<uint64_t> gshots;
+    const List* prev = nullptr;
+    for (size_t t = 0; t < idx.size(); ++t) {
+        auto& s = sets[idx[t]];
+        if (prev && *prev == s.first) {
+            out.mult.back() += s.second;
+            if (given_shots) gshots.back() += (*given_shots)[idx[t]];
+            continue;
+        }
+        for (const Entry& e : s.first) { out.site.push_back(e.site); out.k.push_back(e.k); }
+        out.off.push_back((uint32_t)out.site.size());
+        out.mult.push_back(s.second);
+        if (given_shots) gshots.push_back((*given_shots)[idx[t]]);
+        prev = &s.first;
+    }
+    const uint32_t n = (uint32_t)out.mult.size();
+    out.key.resize(n); out.q.resize(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        out.key[i] = set_key(c, out.site.data() + out.off[i], out.k.data() + out.off[i], out.off[i + 1] - out.off[i]);
+        out.q[i] = c.Q0 * out.key[i];
+    }
+    if (given_shots) out.shots = gshots;
+}
+
+void allocate_shots(KSet& s, uint32_t alloc, uint64_t total, uint64_t per_set) {
+    const uint32_t n = s.count();
+    if (alloc == PTSBE_SHOTS_BY_COUNT) apportion_counts(s.mult, total, s.shots);
+    else if (alloc == PTSBE_SHOTS_UNIFORM) s.shots.assign(n, per_set);
+    else if (alloc == PTSBE_SHOTS_BY_PROB) apportion_weights(s.q, total, s.shots);
+    else if (alloc == PTSBE_SHOTS_GIVEN) { /* already set */ }
+    else fail(PTSBE_ERR_INVALID, "unknown shot allocation");
+}
+
+// ---- probabilistic modes -------------------------------------------------------------------------
+template <class F>
+void parallel_for(uint64_t n, F&& f) {
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    unsigned nt = (unsigned)std::min<uint64_t>(hw, std::max<uint64_t>(1, n / 64));
+    if (nt <= 1) { f(0, n); return; }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+        uint64_t b = n * t / nt, e = n * (t + 1) / nt;
+        th.emplace_back([&f, b, e] { f(b, e); });
+    }
+    for (auto& x : th) x.join();
+}
+
+void pts_proportional(const Circuit& c, uint64_t ns, uint64_t seed, std::vector<std::pair<List, uint64_t>>& sets) {
+    sets.assign(ns, {});
+    const uint32_t S = (uint32_t)c.site_ch.size();
+    parallel_for(ns, [&](uint64_t b, uint64_t e) {
+        for (uint64_t i = b; i < e; ++i) {
+            List& l = sets[i].first;
+            sets[i].second = 1;
+            for (uint32_t s = 0; s < S; ++s) {
+                const HostChannel& ch = c.ch[c.site_ch[s]];
+                const double u = uniform53(seed, s, (uint32_t)i, (uint32_t)(i >> 32), kDomPts);
+                const int k = categorical(u, ch.q.data(), (int)ch.nk);
+                if (k != 0) l.push_back({s, (uint8_t)k});
+            }
+        }
+    });
+}
+
+void pts_literal(const Circuit& c, uint64_t ns, uint64_t seed, std::vector<std::pair<List, uint64_t>>& sets) {
+    sets.assign(ns, {});
+    const uint32_t S = (uint32_t)c.site_ch.size();
+    parallel_for(ns, [&](uint64_t b, uint64_t e) {
+        for (uint64_t i = b; i < e; ++i) {
+            List& l = sets[i].first;
+            sets[i].second = 1;
+            for (uint32_t s = 0; s < S; ++s) {
+                const HostChannel& ch = c.ch[c.site_ch[s]];
+                bool taken = false;
+                for (uint32_t k = 1; k < ch.nk; ++k) {
+                    const double r = uniform53(seed, s, (uint32_t)i, (uint32_t)(i >> 32), kDomLiteral | (k << 8));
+                    if (r <= ch.q[k] && !taken) { l.push_back({s, (uint8_t)k}); taken = true; }
+                }
+            }
+        }
+    });
+}
+
+// ---- most-likely modes: best-first enumeration ------------------------------------------------------
+// Options (s, k != 0) with q_{s,k} > 0 sorted by ratio descending, then (s, k). A set is an
+// increasing list of option indices with distinct sites. Children of a set S with last option j:
+//   extend : S + {next option after j whose site is not in S}
+//   replace: S - {j} + {next option after j whose site is not in S - {j}}
+// Every set has exactly one parent, and a child never precedes its parent in the order
+// (key descending, canonical ascending): extending multiplies by a ratio < 1; replacing with an
+// equal ratio moves an entry to a larger (site, k). Best-first search on a max-heap in that order
+// therefore pops sets exactly in sorted order.
+struct Opt { uint32_t site; uint8_t k; double r; };
+
+struct Node {
+    double key;          // product of the ratios of opts, in option order
+    double prefix;       // product without the last option
+    std::vector<uint32_t> opts;
+    List canon;          // site-sorted entries
+};
+
+struct NodeOrder {
+    bool operator()(const Node* a, const Node* b) const {  // true if a comes AFTER b
+        if (a->key != b->key) return a->key < b->key;
+        return canon_less(b->canon, a->canon);
+    }
+};
+
+class BestFirst {
+  public:
+    explicit BestFirst(const Circuit& c) : c_(c) {
+        const uint32_t S = (uint32_t)c.site_ch.size();
+        for (uint32_t s = 0; s < S; ++s) {
+            const HostChannel& ch = c.ch[c.site_ch[s]];
+            for (uint32_t k = 1; k < ch.nk; ++k)
+                if (ch.q[k] > 0) opts_.push_back({s, (uint8_t)k, ratio(c, s, (int)k)});
+        }
+        std::sort(opts_.begin(), opts_.end(), [](const Opt& a, const Opt& b) {
+            if (a.r != b.r) return a.r > b.r;
+            if (a.site != b.site) return a.site < b.site;
+            return a.k < b.k;
+        });
+        Node* root = alloc();
+        root->key = 1.0; root->prefix = 1.0;
+        heap_.push(root);
+    }
+
+    // Pops the next set in order; false when exhausted.
+    bool next(double& key, List& canon) {
+        if (heap_.empty()) return false;
+        Node* nd = heap_.top();
+        heap_.pop();
+        key = nd->key;
+        canon = nd->canon;
+        expand(nd);
+        return true;
+    }
+
+  private:
+    Node* alloc() { pool_.emplace_back(new Node()); return pool_.back().get(); }
+
+    bool site_used(const std::vector<uint32_t>& opts, size_t upto, uint32_t site) const {
+        for (size_t i = 0; i < upto; ++i) if (opts_[opts[i]].site == site) return true;
+        return false;
+    }
+    // Smallest option index > after whose site is not among opts[0..upto).
+    int64_t next_valid(const std::vector<uint32_t>& opts, size_t upto, int64_t after) const {
+        for (int64_t j = after + 1; j < (int64_t)opts_.size(); ++j)
+            if (!site_used(opts, upto, opts_[j].site)) return j;
+        return -1;
+    }
+    void push_child(const std::vector<uint32_t>& base, size_t keep, double prefix, uint32_t j) {
+        Node* ch = alloc();
+        ch->opts.assign(base.begin(), base.begin() + keep);
+        ch->opts.push_back(j);
+        ch->prefix = prefix;
+        ch->key = prefix * opts_[j].r;
+        for (uint32_t o : ch->opts) ch->canon.push_back({opts_[o].site, opts_[o].k});
+        std::sort(ch->canon.begin(), ch->canon.end());
+        heap_.push(ch);
+    }
+    void expand(const Node* nd) {
+        const auto& o = nd->opts;
+        const int64_t last = o.empty() ? -1 : (int64_t)o.back();
+        int64_t j = next_valid(o, o.size(), last);
+        if (j >= 0) push_child(o, o.size(), nd->key, (uint32_t)j);
+        if (!o.empty()) {
+            j = next_valid(o, o.size() - 1, last);
+            if (j >= 0) push_child(o, o.size() - 1, nd->prefix, (uint32_t)j);
+        }
+    }
+
+    const Circuit& c_;
+    std::vector<Opt> opts_;
+    std::vector<std::unique_ptr<Node>> pool_;
+    std::priority_queue<Node*, std::vector<Node*>, NodeOrder> heap_;
+};
+
+}  // namespace
+
+double set_key(const Circuit& c, const uint32_t* sites, const uint8_t* ks, uint32_t len) {
+    if (len == 0) return 1.0;
+    std::vector<double> r(len);
+    for (uint32_t i = 0; i < len; ++i) r[i] = ratio(c, sites[i], ks[i]);
+    std::sort(r.begin(), r.end(), [](double a, double b) { return a > b; });
+    double key = 1.0;
+    for (double x : r) key *= x;
+    return key;
+}
+
+void apportion_counts(const std::vector<uint64_t>& c, uint64_t M, std::vector<uint64_t>& out) {
+    const size_t n = c.size();
+    out.assign(n, 0);
+    unsigned __int128 N = 0;
+    for (uint64_t x : c) N += x;
+    if (n == 0 || N == 0) return;
+    std::vector<std::pair<uint64_t, uint32_t>> rem(n);
+    uint64_t used = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const unsigned __int128 p = (unsigned __int128)M * c[i];
+        out[i] = (uint64_t)(p / N);
+        rem[i] = {(uint64_t)(p % N), (uint32_t)i};
+        used += out[i];
+    }
+    std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
+        return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    for (uint64_t j = 0; j < M - used; ++j) out[rem[j].second] += 1;
+}
+
+void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uint64_t>& out) {
+    const size_t n = w.size();
+    out.assign(n, 0);
+    if (n == 0) return;
+    double W = 0.0;
+    for (double x : w) W += x;
+    std::vector<std::pair<double, uint32_t>> rem(n);
+    uint64_t used = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const double quota = W > 0 ? ((double)M * w[i]) / W : 0.0;
+        const double fl = std::floor(quota);
+        out[i] = (uint64_t)fl;
+        rem[i] = {quota - fl, (uint32_t)i};
+        used += out[i];
+    }
+    if (used <= M) {
+        std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
+            return a.first != b.first ? a.first > b.first : a.second < b.second;
+        });
+        for (uint64_t j = 0; j < M - used && j < n; ++j) out[rem[j].second] += 1;
+    } else {
+        std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
+            return a.first != b.first ? a.first < b.first : a.second > b.second;
+        });
+        uint64_t R = used - M;
+        for (size_t j = 0; j < n && R > 0; ++j)
+            if (out[rem[j].second] > 0) { out[rem[j].second] -= 1; --R; }
+    }
+}
+
+void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& out) {
+    std::vector<std::pair<List, uint64_t>> sets;
+    std::vector<uint64_t> given;
+    uint32_t alloc = p.shot_alloc;
+    switch (p.mode) {
+    case PTSBE_PTS_PROPORTIONAL:
+        pts_proportional(c, p.nsamples, seed, sets);
+        break;
+    case PTSBE_PTS_LITERAL:
+        pts_literal(c, p.nsamples, seed, sets);
+        break;
+    case PTSBE_PTS_TOPK:
+    case PTSBE_PTS_BAND: {
+        if (!c.k0_strict_mode)
+            fail(PTSBE_ERR_UNSUPPORTED, "TOPK/BAND need q_{s,0} to be the strict maximum at every site");
+        if (p.mode == PTSBE_PTS_BAND && !(p.p_min > 0) )
+            fail(PTSBE_ERR_INVALID, "BAND needs p_min > 0");
+        BestFirst bf(c);
+        double key;
+        List canon;
+        if (p.mode == PTSBE_PTS_TOPK) {
+            for (uint64_t i = 0; i < p.k && bf.next(key, canon); ++i) sets.push_back({canon, 1});
+        } else {
+            while (bf.next(key, canon)) {
+                const double q = c.Q0 * key;
+                if (q < p.p_min) break;
+                if (q <= p.p_max) sets.push_back({canon, 1});
+                if (sets.size() > (1ull << 31)) fail(PTSBE_ERR_UNSUPPORTED, "band selects more than 2^31 sets");
+            }
+        }
+        break;
+    }
+    case PTSBE_PTS_TARGETED: {
+        if (p.t_count && (!p.t_offsets || !p.t_sites || !p.t_kidx)) fail(PTSBE_ERR_INVALID, "targeted set arrays missing");
+        const uint32_t S = (uint32_t)c.site_ch.size();
+        for (uint32_t i = 0; i < p.t_count; ++i) {
+            const uint32_t b = p.t_offsets[i], e = p.t_offsets[i + 1];
+            if (e < b) fail(PTSBE_ERR_INVALID, "targeted offsets decrease");
+            List l;
+            for (uint32_t j = b; j < e; ++j) {
+                const uint32_t s = p.t_sites[j];
+                if (s >= S) fail(PTSBE_ERR_INVALID, "targeted site out of range");
+                if (p.t_kidx[j] == 0 || p.t_kidx[j] >= c.ch[c.site_ch[s]].nk) fail(PTSBE_ERR_INVALID, "targeted Kraus index out of range");
+                if (j > b && s <= p.t_sites[j - 1]) fail(PTSBE_ERR_INVALID, "targeted sites must increase");
+                l.push_back({s, p.t_kidx[j]});
+            }
+            sets.push_back({std::move(l), 1});
+        }
+        if (alloc == PTSBE_SHOTS_GIVEN) {
+            if (!p.t_shots) fail(PTSBE_ERR_INVALID, "SHOTS_GIVEN needs t_shots");
+            given.assign(p.t_shots, p.t_shots + p.t_count);
+        }
+        break;
+    }
+    default:
+        fail(PTSBE_ERR_INVALID, "unknown PTS mode");
+    }
+    if (alloc == PTSBE_SHOTS_GIVEN && p.mode != PTSBE_PTS_TARGETED) fail(PTSBE_ERR_INVALID, "SHOTS_GIVEN is for TARGETED");
+    finish(c, sets, alloc == PTSBE_SHOTS_GIVEN ? &given : nullptr, out);
+    allocate_shots(out, alloc, p.total_shots, p.shots_per_set);
+    out.shot_off.assign(out.count() + 1, 0);
+    for (uint32_t i = 0; i < out.count(); ++i) out.shot_off[i + 1] = out.shot_off[i] + out.shots[i];
+}
+
+}  // namespace ptsbe

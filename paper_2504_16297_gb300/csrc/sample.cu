@@ -1,0 +1,364 @@
+// Batched shot sampling (Sec. 3: all m_alpha shots of a prepared state are drawn at once).
+//
+// For a state with P_i = |psi_i|^2 and FP64 inclusive prefix C, T = C[last], shot j draws
+// u = U53(Philox(seed; j_lo, j_hi, alpha, 2)) and returns the smallest i with u*T < C[i].
+//
+// n <= 17: the whole FP64 CDF is held on chip. A thread-block cluster of CL = 2^(n-14) CTAs
+// (one CTA when n <= 14) owns one state: CTA r builds the prefix of amplitudes
+// [r*2^sb, (r+1)*2^sb) in its shared memory, the cluster exchanges slice totals over distributed
+// shared memory (DSMEM), and every shot binary-searches the slice it falls in, remote or local,
+// through DSMEM. Shots are written in order, so the output stream is coalesced. Heavy states are
+// split into several work items (shot ranges), each rebuilding the CDF.
+//
+// n > 17: the CDF is built in global workspace (block prefixes, block offsets) and searched there.
+//
+// Comparisons of non-negative doubles are done on their bit patterns (same order, integer ALU).
+#include <cooperative_groups.h>
+
+#include "internal.h"
+#include "philox.h"
+
+namespace cg = cooperative_groups;
+
+namespace ptsbe {
+
+namespace {
+
+constexpr int kSliceBits = 14;   // per-CTA CDF slice: 2^14 doubles = 128 KiB
+constexpr int kSampleThreads = 1024;
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Padded shared-memory address of CDF entry l when every thread owns K = 2^kb consecutive
+// entries: one pad slot per K entries keeps a warp's accesses on distinct banks.
+__device__ __forceinline__ uint32_t paddr(uint32_t l, int kb) { return l + (l >> kb); }
+
+// log2 of the CDF entries each thread owns for a slice of 2^cb entries (0 when the slice is
+// smaller than the CTA).
+__device__ __forceinline__ int entries_log2(int cb) {
+    const int tl = 31 - __clz(blockDim.x);
+    return cb > tl ? cb - tl : 0;
+}
+
+// Builds the inclusive FP64 prefix of |psi|^2 over 2^cb amplitudes into cdf (padded layout).
+// Thread t owns entries [t*K, (t+1)*K): pass 1 stores the probabilities and the thread total,
+// the thread totals are scanned across the CTA, pass 2 runs the sequential prefix of each
+// thread's entries from its offset. Returns the last entry (the slice total).
+__device__ double build_prefix(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
+    const uint32_t count = 1u << cb;
+    const int kb = entries_log2(cb);
+    const uint32_t K = 1u << kb;
+    const uint32_t l0 = threadIdx.x * K;
+    const bool mine = l0 < count;
+    double tot = 0.0;
+    if (mine) {
+        if (K == 1) {
+            const float2 v = amps[l0];
+            const double p = (double)fmaf(v.x, v.x, v.y * v.y);
+            cdf[paddr(l0, kb)] = p;
+            tot = p;
+        } else {
+            for (uint32_t i = 0; i < K; i += 2) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(amps + l0 + i));
+                const double p0 = (double)fmaf(v.x, v.x, v.y * v.y);
+                const double p1 = (double)fmaf(v.z, v.z, v.w * v.w);
+                cdf[paddr(l0 + i, kb)] = p0;
+                cdf[paddr(l0 + i + 1, kb)] = p1;
+                tot += p0;
+                tot += p1;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const double prev = __shfl_up_sync(0xffffffffu, x, 1);   // inclusive sum of the lanes before
+    if (lane == 31) red[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < nw; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+    }
+    __syncthreads();
+    if (mine) {
+        double run = red[w] + (lane == 0 ? 0.0 : prev);   // exclusive offset of this thread
+        for (uint32_t i = 0; i < K; ++i) {
+            run += cdf[paddr(l0 + i, kb)];
+            cdf[paddr(l0 + i, kb)] = run;
+        }
+    }
+    __syncthreads();
+    return cdf[paddr(count - 1, kb)];
+}
+
+// smallest l in [0, 2^cb) with t < cdf[l] (the last index if none)
+__device__ __forceinline__ uint32_t search_slice(const double* cdf, int cb, int kb, long long tb) {
+    uint32_t lo = 0, hi = (1u << cb) - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (tb < dbits(cdf[paddr(mid, kb)])) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs a, const SampleItem* __restrict__ items, int sb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[33];
+    __shared__ double endv[CL];
+    double* cdf = reinterpret_cast<double*>(smem);
+    int rank = 0;
+    if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
+    const SampleItem it = items[blockIdx.x / CL];
+    const uint32_t nth = blockDim.x;
+    const int kb = entries_log2(sb);
+    const uint64_t nshots = it.j1 - it.j0;
+    if (a.status && a.status[it.state]) {      // null branch: sentinel outcomes
+        for (uint64_t k = (uint64_t)rank * nth + threadIdx.x; k < nshots; k += (uint64_t)CL * nth)
+            a.bits[it.out0 + k] = 0xFFFFFFFFu;
+        return;
+    }
+    const float2* amps = a.states + ((size_t)it.state << a.n) + ((size_t)rank << sb);
+    const double local_total = build_prefix(amps, sb, cdf, red);
+    double T;
+    if constexpr (CL > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        cluster.sync();
+        if (threadIdx.x == 0) {
+            double off = 0.0, my_off = 0.0;
+            for (int r = 0; r < CL; ++r) {
+                const double* rc = cluster.map_shared_rank(cdf, r);
+                const double tot_r = rc[paddr((1u << sb) - 1, kb)];
+                if (r == rank) my_off = off;
+                endv[r] = off + tot_r;     // == the remote last entry after its own offset add
+                off = endv[r];
+            }
+            red[32] = my_off;
+        }
+        cluster.sync();                    // everyone has read the raw slice totals
+        const double my_off = red[32];
+        if (my_off != 0.0)
+            for (uint32_t l = threadIdx.x; l < (1u << sb); l += nth) cdf[paddr(l, kb)] += my_off;
+        cluster.sync();
+        T = endv[CL - 1];
+    } else {
+        T = local_total;
+        if (threadIdx.x == 0) endv[0] = local_total;
+        __syncthreads();
+    }
+    for (uint64_t k = (uint64_t)rank * nth + threadIdx.x; k < nshots; k += (uint64_t)CL * nth) {
+        const uint64_t j = it.j0 + k;
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, kDomShot,
+                                        (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        const double t = u53(x.x[0], x.x[1]) * T;
+        const long long tb = dbits(t);
+        int r = 0;
+        while (r < CL - 1 && !(tb < dbits(endv[r]))) ++r;
+        uint32_t idx;
+        if (!(tb < dbits(endv[r]))) {
+            idx = (1u << a.n) - 1;                 // rounding put t at or above T
+        } else {
+            const double* rc = cdf;
+            if constexpr (CL > 1) rc = cg::this_cluster().map_shared_rank(cdf, r);
+            idx = ((uint32_t)r << sb) | search_slice(rc, sb, kb, tb);
+        }
+        a.bits[it.out0 + k] = idx;
+    }
+    if constexpr (CL > 1) cg::this_cluster().sync();  // keep this CTA's slice alive for remote readers
+}
+
+// ---- n > 17: global-memory CDF -----------------------------------------------------------------------
+
+// One CTA per block of 2^14 amplitudes: local inclusive prefix (unpadded) and block total.
+__global__ void __launch_bounds__(kSampleThreads) k_block_prefix(const float2* __restrict__ amps, double* cdf, double* btot) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[33];
+    double* s = reinterpret_cast<double*>(smem);
+    const uint32_t b = blockIdx.x;
+    const int kb = entries_log2(kSliceBits);
+    const double tot = build_prefix(amps + ((size_t)b << kSliceBits), kSliceBits, s, red);
+    for (uint32_t l = threadIdx.x; l < (1u << kSliceBits); l += blockDim.x)
+        cdf[((size_t)b << kSliceBits) + l] = s[paddr(l, kb)];
+    if (threadIdx.x == 0) btot[b] = tot;
+}
+
+// One CTA: exclusive block offsets (sequential per thread chunk, then across threads); writes
+// the block end values bend[b] = offset[b] + btot[b] and T into bend[nb].
+__global__ void k_block_scan(const double* __restrict__ btot, double* boff, double* bend, uint32_t nb) {
+    __shared__ double red[1024];
+    const uint32_t nth = blockDim.x;
+    const uint32_t per = (nb + nth - 1) / nth;
+    const uint32_t b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+    double s = 0.0;
+    for (uint32_t b = b0; b < b1; ++b) s += btot[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (uint32_t i = 0; i < nth; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+    }
+    __syncthreads();
+    double run = red[threadIdx.x];
+    for (uint32_t b = b0; b < b1; ++b) {
+        boff[b] = run;
+        run += btot[b];
+        bend[b] = run;
+    }
+}
+
+__global__ void k_block_add(double* cdf, const double* __restrict__ boff) {
+    const uint32_t b = blockIdx.x;
+    const double off = boff[b];
+    if (off == 0.0) return;
+    double* c = cdf + ((size_t)b << kSliceBits);
+    for (uint32_t l = threadIdx.x; l < (1u << kSliceBits); l += blockDim.x) c[l] += off;
+}
+
+__global__ void k_search_global(SampleArgs a, const double* __restrict__ cdf, const double* __restrict__ bend,
+                                uint32_t nb, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1, uint64_t out0) {
+    const double T = bend[nb - 1];
+    const bool null = a.status && a.status[state];
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < j1 - j0; k += (uint64_t)gridDim.x * blockDim.x) {
+        if (null) { a.bits[out0 + k] = 0xFFFFFFFFu; continue; }
+        const uint64_t j = j0 + k;
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), alpha, kDomShot,
+                                        (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        const long long tb = dbits(u53(x.x[0], x.x[1]) * T);
+        uint32_t lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tb < dbits(bend[mid])) hi = mid; else lo = mid + 1;
+        }
+        uint64_t idx;
+        if (!(tb < dbits(bend[lo]))) {
+            idx = (1ull << a.n) - 1;
+        } else {
+            const double* c = cdf + ((size_t)lo << kSliceBits);
+            uint32_t l = 0, h = (1u << kSliceBits) - 1;
+            while (l < h) {
+                const uint32_t mid = (l + h) >> 1;
+                if (tb < dbits(c[mid])) h = mid; else l = mid + 1;
+            }
+            idx = ((uint64_t)lo << kSliceBits) | l;
+        }
+        a.bits[out0 + k] = (uint32_t)idx;
+    }
+}
+
+__global__ void k_fill(uint32_t* bits, uint64_t count, uint32_t v) {
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x)
+        bits[k] = v;
+}
+
+// Padded CDF slice of 2^sb doubles for a CTA of `threads` threads.
+size_t cdf_smem_bytes(int sb, uint32_t threads) {
+    const size_t count = (size_t)1 << sb;
+    size_t K = count / threads;
+    if (K == 0) K = 1;
+    return 8 * (count + count / K + 1);
+}
+
+template <int CL>
+void launch_cluster(const SampleArgs& a, const SampleItem* items, uint32_t n_items, int sb, cudaStream_t s) {
+    uint32_t threads = (1u << sb) / 2;
+    if (threads < 32) threads = 32;
+    if (threads > kSampleThreads) threads = kSampleThreads;
+    const size_t smem = cdf_smem_bytes(sb, threads);
+    static bool configured = false;
+    if (!configured) {
+        PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+        configured = true;
+    }
+    for (uint32_t b = 0; b < n_items; b += (1u << 20)) {
+        const uint32_t cnt = (n_items - b) < (1u << 20) ? (n_items - b) : (1u << 20);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cnt * CL);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        PTSBE_CUDA(cudaLaunchKernelEx(&cfg, k_sample_cluster<CL>, a, items + b, sb));
+        count_launch();
+    }
+}
+
+}  // namespace
+
+int sample_cluster_max_qubits() { return kSliceBits + 3; }
+
+void launch_sample_cluster(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
+    if (n_items == 0) return;
+    const int n = a.n;
+    if (n <= kSliceBits) {
+        // small states: at least 2 amplitudes per thread
+        launch_cluster<1>(a, d_items, n_items, n < 1 ? 1 : n, s);
+    } else if (n == kSliceBits + 1) {
+        launch_cluster<2>(a, d_items, n_items, kSliceBits, s);
+    } else if (n == kSliceBits + 2) {
+        launch_cluster<4>(a, d_items, n_items, kSliceBits, s);
+    } else if (n == kSliceBits + 3) {
+        launch_cluster<8>(a, d_items, n_items, kSliceBits, s);
+    } else {
+        fail(PTSBE_ERR_UNSUPPORTED, "cluster sampler handles n <= 17");
+    }
+}
+
+size_t sample_global_scratch_doubles(int n) {
+    const size_t nb = (size_t)1 << (n - kSliceBits);
+    return ((size_t)1 << n) + 3 * nb + 8;
+}
+
+void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1,
+                          uint64_t out0, cudaStream_t s) {
+    const int n = a.n;
+    if (j1 <= j0) return;
+    const uint32_t nb = 1u << (n - kSliceBits);
+    double* cdf = a.scratch;
+    double* btot = cdf + ((size_t)1 << n);
+    double* boff = btot + nb;
+    double* bend = boff + nb;
+    static bool configured = false;
+    if (!configured) {
+        PTSBE_CUDA(cudaFuncSetAttribute(k_block_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+        configured = true;
+    }
+    const float2* amps = a.states + ((size_t)state << n);
+    k_block_prefix<<<nb, kSampleThreads, cdf_smem_bytes(kSliceBits, kSampleThreads), s>>>(amps, cdf, btot);
+    PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    k_block_scan<<<1, 1024, 0, s>>>(btot, boff, bend, nb);
+    PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    k_block_add<<<nb, 256, 0, s>>>(cdf, boff);
+    PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    const uint64_t m = j1 - j0;
+    uint32_t blocks = (uint32_t)((m + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_search_global<<<blocks, 256, 0, s>>>(a, cdf, bend, nb, state, alpha, j0, j1, out0);
+    PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+}
+
+void launch_fill(uint32_t* bits, uint64_t count, uint32_t v, cudaStream_t s) {
+    if (count == 0) return;
+    uint32_t blocks = (uint32_t)((count + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    k_fill<<<blocks, 256, 0, s>>>(bits, count, v);
+    PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+}
+
+}  // namespace ptsbe

@@ -1,0 +1,183 @@
+"""Marshalling between Python objects and the libptsbe C ABI.
+
+Circuits come in the flat encoding of ``workloads`` (op_ints, op_params, channels); device
+buffers are PyTorch tensors whose pointers and the current CUDA stream are handed to the
+library. No arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import capi
+
+
+@dataclass
+class KrausSetInfo:
+    set_id: int
+    circuit_id: int
+    count: int
+    n_entries: int
+    total_shots: int
+    offsets: np.ndarray
+    sites: np.ndarray
+    kidx: np.ndarray
+    mult: np.ndarray
+    q: np.ndarray
+    shots: np.ndarray
+    shot_offsets: np.ndarray
+
+    def entries(self, i):
+        b, e = int(self.offsets[i]), int(self.offsets[i + 1])
+        return list(zip(self.sites[b:e].tolist(), self.kidx[b:e].tolist()))
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+class Ptsbe:
+    """One libptsbe context. device=-1 gives a host-only context (registration and PTS)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.device = device
+        self._keep = []
+        if stream is None and device >= 0:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.ctx = capi.ptsbe_create(device, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            capi.ptsbe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        capi.ptsbe_set_stream(self.ctx, stream)
+
+    def synchronize(self):
+        capi.ptsbe_synchronize(self.ctx)
+
+    # -- registration ----------------------------------------------------------------------------
+    def register(self, circ) -> int:
+        n_ops = circ.n_ops
+        ops = (capi.ptsbe_op * max(n_ops, 1))()
+        oi = np.asarray(circ.op_ints)
+        op = np.asarray(circ.op_params)
+        for i in range(n_ops):
+            o = ops[i]
+            o.kind, o.id, o.n_targets = int(oi[i, 0]), int(oi[i, 1]), int(oi[i, 2])
+            o.targets[0], o.targets[1] = int(oi[i, 3]), int(oi[i, 4])
+            o.params[0], o.params[1], o.params[2] = float(op[i, 0]), float(op[i, 1]), float(op[i, 2])
+        n_ch = len(circ.ch_params)
+        chans = (capi.ptsbe_channel * max(n_ch, 1))()
+        keep = []
+        for j in range(n_ch):
+            kind, arity, nk = (int(x) for x in circ.ch_ints[j])
+            c = chans[j]
+            c.kind, c.arity, c.n_kraus, c.param = kind, arity, nk, float(circ.ch_params[j])
+            off = int(circ.ch_kraus_off[j])
+            if off >= 0:
+                d = 1 << arity
+                arr = np.ascontiguousarray(circ.ch_kraus[off: off + nk * d * d]).view(np.float64).copy()
+                keep.append(arr)
+                c.kraus = arr.ctypes.data_as(C.POINTER(C.c_double))
+        cg = np.ascontiguousarray(np.asarray(circ.custom_gates, np.complex128)).view(np.float64).reshape(-1)
+        cg_ptr = cg.ctypes.data if cg.size else None
+        return capi.ptsbe_register_circuit(self.ctx, circ.n_qubits, ops, n_ops, chans, n_ch, cg_ptr,
+                                           int(circ.custom_gates.shape[0]))
+
+    def release_circuit(self, cid):
+        capi.ptsbe_release_circuit(self.ctx, cid)
+
+    def set_timing(self, enable: bool):
+        capi.ptsbe_set_timing(self.ctx, enable)
+
+    def timing(self, kernel_class: int, reset: bool = False):
+        """(milliseconds, launches, algorithmic bytes) accumulated for one kernel class."""
+        return capi.ptsbe_get_timing(self.ctx, kernel_class, reset)
+
+    def circuit_info(self, cid):
+        return capi.ptsbe_circuit_info(self.ctx, cid)
+
+    # -- pre-trajectory sampling -------------------------------------------------------------------
+    def sample_kraus(self, cid: int, mode: str, seed: int = 0, *, nsamples=0, k=0, p_min=0.0, p_max=1.0,
+                     total_shots=0, shots_per_set=0, shot_alloc=None, targeted=None, targeted_shots=None,
+                     export=True):
+        p = capi.ptsbe_pts_params()
+        modes = dict(proportional=capi.PTSBE_PTS_PROPORTIONAL, topk=capi.PTSBE_PTS_TOPK,
+                     band=capi.PTSBE_PTS_BAND, targeted=capi.PTSBE_PTS_TARGETED, literal=capi.PTSBE_PTS_LITERAL)
+        p.mode = modes[mode]
+        allocs = dict(count=capi.PTSBE_SHOTS_BY_COUNT, uniform=capi.PTSBE_SHOTS_UNIFORM,
+                      prob=capi.PTSBE_SHOTS_BY_PROB, given=capi.PTSBE_SHOTS_GIVEN)
+        if shot_alloc is None:
+            shot_alloc = {"proportional": "count", "topk": "prob", "band": "prob", "literal": "uniform",
+                          "targeted": "given" if targeted_shots is not None else "prob"}[mode]
+        p.shot_alloc = allocs[shot_alloc]
+        p.nsamples, p.k, p.p_min, p.p_max = nsamples, k, p_min, p_max
+        p.total_shots, p.shots_per_set = total_shots, shots_per_set
+        keep = []
+        if targeted is not None:
+            offs, sites, ks = [0], [], []
+            for s in targeted:
+                for (a, b) in s:
+                    sites.append(a); ks.append(b)
+                offs.append(len(sites))
+            to = np.asarray(offs, np.uint32); ts = np.asarray(sites + [0], np.uint32); tk = np.asarray(ks + [0], np.uint8)
+            keep += [to, ts, tk]
+            p.t_count = len(targeted)
+            p.t_offsets = to.ctypes.data_as(C.POINTER(C.c_uint32))
+            p.t_sites = ts.ctypes.data_as(C.POINTER(C.c_uint32))
+            p.t_kidx = tk.ctypes.data_as(C.POINTER(C.c_uint8))
+            if targeted_shots is not None:
+                tsh = np.ascontiguousarray(targeted_shots, np.uint64)
+                keep.append(tsh)
+                p.t_shots = tsh.ctypes.data_as(C.POINTER(C.c_uint64))
+        sid, cnt, ne, tot = capi.ptsbe_sample_kraus(self.ctx, cid, p, seed)
+        info = KrausSetInfo(sid, cid, cnt, ne, tot, *(np.zeros(0),) * 7)
+        if export:
+            self.export(info)
+        return info
+
+    def export(self, info: KrausSetInfo):
+        n, e = info.count, info.n_entries
+        info.offsets = np.zeros(n + 1, np.uint32)
+        info.sites = np.zeros(max(e, 1), np.uint32)
+        info.kidx = np.zeros(max(e, 1), np.uint8)
+        info.mult = np.zeros(max(n, 1), np.uint64)
+        info.q = np.zeros(max(n, 1), np.float64)
+        info.shots = np.zeros(max(n, 1), np.uint64)
+        info.shot_offsets = np.zeros(n + 1, np.uint64)
+        v = capi.ptsbe_set_view(info.offsets.ctypes.data, info.sites.ctypes.data, info.kidx.ctypes.data,
+                                info.mult.ctypes.data, info.q.ctypes.data, info.shots.ctypes.data,
+                                info.shot_offsets.ctypes.data)
+        capi.ptsbe_set_export(self.ctx, info.set_id, v)
+        info.sites, info.kidx = info.sites[:e], info.kidx[:e]
+        info.mult, info.q, info.shots = info.mult[:n], info.q[:n], info.shots[:n]
+        return info
+
+    def release_set(self, info: KrausSetInfo):
+        capi.ptsbe_release_set(self.ctx, info.set_id)
+
+    # -- batched execution ---------------------------------------------------------------------------
+    def evolve(self, info: KrausSetInfo, first: int, count: int, states, weights=None, status=None,
+               prefix_reuse: bool = False):
+        flags = capi.PTSBE_EVOLVE_PREFIX_REUSE if prefix_reuse else 0
+        capi.ptsbe_evolve_batch(self.ctx, info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), flags)
+
+    def sample(self, info: KrausSetInfo, first: int, count: int, states, status, seed: int, bits):
+        capi.ptsbe_sample_shots(self.ctx, info.set_id, first, count, _ptr(states), _ptr(status), seed, _ptr(bits),
+                                bits.numel())
+
+    def pershot(self, cid: int, seed: int, first_shot: int, n_shots: int, bits, kraus=None):
+        capi.ptsbe_pershot_run(self.ctx, cid, seed, first_shot, n_shots, _ptr(bits), _ptr(kraus))
