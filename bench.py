@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
+    ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "sweep", "registers"])
     return ap.parse_args()
 
 
@@ -228,6 +229,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     P = Ptsbe(device=local, stream=stream.cuda_stream)
+    P.set_evolve_kernel(args.evolve_kernel)
     states = torch.empty((K, 1 << n), dtype=torch.complex64, device=dev)
     weights = torch.empty(K, dtype=torch.float64, device=dev)
     status = torch.empty(K, dtype=torch.uint8, device=dev)

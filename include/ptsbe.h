@@ -271,6 +271,20 @@ PTSBE_API int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t se
                       uint64_t n_shots, uint32_t* d_bits, uint8_t* d_kraus);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Options                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+enum {
+    /* Kernel for the tile passes of ptsbe_evolve_batch: 0 auto, 1 shared-memory sweeps (one pass
+     * of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
+     * registers, the tile re-shuffled through shared memory between register groups). */
+    PTSBE_OPT_EVOLVE_KERNEL = 0
+};
+
+/* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
+PTSBE_API int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Instrumentation                                                                           */
 /* ---------------------------------------------------------------------------------------- */
 

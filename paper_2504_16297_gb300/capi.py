@@ -16,6 +16,7 @@ PTSBE_OP_GATE, PTSBE_OP_NOISE = 0, 1
 PTSBE_PTS_PROPORTIONAL, PTSBE_PTS_TOPK, PTSBE_PTS_BAND, PTSBE_PTS_TARGETED, PTSBE_PTS_LITERAL = range(5)
 PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVEN = range(4)
 PTSBE_EVOLVE_PREFIX_REUSE = 1
+PTSBE_OPT_EVOLVE_KERNEL = 0
 PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT = range(4)
 
 
@@ -75,6 +76,7 @@ _PROTOS = {
                                      C.c_uint64, C.c_void_p, C.c_uint64]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "ptsbe_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "ptsbe_get_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
                                    C.POINTER(C.c_double), C.c_int]),
@@ -192,6 +194,10 @@ def ptsbe_h2d_bytes() -> int:
     if st != PTSBE_OK:
         raise PtsbeError(st, "ptsbe_h2d_bytes failed")
     return n.value
+
+
+def ptsbe_set_option(ctx, option: int, value: int):
+    check(ctx, load().ptsbe_set_option(ctx, option, value))
 
 
 def ptsbe_set_timing(ctx, enable: bool):

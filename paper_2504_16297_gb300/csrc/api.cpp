@@ -54,6 +54,7 @@ struct ptsbe_ctx {
     DevBuf nodes, part, scale, items, scratch, pershot;
     std::vector<unsigned char> host_blob;
     bool timing = false;
+    int evolve_kernel = 0;
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
     cudaEvent_t take_event(ClassTimer& t) {
@@ -161,7 +162,7 @@ T* dev_upload(const std::vector<T>& v) {
 
 void free_device_circuit(DeviceCircuit& d) {
     cudaFree(d.ops); cudaFree(d.micro); cudaFree(d.mats); cudaFree(d.chans);
-    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.hi);
+    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.groups); cudaFree(d.hi);
     d = DeviceCircuit{};
 }
 
@@ -172,6 +173,7 @@ void upload_circuit(const Circuit& c, const Plan& P, DeviceCircuit& d) {
     d.chans = dev_upload(c.dchans);
     d.site_op = dev_upload(c.site_op);
     d.stages = dev_upload(P.stages);
+    d.groups = dev_upload(P.groups);
     d.hi = dev_upload(P.hi);
 }
 
@@ -446,7 +448,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
 
         EvolveArgs A{};
         A.ops = c.dev.ops; A.micro = c.dev.micro; A.mats = c.dev.mats; A.chans = c.dev.chans;
-        A.site_op = c.dev.site_op; A.stages = c.dev.stages; A.hi = c.dev.hi;
+        A.site_op = c.dev.site_op; A.stages = c.dev.stages; A.groups = c.dev.groups; A.hi = c.dev.hi;
         A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
         A.ent_site = s.d_site; A.ent_k = s.d_k;
         A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
@@ -479,7 +481,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
                         if ((uint32_t)P.op_stage[child_op[ci]] == j) bytes += sbytes;
                 }
                 ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
-                    launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream);
+                    launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
                 });
             }
         if (ob > 0)
@@ -533,6 +535,17 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
                 const double sb = 8.0 * (double)(1ull << c.n);
                 if (m) ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
             }
+        }
+    });
+}
+
+int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
+    return guarded(ctx, [&] {
+        if (option == PTSBE_OPT_EVOLVE_KERNEL) {
+            if (value < 0 || value > 2) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0, 1 or 2");
+            ctx->evolve_kernel = (int)value;
+        } else {
+            fail(PTSBE_ERR_INVALID, "unknown option");
         }
     });
 }

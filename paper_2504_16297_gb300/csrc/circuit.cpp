@@ -276,6 +276,8 @@ bool kron_split(const cd* m, cd* A, cd* B) {
 
 }  // namespace
 
+void fuse_gates_with_noise(Circuit& c);
+
 void build_device_ops(Circuit& c) {
     c.dops.clear(); c.dmicro.clear(); c.dmats.clear(); c.dchans.clear();
     // channels: micro ops of every Kraus operator
@@ -317,6 +319,7 @@ void build_device_ops(Circuit& c) {
     for (size_t i = 0; i < c.ops.size(); ++i) {
         const ptsbe_op& o = c.ops[i];
         DevOp d{};
+        d.fkind = DOP_NOP;
         d.q0 = (uint8_t)o.targets[0];
         d.q1 = (uint8_t)(o.n_targets == 2 ? o.targets[1] : o.targets[0]);
         d.nt = (uint8_t)o.n_targets;
@@ -344,6 +347,131 @@ void build_device_ops(Circuit& c) {
         }
         c.dops.push_back(d);
     }
+    fuse_gates_with_noise(c);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gate fusion: gate G followed by noise sites on (a subset of) its own qubits. For the "no error"
+// branch every such site applies its Kraus operator 0 (U_0 for a unitary mixture), so the whole
+// block is the single operator K0_m ... K0_1 G. Sets with an error among those sites fall back to
+// applying the ops one by one, so the result is the same operator product either way.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// 4x4 operator of `m` (dim x dim on qubits qs) within the two-qubit space (q0, q1), local index
+// 2*bit(q0) + bit(q1).
+void embed2(const cd* m, int dim, const uint32_t* qs, uint32_t q0, uint32_t q1, cd* out) {
+    for (int i = 0; i < 16; ++i) out[i] = 0;
+    for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 4; ++col) {
+            const int r0 = r >> 1, r1 = r & 1, c0 = col >> 1, c1 = col & 1;
+            auto bit = [&](int b0, int b1, uint32_t q) { return q == q0 ? b0 : b1; };
+            if (dim == 2) {
+                const uint32_t q = qs[0];
+                // identity on the other qubit
+                const int other_same = (q == q0) ? (r1 == c1) : (r0 == c0);
+                if (!other_same) continue;
+                out[r * 4 + col] = m[bit(r0, r1, q) * 2 + bit(c0, c1, q)];
+            } else {
+                const int lr = bit(r0, r1, qs[0]) * 2 + bit(r0, r1, qs[1]);
+                const int lc = bit(c0, c1, qs[0]) * 2 + bit(c0, c1, qs[1]);
+                out[r * 4 + col] = m[lr * 4 + lc];
+            }
+        }
+}
+
+void matmul(const cd* A, const cd* B, cd* out, int d) {  // out = A B
+    cd t[16];
+    for (int r = 0; r < d; ++r)
+        for (int col = 0; col < d; ++col) {
+            cd s = 0;
+            for (int k = 0; k < d; ++k) s += A[r * d + k] * B[k * d + col];
+            t[r * d + col] = s;
+        }
+    for (int i = 0; i < d * d; ++i) out[i] = t[i];
+}
+
+bool is_identity(const cd* m, int d) {
+    for (int r = 0; r < d; ++r)
+        for (int col = 0; col < d; ++col)
+            if (m[r * d + col] != (r == col ? cd(1.0) : cd(0.0))) return false;
+    return true;
+}
+
+}  // namespace
+
+void fuse_gates_with_noise(Circuit& c) {
+    const size_t nops = c.ops.size();
+    for (size_t i = 0; i < nops; ++i) {
+        const ptsbe_op& g = c.ops[i];
+        if (g.kind != PTSBE_OP_GATE) continue;
+        size_t j = i + 1;
+        while (j < nops && c.ops[j].kind == PTSBE_OP_NOISE) {
+            const ptsbe_op& nz = c.ops[j];
+            bool inside = true;
+            for (uint32_t t = 0; t < nz.n_targets; ++t) {
+                const uint32_t q = nz.targets[t];
+                if (!(q == g.targets[0] || (g.n_targets == 2 && q == g.targets[1]))) inside = false;
+            }
+            if (!inside) break;
+            ++j;
+        }
+        if (j == i + 1) continue;
+        const int dim = g.n_targets == 2 ? 4 : 2;
+        cd M[16];
+        int gd;
+        const double* custom = nullptr;
+        if (g.id == PTSBE_G_U1 || g.id == PTSBE_G_U2) custom = c.custom.data() + 32 * (size_t)g.params[0];
+        gate_matrix(g.id, g.params, custom, M, gd);
+        bool any = false;
+        for (size_t t = i + 1; t < j; ++t) {
+            const ptsbe_op& nz = c.ops[t];
+            const HostChannel& ch = c.ch[nz.id];
+            const cd* K0 = ch.mixture ? &ch.U[0] : &ch.K[0];
+            if (is_identity(K0, (int)ch.dim)) continue;
+            any = true;
+            if (dim == 2) {
+                matmul(K0, M, M, 2);
+            } else {
+                cd E[16];
+                embed2(K0, (int)ch.dim, nz.targets, g.targets[0], g.targets[1], E);
+                matmul(E, M, M, 4);
+            }
+        }
+        DevOp& d = c.dops[i];
+        d.fend = (uint32_t)j;
+        d.fsite1 = c.dops[j - 1].site + 1;
+        if (!any) {              // only identity no-error operators: skip them in one step
+            d.fkind = d.kind; d.fmat = d.mat; d.fperm = 0;
+            continue;
+        }
+        if (dim == 2) {
+            DevMicro u = micro1(c, M, 0);
+            d.fkind = u.kind; d.fmat = u.mat;
+        } else {
+            // monomial? one nonzero per row and column
+            int perm[4];
+            bool mono = true;
+            for (int r = 0; r < 4 && mono; ++r) {
+                int nz = -1;
+                for (int col = 0; col < 4; ++col)
+                    if ((float)M[r * 4 + col].real() != 0.0f || (float)M[r * 4 + col].imag() != 0.0f) {
+                        if (nz >= 0) mono = false;
+                        nz = col;
+                    }
+                if (nz < 0) mono = false;
+                perm[r] = nz;
+            }
+            if (mono) {
+                cd dv[4];
+                uint8_t packed = 0;
+                for (int r = 0; r < 4; ++r) { dv[r] = M[r * 4 + perm[r]]; packed |= (uint8_t)(perm[r] << (2 * r)); }
+                d.fkind = DOP_M2; d.fmat = push_mat(c, dv, 4); d.fperm = packed;
+            } else {
+                d.fkind = DOP_G2; d.fmat = push_mat(c, M, 16);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -361,6 +489,49 @@ uint64_t op_mask(const Circuit& c, size_t i) {
 bool general_noise(const Circuit& c, size_t i) {
     const ptsbe_op& o = c.ops[i];
     return o.kind == PTSBE_OP_NOISE && !c.ch[o.id].mixture;
+}
+
+uint32_t tile_mask(const Circuit& c, const DevStage& st, size_t i) {
+    const ptsbe_op& o = c.ops[i];
+    uint32_t m = 1u << st.pos[o.targets[0]];
+    if (o.n_targets == 2) m |= 1u << st.pos[o.targets[1]];
+    return m;
+}
+
+void emit_group(Plan& P, uint32_t b, uint32_t e, const std::vector<int>& used) {
+    DevGroup g{};
+    g.op_begin = b; g.op_end = e;
+    std::memset(g.rbit, 0xFF, sizeof(g.rbit));
+    std::memset(g.lane_pos, 0xFF, sizeof(g.lane_pos));
+    int nb = 0;
+    uint32_t taken = 0;
+    for (int p : used) { g.reg_pos[nb] = (uint8_t)p; g.rbit[p] = (uint8_t)nb; taken |= 1u << p; ++nb; }
+    // fill with the highest free positions so the lanes keep the low (contiguous) ones
+    for (int p = P.tb - 1; p >= 0 && nb < kRegBits; --p)
+        if (!(taken & (1u << p))) { g.reg_pos[nb] = (uint8_t)p; g.rbit[p] = (uint8_t)nb; taken |= 1u << p; ++nb; }
+    int nl = 0;
+    for (int p = 0; p < P.tb; ++p) if (!(taken & (1u << p))) g.lane_pos[nl++] = (uint8_t)p;
+    P.groups.push_back(g);
+}
+
+// Splits the ops of a stage into register groups of at most kRegBits tile positions each.
+void plan_groups(Plan& P, const Circuit& c, DevStage& st) {
+    st.group_begin = st.group_end = (uint32_t)P.groups.size();
+    if (P.tb < kRegBits || st.op_end == st.op_begin) return;
+    uint32_t cur = 0, gb = st.op_begin;
+    std::vector<int> used;
+    for (uint32_t i = st.op_begin; i < st.op_end; ++i) {
+        const uint32_t m = tile_mask(c, st, i);
+        if (__builtin_popcount(cur | m) > kRegBits) {
+            emit_group(P, gb, i, used);
+            cur = 0; used.clear(); gb = i;
+        }
+        for (int p = 0; p < P.tb; ++p)
+            if ((m & (1u << p)) && !(cur & (1u << p))) used.push_back(p);
+        cur |= m;
+    }
+    emit_group(P, gb, st.op_end, used);
+    st.group_end = (uint32_t)P.groups.size();
 }
 
 void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, bool probe, uint32_t probe_op) {
@@ -387,6 +558,7 @@ void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, 
         P.hi.push_back(g);
     }
     for (uint32_t i = b; i < e; ++i) P.op_stage[i] = (int32_t)P.stages.size();
+    plan_groups(P, c, st);
     P.stages.push_back(st);
 }
 

@@ -132,7 +132,26 @@ __device__ void t_g2(float2* s, int tb, int pa, int pb, const float2* __restrict
     }
 }
 
-__device__ __forceinline__ void apply_micro(float2* s, int tb, uint8_t kind, int pa, int pb, const float2* m) {
+// monomial 4x4: out[l] = d[l] * in[perm_l] on local index 2*bit(pa) + bit(pb)
+__device__ __forceinline__ float2 pick4(const float2 (&x)[4], int p) {
+    return p == 0 ? x[0] : (p == 1 ? x[1] : (p == 2 ? x[2] : x[3]));
+}
+__device__ void t_m2(float2* s, int tb, int pa, int pb, const float2* __restrict__ m, uint32_t perm) {
+    const uint32_t q = 1u << (tb - 2);
+    const float2 d[4] = {m[0], m[1], m[2], m[3]};
+    for (uint32_t i = threadIdx.x; i < q; i += blockDim.x) {
+        const uint32_t b = ins00(i, pa, pb);
+        const uint32_t idx[4] = {b, b | (1u << pb), b | (1u << pa), b | (1u << pa) | (1u << pb)};
+        float2 x[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) x[l] = s[idx[l]];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) s[idx[l]] = cmul(d[l], pick4(x, (perm >> (2 * l)) & 3));
+    }
+}
+
+__device__ __forceinline__ void apply_micro(float2* s, int tb, uint8_t kind, int pa, int pb, const float2* m,
+                                            uint32_t perm = 0) {
     switch (kind) {
     case DOP_G1: t_g1(s, tb, pa, m); break;
     case DOP_D1: t_d1(s, tb, pa, m); break;
@@ -141,6 +160,7 @@ __device__ __forceinline__ void apply_micro(float2* s, int tb, uint8_t kind, int
     case DOP_CZ: t_cz(s, tb, pa, pb); break;
     case DOP_SWAP: t_swap(s, tb, pa, pb); break;
     case DOP_G2: t_g2(s, tb, pa, pb, m); break;
+    case DOP_M2: t_m2(s, tb, pa, pb, m, perm); break;
     default: break;
     }
 }
@@ -169,8 +189,21 @@ __device__ void tile_store(const float2* tile, float2* g, int tb, int lb, const 
     }
 }
 
-// Deterministic CTA sum in FP64 of per-thread values; every thread gets the result.
+// Deterministic CTA sum in FP64 of per-thread values; every thread gets the result. Blocks
+// smaller than a warp add their values sequentially.
 __device__ double cta_sum(double v, double* red) {
+    if (blockDim.x < 32) {
+        __syncthreads();
+        red[threadIdx.x] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (uint32_t i = 0; i < blockDim.x; ++i) t += red[i];
+            red[32] = t;
+        }
+        __syncthreads();
+        return red[32];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -248,9 +281,20 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
                 apply_micro(tile, tb, mi.kind, pa, pb, a.mats + mi.mat);
                 __syncthreads();
             }
-        } else if (o.kind != DOP_NOP) {
-            apply_micro(tile, tb, o.kind, st.pos[o.q0], st.pos[o.q1], a.mats + o.mat);
-            __syncthreads();
+        } else {
+            if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1) && (c >= ce || a.child_op[c] >= o.fend)) {
+                // no error and no branch inside the fused block: gate and no-error operators at once
+                if (o.fkind != DOP_NOP) {
+                    apply_micro(tile, tb, o.fkind, st.pos[o.q0], st.pos[o.q1], a.mats + o.fmat, o.fperm);
+                    __syncthreads();
+                }
+                op = o.fend - 1;
+                continue;
+            }
+            if (o.kind != DOP_NOP) {
+                apply_micro(tile, tb, o.kind, st.pos[o.q0], st.pos[o.q1], a.mats + o.mat);
+                __syncthreads();
+            }
         }
     }
 
@@ -304,6 +348,326 @@ __global__ void k_evolve_scale(float2* states, int n, const float* __restrict__ 
     }
 }
 
+
+// --- register-blocked execution --------------------------------------------------------------------
+// Each thread keeps NR = 2^kRegBits amplitudes in registers; register bit b of the index j is the
+// tile position reg_pos[b] of the current group. Every op of the group acts on register bits only,
+// so it runs as an unrolled loop over j with compile-time partner indices (a Pauli X or CX is a
+// register permutation).
+constexpr int NR = 1 << kRegBits;
+typedef float2 RegArr[NR];
+
+template <int B>
+__device__ __forceinline__ void rg1(RegArr& v, const float2* __restrict__ m) {
+    const float2 m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+    if (m00.y == 0.f && m01.y == 0.f && m10.y == 0.f && m11.y == 0.f) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << B)) continue;
+            const float2 x = v[j], y = v[j | (1 << B)];
+            v[j] = make_float2(fmaf(m00.x, x.x, m01.x * y.x), fmaf(m00.x, x.y, m01.x * y.y));
+            v[j | (1 << B)] = make_float2(fmaf(m10.x, x.x, m11.x * y.x), fmaf(m10.x, x.y, m11.x * y.y));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << B)) continue;
+            const float2 x = v[j], y = v[j | (1 << B)];
+            v[j] = cmul2(m00, x, m01, y);
+            v[j | (1 << B)] = cmul2(m10, x, m11, y);
+        }
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void rd1(RegArr& v, const float2* __restrict__ m) {
+    const float2 d0 = m[0], d1 = m[1];
+    if (d0.x == 1.f && d0.y == 0.f) {
+        if (d1.y == 0.f) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if (j & (1 << B)) { v[j].x *= d1.x; v[j].y *= d1.x; }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if (j & (1 << B)) v[j] = cmul(d1, v[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) v[j] = cmul((j & (1 << B)) ? d1 : d0, v[j]);
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void rx1(RegArr& v, const float2* __restrict__ m) {
+    const float2 a = m[0], b = m[1];
+    if (a.x == 1.f && a.y == 0.f && b.x == 1.f && b.y == 0.f) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << B)) continue;
+            const float2 t = v[j]; v[j] = v[j | (1 << B)]; v[j | (1 << B)] = t;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (j & (1 << B)) continue;
+            const float2 x = v[j], y = v[j | (1 << B)];
+            v[j] = cmul(a, y);
+            v[j | (1 << B)] = cmul(b, x);
+        }
+    }
+}
+
+struct RCX {   // control bit A, target bit B
+    template <int A, int B>
+    __device__ __forceinline__ static void run(RegArr& v, const float2*) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << A)) && !(j & (1 << B))) { const float2 t = v[j]; v[j] = v[j | (1 << B)]; v[j | (1 << B)] = t; }
+    }
+};
+struct RCZ {
+    template <int A, int B>
+    __device__ __forceinline__ static void run(RegArr& v, const float2*) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << A)) && (j & (1 << B))) { v[j].x = -v[j].x; v[j].y = -v[j].y; }
+    }
+};
+struct RSWAP {
+    template <int A, int B>
+    __device__ __forceinline__ static void run(RegArr& v, const float2*) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+            if ((j & (1 << A)) && !(j & (1 << B))) {
+                const int k = (j ^ (1 << A)) | (1 << B);
+                const float2 t = v[j]; v[j] = v[k]; v[k] = t;
+            }
+    }
+};
+struct RM2 {   // monomial on local index 2*bit(A) + bit(B); perm passed in `perm`
+    template <int A, int B>
+    __device__ __forceinline__ static void run(RegArr& v, const float2* __restrict__ m, uint32_t perm) {
+        const float2 d[4] = {m[0], m[1], m[2], m[3]};
+        const int p0 = perm & 3, p1 = (perm >> 2) & 3, p2 = (perm >> 4) & 3, p3 = (perm >> 6) & 3;
+        const bool real = d[0].y == 0.f && d[1].y == 0.f && d[2].y == 0.f && d[3].y == 0.f;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if ((j & (1 << A)) || (j & (1 << B))) continue;
+            const int idx[4] = {j, j | (1 << B), j | (1 << A), j | (1 << A) | (1 << B)};
+            const float2 x[4] = {v[idx[0]], v[idx[1]], v[idx[2]], v[idx[3]]};
+            const float2 y0 = pick4(x, p0), y1 = pick4(x, p1), y2 = pick4(x, p2), y3 = pick4(x, p3);
+            if (real) {
+                v[idx[0]] = make_float2(d[0].x * y0.x, d[0].x * y0.y);
+                v[idx[1]] = make_float2(d[1].x * y1.x, d[1].x * y1.y);
+                v[idx[2]] = make_float2(d[2].x * y2.x, d[2].x * y2.y);
+                v[idx[3]] = make_float2(d[3].x * y3.x, d[3].x * y3.y);
+            } else {
+                v[idx[0]] = cmul(d[0], y0); v[idx[1]] = cmul(d[1], y1);
+                v[idx[2]] = cmul(d[2], y2); v[idx[3]] = cmul(d[3], y3);
+            }
+        }
+    }
+};
+
+#define PTSBE_C1(F, B) case B: F<B>(v, m); break;
+#define PTSBE_C2(K, A, B) case (A) * 8 + (B): K::template run<A, B>(v, m); break;
+
+#define PTSBE_C2P(K, A, B) case (A) * 8 + (B): K::template run<A, B>(v, m, perm); break;
+template <class K>
+__device__ __forceinline__ void dispatch2p(RegArr& v, int a, int b, const float2* m, uint32_t perm) {
+    switch (a * 8 + b) {
+        PTSBE_C2P(K, 0, 1) PTSBE_C2P(K, 0, 2) PTSBE_C2P(K, 0, 3)
+        PTSBE_C2P(K, 1, 0) PTSBE_C2P(K, 1, 2) PTSBE_C2P(K, 1, 3)
+        PTSBE_C2P(K, 2, 0) PTSBE_C2P(K, 2, 1) PTSBE_C2P(K, 2, 3)
+        PTSBE_C2P(K, 3, 0) PTSBE_C2P(K, 3, 1) PTSBE_C2P(K, 3, 2)
+        default: break;
+    }
+}
+
+template <class K>
+__device__ __forceinline__ void dispatch2(RegArr& v, int a, int b, const float2* m) {
+    switch (a * 8 + b) {
+        PTSBE_C2(K, 0, 1) PTSBE_C2(K, 0, 2) PTSBE_C2(K, 0, 3)
+        PTSBE_C2(K, 1, 0) PTSBE_C2(K, 1, 2) PTSBE_C2(K, 1, 3)
+        PTSBE_C2(K, 2, 0) PTSBE_C2(K, 2, 1) PTSBE_C2(K, 2, 3)
+        PTSBE_C2(K, 3, 0) PTSBE_C2(K, 3, 1) PTSBE_C2(K, 3, 2)
+        default: break;
+    }
+}
+static_assert(kRegBits == 4, "dispatch tables are written for 4 register bits");
+
+__device__ __forceinline__ void apply_reg(RegArr& v, uint8_t kind, int b0, int b1, const float2* m, uint32_t perm = 0) {
+    switch (kind) {
+    case DOP_M2: dispatch2p<RM2>(v, b0, b1, m, perm); break;
+    case DOP_G1: switch (b0) { PTSBE_C1(rg1, 0) PTSBE_C1(rg1, 1) PTSBE_C1(rg1, 2) PTSBE_C1(rg1, 3) default: break; } break;
+    case DOP_D1: switch (b0) { PTSBE_C1(rd1, 0) PTSBE_C1(rd1, 1) PTSBE_C1(rd1, 2) PTSBE_C1(rd1, 3) default: break; } break;
+    case DOP_X1: switch (b0) { PTSBE_C1(rx1, 0) PTSBE_C1(rx1, 1) PTSBE_C1(rx1, 2) PTSBE_C1(rx1, 3) default: break; } break;
+    case DOP_CX: dispatch2<RCX>(v, b0, b1, m); break;
+    case DOP_CZ: dispatch2<RCZ>(v, b0, b1, m); break;
+    case DOP_SWAP: dispatch2<RSWAP>(v, b0, b1, m); break;
+    default: break;
+    }
+}
+
+// Tile index of register slot j for a thread with lane base `base`.
+__device__ __forceinline__ uint32_t slot_index(uint32_t base, const uint32_t (&bitv)[kRegBits], int j) {
+    uint32_t o = base;
+#pragma unroll
+    for (int b = 0; b < kRegBits; ++b)
+        if (j & (1 << b)) o |= bitv[b];
+    return o;
+}
+
+// General 4x4 operator on register bits (ba, bb), local index 2*bit(ba) + bit(bb). Every quad
+// lies in one thread's own slots, so the caller parks its registers in its shared-memory slots,
+// this function updates the quads there and the caller reloads -- no barrier, and the rare
+// general case stays out of the unrolled register code (the register array never has its
+// address taken, so it stays in registers).
+__device__ __noinline__ void own_slots_g2(float2* tile, uint32_t base, const uint32_t* bits, int ba, int bb,
+                                          const float2* __restrict__ m) {
+    uint32_t bitv[kRegBits];
+    for (int b = 0; b < kRegBits; ++b) bitv[b] = bits[b];
+    for (int j = 0; j < NR; ++j) {
+        if ((j >> ba) & 1 || (j >> bb) & 1) continue;
+        const int idx[4] = {j, j | (1 << bb), j | (1 << ba), j | (1 << ba) | (1 << bb)};
+        float2 x[4];
+        for (int l = 0; l < 4; ++l) x[l] = tile[slot_index(base, bitv, idx[l])];
+        for (int r = 0; r < 4; ++r) {
+            float2 acc = cmul(m[4 * r], x[0]);
+            for (int l = 1; l < 4; ++l) {
+                const float2 t = cmul(m[4 * r + l], x[l]);
+                acc.x += t.x; acc.y += t.y;
+            }
+            tile[slot_index(base, bitv, idx[r])] = acc;
+        }
+    }
+}
+
+#define PTSBE_G2_VIA_SLOTS(BA, BB, M)                                                                   \
+    do {                                                                                              \
+        _Pragma("unroll") for (int j = 0; j < NR; ++j) tile[slot_index(base, bitv, j)] = v[j];        \
+        own_slots_g2(tile, base, G_bits, (BA), (BB), (M));                                            \
+        _Pragma("unroll") for (int j = 0; j < NR; ++j) v[j] = tile[slot_index(base, bitv, j)];        \
+    } while (0)
+
+__global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DevStage st;
+    __shared__ DevGroup G;
+    __shared__ uint32_t G_bits[kRegBits];
+    __shared__ double red[33];
+    const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
+    float2* tile = reinterpret_cast<float2*>(smem);
+    uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
+    if (threadIdx.x == 0) st = a.stages[stage_idx];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < (1u << (tb - lb)); i += blockDim.x) hi[i] = a.hi[st.hi_off + i];
+    const uint32_t node = nodes[blockIdx.y];
+    const uint32_t tau = blockIdx.x;
+    uint64_t outer = 0;
+    for (int b = 0; b < ob; ++b)
+        if ((tau >> b) & 1u) outer |= 1ull << st.outer_q[b];
+    float2* g = a.states + ((size_t)node << n);
+    const uint32_t nstart = a.node_start[node];
+    const uint32_t start = nstart > st.op_begin ? nstart : st.op_begin;
+    __syncthreads();
+    if (a.node_fresh[node] && stage_idx == 0) {
+        for (uint32_t l = threadIdx.x; l < (1u << tb); l += blockDim.x)
+            tile[l] = make_float2((l == 0 && tau == 0) ? 1.0f : 0.0f, 0.0f);
+    } else {
+        tile_load(tile, g, tb, lb, hi, outer);
+    }
+    uint32_t e = a.node_ebeg[node];
+    const uint32_t ee = a.node_eend[node];
+    while (e < ee && a.site_op[a.ent_site[e]] < start) ++e;
+    uint32_t c = a.node_cbeg[node];
+    const uint32_t ce = a.node_cend[node];
+    while (c < ce && a.child_op[c] < start) ++c;
+
+    for (uint32_t gi = st.group_begin; gi < st.group_end; ++gi) {
+        __syncthreads();                     // tile writes of the previous group, G reuse
+        if (threadIdx.x == 0) {
+            G = a.groups[gi];
+            for (int b = 0; b < kRegBits; ++b) G_bits[b] = 1u << G.reg_pos[b];
+        }
+        __syncthreads();
+        if (G.op_end <= start) continue;
+        uint32_t base = 0;
+        for (int i = 0; i < tb - kRegBits; ++i) base |= ((threadIdx.x >> i) & 1u) << G.lane_pos[i];
+        uint32_t bitv[kRegBits];
+#pragma unroll
+        for (int b = 0; b < kRegBits; ++b) bitv[b] = 1u << G.reg_pos[b];
+        RegArr v;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) v[j] = tile[slot_index(base, bitv, j)];
+        const uint32_t op0 = G.op_begin > start ? G.op_begin : start;
+        for (uint32_t op = op0; op < G.op_end; ++op) {
+            const DevOp o = a.ops[op];
+            if (o.kind == DOP_NOISE) {
+                while (c < ce && a.child_op[c] == op) {
+                    // checkpoint for a prefix-reuse child: every thread writes its slots
+                    float2* gc = a.states + ((size_t)a.child_node[c] << n);
+                    uint32_t bb = base;
+                    asm volatile("" : "+r"(bb));   // recompute slot indices here, do not keep 32 live
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) gc[gidx(slot_index(bb, bitv, j), lb, hi, outer)] = v[j];
+                    ++c;
+                }
+                uint32_t k = 0;
+                if (e < ee && a.ent_site[e] == o.site) { k = a.ent_k[e]; ++e; }
+                const uint32_t u0 = a.chans[o.ch].micro_off[k], u1 = a.chans[o.ch].micro_off[k + 1];
+                for (uint32_t u = u0; u < u1; ++u) {
+                    const DevMicro mi = a.micro[u];
+                    if (mi.kind == DOP_G2) {
+                        PTSBE_G2_VIA_SLOTS(G.rbit[st.pos[o.q0]], G.rbit[st.pos[o.q1]], a.mats + mi.mat);
+                        continue;
+                    }
+                    const int p0 = G.rbit[st.pos[mi.operand == 1 ? o.q1 : o.q0]];
+                    const int p1 = G.rbit[st.pos[o.q1]];
+                    apply_reg(v, mi.kind, p0, p1, a.mats + mi.mat);
+                }
+            } else {
+                const int r0 = G.rbit[st.pos[o.q0]], r1 = G.rbit[st.pos[o.q1]];
+                uint8_t kind = o.kind;
+                uint32_t mat = o.mat, perm = 0;
+                if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1) && (c >= ce || a.child_op[c] >= o.fend)) {
+                    kind = o.fkind; mat = o.fmat; perm = o.fperm;
+                    op = o.fend - 1;         // the absorbed noise ops are done
+                }
+                if (kind == DOP_G2) PTSBE_G2_VIA_SLOTS(r0, r1, a.mats + mat);
+                else if (kind != DOP_NOP) apply_reg(v, kind, r0, r1, a.mats + mat, perm);
+            }
+        }
+        asm volatile("" : "+r"(base));         // slot indices are recomputed, not held across the ops
+#pragma unroll
+        for (int j = 0; j < NR; ++j) tile[slot_index(base, bitv, j)] = v[j];
+    }
+    __syncthreads();
+
+    if (!last) {
+        tile_store(tile, g, tb, lb, hi, outer, 1.0f);
+        return;
+    }
+    const double part = cta_sum(tile_norm_partial(tile, tb), red);
+    if (ob == 0) {
+        const double w = a.wmix[node] * part;
+        const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
+        const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
+        tile_store(tile, g, tb, lb, hi, outer, scale);
+        if (threadIdx.x == 0) {
+            if (a.weights) a.weights[node] = w;
+            if (a.status) a.status[node] = null ? 1 : 0;
+        }
+    } else {
+        tile_store(tile, g, tb, lb, hi, outer, 1.0f);
+        if (threadIdx.x == 0) a.part[((size_t)node << ob) + tau] = part;
+    }
+}
+
+// Default kernel choice for tile passes (measured on GB300, see the design notes).
+constexpr bool kEvolveAutoRegisters = false;
+
 int evolve_threads(int tb) {
     const int amps = 1 << tb;
     int t = amps / 16;
@@ -317,20 +681,26 @@ int evolve_threads(int tb) {
 size_t evolve_smem_bytes(int tb, int lb) { return ((size_t)8 << tb) + ((size_t)4 << (tb - lb)); }
 
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
-                         cudaStream_t s) {
+                         cudaStream_t s, int kernel) {
     if (n_nodes == 0) return;
     static bool configured = false;
     if (!configured) {
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_smem_bytes(kTileMax, 1)));
+        PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)evolve_smem_bytes(kTileMax, 1)));
         configured = true;
     }
     const size_t smem = evolve_smem_bytes(a.tb, a.lb);
-    const int threads = evolve_threads(a.tb);
+    const bool regs = a.tb >= kRegBits && kernel != 1 && (kernel == 2 || kEvolveAutoRegisters);
+    const int threads = regs ? (1 << (a.tb - kRegBits)) : evolve_threads(a.tb);
     const uint32_t tiles = 1u << (a.n - a.tb);
     for (uint32_t b = 0; b < n_nodes; b += 65535) {
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
-        k_evolve_stage<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
+        if (regs)
+            k_evolve_rb<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
+        else
+            k_evolve_stage<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }

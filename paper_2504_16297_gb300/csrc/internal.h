@@ -46,7 +46,8 @@ enum : uint8_t {
     DOP_SWAP = 5,
     DOP_G2 = 6,    // general 4x4 on local index 2*bit(q0) + bit(q1): mat[0..15]
     DOP_NOISE = 7, // noise site: ch, site
-    DOP_NOP = 8    // identity
+    DOP_NOP = 8,   // identity
+    DOP_M2 = 9     // monomial 4x4: out[l] = d[l] * in[perm_l], d = mat[0..3], perm packed 2 bits per l
 };
 
 struct DevOp {
@@ -56,6 +57,15 @@ struct DevOp {
     uint32_t mat;    // offset into the complex64 matrix pool
     uint32_t site;   // DOP_NOISE: site index
     uint32_t ch;     // DOP_NOISE: channel index
+    // A gate fused with the "no error" Kraus operators of the noise sites right after it on its
+    // own qubits. Used when the state's set has no entry among those sites and no prefix-reuse
+    // child branches there; otherwise the ops run one by one.
+    uint8_t fkind;   // DOP_NOP when nothing is fused (kind of the fused operator otherwise)
+    uint8_t fperm;   // DOP_M2 permutation
+    uint8_t pad[2];
+    uint32_t fmat;   // fused operator in the matrix pool
+    uint32_t fend;   // op index after the absorbed noise ops
+    uint32_t fsite1; // one past the last absorbed site
 };
 
 struct DevMicro {
@@ -78,6 +88,7 @@ struct DevChannel {
 // (outer_q) enumerate the 2^(n-tb) tiles of a state.
 struct DevStage {
     uint32_t op_begin, op_end;
+    uint32_t group_begin, group_end; // register groups of this stage
     uint32_t hi_off;                 // offset of this stage's hi table (2^(tb-lb) uint32)
     uint32_t flags;                  // bit 0: ends right before a general noise site (Algorithm 1 mode)
     uint32_t probe_op;               // Algorithm 1 mode: the general noise op whose probabilities
@@ -86,9 +97,22 @@ struct DevStage {
     uint8_t outer_q[kMaxQubits];     // outer bit b -> global qubit
 };
 
+// Register group: consecutive ops of a stage that only touch kRegBits tile positions. Each thread
+// of the CTA holds the 2^kRegBits amplitudes whose tile index has its thread id spread over
+// lane_pos and runs over every combination of reg_pos, so the ops apply without shared memory.
+constexpr int kRegBits = 4;
+struct DevGroup {
+    uint32_t op_begin, op_end;
+    uint8_t reg_pos[kRegBits];       // register bit b <- tile position reg_pos[b]
+    uint8_t rbit[kTileMax];          // tile position -> register bit (0xFF when it is a lane bit)
+    uint8_t lane_pos[kTileMax];      // thread-id bit i -> tile position lane_pos[i] (ascending)
+    uint8_t pad[3];
+};
+
 struct Plan {
     int tb = 0, lb = 0;              // tile bits, contiguous low bits
     std::vector<DevStage> stages;
+    std::vector<DevGroup> groups;
     std::vector<uint32_t> hi;        // concatenated hi tables: global offset of tile bits [lb, tb)
     std::vector<int32_t> op_stage;   // op index -> stage
 };
@@ -114,6 +138,7 @@ struct DeviceCircuit {
     DevChannel* chans = nullptr;
     uint32_t* site_op = nullptr;
     DevStage* stages = nullptr;
+    DevGroup* groups = nullptr;
     uint32_t* hi = nullptr;
     size_t bytes = 0;
 };
@@ -175,6 +200,7 @@ struct EvolveArgs {
     const DevChannel* chans;
     const uint32_t* site_op;
     const DevStage* stages;
+    const DevGroup* groups;
     const uint32_t* hi;
     int n, tb, lb;
     // Kraus-set entries (whole set, on device)
@@ -198,8 +224,9 @@ struct EvolveArgs {
     uint8_t* status;
 };
 
+// kernel: 0 auto, 1 shared-memory sweeps, 2 register-blocked
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
-                         cudaStream_t s);
+                         cudaStream_t s, int kernel = 0);
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 
 struct SampleItem {                  // one cluster's share of one state's shots

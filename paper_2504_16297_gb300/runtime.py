@@ -100,6 +100,10 @@ class Ptsbe:
     def release_circuit(self, cid):
         capi.ptsbe_release_circuit(self.ctx, cid)
 
+    def set_evolve_kernel(self, kernel: str):
+        """'auto', 'sweep' (one shared-memory pass per operator) or 'registers'."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL, {"auto": 0, "sweep": 1, "registers": 2}[kernel])
+
     def set_timing(self, enable: bool):
         capi.ptsbe_set_timing(self.ctx, enable)
 

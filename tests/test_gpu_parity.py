@@ -16,9 +16,11 @@ from workloads import CircuitBuilder, brickwork, config
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def P():
-    return gpu_ctx()
+@pytest.fixture(scope="module", params=["sweep", "registers"])
+def P(request):
+    ctx = gpu_ctx()
+    ctx.set_evolve_kernel(request.param)
+    return ctx
 
 
 def _evolve_and_compare(P, oracle_mod, circ, info, idxs, prefix_reuse, first=0, count=None):
