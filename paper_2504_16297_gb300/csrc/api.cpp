@@ -55,6 +55,7 @@ struct ptsbe_ctx {
     std::vector<unsigned char> host_blob;
     bool timing = false;
     int evolve_kernel = 0;
+    int n_sm = 0;                      // streaming multiprocessors of the device
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
     cudaEvent_t take_event(ClassTimer& t) {
@@ -218,6 +219,10 @@ int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
             return PTSBE_ERR_NO_DEVICE;
         }
         if (cudaSetDevice(device) != cudaSuccess) { (void)cudaGetLastError(); return PTSBE_ERR_CUDA; }
+        if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PTSBE_ERR_CUDA;
+        }
     }
     *out = ctx.release();
     return PTSBE_OK;
@@ -513,8 +518,12 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         A.seed = seed;
         A.bits = d_bits;
         if ((int)c.n <= sample_cluster_max_qubits()) {
-            // split heavy states so the clusters stay busy; every item rebuilds its state's CDF
-            const uint64_t chunk = std::max<uint64_t>(1u << 14, (total + 1023) / 1024);
+            // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
+            // state's CDF. About four items per resident cluster over the whole shot budget.
+            const int n = (int)c.n;
+            const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
+            const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
+            const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
             std::vector<SampleItem> items;
             for (uint32_t a = 0; a < count; ++a) {
                 const uint32_t alpha = first + a;

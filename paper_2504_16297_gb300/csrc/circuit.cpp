@@ -509,8 +509,17 @@ void emit_group(Plan& P, uint32_t b, uint32_t e, const std::vector<int>& used) {
     // fill with the highest free positions so the lanes keep the low (contiguous) ones
     for (int p = P.tb - 1; p >= 0 && nb < kRegBits; --p)
         if (!(taken & (1u << p))) { g.reg_pos[nb] = (uint8_t)p; g.rbit[p] = (uint8_t)nb; taken |= 1u << p; ++nb; }
+    // Lane positions: the first five (the lane id bits of a warp) get distinct residues mod 5, so
+    // the kernel's XOR swizzle of shared memory (bits 5..9 and 10..14 folded onto bits 0..4) puts a
+    // warp's 32 slots on 32 distinct banks; the rest follow in ascending order.
     int nl = 0;
-    for (int p = 0; p < P.tb; ++p) if (!(taken & (1u << p))) g.lane_pos[nl++] = (uint8_t)p;
+    uint32_t lanes = 0, residues = 0;
+    for (int p = 0; p < P.tb && nl < 5; ++p)
+        if (!(taken & (1u << p)) && !(residues & (1u << (p % 5)))) {
+            g.lane_pos[nl++] = (uint8_t)p; lanes |= 1u << p; residues |= 1u << (p % 5);
+        }
+    for (int p = 0; p < P.tb; ++p)
+        if (!(taken & (1u << p)) && !(lanes & (1u << p))) g.lane_pos[nl++] = (uint8_t)p;
     P.groups.push_back(g);
 }
 

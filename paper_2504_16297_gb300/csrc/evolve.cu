@@ -510,58 +510,148 @@ __device__ __forceinline__ void apply_reg(RegArr& v, uint8_t kind, int b0, int b
     }
 }
 
-// Tile index of register slot j for a thread with lane base `base`.
-__device__ __forceinline__ uint32_t slot_index(uint32_t base, const uint32_t (&bitv)[kRegBits], int j) {
-    uint32_t o = base;
+// Shared-memory layout of the register-blocked kernel: tile index l lives at sw(l), an XOR swizzle
+// that folds bits 5..9 and 10..14 into the bank bits 0..4. It is linear over GF(2), so the slot
+// address of a thread is sw(lane base) ^ sw(register offset). The planner orders each group's
+// lane positions so that the 32 lanes of a warp land on 32 distinct banks (distinct residues of
+// their positions mod 5).
+__device__ __forceinline__ uint32_t sw(uint32_t l) { return l ^ (((l >> 5) ^ (l >> 10)) & 31u); }
+
+__device__ __forceinline__ uint32_t slot_addr(uint32_t sbase, const uint32_t (&sbit)[kRegBits], int j) {
+    uint32_t o = sbase;
 #pragma unroll
     for (int b = 0; b < kRegBits; ++b)
-        if (j & (1 << b)) o |= bitv[b];
+        if (j & (1 << b)) o ^= sbit[b];
     return o;
 }
 
-// General 4x4 operator on register bits (ba, bb), local index 2*bit(ba) + bit(bb). Every quad
-// lies in one thread's own slots, so the caller parks its registers in its shared-memory slots,
-// this function updates the quads there and the caller reloads -- no barrier, and the rare
-// general case stays out of the unrolled register code (the register array never has its
-// address taken, so it stays in registers).
-__device__ __noinline__ void own_slots_g2(float2* tile, uint32_t base, const uint32_t* bits, int ba, int bb,
+// Per-CTA instruction stream of one stage (built by thread 0 while the other threads load the
+// tile): x = opcode | rb0 << 8 | rb1 << 12 | perm << 16, y = matrix offset / group / child.
+enum : uint32_t { OPC_GROUP = 16, OPC_CKPT = 17, OPC_END = 18 };
+constexpr int kMaxStream = 1024;
+
+__device__ __forceinline__ uint2 instr(uint32_t opc, uint32_t rb0, uint32_t rb1, uint32_t perm, uint32_t y) {
+    return make_uint2(opc | (rb0 << 8) | (rb1 << 12) | (perm << 16), y);
+}
+
+// General 4x4 on register bits (ba, bb): every quad lies in one thread's own slots, so the caller
+// parks its registers in those slots, this updates the quads there, and the caller reloads.
+__device__ __noinline__ void own_slots_g2(float2* tile, uint32_t sbase, const uint32_t* sbits, int ba, int bb,
                                           const float2* __restrict__ m) {
-    uint32_t bitv[kRegBits];
-    for (int b = 0; b < kRegBits; ++b) bitv[b] = bits[b];
+    uint32_t sb[kRegBits];
+    for (int b = 0; b < kRegBits; ++b) sb[b] = sbits[b];
     for (int j = 0; j < NR; ++j) {
         if ((j >> ba) & 1 || (j >> bb) & 1) continue;
         const int idx[4] = {j, j | (1 << bb), j | (1 << ba), j | (1 << ba) | (1 << bb)};
         float2 x[4];
-        for (int l = 0; l < 4; ++l) x[l] = tile[slot_index(base, bitv, idx[l])];
+        uint32_t ad[4];
+        for (int l = 0; l < 4; ++l) {
+            uint32_t o = sbase;
+            for (int b = 0; b < kRegBits; ++b) if (idx[l] & (1 << b)) o ^= sb[b];
+            ad[l] = o;
+            x[l] = tile[o];
+        }
         for (int r = 0; r < 4; ++r) {
             float2 acc = cmul(m[4 * r], x[0]);
             for (int l = 1; l < 4; ++l) {
                 const float2 t = cmul(m[4 * r + l], x[l]);
                 acc.x += t.x; acc.y += t.y;
             }
-            tile[slot_index(base, bitv, idx[r])] = acc;
+            tile[ad[r]] = acc;
         }
     }
 }
 
-#define PTSBE_G2_VIA_SLOTS(BA, BB, M)                                                                   \
-    do {                                                                                              \
-        _Pragma("unroll") for (int j = 0; j < NR; ++j) tile[slot_index(base, bitv, j)] = v[j];        \
-        own_slots_g2(tile, base, G_bits, (BA), (BB), (M));                                            \
-        _Pragma("unroll") for (int j = 0; j < NR; ++j) v[j] = tile[slot_index(base, bitv, j)];        \
-    } while (0)
+__device__ void tile_load_sw(float2* tile, const float2* __restrict__ g, int tb, int lb, const uint32_t* hi, uint64_t outer) {
+    const uint32_t nv = 1u << (tb - 1);
+    for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+        const uint32_t l = 2 * v;
+        const float4 x = __ldg(reinterpret_cast<const float4*>(g + gidx(l, lb, hi, outer)));
+        tile[sw(l)] = make_float2(x.x, x.y);
+        tile[sw(l + 1)] = make_float2(x.z, x.w);
+    }
+}
+
+__device__ void tile_store_sw(const float2* tile, float2* g, int tb, int lb, const uint32_t* hi, uint64_t outer, float scale) {
+    const uint32_t nv = 1u << (tb - 1);
+    for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
+        const uint32_t l = 2 * v;
+        const float2 p = tile[sw(l)], q = tile[sw(l + 1)];
+        float4 x = make_float4(p.x, p.y, q.x, q.y);
+        if (scale != 1.0f) { x.x *= scale; x.y *= scale; x.z *= scale; x.w *= scale; }
+        *reinterpret_cast<float4*>(g + gidx(l, lb, hi, outer)) = x;
+    }
+}
+
+// Resumable builder of the stage's instruction stream for one state (thread 0 only). Emits at most
+// kMaxStream - 1 instructions, then OPC_MORE when ops remain.
+enum : uint32_t { OPC_MORE = 19 };
+struct StreamState {
+    uint32_t op, e, ee, c, ce, g;
+    int started;
+};
+
+__device__ __noinline__ void build_stream(const EvolveArgs& a, const DevStage& st, const DevGroup* sg, StreamState& S, uint2* out) {
+    int ip = 0;
+    const uint32_t ng = st.group_end - st.group_begin;
+    if (!S.started) {
+        S.started = 1;
+        while (S.g < ng && sg[S.g].op_end <= S.op) ++S.g;
+        if (S.g >= ng || S.op >= st.op_end) { out[ip++] = instr(OPC_END, 0, 0, 0, 0); return; }
+        out[ip++] = instr(OPC_GROUP, 0, 0, 0, S.g);
+    }
+    for (; S.op < st.op_end; ++S.op) {
+        if (ip > kMaxStream - 24) { out[ip++] = instr(OPC_MORE, 0, 0, 0, 0); return; }
+        const uint32_t op = S.op;
+        if (op >= sg[S.g].op_end) {
+            while (op >= sg[S.g].op_end) ++S.g;
+            out[ip++] = instr(OPC_GROUP, 0, 0, 0, S.g);
+        }
+        const DevOp o = a.ops[op];
+        const uint8_t* rbit = sg[S.g].rbit;
+        if (o.kind == DOP_NOISE) {
+            // checkpoints of children branching at this site (one per stream slot, resumable)
+            while (S.c < S.ce && a.child_op[S.c] == op) {
+                if (ip > kMaxStream - 24) { out[ip++] = instr(OPC_MORE, 0, 0, 0, 0); return; }
+                out[ip++] = instr(OPC_CKPT, 0, 0, 0, a.child_node[S.c]);
+                ++S.c;
+            }
+            uint32_t k = 0;
+            if (S.e < S.ee && a.ent_site[S.e] == o.site) { k = a.ent_k[S.e]; ++S.e; }
+            const uint32_t u0 = a.chans[o.ch].micro_off[k], u1 = a.chans[o.ch].micro_off[k + 1];
+            for (uint32_t u = u0; u < u1; ++u) {
+                const DevMicro mi = a.micro[u];
+                if (mi.kind == DOP_NOP) continue;
+                const uint32_t r0 = rbit[st.pos[mi.operand == 1 ? o.q1 : o.q0]], r1 = rbit[st.pos[o.q1]];
+                out[ip++] = instr(mi.kind, r0, r1, 0, mi.mat);
+            }
+        } else {
+            const uint32_t r0 = rbit[st.pos[o.q0]], r1 = rbit[st.pos[o.q1]];
+            if (o.fend != 0 && (S.e >= S.ee || a.ent_site[S.e] >= o.fsite1) && (S.c >= S.ce || a.child_op[S.c] >= o.fend)) {
+                if (o.fkind != DOP_NOP) out[ip++] = instr(o.fkind, r0, r1, o.fperm, o.fmat);
+                S.op = o.fend - 1;
+            } else if (o.kind != DOP_NOP) {
+                out[ip++] = instr(o.kind, r0, r1, 0, o.mat);
+            }
+        }
+    }
+    out[ip++] = instr(OPC_END, 0, 0, 0, 0);
+}
 
 __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevStage st;
-    __shared__ DevGroup G;
-    __shared__ uint32_t G_bits[kRegBits];
+    __shared__ uint32_t sbits_sh[kRegBits];
+    __shared__ StreamState S;
     __shared__ double red[33];
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     float2* tile = reinterpret_cast<float2*>(smem);
     uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
+    // instruction stream after the hi table, 16-byte aligned (the hi table is 4 bytes when tb == lb)
+    uint2* stream = reinterpret_cast<uint2*>(smem + ((((size_t)8 << tb) + ((size_t)4 << (tb - lb)) + 15) & ~(size_t)15));
     if (threadIdx.x == 0) st = a.stages[stage_idx];
     __syncthreads();
+    const DevGroup* sg = a.groups + st.group_begin;   // this stage's register groups (global, broadcast reads)
     for (uint32_t i = threadIdx.x; i < (1u << (tb - lb)); i += blockDim.x) hi[i] = a.hi[st.hi_off + i];
     const uint32_t node = nodes[blockIdx.y];
     const uint32_t tau = blockIdx.x;
@@ -572,81 +662,83 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
     const uint32_t nstart = a.node_start[node];
     const uint32_t start = nstart > st.op_begin ? nstart : st.op_begin;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        S.op = start; S.g = 0; S.started = 0;
+        S.e = a.node_ebeg[node]; S.ee = a.node_eend[node];
+        while (S.e < S.ee && a.site_op[a.ent_site[S.e]] < start) ++S.e;
+        S.c = a.node_cbeg[node]; S.ce = a.node_cend[node];
+        while (S.c < S.ce && a.child_op[S.c] < start) ++S.c;
+        build_stream(a, st, sg, S, stream);
+    }
     if (a.node_fresh[node] && stage_idx == 0) {
         for (uint32_t l = threadIdx.x; l < (1u << tb); l += blockDim.x)
-            tile[l] = make_float2((l == 0 && tau == 0) ? 1.0f : 0.0f, 0.0f);
+            tile[l] = make_float2((l == 0 && tau == 0) ? 1.0f : 0.0f, 0.0f);   // sw(0) == 0
     } else {
-        tile_load(tile, g, tb, lb, hi, outer);
-    }
-    uint32_t e = a.node_ebeg[node];
-    const uint32_t ee = a.node_eend[node];
-    while (e < ee && a.site_op[a.ent_site[e]] < start) ++e;
-    uint32_t c = a.node_cbeg[node];
-    const uint32_t ce = a.node_cend[node];
-    while (c < ce && a.child_op[c] < start) ++c;
-
-    for (uint32_t gi = st.group_begin; gi < st.group_end; ++gi) {
-        __syncthreads();                     // tile writes of the previous group, G reuse
-        if (threadIdx.x == 0) {
-            G = a.groups[gi];
-            for (int b = 0; b < kRegBits; ++b) G_bits[b] = 1u << G.reg_pos[b];
-        }
-        __syncthreads();
-        if (G.op_end <= start) continue;
-        uint32_t base = 0;
-        for (int i = 0; i < tb - kRegBits; ++i) base |= ((threadIdx.x >> i) & 1u) << G.lane_pos[i];
-        uint32_t bitv[kRegBits];
-#pragma unroll
-        for (int b = 0; b < kRegBits; ++b) bitv[b] = 1u << G.reg_pos[b];
-        RegArr v;
-#pragma unroll
-        for (int j = 0; j < NR; ++j) v[j] = tile[slot_index(base, bitv, j)];
-        const uint32_t op0 = G.op_begin > start ? G.op_begin : start;
-        for (uint32_t op = op0; op < G.op_end; ++op) {
-            const DevOp o = a.ops[op];
-            if (o.kind == DOP_NOISE) {
-                while (c < ce && a.child_op[c] == op) {
-                    // checkpoint for a prefix-reuse child: every thread writes its slots
-                    float2* gc = a.states + ((size_t)a.child_node[c] << n);
-                    uint32_t bb = base;
-                    asm volatile("" : "+r"(bb));   // recompute slot indices here, do not keep 32 live
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) gc[gidx(slot_index(bb, bitv, j), lb, hi, outer)] = v[j];
-                    ++c;
-                }
-                uint32_t k = 0;
-                if (e < ee && a.ent_site[e] == o.site) { k = a.ent_k[e]; ++e; }
-                const uint32_t u0 = a.chans[o.ch].micro_off[k], u1 = a.chans[o.ch].micro_off[k + 1];
-                for (uint32_t u = u0; u < u1; ++u) {
-                    const DevMicro mi = a.micro[u];
-                    if (mi.kind == DOP_G2) {
-                        PTSBE_G2_VIA_SLOTS(G.rbit[st.pos[o.q0]], G.rbit[st.pos[o.q1]], a.mats + mi.mat);
-                        continue;
-                    }
-                    const int p0 = G.rbit[st.pos[mi.operand == 1 ? o.q1 : o.q0]];
-                    const int p1 = G.rbit[st.pos[o.q1]];
-                    apply_reg(v, mi.kind, p0, p1, a.mats + mi.mat);
-                }
-            } else {
-                const int r0 = G.rbit[st.pos[o.q0]], r1 = G.rbit[st.pos[o.q1]];
-                uint8_t kind = o.kind;
-                uint32_t mat = o.mat, perm = 0;
-                if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1) && (c >= ce || a.child_op[c] >= o.fend)) {
-                    kind = o.fkind; mat = o.fmat; perm = o.fperm;
-                    op = o.fend - 1;         // the absorbed noise ops are done
-                }
-                if (kind == DOP_G2) PTSBE_G2_VIA_SLOTS(r0, r1, a.mats + mat);
-                else if (kind != DOP_NOP) apply_reg(v, kind, r0, r1, a.mats + mat, perm);
-            }
-        }
-        asm volatile("" : "+r"(base));         // slot indices are recomputed, not held across the ops
-#pragma unroll
-        for (int j = 0; j < NR; ++j) tile[slot_index(base, bitv, j)] = v[j];
+        tile_load_sw(tile, g, tb, lb, hi, outer);
     }
     __syncthreads();
 
+    RegArr v;
+    uint32_t sbase = 0;
+    uint32_t sbit[kRegBits];
+#pragma unroll
+    for (int b = 0; b < kRegBits; ++b) sbit[b] = 0;
+    bool loaded = false;
+    for (int ip = 0;; ++ip) {
+        const uint2 ins = stream[ip];
+        const uint32_t opc = ins.x & 0xFFu;
+        if (opc == OPC_MORE) {                  // refill the stream; registers stay loaded
+            __syncthreads();
+            if (threadIdx.x == 0) build_stream(a, st, sg, S, stream);
+            __syncthreads();
+            ip = -1;
+            continue;
+        }
+        if (opc == OPC_GROUP || opc == OPC_END || opc == OPC_CKPT) {
+            if (loaded) {
+                asm volatile("" : "+r"(sbase));
+#pragma unroll
+                for (int j = 0; j < NR; ++j) tile[slot_addr(sbase, sbit, j)] = v[j];
+                loaded = false;
+            }
+            __syncthreads();
+            if (opc == OPC_END) break;
+            if (opc == OPC_CKPT) {
+                // prefix-reuse checkpoint: the whole tile (in shared memory now) goes to the child
+                tile_store_sw(tile, a.states + ((size_t)ins.y << n), tb, lb, hi, outer, 1.0f);
+                __syncthreads();
+            } else {
+                const DevGroup& G = sg[ins.y];
+                uint32_t base = 0;
+                for (int i = 0; i < tb - kRegBits; ++i) base |= ((threadIdx.x >> i) & 1u) << G.lane_pos[i];
+                sbase = sw(base);
+#pragma unroll
+                for (int b = 0; b < kRegBits; ++b) sbit[b] = sw(1u << G.reg_pos[b]);
+                if (threadIdx.x == 0) {
+#pragma unroll
+                    for (int b = 0; b < kRegBits; ++b) sbits_sh[b] = sbit[b];
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) v[j] = tile[slot_addr(sbase, sbit, j)];
+            loaded = true;
+            continue;
+        }
+        const int rb0 = (ins.x >> 8) & 0xF, rb1 = (ins.x >> 12) & 0xF;
+        if (opc == DOP_G2) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) tile[slot_addr(sbase, sbit, j)] = v[j];
+            own_slots_g2(tile, sbase, sbits_sh, rb0, rb1, a.mats + ins.y);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) v[j] = tile[slot_addr(sbase, sbit, j)];
+        } else {
+            apply_reg(v, (uint8_t)opc, rb0, rb1, a.mats + ins.y, (ins.x >> 16) & 0xFF);
+        }
+    }
+
     if (!last) {
-        tile_store(tile, g, tb, lb, hi, outer, 1.0f);
+        tile_store_sw(tile, g, tb, lb, hi, outer, 1.0f);
         return;
     }
     const double part = cta_sum(tile_norm_partial(tile, tb), red);
@@ -654,13 +746,13 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
         const double w = a.wmix[node] * part;
         const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
         const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
-        tile_store(tile, g, tb, lb, hi, outer, scale);
+        tile_store_sw(tile, g, tb, lb, hi, outer, scale);
         if (threadIdx.x == 0) {
             if (a.weights) a.weights[node] = w;
             if (a.status) a.status[node] = null ? 1 : 0;
         }
     } else {
-        tile_store(tile, g, tb, lb, hi, outer, 1.0f);
+        tile_store_sw(tile, g, tb, lb, hi, outer, 1.0f);
         if (threadIdx.x == 0) a.part[((size_t)node << ob) + tau] = part;
     }
 }
@@ -679,6 +771,7 @@ int evolve_threads(int tb) {
 }  // namespace
 
 size_t evolve_smem_bytes(int tb, int lb) { return ((size_t)8 << tb) + ((size_t)4 << (tb - lb)); }
+size_t evolve_rb_smem_bytes(int tb, int lb) { return ((evolve_smem_bytes(tb, lb) + 15) & ~(size_t)15) + 8 * (size_t)kMaxStream; }
 
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
                          cudaStream_t s, int kernel) {
@@ -688,12 +781,12 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_smem_bytes(kTileMax, 1)));
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)evolve_smem_bytes(kTileMax, 1)));
+                                        (int)evolve_rb_smem_bytes(kTileMax, 1)));
         configured = true;
     }
-    const size_t smem = evolve_smem_bytes(a.tb, a.lb);
     const bool regs = a.tb >= kRegBits && kernel != 1 && (kernel == 2 || kEvolveAutoRegisters);
     const int threads = regs ? (1 << (a.tb - kRegBits)) : evolve_threads(a.tb);
+    const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = 1u << (a.n - a.tb);
     for (uint32_t b = 0; b < n_nodes; b += 65535) {
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
