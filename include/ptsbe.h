@@ -256,6 +256,24 @@ PTSBE_API int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
 PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                        const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity);
 
+/* Same shots as ptsbe_sample_shots, bit for bit, for callers that cannot allocate device memory:
+ * a program whose memory pool has already reserved the GPU, a fixed-footprint deployment that
+ * plans every byte up front, or a latency-critical loop that must not hit the device-wide
+ * synchronisation a cudaFree implies. (The paper has no counterpart; this is an interface choice
+ * of the library.) The call's scratch -- the work-item list for n <= 17, the CDF workspace for
+ * 18 <= n <= 21 -- lives in a fixed 32 MiB device array compiled into the library, which every
+ * GPU that loads the library holds until the process exits; no cudaMalloc, cudaFree or other
+ * allocating routine is called. Requests that need more (more than 2^20 work items, or n > 21)
+ * return PTSBE_ERR_UNSUPPORTED with the sizes in the message. The first call on a device looks up
+ * the array's device address (a one-time driver query): make that first call before any stream
+ * capture. Every call shares the one array and overwrites what the previous call left there
+ * (nothing is read before this call writes it); calls whose work can overlap on the GPU -- on
+ * different streams or contexts of the same device -- race on it and must be serialised by the
+ * caller. Arguments, layout and other errors as for ptsbe_sample_shots. */
+PTSBE_API int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count,
+                                         const void* d_states, const uint8_t* d_status, uint64_t seed,
+                                         uint32_t* d_bits, uint64_t d_bits_capacity);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Traditional trajectories (Algorithm 1), one prepared state per shot, for comparison        */
 /* ---------------------------------------------------------------------------------------- */

@@ -74,6 +74,8 @@ _PROTOS = {
                                      C.c_void_p, C.c_uint32]),
     "ptsbe_sample_shots": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
                                      C.c_uint64, C.c_void_p, C.c_uint64]),
+    "ptsbe_sample_shots_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p,
+                                             C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -178,6 +180,10 @@ def ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status,
 
 def ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity):
     check(ctx, load().ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity))
+
+
+def ptsbe_sample_shots_noalloc(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity):
+    check(ctx, load().ptsbe_sample_shots_noalloc(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity))
 
 
 def ptsbe_kernel_launches() -> int:

@@ -18,6 +18,8 @@ void cuda_check(cudaError_t e, const char* what) {
 }
 
 size_t sample_global_scratch_doubles(int n);
+size_t noalloc_scratch_bytes();
+void* noalloc_scratch(int device);
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_h2d{0};
@@ -53,6 +55,7 @@ struct ptsbe_ctx {
     uint32_t next_circuit = 1, next_set = 1;
     DevBuf nodes, part, scale, items, scratch, pershot;
     std::vector<unsigned char> host_blob;
+    std::vector<SampleItem> noalloc_items;
     bool timing = false;
     int evolve_kernel = 0;
     int n_sm = 0;                      // streaming multiprocessors of the device
@@ -590,6 +593,65 @@ int ptsbe_h2d_bytes(uint64_t* bytes) {
     if (!bytes) return PTSBE_ERR_INVALID;
     *bytes = g_h2d.load(std::memory_order_relaxed);
     return PTSBE_OK;
+}
+
+int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
+                               const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        KSet& s = ctx->set(set_id);
+        Circuit& c = ctx->circuit(s.circuit);
+        if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (count == 0) return;
+        const uint64_t base = s.shot_off[first];
+        const uint64_t total = s.shot_off[first + count] - base;
+        if (total == 0) return;
+        if (!d_states || !d_bits) fail(PTSBE_ERR_INVALID, "null device pointer");
+        if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
+        if (d_bits_capacity < total) fail(PTSBE_ERR_BUFFER_TOO_SMALL, "d_bits holds " + std::to_string(d_bits_capacity) +
+                                                                          " shots, the range needs " + std::to_string(total));
+        const int n = (int)c.n;
+        const size_t cap = noalloc_scratch_bytes();
+        SampleArgs A{};
+        A.n = n;
+        A.states = (const float2*)d_states;
+        A.status = d_status;
+        A.seed = seed;
+        A.bits = d_bits;
+        if (n <= sample_cluster_max_qubits()) {
+            const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
+            const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
+            const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+            std::vector<SampleItem>& items = ctx->noalloc_items;
+            items.clear();
+            for (uint32_t a = 0; a < count; ++a) {
+                const uint32_t alpha = first + a;
+                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+                for (uint64_t j0 = 0; j0 < m; j0 += chunk)
+                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0});
+            }
+            if (items.size() * sizeof(SampleItem) > cap)
+                fail(PTSBE_ERR_UNSUPPORTED, "range needs " + std::to_string(items.size()) + " work items; the fixed scratch holds " +
+                                                std::to_string(cap / sizeof(SampleItem)));
+            ctx->use_device();
+            SampleItem* d_items = (SampleItem*)noalloc_scratch(ctx->device);
+            PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
+            launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream);
+        } else {
+            const size_t need = sample_global_scratch_doubles(n) * sizeof(double);
+            if (need > cap)
+                fail(PTSBE_ERR_UNSUPPORTED, std::to_string(n) + "-qubit states need " + std::to_string(need) +
+                                                " bytes of CDF workspace; the fixed scratch holds " + std::to_string(cap) +
+                                                " (at most 21 qubits)");
+            ctx->use_device();
+            A.scratch = (double*)noalloc_scratch(ctx->device);
+            for (uint32_t a = 0; a < count; ++a) {
+                const uint32_t alpha = first + a;
+                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+                if (m) launch_sample_global(A, a, alpha, 0, m, o, ctx->stream);
+            }
+        }
+    });
 }
 
 int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64_t first_shot, uint64_t n_shots,

@@ -14,6 +14,7 @@
 //
 // Comparisons of non-negative doubles are done on their bit patterns (same order, integer ALU).
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "internal.h"
 #include "philox.h"
@@ -293,7 +294,33 @@ void launch_cluster(const SampleArgs& a, const SampleItem* items, uint32_t n_ite
     }
 }
 
+// Fixed scratch for ptsbe_sample_shots_noalloc: every GPU that loads the library holds these
+// bytes until the process exits. In host code the name is only a stand-in for the symbol; the
+// device address comes from cudaGetSymbolAddress, looked up once per device below.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
 }  // namespace
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+// Device address of the fixed scratch on `device`, which must be the current device. The first
+// call on a device resolves the symbol (a driver call that is not a stream operation, so it has to
+// happen before any stream capture that uses the entry point); later calls return the cached value.
+void* noalloc_scratch(int device) {
+    if (device < 0 || device >= kMaxDevices) fail(PTSBE_ERR_UNSUPPORTED, "device index out of range for the fixed scratch");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        PTSBE_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[device] = p;
+    }
+    return g_noalloc_ptr[device];
+}
 
 int sample_cluster_max_qubits() { return kSliceBits + 3; }
 
