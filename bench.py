@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
     ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "sweep", "registers"])
+    ap.add_argument("--pershot-shots", type=int, default=2048,
+                    help="shots of the traditional per-shot path timed for comparison (0 = skip)")
     return ap.parse_args()
 
 
@@ -296,6 +298,25 @@ def main():
     ms_e2e, _, _ = timed(True, steps_e2e, False)
     h2d_bytes[0] = (capi.ptsbe_h2d_bytes() - hb0) // steps_e2e
 
+    # Traditional trajectories (Algorithm 1) on the same GPU and workload: one prepared state per
+    # shot, Kraus operators drawn during the evolution. Timed on a bounded number of shots.
+    pershot = None
+    if args.pershot_shots > 0:
+        cid = P.register(circ)
+        ps_bits = torch.empty(args.pershot_shots, dtype=torch.int32, device=dev)
+        P.pershot(cid, seed, 0, min(64, args.pershot_shots), ps_bits)      # warm-up
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.pershot(cid, seed, 0, args.pershot_shots, ps_bits)
+        e1.record(stream)
+        barrier()
+        ps_ms = e0.elapsed_time(e1)
+        P.release_circuit(cid)
+        del ps_bits
+        pershot = {"value": args.pershot_shots / (ps_ms / 1e3), "unit": "shots/s", "shots": args.pershot_shots,
+                   "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot"}
+
     ms_step = ms / args.steps
     value = world * M / (ms_step / 1e3)
     e2e_value = world * M / (ms_e2e / steps_e2e / 1e3)
@@ -326,6 +347,8 @@ def main():
                        "l2": "inputs larger than L2 (10.5 GB of states per step)",
                        "parallelism": f"{world} independent replicas (weak scaling)"},
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,
+            "pershot": pershot,
+            "speedup_vs_pershot": (value / world / pershot["value"]) if pershot else None,
             "kernels": kern,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -15,8 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libptsbe.so")
 
 CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp"]
-CU_SOURCES = ["evolve.cu", "sample.cu"]
-HEADERS = ["internal.h", "philox.h"]
+CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu"]
+HEADERS = ["internal.h", "philox.h", "tile_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

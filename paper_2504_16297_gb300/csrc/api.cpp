@@ -8,6 +8,7 @@
 #include <unordered_map>
 
 #include "internal.h"
+#include "philox.h"
 
 namespace ptsbe {
 
@@ -532,7 +533,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
                 for (uint64_t j0 = 0; j0 < m; j0 += chunk)
-                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0});
+                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
             }
             SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
             PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
@@ -628,7 +629,7 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
                 for (uint64_t j0 = 0; j0 < m; j0 += chunk)
-                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0});
+                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
             }
             if (items.size() * sizeof(SampleItem) > cap)
                 fail(PTSBE_ERR_UNSUPPORTED, "range needs " + std::to_string(items.size()) + " work items; the fixed scratch holds " +
@@ -658,8 +659,58 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
                       uint32_t* d_bits, uint8_t* d_kraus) {
     return guarded(ctx, [&] {
         ctx->need_device();
-        (void)circuit_id; (void)seed; (void)first_shot; (void)n_shots; (void)d_bits; (void)d_kraus;
-        fail(PTSBE_ERR_UNSUPPORTED, "per-shot trajectories are not built yet");
+        Circuit& c = ctx->circuit(circuit_id);
+        if (n_shots == 0) return;
+        if (!d_bits) fail(PTSBE_ERR_INVALID, "d_bits is NULL");
+        ctx->use_device();
+        if (!c.pershot_planned) {
+            c.plan_pershot = make_plan(c, kTileMax, true);
+            upload_circuit(c, c.plan_pershot, c.dev_pershot);
+            c.pershot_planned = true;
+        }
+        const Plan& P = c.plan_pershot;
+        const int n = (int)c.n, ob = n - P.tb;
+        const size_t sbytes = (size_t)8 << n;
+        // states in flight: up to 2 GiB of workspace, at most 65535 per launch
+        const uint64_t batch = std::min<uint64_t>({n_shots, std::max<uint64_t>(1, ((size_t)2 << 30) / sbytes), 65535});
+        PershotArgs A{};
+        A.ops = c.dev_pershot.ops; A.micro = c.dev_pershot.micro; A.mats = c.dev_pershot.mats;
+        A.chans = c.dev_pershot.chans; A.stages = c.dev_pershot.stages; A.hi = c.dev_pershot.hi;
+        A.n = n; A.tb = P.tb; A.lb = P.lb; A.seed = seed; A.n_sites = c.site_op.size();
+        A.states = (float2*)ctx->ws(ctx->pershot, batch * sbytes);
+        A.part = (double*)ctx->ws(ctx->part, 2 * (batch << ob) * kMaxKraus * sizeof(double));
+        SampleArgs R{};
+        R.n = n; R.states = A.states; R.status = nullptr; R.seed = seed;
+        const bool cluster = n <= sample_cluster_max_qubits();
+        if (!cluster) R.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * sizeof(double));
+        std::vector<SampleItem> items;
+        for (uint64_t b0 = 0; b0 < n_shots; b0 += batch) {
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(batch, n_shots - b0);
+            A.first_shot = first_shot + b0;
+            A.kraus = d_kraus ? d_kraus + b0 * A.n_sites : nullptr;
+            ctx->timed(PTSBE_TIMER_PERSHOT, 2.0 * sbytes * cnt * P.stages.size(), [&] {
+                for (size_t j = 0; j < P.stages.size(); ++j) launch_pershot_stage(A, (int)j, cnt, ctx->stream);
+            });
+            // read every state out once with its own uniform (the sampler with the per-shot domain)
+            R.bits = d_bits + b0;
+            if (cluster) {
+                items.clear();
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    const uint64_t jj = first_shot + b0 + i;
+                    items.push_back({i, 0u, jj, jj + 1, (uint64_t)i, kDomPershotRead, 0});   // bits[b0 + i]
+                }
+                SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
+                PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
+                count_h2d(items.size() * sizeof(SampleItem));
+                ctx->timed(PTSBE_TIMER_PERSHOT, 8.0 * sbytes * cnt, [&] { launch_sample_cluster(R, d_items, cnt, ctx->stream); });
+            } else {
+                for (uint32_t i = 0; i < cnt; ++i) {
+                    const uint64_t jj = first_shot + b0 + i;
+                    ctx->timed(PTSBE_TIMER_PERSHOT, 5.0 * sbytes,
+                               [&] { launch_sample_global(R, i, 0u, jj, jj + 1, (uint64_t)i, ctx->stream, kDomPershotRead); });
+                }
+            }
+        }
     });
 }
 

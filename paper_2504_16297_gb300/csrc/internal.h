@@ -234,6 +234,8 @@ struct SampleItem {                  // one cluster's share of one state's shots
     uint32_t alpha;                  // global set index (Philox counter word 2)
     uint64_t j0, j1;                 // shot interval within the set
     uint64_t out0;                   // output slot of shot j0
+    uint32_t dom;                    // Philox counter word 3 (counter domain)
+    uint32_t pad;
 };
 
 struct SampleArgs {
@@ -248,7 +250,25 @@ struct SampleArgs {
 
 void launch_sample_cluster(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);
 void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1,
-                          uint64_t out0, cudaStream_t s);
+                          uint64_t out0, cudaStream_t s, uint32_t dom = 2);
+
+// Algorithm 1: one trajectory per shot, Kraus operators drawn while the state evolves.
+struct PershotArgs {
+    const DevOp* ops;
+    const DevMicro* micro;
+    const float2* mats;
+    const DevChannel* chans;
+    const DevStage* stages;
+    const uint32_t* hi;
+    int n, tb, lb;
+    uint64_t seed;
+    uint64_t first_shot;             // global index of the batch's first shot
+    float2* states;                  // [batch][2^n]
+    double* part;                    // [2][batch][2^(n-tb)][kMaxKraus] branch-probability partials
+    uint8_t* kraus;                  // optional [batch][n_sites] chosen Kraus index per site
+    uint64_t n_sites;
+};
+void launch_pershot_stage(const PershotArgs& a, int stage, uint32_t batch, cudaStream_t s);
 int sample_cluster_max_qubits();
 
 }  // namespace ptsbe

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
     }
     for (uint64_t k = (uint64_t)rank * nth + threadIdx.x; k < nshots; k += (uint64_t)CL * nth) {
         const uint64_t j = it.j0 + k;
-        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, kDomShot,
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom,
                                         (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
         const double t = u53(x.x[0], x.x[1]) * T;
         const long long tb = dbits(t);
@@ -220,13 +220,14 @@ __global__ void k_block_add(double* cdf, const double* __restrict__ boff) {
 }
 
 __global__ void k_search_global(SampleArgs a, const double* __restrict__ cdf, const double* __restrict__ bend,
-                                uint32_t nb, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1, uint64_t out0) {
+                                uint32_t nb, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1, uint64_t out0,
+                                uint32_t dom) {
     const double T = bend[nb - 1];
     const bool null = a.status && a.status[state];
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < j1 - j0; k += (uint64_t)gridDim.x * blockDim.x) {
         if (null) { a.bits[out0 + k] = 0xFFFFFFFFu; continue; }
         const uint64_t j = j0 + k;
-        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), alpha, kDomShot,
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), alpha, dom,
                                         (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
         const long long tb = dbits(u53(x.x[0], x.x[1]) * T);
         uint32_t lo = 0, hi = nb - 1;
@@ -347,7 +348,7 @@ size_t sample_global_scratch_doubles(int n) {
 }
 
 void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1,
-                          uint64_t out0, cudaStream_t s) {
+                          uint64_t out0, cudaStream_t s, uint32_t dom) {
     const int n = a.n;
     if (j1 <= j0) return;
     const uint32_t nb = 1u << (n - kSliceBits);
@@ -374,7 +375,7 @@ void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, u
     const uint64_t m = j1 - j0;
     uint32_t blocks = (uint32_t)((m + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_search_global<<<blocks, 256, 0, s>>>(a, cdf, bend, nb, state, alpha, j0, j1, out0);
+    k_search_global<<<blocks, 256, 0, s>>>(a, cdf, bend, nb, state, alpha, j0, j1, out0, dom);
     PTSBE_CUDA(cudaGetLastError());
         count_launch();
 }
