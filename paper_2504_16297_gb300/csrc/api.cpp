@@ -521,32 +521,48 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         A.status = d_status;
         A.seed = seed;
         A.bits = d_bits;
-        if ((int)c.n <= sample_cluster_max_qubits()) {
-            // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
-            // state's CDF. About four items per resident cluster over the whole shot budget.
-            const int n = (int)c.n;
-            const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
-            const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
-            const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
-            std::vector<SampleItem> items;
-            for (uint32_t a = 0; a < count; ++a) {
-                const uint32_t alpha = first + a;
-                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+        const int n = (int)c.n;
+        const bool light_ok = n > 14 && n <= sample_light_max_qubits();
+        std::vector<SampleItem> light, items;
+        // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
+        // state's CDF. About four items per resident cluster over the whole shot budget.
+        const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
+        const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
+        const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+        for (uint32_t a = 0; a < count; ++a) {
+            const uint32_t alpha = first + a;
+            const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+            if (m == 0) continue;
+            if (light_ok && m <= kLightShotLimit) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
+            if (n <= sample_cluster_max_qubits())
                 for (uint64_t j0 = 0; j0 < m; j0 += chunk)
                     items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
+        }
+        const size_t nl = light.size(), nh = items.size();
+        if (nl + nh) {
+            light.insert(light.end(), items.begin(), items.end());
+            SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
+            PTSBE_CUDA(cudaMemcpyAsync(d_items, light.data(), light.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
+            count_h2d(light.size() * sizeof(SampleItem));
+            if (nl) {
+                const double bytes = 8.0 * (double)(1ull << n) * (double)nl * 1.1;
+                ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
             }
-            SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
-            PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
-            count_h2d(items.size() * sizeof(SampleItem));
-            const double bytes = 8.0 * (double)(1ull << c.n) * (double)items.size() + 4.0 * (double)total;
-            ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream); });
-        } else {
-            A.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles((int)c.n) * sizeof(double));
+            if (nh) {
+                uint64_t heavy_shots = 0;
+                for (size_t i = nl; i < light.size(); ++i) heavy_shots += light[i].j1 - light[i].j0;
+                const double bytes = 8.0 * (double)(1ull << n) * (double)nh + 4.0 * (double)heavy_shots;
+                ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items + nl, (uint32_t)nh, ctx->stream); });
+            }
+        }
+        if (n > sample_cluster_max_qubits()) {
+            A.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * sizeof(double));
             for (uint32_t a = 0; a < count; ++a) {
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
-                const double sb = 8.0 * (double)(1ull << c.n);
-                if (m) ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
+                if (m == 0 || (light_ok && m <= kLightShotLimit)) continue;
+                const double sb = 8.0 * (double)(1ull << n);
+                ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
             }
         }
     });

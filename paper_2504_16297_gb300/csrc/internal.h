@@ -270,5 +270,9 @@ struct PershotArgs {
 };
 void launch_pershot_stage(const PershotArgs& a, int stage, uint32_t batch, cudaStream_t s);
 int sample_cluster_max_qubits();
+int sample_light_max_qubits();
+// States with at most this many shots go to the one-CTA-per-state light sampler (15 <= n <= 20).
+constexpr uint64_t kLightShotLimit = 512;
+void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);
 
 }  // namespace ptsbe

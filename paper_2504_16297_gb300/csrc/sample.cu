@@ -41,11 +41,27 @@ __device__ __forceinline__ int entries_log2(int cb) {
     return cb > tl ? cb - tl : 0;
 }
 
-// Builds the inclusive FP64 prefix of |psi|^2 over 2^cb amplitudes into cdf (padded layout).
-// Thread t owns entries [t*K, (t+1)*K): pass 1 stores the probabilities and the thread total,
-// the thread totals are scanned across the CTA, pass 2 runs the sequential prefix of each
-// thread's entries from its offset. Returns the last entry (the slice total).
-__device__ double build_prefix(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
+// Exact FP32 -> FP64 of a non-negative finite float by integer operations, keeping the
+// conversion off the FP64 pipe (1/64 of the FP32 rate on GB300).
+__device__ __forceinline__ double f2d_exact(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = u >> 23;
+    unsigned long long bits;
+    if (e != 0) {
+        bits = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    } else if (u == 0) {
+        bits = 0ull;
+    } else {                                        // subnormal: value = u * 2^-149
+        const int k = 31 - __clz(u);
+        bits = ((unsigned long long)(k + 874) << 52) | ((unsigned long long)(u ^ (1u << k)) << (52 - k));
+    }
+    return __longlong_as_double((long long)bits);
+}
+
+// Stage 1 of a slice prefix: P_i = |psi_i|^2 (FP32 product, exact FP64 value) into cdf (padded
+// layout); thread t owns entries [t*K, (t+1)*K) and sums them sequentially in FP64; the thread sums
+// are scanned across the CTA in a fixed order. Returns the thread's exclusive offset.
+__device__ double slice_stage1(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
     const uint32_t count = 1u << cb;
     const int kb = entries_log2(cb);
     const uint32_t K = 1u << kb;
@@ -55,14 +71,14 @@ __device__ double build_prefix(const float2* __restrict__ amps, int cb, double* 
     if (mine) {
         if (K == 1) {
             const float2 v = amps[l0];
-            const double p = (double)fmaf(v.x, v.x, v.y * v.y);
+            const double p = f2d_exact(fmaf(v.x, v.x, v.y * v.y));
             cdf[paddr(l0, kb)] = p;
             tot = p;
         } else {
             for (uint32_t i = 0; i < K; i += 2) {
                 const float4 v = __ldg(reinterpret_cast<const float4*>(amps + l0 + i));
-                const double p0 = (double)fmaf(v.x, v.x, v.y * v.y);
-                const double p1 = (double)fmaf(v.z, v.z, v.w * v.w);
+                const double p0 = f2d_exact(fmaf(v.x, v.x, v.y * v.y));
+                const double p1 = f2d_exact(fmaf(v.z, v.z, v.w * v.w));
                 cdf[paddr(l0 + i, kb)] = p0;
                 cdf[paddr(l0 + i + 1, kb)] = p1;
                 tot += p0;
@@ -85,15 +101,39 @@ __device__ double build_prefix(const float2* __restrict__ amps, int cb, double* 
         for (int i = 0; i < nw; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
     }
     __syncthreads();
-    if (mine) {
-        double run = red[w] + (lane == 0 ? 0.0 : prev);   // exclusive offset of this thread
+    return red[w] + (lane == 0 ? 0.0 : prev);
+}
+
+// Inclusive FP64 prefix of |psi|^2 over 2^cb amplitudes into cdf: stage 1, then every thread runs
+// the sequential prefix of its own entries from its offset. Returns the last entry.
+__device__ double build_prefix(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
+    const int kb = entries_log2(cb);
+    const uint32_t K = 1u << kb, l0 = threadIdx.x * K;
+    double run = slice_stage1(amps, cb, cdf, red);
+    if (l0 < (1u << cb))
         for (uint32_t i = 0; i < K; ++i) {
             run += cdf[paddr(l0 + i, kb)];
             cdf[paddr(l0 + i, kb)] = run;
         }
+    __syncthreads();
+    return cdf[paddr((1u << cb) - 1, kb)];
+}
+
+// The last entry build_prefix would produce, computed with the same operations: stage 1, then only
+// the thread owning the last entries runs its prefix. `excl` receives this thread's offset.
+__device__ double slice_total(const float2* __restrict__ amps, int cb, double* cdf, double* red, double& excl,
+                              double* total_slot) {
+    const int kb = entries_log2(cb);
+    const uint32_t K = 1u << kb, count = 1u << cb;
+    excl = slice_stage1(amps, cb, cdf, red);
+    const uint32_t l0 = threadIdx.x * K;
+    if (l0 < count && l0 + K >= count) {
+        double run = excl;
+        for (uint32_t i = 0; i < K; ++i) run += cdf[paddr(l0 + i, kb)];
+        *total_slot = run;
     }
     __syncthreads();
-    return cdf[paddr(count - 1, kb)];
+    return *total_slot;
 }
 
 // smallest l in [0, 2^cb) with t < cdf[l] (the last index if none)
@@ -170,6 +210,99 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
         a.bits[it.out0 + k] = idx;
     }
     if constexpr (CL > 1) cg::this_cluster().sync();  // keep this CTA's slice alive for remote readers
+}
+
+// ---- light states: one CTA per state, slice by slice --------------------------------------------------
+// For a state with few shots the CDF is never stored: pass 1 runs the slice prefix (the same routine
+// as above, so a slice's last entry is bit-identical whenever it is recomputed) over 2^kLightBits-
+// amplitude slices and keeps only the slice totals; thread 0 turns them into slice offsets by a
+// sequential FP64 scan, so C at a slice end is off[s+1] = off[s] + total[s] exactly. Pass 2 rebuilds
+// only the slices that hold a shot and resolves those shots against off[s] + local prefix.
+constexpr int kLightBits = 12;
+constexpr int kLightMaxSlices = 256;         // n <= 20
+
+constexpr int kLightThreads = 512;          // one shot per thread at most
+
+__global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a, const SampleItem* __restrict__ items) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[33];
+    __shared__ double off[kLightMaxSlices + 1];
+    __shared__ double texcl[kLightThreads + 1];
+    __shared__ double total_slot;
+    __shared__ uint8_t used[kLightMaxSlices];
+    double* cdf = reinterpret_cast<double*>(smem);
+    const SampleItem it = items[blockIdx.x];
+    const uint64_t nshots = it.j1 - it.j0;          // <= blockDim.x
+    if (a.status && a.status[it.state]) {
+        if (threadIdx.x < nshots) a.bits[it.out0 + threadIdx.x] = 0xFFFFFFFFu;
+        return;
+    }
+    const int n = a.n, cb = kLightBits;
+    const uint32_t nsl = 1u << (n - cb);
+    const int kb = entries_log2(cb);
+    const uint32_t K = 1u << kb;
+    const float2* amps = a.states + ((size_t)it.state << n);
+    // pass 1: slice totals (each equal to the slice's last prefix entry), then offsets by a
+    // sequential FP64 scan
+    for (uint32_t sl = 0; sl < nsl; ++sl) {
+        double excl;
+        const double tot = slice_total(amps + ((size_t)sl << cb), cb, cdf, red, excl, &total_slot);
+        if (threadIdx.x == 0) off[sl + 1] = tot;
+        __syncthreads();                             // every thread has read the slot before reuse
+    }
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        off[0] = 0.0;
+        for (uint32_t sl = 0; sl < nsl; ++sl) { acc += off[sl + 1]; off[sl + 1] = acc; }
+    }
+    for (uint32_t sl = threadIdx.x; sl < nsl; sl += blockDim.x) used[sl] = 0;
+    __syncthreads();
+    const bool mine = threadIdx.x < nshots;
+    long long tb = 0;
+    int slice = -1;
+    if (mine) {
+        const uint64_t j = it.j0 + threadIdx.x;
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        tb = dbits(u53(x.x[0], x.x[1]) * off[nsl]);
+        uint32_t lo = 0, hi = nsl;                   // smallest s with t < off[s + 1]
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tb < dbits(off[mid + 1])) hi = mid; else lo = mid + 1;
+        }
+        if (lo < nsl) { slice = (int)lo; used[lo] = 1; }
+        else a.bits[it.out0 + threadIdx.x] = (1u << n) - 1;
+    }
+    __syncthreads();
+    // pass 2: in a slice that holds shots, stage 1 again (same operations, same values) gives the
+    // thread offsets; each shot runs the sequential prefix from the chunk its target falls in.
+    for (uint32_t sl = 0; sl < nsl; ++sl) {
+        if (!used[sl]) continue;
+        const double excl = slice_stage1(amps + ((size_t)sl << cb), cb, cdf, red);
+        texcl[threadIdx.x] = excl;
+        __syncthreads();
+        if (slice == (int)sl) {
+            const double base = off[sl];
+            // first chunk whose starting offset lies beyond the target, then back one chunk
+            uint32_t lo = 0, hi = blockDim.x;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (tb < dbits(base + texcl[mid])) hi = mid; else lo = mid + 1;
+            }
+            uint32_t c = lo > 0 ? lo - 1 : 0;
+            if (c > 0) --c;                          // one more chunk back for ulp-level ties
+            uint32_t idx = (1u << cb) - 1;
+            bool found = false;
+            for (; c < blockDim.x && !found; ++c) {
+                double run = texcl[c];
+                for (uint32_t i = 0; i < K; ++i) {
+                    run += cdf[paddr(c * K + i, kb)];
+                    if (tb < dbits(base + run)) { idx = c * K + i; found = true; break; }
+                }
+            }
+            a.bits[it.out0 + threadIdx.x] = (sl << cb) | idx;
+        }
+        __syncthreads();
+    }
 }
 
 // ---- n > 17: global-memory CDF -----------------------------------------------------------------------
@@ -324,6 +457,23 @@ void* noalloc_scratch(int device) {
 }
 
 int sample_cluster_max_qubits() { return kSliceBits + 3; }
+int sample_light_max_qubits() { return kLightBits + 8; }
+
+void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
+    if (n_items == 0) return;
+    static bool configured = false;
+    const size_t smem = cdf_smem_bytes(kLightBits, kLightThreads);
+    if (!configured) {
+        PTSBE_CUDA(cudaFuncSetAttribute(k_sample_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    for (uint32_t b = 0; b < n_items; b += (1u << 30)) {
+        const uint32_t cnt = (n_items - b) < (1u << 30) ? (n_items - b) : (1u << 30);
+        k_sample_light<<<cnt, kLightThreads, smem, s>>>(a, d_items + b);
+        PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    }
+}
 
 void launch_sample_cluster(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
     if (n_items == 0) return;

@@ -209,3 +209,26 @@ def test_sampler_capacity_and_alignment_errors(P):
     with pytest.raises(PtsbeError) as e:
         P.evolve(info, info.count, 1, st)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n", [15, 17, 20])
+def test_sampler_light_states_bit_exact(P, oracle_mod, n):
+    """States with few shots (one CTA per state, slices rebuilt only where shots land) next to a
+    heavy state (cluster or global path) in the same call."""
+    torch = torch_cuda()
+    circ = brickwork(n, 2, 0.05, 0.05, seed=70 + n)
+    cid = P.register(circ)
+    sets = [[], [(0, 1)], [(1, 2)], [(2, 3)], [(3, 1), (5, 2)]]
+    shots = np.array([3000, 1, 37, 512, 200], np.uint64)
+    info = P.sample_kraus(cid, "targeted", targeted=sets, targeted_shots=shots)
+    count = info.count
+    st, w, s = evolve_gpu(P, info, 0, count, n)
+    total = int(info.shot_offsets[count])
+    bits = torch.zeros(total, dtype=torch.int32, device="cuda")
+    P.sample(info, 0, count, st, s, 4242, bits)
+    torch.cuda.synchronize()
+    b_h = bits.cpu().numpy().view(np.uint32)
+    st_h = st.cpu().numpy()
+    for a in range(count):
+        o0, o1 = int(info.shot_offsets[a]), int(info.shot_offsets[a + 1])
+        check_shots(b_h[o0:o1], st_h[a], 4242, a, 0, oracle_mod, n)
