@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
-    ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "sweep", "registers"])
+    ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "frame", "sweep", "registers"])
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
     return ap.parse_args()

@@ -293,9 +293,11 @@ PTSBE_API int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t se
 /* ---------------------------------------------------------------------------------------- */
 
 enum {
-    /* Kernel for the tile passes of ptsbe_evolve_batch: 0 auto, 1 shared-memory sweeps (one pass
-     * of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
-     * registers, the tile re-shuffled through shared memory between register groups). */
+    /* Kernel for the tile passes of ptsbe_evolve_batch: 0 auto (= 3), 1 shared-memory sweeps (one
+     * pass of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
+     * registers, the tile re-shuffled through shared memory between register groups), 3 deferred
+     * frame (permutations and diagonals tracked as an index map and factor tables; only
+     * operators that mix amplitudes pass over the tile). */
     PTSBE_OPT_EVOLVE_KERNEL = 0
 };
 

@@ -16,7 +16,7 @@ LIB = os.path.join(BUILD, "libptsbe.so")
 
 CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp"]
 CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu"]
-HEADERS = ["internal.h", "philox.h", "tile_ops.cuh"]
+HEADERS = ["internal.h", "philox.h", "tile_ops.cuh", "frame.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -54,7 +54,7 @@ struct ptsbe_ctx {
     std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
     uint32_t next_circuit = 1, next_set = 1;
-    DevBuf nodes, part, scale, items, scratch, pershot;
+    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong;
     std::vector<unsigned char> host_blob;
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
@@ -241,6 +241,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         for (auto& kv : ctx->sets) { cudaFree(kv.second->d_site); cudaFree(kv.second->d_k); }
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
+        ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong);
         ctx->free_timers();
     }
     delete ctx;
@@ -374,7 +375,11 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
 
         // --- node tables ---
-        std::vector<uint32_t> ebeg(count), eend(count), start(count), depth(count), parent(count, UINT32_MAX);
+        // With prefix reuse a set whose entries extend those of an earlier set of the range (its
+        // parent: longest such prefix) starts at the stage holding its first extra site, from the
+        // parent's input of that stage; a start in stage 0 is a start from |0...0>.
+        const uint32_t J = (uint32_t)P.stages.size();
+        std::vector<uint32_t> ebeg(count), eend(count), sstage(count), src(count);
         std::vector<uint8_t> fresh(count);
         std::vector<double> wmix(count), qa(count);
         std::unordered_map<std::string, uint32_t> index;
@@ -387,28 +392,27 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             }
             return k;
         };
-        uint32_t max_depth = 0;
         for (uint32_t a = 0; a < count; ++a) {
             const uint32_t alpha = first + a;
             const uint32_t len = s.off[alpha + 1] - s.off[alpha];
             ebeg[a] = s.off[alpha]; eend[a] = s.off[alpha + 1];
             qa[a] = s.q[alpha];
+            uint32_t parent = UINT32_MAX;
             if (reuse) {
                 for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
                     auto it = index.find(key_of(alpha, (uint32_t)p));
-                    if (it != index.end()) { parent[a] = it->second; break; }
+                    if (it != index.end()) { parent = it->second; break; }
                 }
                 index.emplace(key_of(alpha, len), a);
             }
-            if (parent[a] != UINT32_MAX) {
-                const uint32_t plen = s.off[first + parent[a] + 1] - s.off[first + parent[a]];
-                start[a] = c.site_op[s.site[s.off[alpha] + plen]];
-                fresh[a] = 0;
-                depth[a] = depth[parent[a]] + 1;
-            } else {
-                start[a] = 0; fresh[a] = 1; depth[a] = 0;
+            sstage[a] = 0; src[a] = a; fresh[a] = 1;
+            if (parent != UINT32_MAX) {
+                const uint32_t plen = s.off[first + parent + 1] - s.off[first + parent];
+                const uint32_t j = (uint32_t)P.op_stage[c.site_op[s.site[s.off[alpha] + plen]]];
+                // The parent starts no later than the child (its extra sites come first). If it
+                // starts in the same stage, both read the same input: the parent's source.
+                if (j > 0) { sstage[a] = j; src[a] = sstage[parent] == j ? src[parent] : parent; fresh[a] = 0; }
             }
-            max_depth = std::max(max_depth, depth[a]);
             // prod over unitary-mixture sites of q_{s,k_s}
             double w = 1.0;
             uint32_t e = s.off[alpha];
@@ -420,79 +424,66 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             }
             wmix[a] = w;
         }
-        // children grouped by parent, ascending branch op
-        std::vector<uint32_t> cbeg(count, 0), cend(count, 0), child_op, child_node;
-        {
-            std::vector<std::vector<std::pair<uint32_t, uint32_t>>> kids(count);
-            for (uint32_t a = 0; a < count; ++a)
-                if (parent[a] != UINT32_MAX) kids[parent[a]].push_back({start[a], a});
-            for (uint32_t a = 0; a < count; ++a) {
-                std::sort(kids[a].begin(), kids[a].end());
-                cbeg[a] = (uint32_t)child_op.size();
-                for (auto& kv : kids[a]) { child_op.push_back(kv.first); child_node.push_back(kv.second); }
-                cend[a] = (uint32_t)child_op.size();
-            }
-        }
-        // launch lists: generation g, stage j -> nodes of depth g whose start stage <= j
-        const uint32_t J = (uint32_t)P.stages.size();
+        // one launch per stage: every set whose start stage is at or before it
         std::vector<uint32_t> lists;
-        std::vector<std::pair<size_t, uint32_t>> launches;  // (offset, count) per (g, j)
-        std::vector<uint32_t> sstage(count);
-        for (uint32_t a = 0; a < count; ++a) sstage[a] = fresh[a] ? 0 : (uint32_t)P.op_stage[start[a]];
-        for (uint32_t g = 0; g <= max_depth; ++g)
-            for (uint32_t j = 0; j < J; ++j) {
-                const size_t off = lists.size();
-                for (uint32_t a = 0; a < count; ++a)
-                    if (depth[a] == g && sstage[a] <= j) lists.push_back(a);
-                launches.push_back({off, (uint32_t)(lists.size() - off)});
-            }
+        std::vector<std::pair<size_t, uint32_t>> launches;  // (offset, count) per stage
+        for (uint32_t j = 0; j < J; ++j) {
+            const size_t off = lists.size();
+            for (uint32_t a = 0; a < count; ++a)
+                if (sstage[a] <= j) lists.push_back(a);
+            launches.push_back({off, (uint32_t)(lists.size() - off)});
+        }
         Blob blob(ctx->host_blob);
-        const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_start = blob.add(start);
-        const size_t o_fresh = blob.add(fresh), o_cbeg = blob.add(cbeg), o_cend = blob.add(cend);
-        const size_t o_cop = blob.add(child_op), o_cnode = blob.add(child_node);
+        const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_sstage = blob.add(sstage);
+        const size_t o_src = blob.add(src), o_fresh = blob.add(fresh);
         const size_t o_wmix = blob.add(wmix), o_q = blob.add(qa), o_lists = blob.add(lists);
         unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
         PTSBE_CUDA(cudaMemcpyAsync(dblob, ctx->host_blob.data(), ctx->host_blob.size(), cudaMemcpyHostToDevice, ctx->stream));
         count_h2d(ctx->host_blob.size());
 
         EvolveArgs A{};
-        A.ops = c.dev.ops; A.micro = c.dev.micro; A.mats = c.dev.mats; A.chans = c.dev.chans;
-        A.site_op = c.dev.site_op; A.stages = c.dev.stages; A.groups = c.dev.groups; A.hi = c.dev.hi;
+        const DeviceCircuit& D = c.dev;
+        A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
+        A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi;
         A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
         A.ent_site = s.d_site; A.ent_k = s.d_k;
         A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
-        A.node_start = (const uint32_t*)(dblob + o_start); A.node_fresh = (const uint8_t*)(dblob + o_fresh);
-        A.node_cbeg = (const uint32_t*)(dblob + o_cbeg); A.node_cend = (const uint32_t*)(dblob + o_cend);
-        A.child_op = (const uint32_t*)(dblob + o_cop); A.child_node = (const uint32_t*)(dblob + o_cnode);
+        A.node_sstage = (const uint32_t*)(dblob + o_sstage); A.node_src = (const uint32_t*)(dblob + o_src);
+        A.node_fresh = (const uint8_t*)(dblob + o_fresh);
         A.wmix = (const double*)(dblob + o_wmix); A.qalpha = (const double*)(dblob + o_q);
-        A.states = (float2*)d_states;
         A.weights = d_weights; A.status = d_status;
+        const double sbytes = 8.0 * (double)(1ull << c.n);
+        // stage j writes out(j); out(J-1) is the caller's buffer. Without reuse every stage reads
+        // and writes the caller's buffer in place (a tile is read whole before it is written).
+        float2* const user = (float2*)d_states;
+        float2* const other = reuse && J > 1 ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * (size_t)sbytes) : user;
+        auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
         const int ob = (int)c.n - P.tb;
         float* d_scale = nullptr;
         if (ob > 0) {
             A.part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
             d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
         }
+        if (ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3) {
+            uint32_t widest = 0;
+            for (const auto& L : launches) widest = std::max(widest, L.second);
+            A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());
+        }
         const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
-        const double sbytes = 8.0 * (double)(1ull << c.n);
-        std::vector<uint32_t> kids_in_stage;
-        size_t li = 0;
-        for (uint32_t g = 0; g <= max_depth; ++g)
-            for (uint32_t j = 0; j < J; ++j, ++li) {
-                const auto& L = launches[li];
-                if (L.second == 0) continue;
-                // algorithmic bytes: read (unless started from |0>), write, checkpoints for children
-                double bytes = 0;
-                for (size_t t = L.first; t < L.first + L.second; ++t) {
-                    const uint32_t a = lists[t];
-                    bytes += (fresh[a] && j == 0) ? sbytes : 2 * sbytes;
-                    for (uint32_t ci = cbeg[a]; ci < cend[a]; ++ci)
-                        if ((uint32_t)P.op_stage[child_op[ci]] == j) bytes += sbytes;
-                }
-                ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
-                    launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
-                });
-            }
+        for (uint32_t j = 0; j < J; ++j) {
+            const auto& L = launches[j];
+            if (L.second == 0) continue;
+            A.states = out_buf(j);
+            A.states_in = j > 0 ? out_buf(j - 1) : out_buf(j);
+            // algorithmic bytes: read (unless started from |0>) and write of each set's state
+            double bytes = 0;
+            for (size_t t = L.first; t < L.first + L.second; ++t)
+                bytes += (fresh[lists[t]] && j == 0) ? sbytes : 2 * sbytes;
+            ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
+                launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
+            });
+        }
+        A.states = user;
         if (ob > 0)
             ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
     });
@@ -571,7 +562,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
 int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
     return guarded(ctx, [&] {
         if (option == PTSBE_OPT_EVOLVE_KERNEL) {
-            if (value < 0 || value > 2) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0, 1 or 2");
+            if (value < 0 || value > 3) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0, 1, 2 or 3");
             ctx->evolve_kernel = (int)value;
         } else {
             fail(PTSBE_ERR_INVALID, "unknown option");

@@ -463,10 +463,16 @@ void fuse_gates_with_noise(Circuit& c) {
                 perm[r] = nz;
             }
             if (mono) {
-                cd dv[4];
+                cd dv[8];
                 uint8_t packed = 0;
                 for (int r = 0; r < 4; ++r) { dv[r] = M[r * 4 + perm[r]]; packed |= (uint8_t)(perm[r] << (2 * r)); }
-                d.fkind = DOP_M2; d.fmat = push_mat(c, dv, 4); d.fperm = packed;
+                // separable diagonal d[2 l_a + l_b] = alpha[l_a] beta[l_b] (damping on both qubits)
+                d.fsep = 0;
+                if (std::abs(dv[0]) > 0) {
+                    dv[4] = dv[0]; dv[5] = dv[2]; dv[6] = 1.0; dv[7] = dv[1] / dv[0];
+                    if (std::abs(dv[5] * dv[7] - dv[3]) <= 1e-12 * std::abs(dv[0])) d.fsep = 1;
+                }
+                d.fkind = DOP_M2; d.fmat = push_mat(c, dv, d.fsep ? 8 : 4); d.fperm = packed;
             } else {
                 d.fkind = DOP_G2; d.fmat = push_mat(c, M, 16);
             }

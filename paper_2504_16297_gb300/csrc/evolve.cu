@@ -11,11 +11,14 @@
 // the unnormalised state times the unitary-mixture probabilities, and dividing once at the end
 // gives the same normalised state as dividing after every general Kraus operator.
 //
-// Prefix reuse: when set beta extends set alpha of the same batch, alpha writes its tile into
-// beta's output slot just before alpha reaches beta's first extra site; beta later resumes from
-// that op. Generations (depth in the prefix tree) run one after the other.
+// Prefix reuse: when set beta extends set alpha of the same batch (alpha's entries are a prefix of
+// beta's), beta skips the stages before the one holding its first extra site. In that stage it
+// reads alpha's input of the stage and runs the whole stage with its own operators (identical to
+// alpha's up to the extra site). Stages alternate between two state buffers, so every input of a
+// stage is still intact while the stage writes its outputs; one launch per stage covers all sets.
 #include <cstdio>
 
+#include "frame.cuh"
 #include "internal.h"
 #include "tile_ops.cuh"
 
@@ -40,33 +43,24 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
     for (int b = 0; b < ob; ++b)
         if ((tau >> b) & 1u) outer |= 1ull << st.outer_q[b];
     float2* g = a.states + ((size_t)node << n);
-    const uint32_t nstart = a.node_start[node];
-    const uint32_t start = nstart > st.op_begin ? nstart : st.op_begin;
+    const uint32_t src = stage_idx == (int)a.node_sstage[node] ? a.node_src[node] : node;
+    const float2* gin = a.states_in + ((size_t)src << n);
+    const uint32_t start = st.op_begin;
     __syncthreads();
     if (a.node_fresh[node] && stage_idx == 0) {
         for (uint32_t l = threadIdx.x; l < (1u << tb); l += blockDim.x)
             tile[l] = make_float2((l == 0 && tau == 0) ? 1.0f : 0.0f, 0.0f);
     } else {
-        tile_load(tile, g, tb, lb, hi, outer);
+        tile_load(tile, gin, tb, lb, hi, outer);
     }
     uint32_t e = a.node_ebeg[node];
     const uint32_t ee = a.node_eend[node];
     while (e < ee && a.site_op[a.ent_site[e]] < start) ++e;
-    uint32_t c = a.node_cbeg[node];
-    const uint32_t ce = a.node_cend[node];
-    while (c < ce && a.child_op[c] < start) ++c;
     __syncthreads();
 
     for (uint32_t op = start; op < st.op_end; ++op) {
         const DevOp o = a.ops[op];
         if (o.kind == DOP_NOISE) {
-            if (c < ce && a.child_op[c] == op) {
-                do {
-                    tile_store(tile, a.states + ((size_t)a.child_node[c] << n), tb, lb, hi, outer, 1.0f);
-                    ++c;
-                } while (c < ce && a.child_op[c] == op);
-                __syncthreads();
-            }
             uint32_t k = 0;
             if (e < ee && a.ent_site[e] == o.site) { k = a.ent_k[e]; ++e; }
             const uint32_t u0 = a.chans[o.ch].micro_off[k], u1 = a.chans[o.ch].micro_off[k + 1];
@@ -78,8 +72,8 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
                 __syncthreads();
             }
         } else {
-            if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1) && (c >= ce || a.child_op[c] >= o.fend)) {
-                // no error and no branch inside the fused block: gate and no-error operators at once
+            if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1)) {
+                // no error inside the fused block: gate and no-error operators at once
                 if (o.fkind != DOP_NOP) {
                     apply_micro(tile, tb, o.fkind, st.pos[o.q0], st.pos[o.q1], a.mats + o.fmat, o.fperm);
                     __syncthreads();
@@ -111,6 +105,133 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
     } else {
         tile_store(tile, g, tb, lb, hi, outer, 1.0f);
         if (threadIdx.x == 0) a.part[((size_t)node << ob) + tau] = part;
+    }
+}
+
+// Frame kernel: same work as k_evolve_stage, with permutations and diagonals deferred (frame.cuh).
+// Thread 0 builds the program of the stage while the other warps bring the tile in.
+__host__ __device__ inline size_t frame_tab_offset(int tb, int lb) { return (((size_t)8 << tb) + ((size_t)4 << (tb - lb)) + 15) & ~(size_t)15; }
+
+// One thread per node of a launch builds the node's program for the stage (the first segment, and
+// the builder state a tile CTA needs to continue when the program is longer).
+constexpr int kProgThreads = 16;
+__global__ void __launch_bounds__(kProgThreads) k_frame_program(EvolveArgs a, int stage_idx, const uint32_t* __restrict__ nodes,
+                                                                uint32_t n_nodes, frame::Program* progs) {
+    using namespace frame;
+    __shared__ Builder Bs[kProgThreads];
+    __shared__ DevStage st;
+    if (threadIdx.x == 0) st = a.stages[stage_idx];
+    __syncthreads();
+    const uint32_t i = blockIdx.x * kProgThreads + threadIdx.x;
+    if (i >= n_nodes) return;
+    const uint32_t node = nodes[i];
+    Builder& B = Bs[threadIdx.x];
+    Program& P = progs[i];
+    builder_init(B, a, st, node);
+    build_segment(B, P.S, P.pool, a, st);
+    P.B = B;
+}
+
+__device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t bytes, uint32_t t, uint32_t nt) {
+    uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+    for (uint32_t i = t; i < bytes / 4; i += nt) d[i] = __ldg(s + i);
+}
+
+__global__ void __launch_bounds__(1024) k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
+                                                       const frame::Program* __restrict__ progs) {
+    using namespace frame;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DevStage st;
+    __shared__ double red[33];
+    __shared__ Builder B;
+    __shared__ Step S[kMaxSteps];
+    __shared__ Factor pool[kMaxPool];
+    __shared__ uint32_t delta[kMaxTabs * kDeltaSlots];
+    const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
+    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
+    float2* tile = reinterpret_cast<float2*>(smem);
+    uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
+    float2* tabs = reinterpret_cast<float2*>(smem + frame_tab_offset(tb, lb));
+    if (tid == 0) st = a.stages[stage_idx];
+    __syncthreads();
+    for (uint32_t i = tid; i < (1u << (tb - lb)); i += nthr) hi[i] = a.hi[st.hi_off + i];
+    const uint32_t node = nodes[blockIdx.y];
+    const uint32_t tau = blockIdx.x;
+    uint64_t outer = 0;
+    for (int b = 0; b < ob; ++b)
+        if ((tau >> b) & 1u) outer |= 1ull << st.outer_q[b];
+    float2* g = a.states + ((size_t)node << n);
+    const uint32_t src = stage_idx == (int)a.node_sstage[node] ? a.node_src[node] : node;
+    const float2* gin = a.states_in + ((size_t)src << n);
+    const bool fresh = a.node_fresh[node] && stage_idx == 0;
+    __syncthreads();
+    if (tid < 32) {
+        // warp 0 brings the program in while the other warps bring the tile
+        const Program& P = progs[blockIdx.y];
+        copy_words(&B, &P.B, sizeof(Builder), tid, 32);
+        __syncwarp();
+        copy_words(S, P.S, B.nsteps * (uint32_t)sizeof(Step), tid, 32);
+        copy_words(pool, P.pool, B.npool * (uint32_t)sizeof(Factor), tid, 32);
+    } else {
+        const uint32_t t = tid - 32, nt = nthr - 32, nv = 1u << (tb - 1);
+        float4* tile4 = reinterpret_cast<float4*>(tile);
+        if (fresh) {
+            for (uint32_t v = t; v < nv; v += nt)
+                tile4[v] = make_float4((v == 0 && tau == 0) ? 1.0f : 0.0f, 0.f, 0.f, 0.f);
+        } else {
+            // eight independent loads in flight per thread before any lands in shared memory
+            for (uint32_t v0 = t; v0 < nv; v0 += 8 * nt) {
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t v = v0 + u * nt;
+                    if (v < nv) x[u] = __ldg(reinterpret_cast<const float4*>(gin + gaddr(2u * v, lb, hi, outer)));
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t v = v0 + u * nt;
+                    if (v < nv) tile4[v] = x[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    while (true) {
+        const uint32_t ns = B.nsteps;
+        for (uint32_t si = 0; si < ns; ++si) {
+            const Step& sp = S[si];
+            if (sp.ntab) {
+                prepare_tables(sp, pool, tabs, delta, tb, tid, nthr);
+                __syncthreads();
+            }
+            if (sp.kind == ST_MIX1) {
+                run_mix1(sp, tile, tabs, delta, tb, tid, nthr);
+            } else if (sp.kind == ST_MIX2) {
+                run_mix2(sp, tile, tabs, delta, tb, tid, nthr);
+            } else if (sp.kind == ST_DIAG) {
+                run_diag(sp, tile, tabs, delta, tb, tid, nthr);
+            } else if (!last) {
+                run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, 1.0f, false, tid, nthr);
+            } else if (ob == 0) {
+                const double part = cta_sum(run_store(sp, tile, tabs, delta, tb, lb, hi, outer, nullptr, 1.0f, true, tid, nthr), red);
+                const double w = a.wmix[node] * part;
+                const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
+                const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
+                run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, scale, false, tid, nthr);
+                if (tid == 0) {
+                    if (a.weights) a.weights[node] = w;
+                    if (a.status) a.status[node] = null ? 1 : 0;
+                }
+            } else {
+                const double part = cta_sum(run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, 1.0f, true, tid, nthr), red);
+                if (tid == 0) a.part[((size_t)node << ob) + tau] = part;
+            }
+            __syncthreads();
+        }
+        if (B.done) break;
+        if (tid == 0) build_segment(B, S, pool, a, st);
+        __syncthreads();
     }
 }
 
@@ -322,8 +443,8 @@ __device__ __forceinline__ uint32_t slot_addr(uint32_t sbase, const uint32_t (&s
 }
 
 // Per-CTA instruction stream of one stage (built by thread 0 while the other threads load the
-// tile): x = opcode | rb0 << 8 | rb1 << 12 | perm << 16, y = matrix offset / group / child.
-enum : uint32_t { OPC_GROUP = 16, OPC_CKPT = 17, OPC_END = 18 };
+// tile): x = opcode | rb0 << 8 | rb1 << 12 | perm << 16, y = matrix offset / group.
+enum : uint32_t { OPC_GROUP = 16, OPC_END = 18 };
 constexpr int kMaxStream = 1024;
 
 __device__ __forceinline__ uint2 instr(uint32_t opc, uint32_t rb0, uint32_t rb1, uint32_t perm, uint32_t y) {
@@ -383,7 +504,7 @@ __device__ void tile_store_sw(const float2* tile, float2* g, int tb, int lb, con
 // kMaxStream - 1 instructions, then OPC_MORE when ops remain.
 enum : uint32_t { OPC_MORE = 19 };
 struct StreamState {
-    uint32_t op, e, ee, c, ce, g;
+    uint32_t op, e, ee, g;
     int started;
 };
 
@@ -406,12 +527,6 @@ __device__ __noinline__ void build_stream(const EvolveArgs& a, const DevStage& s
         const DevOp o = a.ops[op];
         const uint8_t* rbit = sg[S.g].rbit;
         if (o.kind == DOP_NOISE) {
-            // checkpoints of children branching at this site (one per stream slot, resumable)
-            while (S.c < S.ce && a.child_op[S.c] == op) {
-                if (ip > kMaxStream - 24) { out[ip++] = instr(OPC_MORE, 0, 0, 0, 0); return; }
-                out[ip++] = instr(OPC_CKPT, 0, 0, 0, a.child_node[S.c]);
-                ++S.c;
-            }
             uint32_t k = 0;
             if (S.e < S.ee && a.ent_site[S.e] == o.site) { k = a.ent_k[S.e]; ++S.e; }
             const uint32_t u0 = a.chans[o.ch].micro_off[k], u1 = a.chans[o.ch].micro_off[k + 1];
@@ -423,7 +538,7 @@ __device__ __noinline__ void build_stream(const EvolveArgs& a, const DevStage& s
             }
         } else {
             const uint32_t r0 = rbit[st.pos[o.q0]], r1 = rbit[st.pos[o.q1]];
-            if (o.fend != 0 && (S.e >= S.ee || a.ent_site[S.e] >= o.fsite1) && (S.c >= S.ce || a.child_op[S.c] >= o.fend)) {
+            if (o.fend != 0 && (S.e >= S.ee || a.ent_site[S.e] >= o.fsite1)) {
                 if (o.fkind != DOP_NOP) out[ip++] = instr(o.fkind, r0, r1, o.fperm, o.fmat);
                 S.op = o.fend - 1;
             } else if (o.kind != DOP_NOP) {
@@ -455,22 +570,21 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
     for (int b = 0; b < ob; ++b)
         if ((tau >> b) & 1u) outer |= 1ull << st.outer_q[b];
     float2* g = a.states + ((size_t)node << n);
-    const uint32_t nstart = a.node_start[node];
-    const uint32_t start = nstart > st.op_begin ? nstart : st.op_begin;
+    const uint32_t src = stage_idx == (int)a.node_sstage[node] ? a.node_src[node] : node;
+    const float2* gin = a.states_in + ((size_t)src << n);
+    const uint32_t start = st.op_begin;
     __syncthreads();
     if (threadIdx.x == 0) {
         S.op = start; S.g = 0; S.started = 0;
         S.e = a.node_ebeg[node]; S.ee = a.node_eend[node];
         while (S.e < S.ee && a.site_op[a.ent_site[S.e]] < start) ++S.e;
-        S.c = a.node_cbeg[node]; S.ce = a.node_cend[node];
-        while (S.c < S.ce && a.child_op[S.c] < start) ++S.c;
         build_stream(a, st, sg, S, stream);
     }
     if (a.node_fresh[node] && stage_idx == 0) {
         for (uint32_t l = threadIdx.x; l < (1u << tb); l += blockDim.x)
             tile[l] = make_float2((l == 0 && tau == 0) ? 1.0f : 0.0f, 0.0f);   // sw(0) == 0
     } else {
-        tile_load_sw(tile, g, tb, lb, hi, outer);
+        tile_load_sw(tile, gin, tb, lb, hi, outer);
     }
     __syncthreads();
 
@@ -490,7 +604,7 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
             ip = -1;
             continue;
         }
-        if (opc == OPC_GROUP || opc == OPC_END || opc == OPC_CKPT) {
+        if (opc == OPC_GROUP || opc == OPC_END) {
             if (loaded) {
                 asm volatile("" : "+r"(sbase));
 #pragma unroll
@@ -499,11 +613,7 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
             }
             __syncthreads();
             if (opc == OPC_END) break;
-            if (opc == OPC_CKPT) {
-                // prefix-reuse checkpoint: the whole tile (in shared memory now) goes to the child
-                tile_store_sw(tile, a.states + ((size_t)ins.y << n), tb, lb, hi, outer, 1.0f);
-                __syncthreads();
-            } else {
+            {
                 const DevGroup& G = sg[ins.y];
                 uint32_t base = 0;
                 for (int i = 0; i < tb - kRegBits; ++i) base |= ((threadIdx.x >> i) & 1u) << G.lane_pos[i];
@@ -554,7 +664,6 @@ __global__ void __launch_bounds__(1024, 1) k_evolve_rb(EvolveArgs a, int stage_i
 }
 
 // Default kernel choice for tile passes (measured on GB300, see the design notes).
-constexpr bool kEvolveAutoRegisters = false;
 
 int evolve_threads(int tb) {
     const int amps = 1 << tb;
@@ -567,27 +676,46 @@ int evolve_threads(int tb) {
 }  // namespace
 
 size_t evolve_smem_bytes(int tb, int lb) { return ((size_t)8 << tb) + ((size_t)4 << (tb - lb)); }
+size_t evolve_frame_program_bytes() { return sizeof(frame::Program); }
+size_t evolve_frame_smem_bytes(int tb, int lb) {
+    return frame_tab_offset(tb, lb) + (size_t)frame::kMaxTabs * frame::kTabSize * sizeof(float2);
+}
 size_t evolve_rb_smem_bytes(int tb, int lb) { return ((evolve_smem_bytes(tb, lb) + 15) & ~(size_t)15) + 8 * (size_t)kMaxStream; }
 
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
                          cudaStream_t s, int kernel) {
     if (n_nodes == 0) return;
+    static_assert(sizeof(frame::Builder) % 4 == 0 && sizeof(frame::Step) % 4 == 0 && sizeof(frame::Factor) % 4 == 0,
+                  "program copies move 4-byte words");
     static bool configured = false;
     if (!configured) {
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_smem_bytes(kTileMax, 1)));
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_rb_smem_bytes(kTileMax, 1)));
+        PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_frame, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)evolve_frame_smem_bytes(kTileMax, 1)));
         configured = true;
     }
-    const bool regs = a.tb >= kRegBits && kernel != 1 && (kernel == 2 || kEvolveAutoRegisters);
+    const bool regs = a.tb >= kRegBits && kernel == 2;
+    const bool frm = kernel == 0 || kernel == 3;
     const int threads = regs ? (1 << (a.tb - kRegBits)) : evolve_threads(a.tb);
-    const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : evolve_smem_bytes(a.tb, a.lb);
+    const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : frm ? evolve_frame_smem_bytes(a.tb, a.lb)
+                                                                       : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = 1u << (a.n - a.tb);
+    frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
+    if (frm) {
+        if (!progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");
+        k_frame_program<<<(n_nodes + kProgThreads - 1) / kProgThreads, kProgThreads, 0, s>>>(a, stage, d_nodes, n_nodes, progs);
+        PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    }
     for (uint32_t b = 0; b < n_nodes; b += 65535) {
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
         if (regs)
             k_evolve_rb<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
+        else if (frm)
+            k_evolve_frame<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b, progs + b);
         else
             k_evolve_stage<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
         PTSBE_CUDA(cudaGetLastError());

@@ -62,7 +62,8 @@ struct DevOp {
     // child branches there; otherwise the ops run one by one.
     uint8_t fkind;   // DOP_NOP when nothing is fused (kind of the fused operator otherwise)
     uint8_t fperm;   // DOP_M2 permutation
-    uint8_t pad[2];
+    uint8_t fsep;    // DOP_M2: 1 when d[2 l_a + l_b] = alpha[l_a] beta[l_b]; fmat[4..7] = alpha, beta
+    uint8_t pad;
     uint32_t fmat;   // fused operator in the matrix pool
     uint32_t fend;   // op index after the absorbed noise ops
     uint32_t fsite1; // one past the last absorbed site
@@ -206,28 +207,31 @@ struct EvolveArgs {
     // Kraus-set entries (whole set, on device)
     const uint32_t* ent_site;
     const uint8_t* ent_k;
-    // per-node tables (range-local node index)
+    // per-node tables (range-local node index). A node runs stages node_sstage .. J-1; in its first
+    // stage it reads the state of slot node_src (its prefix parent's input of that stage, or its
+    // own slot), later its own slot; node_fresh: it starts from |0...0> in stage 0.
     const uint32_t* node_ebeg;
     const uint32_t* node_eend;
-    const uint32_t* node_start;      // first op to apply
-    const uint8_t* node_fresh;       // 1: start from |0...0>
-    const uint32_t* node_cbeg;
-    const uint32_t* node_cend;
-    const uint32_t* child_op;        // branch op of each child, ascending per parent
-    const uint32_t* child_node;
+    const uint32_t* node_sstage;
+    const uint32_t* node_src;
+    const uint8_t* node_fresh;
     const double* wmix;              // prod of unitary-mixture q over all sites
     const double* qalpha;
-    // outputs
-    float2* states;                  // [count][2^n]
+    // states: a stage reads states_in and writes states ([count][2^n] each; the same buffer
+    // without prefix reuse, alternating buffers with it)
+    const float2* states_in;
+    float2* states;
     double* part;                    // [count][2^(n-tb)] last-stage partial norms
     double* weights;
     uint8_t* status;
+    void* frame_progs;               // frame kernel: one program per node of a launch
 };
 
-// kernel: 0 auto, 1 shared-memory sweeps, 2 register-blocked
+// kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
                          cudaStream_t s, int kernel = 0);
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
+size_t evolve_frame_program_bytes();   // workspace per node of a frame-kernel launch
 
 struct SampleItem {                  // one cluster's share of one state's shots
     uint32_t state;                  // range-local state index

@@ -101,8 +101,10 @@ class Ptsbe:
         capi.ptsbe_release_circuit(self.ctx, cid)
 
     def set_evolve_kernel(self, kernel: str):
-        """'auto', 'sweep' (one shared-memory pass per operator) or 'registers'."""
-        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL, {"auto": 0, "sweep": 1, "registers": 2}[kernel])
+        """'auto' (= 'frame'), 'frame' (permutations and diagonals deferred; tile passes only for
+        operators that mix amplitudes), 'sweep' (one shared-memory pass per operator) or 'registers'."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL,
+                              {"auto": 0, "sweep": 1, "registers": 2, "frame": 3}[kernel])
 
     def set_timing(self, enable: bool):
         capi.ptsbe_set_timing(self.ctx, enable)

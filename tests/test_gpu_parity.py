@@ -16,7 +16,7 @@ from workloads import CircuitBuilder, brickwork, config
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=["sweep", "registers"])
+@pytest.fixture(scope="module", params=["frame", "sweep", "registers"])
 def P(request):
     ctx = gpu_ctx()
     ctx.set_evolve_kernel(request.param)
