@@ -167,7 +167,7 @@ T* dev_upload(const std::vector<T>& v) {
 
 void free_device_circuit(DeviceCircuit& d) {
     cudaFree(d.ops); cudaFree(d.micro); cudaFree(d.mats); cudaFree(d.chans);
-    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.groups); cudaFree(d.hi);
+    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.groups); cudaFree(d.hi); cudaFree(d.fstages);
     d = DeviceCircuit{};
 }
 
@@ -180,6 +180,7 @@ void upload_circuit(const Circuit& c, const Plan& P, DeviceCircuit& d) {
     d.stages = dev_upload(P.stages);
     d.groups = dev_upload(P.groups);
     d.hi = dev_upload(P.hi);
+    d.fstages = dev_upload(P.fstages);
 }
 
 // Builds a blob of aligned arrays on the host and returns the device pointers after one upload.
@@ -237,7 +238,10 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
     if (ctx->has_device()) {
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
-        for (auto& kv : ctx->circuits) { free_device_circuit(kv.second->dev); free_device_circuit(kv.second->dev_pershot); }
+        for (auto& kv : ctx->circuits) {
+            free_device_circuit(kv.second->dev); free_device_circuit(kv.second->dev_pershot);
+            free_device_circuit(kv.second->dev_frame);
+        }
         for (auto& kv : ctx->sets) { cudaFree(kv.second->d_site); cudaFree(kv.second->d_k); }
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
@@ -307,6 +311,7 @@ int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
             PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
             free_device_circuit(c.dev);
             free_device_circuit(c.dev_pershot);
+            free_device_circuit(c.dev_frame);
         }
         ctx->circuits.erase(circuit_id);
     });
@@ -370,7 +375,14 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
         ctx->use_device();
         ensure_set_on_device(s);
-        const Plan& P = c.plan;
+        const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
+        if (frame && !c.frame_planned) {
+            c.plan_frame = make_frame_plan(c, kTileMax);
+            upload_circuit(c, c.plan_frame, c.dev_frame);
+            c.frame_planned = true;
+        }
+        const Plan& P = frame ? c.plan_frame : c.plan;
+        const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
         const uint32_t S = (uint32_t)c.site_op.size();
         const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
 
@@ -442,9 +454,8 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         count_h2d(ctx->host_blob.size());
 
         EvolveArgs A{};
-        const DeviceCircuit& D = c.dev;
         A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
-        A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi;
+        A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi; A.fstages = D.fstages;
         A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
         A.ent_site = s.d_site; A.ent_k = s.d_k;
         A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
@@ -453,10 +464,11 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         A.wmix = (const double*)(dblob + o_wmix); A.qalpha = (const double*)(dblob + o_q);
         A.weights = d_weights; A.status = d_status;
         const double sbytes = 8.0 * (double)(1ull << c.n);
-        // stage j writes out(j); out(J-1) is the caller's buffer. Without reuse every stage reads
-        // and writes the caller's buffer in place (a tile is read whole before it is written).
+        // stage j writes out(j); out(J-1) is the caller's buffer. The per-operator kernels without
+        // reuse read and write the caller's buffer in place (a tile is read whole before it is
+        // written); frame stores move amplitudes between tiles, so they always alternate.
         float2* const user = (float2*)d_states;
-        float2* const other = reuse && J > 1 ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * (size_t)sbytes) : user;
+        float2* const other = (reuse || frame) && J > 1 ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * (size_t)sbytes) : user;
         auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
         const int ob = (int)c.n - P.tb;
         float* d_scale = nullptr;
@@ -464,7 +476,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             A.part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
             d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
         }
-        if (ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3) {
+        if (frame) {
             uint32_t widest = 0;
             for (const auto& L : launches) widest = std::max(widest, L.second);
             A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());

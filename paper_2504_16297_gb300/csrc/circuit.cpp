@@ -400,6 +400,15 @@ bool is_identity(const cd* m, int d) {
 
 }  // namespace
 
+// Linear part over GF(2) of a two-qubit permutation on x = 2 l_a + l_b, as the images of e_b and
+// e_a packed in 4 bits; CX (control a) and SWAP have their own, every other gate the identity's.
+uint32_t perm_linear(const int* perm) { return (uint32_t)((perm[1] ^ perm[0]) | ((perm[2] ^ perm[0]) << 2)); }
+uint32_t gate_linear(uint8_t kind) {
+    if (kind == DOP_CX) return 1u | (3u << 2);
+    if (kind == DOP_SWAP) return 2u | (1u << 2);
+    return 1u | (2u << 2);
+}
+
 void fuse_gates_with_noise(Circuit& c) {
     const size_t nops = c.ops.size();
     for (size_t i = 0; i < nops; ++i) {
@@ -462,6 +471,7 @@ void fuse_gates_with_noise(Circuit& c) {
                 if (nz < 0) mono = false;
                 perm[r] = nz;
             }
+            if (mono && perm_linear(perm) != gate_linear(c.dops[i].kind)) mono = false;   // keeps the frame set-independent
             if (mono) {
                 cd dv[8];
                 uint8_t packed = 0;
@@ -549,7 +559,8 @@ void plan_groups(Plan& P, const Circuit& c, DevStage& st) {
     st.group_end = (uint32_t)P.groups.size();
 }
 
-void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, bool probe, uint32_t probe_op) {
+void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, bool probe, uint32_t probe_op,
+                 bool groups = true) {
     const int n = (int)c.n, tb = P.tb, lb = P.lb;
     // fill the qubit set up to tb with the lowest unused qubits
     for (int q = 0; q < n && __builtin_popcountll(Q) < tb; ++q) Q |= 1ull << q;
@@ -564,7 +575,8 @@ void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, 
     for (int q = 0; q < lb; ++q) tq[t++] = q;
     for (int q = lb; q < n; ++q) if (Q & (1ull << q)) tq[t++] = q;
     int ob = 0;
-    for (int q = 0; q < n; ++q) if (!(Q & (1ull << q))) st.outer_q[ob++] = (uint8_t)q;
+    for (int q = 0; q < n; ++q)
+        if (!(Q & (1ull << q))) { st.pos[q] = (uint8_t)(0x80 | ob); st.outer_q[ob++] = (uint8_t)q; }
     for (int i = 0; i < tb; ++i) st.pos[tq[i]] = (uint8_t)i;
     st.hi_off = (uint32_t)P.hi.size();
     for (uint32_t h = 0; h < (1u << (tb - lb)); ++h) {
@@ -573,7 +585,8 @@ void close_stage(Plan& P, const Circuit& c, uint64_t Q, uint32_t b, uint32_t e, 
         P.hi.push_back(g);
     }
     for (uint32_t i = b; i < e; ++i) P.op_stage[i] = (int32_t)P.stages.size();
-    plan_groups(P, c, st);
+    if (groups) plan_groups(P, c, st);
+    else st.group_begin = st.group_end = (uint32_t)P.groups.size();
     P.stages.push_back(st);
 }
 
@@ -617,6 +630,178 @@ Plan make_plan(const Circuit& c, int tile_bits, bool pershot) {
         Q = need;
     }
     close_stage(P, c, Q, begin, (uint32_t)nops, false, 0);
+    return P;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Deferred-frame plan. The permutation part of the frame (columns A) changes only at CX and SWAP
+// gates (fused blocks keep the gate's permutation part, see fuse_gates_with_noise), so it is the
+// same for every Kraus set and the host can follow it. A stage needs the global directions of
+// the operators that may mix amplitudes inside its tile; everything else is bookkeeping.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+bool mixing_kind(uint8_t k) { return k == DOP_G1 || k == DOP_G2; }
+
+bool perm_bijective(uint32_t perm) {
+    uint32_t seen = 0;
+    for (int x = 0; x < 4; ++x) seen |= 1u << ((perm >> (2 * x)) & 3u);
+    return seen == 15u;
+}
+
+// Global directions op i may mix along (0 if it never mixes), for the current columns.
+uint32_t frame_dirs(const Circuit& c, size_t i, const uint32_t* col) {
+    const DevOp& o = c.dops[i];
+    uint32_t d = 0;
+    if (o.kind == DOP_NOISE) {
+        const DevChannel& ch = c.dchans[o.ch];
+        for (uint32_t u = ch.micro_off[0]; u < ch.micro_off[ch.nk]; ++u) {
+            const DevMicro& mi = c.dmicro[u];
+            if (!mixing_kind(mi.kind)) continue;
+            if (mi.operand != 1) d |= col[o.q0];
+            if (mi.operand != 0) d |= col[o.q1];
+        }
+        return d;
+    }
+    bool mix = mixing_kind(o.kind);
+    if (o.fend != 0 && (mixing_kind(o.fkind) || (o.fkind == DOP_M2 && !perm_bijective(o.fperm)))) mix = true;
+    if (!mix) return 0;
+    d = col[o.q0];
+    if (o.nt == 2) d |= col[o.q1];
+    return d;
+}
+
+void frame_linear(const Circuit& c, size_t i, uint32_t* col) {
+    const DevOp& o = c.dops[i];
+    if (o.kind == DOP_CX) col[o.q0] ^= col[o.q1];
+    else if (o.kind == DOP_SWAP) std::swap(col[o.q0], col[o.q1]);
+}
+
+// Rows of A^-1 for the columns of A (n x n over GF(2), Gauss-Jordan).
+void invert_cols(int n, const uint32_t* col, uint32_t* row) {
+    uint32_t M[kMaxQubits], I[kMaxQubits];     // row x of A (bit q = bit x of col[q]), identity
+    for (int x = 0; x < n; ++x) {
+        M[x] = 0;
+        for (int q = 0; q < n; ++q) if ((col[q] >> x) & 1u) M[x] |= 1u << q;
+        I[x] = 1u << x;
+    }
+    for (int q = 0; q < n; ++q) {
+        int piv = -1;
+        for (int x = q; x < n; ++x) if ((M[x] >> q) & 1u) { piv = x; break; }
+        if (piv < 0) fail(PTSBE_ERR_INVALID, "frame plan: singular permutation");
+        std::swap(M[q], M[piv]); std::swap(I[q], I[piv]);
+        for (int x = 0; x < n; ++x)
+            if (x != q && ((M[x] >> q) & 1u)) { M[x] ^= M[q]; I[x] ^= I[q]; }
+    }
+    for (int q = 0; q < n; ++q) row[q] = I[q];   // row q of A^-1 as a mask over global bits
+}
+
+void close_frame_stage(Plan& P, const Circuit& c, uint32_t T, uint32_t b, uint32_t e, const uint32_t* entry,
+                       bool last, int lbf) {
+    const int n = (int)c.n;
+    close_stage(P, c, T, b, e, false, 0, false);
+    const DevStage& st = P.stages.back();
+    DevFrameStage f{};
+    for (int q = 0; q < n; ++q) f.col[q] = entry[q];
+    invert_cols(n, f.col, f.row);
+    f.last = last ? 1u : 0u;
+    f.lbf = (uint32_t)lbf;
+    if (last) {
+        uint32_t col[kMaxQubits], row[kMaxQubits];
+        for (int q = 0; q < n; ++q) col[q] = entry[q];
+        for (uint32_t i = b; i < e; ++i) frame_linear(c, i, col);
+        invert_cols(n, col, row);
+        auto logical_of = [&](int x) {          // R e_x
+            uint32_t v = 0;
+            for (int q = 0; q < n; ++q) if ((row[q] >> x) & 1u) v |= 1u << q;
+            return v;
+        };
+        // basis of R(span T): e_0 .. e_{lbf-1} first, then R e_x for tile bits x
+        uint32_t ech[kMaxQubits];
+        int piv[kMaxQubits], d = 0;
+        auto try_add = [&](uint32_t v) {
+            uint32_t x = v;
+            for (int i = 0; i < d; ++i) if ((x >> piv[i]) & 1u) x ^= ech[i];
+            if (!x) return false;
+            ech[d] = x; piv[d] = 31 - __builtin_clz(x); f.w[d] = v; ++d;
+            return true;
+        };
+        for (int k = 0; k < lbf; ++k)
+            if (!try_add(1u << k)) fail(PTSBE_ERR_INVALID, "frame plan: output bits outside the last tile");
+        for (int t = 0; t < P.tb && d < P.tb; ++t) {
+            int x = -1;
+            for (int g = 0; g < n; ++g) if (st.pos[g] == t) x = g;
+            try_add(logical_of(x));
+        }
+        if (d != P.tb) fail(PTSBE_ERR_INVALID, "frame plan: incomplete output basis");
+        for (int k = 0; k < P.tb; ++k) {
+            uint32_t g = 0;   // A w_k (global), then its tile-local address
+            for (int q = 0; q < n; ++q) if ((f.w[k] >> q) & 1u) g ^= col[q];
+            uint32_t m = 0;
+            for (int x = 0; x < n; ++x)
+                if ((g >> x) & 1u) {
+                    if (st.pos[x] & 0x80) fail(PTSBE_ERR_INVALID, "frame plan: output basis leaves the tile");
+                    m |= 1u << st.pos[x];
+                }
+            f.m[k] = (uint16_t)m;
+        }
+        for (int i = 0; i < n - P.tb; ++i) f.ox[i] = logical_of(st.outer_q[i]);
+    }
+    P.fstages.push_back(f);
+}
+
+}  // namespace
+
+Plan make_frame_plan(const Circuit& c, int tile_bits) {
+    Plan P;
+    const int n = (int)c.n;
+    if (n > 32) fail(PTSBE_ERR_UNSUPPORTED, "more than 32 qubits");
+    P.tb = std::min(n, tile_bits);
+    P.lb = std::min(P.tb, kLowBits);
+    const size_t nops = c.ops.size();
+    P.op_stage.assign(nops, 0);
+    uint32_t col[kMaxQubits], entry[kMaxQubits];
+    for (int q = 0; q < n; ++q) col[q] = entry[q] = 1u << q;
+    const uint32_t all = n == 32 ? ~0u : ((1u << n) - 1u);
+    if (n <= tile_bits) {
+        close_frame_stage(P, c, all, 0, (uint32_t)nops, entry, true, P.lb);
+        return P;
+    }
+    const uint32_t low = (1u << P.lb) - 1u;
+    uint32_t U = low, begin = 0;
+    for (size_t i = 0; i < nops; ++i) {
+        const uint32_t d = frame_dirs(c, i, col);
+        if (__builtin_popcount(U | d) > P.tb) {
+            if (__builtin_popcount(low | d) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "frame plan: mixing directions wider than a tile");
+            close_frame_stage(P, c, U, begin, (uint32_t)i, entry, false, 0);
+            begin = (uint32_t)i;
+            U = low | d;
+            for (int q = 0; q < n; ++q) entry[q] = col[q];
+        } else {
+            U |= d;
+        }
+        frame_linear(c, i, col);
+    }
+    // the last tile also holds the images of the low logical bits (coalesced output)
+    uint32_t F = 0;
+    for (int k = 0; k < P.lb; ++k) F |= col[k];
+    if (__builtin_popcount(U | F) <= P.tb) {
+        close_frame_stage(P, c, U | F, begin, (uint32_t)nops, entry, true, P.lb);
+        return P;
+    }
+    close_frame_stage(P, c, U, begin, (uint32_t)nops, entry, false, 0);
+    // one more stage without ops that writes logical order
+    int lbf = P.lb;
+    while (lbf > 1) {
+        uint32_t G = 0;
+        for (int k = 0; k < lbf; ++k) G |= col[k];
+        if (__builtin_popcount(low | G) <= P.tb) break;
+        --lbf;
+    }
+    uint32_t G = 0;
+    for (int k = 0; k < lbf; ++k) G |= col[k];
+    if (__builtin_popcount(low | G) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "frame plan: output bit wider than a tile");
+    close_frame_stage(P, c, low | G, (uint32_t)nops, (uint32_t)nops, col, true, lbf);
     return P;
 }
 

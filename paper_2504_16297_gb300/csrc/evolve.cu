@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kProgThreads) k_frame_program(EvolveArgs a, in
     const uint32_t node = nodes[i];
     Builder& B = Bs[threadIdx.x];
     Program& P = progs[i];
-    builder_init(B, a, st, node);
-    build_segment(B, P.S, P.pool, a, st);
+    builder_init(B, a, st, a.fstages[stage_idx], node);
+    build_segment(B, P.S, P.pool, a, st, kProgSteps, kProgPool);
     P.B = B;
 }
 
@@ -138,11 +138,13 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t 
     for (uint32_t i = t; i < bytes / 4; i += nt) d[i] = __ldg(s + i);
 }
 
-__global__ void __launch_bounds__(1024) k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
+constexpr int kFrameThreads = 512;   // 128 registers per thread: grouped mixes stay in registers
+__global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
                                                        const frame::Program* __restrict__ progs) {
     using namespace frame;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevStage st;
+    __shared__ DevFrameStage fs;
     __shared__ double red[33];
     __shared__ Builder B;
     __shared__ Step S[kMaxSteps];
@@ -153,26 +155,25 @@ __global__ void __launch_bounds__(1024) k_evolve_frame(EvolveArgs a, int stage_i
     float2* tile = reinterpret_cast<float2*>(smem);
     uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
     float2* tabs = reinterpret_cast<float2*>(smem + frame_tab_offset(tb, lb));
-    if (tid == 0) st = a.stages[stage_idx];
+    copy_words(&st, a.stages + stage_idx, sizeof(DevStage), tid, nthr);
+    copy_words(&fs, a.fstages + stage_idx, sizeof(DevFrameStage), tid, nthr);
     __syncthreads();
     for (uint32_t i = tid; i < (1u << (tb - lb)); i += nthr) hi[i] = a.hi[st.hi_off + i];
     const uint32_t node = nodes[blockIdx.y];
     const uint32_t tau = blockIdx.x;
-    uint64_t outer = 0;
-    for (int b = 0; b < ob; ++b)
-        if ((tau >> b) & 1u) outer |= 1ull << st.outer_q[b];
+    const uint64_t outer = outer_offset(st, ob, tau);
     float2* g = a.states + ((size_t)node << n);
     const uint32_t src = stage_idx == (int)a.node_sstage[node] ? a.node_src[node] : node;
     const float2* gin = a.states_in + ((size_t)src << n);
     const bool fresh = a.node_fresh[node] && stage_idx == 0;
     __syncthreads();
+    // The first program segment is read in place (global memory, the same for all tiles of the
+    // set); segments built here when the program is longer live in shared memory.
+    const Program& P = progs[blockIdx.y];
+    const Step* Sp = P.S;
+    const Factor* poolp = P.pool;
     if (tid < 32) {
-        // warp 0 brings the program in while the other warps bring the tile
-        const Program& P = progs[blockIdx.y];
-        copy_words(&B, &P.B, sizeof(Builder), tid, 32);
-        __syncwarp();
-        copy_words(S, P.S, B.nsteps * (uint32_t)sizeof(Step), tid, 32);
-        copy_words(pool, P.pool, B.npool * (uint32_t)sizeof(Factor), tid, 32);
+        copy_words(&B, &P.B, sizeof(Builder), tid, 32);   // warp 0, while the others bring the tile
     } else {
         const uint32_t t = tid - 32, nt = nthr - 32, nv = 1u << (tb - 1);
         float4* tile4 = reinterpret_cast<float4*>(tile);
@@ -200,39 +201,42 @@ __global__ void __launch_bounds__(1024) k_evolve_frame(EvolveArgs a, int stage_i
     while (true) {
         const uint32_t ns = B.nsteps;
         for (uint32_t si = 0; si < ns; ++si) {
-            const Step& sp = S[si];
+            const Step& sp = Sp[si];
             if (sp.ntab) {
-                prepare_tables(sp, pool, tabs, delta, tb, tid, nthr);
+                prepare_tables(sp, fs, poolp, tabs, delta, tb, tau, tid, nthr);
                 __syncthreads();
             }
             if (sp.kind == ST_MIX1) {
-                run_mix1(sp, tile, tabs, delta, tb, tid, nthr);
+                run_mix1(sp, tile, tabs, delta, tb, tau, tid, nthr);
             } else if (sp.kind == ST_MIX2) {
-                run_mix2(sp, tile, tabs, delta, tb, tid, nthr);
+                run_mix2(sp, tile, tabs, delta, tb, tau, tid, nthr);
             } else if (sp.kind == ST_DIAG) {
                 run_diag(sp, tile, tabs, delta, tb, tid, nthr);
-            } else if (!last) {
-                run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, 1.0f, false, tid, nthr);
+            } else if (sp.kind == ST_STORE) {
+                run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr);
             } else if (ob == 0) {
-                const double part = cta_sum(run_store(sp, tile, tabs, delta, tb, lb, hi, outer, nullptr, 1.0f, true, tid, nthr), red);
+                const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, nullptr, 1.0f, true, tid, nthr), red);
                 const double w = a.wmix[node] * part;
                 const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
                 const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
-                run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, scale, false, tid, nthr);
+                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, scale, false, tid, nthr);
                 if (tid == 0) {
                     if (a.weights) a.weights[node] = w;
                     if (a.status) a.status[node] = null ? 1 : 0;
                 }
             } else {
-                const double part = cta_sum(run_store(sp, tile, tabs, delta, tb, lb, hi, outer, g, 1.0f, true, tid, nthr), red);
+                const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, true, tid, nthr), red);
                 if (tid == 0) a.part[((size_t)node << ob) + tau] = part;
             }
             __syncthreads();
         }
         if (B.done) break;
-        if (tid == 0) build_segment(B, S, pool, a, st);
+        if (tid == 0) build_segment(B, S, pool, a, st, kMaxSteps, kMaxPool);
+        Sp = S;
+        poolp = pool;
         __syncthreads();
     }
+    (void)last;
 }
 
 // Per node: total squared norm from the tile partials (fixed order), weight, null flag, scale.
@@ -699,7 +703,7 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
     }
     const bool regs = a.tb >= kRegBits && kernel == 2;
     const bool frm = kernel == 0 || kernel == 3;
-    const int threads = regs ? (1 << (a.tb - kRegBits)) : evolve_threads(a.tb);
+    const int threads = regs ? (1 << (a.tb - kRegBits)) : frm ? std::min(evolve_threads(a.tb), kFrameThreads) : evolve_threads(a.tb);
     const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : frm ? evolve_frame_smem_bytes(a.tb, a.lb)
                                                                        : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = 1u << (a.n - a.tb);

@@ -1,25 +1,30 @@
 // Deferred-frame tile pass of batched state preparation (the default evolve kernel).
 //
-// Most operators of a noisy, CX-heavy circuit are monomial inside a tile: a permutation of basis
-// states times a diagonal (CX, CZ, SWAP, Pauli errors, amplitude-damping Kraus operators, and
-// two-qubit gates fused with their no-error operators). Moving 2^tb amplitudes through shared
-// memory for each of them is what bounds the per-operator sweep. Here the tile is kept in a frame
+// Most operators of a noisy, CX-heavy circuit are monomial: a permutation of basis states times a
+// diagonal (CX, CZ, SWAP, Pauli errors, amplitude-damping Kraus operators, and gates fused with
+// their no-error operators). Moving amplitudes for each of them is what bounds a per-operator
+// sweep. Here a state is kept in a frame
 //
-//     psi(l) = D(p) * s[p],      p = A l ^ b,
+//     psi(l) = D(x) * s[x],      x = A l ^ b,
 //
-// l the logical tile index, s the tile in shared memory, A an invertible matrix over GF(2)
-// (column j = col[j], the physical image of logical bit j), b a translation, and D a product of
-// factors f(<r1,p>, <r2,p>) of parities of the physical address (<r,p> = popcount(r & p) mod 2).
-// A permutation only updates A and b, a diagonal only adds a factor; operators that mix
-// amplitudes (a general 2x2 or 4x4) run as tile passes, and stores write logical order. Before a
-// mixing pass, the factors that are not constant along its pair directions are applied (they do
-// not commute with it); the others stay deferred. At every pass, the factors it applies are
-// grouped into at most kMaxTabs tables of 2^d entries, d <= kTabBits: a table is indexed by the
-// parities of the address against d basis rows, so a lookup replaces a product of factors.
+// l the logical index, x the global (physical) index, s the stored amplitudes, A an invertible
+// matrix over GF(2) (column q = col[q], the physical image of logical bit q), b a translation and
+// D a product of factors f(<r1,x>, <r2,x>) of parities of the physical index (<r,x> = popcount(r
+// & x) mod 2). A permutation updates A and b, a diagonal adds a factor; only operators that mix
+// amplitudes (a general 2x2 or 4x4) pass over the tile, along physical directions that the plan
+// keeps inside the stage's tile (a set of global index bits). A changes only at gates, so it is
+// the same for every Kraus set; b and D are per set. Between stages the state is stored with b
+// and D applied (global index x holds psi(A^-1 x)); the last stage writes logical order.
 //
-// One thread turns the op list of the stage into a short program (steps); the CTA runs it. The
-// step functions take the thread index and count explicitly and touch disjoint amplitudes per
-// thread, so the host can run them one thread at a time.
+// Before a mixing pass, the factors not constant along its directions are applied (they do not
+// commute with it); the others stay deferred. The factors a pass applies are grouped into at most
+// kMaxTabs tables of 2^d entries (d <= kTabBits), indexed by the parities of the tile-local
+// address against d basis rows, so one lookup replaces a product of factors. A factor's parity
+// against the outer bits of the index is constant on a tile and folds into its table.
+//
+// One thread turns the op list of a (set, stage) into a short program (steps); the CTAs of the
+// set's tiles run it. The step functions take the thread index and count explicitly and touch
+// disjoint amplitudes per thread, so the host can run them one thread at a time.
 #pragma once
 #include <cstdint>
 
@@ -36,56 +41,66 @@
 namespace ptsbe {
 namespace frame {
 
-constexpr int kMaxSteps = 40;
+constexpr int kMaxSteps = 40;                        // program segment held in shared memory
+constexpr int kMaxPool = 256;
+constexpr int kProgSteps = 160;                      // program built by the prepass (global memory)
+constexpr int kProgPool = 1024;
 constexpr int kMaxTabs = 3;
 constexpr int kTabBits = 10;
 constexpr int kTabSize = 1 << kTabBits;
 constexpr int kMaxPending = 40;
-constexpr int kMaxPool = 256;
 constexpr int kStepsPerOp = 16;                      // worst case steps one op can emit
 constexpr int kPoolPerOp = 4 * kMaxPending;          // worst case pool entries one op can take
 constexpr int kDeltaSlots = 16;                      // per-table index deltas of a step
+constexpr int kMaxDirs = 4;                          // single-qubit mixes grouped into one pass
 
-enum : uint8_t { ST_MIX1 = 0, ST_MIX2 = 1, ST_DIAG = 2, ST_STORE = 3 };
+// MIX1: 1..kMaxDirs single-qubit mixes on independent directions (one pass, 2^ndir amplitudes per
+// thread in registers); MIX2: one two-qubit mix; DIAG: factors only; STORE / FINAL: stage end.
+enum : uint8_t { ST_MIX1 = 0, ST_MIX2 = 1, ST_DIAG = 2, ST_STORE = 3, ST_FINAL = 4 };
 
 struct Factor {
-    uint16_t r1, r2;   // value f[2 <r1,p> + <r2,p>]
-    uint16_t c1, c2;   // r1, r2 in the coordinates of the table basis (set when grouped)
+    uint32_t r1, r2;   // value f[2 <r1,x> + <r2,x>] (global index masks)
+    uint32_t r1o, r2o; // outer parts of r1, r2 in tile-index bits (set when grouped)
+    uint16_t c1, c2;   // tile parts of r1, r2 in the coordinates of the table basis (set when grouped)
+    uint32_t pad;
     float2 f[4];
 };
 
 struct Table {
     uint16_t fb, fe;                 // pool factors [fb, fe)
     uint8_t d, pad[3];
-    uint16_t basis[kTabBits];        // index bit i = <basis[i], p>
+    uint16_t basis[kTabBits];        // index bit i = <basis[i], tile-local address>
 };
 
 struct Step {
-    uint8_t kind, ntab, pa, pb;      // MIX1/MIX2: pivot bits of the pair enumeration
-    uint16_t u, v;                   // MIX1: pair direction u; MIX2: directions of the two qubits
-    uint16_t ra, rb;                 // MIX: rows giving the logical bits of the operand qubits
-    uint8_t ca, cb, ident, pad;      // MIX: parities <ra,b>, <rb,b>; STORE: frame is the identity
-    uint16_t col[kTileMax];          // STORE: frame columns
-    uint16_t bv, pad2;               // STORE: frame translation
+    uint8_t kind, ntab, ndir, pad0;
+    uint8_t piv[kMaxDirs];           // MIX1: pivot bits of the coset enumeration (ascending); MIX2: pa, pb
+    uint16_t dir[kMaxDirs];          // MIX: tile-local directions (MIX2: dir[0] first qubit, dir[1] second)
+    uint16_t rin[kMaxDirs];          // MIX: tile parts of the rows of the operand qubits
+    uint32_t rout[kMaxDirs];         // MIX: outer parts of those rows; STORE: rout[0] = outer part of b
+    uint8_t cpar[kMaxDirs];          // MIX: <row, b>
+    uint32_t lb0;                    // FINAL: R b (logical); STORE: tile part of b
+    uint32_t npush, nframe;          // builder counters when emitted (grouping test)
     Table tab[kMaxTabs];
-    float2 m[16];                    // MIX1: 2x2, MIX2: 4x4 on 2 l_a + l_b
+    float2 m[16];                    // MIX1: 2x2 of direction i at m[4i..4i+3]; MIX2: 4x4 on 2 l_a + l_b
 };
 
 struct Builder {
-    uint16_t col[kTileMax], row[kTileMax];   // A and A^-1 (rows)
-    uint16_t bv, pad;
-    uint32_t op, e, ee;                      // next op and entry cursor of the node
-    uint32_t npend, nsteps, npool, done;
-    uint16_t ech[kTabBits], comb[kTabBits];  // echelon rows of the table being filled
+    uint32_t col[kMaxQubits], row[kMaxQubits];   // A and the rows of A^-1
+    uint32_t bv;
+    uint32_t op, e, ee;                          // next op and entry cursor of the set
+    uint32_t npend, nsteps, npool, done, last;
+    uint32_t npush, nframe;                      // factor changes and frame changes so far
+    uint16_t ech[kTabBits], comb[kTabBits];      // echelon rows of the table being filled
     uint8_t piv[kTabBits], pad2[2];
     Factor pend[kMaxPending];
 };
 
-// Program of one (state, stage): built once by a prepass kernel, shared by the state's tiles.
+// Program of one (set, stage): built once by a prepass kernel, shared by the set's tiles.
 struct Program {
     Builder B;
-    Step S[kMaxSteps];
-    Factor pool[kMaxPool];
+    Step S[kProgSteps];
+    Factor pool[kProgPool];
 };
 
 PTSBE_HD uint32_t par(uint32_t x) {
@@ -125,6 +140,26 @@ PTSBE_HD uint32_t ins00(uint32_t i, int pa, int pb) {
 }
 PTSBE_HD bool is_one(float2 z) { return z.x == 1.0f && z.y == 0.0f; }
 
+// Tile-local and outer parts of a global index mask (DevStage::pos: tile bit, or 0x80 | outer bit).
+PTSBE_HD uint32_t tile_part(const DevStage& st, uint32_t m) {
+    uint32_t r = 0;
+    while (m) {
+        const int g = low_bit(m);
+        m &= m - 1u;
+        if (!(st.pos[g] & 0x80)) r |= 1u << st.pos[g];
+    }
+    return r;
+}
+PTSBE_HD uint32_t outer_part(const DevStage& st, uint32_t m) {
+    uint32_t r = 0;
+    while (m) {
+        const int g = low_bit(m);
+        m &= m - 1u;
+        if (st.pos[g] & 0x80) r |= 1u << (st.pos[g] & 0x7F);
+    }
+    return r;
+}
+
 // ------------------------------------------------------------------------------------------
 // Builder (one thread)
 // ------------------------------------------------------------------------------------------
@@ -146,16 +181,37 @@ PTSBE_HD uint32_t reduce_or_add(uint32_t r, Table& T, uint16_t* ech, uint16_t* c
     return 1u << (d - 1);
 }
 
+// Orders the index bits of a finished table by the lowest set bit of their basis rows. The lanes
+// of a warp differ in the low tile-local bits, so their lookups then differ in the low index bits
+// and spread over the shared-memory banks.
+PTSBE_HD void order_table(Table& T, Factor* pool) {
+    uint8_t ord[kTabBits], at[kTabBits];
+    for (int i = 0; i < T.d; ++i) {
+        int j = i;
+        while (j > 0 && low_bit(T.basis[ord[j - 1]]) > low_bit(T.basis[i])) { ord[j] = ord[j - 1]; --j; }
+        ord[j] = (uint8_t)i;
+    }
+    uint16_t nb[kTabBits];
+    for (int i = 0; i < T.d; ++i) { nb[i] = T.basis[ord[i]]; at[ord[i]] = (uint8_t)i; }
+    for (int i = 0; i < T.d; ++i) T.basis[i] = nb[i];
+    for (uint32_t j = T.fb; j < T.fe; ++j) {
+        uint32_t c1 = 0, c2 = 0;
+        for (int i = 0; i < T.d; ++i) {
+            if ((pool[j].c1 >> i) & 1u) c1 |= 1u << at[i];
+            if ((pool[j].c2 >> i) & 1u) c2 |= 1u << at[i];
+        }
+        pool[j].c1 = (uint16_t)c1;
+        pool[j].c2 = (uint16_t)c2;
+    }
+}
+
 // Groups the pending factors of `mask` into tables of st; copies them into the pool. Returns the
 // factors that found a table (all of them unless more than kMaxTabs tables would be needed).
-PTSBE_HD uint64_t fill_tables(Builder& B, Step& st, Factor* pool, uint64_t mask) {
+PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor* pool, uint64_t mask) {
     st.ntab = 0;
     uint64_t used = 0, left = mask;
     while (left && st.ntab < kMaxTabs) {
         Table& T = st.tab[st.ntab];
-        uint16_t* ech = B.ech;
-        uint16_t* comb = B.comb;
-        uint8_t* piv = B.piv;
         int d = 0;
         T.fb = (uint16_t)B.npool;
         uint64_t took = 0;
@@ -163,18 +219,21 @@ PTSBE_HD uint64_t fill_tables(Builder& B, Step& st, Factor* pool, uint64_t mask)
             if (!((left >> j) & 1u)) continue;
             const Factor& f = B.pend[j];
             const int d0 = d;
-            const uint32_t c1 = reduce_or_add(f.r1, T, ech, comb, piv, d);
+            const uint32_t c1 = reduce_or_add(tile_part(stg, f.r1), T, B.ech, B.comb, B.piv, d);
             uint32_t c2 = 0;
-            if (d <= kTabBits) c2 = reduce_or_add(f.r2, T, ech, comb, piv, d);
+            if (d <= kTabBits) c2 = reduce_or_add(tile_part(stg, f.r2), T, B.ech, B.comb, B.piv, d);
             if (d > kTabBits) { d = d0; continue; }
             Factor& g = pool[B.npool++];
             g = f;
             g.c1 = (uint16_t)c1;
             g.c2 = (uint16_t)c2;
+            g.r1o = outer_part(stg, f.r1);
+            g.r2o = outer_part(stg, f.r2);
             took |= 1ull << j;
         }
         T.fe = (uint16_t)B.npool;
         T.d = (uint8_t)d;
+        order_table(T, pool);
         ++st.ntab;
         used |= took;
         left &= ~took;
@@ -199,10 +258,10 @@ PTSBE_HD uint64_t drop_pending(Builder& B, uint64_t rm, uint64_t keep) {
 // Returns the step S[B.nsteps] with tables for the factors of mask. If they need more than
 // kMaxTabs tables, DIAG steps apply the overflow to the tile first (those factors leave the
 // pending list). With remove, the factors of the returned step leave the pending list too.
-PTSBE_HD Step& take_tables(Builder& B, Step* S, Factor* pool, uint64_t mask, bool remove) {
+PTSBE_HD Step& take_tables(Builder& B, const DevStage& stg, Step* S, Factor* pool, uint64_t mask, bool remove) {
     while (true) {
         Step& st = S[B.nsteps];
-        const uint64_t used = fill_tables(B, st, pool, mask);
+        const uint64_t used = fill_tables(B, stg, st, pool, mask);
         if (used == mask) {
             if (remove) drop_pending(B, used, 0);
             return st;
@@ -215,8 +274,9 @@ PTSBE_HD Step& take_tables(Builder& B, Step* S, Factor* pool, uint64_t mask, boo
 
 PTSBE_HD uint64_t all_pending(const Builder& B) { return B.npend >= 64 ? ~0ull : ((1ull << B.npend) - 1ull); }
 
-// Adds the factor g[2 <r1,p> + <r2,p>], merging it with a pending factor on the same rows.
-PTSBE_HD void push_factor(Builder& B, Step* S, Factor* pool, uint32_t r1, uint32_t r2, const float2* gin) {
+// Adds the factor g[2 <r1,x> + <r2,x>], merging it with a pending factor on the same rows.
+PTSBE_HD void push_factor(Builder& B, const DevStage& stg, Step* S, Factor* pool, uint32_t r1, uint32_t r2,
+                          const float2* gin) {
     float2 g[4] = {gin[0], gin[1], gin[2], gin[3]};
     if (r1 == 0 && r2 != 0) { r1 = r2; r2 = 0; const float2 t = g[1]; g[1] = g[2]; g[2] = t; }
     if (r2 != 0 && r1 > r2) {
@@ -226,6 +286,7 @@ PTSBE_HD void push_factor(Builder& B, Step* S, Factor* pool, uint32_t r1, uint32
     if (r2 == 0) { g[1] = g[0]; g[3] = g[2]; }
     if (r1 == 0) { g[1] = g[2] = g[3] = g[0]; }
     if (is_one(g[0]) && is_one(g[1]) && is_one(g[2]) && is_one(g[3])) return;
+    ++B.npush;
     for (uint32_t j = 0; j < B.npend; ++j) {
         Factor& f = B.pend[j];
         if (f.r1 == r1 && f.r2 == r2) {
@@ -234,28 +295,28 @@ PTSBE_HD void push_factor(Builder& B, Step* S, Factor* pool, uint32_t r1, uint32
         }
     }
     if (B.npend == kMaxPending) {
-        Step& st = take_tables(B, S, pool, all_pending(B), true);
+        Step& st = take_tables(B, stg, S, pool, all_pending(B), true);
         st.kind = ST_DIAG;
         ++B.nsteps;
     }
     Factor& f = B.pend[B.npend++];
-    f.r1 = (uint16_t)r1; f.r2 = (uint16_t)r2; f.c1 = f.c2 = 0;
+    f.r1 = r1; f.r2 = r2; f.r1o = f.r2o = 0; f.c1 = f.c2 = 0; f.pad = 0;
     for (int x = 0; x < 4; ++x) f.f[x] = g[x];
 }
 
 // diag(d0, d1) on logical bit q
-PTSBE_HD void factor1(Builder& B, Step* S, Factor* pool, int q, float2 d0, float2 d1) {
+PTSBE_HD void factor1(Builder& B, const DevStage& stg, Step* S, Factor* pool, int q, float2 d0, float2 d1) {
     const uint32_t r = B.row[q], c = par(r & B.bv);
     const float2 g[4] = {c ? d1 : d0, c ? d1 : d0, c ? d0 : d1, c ? d0 : d1};
-    push_factor(B, S, pool, r, 0, g);
+    push_factor(B, stg, S, pool, r, 0, g);
 }
 
 // diagonal d[2 l_a + l_b] on logical bits (a, b)
-PTSBE_HD void factor2(Builder& B, Step* S, Factor* pool, int a, int b, const float2* d) {
+PTSBE_HD void factor2(Builder& B, const DevStage& stg, Step* S, Factor* pool, int a, int b, const float2* d) {
     const uint32_t ra = B.row[a], rb = B.row[b];
     const uint32_t x = 2u * par(ra & B.bv) + par(rb & B.bv);
     const float2 g[4] = {d[0 ^ x], d[1 ^ x], d[2 ^ x], d[3 ^ x]};
-    push_factor(B, S, pool, ra, rb, g);
+    push_factor(B, stg, S, pool, ra, rb, g);
 }
 
 PTSBE_HD uint64_t varying(const Builder& B, uint32_t u, uint32_t v) {
@@ -267,100 +328,158 @@ PTSBE_HD uint64_t varying(const Builder& B, uint32_t u, uint32_t v) {
     return m;
 }
 
-PTSBE_HD void emit_mix1(Builder& B, Step* S, Factor* pool, int q, const float2* m) {
+// Pivot bits of the coset enumeration of independent directions (reduced echelon form: each
+// direction contributes a distinct lowest bit; representatives have those bits clear).
+PTSBE_HD void set_pivots(Step& st) {
+    uint32_t ech[kMaxDirs];
+    uint8_t pv[kMaxDirs];
+    for (int i = 0; i < st.ndir; ++i) {
+        uint32_t x = st.dir[i];
+        for (int j = 0; j < i; ++j)
+            if ((x >> pv[j]) & 1u) x ^= ech[j];
+        ech[i] = x;
+        pv[i] = (uint8_t)low_bit(x);
+    }
+    for (int i = 0; i < st.ndir; ++i) {   // ascending
+        uint8_t b = pv[i];
+        int j = i;
+        while (j > 0 && st.piv[j - 1] > b) { st.piv[j] = st.piv[j - 1]; --j; }
+        st.piv[j] = b;
+    }
+}
+
+PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, int q, const float2* m) {
     const uint32_t u = B.col[q];
-    Step& st = take_tables(B, S, pool, varying(B, u, 0), true);
+    const uint32_t n0 = B.nsteps;
+    Step& st = take_tables(B, stg, S, pool, varying(B, u, 0), true);
+    const uint32_t ut = tile_part(stg, u);
+    // Join the previous single-qubit pass when nothing changed the factors or the frame since it
+    // (its factors commute with the earlier mixes: they were pending and constant along them).
+    if (B.nsteps == n0 && n0 > 0) {
+        Step& pr = S[n0 - 1];
+        bool ok = pr.kind == ST_MIX1 && pr.ndir < kMaxDirs && pr.npush == B.npush && pr.nframe == B.nframe &&
+                  pr.ntab + st.ntab <= kMaxTabs;
+        for (int i = 0; ok && i < pr.ndir; ++i) ok = par(pr.rin[i] & ut) == 0;
+        if (ok) {
+            for (int t = 0; t < st.ntab; ++t) pr.tab[pr.ntab + t] = st.tab[t];
+            pr.ntab = (uint8_t)(pr.ntab + st.ntab);
+            const int i = pr.ndir++;
+            pr.dir[i] = (uint16_t)ut;
+            pr.rin[i] = (uint16_t)tile_part(stg, B.row[q]);
+            pr.rout[i] = outer_part(stg, B.row[q]);
+            pr.cpar[i] = (uint8_t)par(B.row[q] & B.bv);
+            for (int k = 0; k < 4; ++k) pr.m[4 * i + k] = m[k];
+            set_pivots(pr);
+            return;
+        }
+    }
     st.kind = ST_MIX1;
-    st.u = (uint16_t)u;
-    st.pa = (uint8_t)low_bit(u);
-    st.ra = B.row[q];
-    st.ca = (uint8_t)par(B.row[q] & B.bv);
-    for (int i = 0; i < 4; ++i) st.m[i] = m[i];
+    st.ndir = 1;
+    st.dir[0] = (uint16_t)ut;
+    st.rin[0] = (uint16_t)tile_part(stg, B.row[q]);
+    st.rout[0] = outer_part(stg, B.row[q]);
+    st.cpar[0] = (uint8_t)par(B.row[q] & B.bv);
+    st.npush = B.npush;
+    st.nframe = B.nframe;
+    for (int k = 0; k < 4; ++k) st.m[k] = m[k];
+    set_pivots(st);
     ++B.nsteps;
 }
 
-PTSBE_HD void emit_mix2(Builder& B, Step* S, Factor* pool, int a, int b, const float2* m) {
-    const uint32_t u = B.col[a], v = B.col[b];
-    Step& st = take_tables(B, S, pool, varying(B, u, v), true);
+PTSBE_HD void emit_mix2(Builder& B, const DevStage& stg, Step* S, Factor* pool, int a, int b, const float2* m) {
+    Step& st = take_tables(B, stg, S, pool, varying(B, B.col[a], B.col[b]), true);
+    const uint32_t u = tile_part(stg, B.col[a]), v = tile_part(stg, B.col[b]);
     st.kind = ST_MIX2;
-    st.u = (uint16_t)u;
-    st.v = (uint16_t)v;
+    st.ndir = 2;
+    st.dir[0] = (uint16_t)u;
+    st.dir[1] = (uint16_t)v;
     const int pa = low_bit(u);
     const uint32_t v2 = ((v >> pa) & 1u) ? (v ^ u) : v;
-    st.pa = (uint8_t)pa;
-    st.pb = (uint8_t)low_bit(v2);
-    st.ra = B.row[a];
-    st.rb = B.row[b];
-    st.ca = (uint8_t)par(B.row[a] & B.bv);
-    st.cb = (uint8_t)par(B.row[b] & B.bv);
+    st.piv[0] = (uint8_t)pa;
+    st.piv[1] = (uint8_t)low_bit(v2);
+    st.rin[0] = (uint16_t)tile_part(stg, B.row[a]);
+    st.rin[1] = (uint16_t)tile_part(stg, B.row[b]);
+    st.rout[0] = outer_part(stg, B.row[a]);
+    st.rout[1] = outer_part(stg, B.row[b]);
+    st.cpar[0] = (uint8_t)par(B.row[a] & B.bv);
+    st.cpar[1] = (uint8_t)par(B.row[b] & B.bv);
+    st.npush = B.npush;
+    st.nframe = B.nframe;
     for (int i = 0; i < 16; ++i) st.m[i] = m[i];
     ++B.nsteps;
 }
 
-PTSBE_HD void emit_store(Builder& B, Step* S, Factor* pool, int tb) {
-    Step& st = take_tables(B, S, pool, all_pending(B), false);
-    st.kind = ST_STORE;
-    bool ident = B.bv == 0;
-    for (int j = 0; j < tb; ++j) {
-        st.col[j] = B.col[j];
-        ident = ident && B.col[j] == (1u << j);
+// End of the stage: STORE writes D(x) s[x] to global index x ^ b; FINAL writes logical order.
+PTSBE_HD void emit_end(Builder& B, const DevStage& stg, Step* S, Factor* pool, int n) {
+    Step& st = take_tables(B, stg, S, pool, all_pending(B), false);
+    if (B.last) {
+        st.kind = ST_FINAL;
+        uint32_t l = 0;
+        for (int q = 0; q < n; ++q) l |= par(B.row[q] & B.bv) << q;
+        st.lb0 = l;
+    } else {
+        st.kind = ST_STORE;
+        st.lb0 = tile_part(stg, B.bv);
+        st.rout[0] = outer_part(stg, B.bv);
     }
-    st.bv = B.bv;
-    st.ident = ident ? 1 : 0;
     ++B.nsteps;
 }
 
 // out[x] = d[x] * in[perm_x] on x = 2 l_a + l_b as a frame change (perm is a bijection).
 PTSBE_HD void perm2(Builder& B, int a, int b, const uint32_t* pm) {
+    ++B.nframe;
     const uint32_t t = pm[0], c1 = pm[1] ^ t, c2 = pm[2] ^ t;   // images of e_b and e_a
     const uint32_t ca = B.col[a], cb = B.col[b], ra = B.row[a], rb = B.row[b];
-    B.bv ^= (uint16_t)(((t >> 1) ? ca : 0u) ^ ((t & 1u) ? cb : 0u));
-    B.col[a] = (uint16_t)(((c2 >> 1) ? ca : 0u) ^ ((c2 & 1u) ? cb : 0u));
-    B.col[b] = (uint16_t)(((c1 >> 1) ? ca : 0u) ^ ((c1 & 1u) ? cb : 0u));
-    B.row[a] = (uint16_t)(((c1 & 1u) ? ra : 0u) ^ ((c1 >> 1) ? rb : 0u));
-    B.row[b] = (uint16_t)(((c2 & 1u) ? ra : 0u) ^ ((c2 >> 1) ? rb : 0u));
+    B.bv ^= ((t >> 1) ? ca : 0u) ^ ((t & 1u) ? cb : 0u);
+    B.col[a] = ((c2 >> 1) ? ca : 0u) ^ ((c2 & 1u) ? cb : 0u);
+    B.col[b] = ((c1 >> 1) ? ca : 0u) ^ ((c1 & 1u) ? cb : 0u);
+    B.row[a] = ((c1 & 1u) ? ra : 0u) ^ ((c1 >> 1) ? rb : 0u);
+    B.row[b] = ((c2 & 1u) ? ra : 0u) ^ ((c2 >> 1) ? rb : 0u);
 }
 
-// One operator on tile positions (a, b).
-PTSBE_HD void process(Builder& B, Step* S, Factor* pool, uint8_t kind, int a, int b, const float2* m, uint32_t perm,
-                      bool sep) {
+// One operator on logical qubits (a, b).
+PTSBE_HD void process(Builder& B, const DevStage& stg, Step* S, Factor* pool, uint8_t kind, int a, int b,
+                      const float2* m, uint32_t perm, bool sep) {
     switch (kind) {
-    case DOP_G1: emit_mix1(B, S, pool, a, m); break;
-    case DOP_D1: factor1(B, S, pool, a, m[0], m[1]); break;
+    case DOP_G1: emit_mix1(B, stg, S, pool, a, m); break;
+    case DOP_D1: factor1(B, stg, S, pool, a, m[0], m[1]); break;
     case DOP_X1:   // [[0, m0], [m1, 0]]: psi'(l) = d[l_a] psi(l ^ e_a), d = (m0, m1)
+        ++B.nframe;
         B.bv ^= B.col[a];
-        factor1(B, S, pool, a, m[0], m[1]);
+        factor1(B, stg, S, pool, a, m[0], m[1]);
         break;
     case DOP_CX:
+        ++B.nframe;
         B.col[a] ^= B.col[b];
         B.row[b] ^= B.row[a];
         break;
     case DOP_CZ: {
         const float2 d[4] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f), make_float2(1.f, 0.f), make_float2(-1.f, 0.f)};
-        factor2(B, S, pool, a, b, d);
+        factor2(B, stg, S, pool, a, b, d);
         break;
     }
     case DOP_SWAP: {
-        uint16_t t = B.col[a]; B.col[a] = B.col[b]; B.col[b] = t;
+        ++B.nframe;
+        uint32_t t = B.col[a]; B.col[a] = B.col[b]; B.col[b] = t;
         t = B.row[a]; B.row[a] = B.row[b]; B.row[b] = t;
         break;
     }
-    case DOP_G2: emit_mix2(B, S, pool, a, b, m); break;
+    case DOP_G2: emit_mix2(B, stg, S, pool, a, b, m); break;
     case DOP_M2: {
         const uint32_t pm[4] = {perm & 3u, (perm >> 2) & 3u, (perm >> 4) & 3u, (perm >> 6) & 3u};
         if (((1u << pm[0]) | (1u << pm[1]) | (1u << pm[2]) | (1u << pm[3])) != 15u) {
             float2 g[16];
             for (int i = 0; i < 16; ++i) g[i] = make_float2(0.f, 0.f);
             for (int x = 0; x < 4; ++x) g[4 * x + pm[x]] = m[x];
-            emit_mix2(B, S, pool, a, b, g);
+            emit_mix2(B, stg, S, pool, a, b, g);
             break;
         }
         perm2(B, a, b, pm);
         if (sep) {
-            factor1(B, S, pool, a, m[4], m[5]);
-            factor1(B, S, pool, b, m[6], m[7]);
+            factor1(B, stg, S, pool, a, m[4], m[5]);
+            factor1(B, stg, S, pool, b, m[6], m[7]);
         } else {
-            factor2(B, S, pool, a, b, m);
+            factor2(B, stg, S, pool, a, b, m);
         }
         break;
     }
@@ -368,8 +487,25 @@ PTSBE_HD void process(Builder& B, Step* S, Factor* pool, uint8_t kind, int a, in
     }
 }
 
-PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage& st, uint32_t node) {
-    for (int j = 0; j < kTileMax; ++j) B.col[j] = B.row[j] = (uint16_t)(1u << j);
+PTSBE_HD bool perm_is_bijection(uint32_t perm) {
+    uint32_t seen = 0;
+    for (int x = 0; x < 4; ++x) seen |= 1u << ((perm >> (2 * x)) & 3u);
+    return seen == 15u;
+}
+
+// 4x4 matrix of a fused two-qubit block (general, or monomial d[x] at column perm_x).
+PTSBE_HD void fused_matrix(const DevOp& o, const float2* m, float2* g) {
+    if (o.fkind == DOP_G2) {
+        for (int i = 0; i < 16; ++i) g[i] = m[i];
+        return;
+    }
+    for (int i = 0; i < 16; ++i) g[i] = make_float2(0.f, 0.f);
+    for (int x = 0; x < 4; ++x) g[4 * x + ((o.fperm >> (2 * x)) & 3u)] = m[x];
+}
+
+PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage& st, const DevFrameStage& fs,
+                                uint32_t node) {
+    for (int q = 0; q < kMaxQubits; ++q) { B.col[q] = fs.col[q]; B.row[q] = fs.row[q]; }
     B.bv = 0;
     B.op = st.op_begin;
     uint32_t e = a.node_ebeg[node];
@@ -378,17 +514,20 @@ PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage&
     B.e = e;
     B.npend = 0;
     B.done = 0;
+    B.last = fs.last;
+    B.npush = B.nframe = 0;
 }
 
-// Emits steps until the stage ends (then the final store and done = 1) or the step list or the
+// Emits steps until the stage ends (then the end step and done = 1) or the step list or the
 // factor pool could overflow with one more op (the next segment continues from B.op).
-PTSBE_HD_CALL void build_segment(Builder& B, Step* S, Factor* pool, const EvolveArgs& a, const DevStage& st) {
+PTSBE_HD_CALL void build_segment(Builder& B, Step* S, Factor* pool, const EvolveArgs& a, const DevStage& st,
+                                 uint32_t max_steps, uint32_t max_pool) {
     B.nsteps = 0;
     B.npool = 0;
     while (true) {
-        if (B.nsteps + kStepsPerOp > kMaxSteps || B.npool + kPoolPerOp > kMaxPool) return;
+        if (B.nsteps + kStepsPerOp > max_steps || B.npool + kPoolPerOp > max_pool) return;
         if (B.op >= st.op_end) {
-            emit_store(B, S, pool, a.tb);
+            emit_end(B, st, S, pool, a.n);
             B.done = 1;
             return;
         }
@@ -400,22 +539,35 @@ PTSBE_HD_CALL void build_segment(Builder& B, Step* S, Factor* pool, const Evolve
             const DevChannel& ch = a.chans[o.ch];
             for (uint32_t u = ch.micro_off[k]; u < ch.micro_off[k + 1]; ++u) {
                 const DevMicro mi = a.micro[u];
-                process(B, S, pool, mi.kind, st.pos[mi.operand == 1 ? o.q1 : o.q0], st.pos[o.q1], a.mats + mi.mat, 0, false);
+                process(B, st, S, pool, mi.kind, mi.operand == 1 ? o.q1 : o.q0, o.q1, a.mats + mi.mat, 0, false);
             }
             B.op = op + 1;
         } else if (o.fend != 0 && (B.e >= B.ee || a.ent_site[B.e] >= o.fsite1)) {
             // no error inside the fused block: gate and no-error operators at once
-            process(B, S, pool, o.fkind, st.pos[o.q0], st.pos[o.q1], a.mats + o.fmat, o.fperm, o.fsep != 0);
+            const bool mixes = o.fkind == DOP_G2 || (o.fkind == DOP_M2 && !perm_is_bijection(o.fperm));
+            if (mixes && (o.kind == DOP_CX || o.kind == DOP_SWAP)) {
+                // The block M is not monomial, but the gate's permutation P must still move the
+                // frame (the unfused path moves it too): P first, then M P^-1 mixes.
+                const uint32_t pm[4] = {0u, o.kind == DOP_CX ? 1u : 2u, o.kind == DOP_CX ? 3u : 1u, o.kind == DOP_CX ? 2u : 3u};
+                float2 g[16], h[16];
+                fused_matrix(o, a.mats + o.fmat, g);
+                for (int r = 0; r < 4; ++r)
+                    for (int y = 0; y < 4; ++y) h[4 * r + y] = g[4 * r + pm[y]];
+                perm2(B, o.q0, o.q1, pm);
+                emit_mix2(B, st, S, pool, o.q0, o.q1, h);
+            } else {
+                process(B, st, S, pool, o.fkind, o.q0, o.q1, a.mats + o.fmat, o.fperm, o.fsep != 0);
+            }
             B.op = o.fend;
         } else {
-            process(B, S, pool, o.kind, st.pos[o.q0], st.pos[o.q1], a.mats + o.mat, 0, false);
+            process(B, st, S, pool, o.kind, o.q0, o.q1, a.mats + o.mat, 0, false);
             B.op = op + 1;
         }
     }
 }
 
 // ------------------------------------------------------------------------------------------
-// Steps (every thread of the CTA; thread `tid` of `nthr`)
+// Steps (every thread of the CTA; thread `tid` of `nthr`, tile index `tau`)
 // ------------------------------------------------------------------------------------------
 
 PTSBE_HD uint32_t lin_idx(const Table& T, uint32_t p) {
@@ -424,32 +576,45 @@ PTSBE_HD uint32_t lin_idx(const Table& T, uint32_t p) {
     return r;
 }
 
-// Physical address delta of bit j of the iteration counter (slots < 14), and of the pair
-// directions (slots 14, 15), for a step.
-PTSBE_HD uint32_t step_delta(const Step& st, int tb, uint32_t nthr, int j) {
+PTSBE_HD int log2u(uint32_t x) {
+    int lg = 0;
+    while ((1u << lg) < x) ++lg;
+    return lg;
+}
+
+PTSBE_HD uint32_t ins_piv(uint32_t i, const uint8_t* piv, int k) {   // zeros at ascending pivots
+    for (int j = 0; j < k; ++j) i = ins0(i, piv[j]);
+    return i;
+}
+
+// Tile-local address delta of bit j of the iteration counter (slots < 10), of the directions of
+// a grouped mix (slots 10 + i), and of the fixed offsets of the other steps (slots 14, 15).
+PTSBE_HD uint32_t step_delta(const Step& st, const DevFrameStage& fs, int tb, uint32_t nthr, int j) {
+    const uint32_t mask = (1u << tb) - 1u;
     switch (st.kind) {
     case ST_MIX1:
-        if (j == 15) return st.u;
-        return j < 14 ? ins0(nthr << j, st.pa) & ((1u << tb) - 1u) : 0u;
+        if (j >= 10) return j - 10 < st.ndir ? st.dir[j - 10] : 0u;
+        return ins_piv(nthr << j, st.piv, st.ndir) & mask;
     case ST_MIX2:
-        if (j == 14) return st.v;
-        if (j == 15) return st.u;
-        return j < 14 ? ins00(nthr << j, st.pa, st.pb) & ((1u << tb) - 1u) : 0u;
+        if (j == 14) return st.dir[1];
+        if (j == 15) return st.dir[0];
+        return j < 14 ? ins00(nthr << j, st.piv[0], st.piv[1]) & mask : 0u;
     case ST_DIAG:
-        return j < 14 ? (nthr << j) & ((1u << tb) - 1u) : 0u;
-    default: {   // STORE: logical index l = 2 (tid + k nthr) + {0, 1}
-        if (j == 15) return st.col[0];
-        int lg = 0;
-        while ((1u << lg) < nthr) ++lg;
-        const int bit = 1 + lg + j;
-        return (j < 14 && bit < tb) ? st.col[bit] : 0u;
+        return j < 14 ? (nthr << j) & mask : 0u;
+    case ST_STORE:   // destination d = 2 (tid + k nthr) + {0, 1}, source d ^ b
+        if (j == 15) return 1u;
+        return j < 14 ? ((2u * nthr) << j) & mask : 0u;
+    default: {       // FINAL: tile-local address M t, t = 2 (tid + k nthr) + {0, 1}
+        if (j == 15) return fs.m[0];
+        const int bit = 1 + log2u(nthr) + j;
+        return (j < 14 && bit < tb) ? fs.m[bit] : 0u;
     }
     }
 }
 
 // Table entries and index deltas of a step (before the pass; a barrier separates them).
-PTSBE_HD void prepare_tables(const Step& st, const Factor* pool, float2* tabs, uint32_t* delta, int tb, uint32_t tid,
-                             uint32_t nthr) {
+PTSBE_HD void prepare_tables(const Step& st, const DevFrameStage& fs, const Factor* pool, float2* tabs, uint32_t* delta,
+                             int tb, uint32_t tau, uint32_t tid, uint32_t nthr) {
     for (int t = 0; t < st.ntab; ++t) {
         const Table& T = st.tab[t];
         const uint32_t size = 1u << T.d;
@@ -457,14 +622,14 @@ PTSBE_HD void prepare_tables(const Step& st, const Factor* pool, float2* tabs, u
             float2 v = make_float2(1.f, 0.f);
             for (uint32_t j = T.fb; j < T.fe; ++j) {
                 const Factor& f = pool[j];
-                v = fmul(v, f.f[2u * par(f.c1 & idx) + par(f.c2 & idx)]);
+                v = fmul(v, f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))]);
             }
             tabs[t * kTabSize + idx] = v;
         }
     }
     const uint32_t nd = (uint32_t)st.ntab * kDeltaSlots;
     for (uint32_t i = tid; i < nd; i += nthr)
-        delta[i] = lin_idx(st.tab[i / kDeltaSlots], step_delta(st, tb, nthr, (int)(i % kDeltaSlots)));
+        delta[i] = lin_idx(st.tab[i / kDeltaSlots], step_delta(st, fs, tb, nthr, (int)(i % kDeltaSlots)));
 }
 
 struct Lookup {
@@ -495,30 +660,78 @@ PTSBE_HD void lookup_step(Lookup& L, const uint32_t* delta, int j) {
 
 // The iterations of a thread visit k = 0 .. K-1 in Gray-code order, so each step flips one bit
 // of the address and of every table index.
-PTSBE_HD void run_mix1(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tid,
-                       uint32_t nthr) {
-    const uint32_t N = 1u << (tb - 1);
+//
+// Grouped single-qubit mixes: the thread holds the 2^ND amplitudes base ^ sum_i y_i dir[i] of one
+// coset of the directions. The logical bit of operand i there is <rin[i], base> ^ cpar[i] ^ y_i
+// (rows and columns of one frame), so each 2x2 acts on register pairs y, y | 1 << i with one
+// orientation per coset.
+template <int ND>
+PTSBE_HD void run_mix1_n(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
+                         uint32_t tid, uint32_t nthr) {
+    constexpr int NA = 1 << ND;
+    const uint32_t N = 1u << (tb - ND);
     if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
-    const float2 m00 = st.m[0], m01 = st.m[1], m10 = st.m[2], m11 = st.m[3];
-    const uint32_t u = st.u, ra = st.ra, ca = st.ca;
-    uint32_t p0 = ins0(tid, st.pa);
+    uint32_t dir[ND], rin[ND], c0[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) { dir[i] = st.dir[i]; rin[i] = st.rin[i]; c0[i] = st.cpar[i] ^ par(st.rout[i] & tau); }
+    uint32_t base = ins_piv(tid, st.piv, ND);
     Lookup L;
-    lookup_init(L, st, p0);
+    lookup_init(L, st, base);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            p0 ^= ins0(nthr << j, st.pa);
+            base ^= ins_piv(nthr << j, st.piv, ND);
             lookup_step(L, delta, j);
         }
-        const uint32_t p1 = p0 ^ u;
-        float2 x0 = s[p0], x1 = s[p1];
-        if (L.ntab) { x0 = apply_tabs(x0, L, tabs, delta, -1); x1 = apply_tabs(x1, L, tabs, delta, 15); }
-        const bool fl = (par(ra & p0) ^ ca) != 0;
-        const float2 a = fl ? x1 : x0, b = fl ? x0 : x1;
-        const float2 y0 = fmul2(m00, a, m01, b), y1 = fmul2(m10, a, m11, b);
-        s[p0] = fl ? y1 : y0;
-        s[p1] = fl ? y0 : y1;
+        float2 v[NA];
+#pragma unroll
+        for (int y = 0; y < NA; ++y) {
+            uint32_t off = 0;
+#pragma unroll
+            for (int i = 0; i < ND; ++i) if ((y >> i) & 1) off ^= dir[i];
+            v[y] = s[base ^ off];
+        }
+        if (L.ntab) {
+#pragma unroll
+            for (int y = 0; y < NA; ++y) {
+                Lookup Ly = L;
+#pragma unroll
+                for (int i = 0; i < ND; ++i) if ((y >> i) & 1) lookup_step(Ly, delta, 10 + i);
+                v[y] = apply_tabs(v[y], Ly, tabs, delta, -1);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            const bool fl = (par(rin[i] & base) ^ c0[i]) != 0;
+            const float2 a00 = st.m[4 * i], a01 = st.m[4 * i + 1], a10 = st.m[4 * i + 2], a11 = st.m[4 * i + 3];
+            const float2 g00 = fl ? a11 : a00, g01 = fl ? a10 : a01, g10 = fl ? a01 : a10, g11 = fl ? a00 : a11;
+#pragma unroll
+            for (int y = 0; y < NA; ++y) {
+                if ((y >> i) & 1) continue;
+                const float2 a = v[y], b = v[y | (1 << i)];
+                v[y] = fmul2(g00, a, g01, b);
+                v[y | (1 << i)] = fmul2(g10, a, g11, b);
+            }
+        }
+#pragma unroll
+        for (int y = 0; y < NA; ++y) {
+            uint32_t off = 0;
+#pragma unroll
+            for (int i = 0; i < ND; ++i) if ((y >> i) & 1) off ^= dir[i];
+            s[base ^ off] = v[y];
+        }
+    }
+}
+
+PTSBE_HD void run_mix1(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
+                       uint32_t tid, uint32_t nthr) {
+    static_assert(kMaxDirs == 4, "one instantiation per group size");
+    switch (st.ndir) {
+    case 1: run_mix1_n<1>(st, s, tabs, delta, tb, tau, tid, nthr); break;
+    case 2: run_mix1_n<2>(st, s, tabs, delta, tb, tau, tid, nthr); break;
+    case 3: run_mix1_n<3>(st, s, tabs, delta, tb, tau, tid, nthr); break;
+    default: run_mix1_n<4>(st, s, tabs, delta, tb, tau, tid, nthr); break;
     }
 }
 
@@ -527,19 +740,20 @@ PTSBE_HD void xswap(float2* z, uint32_t x0) {
     if (x0 & 2u) { float2 t = z[0]; z[0] = z[2]; z[2] = t; t = z[1]; z[1] = z[3]; z[3] = t; }
 }
 
-PTSBE_HD void run_mix2(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tid,
-                       uint32_t nthr) {
+PTSBE_HD void run_mix2(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
+                       uint32_t tid, uint32_t nthr) {
     const uint32_t N = 1u << (tb - 2);
     if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
-    const uint32_t w[4] = {0u, st.v, st.u, (uint32_t)(st.u ^ st.v)};   // logical difference y -> offset
-    uint32_t base = ins00(tid, st.pa, st.pb);
+    const uint32_t w[4] = {0u, st.dir[1], st.dir[0], (uint32_t)(st.dir[0] ^ st.dir[1])};   // logical difference y -> offset
+    const uint32_t ca = st.cpar[0] ^ par(st.rout[0] & tau), cb = st.cpar[1] ^ par(st.rout[1] & tau);
+    uint32_t base = ins00(tid, st.piv[0], st.piv[1]);
     Lookup L;
     lookup_init(L, st, base);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            base ^= ins00(nthr << j, st.pa, st.pb);
+            base ^= ins00(nthr << j, st.piv[0], st.piv[1]);
             lookup_step(L, delta, j);
         }
         float2 z[4];
@@ -553,7 +767,7 @@ PTSBE_HD void run_mix2(const Step& st, float2* s, const float2* tabs, const uint
             lookup_step(L3, delta, 14);
             z[3] = apply_tabs(z[3], L3, tabs, delta, 15);
         }
-        const uint32_t x0 = 2u * (par(st.ra & base) ^ st.ca) + (par(st.rb & base) ^ st.cb);
+        const uint32_t x0 = 2u * (par(st.rin[0] & base) ^ ca) + (par(st.rin[1] & base) ^ cb);
         xswap(z, x0);   // z[x] = amplitude of logical x
         float2 o[4];
 #pragma unroll
@@ -594,38 +808,71 @@ PTSBE_HD uint64_t gaddr(uint32_t l, int lb, const uint32_t* hi, uint64_t outer) 
     return (uint64_t)(l & ((1u << lb) - 1u)) | (uint64_t)hi[l >> lb] | outer;
 }
 
-// Writes the logical tile times `scale` to dst (when not null) and returns this thread's part of
-// the squared norm of the logical amplitudes (when want_norm).
-PTSBE_HD double run_store(const Step& st, const float2* s, const float2* tabs, const uint32_t* delta, int tb, int lb,
-                          const uint32_t* hi, uint64_t outer, float2* dst, float scale, bool want_norm, uint32_t tid,
-                          uint32_t nthr) {
+PTSBE_HD uint64_t outer_offset(const DevStage& stg, int ob, uint32_t tau) {
+    uint64_t o = 0;
+    for (int b = 0; b < ob; ++b)
+        if ((tau >> b) & 1u) o |= 1ull << stg.outer_q[b];
+    return o;
+}
+
+// Intermediate store: tile-local d of tile tau ^ b_out receives D(x) s[d ^ b_in] (x the source).
+PTSBE_HD void run_store(const Step& st, const DevStage& stg, const float2* s, const float2* tabs, const uint32_t* delta,
+                        int tb, int lb, int ob, const uint32_t* hi, uint32_t tau, float2* dst, uint32_t tid, uint32_t nthr) {
     const uint32_t N = 1u << (tb - 1);
-    double acc = 0.0;
-    if (tid >= N) return acc;
+    if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
-    int lg = 0;
-    while ((1u << lg) < nthr) ++lg;
-    uint32_t v = tid;
-    uint32_t p0 = st.bv;
-    for (int b = 0; (1u << b) <= tid; ++b)
-        if ((tid >> b) & 1u) p0 ^= st.col[b + 1];
+    const uint32_t bin = st.lb0;
+    const uint64_t outer = outer_offset(stg, ob, tau ^ st.rout[0]);
+    uint32_t d = 2u * tid;
     Lookup L;
-    lookup_init(L, st, p0);
+    lookup_init(L, st, d ^ bin);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            v ^= nthr << j;
-            p0 ^= st.col[1 + lg + j];
+            d ^= (2u * nthr) << j;
             lookup_step(L, delta, j);
         }
-        float2 a0 = s[p0], a1 = s[p0 ^ st.col[0]];
+        float2 a0 = s[d ^ bin], a1 = s[(d ^ bin) ^ 1u];
         if (L.ntab) { a0 = apply_tabs(a0, L, tabs, delta, -1); a1 = apply_tabs(a1, L, tabs, delta, 15); }
-        if (want_norm) acc += (double)fmaf(a0.x, a0.x, a0.y * a0.y) + (double)fmaf(a1.x, a1.x, a1.y * a1.y);
-        if (dst)
-            *reinterpret_cast<float4*>(dst + gaddr(2u * v, lb, hi, outer)) =
-                make_float4(a0.x * scale, a0.y * scale, a1.x * scale, a1.y * scale);
+        *reinterpret_cast<float4*>(dst + gaddr(d, lb, hi, outer)) = make_float4(a0.x, a0.y, a1.x, a1.y);
     }
-    return acc;
+}
+
+// Last stage: writes the logical amplitudes of this tile, times `scale`, to dst (when not null) and
+// returns this thread's part of their squared norm (when want_norm).
+PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2* s, const float2* tabs,
+                          const uint32_t* delta, int tb, int ob, uint32_t tau, float2* dst, float scale, bool want_norm,
+                          uint32_t tid, uint32_t nthr) {
+    const uint32_t N = 1u << (tb - 1);
+    if (tid >= N) return 0.0;
+    const uint32_t K = N > nthr ? N / nthr : 1u;
+    const int lg = log2u(nthr);
+    uint32_t p = 0, l = st.lb0;
+    for (int i = 0; i < ob; ++i)
+        if ((tau >> i) & 1u) l ^= fs.ox[i];
+    for (int b = 0; (1u << b) <= tid; ++b)
+        if ((tid >> b) & 1u) { p ^= fs.m[b + 1]; l ^= fs.w[b + 1]; }
+    Lookup L;
+    lookup_init(L, st, p);
+    float part = 0.f;
+    for (uint32_t k = 0; k < K; ++k) {
+        if (k) {
+            const int j = low_bit(k);
+            p ^= fs.m[1 + lg + j];
+            l ^= fs.w[1 + lg + j];
+            lookup_step(L, delta, j);
+        }
+        float2 a0 = s[p], a1 = s[p ^ fs.m[0]];
+        if (L.ntab) { a0 = apply_tabs(a0, L, tabs, delta, -1); a1 = apply_tabs(a1, L, tabs, delta, 15); }
+        if (want_norm) part += fmaf(a0.x, a0.x, a0.y * a0.y) + fmaf(a1.x, a1.x, a1.y * a1.y);
+        if (dst) {
+            // w[0] = e_0: the pair is {l, l ^ 1}
+            const float4 x = (l & 1u) ? make_float4(a1.x * scale, a1.y * scale, a0.x * scale, a0.y * scale)
+                                      : make_float4(a0.x * scale, a0.y * scale, a1.x * scale, a1.y * scale);
+            *reinterpret_cast<float4*>(dst + (l & ~1u)) = x;
+        }
+    }
+    return (double)part;
 }
 
 }  // namespace frame

@@ -110,12 +110,28 @@ struct DevGroup {
     uint8_t pad[3];
 };
 
+// Deferred-frame plan, per stage. Between stages the state of logical index l is stored at global
+// index A_j l (A_j invertible over GF(2), the same for every Kraus set); a stage's tile is a set of
+// global index bits (DevStage::pos/outer_q/hi) that holds the directions of its mixing operators.
+struct DevFrameStage {
+    uint32_t col[kMaxQubits];        // A at the stage start: global image of logical bit q
+    uint32_t row[kMaxQubits];        // rows of A^-1: logical bit q = <row[q], global index>
+    // Last stage (logical output order): tile-local index t holds logical l = l0 ^ sum_k t_k w[k]
+    // at tile-local address sum_k t_k m[k]; l0 = R b ^ (xor of ox[i] over the set outer bits i of
+    // the tile index); w[k] = e_k for k < lbf, so runs of 2^lbf amplitudes stay contiguous.
+    uint32_t w[kTileMax];
+    uint16_t m[kTileMax];
+    uint32_t ox[kMaxQubits];
+    uint32_t last, lbf;
+};
+
 struct Plan {
     int tb = 0, lb = 0;              // tile bits, contiguous low bits
     std::vector<DevStage> stages;
     std::vector<DevGroup> groups;
     std::vector<uint32_t> hi;        // concatenated hi tables: global offset of tile bits [lb, tb)
     std::vector<int32_t> op_stage;   // op index -> stage
+    std::vector<DevFrameStage> fstages;   // deferred-frame plans only
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -141,6 +157,7 @@ struct DeviceCircuit {
     DevStage* stages = nullptr;
     DevGroup* groups = nullptr;
     uint32_t* hi = nullptr;
+    DevFrameStage* fstages = nullptr;
     size_t bytes = 0;
 };
 
@@ -158,11 +175,14 @@ struct Circuit {
     std::vector<DevMicro> dmicro;
     std::vector<float2> dmats;
     std::vector<DevChannel> dchans;
-    Plan plan;                       // PTSBE evolution plan
+    Plan plan;                       // PTSBE evolution plan (ops inside each stage's qubit set)
     Plan plan_pershot;               // Algorithm 1 plan (stage break before every general site)
+    Plan plan_frame;                 // deferred-frame plan (mixing directions inside each tile)
     bool pershot_planned = false;
+    bool frame_planned = false;
     DeviceCircuit dev;
     DeviceCircuit dev_pershot;
+    DeviceCircuit dev_frame;
 };
 
 struct KSet {
@@ -189,6 +209,7 @@ void build_channel(const ptsbe_channel& in, HostChannel& c);
 void register_ops(Circuit& c, const ptsbe_op* ops, uint64_t n_ops, const double* custom, uint32_t n_custom);
 void build_device_ops(Circuit& c);
 Plan make_plan(const Circuit& c, int tile_bits, bool pershot);
+Plan make_frame_plan(const Circuit& c, int tile_bits);
 
 // ---------------------------------------------------------------------------------------------
 // Kernel launch interface (evolve.cu / sample.cu / pershot.cu).
@@ -203,6 +224,7 @@ struct EvolveArgs {
     const DevStage* stages;
     const DevGroup* groups;
     const uint32_t* hi;
+    const DevFrameStage* fstages;
     int n, tb, lb;
     // Kraus-set entries (whole set, on device)
     const uint32_t* ent_site;
