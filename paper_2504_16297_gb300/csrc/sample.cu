@@ -6,9 +6,11 @@
 // n <= 17: the whole FP64 CDF is held on chip. A thread-block cluster of CL = 2^(n-14) CTAs
 // (one CTA when n <= 14) owns one state: CTA r builds the prefix of amplitudes
 // [r*2^sb, (r+1)*2^sb) in its shared memory, the cluster exchanges slice totals over distributed
-// shared memory (DSMEM), and every shot binary-searches the slice it falls in, remote or local,
-// through DSMEM. Shots are written in order, so the output stream is coalesced. Heavy states are
-// split into several work items (shot ranges), each rebuilding the CDF.
+// shared memory (DSMEM), and every shot searches the slice it falls in, remote or local, through
+// DSMEM. A guide table per slice (the first index past each of 256 equal-probability cuts of the
+// slice) narrows each search to a few entries; each thread runs four searches interleaved, so
+// their dependent DSMEM loads overlap. Shots are written in order, so the output stream is
+// coalesced. Heavy states are split into several work items (shot ranges), each rebuilding the CDF.
 //
 // n > 17: the CDF is built in global workspace (block prefixes, block offsets) and searched there.
 //
@@ -137,20 +139,28 @@ __device__ double slice_total(const float2* __restrict__ amps, int cb, double* c
 }
 
 // smallest l in [0, 2^cb) with t < cdf[l] (the last index if none)
-__device__ __forceinline__ uint32_t search_slice(const double* cdf, int cb, int kb, long long tb) {
-    uint32_t lo = 0, hi = (1u << cb) - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (tb < dbits(cdf[paddr(mid, kb)])) hi = mid; else lo = mid + 1;
-    }
-    return lo;
+constexpr int kGuideBits = 12;
+constexpr int kGuide = 1 << kGuideBits;
+constexpr int kShotIlp = 4;
+
+// Float approximation (truncated mantissa) of a double in [0, 1) by integer operations; values
+// below the float range become 0. Only used to pick a guide bucket.
+__device__ __forceinline__ float d2f_trunc(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)(b >> 52);
+    if (e <= 896) return 0.0f;
+    return __uint_as_float(((uint32_t)(e - 896) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
 }
+
+// Guide threshold b of a CDF with total T: b * T * 2^-kGuideBits (the same value everywhere).
+__device__ __forceinline__ double guide_thr(uint32_t b, double T) { return ((double)b * T) * (1.0 / kGuide); }
 
 template <int CL>
 __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs a, const SampleItem* __restrict__ items, int sb) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[33];
     __shared__ double endv[CL];
+    __shared__ uint32_t guide[kGuide + 1];   // first state index with C > guide_thr(b, T)
     double* cdf = reinterpret_cast<double*>(smem);
     int rank = 0;
     if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
@@ -184,30 +194,88 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
         const double my_off = red[32];
         if (my_off != 0.0)
             for (uint32_t l = threadIdx.x; l < (1u << sb); l += nth) cdf[paddr(l, kb)] += my_off;
-        cluster.sync();
+        __syncthreads();
         T = endv[CL - 1];
     } else {
         T = local_total;
         if (threadIdx.x == 0) endv[0] = local_total;
         __syncthreads();
     }
-    for (uint64_t k = (uint64_t)rank * nth + threadIdx.x; k < nshots; k += (uint64_t)CL * nth) {
-        const uint64_t j = it.j0 + k;
-        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom,
-                                        (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        const double t = u53(x.x[0], x.x[1]) * T;
-        const long long tb = dbits(t);
-        int r = 0;
-        while (r < CL - 1 && !(tb < dbits(endv[r]))) ++r;
-        uint32_t idx;
-        if (!(tb < dbits(endv[r]))) {
-            idx = (1u << a.n) - 1;                 // rounding put t at or above T
-        } else {
-            const double* rc = cdf;
-            if constexpr (CL > 1) rc = cg::this_cluster().map_shared_rank(cdf, r);
-            idx = ((uint32_t)r << sb) | search_slice(rc, sb, kb, tb);
+    // Guide over the whole CDF: each CTA resolves the thresholds that fall in its slice (local
+    // search), then copies the others' entries over DSMEM, so every CTA holds the full table.
+    const uint32_t last = (1u << a.n) - 1;
+    const uint32_t slast = (1u << sb) - 1;
+    {
+        const long long st_b = rank == 0 ? 0ll : dbits(endv[rank - 1]), en_b = dbits(endv[rank]);
+        for (uint32_t b = threadIdx.x; b <= (uint32_t)kGuide; b += nth) {
+            const long long thr = dbits(guide_thr(b, T));
+            if (b == (uint32_t)kGuide || !(thr >= st_b && thr < en_b)) continue;
+            uint32_t lo = 0, hi = slast;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (thr < dbits(cdf[paddr(mid, kb)])) hi = mid; else lo = mid + 1;
+            }
+            guide[b] = ((uint32_t)rank << sb) | lo;
         }
-        a.bits[it.out0 + k] = idx;
+        if (threadIdx.x == 0) guide[kGuide] = last;
+    }
+    if constexpr (CL > 1) {
+        cg::cluster_group cluster = cg::this_cluster();
+        cluster.sync();
+        for (uint32_t b = threadIdx.x; b < (uint32_t)kGuide; b += nth) {
+            const long long thr = dbits(guide_thr(b, T));
+            int r = 0;
+            while (r < CL - 1 && !(thr < dbits(endv[r]))) ++r;
+            if (r != rank) guide[b] = cluster.map_shared_rank(guide, r)[b];
+        }
+    }
+    __syncthreads();
+    // Shots k, k + stride, ... : kShotIlp of them per thread at a time. The bucket of u is
+    // estimated in float (error far below one bucket), so the true bucket is b-1, b or b+1 and
+    // the answer lies in [guide[b-1], guide[b+2]]; it is resolved from the local guide when that
+    // range is one index, else by a search of those entries (through DSMEM for remote slices).
+    const uint64_t stride = (uint64_t)CL * nth;
+    for (uint64_t k0 = (uint64_t)rank * nth + threadIdx.x; k0 < nshots; k0 += kShotIlp * stride) {
+        uint32_t lo[kShotIlp], hi[kShotIlp];
+        long long tb[kShotIlp];
+#pragma unroll
+        for (int q = 0; q < kShotIlp; ++q) {
+            const uint64_t k = k0 + q * stride;
+            lo[q] = hi[q] = last;
+            tb[q] = 0;
+            if (k >= nshots) continue;
+            const uint64_t j = it.j0 + k;
+            const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom,
+                                            (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+            const double u = u53(x.x[0], x.x[1]);
+            const double t = u * T;
+            tb[q] = dbits(t);
+            if (!(tb[q] < dbits(T))) continue;          // rounding put t at or above T
+            int b = (int)(d2f_trunc(u) * (float)kGuide);
+            b = b < 0 ? 0 : (b > kGuide - 1 ? kGuide - 1 : b);
+            lo[q] = guide[b > 0 ? b - 1 : 0];
+            hi[q] = guide[b + 2 < kGuide ? b + 2 : kGuide];
+        }
+        while (true) {
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < kShotIlp; ++q) {
+                if (lo[q] < hi[q]) {
+                    any = true;
+                    const uint32_t mid = (lo[q] + hi[q]) >> 1;
+                    const int r = (int)(mid >> sb);
+                    const double* rc = cdf;
+                    if constexpr (CL > 1) rc = cg::this_cluster().map_shared_rank(cdf, r);
+                    if (tb[q] < dbits(rc[paddr(mid & slast, kb)])) hi[q] = mid; else lo[q] = mid + 1;
+                }
+            }
+            if (!any) break;
+        }
+#pragma unroll
+        for (int q = 0; q < kShotIlp; ++q) {
+            const uint64_t k = k0 + q * stride;
+            if (k < nshots) a.bits[it.out0 + k] = lo[q];
+        }
     }
     if constexpr (CL > 1) cg::this_cluster().sync();  // keep this CTA's slice alive for remote readers
 }
