@@ -173,7 +173,12 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
     const Step* Sp = P.S;
     const Factor* poolp = P.pool;
     if (tid < 32) {
-        copy_words(&B, &P.B, sizeof(Builder), tid, 32);   // warp 0, while the others bring the tile
+        // warp 0, while the others bring the tile: the builder state, and the factor pool when it
+        // fits shared memory (table builds read it over and over)
+        copy_words(&B, &P.B, sizeof(Builder), tid, 32);
+        __syncwarp();
+        if (B.npool <= (uint32_t)kMaxPool) copy_words(pool, P.pool, B.npool * (uint32_t)sizeof(Factor), tid, 32);
+        if (B.nsteps <= (uint32_t)kMaxSteps) copy_words(S, P.S, B.nsteps * (uint32_t)sizeof(Step), tid, 32);
     } else {
         const uint32_t t = tid - 32, nt = nthr - 32, nv = 1u << (tb - 1);
         float4* tile4 = reinterpret_cast<float4*>(tile);
@@ -198,6 +203,8 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
         }
     }
     __syncthreads();
+    if (B.npool <= (uint32_t)kMaxPool) poolp = pool;
+    if (B.nsteps <= (uint32_t)kMaxSteps) Sp = S;
     while (true) {
         const uint32_t ns = B.nsteps;
         for (uint32_t si = 0; si < ns; ++si) {
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
                 __syncthreads();
             }
             if (sp.kind == ST_MIX1) {
-                run_mix1(sp, tile, tabs, delta, tb, tau, tid, nthr);
+                run_mix1(sp, poolp, tile, tabs, delta, tb, tau, tid, nthr);
             } else if (sp.kind == ST_MIX2) {
                 run_mix2(sp, tile, tabs, delta, tb, tau, tid, nthr);
             } else if (sp.kind == ST_DIAG) {

@@ -68,12 +68,12 @@ struct Factor {
 
 struct Table {
     uint16_t fb, fe;                 // pool factors [fb, fe)
-    uint8_t d, pad[3];
+    uint8_t d, real, pad[2];         // real: every factor value is real (float entries, real products)
     uint16_t basis[kTabBits];        // index bit i = <basis[i], tile-local address>
 };
 
 struct Step {
-    uint8_t kind, ntab, ndir, pad0;
+    uint8_t kind, ntab, ndir, mreal;   // mreal bit i: the 2x2 of direction i and its folded factors are real
     uint8_t piv[kMaxDirs];           // MIX1: pivot bits of the coset enumeration (ascending); MIX2: pa, pb
     uint16_t dir[kMaxDirs];          // MIX: tile-local directions (MIX2: dir[0] first qubit, dir[1] second)
     uint16_t rin[kMaxDirs];          // MIX: tile parts of the rows of the operand qubits
@@ -81,6 +81,7 @@ struct Step {
     uint8_t cpar[kMaxDirs];          // MIX: <row, b>
     uint32_t lb0;                    // FINAL: R b (logical); STORE: tile part of b
     uint32_t npush, nframe;          // builder counters when emitted (grouping test)
+    uint16_t fold_b[kMaxDirs], fold_e[kMaxDirs];   // MIX1: pool factors folded into direction i
     Table tab[kMaxTabs];
     float2 m[16];                    // MIX1: 2x2 of direction i at m[4i..4i+3]; MIX2: 4x4 on 2 l_a + l_b
 };
@@ -233,6 +234,9 @@ PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor*
         }
         T.fe = (uint16_t)B.npool;
         T.d = (uint8_t)d;
+        T.real = 1;
+        for (uint32_t j = T.fb; j < T.fe; ++j)
+            for (int x = 0; x < 4; ++x) if (pool[j].f[x].y != 0.0f) T.real = 0;
         order_table(T, pool);
         ++st.ntab;
         used |= took;
@@ -348,22 +352,59 @@ PTSBE_HD void set_pivots(Step& st) {
     }
 }
 
+// Single-row factors that vary along u are folded into the mix of direction u: within a coset of
+// the pass they only depend on the coordinate along u, so they scale the 2x2's columns by values
+// computed once per coset. They go to the pool as [fb, fe) with c1 = tile part of the row.
+PTSBE_HD uint64_t fold_factors(Builder& B, const DevStage& stg, Factor* pool, uint64_t var, uint16_t& fb, uint16_t& fe) {
+    fb = (uint16_t)B.npool;
+    uint64_t folded = 0;
+    for (uint32_t j = 0; j < B.npend; ++j) {
+        if (!((var >> j) & 1u) || B.pend[j].r2 != 0) continue;
+        Factor& g = pool[B.npool++];
+        g = B.pend[j];
+        g.c1 = (uint16_t)tile_part(stg, g.r1);
+        g.c2 = 0;
+        g.r1o = outer_part(stg, g.r1);
+        g.r2o = 0;
+        folded |= 1ull << j;
+    }
+    fe = (uint16_t)B.npool;
+    return folded;
+}
+
+PTSBE_HD bool real_mix(const float2* m, const Factor* pool, uint32_t fb, uint32_t fe) {
+    bool r = m[0].y == 0.f && m[1].y == 0.f && m[2].y == 0.f && m[3].y == 0.f;
+    for (uint32_t j = fb; r && j < fe; ++j) r = pool[j].f[0].y == 0.f && pool[j].f[2].y == 0.f;
+    return r;
+}
+
 PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, int q, const float2* m) {
     const uint32_t u = B.col[q];
     const uint32_t n0 = B.nsteps;
-    Step& st = take_tables(B, stg, S, pool, varying(B, u, 0), true);
+    uint64_t var = varying(B, u, 0);
+    uint16_t fb, fe;
+    const uint64_t folded = fold_factors(B, stg, pool, var, fb, fe);
+    var = drop_pending(B, folded, var & ~folded);
+    Step& st = take_tables(B, stg, S, pool, var, true);
     const uint32_t ut = tile_part(stg, u);
     // Join the previous single-qubit pass when nothing changed the factors or the frame since it
-    // (its factors commute with the earlier mixes: they were pending and constant along them).
+    // (its factors commute with the earlier mixes: they were pending and constant along them), and
+    // no factor folded into its mixes varies along the new direction.
     if (B.nsteps == n0 && n0 > 0) {
         Step& pr = S[n0 - 1];
         bool ok = pr.kind == ST_MIX1 && pr.ndir < kMaxDirs && pr.npush == B.npush && pr.nframe == B.nframe &&
                   pr.ntab + st.ntab <= kMaxTabs;
-        for (int i = 0; ok && i < pr.ndir; ++i) ok = par(pr.rin[i] & ut) == 0;
+        for (int i = 0; ok && i < pr.ndir; ++i) {
+            ok = par(pr.rin[i] & ut) == 0;
+            for (uint32_t j = pr.fold_b[i]; ok && j < pr.fold_e[i]; ++j) ok = par(pool[j].r1 & u) == 0;
+        }
         if (ok) {
             for (int t = 0; t < st.ntab; ++t) pr.tab[pr.ntab + t] = st.tab[t];
             pr.ntab = (uint8_t)(pr.ntab + st.ntab);
             const int i = pr.ndir++;
+            pr.fold_b[i] = fb;
+            pr.fold_e[i] = fe;
+            if (real_mix(m, pool, fb, fe)) pr.mreal |= (uint8_t)(1u << i);
             pr.dir[i] = (uint16_t)ut;
             pr.rin[i] = (uint16_t)tile_part(stg, B.row[q]);
             pr.rout[i] = outer_part(stg, B.row[q]);
@@ -375,6 +416,9 @@ PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
     }
     st.kind = ST_MIX1;
     st.ndir = 1;
+    st.mreal = real_mix(m, pool, fb, fe) ? 1 : 0;
+    st.fold_b[0] = fb;
+    st.fold_e[0] = fe;
     st.dir[0] = (uint16_t)ut;
     st.rin[0] = (uint16_t)tile_part(stg, B.row[q]);
     st.rout[0] = outer_part(stg, B.row[q]);
@@ -391,6 +435,8 @@ PTSBE_HD void emit_mix2(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
     const uint32_t u = tile_part(stg, B.col[a]), v = tile_part(stg, B.col[b]);
     st.kind = ST_MIX2;
     st.ndir = 2;
+    st.mreal = 0;
+    for (int i = 0; i < kMaxDirs; ++i) st.fold_b[i] = st.fold_e[i] = 0;
     st.dir[0] = (uint16_t)u;
     st.dir[1] = (uint16_t)v;
     const int pa = low_bit(u);
@@ -619,12 +665,21 @@ PTSBE_HD void prepare_tables(const Step& st, const DevFrameStage& fs, const Fact
         const Table& T = st.tab[t];
         const uint32_t size = 1u << T.d;
         for (uint32_t idx = tid; idx < size; idx += nthr) {
-            float2 v = make_float2(1.f, 0.f);
-            for (uint32_t j = T.fb; j < T.fe; ++j) {
-                const Factor& f = pool[j];
-                v = fmul(v, f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))]);
+            if (T.real) {
+                float v = 1.f;
+                for (uint32_t j = T.fb; j < T.fe; ++j) {
+                    const Factor& f = pool[j];
+                    v *= f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))].x;
+                }
+                tabs[t * kTabSize + idx] = make_float2(v, 0.f);
+            } else {
+                float2 v = make_float2(1.f, 0.f);
+                for (uint32_t j = T.fb; j < T.fe; ++j) {
+                    const Factor& f = pool[j];
+                    v = fmul(v, f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))]);
+                }
+                tabs[t * kTabSize + idx] = v;
             }
-            tabs[t * kTabSize + idx] = v;
         }
     }
     const uint32_t nd = (uint32_t)st.ntab * kDeltaSlots;
@@ -633,7 +688,7 @@ PTSBE_HD void prepare_tables(const Step& st, const DevFrameStage& fs, const Fact
 }
 
 struct Lookup {
-    int ntab;
+    int ntab, real;                  // real bit t: table t holds real values
     uint32_t ix[kMaxTabs];
 };
 
@@ -642,13 +697,21 @@ PTSBE_HD float2 apply_tabs(float2 x, const Lookup& L, const float2* tabs, const 
     for (int t = 0; t < kMaxTabs; ++t)
         if (t < L.ntab) {
             const uint32_t i = slot < 0 ? L.ix[t] : (L.ix[t] ^ delta[t * kDeltaSlots + slot]);
-            x = fmul(x, tabs[t * kTabSize + i]);
+            if ((L.real >> t) & 1) {
+                const float r = reinterpret_cast<const float*>(tabs + t * kTabSize + i)[0];
+                x.x *= r;
+                x.y *= r;
+            } else {
+                x = fmul(x, tabs[t * kTabSize + i]);
+            }
         }
     return x;
 }
 
 PTSBE_HD void lookup_init(Lookup& L, const Step& st, uint32_t p) {
     L.ntab = st.ntab;
+    L.real = 0;
+    for (int t = 0; t < st.ntab; ++t) L.real |= st.tab[t].real << t;
 #pragma unroll
     for (int t = 0; t < kMaxTabs; ++t) L.ix[t] = t < L.ntab ? lin_idx(st.tab[t], p) : 0u;
 }
@@ -666,8 +729,8 @@ PTSBE_HD void lookup_step(Lookup& L, const uint32_t* delta, int j) {
 // (rows and columns of one frame), so each 2x2 acts on register pairs y, y | 1 << i with one
 // orientation per coset.
 template <int ND>
-PTSBE_HD void run_mix1_n(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
-                         uint32_t tid, uint32_t nthr) {
+PTSBE_HD void run_mix1_n(const Step& st, const Factor* pool, float2* s, const float2* tabs, const uint32_t* delta, int tb,
+                         uint32_t tau, uint32_t tid, uint32_t nthr) {
     constexpr int NA = 1 << ND;
     const uint32_t N = 1u << (tb - ND);
     if (tid >= N) return;
@@ -705,13 +768,36 @@ PTSBE_HD void run_mix1_n(const Step& st, float2* s, const float2* tabs, const ui
         for (int i = 0; i < ND; ++i) {
             const bool fl = (par(rin[i] & base) ^ c0[i]) != 0;
             const float2 a00 = st.m[4 * i], a01 = st.m[4 * i + 1], a10 = st.m[4 * i + 2], a11 = st.m[4 * i + 3];
-            const float2 g00 = fl ? a11 : a00, g01 = fl ? a10 : a01, g10 = fl ? a01 : a10, g11 = fl ? a00 : a11;
+            float2 g00 = fl ? a11 : a00, g01 = fl ? a10 : a01, g10 = fl ? a01 : a10, g11 = fl ? a00 : a11;
+            // folded factors: F0 on the half with y_i = 0, F1 on y_i = 1 (the matrix's columns)
+            const uint32_t fb = st.fold_b[i], fe = st.fold_e[i];
+            if (fb < fe) {
+                float2 F0 = make_float2(1.f, 0.f), F1 = make_float2(1.f, 0.f);
+                for (uint32_t j = fb; j < fe; ++j) {
+                    const Factor& f = pool[j];
+                    const uint32_t c = par(f.c1 & base) ^ par(f.r1o & tau);
+                    F0 = fmul(F0, f.f[2u * c]);
+                    F1 = fmul(F1, f.f[2u * (c ^ 1u)]);
+                }
+                g00 = fmul(g00, F0); g10 = fmul(g10, F0);
+                g01 = fmul(g01, F1); g11 = fmul(g11, F1);
+            }
+            if ((st.mreal >> i) & 1) {
 #pragma unroll
-            for (int y = 0; y < NA; ++y) {
-                if ((y >> i) & 1) continue;
-                const float2 a = v[y], b = v[y | (1 << i)];
-                v[y] = fmul2(g00, a, g01, b);
-                v[y | (1 << i)] = fmul2(g10, a, g11, b);
+                for (int y = 0; y < NA; ++y) {
+                    if ((y >> i) & 1) continue;
+                    const float2 a = v[y], b = v[y | (1 << i)];
+                    v[y] = make_float2(fmaf(g00.x, a.x, g01.x * b.x), fmaf(g00.x, a.y, g01.x * b.y));
+                    v[y | (1 << i)] = make_float2(fmaf(g10.x, a.x, g11.x * b.x), fmaf(g10.x, a.y, g11.x * b.y));
+                }
+            } else {
+#pragma unroll
+                for (int y = 0; y < NA; ++y) {
+                    if ((y >> i) & 1) continue;
+                    const float2 a = v[y], b = v[y | (1 << i)];
+                    v[y] = fmul2(g00, a, g01, b);
+                    v[y | (1 << i)] = fmul2(g10, a, g11, b);
+                }
             }
         }
 #pragma unroll
@@ -724,14 +810,14 @@ PTSBE_HD void run_mix1_n(const Step& st, float2* s, const float2* tabs, const ui
     }
 }
 
-PTSBE_HD void run_mix1(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
-                       uint32_t tid, uint32_t nthr) {
+PTSBE_HD void run_mix1(const Step& st, const Factor* pool, float2* s, const float2* tabs, const uint32_t* delta, int tb,
+                       uint32_t tau, uint32_t tid, uint32_t nthr) {
     static_assert(kMaxDirs == 4, "one instantiation per group size");
     switch (st.ndir) {
-    case 1: run_mix1_n<1>(st, s, tabs, delta, tb, tau, tid, nthr); break;
-    case 2: run_mix1_n<2>(st, s, tabs, delta, tb, tau, tid, nthr); break;
-    case 3: run_mix1_n<3>(st, s, tabs, delta, tb, tau, tid, nthr); break;
-    default: run_mix1_n<4>(st, s, tabs, delta, tb, tau, tid, nthr); break;
+    case 1: run_mix1_n<1>(st, pool, s, tabs, delta, tb, tau, tid, nthr); break;
+    case 2: run_mix1_n<2>(st, pool, s, tabs, delta, tb, tau, tid, nthr); break;
+    case 3: run_mix1_n<3>(st, pool, s, tabs, delta, tb, tau, tid, nthr); break;
+    default: run_mix1_n<4>(st, pool, s, tabs, delta, tb, tau, tid, nthr); break;
     }
 }
 
