@@ -482,11 +482,18 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());
         }
         const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
+        // When the last frame stage only reorders (no ops), the norm is known after the stage
+        // before it: that stage's stores leave tile norms, a reduce turns them into scales, and
+        // the last stage writes the normalised state (no separate renormalisation pass).
+        const bool early_norm = frame && ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end &&
+                                launches[J - 2].second == count;
         for (uint32_t j = 0; j < J; ++j) {
             const auto& L = launches[j];
             if (L.second == 0) continue;
             A.states = out_buf(j);
             A.states_in = j > 0 ? out_buf(j - 1) : out_buf(j);
+            A.store_norm = early_norm && j + 2 == J;
+            A.scale_in = early_norm && j + 1 == J ? d_scale : nullptr;
             // algorithmic bytes: read (unless started from |0>) and write of each set's state
             double bytes = 0;
             for (size_t t = L.first; t < L.first + L.second; ++t)
@@ -494,9 +501,13 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
                 launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
             });
+            if (A.store_norm)
+                ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 0.0, [&] { launch_evolve_reduce(A, count, d_scale, ctx->stream); });
         }
         A.states = user;
-        if (ob > 0)
+        A.store_norm = 0;
+        A.scale_in = nullptr;
+        if (ob > 0 && !early_norm)
             ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
     });
 }

@@ -220,7 +220,13 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
             } else if (sp.kind == ST_DIAG) {
                 run_diag(sp, tile, tabs, delta, tb, tid, nthr);
             } else if (sp.kind == ST_STORE) {
-                run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr);
+                const double part = run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr);
+                if (a.store_norm) {
+                    const double tot = cta_sum(part, red);
+                    if (tid == 0) a.part[((size_t)node << ob) + tau] = tot;
+                }
+            } else if (a.scale_in) {
+                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, a.scale_in[node], false, tid, nthr);
             } else if (ob == 0) {
                 const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, nullptr, 1.0f, true, tid, nthr), red);
                 const double w = a.wmix[node] * part;
@@ -732,6 +738,13 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }
+}
+
+void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s) {
+    if (count == 0) return;
+    k_evolve_reduce<<<count, 256, 0, s>>>(a, d_scale);
+    PTSBE_CUDA(cudaGetLastError());
+    count_launch();
 }
 
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s) {

@@ -902,10 +902,12 @@ PTSBE_HD uint64_t outer_offset(const DevStage& stg, int ob, uint32_t tau) {
 }
 
 // Intermediate store: tile-local d of tile tau ^ b_out receives D(x) s[d ^ b_in] (x the source).
-PTSBE_HD void run_store(const Step& st, const DevStage& stg, const float2* s, const float2* tabs, const uint32_t* delta,
-                        int tb, int lb, int ob, const uint32_t* hi, uint32_t tau, float2* dst, uint32_t tid, uint32_t nthr) {
+// Returns this thread's part of the squared norm of what it wrote.
+PTSBE_HD double run_store(const Step& st, const DevStage& stg, const float2* s, const float2* tabs, const uint32_t* delta,
+                          int tb, int lb, int ob, const uint32_t* hi, uint32_t tau, float2* dst, uint32_t tid, uint32_t nthr) {
     const uint32_t N = 1u << (tb - 1);
-    if (tid >= N) return;
+    if (tid >= N) return 0.0;
+    float part = 0.f;
     const uint32_t K = N > nthr ? N / nthr : 1u;
     const uint32_t bin = st.lb0;
     const uint64_t outer = outer_offset(stg, ob, tau ^ st.rout[0]);
@@ -920,8 +922,10 @@ PTSBE_HD void run_store(const Step& st, const DevStage& stg, const float2* s, co
         }
         float2 a0 = s[d ^ bin], a1 = s[(d ^ bin) ^ 1u];
         if (L.ntab) { a0 = apply_tabs(a0, L, tabs, delta, -1); a1 = apply_tabs(a1, L, tabs, delta, 15); }
+        part += fmaf(a0.x, a0.x, a0.y * a0.y) + fmaf(a1.x, a1.x, a1.y * a1.y);
         *reinterpret_cast<float4*>(dst + gaddr(d, lb, hi, outer)) = make_float4(a0.x, a0.y, a1.x, a1.y);
     }
+    return (double)part;
 }
 
 // Last stage: writes the logical amplitudes of this tile, times `scale`, to dst (when not null) and

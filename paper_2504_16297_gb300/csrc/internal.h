@@ -247,12 +247,15 @@ struct EvolveArgs {
     double* weights;
     uint8_t* status;
     void* frame_progs;               // frame kernel: one program per node of a launch
+    int store_norm;                  // frame kernel: stage-end stores also leave tile norm partials in part
+    const float* scale_in;           // frame kernel: the last stage writes psi * scale_in[node] (norm known)
 };
 
 // kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
                          cudaStream_t s, int kernel = 0);
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
+void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 size_t evolve_frame_program_bytes();   // workspace per node of a frame-kernel launch
 
 struct SampleItem {                  // one cluster's share of one state's shots

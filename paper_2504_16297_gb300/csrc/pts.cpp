@@ -153,18 +153,18 @@ void pts_literal(const Circuit& c, uint64_t ns, uint64_t seed, std::vector<std::
 // therefore pops sets exactly in sorted order.
 struct Opt { uint32_t site; uint8_t k; double r; };
 
+// Nodes live in flat arenas: options and site-sorted entries of node i are [off, off + len) of
+// opt_ and ent_ (entries packed as site << 8 | k, so packed order is the canonical entry order).
+// Heap entries carry the key, so comparisons only touch the arenas on ties.
 struct Node {
     double key;          // product of the ratios of opts, in option order
     double prefix;       // product without the last option
-    std::vector<uint32_t> opts;
-    List canon;          // site-sorted entries
+    uint32_t off, len;
 };
 
-struct NodeOrder {
-    bool operator()(const Node* a, const Node* b) const {  // true if a comes AFTER b
-        if (a->key != b->key) return a->key < b->key;
-        return canon_less(b->canon, a->canon);
-    }
+struct HeapItem {
+    double key;
+    uint32_t node;
 };
 
 class BestFirst {
@@ -181,60 +181,90 @@ class BestFirst {
             if (a.site != b.site) return a.site < b.site;
             return a.k < b.k;
         });
-        Node* root = alloc();
-        root->key = 1.0; root->prefix = 1.0;
-        heap_.push(root);
+        nodes_.push_back({1.0, 1.0, 0, 0});
+        push({1.0, 0});
     }
 
     // Pops the next set in order; false when exhausted.
     bool next(double& key, List& canon) {
         if (heap_.empty()) return false;
-        Node* nd = heap_.top();
-        heap_.pop();
-        key = nd->key;
-        canon = nd->canon;
-        expand(nd);
+        const HeapItem top = heap_.front();
+        std::pop_heap(heap_.begin(), heap_.end(), after_);
+        heap_.pop_back();
+        const Node nd = nodes_[top.node];
+        key = nd.key;
+        canon.clear();
+        for (uint32_t i = 0; i < nd.len; ++i) {
+            const uint64_t e = ent_[nd.off + i];
+            canon.push_back({(uint32_t)(e >> 8), (uint8_t)(e & 0xFF)});
+        }
+        expand(top.node);
         return true;
     }
 
   private:
-    Node* alloc() { pool_.emplace_back(new Node()); return pool_.back().get(); }
-
-    bool site_used(const std::vector<uint32_t>& opts, size_t upto, uint32_t site) const {
-        for (size_t i = 0; i < upto; ++i) if (opts_[opts[i]].site == site) return true;
+    struct After {   // true if a comes after b (max-heap on key, then canonical ascending)
+        const BestFirst* bf;
+        bool operator()(const HeapItem& a, const HeapItem& b) const {
+            if (a.key != b.key) return a.key < b.key;
+            const Node& na = bf->nodes_[a.node];
+            const Node& nb = bf->nodes_[b.node];
+            return std::lexicographical_compare(bf->ent_.begin() + nb.off, bf->ent_.begin() + nb.off + nb.len,
+                                                bf->ent_.begin() + na.off, bf->ent_.begin() + na.off + na.len);
+        }
+    };
+    void push(HeapItem h) {
+        heap_.push_back(h);
+        std::push_heap(heap_.begin(), heap_.end(), after_);
+    }
+    bool site_used(uint32_t node, size_t upto, uint32_t site) const {
+        const Node& nd = nodes_[node];
+        for (size_t i = 0; i < upto; ++i) if (opts_[opt_[nd.off + i]].site == site) return true;
         return false;
     }
-    // Smallest option index > after whose site is not among opts[0..upto).
-    int64_t next_valid(const std::vector<uint32_t>& opts, size_t upto, int64_t after) const {
+    // Smallest option index > after whose site is not among the first `upto` options of node.
+    int64_t next_valid(uint32_t node, size_t upto, int64_t after) const {
         for (int64_t j = after + 1; j < (int64_t)opts_.size(); ++j)
-            if (!site_used(opts, upto, opts_[j].site)) return j;
+            if (!site_used(node, upto, opts_[j].site)) return j;
         return -1;
     }
-    void push_child(const std::vector<uint32_t>& base, size_t keep, double prefix, uint32_t j) {
-        Node* ch = alloc();
-        ch->opts.assign(base.begin(), base.begin() + keep);
-        ch->opts.push_back(j);
-        ch->prefix = prefix;
-        ch->key = prefix * opts_[j].r;
-        for (uint32_t o : ch->opts) ch->canon.push_back({opts_[o].site, opts_[o].k});
-        std::sort(ch->canon.begin(), ch->canon.end());
-        heap_.push(ch);
+    void push_child(uint32_t base, size_t keep, double prefix, uint32_t j) {
+        const uint32_t off = (uint32_t)opt_.size();
+        const uint32_t boff = nodes_[base].off;
+        for (size_t i = 0; i < keep; ++i) {
+            const uint32_t o = opt_[boff + i];
+            opt_.push_back(o);
+        }
+        opt_.push_back(j);
+        ent_.resize(opt_.size());
+        for (size_t i = 0; i <= keep; ++i) {
+            const Opt& o = opts_[opt_[off + i]];
+            ent_[off + i] = ((uint64_t)o.site << 8) | o.k;
+        }
+        std::sort(ent_.begin() + off, ent_.begin() + off + keep + 1);
+        const uint32_t id = (uint32_t)nodes_.size();
+        nodes_.push_back({prefix * opts_[j].r, prefix, off, (uint32_t)(keep + 1)});
+        push({nodes_[id].key, id});
     }
-    void expand(const Node* nd) {
-        const auto& o = nd->opts;
-        const int64_t last = o.empty() ? -1 : (int64_t)o.back();
-        int64_t j = next_valid(o, o.size(), last);
-        if (j >= 0) push_child(o, o.size(), nd->key, (uint32_t)j);
-        if (!o.empty()) {
-            j = next_valid(o, o.size() - 1, last);
-            if (j >= 0) push_child(o, o.size() - 1, nd->prefix, (uint32_t)j);
+    void expand(uint32_t node) {
+        const uint32_t len = nodes_[node].len;
+        const int64_t last = len == 0 ? -1 : (int64_t)opt_[nodes_[node].off + len - 1];
+        const double key = nodes_[node].key, prefix = nodes_[node].prefix;
+        int64_t j = next_valid(node, len, last);
+        if (j >= 0) push_child(node, len, key, (uint32_t)j);
+        if (len > 0) {
+            j = next_valid(node, len - 1, last);
+            if (j >= 0) push_child(node, len - 1, prefix, (uint32_t)j);
         }
     }
 
     const Circuit& c_;
     std::vector<Opt> opts_;
-    std::vector<std::unique_ptr<Node>> pool_;
-    std::priority_queue<Node*, std::vector<Node*>, NodeOrder> heap_;
+    std::vector<Node> nodes_;
+    std::vector<uint32_t> opt_;
+    std::vector<uint64_t> ent_;
+    std::vector<HeapItem> heap_;
+    After after_{this};
 };
 
 }  // namespace
@@ -257,11 +287,23 @@ void apportion_counts(const std::vector<uint64_t>& c, uint64_t M, std::vector<ui
     if (n == 0 || N == 0) return;
     std::vector<std::pair<uint64_t, uint32_t>> rem(n);
     uint64_t used = 0;
-    for (size_t i = 0; i < n; ++i) {
-        const unsigned __int128 p = (unsigned __int128)M * c[i];
-        out[i] = (uint64_t)(p / N);
-        rem[i] = {(uint64_t)(p % N), (uint32_t)i};
-        used += out[i];
+    uint64_t cmax = 0;
+    for (uint64_t x : c) cmax = std::max(cmax, x);
+    if (N <= UINT64_MAX && (cmax == 0 || M <= UINT64_MAX / cmax)) {   // the same quotients in 64 bits
+        const uint64_t N64 = (uint64_t)N;
+        for (size_t i = 0; i < n; ++i) {
+            const uint64_t p = M * c[i];
+            out[i] = p / N64;
+            rem[i] = {p % N64, (uint32_t)i};
+            used += out[i];
+        }
+    } else {
+        for (size_t i = 0; i < n; ++i) {
+            const unsigned __int128 p = (unsigned __int128)M * c[i];
+            out[i] = (uint64_t)(p / N);
+            rem[i] = {(uint64_t)(p % N), (uint32_t)i};
+            used += out[i];
+        }
     }
     std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
         return a.first != b.first ? a.first > b.first : a.second < b.second;
