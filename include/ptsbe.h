@@ -222,9 +222,10 @@ PTSBE_API int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id);
 /* ---------------------------------------------------------------------------------------- */
 
 enum {
-    /* Prefix reuse: a set whose (site, k) list extends another set of the same call starts from
-     * that set's state at the first differing site instead of from |0...0>. The parent writes
-     * its state into the child's output slot when it reaches the branch site. */
+    /* Prefix reuse: a set whose (site, k) list extends another set of the same call skips the
+     * tile stages before the one holding its first extra site, starting there from the other
+     * set's input of that stage instead of from |0...0>. Stages alternate between d_states and a
+     * library workspace of the same size. */
     PTSBE_EVOLVE_PREFIX_REUSE = 1u
 };
 
@@ -318,7 +319,7 @@ PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
 /* Kernel classes of the timing counters. */
 enum {
     PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
-    PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* renormalisation pass of ptsbe_evolve_batch (n > 14)      */
+    PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* norm reduction / renormalisation of ptsbe_evolve_batch   */
     PTSBE_TIMER_SAMPLE = 2,           /* ptsbe_sample_shots                                       */
     PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
     PTSBE_TIMER_CLASSES = 4
@@ -326,7 +327,7 @@ enum {
 
 /* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and
  * its algorithmic bytes are added up per kernel class (state bytes read and written by a pass,
- * checkpoint writes, 4 bytes per shot ...). Adds two event records per launch. */
+ * 4 bytes per shot ...). Adds two event records per launch. */
 PTSBE_API int ptsbe_set_timing(ptsbe_ctx* ctx, int enable);
 
 /* Waits for the timed launches and returns, for one kernel class, the summed event time in

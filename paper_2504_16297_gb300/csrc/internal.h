@@ -58,8 +58,8 @@ struct DevOp {
     uint32_t site;   // DOP_NOISE: site index
     uint32_t ch;     // DOP_NOISE: channel index
     // A gate fused with the "no error" Kraus operators of the noise sites right after it on its
-    // own qubits. Used when the state's set has no entry among those sites and no prefix-reuse
-    // child branches there; otherwise the ops run one by one.
+    // own qubits. Used when the state's set has no entry among those sites; otherwise the ops run
+    // one by one.
     uint8_t fkind;   // DOP_NOP when nothing is fused (kind of the fused operator otherwise)
     uint8_t fperm;   // DOP_M2 permutation
     uint8_t fsep;    // DOP_M2: 1 when d[2 l_a + l_b] = alpha[l_a] beta[l_b]; fmat[4..7] = alpha, beta
