@@ -203,6 +203,26 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 # GPU leg
 # ----------------------------------------------------------------------------------------------
+# Ranks (torchrun, one GPU each): weak scaling. Every rank prepares the same top-K Kraus sets and
+# draws its own M shots (shot seed = base + rank), so ranks exchange no data; only the timing uses
+# a barrier and a max over ranks, and the job's shots are world * M.
+# ----------------------------------------------------------------------------------------------
+def rank_seed(base: int, rank: int) -> int:
+    return base + rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, shots_per_rank: int, ms_per_step: float) -> float:
+    return world * shots_per_rank / (ms_per_step / 1e3)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -227,7 +247,7 @@ def main():
     circ = cfg["circuit"]
     n = circ.n_qubits
     K, M = args.k, args.shots
-    seed = cfg["seed"] + rank          # weak scaling: every rank collects its own 1e8 shots
+    seed = rank_seed(cfg["seed"], rank)   # weak scaling: every rank collects its own 1e8 shots
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     P = Ptsbe(device=local, stream=stream.cuda_stream)
@@ -282,10 +302,7 @@ def main():
                 if kl:
                     kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
             P.set_timing(False)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), launches, kern
+        return max_over_ranks(ms, dist, dev), launches, kern
 
     for _ in range(args.warmup):
         step(False)
@@ -318,8 +335,8 @@ def main():
                    "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot"}
 
     ms_step = ms / args.steps
-    value = world * M / (ms_step / 1e3)
-    e2e_value = world * M / (ms_e2e / steps_e2e / 1e3)
+    value = job_throughput(world, M, ms_step)
+    e2e_value = job_throughput(world, M, ms_e2e / steps_e2e)
     peak, peak_kind = peaks()
     dom = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
     roof = None

@@ -769,39 +769,50 @@ Plan make_frame_plan(const Circuit& c, int tile_bits) {
     }
     const uint32_t low = (1u << P.lb) - 1u;
     uint32_t U = low, begin = 0;
+    // Ends the stage [begin, e) with a store in logical order (the tile then also holds the images
+    // of the low logical bits, else one more op-free stage does that store); the frame restarts
+    // at the identity.
+    auto close_logical = [&](uint32_t e) {
+        uint32_t F = 0;
+        for (int k = 0; k < P.lb; ++k) F |= col[k];
+        if (__builtin_popcount(U | F) <= P.tb) {
+            close_frame_stage(P, c, U | F, begin, e, entry, true, P.lb);
+        } else {
+            close_frame_stage(P, c, U, begin, e, entry, false, 0);
+            int lbf = P.lb;
+            while (lbf > 1) {
+                uint32_t G = 0;
+                for (int k = 0; k < lbf; ++k) G |= col[k];
+                if (__builtin_popcount(low | G) <= P.tb) break;
+                --lbf;
+            }
+            uint32_t G = 0;
+            for (int k = 0; k < lbf; ++k) G |= col[k];
+            if (__builtin_popcount(low | G) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "frame plan: output bit wider than a tile");
+            close_frame_stage(P, c, low | G, e, e, col, true, lbf);
+        }
+        for (int q = 0; q < n; ++q) col[q] = entry[q] = 1u << q;
+    };
     for (size_t i = 0; i < nops; ++i) {
-        const uint32_t d = frame_dirs(c, i, col);
+        uint32_t d = frame_dirs(c, i, col);
         if (__builtin_popcount(U | d) > P.tb) {
-            if (__builtin_popcount(low | d) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "frame plan: mixing directions wider than a tile");
-            close_frame_stage(P, c, U, begin, (uint32_t)i, entry, false, 0);
+            if (__builtin_popcount(low | d) > P.tb) {
+                // the permutation spread this operator's directions wider than a tile: go back
+                // to logical order (directions are single bits again)
+                close_logical((uint32_t)i);
+                d = frame_dirs(c, i, col);
+            } else {
+                close_frame_stage(P, c, U, begin, (uint32_t)i, entry, false, 0);
+                for (int q = 0; q < n; ++q) entry[q] = col[q];
+            }
             begin = (uint32_t)i;
             U = low | d;
-            for (int q = 0; q < n; ++q) entry[q] = col[q];
         } else {
             U |= d;
         }
         frame_linear(c, i, col);
     }
-    // the last tile also holds the images of the low logical bits (coalesced output)
-    uint32_t F = 0;
-    for (int k = 0; k < P.lb; ++k) F |= col[k];
-    if (__builtin_popcount(U | F) <= P.tb) {
-        close_frame_stage(P, c, U | F, begin, (uint32_t)nops, entry, true, P.lb);
-        return P;
-    }
-    close_frame_stage(P, c, U, begin, (uint32_t)nops, entry, false, 0);
-    // one more stage without ops that writes logical order
-    int lbf = P.lb;
-    while (lbf > 1) {
-        uint32_t G = 0;
-        for (int k = 0; k < lbf; ++k) G |= col[k];
-        if (__builtin_popcount(low | G) <= P.tb) break;
-        --lbf;
-    }
-    uint32_t G = 0;
-    for (int k = 0; k < lbf; ++k) G |= col[k];
-    if (__builtin_popcount(low | G) > P.tb) fail(PTSBE_ERR_UNSUPPORTED, "frame plan: output bit wider than a tile");
-    close_frame_stage(P, c, low | G, (uint32_t)nops, (uint32_t)nops, col, true, lbf);
+    close_logical((uint32_t)nops);
     return P;
 }
 

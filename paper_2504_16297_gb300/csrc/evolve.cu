@@ -225,6 +225,8 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
                     const double tot = cta_sum(part, red);
                     if (tid == 0) a.part[((size_t)node << ob) + tau] = tot;
                 }
+            } else if (!last) {       // logical order before a frame restart
+                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, false, tid, nthr);
             } else if (a.scale_in) {
                 run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, a.scale_in[node], false, tid, nthr);
             } else if (ob == 0) {
@@ -249,7 +251,6 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
         poolp = pool;
         __syncthreads();
     }
-    (void)last;
 }
 
 // Per node: total squared norm from the tile partials (fixed order), weight, null flag, scale.

@@ -116,13 +116,15 @@ struct DevGroup {
 struct DevFrameStage {
     uint32_t col[kMaxQubits];        // A at the stage start: global image of logical bit q
     uint32_t row[kMaxQubits];        // rows of A^-1: logical bit q = <row[q], global index>
-    // Last stage (logical output order): tile-local index t holds logical l = l0 ^ sum_k t_k w[k]
-    // at tile-local address sum_k t_k m[k]; l0 = R b ^ (xor of ox[i] over the set outer bits i of
-    // the tile index); w[k] = e_k for k < lbf, so runs of 2^lbf amplitudes stay contiguous.
+    // Stages that end in logical order (the last one, and any stage after which the frame restarts
+    // at the identity because a permutation spread a mixing direction wider than a tile): tile-local
+    // index t holds logical l = l0 ^ sum_k t_k w[k] at tile-local address sum_k t_k m[k];
+    // l0 = R b ^ (xor of ox[i] over the set outer bits i of the tile index); w[k] = e_k for k < lbf,
+    // so runs of 2^lbf amplitudes stay contiguous.
     uint32_t w[kTileMax];
     uint16_t m[kTileMax];
     uint32_t ox[kMaxQubits];
-    uint32_t last, lbf;
+    uint32_t last, lbf;              // last: the stage ends in logical order
 };
 
 struct Plan {
