@@ -102,6 +102,68 @@ struct ptsbe_ctx {
         }
     }
 
+    // Device tables of circuits and Kraus sets live in a library memory pool and are allocated and
+    // freed in stream order, so releasing them does not wait for the device. Host-to-device copies
+    // go through recycled pinned staging slots: a copy from pageable memory would first wait for
+    // every earlier launch on the stream, and the host could not run ahead of the device.
+    cudaMemPool_t pool = nullptr;
+    struct Slot {
+        unsigned char* p = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;     // recorded after the slot's last copy
+        bool used = false;
+    };
+    static constexpr size_t kSlots = 128;
+    Slot slots[kSlots];
+    size_t next_slot = 0;
+
+    void* dalloc(size_t bytes) {
+        void* p = nullptr;
+        const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "device table allocation failed"); }
+        return p;
+    }
+    void dfree(void* p) {
+        if (p) PTSBE_CUDA(cudaFreeAsync(p, stream));
+    }
+    // Stream-ordered copy of `bytes` host bytes to dst through the oldest staging slot (its
+    // previous copy was issued kSlots copies ago; waiting for it is normally immediate).
+    void h2d(void* dst, const void* src, size_t bytes) {
+        if (!bytes) return;
+        Slot& sl = slots[next_slot];
+        next_slot = (next_slot + 1) % kSlots;
+        if (sl.used) PTSBE_CUDA(cudaEventSynchronize(sl.ev));
+        if (sl.cap < bytes) {
+            if (sl.p) PTSBE_CUDA(cudaFreeHost(sl.p));
+            sl.p = nullptr;
+            size_t cap = 64 * 1024;
+            while (cap < bytes) cap *= 2;
+            const cudaError_t e = cudaHostAlloc((void**)&sl.p, cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) { (void)cudaGetLastError(); sl.p = nullptr; sl.cap = 0; fail(PTSBE_ERR_OOM, "pinned staging allocation failed"); }
+            sl.cap = cap;
+        }
+        if (!sl.ev) PTSBE_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
+        std::memcpy(sl.p, src, bytes);
+        PTSBE_CUDA(cudaMemcpyAsync(dst, sl.p, bytes, cudaMemcpyHostToDevice, stream));
+        PTSBE_CUDA(cudaEventRecord(sl.ev, stream));
+        sl.used = true;
+        count_h2d(bytes);
+    }
+    template <class T>
+    T* upload(const std::vector<T>& v) {
+        if (v.empty()) return nullptr;
+        T* p = (T*)dalloc(v.size() * sizeof(T));
+        h2d(p, v.data(), v.size() * sizeof(T));
+        return p;
+    }
+    void free_staging() {
+        for (Slot& sl : slots) {
+            if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.p) cudaFreeHost(sl.p);
+            sl = Slot{};
+        }
+    }
+
     bool has_device() const { return device >= 0; }
     void need_device() const {
         if (!has_device()) fail(PTSBE_ERR_NO_DEVICE, "device entry point on a host-only context");
@@ -154,33 +216,23 @@ int guarded(ptsbe_ctx* ctx, F&& f) {
     }
 }
 
-template <class T>
-T* dev_upload(const std::vector<T>& v) {
-    if (v.empty()) return nullptr;
-    T* p = nullptr;
-    const cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
-    if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "device table allocation failed"); }
-    PTSBE_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    count_h2d(v.size() * sizeof(T));
-    return p;
-}
-
-void free_device_circuit(DeviceCircuit& d) {
-    cudaFree(d.ops); cudaFree(d.micro); cudaFree(d.mats); cudaFree(d.chans);
-    cudaFree(d.site_op); cudaFree(d.stages); cudaFree(d.groups); cudaFree(d.hi); cudaFree(d.fstages);
+void free_device_circuit(ptsbe_ctx* ctx, DeviceCircuit& d) {
+    for (void* p : {(void*)d.ops, (void*)d.micro, (void*)d.mats, (void*)d.chans, (void*)d.site_op, (void*)d.stages,
+                    (void*)d.groups, (void*)d.hi, (void*)d.fstages})
+        ctx->dfree(p);
     d = DeviceCircuit{};
 }
 
-void upload_circuit(const Circuit& c, const Plan& P, DeviceCircuit& d) {
-    d.ops = dev_upload(c.dops);
-    d.micro = dev_upload(c.dmicro);
-    d.mats = dev_upload(c.dmats);
-    d.chans = dev_upload(c.dchans);
-    d.site_op = dev_upload(c.site_op);
-    d.stages = dev_upload(P.stages);
-    d.groups = dev_upload(P.groups);
-    d.hi = dev_upload(P.hi);
-    d.fstages = dev_upload(P.fstages);
+void upload_circuit(ptsbe_ctx* ctx, const Circuit& c, const Plan& P, DeviceCircuit& d) {
+    d.ops = ctx->upload(c.dops);
+    d.micro = ctx->upload(c.dmicro);
+    d.mats = ctx->upload(c.dmats);
+    d.chans = ctx->upload(c.dchans);
+    d.site_op = ctx->upload(c.site_op);
+    d.stages = ctx->upload(P.stages);
+    d.groups = ctx->upload(P.groups);
+    d.hi = ctx->upload(P.hi);
+    d.fstages = ctx->upload(P.fstages);
 }
 
 // Builds a blob of aligned arrays on the host and returns the device pointers after one upload.
@@ -196,10 +248,10 @@ struct Blob {
     }
 };
 
-void ensure_set_on_device(KSet& s) {
+void ensure_set_on_device(ptsbe_ctx* ctx, KSet& s) {
     if (s.d_site || s.site.empty()) return;
-    s.d_site = dev_upload(s.site);
-    s.d_k = dev_upload(s.k);
+    s.d_site = ctx->upload(s.site);
+    s.d_k = ctx->upload(s.k);
 }
 
 }  // namespace
@@ -228,6 +280,16 @@ int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
             (void)cudaGetLastError();
             return PTSBE_ERR_CUDA;
         }
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        const uint64_t keep = UINT64_MAX;   // freed blocks stay in the pool for the next call
+        if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PTSBE_ERR_CUDA;
+        }
     }
     *out = ctx.release();
     return PTSBE_OK;
@@ -239,10 +301,13 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
         for (auto& kv : ctx->circuits) {
-            free_device_circuit(kv.second->dev); free_device_circuit(kv.second->dev_pershot);
-            free_device_circuit(kv.second->dev_frame);
+            free_device_circuit(ctx, kv.second->dev); free_device_circuit(ctx, kv.second->dev_pershot);
+            free_device_circuit(ctx, kv.second->dev_frame);
         }
-        for (auto& kv : ctx->sets) { cudaFree(kv.second->d_site); cudaFree(kv.second->d_k); }
+        for (auto& kv : ctx->sets) { ctx->dfree(kv.second->d_site); ctx->dfree(kv.second->d_k); }
+        cudaStreamSynchronize(ctx->stream);
+        ctx->free_staging();
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
         ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong);
@@ -283,11 +348,7 @@ int ptsbe_register_circuit(ptsbe_ctx* ctx, uint32_t n_qubits, const ptsbe_op* op
         for (uint32_t j = 0; j < n_channels; ++j) build_channel(channels[j], c->ch[j]);
         register_ops(*c, ops, n_ops, custom_gates, n_custom);
         build_device_ops(*c);
-        c->plan = make_plan(*c, kTileMax, false);
-        if (ctx->has_device()) {
-            ctx->use_device();
-            upload_circuit(*c, c->plan, c->dev);
-        }
+        c->plan = make_plan(*c, kTileMax, false);   // device tables uploaded by the first call that needs them
         const uint32_t id = ctx->next_circuit++;
         ctx->circuits[id] = std::move(c);
         *circuit_id = id;
@@ -308,10 +369,9 @@ int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
         Circuit& c = ctx->circuit(circuit_id);
         if (ctx->has_device()) {
             ctx->use_device();
-            PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
-            free_device_circuit(c.dev);
-            free_device_circuit(c.dev_pershot);
-            free_device_circuit(c.dev_frame);
+            free_device_circuit(ctx, c.dev);            // stream-ordered: after the launches that use them
+            free_device_circuit(ctx, c.dev_pershot);
+            free_device_circuit(ctx, c.dev_frame);
         }
         ctx->circuits.erase(circuit_id);
     });
@@ -355,8 +415,8 @@ int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id) {
         KSet& s = ctx->set(set_id);
         if (ctx->has_device() && s.d_site) {
             ctx->use_device();
-            PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
-            cudaFree(s.d_site); cudaFree(s.d_k);
+            ctx->dfree(s.d_site);                        // stream-ordered: after the launches that use them
+            ctx->dfree(s.d_k);
         }
         ctx->sets.erase(set_id);
     });
@@ -374,13 +434,14 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
         if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
         ctx->use_device();
-        ensure_set_on_device(s);
+        ensure_set_on_device(ctx, s);
         const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
         if (frame && !c.frame_planned) {
             c.plan_frame = make_frame_plan(c, kTileMax);
-            upload_circuit(c, c.plan_frame, c.dev_frame);
+            upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
             c.frame_planned = true;
         }
+        if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
         const Plan& P = frame ? c.plan_frame : c.plan;
         const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
         const uint32_t S = (uint32_t)c.site_op.size();
@@ -450,8 +511,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         const size_t o_src = blob.add(src), o_fresh = blob.add(fresh);
         const size_t o_wmix = blob.add(wmix), o_q = blob.add(qa), o_lists = blob.add(lists);
         unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
-        PTSBE_CUDA(cudaMemcpyAsync(dblob, ctx->host_blob.data(), ctx->host_blob.size(), cudaMemcpyHostToDevice, ctx->stream));
-        count_h2d(ctx->host_blob.size());
+        ctx->h2d(dblob, ctx->host_blob.data(), ctx->host_blob.size());
 
         EvolveArgs A{};
         A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
@@ -556,8 +616,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         if (nl + nh) {
             light.insert(light.end(), items.begin(), items.end());
             SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
-            PTSBE_CUDA(cudaMemcpyAsync(d_items, light.data(), light.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
-            count_h2d(light.size() * sizeof(SampleItem));
+            ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
             if (nl) {
                 const double bytes = 8.0 * (double)(1ull << n) * (double)nl * 1.1;
                 ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
@@ -695,7 +754,7 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
         ctx->use_device();
         if (!c.pershot_planned) {
             c.plan_pershot = make_plan(c, kTileMax, true);
-            upload_circuit(c, c.plan_pershot, c.dev_pershot);
+            upload_circuit(ctx, c, c.plan_pershot, c.dev_pershot);
             c.pershot_planned = true;
         }
         const Plan& P = c.plan_pershot;
@@ -730,8 +789,7 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
                     items.push_back({i, 0u, jj, jj + 1, (uint64_t)i, kDomPershotRead, 0});   // bits[b0 + i]
                 }
                 SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
-                PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
-                count_h2d(items.size() * sizeof(SampleItem));
+                ctx->h2d(d_items, items.data(), items.size() * sizeof(SampleItem));
                 ctx->timed(PTSBE_TIMER_PERSHOT, 8.0 * sbytes * cnt, [&] { launch_sample_cluster(R, d_items, cnt, ctx->stream); });
             } else {
                 for (uint32_t i = 0; i < cnt; ++i) {

@@ -134,6 +134,22 @@ PTSBE_HD float2 fmul2(float2 a, float2 b, float2 c, float2 d) {   // a*b + c*d
     r.y = fmaf(a.x, b.y, fmaf(a.y, b.x, r.y));
     return r;
 }
+// Both lanes of a float2 times the same real factor, plus an addend: one packed FP32x2 FMA on the
+// device (a + b*r per lane), two scalar FMAs on the host.
+PTSBE_HD float2 fma2r(float2 b, float r, float2 a) {
+#ifdef __CUDA_ARCH__
+    unsigned long long d;
+    const float2 rr = make_float2(r, r);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&b)), "l"(*reinterpret_cast<const unsigned long long*>(&rr)),
+          "l"(*reinterpret_cast<const unsigned long long*>(&a)));
+    return *reinterpret_cast<const float2*>(&d);
+#else
+    return make_float2(fmaf(b.x, r, a.x), fmaf(b.y, r, a.y));
+#endif
+}
+PTSBE_HD float2 mul2r(float2 b, float r) { return fma2r(b, r, make_float2(-0.0f, -0.0f)); }
+
 PTSBE_HD uint32_t ins0(uint32_t i, int p) { return ((i >> p) << (p + 1)) | (i & ((1u << p) - 1u)); }
 PTSBE_HD uint32_t ins00(uint32_t i, int pa, int pb) {
     const int lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
@@ -698,9 +714,7 @@ PTSBE_HD float2 apply_tabs(float2 x, const Lookup& L, const float2* tabs, const 
         if (t < L.ntab) {
             const uint32_t i = slot < 0 ? L.ix[t] : (L.ix[t] ^ delta[t * kDeltaSlots + slot]);
             if ((L.real >> t) & 1) {
-                const float r = reinterpret_cast<const float*>(tabs + t * kTabSize + i)[0];
-                x.x *= r;
-                x.y *= r;
+                x = mul2r(x, reinterpret_cast<const float*>(tabs + t * kTabSize + i)[0]);
             } else {
                 x = fmul(x, tabs[t * kTabSize + i]);
             }
@@ -771,24 +785,37 @@ PTSBE_HD void run_mix1_n(const Step& st, const Factor* pool, float2* s, const fl
             float2 g00 = fl ? a11 : a00, g01 = fl ? a10 : a01, g10 = fl ? a01 : a10, g11 = fl ? a00 : a11;
             // folded factors: F0 on the half with y_i = 0, F1 on y_i = 1 (the matrix's columns)
             const uint32_t fb = st.fold_b[i], fe = st.fold_e[i];
+            const bool real = (st.mreal >> i) & 1;
             if (fb < fe) {
-                float2 F0 = make_float2(1.f, 0.f), F1 = make_float2(1.f, 0.f);
-                for (uint32_t j = fb; j < fe; ++j) {
-                    const Factor& f = pool[j];
-                    const uint32_t c = par(f.c1 & base) ^ par(f.r1o & tau);
-                    F0 = fmul(F0, f.f[2u * c]);
-                    F1 = fmul(F1, f.f[2u * (c ^ 1u)]);
+                if (real) {
+                    float F0 = 1.f, F1 = 1.f;
+                    for (uint32_t j = fb; j < fe; ++j) {
+                        const Factor& f = pool[j];
+                        const uint32_t c = par(f.c1 & base) ^ par(f.r1o & tau);
+                        F0 *= f.f[2u * c].x;
+                        F1 *= f.f[2u * (c ^ 1u)].x;
+                    }
+                    g00.x *= F0; g10.x *= F0;
+                    g01.x *= F1; g11.x *= F1;
+                } else {
+                    float2 F0 = make_float2(1.f, 0.f), F1 = make_float2(1.f, 0.f);
+                    for (uint32_t j = fb; j < fe; ++j) {
+                        const Factor& f = pool[j];
+                        const uint32_t c = par(f.c1 & base) ^ par(f.r1o & tau);
+                        F0 = fmul(F0, f.f[2u * c]);
+                        F1 = fmul(F1, f.f[2u * (c ^ 1u)]);
+                    }
+                    g00 = fmul(g00, F0); g10 = fmul(g10, F0);
+                    g01 = fmul(g01, F1); g11 = fmul(g11, F1);
                 }
-                g00 = fmul(g00, F0); g10 = fmul(g10, F0);
-                g01 = fmul(g01, F1); g11 = fmul(g11, F1);
             }
-            if ((st.mreal >> i) & 1) {
+            if (real) {
 #pragma unroll
                 for (int y = 0; y < NA; ++y) {
                     if ((y >> i) & 1) continue;
                     const float2 a = v[y], b = v[y | (1 << i)];
-                    v[y] = make_float2(fmaf(g00.x, a.x, g01.x * b.x), fmaf(g00.x, a.y, g01.x * b.y));
-                    v[y | (1 << i)] = make_float2(fmaf(g10.x, a.x, g11.x * b.x), fmaf(g10.x, a.y, g11.x * b.y));
+                    v[y] = fma2r(b, g01.x, mul2r(a, g00.x));
+                    v[y | (1 << i)] = fma2r(b, g11.x, mul2r(a, g10.x));
                 }
             } else {
 #pragma unroll
@@ -957,8 +984,8 @@ PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2*
         if (want_norm) part += fmaf(a0.x, a0.x, a0.y * a0.y) + fmaf(a1.x, a1.x, a1.y * a1.y);
         if (dst) {
             // w[0] = e_0: the pair is {l, l ^ 1}
-            const float4 x = (l & 1u) ? make_float4(a1.x * scale, a1.y * scale, a0.x * scale, a0.y * scale)
-                                      : make_float4(a0.x * scale, a0.y * scale, a1.x * scale, a1.y * scale);
+            const float2 s0 = mul2r(a0, scale), s1 = mul2r(a1, scale);
+            const float4 x = (l & 1u) ? make_float4(s1.x, s1.y, s0.x, s0.y) : make_float4(s0.x, s0.y, s1.x, s1.y);
             *reinterpret_cast<float4*>(dst + (l & ~1u)) = x;
         }
     }
