@@ -253,24 +253,35 @@ def main():
     P = Ptsbe(device=local, stream=stream.cuda_stream)
     P.set_evolve_kernel(args.evolve_kernel)
     states = torch.empty((K, 1 << n), dtype=torch.complex64, device=dev)
-    weights = torch.empty(K, dtype=torch.float64, device=dev)
-    status = torch.empty(K, dtype=torch.uint8, device=dev)
-    bits = torch.empty(M, dtype=torch.int32, device=dev)
-    host_bits = torch.empty(M, dtype=torch.int32, pin_memory=True)
-    host_w = torch.empty(K, dtype=torch.float64, pin_memory=True)
-    host_s = torch.empty(K, dtype=torch.uint8, pin_memory=True)
+    # Results of consecutive steps alternate between two buffers, so the copy of step i's shots,
+    # weights and flags to the host (its own stream) overlaps step i+1's kernels.
+    weights = [torch.empty(K, dtype=torch.float64, device=dev) for _ in range(2)]
+    status = [torch.empty(K, dtype=torch.uint8, device=dev) for _ in range(2)]
+    bits = [torch.empty(M, dtype=torch.int32, device=dev) for _ in range(2)]
+    host_bits = [torch.empty(M, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    host_w = [torch.empty(K, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    host_s = [torch.empty(K, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    done = [torch.cuda.Event(), torch.cuda.Event()]      # buffer b's copy finished
     h2d_bytes = [0]
+    count = [0]
 
     def step(e2e: bool):
+        b = count[0] % 2
+        count[0] += 1
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M, export=False)
         assert info.count == K and info.total_shots == M
-        P.evolve(info, 0, K, states, weights, status, prefix_reuse=True)
-        P.sample(info, 0, K, states, status, seed, bits)
+        stream.wait_event(done[b])                        # buffer b is free again
+        P.evolve(info, 0, K, states, weights[b], status[b], prefix_reuse=True)
+        P.sample(info, 0, K, states, status[b], seed, bits[b])
         if e2e:
-            host_bits.copy_(bits, non_blocking=True)
-            host_w.copy_(weights, non_blocking=True)
-            host_s.copy_(status, non_blocking=True)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                host_bits[b].copy_(bits[b], non_blocking=True)
+                host_w[b].copy_(weights[b], non_blocking=True)
+                host_s[b].copy_(status[b], non_blocking=True)
+            done[b].record(copy_stream)
         P.release_set(info)
         P.release_circuit(cid)
 
@@ -291,6 +302,7 @@ def main():
         ev0.record(stream)
         for _ in range(steps):
             step(e2e)
+        stream.wait_stream(copy_stream)                   # the region ends after the last copy
         ev1.record(stream)
         barrier()
         ms = ev0.elapsed_time(ev1)
@@ -310,7 +322,7 @@ def main():
     clocks.start()
     ms, launches, kern = timed(False, args.steps, True)
     clk = clocks.stop()
-    steps_e2e = max(1, args.steps // 2)
+    steps_e2e = max(2, args.steps)
     hb0 = capi.ptsbe_h2d_bytes()
     ms_e2e, _, _ = timed(True, steps_e2e, False)
     h2d_bytes[0] = (capi.ptsbe_h2d_bytes() - hb0) // steps_e2e
