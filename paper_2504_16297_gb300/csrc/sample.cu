@@ -121,23 +121,6 @@ __device__ double build_prefix(const float2* __restrict__ amps, int cb, double* 
     return cdf[paddr((1u << cb) - 1, kb)];
 }
 
-// The last entry build_prefix would produce, computed with the same operations: stage 1, then only
-// the thread owning the last entries runs its prefix. `excl` receives this thread's offset.
-__device__ double slice_total(const float2* __restrict__ amps, int cb, double* cdf, double* red, double& excl,
-                              double* total_slot) {
-    const int kb = entries_log2(cb);
-    const uint32_t K = 1u << kb, count = 1u << cb;
-    excl = slice_stage1(amps, cb, cdf, red);
-    const uint32_t l0 = threadIdx.x * K;
-    if (l0 < count && l0 + K >= count) {
-        double run = excl;
-        for (uint32_t i = 0; i < K; ++i) run += cdf[paddr(l0 + i, kb)];
-        *total_slot = run;
-    }
-    __syncthreads();
-    return *total_slot;
-}
-
 // smallest l in [0, 2^cb) with t < cdf[l] (the last index if none)
 constexpr int kGuideBits = 12;
 constexpr int kGuide = 1 << kGuideBits;
@@ -280,97 +263,97 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
     if constexpr (CL > 1) cg::this_cluster().sync();  // keep this CTA's slice alive for remote readers
 }
 
-// ---- light states: one CTA per state, slice by slice --------------------------------------------------
-// For a state with few shots the CDF is never stored: pass 1 runs the slice prefix (the same routine
-// as above, so a slice's last entry is bit-identical whenever it is recomputed) over 2^kLightBits-
-// amplitude slices and keeps only the slice totals; thread 0 turns them into slice offsets by a
-// sequential FP64 scan, so C at a slice end is off[s+1] = off[s] + total[s] exactly. Pass 2 rebuilds
-// only the slices that hold a shot and resolves those shots against off[s] + local prefix.
-constexpr int kLightBits = 12;
-constexpr int kLightMaxSlices = 256;         // n <= 20
-
+// ---- light states: one CTA per state, chunk prefixes ----------------------------------------------------
+// For a state with few shots the full CDF is never stored. Pass 1 sums each run of cs = 2^n / 8192
+// consecutive P_i sequentially in FP64 (chunk totals); a fixed-order scan turns them into the FP64
+// prefix at every chunk start, P[c] (P[8192] = T). A shot finds its chunk by binary search on P and
+// then accumulates the chunk's P_i from P[c] in order: C_i = P[c] + p_first + ... + p_i inside the
+// chunk, the chunk's last entry taken as P[c+1] (so C is the chunk-start prefix everywhere). Each
+// shot re-reads one chunk (cs amplitudes, mostly from L2), so FP64 work is one add per amplitude
+// plus at most cs per shot.
+constexpr int kLightChunkBits = 13;
+constexpr int kLightChunks = 1 << kLightChunkBits;
 constexpr int kLightThreads = 512;          // one shot per thread at most
+constexpr int kLightPerThread = kLightChunks / kLightThreads;   // chunks scanned by one thread (16)
+
+__device__ __forceinline__ uint32_t lpad(uint32_t c) { return c + (c >> 4); }   // bank-distinct rows of 16
+
+__device__ __forceinline__ double prob64(float2 a) { return f2d_exact(fmaf(a.x, a.x, a.y * a.y)); }
 
 __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a, const SampleItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[33];
-    __shared__ double off[kLightMaxSlices + 1];
-    __shared__ double texcl[kLightThreads + 1];
-    __shared__ double total_slot;
-    __shared__ uint8_t used[kLightMaxSlices];
-    double* cdf = reinterpret_cast<double*>(smem);
+    double* P = reinterpret_cast<double*>(smem);       // padded: P[lpad(c)], c = 0 .. kLightChunks
     const SampleItem it = items[blockIdx.x];
-    const uint64_t nshots = it.j1 - it.j0;          // <= blockDim.x
+    const uint64_t nshots = it.j1 - it.j0;              // <= blockDim.x
     if (a.status && a.status[it.state]) {
         if (threadIdx.x < nshots) a.bits[it.out0 + threadIdx.x] = 0xFFFFFFFFu;
         return;
     }
-    const int n = a.n, cb = kLightBits;
-    const uint32_t nsl = 1u << (n - cb);
-    const int kb = entries_log2(cb);
-    const uint32_t K = 1u << kb;
+    const int n = a.n;
+    const int csb = n - kLightChunkBits;                // log2 of the chunk size (2 .. 7)
+    const uint32_t cs = 1u << csb;
     const float2* amps = a.states + ((size_t)it.state << n);
-    // pass 1: slice totals (each equal to the slice's last prefix entry), then offsets by a
-    // sequential FP64 scan
-    for (uint32_t sl = 0; sl < nsl; ++sl) {
-        double excl;
-        const double tot = slice_total(amps + ((size_t)sl << cb), cb, cdf, red, excl, &total_slot);
-        if (threadIdx.x == 0) off[sl + 1] = tot;
-        __syncthreads();                             // every thread has read the slot before reuse
+    // pass 1: chunk totals, sequential FP64 sums (two amplitudes per 16-byte load)
+    for (uint32_t c = threadIdx.x; c < (uint32_t)kLightChunks; c += blockDim.x) {
+        const float4* v = reinterpret_cast<const float4*>(amps + ((size_t)c << csb));
+        double acc = 0.0;
+        for (uint32_t i = 0; i < cs / 2; ++i) {
+            const float4 x = __ldg(v + i);
+            acc += prob64(make_float2(x.x, x.y));
+            acc += prob64(make_float2(x.z, x.w));
+        }
+        P[lpad(c)] = acc;
     }
+    __syncthreads();
+    // scan: thread t owns chunks [16 t, 16 t + 16): sequential sum, fixed-order CTA exclusive scan of
+    // the thread sums, then the chunk-start prefixes
+    const uint32_t c0 = threadIdx.x * kLightPerThread;
+    double tot[kLightPerThread];
+    double mine = 0.0;
+#pragma unroll
+    for (int i = 0; i < kLightPerThread; ++i) { tot[i] = P[lpad(c0 + i)]; mine += tot[i]; }
+    double v = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= (uint32_t)o) v += y;
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 31) red[w] = v;
+    __syncthreads();
     if (threadIdx.x == 0) {
         double acc = 0.0;
-        off[0] = 0.0;
-        for (uint32_t sl = 0; sl < nsl; ++sl) { acc += off[sl + 1]; off[sl + 1] = acc; }
+        for (int i = 0; i < nw; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+        red[32] = acc;                                  // T
     }
-    for (uint32_t sl = threadIdx.x; sl < nsl; sl += blockDim.x) used[sl] = 0;
     __syncthreads();
-    const bool mine = threadIdx.x < nshots;
-    long long tb = 0;
-    int slice = -1;
-    if (mine) {
-        const uint64_t j = it.j0 + threadIdx.x;
-        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        tb = dbits(u53(x.x[0], x.x[1]) * off[nsl]);
-        uint32_t lo = 0, hi = nsl;                   // smallest s with t < off[s + 1]
+    double run = red[w] + (v - mine);                   // exclusive prefix of this thread's chunks
+#pragma unroll
+    for (int i = 0; i < kLightPerThread; ++i) { P[lpad(c0 + i)] = run; run += tot[i]; }
+    const double T = red[32];
+    if (threadIdx.x == 0) P[lpad(kLightChunks)] = T;
+    __syncthreads();
+    if (threadIdx.x >= nshots) return;
+    const uint64_t j = it.j0 + threadIdx.x;
+    const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    const long long tb = dbits(u53(x.x[0], x.x[1]) * T);
+    uint32_t idx = (1u << n) - 1;                       // rounding put t at or above T
+    if (tb < dbits(T)) {
+        uint32_t lo = 0, hi = kLightChunks - 1;         // first chunk c with t < P[c + 1]
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (tb < dbits(off[mid + 1])) hi = mid; else lo = mid + 1;
+            if (tb < dbits(P[lpad(mid + 1)])) hi = mid; else lo = mid + 1;
         }
-        if (lo < nsl) { slice = (int)lo; used[lo] = 1; }
-        else a.bits[it.out0 + threadIdx.x] = (1u << n) - 1;
-    }
-    __syncthreads();
-    // pass 2: in a slice that holds shots, stage 1 again (same operations, same values) gives the
-    // thread offsets; each shot runs the sequential prefix from the chunk its target falls in.
-    for (uint32_t sl = 0; sl < nsl; ++sl) {
-        if (!used[sl]) continue;
-        const double excl = slice_stage1(amps + ((size_t)sl << cb), cb, cdf, red);
-        texcl[threadIdx.x] = excl;
-        __syncthreads();
-        if (slice == (int)sl) {
-            const double base = off[sl];
-            // first chunk whose starting offset lies beyond the target, then back one chunk
-            uint32_t lo = 0, hi = blockDim.x;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (tb < dbits(base + texcl[mid])) hi = mid; else lo = mid + 1;
-            }
-            uint32_t c = lo > 0 ? lo - 1 : 0;
-            if (c > 0) --c;                          // one more chunk back for ulp-level ties
-            uint32_t idx = (1u << cb) - 1;
-            bool found = false;
-            for (; c < blockDim.x && !found; ++c) {
-                double run = texcl[c];
-                for (uint32_t i = 0; i < K; ++i) {
-                    run += cdf[paddr(c * K + i, kb)];
-                    if (tb < dbits(base + run)) { idx = c * K + i; found = true; break; }
-                }
-            }
-            a.bits[it.out0 + threadIdx.x] = (sl << cb) | idx;
+        double acc = P[lpad(lo)];
+        const float2* ch = amps + ((size_t)lo << csb);
+        idx = (lo << csb) + cs - 1;
+        for (uint32_t i = 0; i + 1 < cs; ++i) {
+            acc += prob64(__ldg(ch + i));
+            if (tb < dbits(acc)) { idx = (lo << csb) + i; break; }
         }
-        __syncthreads();
     }
+    a.bits[it.out0 + threadIdx.x] = idx;
 }
 
 // ---- n > 17: global-memory CDF -----------------------------------------------------------------------
@@ -525,12 +508,12 @@ void* noalloc_scratch(int device) {
 }
 
 int sample_cluster_max_qubits() { return kSliceBits + 3; }
-int sample_light_max_qubits() { return kLightBits + 8; }
+int sample_light_max_qubits() { return kLightChunkBits + 7; }
 
 void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
     if (n_items == 0) return;
     static bool configured = false;
-    const size_t smem = cdf_smem_bytes(kLightBits, kLightThreads);
+    const size_t smem = ((size_t)kLightChunks + kLightChunks / 16 + 1) * sizeof(double);
     if (!configured) {
         PTSBE_CUDA(cudaFuncSetAttribute(k_sample_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
