@@ -166,6 +166,11 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
     const uint32_t src = stage_idx == (int)a.node_sstage[node] ? a.node_src[node] : node;
     const float2* gin = a.states_in + ((size_t)src << n);
     const bool fresh = a.node_fresh[node] && stage_idx == 0;
+    // From |0...0>, every mix of the first stage moves along directions inside the tile (the plan
+    // guarantees it), and permutations and diagonals never widen the set of nonzero amplitudes: all
+    // of them stay in the tile holding index 0. Every other tile of the state is zero for the whole
+    // stage and only writes zeros where the stage's store puts it.
+    const bool zero_tile = fresh && tau != 0;
     __syncthreads();
     // The first program segment is read in place (global memory, the same for all tiles of the
     // set); segments built here when the program is longer live in shared memory.
@@ -182,7 +187,9 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
     } else {
         const uint32_t t = tid - 32, nt = nthr - 32, nv = 1u << (tb - 1);
         float4* tile4 = reinterpret_cast<float4*>(tile);
-        if (fresh) {
+        if (zero_tile) {
+            // never read
+        } else if (fresh) {
             for (uint32_t v = t; v < nv; v += nt)
                 tile4[v] = make_float4((v == 0 && tau == 0) ? 1.0f : 0.0f, 0.f, 0.f, 0.f);
         } else {
@@ -209,7 +216,8 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
         const uint32_t ns = B.nsteps;
         for (uint32_t si = 0; si < ns; ++si) {
             const Step& sp = Sp[si];
-            if (sp.ntab) {
+            if (zero_tile && sp.kind <= ST_DIAG) continue;    // uniform across the CTA
+            if (sp.ntab && !zero_tile) {
                 prepare_tables(sp, fs, poolp, tabs, delta, tb, tau, tid, nthr);
                 __syncthreads();
             }
@@ -220,15 +228,15 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
             } else if (sp.kind == ST_DIAG) {
                 run_diag(sp, tile, tabs, delta, tb, tid, nthr);
             } else if (sp.kind == ST_STORE) {
-                const double part = run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr);
+                const double part = run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr, zero_tile);
                 if (a.store_norm) {
                     const double tot = cta_sum(part, red);
                     if (tid == 0) a.part[((size_t)node << ob) + tau] = tot;
                 }
             } else if (!last) {       // logical order before a frame restart
-                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, false, tid, nthr);
+                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, false, tid, nthr, zero_tile);
             } else if (a.scale_in) {
-                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, a.scale_in[node], false, tid, nthr);
+                run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, a.scale_in[node], false, tid, nthr, zero_tile);
             } else if (ob == 0) {
                 const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, nullptr, 1.0f, true, tid, nthr), red);
                 const double w = a.wmix[node] * part;
@@ -240,7 +248,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
                     if (a.status) a.status[node] = null ? 1 : 0;
                 }
             } else {
-                const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, true, tid, nthr), red);
+                const double part = cta_sum(run_final(sp, fs, tile, tabs, delta, tb, ob, tau, g, 1.0f, true, tid, nthr, zero_tile), red);
                 if (tid == 0) a.part[((size_t)node << ob) + tau] = part;
             }
             __syncthreads();

@@ -929,9 +929,11 @@ PTSBE_HD uint64_t outer_offset(const DevStage& stg, int ob, uint32_t tau) {
 }
 
 // Intermediate store: tile-local d of tile tau ^ b_out receives D(x) s[d ^ b_in] (x the source).
-// Returns this thread's part of the squared norm of what it wrote.
+// Returns this thread's part of the squared norm of what it wrote. zero: the tile is known to be
+// zero (its amplitudes are not read).
 PTSBE_HD double run_store(const Step& st, const DevStage& stg, const float2* s, const float2* tabs, const uint32_t* delta,
-                          int tb, int lb, int ob, const uint32_t* hi, uint32_t tau, float2* dst, uint32_t tid, uint32_t nthr) {
+                          int tb, int lb, int ob, const uint32_t* hi, uint32_t tau, float2* dst, uint32_t tid, uint32_t nthr,
+                          bool zero = false) {
     const uint32_t N = 1u << (tb - 1);
     if (tid >= N) return 0.0;
     float part = 0.f;
@@ -939,6 +941,11 @@ PTSBE_HD double run_store(const Step& st, const DevStage& stg, const float2* s, 
     const uint32_t bin = st.lb0;
     const uint64_t outer = outer_offset(stg, ob, tau ^ st.rout[0]);
     uint32_t d = 2u * tid;
+    if (zero) {
+        for (uint32_t k = 0; k < K; ++k, d += 2u * nthr)
+            *reinterpret_cast<float4*>(dst + gaddr(d, lb, hi, outer)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        return 0.0;
+    }
     Lookup L;
     lookup_init(L, st, d ^ bin);
     for (uint32_t k = 0; k < K; ++k) {
@@ -959,7 +966,7 @@ PTSBE_HD double run_store(const Step& st, const DevStage& stg, const float2* s, 
 // returns this thread's part of their squared norm (when want_norm).
 PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2* s, const float2* tabs,
                           const uint32_t* delta, int tb, int ob, uint32_t tau, float2* dst, float scale, bool want_norm,
-                          uint32_t tid, uint32_t nthr) {
+                          uint32_t tid, uint32_t nthr, bool zero = false) {
     const uint32_t N = 1u << (tb - 1);
     if (tid >= N) return 0.0;
     const uint32_t K = N > nthr ? N / nthr : 1u;
@@ -979,8 +986,12 @@ PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2*
             l ^= fs.w[1 + lg + j];
             lookup_step(L, delta, j);
         }
-        float2 a0 = s[p], a1 = s[p ^ fs.m[0]];
-        if (L.ntab) { a0 = apply_tabs(a0, L, tabs, delta, -1); a1 = apply_tabs(a1, L, tabs, delta, 15); }
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+        if (!zero) {
+            a0 = s[p];
+            a1 = s[p ^ fs.m[0]];
+            if (L.ntab) { a0 = apply_tabs(a0, L, tabs, delta, -1); a1 = apply_tabs(a1, L, tabs, delta, 15); }
+        }
         if (want_norm) part += fmaf(a0.x, a0.x, a0.y * a0.y) + fmaf(a1.x, a1.x, a1.y * a1.y);
         if (dst) {
             // w[0] = e_0: the pair is {l, l ^ 1}

@@ -54,6 +54,7 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     const Step* Sp = S;
     const Factor* poolp = pool;
     const bool fresh = a.node_fresh[node] && stage == 0;
+    const bool zero_tile = fresh && tau != 0;        // as in the kernel: only tile 0 is nonzero
     for (uint32_t v = 0; v < (1u << (tb - 1)); ++v) {
         if (fresh) {
             tile[2 * v] = make_float2((v == 0 && tau == 0) ? 1.f : 0.f, 0.f);
@@ -67,7 +68,8 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     while (true) {
         for (uint32_t si = 0; si < B.nsteps; ++si) {
             const Step& sp = Sp[si];
-            if (sp.ntab)
+            if (zero_tile && sp.kind <= ST_DIAG) continue;
+            if (sp.ntab && !zero_tile)
                 for (uint32_t t = 0; t < nthr; ++t) prepare_tables(sp, fs, poolp, tabs.data(), delta, tb, tau, t, nthr);
             if (sp.kind == ST_MIX1) {
                 for (uint32_t t = 0; t < nthr; ++t) run_mix1(sp, poolp, tile.data(), tabs.data(), delta, tb, tau, t, nthr);
@@ -78,14 +80,14 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
             } else if (sp.kind == ST_STORE) {
                 double part = 0;
                 for (uint32_t t = 0; t < nthr; ++t)
-                    part += run_store(sp, st, tile.data(), tabs.data(), delta, tb, lb, ob, hi, tau, g, t, nthr);
+                    part += run_store(sp, st, tile.data(), tabs.data(), delta, tb, lb, ob, hi, tau, g, t, nthr, zero_tile);
                 if (a.store_norm) a.part[((size_t)node << ob) + tau] = part;
             } else if (!last) {
                 for (uint32_t t = 0; t < nthr; ++t)
-                    run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, 1.f, false, t, nthr);
+                    run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, 1.f, false, t, nthr, zero_tile);
             } else if (scale_in) {
                 for (uint32_t t = 0; t < nthr; ++t)
-                    run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, scale_in[node], false, t, nthr);
+                    run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, scale_in[node], false, t, nthr, zero_tile);
             } else if (ob == 0) {
                 double part = 0;
                 for (uint32_t t = 0; t < nthr; ++t)
@@ -100,7 +102,7 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
             } else {
                 double part = 0;
                 for (uint32_t t = 0; t < nthr; ++t)
-                    part += run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, 1.f, true, t, nthr);
+                    part += run_final(sp, fs, tile.data(), tabs.data(), delta, tb, ob, tau, g, 1.f, true, t, nthr, zero_tile);
                 a.part[((size_t)node << ob) + tau] = part;
             }
         }
