@@ -547,6 +547,10 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         // the last stage writes the normalised state (no separate renormalisation pass).
         const bool early_norm = frame && ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end &&
                                 launches[J - 2].second == count;
+        A.sparse_final_stage = -1;
+        if (frame)
+            for (uint32_t j = 0; j < J; ++j)
+                if (P.fstages[j].sparse_final) A.sparse_final_stage = (int)j;
         for (uint32_t j = 0; j < J; ++j) {
             const auto& L = launches[j];
             if (L.second == 0) continue;
@@ -567,7 +571,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         A.states = user;
         A.store_norm = 0;
         A.scale_in = nullptr;
-        if (ob > 0 && !early_norm)
+        if (ob > 0 && !early_norm && A.sparse_final_stage < 0)
             ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
     });
 }

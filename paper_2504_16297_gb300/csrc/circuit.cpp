@@ -728,6 +728,7 @@ void close_frame_stage(Plan& P, const Circuit& c, uint32_t T, uint32_t b, uint32
         };
         for (int k = 0; k < lbf; ++k)
             if (!try_add(1u << k)) fail(PTSBE_ERR_INVALID, "frame plan: output bits outside the last tile");
+        if (lbf == 0) { P.fstages.push_back(f); return; }   // sparse final: no dense output map
         for (int t = 0; t < P.tb && d < P.tb; ++t) {
             int x = -1;
             for (int g = 0; g < n; ++g) if (st.pos[g] == t) x = g;
@@ -775,6 +776,16 @@ Plan make_frame_plan(const Circuit& c, int tile_bits) {
     auto close_logical = [&](uint32_t e) {
         uint32_t F = 0;
         for (int k = 0; k < P.lb; ++k) F |= col[k];
+        if (e == nops && begin == 0 && P.stages.empty()) {
+            // the whole circuit in one stage from |0...0>: the final store scatters from the one
+            // nonzero tile (no tile constraint on the output bits)
+            close_frame_stage(P, c, U, begin, e, entry, true, 0);
+            DevFrameStage& f = P.fstages.back();
+            f.sparse_final = 1;
+            invert_cols(n, col, f.rowe);
+            for (int q = 0; q < n; ++q) col[q] = entry[q] = 1u << q;
+            return;
+        }
         if (__builtin_popcount(U | F) <= P.tb) {
             close_frame_stage(P, c, U | F, begin, e, entry, true, P.lb);
         } else {

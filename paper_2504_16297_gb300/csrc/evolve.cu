@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kProgThreads) k_frame_program(EvolveArgs a, in
     const uint32_t node = nodes[i];
     Builder& B = Bs[threadIdx.x];
     Program& P = progs[i];
-    builder_init(B, a, st, a.fstages[stage_idx], node);
+    builder_init(B, a, st, a.fstages[stage_idx], node, a.node_fresh[node] && stage_idx == 0);
     build_segment(B, P.S, P.pool, a, st, kProgSteps, kProgPool);
     P.B = B;
 }
@@ -227,6 +227,20 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
                 run_mix2(sp, tile, tabs, delta, tb, tau, tid, nthr);
             } else if (sp.kind == ST_DIAG) {
                 run_diag(sp, tile, tabs, delta, tb, tid, nthr);
+            } else if (sp.kind == ST_FINAL && fs.sparse_final) {
+                // norm over the support, zero-fill, then scatter in logical order (one CTA per state)
+                const double part = cta_sum(run_sparse_final(sp, fs, tile, tabs, delta, n, lb, hi, nullptr, 1.0f, 0, tid, nthr), red);
+                const double w = a.wmix[node] * part;
+                const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
+                const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
+                float4* g4 = reinterpret_cast<float4*>(g);
+                for (uint32_t v = tid; v < (1u << (n - 1)); v += nthr) g4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+                if (!null) run_sparse_final(sp, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
+                if (tid == 0) {
+                    if (a.weights) a.weights[node] = w;
+                    if (a.status) a.status[node] = null ? 1 : 0;
+                }
             } else if (sp.kind == ST_STORE) {
                 const double part = run_store(sp, st, tile, tabs, delta, tb, lb, ob, hi, tau, g, tid, nthr, zero_tile);
                 if (a.store_norm) {
@@ -728,7 +742,7 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
     const int threads = regs ? (1 << (a.tb - kRegBits)) : frm ? std::min(evolve_threads(a.tb), kFrameThreads) : evolve_threads(a.tb);
     const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : frm ? evolve_frame_smem_bytes(a.tb, a.lb)
                                                                        : evolve_smem_bytes(a.tb, a.lb);
-    const uint32_t tiles = 1u << (a.n - a.tb);
+    const uint32_t tiles = (frm && stage == a.sparse_final_stage) ? 1u : 1u << (a.n - a.tb);
     frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
     if (frm) {
         if (!progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");

@@ -82,6 +82,11 @@ struct Step {
     uint32_t lb0;                    // FINAL: R b (logical); STORE: tile part of b
     uint32_t npush, nframe;          // builder counters when emitted (grouping test)
     uint16_t fold_b[kMaxDirs], fold_e[kMaxDirs];   // MIX1: pool factors folded into direction i
+    // Sparse passes (a stage started from |0...0>): the nonzero amplitudes lie in the span of the
+    // directions mixed so far, so MIX / DIAG passes visit only the cosets base = sum_i bit_i comp[i]
+    // of that span (complemented by the step's own directions); ncomp = 0xFF: the whole tile.
+    uint8_t ncomp, pad3;
+    uint16_t comp[kTileMax];
     Table tab[kMaxTabs];
     float2 m[16];                    // MIX1: 2x2 of direction i at m[4i..4i+3]; MIX2: 4x4 on 2 l_a + l_b
 };
@@ -92,6 +97,10 @@ struct Builder {
     uint32_t op, e, ee;                          // next op and entry cursor of the set
     uint32_t npend, nsteps, npool, done, last;
     uint32_t npush, nframe;                      // factor changes and frame changes so far
+    uint32_t sparse, sdim;                       // support tracking (stage from |0...0>): basis size
+    uint32_t sparse_final;                       // the stage ends with the sparse final store
+    uint16_t sech[kTileMax];                     // echelon basis of the support (tile-local)
+    uint8_t spiv[kTileMax], pad3[2];
     uint16_t ech[kTabBits], comb[kTabBits];      // echelon rows of the table being filled
     uint8_t piv[kTabBits], pad2[2];
     Factor pend[kMaxPending];
@@ -275,6 +284,37 @@ PTSBE_HD uint64_t drop_pending(Builder& B, uint64_t rm, uint64_t keep) {
     return out;
 }
 
+// Adds a tile-local direction to the support span (echelon with distinct lowest-bit pivots).
+PTSBE_HD void support_add(Builder& B, uint32_t u) {
+    for (uint32_t i = 0; i < B.sdim; ++i)
+        if ((u >> B.spiv[i]) & 1u) u ^= B.sech[i];
+    if (!u) return;
+    B.sech[B.sdim] = (uint16_t)u;
+    B.spiv[B.sdim] = (uint8_t)low_bit(u);
+    ++B.sdim;
+}
+
+// Coset representatives of span(dirs) inside the support: the support basis reduced against the
+// directions, keeping the independent remainders. The whole tile when the support is unknown.
+PTSBE_HD void set_enumeration(const Builder& B, Step& st, const uint16_t* dirs, int nd) {
+    if (!B.sparse) { st.ncomp = 0xFF; return; }
+    uint32_t e[kTileMax + kMaxDirs];
+    uint8_t pv[kTileMax + kMaxDirs];
+    int ne = 0;
+    auto reduce_add = [&](uint32_t x) {
+        for (int i = 0; i < ne; ++i)
+            if ((x >> pv[i]) & 1u) x ^= e[i];
+        if (!x) return false;
+        e[ne] = x; pv[ne] = (uint8_t)low_bit(x); ++ne;
+        return true;
+    };
+    for (int i = 0; i < nd; ++i) reduce_add(dirs[i]);
+    int nc = 0;
+    for (uint32_t i = 0; i < B.sdim; ++i)
+        if (reduce_add(B.sech[i])) st.comp[nc++] = (uint16_t)e[ne - 1];
+    st.ncomp = (uint8_t)nc;
+}
+
 // Returns the step S[B.nsteps] with tables for the factors of mask. If they need more than
 // kMaxTabs tables, DIAG steps apply the overflow to the tile first (those factors leave the
 // pending list). With remove, the factors of the returned step leave the pending list too.
@@ -287,6 +327,7 @@ PTSBE_HD Step& take_tables(Builder& B, const DevStage& stg, Step* S, Factor* poo
             return st;
         }
         st.kind = ST_DIAG;
+        set_enumeration(B, st, nullptr, 0);
         ++B.nsteps;
         mask = drop_pending(B, used, mask & ~used);
     }
@@ -317,6 +358,7 @@ PTSBE_HD void push_factor(Builder& B, const DevStage& stg, Step* S, Factor* pool
     if (B.npend == kMaxPending) {
         Step& st = take_tables(B, stg, S, pool, all_pending(B), true);
         st.kind = ST_DIAG;
+        set_enumeration(B, st, nullptr, 0);
         ++B.nsteps;
     }
     Factor& f = B.pend[B.npend++];
@@ -427,6 +469,8 @@ PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
             pr.cpar[i] = (uint8_t)par(B.row[q] & B.bv);
             for (int k = 0; k < 4; ++k) pr.m[4 * i + k] = m[k];
             set_pivots(pr);
+            if (B.sparse) support_add(B, ut);
+            set_enumeration(B, pr, pr.dir, pr.ndir);
             return;
         }
     }
@@ -443,6 +487,8 @@ PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
     st.nframe = B.nframe;
     for (int k = 0; k < 4; ++k) st.m[k] = m[k];
     set_pivots(st);
+    if (B.sparse) support_add(B, ut);
+    set_enumeration(B, st, st.dir, 1);
     ++B.nsteps;
 }
 
@@ -468,12 +514,16 @@ PTSBE_HD void emit_mix2(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
     st.npush = B.npush;
     st.nframe = B.nframe;
     for (int i = 0; i < 16; ++i) st.m[i] = m[i];
+    if (B.sparse) { support_add(B, u); support_add(B, v); }
+    set_enumeration(B, st, st.dir, 2);
     ++B.nsteps;
 }
 
 // End of the stage: STORE writes D(x) s[x] to global index x ^ b; FINAL writes logical order.
 PTSBE_HD void emit_end(Builder& B, const DevStage& stg, Step* S, Factor* pool, int n) {
     Step& st = take_tables(B, stg, S, pool, all_pending(B), false);
+    if (B.sparse_final && B.sparse) set_enumeration(B, st, nullptr, 0);   // the support, for the scatter
+    else st.ncomp = 0xFF;
     if (B.last) {
         st.kind = ST_FINAL;
         uint32_t l = 0;
@@ -566,7 +616,7 @@ PTSBE_HD void fused_matrix(const DevOp& o, const float2* m, float2* g) {
 }
 
 PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage& st, const DevFrameStage& fs,
-                                uint32_t node) {
+                                uint32_t node, bool from_zero) {
     for (int q = 0; q < kMaxQubits; ++q) { B.col[q] = fs.col[q]; B.row[q] = fs.row[q]; }
     B.bv = 0;
     B.op = st.op_begin;
@@ -578,6 +628,9 @@ PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage&
     B.done = 0;
     B.last = fs.last;
     B.npush = B.nframe = 0;
+    B.sparse = from_zero ? 1u : 0u;      // the support starts as {0}
+    B.sdim = 0;
+    B.sparse_final = fs.sparse_final;
 }
 
 // Emits steps until the stage ends (then the end step and done = 1) or the step list or the
@@ -649,6 +702,17 @@ PTSBE_HD uint32_t ins_piv(uint32_t i, const uint8_t* piv, int k) {   // zeros at
     return i;
 }
 
+// Enumeration of a pass: coset index i -> representative. Whole tile: zeros inserted at the pivot
+// bits of the step's directions; sparse: XOR of comp[j] over the set bits j of i.
+PTSBE_HD uint32_t enum_count(const Step& st, int tb, int nd) { return st.ncomp == 0xFF ? 1u << (tb - nd) : 1u << st.ncomp; }
+PTSBE_HD uint32_t enum_base(const Step& st, uint32_t i, const uint8_t* piv, int nd) {
+    if (st.ncomp == 0xFF) return ins_piv(i, piv, nd);
+    uint32_t b = 0;
+    for (int j = 0; j < st.ncomp && (i >> j); ++j)
+        if ((i >> j) & 1u) b ^= st.comp[j];
+    return b;
+}
+
 // Tile-local address delta of bit j of the iteration counter (slots < 10), of the directions of
 // a grouped mix (slots 10 + i), and of the fixed offsets of the other steps (slots 14, 15).
 PTSBE_HD uint32_t step_delta(const Step& st, const DevFrameStage& fs, int tb, uint32_t nthr, int j) {
@@ -656,12 +720,15 @@ PTSBE_HD uint32_t step_delta(const Step& st, const DevFrameStage& fs, int tb, ui
     switch (st.kind) {
     case ST_MIX1:
         if (j >= 10) return j - 10 < st.ndir ? st.dir[j - 10] : 0u;
+        if (st.ncomp != 0xFF) return enum_base(st, nthr << j, st.piv, st.ndir);
         return ins_piv(nthr << j, st.piv, st.ndir) & mask;
     case ST_MIX2:
         if (j == 14) return st.dir[1];
         if (j == 15) return st.dir[0];
+        if (st.ncomp != 0xFF) return j < 14 ? enum_base(st, nthr << j, st.piv, 2) : 0u;
         return j < 14 ? ins00(nthr << j, st.piv[0], st.piv[1]) & mask : 0u;
     case ST_DIAG:
+        if (st.ncomp != 0xFF) return j < 14 ? enum_base(st, nthr << j, st.piv, 0) : 0u;
         return j < 14 ? (nthr << j) & mask : 0u;
     case ST_STORE:   // destination d = 2 (tid + k nthr) + {0, 1}, source d ^ b
         if (j == 15) return 1u;
@@ -746,19 +813,19 @@ template <int ND>
 PTSBE_HD void run_mix1_n(const Step& st, const Factor* pool, float2* s, const float2* tabs, const uint32_t* delta, int tb,
                          uint32_t tau, uint32_t tid, uint32_t nthr) {
     constexpr int NA = 1 << ND;
-    const uint32_t N = 1u << (tb - ND);
+    const uint32_t N = enum_count(st, tb, ND);
     if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
     uint32_t dir[ND], rin[ND], c0[ND];
 #pragma unroll
     for (int i = 0; i < ND; ++i) { dir[i] = st.dir[i]; rin[i] = st.rin[i]; c0[i] = st.cpar[i] ^ par(st.rout[i] & tau); }
-    uint32_t base = ins_piv(tid, st.piv, ND);
+    uint32_t base = enum_base(st, tid, st.piv, ND);
     Lookup L;
     lookup_init(L, st, base);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            base ^= ins_piv(nthr << j, st.piv, ND);
+            base ^= enum_base(st, nthr << j, st.piv, ND);
             lookup_step(L, delta, j);
         }
         float2 v[NA];
@@ -855,18 +922,19 @@ PTSBE_HD void xswap(float2* z, uint32_t x0) {
 
 PTSBE_HD void run_mix2(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tau,
                        uint32_t tid, uint32_t nthr) {
-    const uint32_t N = 1u << (tb - 2);
+    const uint32_t N = enum_count(st, tb, 2);
     if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
     const uint32_t w[4] = {0u, st.dir[1], st.dir[0], (uint32_t)(st.dir[0] ^ st.dir[1])};   // logical difference y -> offset
     const uint32_t ca = st.cpar[0] ^ par(st.rout[0] & tau), cb = st.cpar[1] ^ par(st.rout[1] & tau);
-    uint32_t base = ins00(tid, st.piv[0], st.piv[1]);
+    const uint8_t pv2[2] = {(uint8_t)(st.piv[0] < st.piv[1] ? st.piv[0] : st.piv[1]), (uint8_t)(st.piv[0] < st.piv[1] ? st.piv[1] : st.piv[0])};
+    uint32_t base = enum_base(st, tid, pv2, 2);
     Lookup L;
     lookup_init(L, st, base);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            base ^= ins00(nthr << j, st.piv[0], st.piv[1]);
+            base ^= enum_base(st, nthr << j, pv2, 2);
             lookup_step(L, delta, j);
         }
         float2 z[4];
@@ -901,16 +969,16 @@ PTSBE_HD void run_mix2(const Step& st, float2* s, const float2* tabs, const uint
 
 PTSBE_HD void run_diag(const Step& st, float2* s, const float2* tabs, const uint32_t* delta, int tb, uint32_t tid,
                        uint32_t nthr) {
-    const uint32_t N = 1u << tb;
+    const uint32_t N = enum_count(st, tb, 0);
     if (tid >= N) return;
     const uint32_t K = N > nthr ? N / nthr : 1u;
-    uint32_t p = tid;
+    uint32_t p = enum_base(st, tid, nullptr, 0);
     Lookup L;
     lookup_init(L, st, p);
     for (uint32_t k = 0; k < K; ++k) {
         if (k) {
             const int j = low_bit(k);
-            p ^= nthr << j;
+            p ^= enum_base(st, nthr << j, nullptr, 0);
             lookup_step(L, delta, j);
         }
         s[p] = apply_tabs(s[p], L, tabs, delta, -1);
@@ -1001,6 +1069,34 @@ PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2*
         }
     }
     return (double)part;
+}
+
+// Sparse final store: the support of the state (span of comp, all in this tile) holds every
+// nonzero amplitude. phase 0 returns this thread's part of the squared norm; phase 1 writes
+// D(x) s[x] * scale to logical index R_end x ^ R_end b of dst (the caller zero-filled dst before).
+PTSBE_HD double run_sparse_final(const Step& st, const DevFrameStage& fs, const float2* s, const float2* tabs,
+                                 const uint32_t* delta, int n, int lb, const uint32_t* hi, float2* dst, float scale,
+                                 int phase, uint32_t tid, uint32_t nthr) {
+    const uint32_t N = st.ncomp == 0xFF ? 0u : 1u << st.ncomp;
+    double acc = 0.0;
+    for (uint32_t i = tid; i < N; i += nthr) {
+        const uint32_t p = enum_base(st, i, nullptr, 0);
+        float2 a = s[p];
+        if (st.ntab) {
+            Lookup L;
+            lookup_init(L, st, p);
+            a = apply_tabs(a, L, tabs, delta, -1);
+        }
+        if (phase == 0) {
+            acc += (double)fmaf(a.x, a.x, a.y * a.y);
+        } else {
+            const uint64_t x = gaddr(p, lb, hi, 0);
+            uint32_t l = st.lb0;
+            for (int q = 0; q < n; ++q) l ^= par(fs.rowe[q] & (uint32_t)x) << q;
+            dst[l] = mul2r(a, scale);
+        }
+    }
+    return acc;
 }
 
 }  // namespace frame

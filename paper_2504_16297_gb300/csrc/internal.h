@@ -125,6 +125,12 @@ struct DevFrameStage {
     uint16_t m[kTileMax];
     uint32_t ox[kMaxQubits];
     uint32_t last, lbf;              // last: the stage ends in logical order
+    // Sparse final store (a one-stage plan of a multi-tile state, every set from |0...0>): one CTA
+    // per state holds all nonzero amplitudes (they stay in the tile holding index 0), so it
+    // computes the norm, zero-fills the state and scatters each amplitude to its logical index
+    // l = R_end (x ^ b) (rowe = rows of A^-1 at the stage end). No other tile runs.
+    uint32_t sparse_final;
+    uint32_t rowe[kMaxQubits];
 };
 
 struct Plan {
@@ -250,6 +256,7 @@ struct EvolveArgs {
     uint8_t* status;
     void* frame_progs;               // frame kernel: one program per node of a launch
     int store_norm;                  // frame kernel: stage-end stores also leave tile norm partials in part
+    int sparse_final_stage;          // frame kernel: stage with the sparse final store (one CTA per state), or -1
     const float* scale_in;           // frame kernel: the last stage writes psi * scale_in[node] (norm known)
 };
 

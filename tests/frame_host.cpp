@@ -49,7 +49,7 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     float2* g = a.states + ((size_t)node << n);
     const uint32_t src = stage == (int)a.node_sstage[node] ? a.node_src[node] : node;
     const float2* gin = a.states_in + ((size_t)src << n);
-    builder_init(B, a, st, fs, node);
+    builder_init(B, a, st, fs, node, a.node_fresh[node] && stage == 0);
     build_segment(B, S, pool, a, st, kProgSteps, kProgPool);
     const Step* Sp = S;
     const Factor* poolp = pool;
@@ -77,6 +77,19 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
                 for (uint32_t t = 0; t < nthr; ++t) run_mix2(sp, tile.data(), tabs.data(), delta, tb, tau, t, nthr);
             } else if (sp.kind == ST_DIAG) {
                 for (uint32_t t = 0; t < nthr; ++t) run_diag(sp, tile.data(), tabs.data(), delta, tb, t, nthr);
+            } else if (sp.kind == ST_FINAL && fs.sparse_final) {
+                double part = 0;
+                for (uint32_t t = 0; t < nthr; ++t)
+                    part += run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, nullptr, 1.f, 0, t, nthr);
+                const double w = a.wmix[node] * part;
+                const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
+                const float scale = null ? 0.0f : (float)(1.0 / std::sqrt(part));
+                for (size_t i = 0; i < (1ull << n); ++i) g[i] = make_float2(0.f, 0.f);
+                if (!null)
+                    for (uint32_t t = 0; t < nthr; ++t)
+                        run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, g, scale, 1, t, nthr);
+                a.weights[node] = w;
+                a.status[node] = null ? 1 : 0;
             } else if (sp.kind == ST_STORE) {
                 double part = 0;
                 for (uint32_t t = 0; t < nthr; ++t)
@@ -194,6 +207,9 @@ int fh_evolve(uint32_t count, const uint32_t* off, const uint32_t* site, const u
     float2* oth = J > 1 ? other.data() : states;
     auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? oth : states; };
     const bool early = ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end;
+    int sparse_stage = -1;
+    for (uint32_t j = 0; j < J; ++j)
+        if (P.fstages[j].sparse_final) sparse_stage = (int)j;
     auto reduce = [&]() {
         for (uint32_t a = 0; a < count; ++a) {
             double T = 0;
@@ -212,10 +228,11 @@ int fh_evolve(uint32_t count, const uint32_t* off, const uint32_t* site, const u
         const float* sin = early && j + 1 == J ? scale.data() : nullptr;
         for (uint32_t a = 0; a < count; ++a)
             if (sstage[a] <= j)
-                for (uint32_t tau = 0; tau < (1u << ob); ++tau) run_cta(A, (int)j, j + 1 == J, a, tau, sin);
+                for (uint32_t tau = 0; tau < ((int)j == sparse_stage ? 1u : (1u << ob)); ++tau)
+                    run_cta(A, (int)j, j + 1 == J, a, tau, sin);
         if (A.store_norm) reduce();
     }
-    if (ob > 0 && !early) {
+    if (ob > 0 && !early && sparse_stage < 0) {
         reduce();
         for (uint32_t a = 0; a < count; ++a)
             for (size_t i = 0; i < (1ull << c.n); ++i) {

@@ -104,12 +104,32 @@ def test_deep_cx_network_restarts_the_frame(fh, oracle_mod):
 
 
 def test_syndrome_plan_and_states(fh, oracle_mod):
-    """One syndrome round on 17 qubits: the CX-heavy circuit fits one frame stage plus the
-    logical-order stage; the norm of the op-free last stage comes from the stage before it."""
+    """One syndrome round on 17 qubits: the CX-heavy circuit fits one frame stage; one CTA per
+    state holds every nonzero amplitude and scatters them in logical order (sparse final)."""
     circ = syndrome17(rounds=1)
     sets = oracle_mod.Oracle(circ).pts_topk(24, 1000)
     stages = _compare(fh, oracle_mod, circ, sets, 14, 1, check=range(0, 24, 3))
-    assert stages <= 2
+    assert stages == 1
+
+
+@pytest.mark.parametrize("n,tile_bits", [(10, 8), (12, 9)])
+def test_one_stage_multi_tile_sparse_final(fh, oracle_mod, n, tile_bits):
+    """A circuit whose mixes fit one tile on a multi-tile state: the one-stage plan with the
+    sparse final store (zero-fill, norm and scatter from the tile holding index 0)."""
+    b = CircuitBuilder(n)
+    ad = b.channel("AMPDAMP", 0.05)
+    dp = b.channel("DEPOL1", 0.03)
+    for q in range(3):
+        b.gate("H", [q]); b.noise(dp, [q])
+    for r in range(2):
+        for q in range(3, n):
+            b.gate("CX", [q % 3, q]); b.noise(ad, [q]); b.noise(dp, [q % 3])
+        b.gate("RZ", [1], (0.3 + r,))
+        b.gate("H", [2]); b.noise(ad, [2])
+    circ = b.build()
+    sets = oracle_mod.Oracle(circ).pts_proportional(30, 11, total_shots=300)
+    stages = _compare(fh, oracle_mod, circ, sets, tile_bits, 1)
+    assert stages == 1
 
 
 def _sink(n, seed):
