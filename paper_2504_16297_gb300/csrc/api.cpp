@@ -113,7 +113,8 @@ struct ptsbe_ctx {
         cudaEvent_t ev = nullptr;     // recorded after the slot's last copy
         bool used = false;
     };
-    static constexpr size_t kSlots = 128;
+    static constexpr size_t kSlots = 32;
+    static constexpr size_t kSlotMin = (size_t)2 << 20;   // per-step uploads stay below this
     Slot slots[kSlots];
     size_t next_slot = 0;
 
@@ -134,9 +135,9 @@ struct ptsbe_ctx {
         next_slot = (next_slot + 1) % kSlots;
         if (sl.used) PTSBE_CUDA(cudaEventSynchronize(sl.ev));
         if (sl.cap < bytes) {
-            if (sl.p) PTSBE_CUDA(cudaFreeHost(sl.p));
+            if (sl.p) PTSBE_CUDA(cudaFreeHost(sl.p));   // synchronises the device: rare (large uploads)
             sl.p = nullptr;
-            size_t cap = 64 * 1024;
+            size_t cap = kSlotMin;
             while (cap < bytes) cap *= 2;
             const cudaError_t e = cudaHostAlloc((void**)&sl.p, cap, cudaHostAllocDefault);
             if (e != cudaSuccess) { (void)cudaGetLastError(); sl.p = nullptr; sl.cap = 0; fail(PTSBE_ERR_OOM, "pinned staging allocation failed"); }
@@ -148,13 +149,6 @@ struct ptsbe_ctx {
         PTSBE_CUDA(cudaEventRecord(sl.ev, stream));
         sl.used = true;
         count_h2d(bytes);
-    }
-    template <class T>
-    T* upload(const std::vector<T>& v) {
-        if (v.empty()) return nullptr;
-        T* p = (T*)dalloc(v.size() * sizeof(T));
-        h2d(p, v.data(), v.size() * sizeof(T));
-        return p;
     }
     void free_staging() {
         for (Slot& sl : slots) {
@@ -217,22 +211,30 @@ int guarded(ptsbe_ctx* ctx, F&& f) {
 }
 
 void free_device_circuit(ptsbe_ctx* ctx, DeviceCircuit& d) {
-    for (void* p : {(void*)d.ops, (void*)d.micro, (void*)d.mats, (void*)d.chans, (void*)d.site_op, (void*)d.stages,
-                    (void*)d.groups, (void*)d.hi, (void*)d.fstages})
-        ctx->dfree(p);
+    ctx->dfree(d.base);
     d = DeviceCircuit{};
 }
 
+// All tables of a circuit plan in one allocation and one staged copy.
 void upload_circuit(ptsbe_ctx* ctx, const Circuit& c, const Plan& P, DeviceCircuit& d) {
-    d.ops = ctx->upload(c.dops);
-    d.micro = ctx->upload(c.dmicro);
-    d.mats = ctx->upload(c.dmats);
-    d.chans = ctx->upload(c.dchans);
-    d.site_op = ctx->upload(c.site_op);
-    d.stages = ctx->upload(P.stages);
-    d.groups = ctx->upload(P.groups);
-    d.hi = ctx->upload(P.hi);
-    d.fstages = ctx->upload(P.fstages);
+    std::vector<unsigned char> blob;
+    auto add = [&](const auto& v) {
+        const size_t off = (blob.size() + 255) & ~size_t(255);
+        const size_t bytes = v.size() * sizeof(v[0]);
+        blob.resize(off + std::max<size_t>(bytes, 1));
+        if (bytes) std::memcpy(blob.data() + off, v.data(), bytes);
+        return v.empty() ? SIZE_MAX : off;
+    };
+    const size_t o_ops = add(c.dops), o_micro = add(c.dmicro), o_mats = add(c.dmats), o_chans = add(c.dchans);
+    const size_t o_site = add(c.site_op), o_stages = add(P.stages), o_groups = add(P.groups), o_hi = add(P.hi);
+    const size_t o_fst = add(P.fstages);
+    unsigned char* base = (unsigned char*)ctx->dalloc(blob.size());
+    ctx->h2d(base, blob.data(), blob.size());
+    auto at = [&](size_t off) { return off == SIZE_MAX ? nullptr : (void*)(base + off); };
+    d.base = base;
+    d.ops = (DevOp*)at(o_ops); d.micro = (DevMicro*)at(o_micro); d.mats = (float2*)at(o_mats);
+    d.chans = (DevChannel*)at(o_chans); d.site_op = (uint32_t*)at(o_site); d.stages = (DevStage*)at(o_stages);
+    d.groups = (DevGroup*)at(o_groups); d.hi = (uint32_t*)at(o_hi); d.fstages = (DevFrameStage*)at(o_fst);
 }
 
 // Builds a blob of aligned arrays on the host and returns the device pointers after one upload.
@@ -248,10 +250,17 @@ struct Blob {
     }
 };
 
+// The set's (site, k) entries, one allocation and one staged copy (d_k follows d_site).
 void ensure_set_on_device(ptsbe_ctx* ctx, KSet& s) {
     if (s.d_site || s.site.empty()) return;
-    s.d_site = ctx->upload(s.site);
-    s.d_k = ctx->upload(s.k);
+    const size_t sb = s.site.size() * sizeof(uint32_t), kb = s.k.size();
+    std::vector<unsigned char> blob(sb + kb);
+    std::memcpy(blob.data(), s.site.data(), sb);
+    std::memcpy(blob.data() + sb, s.k.data(), kb);
+    unsigned char* base = (unsigned char*)ctx->dalloc(blob.size());
+    ctx->h2d(base, blob.data(), blob.size());
+    s.d_site = (uint32_t*)base;
+    s.d_k = base + sb;
 }
 
 }  // namespace
@@ -304,7 +313,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
             free_device_circuit(ctx, kv.second->dev); free_device_circuit(ctx, kv.second->dev_pershot);
             free_device_circuit(ctx, kv.second->dev_frame);
         }
-        for (auto& kv : ctx->sets) { ctx->dfree(kv.second->d_site); ctx->dfree(kv.second->d_k); }
+        for (auto& kv : ctx->sets) ctx->dfree(kv.second->d_site);   // d_k shares the allocation
         cudaStreamSynchronize(ctx->stream);
         ctx->free_staging();
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -415,8 +424,7 @@ int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id) {
         KSet& s = ctx->set(set_id);
         if (ctx->has_device() && s.d_site) {
             ctx->use_device();
-            ctx->dfree(s.d_site);                        // stream-ordered: after the launches that use them
-            ctx->dfree(s.d_k);
+            ctx->dfree(s.d_site);                        // stream-ordered (d_k shares the allocation)
         }
         ctx->sets.erase(set_id);
     });

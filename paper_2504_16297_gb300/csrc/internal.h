@@ -157,6 +157,7 @@ struct HostChannel {
 };
 
 struct DeviceCircuit {
+    void* base = nullptr;            // one device allocation holding every table below
     DevOp* ops = nullptr;
     DevMicro* micro = nullptr;
     float2* mats = nullptr;
