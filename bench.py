@@ -295,7 +295,7 @@ def main():
         barrier()
         if instrument:
             P.set_timing(True)
-            for cls in range(4):
+            for cls in range(6):
                 P.timing(cls, reset=True)
         l0 = capi.ptsbe_kernel_launches()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -309,7 +309,7 @@ def main():
         launches = capi.ptsbe_kernel_launches() - l0
         kern = {}
         if instrument:
-            for cls, name in enumerate(["evolve_stage", "evolve_finalize", "sample", "pershot"]):
+            for cls, name in enumerate(["evolve_stage", "evolve_finalize", "sample", "pershot", "evolve_program", "sample_light"]):
                 kms, kl, kb = P.timing(cls, reset=True)
                 if kl:
                     kern[name] = {"ms": kms, "launches": kl, "bytes": kb}

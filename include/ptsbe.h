@@ -320,9 +320,11 @@ PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
 enum {
     PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
     PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* norm reduction / renormalisation of ptsbe_evolve_batch   */
-    PTSBE_TIMER_SAMPLE = 2,           /* ptsbe_sample_shots                                       */
+    PTSBE_TIMER_SAMPLE = 2,           /* ptsbe_sample_shots: cluster and global samplers          */
     PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
-    PTSBE_TIMER_CLASSES = 4
+    PTSBE_TIMER_EVOLVE_PROGRAM = 4,   /* per-set program prepass of the deferred-frame kernel     */
+    PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */
+    PTSBE_TIMER_CLASSES = 6
 };
 
 /* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and

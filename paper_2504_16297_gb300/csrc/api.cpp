@@ -570,6 +570,10 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             double bytes = 0;
             for (size_t t = L.first; t < L.first + L.second; ++t)
                 bytes += (fresh[lists[t]] && j == 0) ? sbytes : 2 * sbytes;
+            if (frame)
+                ctx->timed(PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
+                    launch_frame_program(A, (int)j, d_lists + L.first, L.second, ctx->stream);
+                });
             ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
                 launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
             });
@@ -631,7 +635,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
             if (nl) {
                 const double bytes = 8.0 * (double)(1ull << n) * (double)nl * 1.1;
-                ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
+                ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
             }
             if (nh) {
                 uint64_t heavy_shots = 0;

@@ -744,12 +744,7 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                                                                        : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = (frm && stage == a.sparse_final_stage) ? 1u : 1u << (a.n - a.tb);
     frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
-    if (frm) {
-        if (!progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");
-        k_frame_program<<<(n_nodes + kProgThreads - 1) / kProgThreads, kProgThreads, 0, s>>>(a, stage, d_nodes, n_nodes, progs);
-        PTSBE_CUDA(cudaGetLastError());
-        count_launch();
-    }
+    if (frm && !progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");
     for (uint32_t b = 0; b < n_nodes; b += 65535) {
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
         if (regs)
@@ -761,6 +756,15 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }
+}
+
+void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s) {
+    if (n_nodes == 0) return;
+    frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
+    if (!progs) fail(PTSBE_ERR_INVALID, "frame program prepass launched without workspace");
+    k_frame_program<<<(n_nodes + kProgThreads - 1) / kProgThreads, kProgThreads, 0, s>>>(a, stage, d_nodes, n_nodes, progs);
+    PTSBE_CUDA(cudaGetLastError());
+    count_launch();
 }
 
 void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s) {

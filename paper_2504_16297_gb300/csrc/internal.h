@@ -264,6 +264,9 @@ struct EvolveArgs {
 // kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
                          cudaStream_t s, int kernel = 0);
+// Frame kernel (kernel 0 or 3): builds the per-node programs of a stage; must precede
+// launch_evolve_stage of the same stage and nodes.
+void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s);
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 size_t evolve_frame_program_bytes();   // workspace per node of a frame-kernel launch
