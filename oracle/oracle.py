@@ -74,6 +74,7 @@ def _load():
     lib.or_shot_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64]; lib.or_shot_uniform.restype = C.c_double
     lib.or_pershot.argtypes = [vp, C.c_uint64, C.c_uint64, vp]; lib.or_pershot.restype = C.c_uint64
     lib.or_loss.argtypes = [vp, vp, C.c_uint32, _u64p, _f64p, vp]; lib.or_loss.restype = C.c_double
+    lib.or_loss_diag.argtypes = [vp, vp, C.c_uint32, _u64p, _f64p, vp, vp]; lib.or_loss_diag.restype = C.c_double
     return lib
 
 
@@ -217,12 +218,78 @@ class Oracle:
             return out, kr[: self.n_sites]
         return lib().or_pershot(self.h, seed, j, None)
 
-    def loss(self, sets: KrausSets, masks, coeffs, per_set=False):
-        masks = np.ascontiguousarray(masks, np.uint64)
-        coeffs = np.ascontiguousarray(coeffs, np.float64)
+    def loss(self, sets: KrausSets, masks, coeffs, per_set=False, diag=None):
+        """L = (1/N) sum_a mult_a <psi~_a|O|psi~_a> / q_a over the whole set (N = sum of mult), O the
+        Z-string terms plus an optional dense diagonal; per_set: also e_a / q_a for every set."""
+        masks = np.ascontiguousarray(masks, np.uint64).reshape(-1)
+        coeffs = np.ascontiguousarray(coeffs, np.float64).reshape(-1)
+        if masks.size == 0:
+            masks, coeffs = np.zeros(1, np.uint64), np.zeros(1, np.float64)
         ps = np.zeros(max(sets.count, 1), np.float64)
-        v = lib().or_loss(self.h, sets.handle, len(coeffs), masks, coeffs, ps.ctypes.data)
+        if diag is None:
+            v = lib().or_loss(self.h, sets.handle, len(coeffs), masks, coeffs, ps.ctypes.data)
+        else:
+            d = np.ascontiguousarray(diag, np.float64)
+            if d.size != 1 << self.n:
+                raise ValueError("diag needs 2^n values")
+            v = lib().or_loss_diag(self.h, sets.handle, len(coeffs), masks, coeffs, d.ctypes.data, ps.ctypes.data)
         return (v, ps[: sets.count]) if per_set else v
+
+
+# Gate codes whose matrices depend on op params: RX, RY, RZ (theta) and U3 (theta, phi, lambda).
+PARAM_GATES = {9: 1, 10: 1, 11: 1, 12: 3}
+
+
+def gate_param_slots(circ):
+    """(op index, param index) of every gate angle the circuit's matrices depend on."""
+    out = []
+    for i in range(circ.n_ops):
+        kind, gid = int(circ.op_ints[i][0]), int(circ.op_ints[i][1])
+        if kind == 0 and gid in PARAM_GATES:
+            out += [(i, j) for j in range(PARAM_GATES[gid])]
+    return out
+
+
+def noise_param_slots(circ):
+    """Channel indices whose Kraus operators are a function of their strength (the named kinds)."""
+    return [j for j in range(len(circ.ch_params)) if int(circ.ch_ints[j][0]) != 5]
+
+
+def _with_params(circ, op_params=None, ch_params=None):
+    import dataclasses
+    return dataclasses.replace(circ, op_params=circ.op_params if op_params is None else op_params,
+                               ch_params=circ.ch_params if ch_params is None else ch_params)
+
+
+def loss_grad_fd(circ, sets, masks, coeffs, h=1e-4, diag=None):
+    """Central finite differences of the fixed-set estimator (Sec. 3 with the Kraus sets and their
+    nominal q_alpha held fixed) with respect to every gate angle and every named channel strength.
+
+    Each perturbed circuit is a new oracle circuit (its matrices and Kraus operators rebuilt from
+    the perturbed parameters); the sets, their multiplicities and q_alpha stay those of `sets`.
+    Returns (per_set e_a/q_a [count], dper_params [n_ops, 3, count], dper_noise [n_ch, count]);
+    the gradient of the loss over a range of sets is the mult-weighted mean of these rows."""
+    base = Oracle(circ)
+    _, per = base.loss(sets, masks, coeffs, per_set=True, diag=diag)
+    dp = np.zeros((circ.n_ops, 3, sets.count))
+    dn = np.zeros((len(circ.ch_params), sets.count))
+    for (i, j) in gate_param_slots(circ):
+        vals = []
+        for sgn in (+1.0, -1.0):
+            P = np.array(circ.op_params, np.float64, copy=True)
+            P[i, j] += sgn * h
+            _, ps = Oracle(_with_params(circ, op_params=P)).loss(sets, masks, coeffs, per_set=True, diag=diag)
+            vals.append(ps)
+        dp[i, j] = (vals[0] - vals[1]) / (2 * h)
+    for c in noise_param_slots(circ):
+        vals = []
+        for sgn in (+1.0, -1.0):
+            P = np.array(circ.ch_params, np.float64, copy=True)
+            P[c] += sgn * h
+            _, ps = Oracle(_with_params(circ, ch_params=P)).loss(sets, masks, coeffs, per_set=True, diag=diag)
+            vals.append(ps)
+        dn[c] = (vals[0] - vals[1]) / (2 * h)
+    return per, dp, dn
 
 
 def philox(ctr, key):

@@ -17,6 +17,9 @@
  *   proportional shot reallocation p'_a = p_a / sum p, probability bands,
  *     most-likely combinations above a cutoff                         -- Sec. 3.1
  *   batched execution: prepare each Kraus set once, draw all m_a shots -- Sec. 3
+ *   fixed-set estimator of a diagonal observable (sets and q_a held fixed), the loss the
+ *     adjoint backward differentiates; its gradient here is central finite differences
+ *     (oracle.py, loss_grad_fd)                                       -- Sec. 3, Sec. 2.2
  *   counter-based RNG: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  *     numbers: as easy as 1, 2, 3", SC'11)
  *
@@ -959,8 +962,9 @@ OR_API uint64_t or_pershot(const or_circuit* c, uint64_t seed, uint64_t j, uint8
 /* this is an importance-sampling estimate of Tr(O rho); its derivatives with respect to   */
 /* gate angles and channel strengths are what the backward computes.                        */
 /* ------------------------------------------------------------------------------------ */
-OR_API double or_loss(const or_circuit* c, const or_set* s, uint32_t nterms, const uint64_t* masks, const double* coeffs,
-                      double* per_set /* optional [count] */) {
+/* Shared body: O(x) = diag[x] when diag is given, plus the Z-string terms. */
+static double loss_body(const or_circuit* c, const or_set* s, uint32_t nterms, const uint64_t* masks,
+                        const double* coeffs, const double* diag, double* per_set) {
     uint64_t N = 1ull << c->n;
     cplx* psi = (cplx*)malloc(N * sizeof(cplx));
     double total = 0, Ntot = 0;
@@ -981,7 +985,7 @@ OR_API double or_loss(const or_circuit* c, const or_set* s, uint32_t nterms, con
         double e = 0;
         for (uint64_t x = 0; x < N; x++) {
             double pr = creal(psi[x]) * creal(psi[x]) + cimag(psi[x]) * cimag(psi[x]);
-            double ov = 0;
+            double ov = diag ? diag[x] : 0.0;
             for (uint32_t t = 0; t < nterms; t++) ov += (__builtin_popcountll(x & masks[t]) & 1) ? -coeffs[t] : coeffs[t];
             e += pr * ov;
         }
@@ -991,4 +995,16 @@ OR_API double or_loss(const or_circuit* c, const or_set* s, uint32_t nterms, con
     }
     free(psi);
     return total / Ntot;
+}
+
+OR_API double or_loss(const or_circuit* c, const or_set* s, uint32_t nterms, const uint64_t* masks, const double* coeffs,
+                      double* per_set /* optional [count] */) {
+    return loss_body(c, s, nterms, masks, coeffs, NULL, per_set);
+}
+
+/* Same estimator for a caller-given diagonal observable O = sum_x diag[x] |x><x| (2^n values,
+ * e.g. the indicator of one outcome for the gradient of an outcome probability), plus terms. */
+OR_API double or_loss_diag(const or_circuit* c, const or_set* s, uint32_t nterms, const uint64_t* masks,
+                           const double* coeffs, const double* diag, double* per_set) {
+    return loss_body(c, s, nterms, masks, coeffs, diag, per_set);
 }
