@@ -276,6 +276,47 @@ PTSBE_API int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32
                                          uint32_t* d_bits, uint64_t d_bits_capacity);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Adjoint gradients of the fixed-set estimator (Sec. 3 with the Kraus sets held fixed)        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Diagonal observable O = sum_t coeffs[t] prod_{q in masks[t]} Z_q  +  sum_x diag[x] |x><x|.
+ * masks/coeffs: host arrays of n_terms entries (bit q of a mask = qubit q); diag: optional device
+ * float64 [2^n] indexed by the logical basis index (e.g. the indicator of one outcome, for the
+ * gradient of an outcome probability). masks and coeffs are copied during the call; d_diag is
+ * read by the call's kernels and must stay valid until they complete on the stream. */
+typedef struct {
+    uint32_t n_terms;
+    const uint64_t* masks;
+    const double* coeffs;
+    const double* d_diag;
+} ptsbe_observable;
+
+/* Loss and gradients of the importance-weighted estimator over sets [first, first + count) of
+ * set_id (Sec. 3: each set alpha prepared once; its nominal probability q_alpha and multiplicity
+ * mult_alpha held fixed):
+ *   L = (1 / N) sum_alpha mult_alpha <psi~_alpha| O |psi~_alpha> / q_alpha,  N = sum of mult_alpha,
+ * psi~_alpha the unnormalised state with every Kraus operator applied as given (K_{s,k}, Sec. 2.2).
+ * With the sets drawn by PTS this estimates Tr(O rho) and its gradient that of Tr(O rho); with
+ * count = 1 it is the single trajectory's observable. circuit_id gives the gate angles and channel
+ * strengths to differentiate at; it must have the structure of the set's circuit (same qubits,
+ * operations, targets, channel kinds and Kraus counts), its parameters may differ.
+ * Outputs (device, caller-owned, each may be NULL):
+ *   d_loss        float64 [1]
+ *   d_per_set     float64 [count]: <psi~_alpha|O|psi~_alpha> / q_alpha
+ *   d_grad_params float64 [n_ops][3]: dL / d ops[i].params[j] (RX/RY/RZ theta, U3 theta, phi,
+ *                 lambda; 0 for every other operation and parameter)
+ *   d_grad_noise  float64 [n_channels]: dL / d channels[c].param (the named kinds; 0 for CUSTOM)
+ * checkpoint_every: 0 stores a set's state only before operators it cannot invert (a damping
+ * jump); c > 0 also every c fused blocks (the un-computed state is replaced by the stored one
+ * there). n_qubits <= 16, at most 64 (site, k) entries per set.
+ * Asynchronous on the context stream. Errors: PTSBE_ERR_INVALID (range, structure, null
+ * observable, a set with q_alpha = 0), PTSBE_ERR_UNSUPPORTED (n > 16, longer sets),
+ * PTSBE_ERR_OOM, PTSBE_ERR_CUDA. */
+PTSBE_API int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
+                             const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss,
+                             double* d_per_set, double* d_grad_params, double* d_grad_noise);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Traditional trajectories (Algorithm 1), one prepared state per shot, for comparison        */
 /* ---------------------------------------------------------------------------------------- */
 
@@ -324,7 +365,8 @@ enum {
     PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
     PTSBE_TIMER_EVOLVE_PROGRAM = 4,   /* per-set program prepass of the deferred-frame kernel     */
     PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */
-    PTSBE_TIMER_CLASSES = 6
+    PTSBE_TIMER_BACKWARD = 6,         /* ptsbe_backward                                           */
+    PTSBE_TIMER_CLASSES = 7
 };
 
 /* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and

@@ -261,19 +261,20 @@ def _with_params(circ, op_params=None, ch_params=None):
                                ch_params=circ.ch_params if ch_params is None else ch_params)
 
 
-def loss_grad_fd(circ, sets, masks, coeffs, h=1e-4, diag=None):
+def loss_grad_fd(circ, sets, masks, coeffs, h=1e-4, diag=None, param_slots=None, noise_slots=None):
     """Central finite differences of the fixed-set estimator (Sec. 3 with the Kraus sets and their
     nominal q_alpha held fixed) with respect to every gate angle and every named channel strength.
 
     Each perturbed circuit is a new oracle circuit (its matrices and Kraus operators rebuilt from
     the perturbed parameters); the sets, their multiplicities and q_alpha stay those of `sets`.
     Returns (per_set e_a/q_a [count], dper_params [n_ops, 3, count], dper_noise [n_ch, count]);
-    the gradient of the loss over a range of sets is the mult-weighted mean of these rows."""
+    the gradient of the loss over a range of sets is the mult-weighted mean of these rows.
+    param_slots / noise_slots restrict the differences to those (op, j) pairs / channels (others 0)."""
     base = Oracle(circ)
     _, per = base.loss(sets, masks, coeffs, per_set=True, diag=diag)
     dp = np.zeros((circ.n_ops, 3, sets.count))
     dn = np.zeros((len(circ.ch_params), sets.count))
-    for (i, j) in gate_param_slots(circ):
+    for (i, j) in (gate_param_slots(circ) if param_slots is None else param_slots):
         vals = []
         for sgn in (+1.0, -1.0):
             P = np.array(circ.op_params, np.float64, copy=True)
@@ -281,7 +282,7 @@ def loss_grad_fd(circ, sets, masks, coeffs, h=1e-4, diag=None):
             _, ps = Oracle(_with_params(circ, op_params=P)).loss(sets, masks, coeffs, per_set=True, diag=diag)
             vals.append(ps)
         dp[i, j] = (vals[0] - vals[1]) / (2 * h)
-    for c in noise_param_slots(circ):
+    for c in (noise_param_slots(circ) if noise_slots is None else noise_slots):
         vals = []
         for sgn in (+1.0, -1.0):
             P = np.array(circ.ch_params, np.float64, copy=True)

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libptsbe.so")
 
-CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp"]
-CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu"]
+CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp", "backward.cpp"]
+CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu", "backward.cu"]
 HEADERS = ["internal.h", "philox.h", "tile_ops.cuh", "frame.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,7 +17,8 @@ PTSBE_PTS_PROPORTIONAL, PTSBE_PTS_TOPK, PTSBE_PTS_BAND, PTSBE_PTS_TARGETED, PTSB
 PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVEN = range(4)
 PTSBE_EVOLVE_PREFIX_REUSE = 1
 PTSBE_OPT_EVOLVE_KERNEL = 0
-PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT = range(4)
+(PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
+ PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD) = range(7)
 
 
 class ptsbe_op(C.Structure):
@@ -42,6 +43,11 @@ class ptsbe_set_view(C.Structure):
     _fields_ = [("offsets", C.c_void_p), ("sites", C.c_void_p), ("kidx", C.c_void_p),
                 ("mult", C.c_void_p), ("q", C.c_void_p), ("shots", C.c_void_p),
                 ("shot_offsets", C.c_void_p)]
+
+
+class ptsbe_observable(C.Structure):
+    _fields_ = [("n_terms", C.c_uint32), ("masks", C.POINTER(C.c_uint64)), ("coeffs", C.POINTER(C.c_double)),
+                ("d_diag", C.c_void_p)]
 
 
 class PtsbeError(RuntimeError):
@@ -76,6 +82,9 @@ _PROTOS = {
                                      C.c_uint64, C.c_void_p, C.c_uint64]),
     "ptsbe_sample_shots_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p,
                                              C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]),
+    "ptsbe_backward": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.POINTER(ptsbe_observable), C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -184,6 +193,12 @@ def ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bi
 
 def ptsbe_sample_shots_noalloc(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity):
     check(ctx, load().ptsbe_sample_shots_noalloc(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity))
+
+
+def ptsbe_backward(ctx, circuit_id, set_id, first, count, obs: ptsbe_observable, checkpoint_every, d_loss,
+                   d_per_set, d_grad_params, d_grad_noise):
+    check(ctx, load().ptsbe_backward(ctx, circuit_id, set_id, first, count, C.byref(obs), checkpoint_every, d_loss,
+                                     d_per_set, d_grad_params, d_grad_noise))
 
 
 def ptsbe_kernel_launches() -> int:

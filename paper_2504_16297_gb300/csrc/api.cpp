@@ -263,6 +263,37 @@ void ensure_set_on_device(ptsbe_ctx* ctx, KSet& s) {
     s.d_k = base + sb;
 }
 
+// The backward plan's tables in one allocation and one staged copy.
+void upload_backward_plan(ptsbe_ctx* ctx, BwPlan& P) {
+    std::vector<unsigned char> buf;
+    Blob b(buf);
+    const size_t o_st = b.add(P.steps), o_it = b.add(P.items), o_me = b.add(P.members), o_po = b.add(P.pool);
+    const size_t o_p64 = b.add(P.pool64), o_si = b.add(P.site_item), o_sm = b.add(P.site_mem);
+    const size_t o_ds = b.add(P.dslot_out), o_pf = b.add(P.pos_final);
+    unsigned char* base = (unsigned char*)ctx->dalloc(buf.size());
+    ctx->h2d(base, buf.data(), buf.size());
+    P.dev = base;
+    P.d_steps = (const BwStep*)(base + o_st); P.d_items = (const BwItem*)(base + o_it);
+    P.d_members = (const BwMember*)(base + o_me); P.d_pool = (const float2*)(base + o_po);
+    P.d_pool64 = (const double*)(base + o_p64); P.d_site_item = (const uint32_t*)(base + o_si);
+    P.d_site_mem = (const uint32_t*)(base + o_sm); P.d_dslot_out = (const uint32_t*)(base + o_ds);
+    P.d_pos_final = (const uint8_t*)(base + o_pf);
+}
+
+// Same qubits, operations, targets, channel kinds and Kraus counts (parameters may differ).
+void check_same_structure(const Circuit& a, const Circuit& b) {
+    bool same = a.n == b.n && a.ops.size() == b.ops.size() && a.ch.size() == b.ch.size();
+    for (size_t i = 0; same && i < a.ops.size(); ++i) {
+        const ptsbe_op &x = a.ops[i], &y = b.ops[i];
+        same = x.kind == y.kind && x.id == y.id && x.n_targets == y.n_targets && x.targets[0] == y.targets[0] &&
+               (x.n_targets == 1 || x.targets[1] == y.targets[1]);
+        if (same && x.kind == PTSBE_OP_GATE && (x.id == PTSBE_G_U1 || x.id == PTSBE_G_U2)) same = x.params[0] == y.params[0];
+    }
+    for (size_t c = 0; same && c < a.ch.size(); ++c)
+        same = a.ch[c].kind == b.ch[c].kind && a.ch[c].arity == b.ch[c].arity && a.ch[c].nk == b.ch[c].nk;
+    if (!same) fail(PTSBE_ERR_INVALID, "circuit does not have the structure of the set's circuit");
+}
+
 }  // namespace
 
 extern "C" {
@@ -312,6 +343,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         for (auto& kv : ctx->circuits) {
             free_device_circuit(ctx, kv.second->dev); free_device_circuit(ctx, kv.second->dev_pershot);
             free_device_circuit(ctx, kv.second->dev_frame);
+            ctx->dfree(kv.second->bw.dev);
         }
         for (auto& kv : ctx->sets) ctx->dfree(kv.second->d_site);   // d_k shares the allocation
         cudaStreamSynchronize(ctx->stream);
@@ -381,6 +413,8 @@ int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
             free_device_circuit(ctx, c.dev);            // stream-ordered: after the launches that use them
             free_device_circuit(ctx, c.dev_pershot);
             free_device_circuit(ctx, c.dev_frame);
+            ctx->dfree(c.bw.dev);
+            c.bw.dev = nullptr;
         }
         ctx->circuits.erase(circuit_id);
     });
@@ -757,6 +791,161 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
                 if (m) launch_sample_global(A, a, alpha, 0, m, o, ctx->stream);
             }
         }
+    });
+}
+
+int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
+                   const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss, double* d_per_set,
+                   double* d_grad_params, double* d_grad_noise) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        ctx->use_device();
+        if (!obs) fail(PTSBE_ERR_INVALID, "null observable");
+        if (obs->n_terms && (!obs->masks || !obs->coeffs)) fail(PTSBE_ERR_INVALID, "observable terms without masks or coefficients");
+        KSet& S = ctx->set(set_id);
+        Circuit& c = ctx->circuit(circuit_id);
+        check_same_structure(c, ctx->circuit(S.circuit));
+        if ((uint64_t)first + count > S.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (c.n > (uint32_t)kBwMaxQubits) fail(PTSBE_ERR_UNSUPPORTED, "backward handles at most 16 qubits");
+        const int n = (int)c.n;
+        for (uint32_t t = 0; t < obs->n_terms; ++t)
+            if (obs->masks[t] >> n) fail(PTSBE_ERR_INVALID, "observable mask names a qubit >= n");
+        if (!c.bw.built) {
+            make_backward_plan(c, c.bw);
+            upload_backward_plan(ctx, c.bw);
+        }
+        const BwPlan& P = c.bw;
+        const uint32_t nch = (uint32_t)c.ch.size();
+        // per-set weights: W = mult s^2 / (N q), s^2 = prod over unit-mixture sites of q_{s,k}
+        std::vector<uint32_t> ebeg(count + 1);
+        std::vector<double> W(count), s2q(count), gmix((size_t)count * std::max<uint32_t>(nch, 1), 0.0);
+        std::vector<uint32_t> nsites_ch(nch, 0), nerr_ch(nch, 0);
+        for (uint32_t s = 0; s < c.site_ch.size(); ++s) nsites_ch[c.site_ch[s]]++;
+        double Nmult = 0;
+        for (uint32_t a = 0; a < count; ++a) Nmult += (double)S.mult[first + a];
+        if (count && !(Nmult > 0)) fail(PTSBE_ERR_INVALID, "sets with zero total multiplicity");
+        uint32_t base_ck = (uint32_t)P.defsing_items.size();
+        if (checkpoint_every) base_ck += (uint32_t)((P.items.size() + checkpoint_every - 1) / checkpoint_every);
+        uint32_t extra_ck = 0;
+        std::vector<uint32_t> seen_items;
+        for (uint32_t a = 0; a < count; ++a) {
+            const uint32_t g = first + a;
+            const uint32_t e0 = S.off[g], e1 = S.off[g + 1];
+            if (e1 - e0 > (uint32_t)kBwMaxErr) fail(PTSBE_ERR_UNSUPPORTED, "backward handles sets of at most 64 entries");
+            if (!(S.q[g] > 0)) fail(PTSBE_ERR_INVALID, "a set with q_alpha = 0");
+            ebeg[a] = e0;
+            double s2 = 1.0;
+            std::fill(nerr_ch.begin(), nerr_ch.end(), 0u);
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t ch = c.site_ch[S.site[e]];
+                nerr_ch[ch]++;
+            }
+            // product over every unit-mixture site, factored as (all variant 0) x (ratios at entries)
+            bool ratio_ok = P.P0mix > 0;
+            for (uint32_t e = e0; e < e1 && ratio_ok; ++e) {
+                const HostChannel& H = c.ch[c.site_ch[S.site[e]]];
+                if (bw_unit_channel(H)) s2 *= H.q[S.k[e]] / H.q[0];
+            }
+            if (ratio_ok) s2 *= P.P0mix;
+            else {
+                s2 = 1.0;
+                uint32_t e = e0;
+                for (uint32_t s = 0; s < c.site_ch.size(); ++s) {
+                    uint32_t k = 0;
+                    if (e < e1 && S.site[e] == s) k = S.k[e++];
+                    const HostChannel& H = c.ch[c.site_ch[s]];
+                    if (bw_unit_channel(H)) s2 *= H.q[k];
+                }
+            }
+            W[a] = (double)S.mult[g] * s2 / (Nmult * S.q[g]);
+            s2q[a] = s2 / S.q[g];
+            for (uint32_t ch = 0; ch < nch; ++ch) {
+                const HostChannel& H = c.ch[ch];
+                const bool pauli_kind = H.kind == PTSBE_CH_DEPOL1 || H.kind == PTSBE_CH_DEPOL2 ||
+                                        H.kind == PTSBE_CH_BITFLIP || H.kind == PTSBE_CH_PHASEFLIP;
+                if (!pauli_kind) continue;
+                const double p = H.param;
+                const uint32_t n1 = nerr_ch[ch], n0 = nsites_ch[ch] - n1;
+                double gv = 0;   // d log(prod q_k) / dp: q_0 = 1 - p, q_k = p / (d^2 - 1) or p
+                if (n0) gv += -(double)n0 / (1.0 - p);
+                if (n1) gv += (double)n1 / p;
+                gmix[(size_t)a * nch + ch] = gv;
+            }
+            // items of this set whose chosen variants cannot be inverted (beyond the default ones)
+            seen_items.clear();
+            uint32_t ex = 0;
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t it = P.site_item[S.site[e]];
+                if (std::find(seen_items.begin(), seen_items.end(), it) != seen_items.end()) continue;
+                seen_items.push_back(it);
+                const BwItem& I = P.items[it];
+                if (I.defsing) continue;
+                bool sing = false;
+                for (uint32_t m = I.mbeg; m < I.mend && !sing; ++m) {
+                    uint32_t k = 0;
+                    for (uint32_t f = e0; f < e1; ++f)
+                        if (P.site_mem[S.site[f]] == m) k = S.k[f];
+                    sing = (P.members[m].sing >> k) & 1u;
+                }
+                ex += sing ? 1u : 0u;
+            }
+            extra_ck = std::max(extra_ck, ex);
+        }
+        ebeg[count] = count ? S.off[first + count] : 0;
+        std::vector<uint32_t> pmask(std::max<uint32_t>(obs->n_terms, 1), 0u);
+        std::vector<double> coeff(std::max<uint32_t>(obs->n_terms, 1), 0.0);
+        for (uint32_t t = 0; t < obs->n_terms; ++t) {
+            uint32_t m = 0;
+            for (int q = 0; q < n; ++q)
+                if ((obs->masks[t] >> q) & 1u) m |= 1u << P.pos_final[q];
+            pmask[t] = m;
+            coeff[t] = obs->coeffs[t];
+        }
+        ensure_set_on_device(ctx, S);
+        // per-call tables: one upload
+        std::vector<unsigned char>& hb = ctx->host_blob;
+        Blob blob(hb);
+        const size_t o_eb = blob.add(ebeg), o_w = blob.add(W), o_s2 = blob.add(s2q), o_g = blob.add(gmix);
+        const size_t o_pm = blob.add(pmask), o_co = blob.add(coeff);
+        unsigned char* tab = (unsigned char*)ctx->dalloc(hb.size());
+        ctx->h2d(tab, hb.data(), hb.size());
+        // workspace
+        const int nl = P.nl, cl = 1 << (n - nl);
+        const uint32_t nslots = count ? backward_slots(n, count, ctx->n_sm) : 1u;
+        const uint32_t maxck = base_ck + extra_ck;
+        const size_t ng = P.ngs, nd = std::max<uint32_t>(P.ndslots, 1);
+        const size_t b_ck = (size_t)nslots * maxck * ((size_t)8 << n);
+        const size_t b_g = (size_t)nslots * cl * ng * 32 * sizeof(double);
+        const size_t b_acc = ((size_t)nslots * (nd + std::max<uint32_t>(nch, 1) + 1) + nd) * sizeof(double);
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        unsigned char* wsp = (unsigned char*)ctx->dalloc(al(b_ck) + 2 * al(b_g) + al(b_acc) + 256);
+        unsigned char* zero_begin = wsp + al(b_ck);
+        PTSBE_CUDA(cudaMemsetAsync(zero_begin, 0, 2 * al(b_g) + al(b_acc), ctx->stream));
+        BwArgs A{};
+        A.n = n; A.nl = nl; A.cl = cl; A.nslots = nslots; A.count = count;
+        A.steps = P.d_steps; A.nsteps = (uint32_t)P.steps.size(); A.first_diff_step = P.first_diff_step;
+        A.items = P.d_items; A.nitems = (uint32_t)P.items.size(); A.members = P.d_members;
+        A.pool = P.d_pool; A.pool64 = P.d_pool64; A.site_item = P.d_site_item; A.site_mem = P.d_site_mem;
+        A.dslot_out = P.d_dslot_out; A.pos_final = P.d_pos_final;
+        A.ent_site = S.d_site; A.ent_k = S.d_k;
+        A.ebeg = (const uint32_t*)(tab + o_eb); A.W = (const double*)(tab + o_w); A.s2q = (const double*)(tab + o_s2);
+        A.gmix = (const double*)(tab + o_g); A.nch = (int)nch;
+        A.nterms = obs->n_terms; A.pmask = (const uint32_t*)(tab + o_pm); A.coeff = (const double*)(tab + o_co);
+        A.diag = obs->d_diag;
+        A.ckpt_every = checkpoint_every; A.maxck = maxck; A.ngs = (uint32_t)ng; A.ndslots = P.ndslots;
+        A.n_ops = (uint32_t)c.ops.size();
+        A.ckpt = (float2*)wsp;
+        A.Ga = (double*)zero_begin;
+        A.Gbar = (double*)(zero_begin + al(b_g));
+        double* acc = (double*)(zero_begin + 2 * al(b_g));
+        A.acc_err = acc;
+        A.acc_mix = acc + (size_t)nslots * nd;
+        A.acc_loss = A.acc_mix + (size_t)nslots * std::max<uint32_t>(nch, 1);
+        A.dtot = A.acc_loss + nslots;
+        A.per_set = d_per_set; A.loss = d_loss; A.grad_params = d_grad_params; A.grad_noise = d_grad_noise;
+        ctx->timed(PTSBE_TIMER_BACKWARD, 0.0, [&] { launch_backward(A, ctx->stream); });
+        ctx->dfree(wsp);
+        ctx->dfree(tab);
     });
 }
 

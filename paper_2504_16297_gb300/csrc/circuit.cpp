@@ -73,6 +73,10 @@ void pauli(int a, cd* m) {
 }  // namespace
 
 // Builds the Kraus operators, nominal probabilities and unitary-mixture data of one channel.
+void gate_matrix_of(uint32_t g, const double* params, const double* custom, cd* m, int& dim) {
+    gate_matrix(g, params, custom, m, dim);
+}
+
 void build_channel(const ptsbe_channel& in, HostChannel& c) {
     c.kind = in.kind; c.arity = in.arity; c.nk = in.n_kraus; c.param = in.param;
     if (in.arity < 1 || in.arity > 2) fail(PTSBE_ERR_INVALID, "channel arity must be 1 or 2");
@@ -399,6 +403,10 @@ bool is_identity(const cd* m, int d) {
 }
 
 }  // namespace
+
+void embed_pair(const cd* m, int dim, const uint32_t* qs, uint32_t q0, uint32_t q1, cd* out) {
+    embed2(m, dim, qs, q0, q1, out);
+}
 
 // Linear part over GF(2) of a two-qubit permutation on x = 2 l_a + l_b, as the images of e_b and
 // e_a packed in 4 bits; CX (control a) and SWAP have their own, every other gate the identity's.

@@ -143,6 +143,68 @@ struct Plan {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Adjoint backward. The circuit becomes a list of fused blocks ("items", the consecutive
+// operators of one or two qubits, noise sites included); a set's state lives in the shared memory
+// of a thread-block cluster (local bits = low qubit positions, cluster rank = high positions) and
+// the plan swaps qubit positions between CTAs so that every item acts on local bits.
+// ---------------------------------------------------------------------------------------------
+constexpr int kBwMaxErr = 64;        // (site, k) entries per set
+constexpr int kBwMaxMembers = 48;    // operators fused into one item
+constexpr int kBwLocalBits = 13;     // local bits of a cluster CTA (two complex64 vectors: 128 KiB)
+constexpr int kBwMaxQubits = 16;     // clusters of at most 8 CTAs
+constexpr uint32_t kBwNone = 0xFFFFFFFFu;
+
+struct BwMember {
+    uint32_t mat;      // FP32 pool block of variant 0 (variant k at mat + k); a block = 16 float2
+    uint32_t inv;      // FP32 pool block of the inverse of variant 0 (zeros where singular)
+    uint32_t m64;      // FP64 pool block of variant 0 (variant k at m64 + k)
+    uint32_t d64;      // FP64 pool block of the first derivative matrix (gate: angle j at d64 + j;
+                       // general channel: d(variant k)/d strength at d64 + k)
+    uint32_t sing;     // bit k: variant k cannot be inverted (its input comes from a checkpoint)
+    uint32_t dslot;    // gradient slot of the first angle (gate) or of the site (general channel)
+    uint8_t noise, nk, nd, pad;   // nd: gate angles, or 1 for a differentiable site, else 0
+};
+
+struct BwItem {
+    uint8_t nq, p0, p1, diff;   // 1 or 2 qubits at physical positions p0 (high matrix bit), p1
+    uint32_t mbeg, mend;        // members
+    uint32_t def, definv;       // FP32 pool blocks of the default product (every variant 0) and inverse
+    uint32_t defsing;           // the default product cannot be inverted
+    uint32_t gslot;             // slot of its outer-product accumulator (differentiable items)
+};
+
+struct BwStep {
+    uint32_t kind;              // 0 item, 1 swap local position a with global position g
+    uint32_t a, g, item;
+};
+
+struct BwPlan {
+    bool built = false;
+    int nl = 0;
+    std::vector<BwStep> steps;
+    std::vector<BwItem> items;
+    std::vector<BwMember> members;
+    std::vector<float2> pool;            // 16 per block
+    std::vector<double> pool64;          // 32 per block (complex as re, im)
+    std::vector<uint32_t> site_item, site_mem;
+    std::vector<uint32_t> dslot_out;     // dslot -> 3 op + j (gate angle) or 0x80000000 | channel (site)
+    std::vector<uint8_t> pos_final;      // logical qubit -> physical position after the last step
+    uint32_t ngs = 0, ndslots = 0, first_diff_step = 0;
+    std::vector<uint32_t> defsing_items; // items whose default product cannot be inverted
+    double P0mix = 1.0;                  // prod over unitary-mixture sites of q_{s,0}
+    void* dev = nullptr;                 // device copy (one allocation)
+    const BwStep* d_steps = nullptr;
+    const BwItem* d_items = nullptr;
+    const BwMember* d_members = nullptr;
+    const float2* d_pool = nullptr;
+    const double* d_pool64 = nullptr;
+    const uint32_t* d_site_item = nullptr;
+    const uint32_t* d_site_mem = nullptr;
+    const uint32_t* d_dslot_out = nullptr;
+    const uint8_t* d_pos_final = nullptr;
+};
+
+// ---------------------------------------------------------------------------------------------
 // Host-side circuit and Kraus-set records.
 // ---------------------------------------------------------------------------------------------
 using cd = std::complex<double>;
@@ -155,6 +217,10 @@ struct HostChannel {
     std::vector<cd> U;       // unitary-mixture: K_k / sqrt(q_k)
     bool mixture = false;
 };
+
+// Channels the adjoint backward applies as U_k = K_k / sqrt(q_k) with the scale q_k kept apart:
+// unitary mixtures other than damping (whose derivative is not a multiple of K_k).
+inline bool bw_unit_channel(const HostChannel& ch) { return ch.mixture && ch.kind != PTSBE_CH_AMPDAMP; }
 
 struct DeviceCircuit {
     void* base = nullptr;            // one device allocation holding every table below
@@ -187,6 +253,7 @@ struct Circuit {
     Plan plan;                       // PTSBE evolution plan (ops inside each stage's qubit set)
     Plan plan_pershot;               // Algorithm 1 plan (stage break before every general site)
     Plan plan_frame;                 // deferred-frame plan (mixing directions inside each tile)
+    BwPlan bw;                       // adjoint backward plan (built on the first backward call)
     bool pershot_planned = false;
     bool frame_planned = false;
     DeviceCircuit dev;
@@ -214,6 +281,9 @@ void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uin
 double set_key(const Circuit& c, const uint32_t* sites, const uint8_t* ks, uint32_t len);
 
 // Registration and planning (host) -----------------------------------------------------------------
+void gate_matrix_of(uint32_t g, const double* params, const double* custom, cd* m, int& dim);
+void embed_pair(const cd* m, int dim, const uint32_t* qs, uint32_t q0, uint32_t q1, cd* out);
+void make_backward_plan(const Circuit& c, BwPlan& P);
 void build_channel(const ptsbe_channel& in, HostChannel& c);
 void register_ops(Circuit& c, const ptsbe_op* ops, uint64_t n_ops, const double* custom, uint32_t n_custom);
 void build_device_ops(Circuit& c);
@@ -311,6 +381,50 @@ struct PershotArgs {
     uint64_t n_sites;
 };
 void launch_pershot_stage(const PershotArgs& a, int stage, uint32_t batch, cudaStream_t s);
+// Adjoint backward kernels (backward.cu).
+struct BwArgs {
+    int n, nl, cl;
+    uint32_t nslots, count;
+    const BwStep* steps; uint32_t nsteps, first_diff_step;
+    const BwItem* items; uint32_t nitems;
+    const BwMember* members;
+    const float2* pool;
+    const double* pool64;
+    const uint32_t* site_item;
+    const uint32_t* site_mem;
+    const uint32_t* dslot_out;
+    const uint8_t* pos_final;
+    // Kraus-set entries (whole set) and per-set tables of the range
+    const uint32_t* ent_site;
+    const uint8_t* ent_k;
+    const uint32_t* ebeg;          // [count + 1] absolute entry offsets
+    const double* W;               // mult s^2 / (N q): weight of a set's <phi|O|phi>
+    const double* s2q;             // s^2 / q: per-set output factor
+    const double* gmix;            // [count][nch]: d log s^2 / d strength of channel c
+    int nch;
+    // observable (physical masks of the final layout)
+    uint32_t nterms;
+    const uint32_t* pmask;
+    const double* coeff;
+    const double* diag;            // logical-index diagonal or nullptr
+    uint32_t ckpt_every, maxck, ngs, ndslots, n_ops;
+    // workspace
+    float2* ckpt;                  // [nslots][maxck][2^n]
+    double* Ga;                    // [nslots][cl][ngs][32]: a set's outer products
+    double* Gbar;                  // [nslots][cl][ngs][32]: weighted sums over default items
+    double* acc_err;               // [nslots][ndslots]
+    double* acc_mix;               // [nslots][nch]
+    double* acc_loss;              // [nslots]
+    double* dtot;                  // [ndslots] finish-kernel scratch
+    // outputs
+    double* per_set;
+    double* loss;
+    double* grad_params;
+    double* grad_noise;
+};
+uint32_t backward_slots(int n, uint32_t count, int n_sm);
+void launch_backward(const BwArgs& a, cudaStream_t s);
+
 int sample_cluster_max_qubits();
 int sample_light_max_qubits();
 // States with at most this many shots go to the one-CTA-per-state light sampler (15 <= n <= 20).

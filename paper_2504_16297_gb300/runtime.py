@@ -185,5 +185,23 @@ class Ptsbe:
         capi.ptsbe_sample_shots(self.ctx, info.set_id, first, count, _ptr(states), _ptr(status), seed, _ptr(bits),
                                 bits.numel())
 
+    def backward(self, cid: int, info: KrausSetInfo, first: int, count: int, masks=(), coeffs=(), diag=None,
+                 checkpoint_every: int = 0, loss=None, per_set=None, grad_params=None, grad_noise=None):
+        """Adjoint loss and gradients of the fixed-set estimator over sets [first, first + count) at the
+        parameters of circuit `cid` (same structure as the set's circuit). Outputs are float64 device
+        tensors (loss [1], per_set [count], grad_params [n_ops, 3], grad_noise [n_channels]); any may
+        be None. masks / coeffs: Z-string terms; diag: float64 device tensor [2^n] or None."""
+        m = np.ascontiguousarray(np.asarray(masks, np.uint64).reshape(-1))
+        c = np.ascontiguousarray(np.asarray(coeffs, np.float64).reshape(-1))
+        if m.size != c.size:
+            raise ValueError("masks and coeffs differ in length")
+        obs = capi.ptsbe_observable()
+        obs.n_terms = int(m.size)
+        obs.masks = m.ctypes.data_as(C.POINTER(C.c_uint64)) if m.size else None
+        obs.coeffs = c.ctypes.data_as(C.POINTER(C.c_double)) if c.size else None
+        obs.d_diag = _ptr(diag)
+        capi.ptsbe_backward(self.ctx, cid, info.set_id, first, count, obs, checkpoint_every, _ptr(loss), _ptr(per_set),
+                            _ptr(grad_params), _ptr(grad_noise))
+
     def pershot(self, cid: int, seed: int, first_shot: int, n_shots: int, bits, kraus=None):
         capi.ptsbe_pershot_run(self.ctx, cid, seed, first_shot, n_shots, _ptr(bits), _ptr(kraus))
