@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
     ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "frame", "sweep", "registers"])
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the adjoint-backward measurement (16-qubit ansatz, 4,096 samples)")
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
     return ap.parse_args()
@@ -178,6 +180,53 @@ def oracle_estimate(budget_s: float, k: int, shots: int, seed: int):
             f"preparations ({t_ev / n_ev:.3f}s each), CDF build {t_cdf * 1e3:.1f} ms, {m} shots "
             f"({t_shot * 1e9:.0f} ns each); extrapolated to {sets.count} states + {shots} shots = {total:.0f}s")
     return shots / total, desc
+
+
+def backward_leg(P, dev, reps: int = 3, cpu: bool = True):
+    """Adjoint gradients of the 16-qubit, 8-layer noisy ansatz (256 angles, damping and
+    depolarising strengths) over 4,096 proportional samples: loss L = sum_i c_i <Z_i Z_i+1> of the
+    fixed-set estimator and its 258 derivatives, timed with CUDA events on the launch stream."""
+    import torch
+    from workloads import ansatz
+    circ = ansatz()
+    n = circ.n_qubits
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=2004, nsamples=4096, total_shots=4096)
+    masks = np.array([(1 << i) | (1 << (i + 1)) for i in range(n - 1)], np.uint64)
+    coeffs = np.asarray(circ.meta["zz_coeffs"])
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gp = torch.empty((circ.n_ops, 3), dtype=torch.float64, device=dev)
+    gn = torch.empty(len(circ.ch_params), dtype=torch.float64, device=dev)
+
+    def once():
+        P.backward(cid, info, 0, info.count, masks, coeffs, loss=loss, grad_params=gp, grad_noise=gn)
+    once()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out = {"workload": "ansatz16_8layers_4096samples", "sets": info.count, "ms": ms,
+           "sets_per_s": info.count / (ms / 1e3), "gradient_entries": 256 + 2, "loss": float(loss.cpu()[0]),
+           "kernel": "k_backward (cluster of 8 CTAs per set, state and adjoint in DSMEM) + k_backward_finish"}
+    if cpu:
+        # oracle: one fixed-set loss evaluation of one set; a central-difference gradient needs
+        # 2 x 258 + 1 of them per set
+        from oracle import oracle as orc
+        o = orc.Oracle(circ)
+        one = o.pts_targeted([info.entries(info.count // 2)], shots=np.zeros(1, np.uint64))
+        t0 = time.perf_counter()
+        o.loss(one, masks, coeffs)
+        t = time.perf_counter() - t0
+        out["cpu_fd_oracle"] = {"s_per_loss_eval": t, "s_per_set_gradient": t * (2 * 258 + 1), "cores": 1,
+                                "kind": "oracle central differences, extrapolated from one loss evaluation"}
+    P.release_set(info)
+    P.release_circuit(cid)
+    return out
 
 
 def run_reference(args):
@@ -346,6 +395,10 @@ def main():
         pershot = {"value": args.pershot_shots / (ps_ms / 1e3), "unit": "shots/s", "shots": args.pershot_shots,
                    "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot"}
 
+    bw = None
+    if not args.no_backward:
+        bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+
     ms_step = ms / args.steps
     value = job_throughput(world, M, ms_step)
     e2e_value = job_throughput(world, M, ms_e2e / steps_e2e)
@@ -385,6 +438,7 @@ def main():
                     "d2h_bytes_per_step": M * 4 + K * 9},
             "gpu_launches": launches,
             "clocks": clk,
+            "backward": bw,
         }
         print(json.dumps(out), flush=True)
     if dist:
