@@ -590,9 +590,10 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         const bool early_norm = frame && ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end &&
                                 launches[J - 2].second == count;
         A.sparse_final_stage = -1;
+        A.small_bits = 0;
         if (frame)
             for (uint32_t j = 0; j < J; ++j)
-                if (P.fstages[j].sparse_final) A.sparse_final_stage = (int)j;
+                if (P.fstages[j].sparse_final) { A.sparse_final_stage = (int)j; A.small_bits = (int)P.fstages[j].sbits; }
         for (uint32_t j = 0; j < J; ++j) {
             const auto& L = launches[j];
             if (L.second == 0) continue;

@@ -679,6 +679,30 @@ uint32_t frame_dirs(const Circuit& c, size_t i, const uint32_t* col) {
     return d;
 }
 
+// The individual global directions op i may mix along (one per mixing target), for the current
+// columns; the span of these vectors bounds the support of a state that starts from |0...0>.
+int frame_dir_vectors(const Circuit& c, size_t i, const uint32_t* col, uint32_t* out) {
+    const DevOp& o = c.dops[i];
+    int k = 0;
+    if (o.kind == DOP_NOISE) {
+        const DevChannel& ch = c.dchans[o.ch];
+        bool m0 = false, m1 = false;
+        for (uint32_t u = ch.micro_off[0]; u < ch.micro_off[ch.nk]; ++u) {
+            const DevMicro& mi = c.dmicro[u];
+            if (!mixing_kind(mi.kind)) continue;
+            if (mi.operand != 1) m0 = true;
+            if (mi.operand != 0) m1 = true;
+        }
+        if (m0) out[k++] = col[o.q0];
+        if (m1) out[k++] = col[o.q1];
+        return k;
+    }
+    if (!frame_dirs(c, i, col)) return 0;
+    out[k++] = col[o.q0];
+    if (o.nt == 2) out[k++] = col[o.q1];
+    return k;
+}
+
 void frame_linear(const Circuit& c, size_t i, uint32_t* col) {
     const DevOp& o = c.dops[i];
     if (o.kind == DOP_CX) col[o.q0] ^= col[o.q1];
@@ -761,7 +785,11 @@ void close_frame_stage(Plan& P, const Circuit& c, uint32_t T, uint32_t b, uint32
 
 }  // namespace
 
-Plan make_frame_plan(const Circuit& c, int tile_bits) {
+namespace {
+
+// The frame plan with the first stage entered in layout entry0 (columns: global image of each
+// logical bit); later stages after a logical-order store restart at the identity.
+Plan frame_plan_from(const Circuit& c, int tile_bits, const uint32_t* entry0) {
     Plan P;
     const int n = (int)c.n;
     if (n > 32) fail(PTSBE_ERR_UNSUPPORTED, "more than 32 qubits");
@@ -770,7 +798,7 @@ Plan make_frame_plan(const Circuit& c, int tile_bits) {
     const size_t nops = c.ops.size();
     P.op_stage.assign(nops, 0);
     uint32_t col[kMaxQubits], entry[kMaxQubits];
-    for (int q = 0; q < n; ++q) col[q] = entry[q] = 1u << q;
+    for (int q = 0; q < n; ++q) col[q] = entry[q] = entry0[q];
     const uint32_t all = n == 32 ? ~0u : ((1u << n) - 1u);
     if (n <= tile_bits) {
         close_frame_stage(P, c, all, 0, (uint32_t)nops, entry, true, P.lb);
@@ -833,6 +861,52 @@ Plan make_frame_plan(const Circuit& c, int tile_bits) {
     }
     close_logical((uint32_t)nops);
     return P;
+}
+
+}  // namespace
+
+Plan make_frame_plan(const Circuit& c, int tile_bits) {
+    const int n = (int)c.n;
+    uint32_t id[kMaxQubits];
+    for (int q = 0; q < kMaxQubits; ++q) id[q] = q < 32 ? 1u << q : 0u;
+    Plan P = frame_plan_from(c, tile_bits, id);
+    if (!(P.stages.size() == 1 && P.fstages[0].sparse_final)) return P;
+    // One stage from |0...0>: the stored amplitudes only ever move along the mixing directions,
+    // so they stay in the span V of those vectors. Entering the stage in a layout T with
+    // T V = span(e_0 .. e_{D-1}) puts every nonzero amplitude at a tile address below 2^D, which
+    // lets the kernel hold the support in a small buffer.
+    uint32_t col[kMaxQubits], ech[kMaxQubits], dv[4];
+    int piv[kMaxQubits], D = 0;
+    for (int q = 0; q < n; ++q) col[q] = 1u << q;
+    for (size_t i = 0; i < c.ops.size(); ++i) {
+        const int k = frame_dir_vectors(c, i, col, dv);
+        for (int j = 0; j < k; ++j) {
+            uint32_t x = dv[j];
+            for (int t = 0; t < D; ++t) if ((x >> piv[t]) & 1u) x ^= ech[t];
+            if (!x) continue;
+            if (D == kMaxQubits) break;
+            ech[D] = x; piv[D] = __builtin_ctz(x); ++D;
+        }
+        frame_linear(c, i, col);
+    }
+    if (D > kSmallSupportBits) return P;
+    // columns of V: the echelon vectors, then the unit vectors of the non-pivot bits; T = V^-1
+    uint32_t V[kMaxQubits], R[kMaxQubits], T[kMaxQubits];
+    uint32_t used = 0;
+    for (int t = 0; t < D; ++t) { V[t] = ech[t]; used |= 1u << piv[t]; }
+    int m = D;
+    for (int x = 0; x < n; ++x) if (!((used >> x) & 1u)) V[m++] = 1u << x;
+    invert_cols(n, V, R);                                  // rows of V^-1
+    for (int q = 0; q < n; ++q) {                          // column q of V^-1
+        uint32_t v = 0;
+        for (int x = 0; x < n; ++x) if ((R[x] >> q) & 1u) v |= 1u << x;
+        T[q] = v;
+    }
+    for (int q = n; q < kMaxQubits; ++q) T[q] = 0;
+    Plan Q = frame_plan_from(c, tile_bits, T);
+    if (!(Q.stages.size() == 1 && Q.fstages[0].sparse_final)) return P;
+    Q.fstages[0].sbits = (uint32_t)std::max(D, 1);
+    return Q;
 }
 
 }  // namespace ptsbe

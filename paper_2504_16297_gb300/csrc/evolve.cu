@@ -110,7 +110,11 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
 
 // Frame kernel: same work as k_evolve_stage, with permutations and diagonals deferred (frame.cuh).
 // Thread 0 builds the program of the stage while the other warps bring the tile in.
-__host__ __device__ inline size_t frame_tab_offset(int tb, int lb) { return (((size_t)8 << tb) + ((size_t)4 << (tb - lb)) + 15) & ~(size_t)15; }
+// Dynamic shared memory of the frame kernel: tile (tamps complex64), hi table, factor tables.
+__host__ __device__ inline size_t frame_tab_offset_amps(uint32_t tamps, int tb, int lb) {
+    return ((size_t)8 * tamps + ((size_t)4 << (tb - lb)) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t frame_tab_offset(int tb, int lb) { return frame_tab_offset_amps(1u << tb, tb, lb); }
 
 // One thread per node of a launch builds the node's program for the stage (the first segment, and
 // the builder state a tile CTA needs to continue when the program is longer).
@@ -139,8 +143,15 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t 
 }
 
 constexpr int kFrameThreads = 512;   // 128 registers per thread: grouped mixes stay in registers
-__global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
-                                                       const frame::Program* __restrict__ progs) {
+// SMALL: a sparse final stage whose support lies below tile address 2^fs.sbits (the plan entered
+// the stage in a layout that maps the mixing directions to the low bits); the tile buffer holds
+// only that prefix, so several CTAs share an SM and one CTA's stores overlap another's passes.
+constexpr int kFrameSmallThreads = 128;
+constexpr int kFrameSmallCtas = 3;
+template <bool SMALL>
+__global__ void __launch_bounds__(SMALL ? kFrameSmallThreads : kFrameThreads, SMALL ? kFrameSmallCtas : 1)
+k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
+               const frame::Program* __restrict__ progs) {
     using namespace frame;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevStage st;
@@ -153,11 +164,12 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     float2* tile = reinterpret_cast<float2*>(smem);
-    uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
-    float2* tabs = reinterpret_cast<float2*>(smem + frame_tab_offset(tb, lb));
     copy_words(&st, a.stages + stage_idx, sizeof(DevStage), tid, nthr);
     copy_words(&fs, a.fstages + stage_idx, sizeof(DevFrameStage), tid, nthr);
     __syncthreads();
+    const uint32_t tamps = SMALL ? (1u << fs.sbits) : (1u << tb);
+    uint32_t* hi = reinterpret_cast<uint32_t*>(tile + tamps);
+    float2* tabs = reinterpret_cast<float2*>(smem + frame_tab_offset_amps(tamps, tb, lb));
     for (uint32_t i = tid; i < (1u << (tb - lb)); i += nthr) hi[i] = a.hi[st.hi_off + i];
     const uint32_t node = nodes[blockIdx.y];
     const uint32_t tau = blockIdx.x;
@@ -185,11 +197,11 @@ __global__ void __launch_bounds__(kFrameThreads, 1) k_evolve_frame(EvolveArgs a,
         if (B.npool <= (uint32_t)kMaxPool) copy_words(pool, P.pool, B.npool * (uint32_t)sizeof(Factor), tid, 32);
         if (B.nsteps <= (uint32_t)kMaxSteps) copy_words(S, P.S, B.nsteps * (uint32_t)sizeof(Step), tid, 32);
     } else {
-        const uint32_t t = tid - 32, nt = nthr - 32, nv = 1u << (tb - 1);
+        const uint32_t t = tid - 32, nt = nthr - 32, nv = tamps >> 1;
         float4* tile4 = reinterpret_cast<float4*>(tile);
         if (zero_tile) {
             // never read
-        } else if (fresh) {
+        } else if (fresh || SMALL) {
             for (uint32_t v = t; v < nv; v += nt)
                 tile4[v] = make_float4((v == 0 && tau == 0) ? 1.0f : 0.0f, 0.f, 0.f, 0.f);
         } else {
@@ -720,6 +732,9 @@ size_t evolve_frame_program_bytes() { return sizeof(frame::Program); }
 size_t evolve_frame_smem_bytes(int tb, int lb) {
     return frame_tab_offset(tb, lb) + (size_t)frame::kMaxTabs * frame::kTabSize * sizeof(float2);
 }
+size_t evolve_frame_small_smem_bytes(int sbits, int tb, int lb) {
+    return frame_tab_offset_amps(1u << sbits, tb, lb) + (size_t)frame::kMaxTabs * frame::kTabSize * sizeof(float2);
+}
 size_t evolve_rb_smem_bytes(int tb, int lb) { return ((evolve_smem_bytes(tb, lb) + 15) & ~(size_t)15) + 8 * (size_t)kMaxStream; }
 
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
@@ -733,15 +748,20 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                                         (int)evolve_smem_bytes(kTileMax, 1)));
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_rb_smem_bytes(kTileMax, 1)));
-        PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_frame, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_frame<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_frame_smem_bytes(kTileMax, 1)));
+        PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_frame<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)evolve_frame_small_smem_bytes(kSmallSupportBits, kTileMax, 1)));
         configured = true;
     }
     const bool regs = a.tb >= kRegBits && kernel == 2;
     const bool frm = kernel == 0 || kernel == 3;
-    const int threads = regs ? (1 << (a.tb - kRegBits)) : frm ? std::min(evolve_threads(a.tb), kFrameThreads) : evolve_threads(a.tb);
-    const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : frm ? evolve_frame_smem_bytes(a.tb, a.lb)
-                                                                       : evolve_smem_bytes(a.tb, a.lb);
+    const bool small = frm && stage == a.sparse_final_stage && a.small_bits > 0;
+    if (small && a.small_bits > kSmallSupportBits) fail(PTSBE_ERR_INVALID, "small frame kernel: support too large");
+    const int threads = regs ? (1 << (a.tb - kRegBits)) : small ? kFrameSmallThreads
+                      : frm ? std::min(evolve_threads(a.tb), kFrameThreads) : evolve_threads(a.tb);
+    const size_t smem = regs ? evolve_rb_smem_bytes(a.tb, a.lb) : small ? evolve_frame_small_smem_bytes(a.small_bits, a.tb, a.lb)
+                      : frm ? evolve_frame_smem_bytes(a.tb, a.lb) : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = (frm && stage == a.sparse_final_stage) ? 1u : 1u << (a.n - a.tb);
     frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
     if (frm && !progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");
@@ -749,8 +769,10 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
         if (regs)
             k_evolve_rb<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
+        else if (small)
+            k_evolve_frame<true><<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b, progs + b);
         else if (frm)
-            k_evolve_frame<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b, progs + b);
+            k_evolve_frame<false><<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b, progs + b);
         else
             k_evolve_stage<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
         PTSBE_CUDA(cudaGetLastError());

@@ -17,6 +17,8 @@ constexpr int kMaxKraus = 16;
 constexpr int kMaxQubits = 32;
 constexpr int kTileMax = 14;      // largest tile: 2^14 complex64 = 128 KiB of shared memory
 constexpr int kLowBits = 4;       // low qubits every tile keeps contiguous (16 amplitudes = 128 B)
+constexpr int kSmallSupportBits = 10;   // sparse final stages with a support of at most 2^10 amplitudes
+                                        // run the small-buffer frame kernel
 
 // ---------------------------------------------------------------------------------------------
 // Errors: thrown inside the library, turned into a status at the ABI boundary.
@@ -131,6 +133,10 @@ struct DevFrameStage {
     // l = R_end (x ^ b) (rowe = rows of A^-1 at the stage end). No other tile runs.
     uint32_t sparse_final;
     uint32_t rowe[kMaxQubits];
+    // Sparse final stage whose nonzero amplitudes all sit at tile addresses below 2^sbits (the
+    // stage is entered in a layout that maps the span of its mixing directions to the low bits);
+    // 0 when only the tile bound holds.
+    uint32_t sbits;
 };
 
 struct Plan {
@@ -329,6 +335,7 @@ struct EvolveArgs {
     int store_norm;                  // frame kernel: stage-end stores also leave tile norm partials in part
     int sparse_final_stage;          // frame kernel: stage with the sparse final store (one CTA per state), or -1
     const float* scale_in;           // frame kernel: the last stage writes psi * scale_in[node] (norm known)
+    int small_bits;                  // frame kernel: support bits of the sparse final stage (0: tile-sized buffer)
 };
 
 // kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame

@@ -32,10 +32,21 @@ uint32_t threads_for(int tb) {
     return t < 64 ? 64 : (t > 512 ? 512 : t);
 }
 
+int g_guard_violations = 0;   // small-buffer stages: tile entries past 2^sbits that were touched
+
 void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t tau, const float* scale_in) {
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
-    const uint32_t nthr = threads_for(tb);
+    // the small-buffer kernel (sparse final stage with a support bound) runs 128 threads
+    const bool small = a.fstages[stage].sparse_final && a.fstages[stage].sbits > 0;
+    const uint32_t nthr = small ? 128u : threads_for(tb);
+    const uint32_t tamps = small ? 1u << a.fstages[stage].sbits : 1u << tb;
     std::vector<float2> tile(1u << tb), tabs((size_t)kMaxTabs * kTabSize);
+    // past the buffer the kernel would have: a sentinel that must survive the whole CTA, and that
+    // turns any read into NaN in the result
+    const uint32_t kSentinel = 0x7fc0a5a5u;
+    float sent;
+    std::memcpy(&sent, &kSentinel, 4);
+    for (uint32_t v = tamps; v < (1u << tb); ++v) tile[v] = make_float2(sent, sent);
     static Builder B;
     static Step S[kProgSteps];
     static Factor pool[kProgPool];
@@ -55,7 +66,7 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     const Factor* poolp = pool;
     const bool fresh = a.node_fresh[node] && stage == 0;
     const bool zero_tile = fresh && tau != 0;        // as in the kernel: only tile 0 is nonzero
-    for (uint32_t v = 0; v < (1u << (tb - 1)); ++v) {
+    for (uint32_t v = 0; v < (tamps >> 1); ++v) {
         if (fresh) {
             tile[2 * v] = make_float2((v == 0 && tau == 0) ? 1.f : 0.f, 0.f);
             tile[2 * v + 1] = make_float2(0.f, 0.f);
@@ -124,6 +135,12 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
         Sp = S2;
         poolp = pool2;
     }
+    for (uint32_t v = tamps; v < (1u << tb); ++v) {
+        uint32_t bx, by;
+        std::memcpy(&bx, &tile[v].x, 4);
+        std::memcpy(&by, &tile[v].y, 4);
+        if (bx != kSentinel || by != kSentinel) ++g_guard_violations;
+    }
 }
 
 }  // namespace
@@ -148,6 +165,13 @@ int fh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
 
 // Sets in CSR (off, site, k) with nominal probabilities q; the same schedule as ptsbe_evolve_batch
 // (prefix reuse, alternating buffers, early norm when the last stage has no ops).
+// Support bits of the plan's sparse final stage (0: none, or no support bound).
+int fh_sparse_bits() {
+    for (const DevFrameStage& f : g_plan.fstages)
+        if (f.sparse_final) return (int)f.sbits;
+    return 0;
+}
+
 int fh_evolve(uint32_t count, const uint32_t* off, const uint32_t* site, const uint8_t* kk, const double* q, int reuse,
               float2* states, double* weights, uint8_t* status) {
     const Circuit& c = g_circ;
@@ -221,6 +245,7 @@ int fh_evolve(uint32_t count, const uint32_t* off, const uint32_t* site, const u
             status[a] = null ? 1 : 0;
         }
     };
+    g_guard_violations = 0;
     for (uint32_t j = 0; j < J; ++j) {
         A.states = out_buf(j);
         A.states_in = j > 0 ? out_buf(j - 1) : out_buf(j);
@@ -240,7 +265,7 @@ int fh_evolve(uint32_t count, const uint32_t* off, const uint32_t* site, const u
                 states[((size_t)a << c.n) + i].y *= scale[a];
             }
     }
-    return 0;
+    return g_guard_violations ? -100 : 0;
 }
 
 }  // extern "C"

@@ -112,6 +112,18 @@ def test_syndrome_plan_and_states(fh, oracle_mod):
     assert stages == 1
 
 
+def test_syndrome_support_in_low_bits(fh, oracle_mod):
+    """The 3-round syndrome circuit: the span of its mixing directions has dimension 8, so the
+    stage is entered in a layout that puts it on the low 8 tile bits and every nonzero amplitude
+    lives below tile address 256 (the small-buffer kernel); the harness fills the rest of the tile
+    with a sentinel and fails if any step touches it."""
+    circ = syndrome17(rounds=3)
+    sets = oracle_mod.Oracle(circ).pts_topk(300, 3000)
+    stages = _compare(fh, oracle_mod, circ, sets, 14, 1, check=range(0, 300, 23))
+    assert stages == 1
+    assert fh.fh_sparse_bits() == 8
+
+
 @pytest.mark.parametrize("n,tile_bits", [(10, 8), (12, 9)])
 def test_one_stage_multi_tile_sparse_final(fh, oracle_mod, n, tile_bits):
     """A circuit whose mixes fit one tile on a multi-tile state: the one-stage plan with the
