@@ -438,7 +438,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "qubits": n, "kraus_sets": K, "shots": M, "pts": "topk",
-                       "prefix_reuse": True, "amplitudes": "complex64, FP64 norms and CDF",
+                       "prefix_reuse": True, "amplitudes": "complex64, FP64 norms, CDF in 2^-62 fixed point (exact integer sums)",
                        "l2": "inputs larger than L2 (10.5 GB of states per step)",
                        "parallelism": f"{world} independent replicas (weak scaling)"},
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,

@@ -246,9 +246,13 @@ PTSBE_API int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
 
 /* Draws all m_alpha shots of sets [first, first + count) from their prepared states (Sec. 3,
  * "sampling all m_alpha desired quantum bitstrings at once"). For state alpha with
- * P_i = |psi_i|^2 and C its FP64 inclusive prefix, T = C[2^n - 1]: shot j uses
+ * P_i = |psi_i|^2 and C its inclusive prefix, T = C[2^n - 1]: shot j uses
  * u = U53(Philox(seed; j_lo, j_hi, alpha, 2)) (alpha = index of the set within set_id) and returns
- * the smallest i with u*T < C[i] (2^n - 1 if none). Outputs:
+ * the smallest i with u*T < C[i] (2^n - 1 if none). Arithmetic: P_i is the FP32 value
+ * re^2 + im^2, held as floor(P_i 2^62) in 64-bit integers; C and T are exact integer sums of those
+ * and u*T is floor(m T / 2^53) for u = m / 2^53, so the prefix carries no rounding (resolution
+ * 2^-62 against 2^-53 for an FP64 running sum near 1). States must have T < 4 (normalised states
+ * from ptsbe_evolve_batch have T = 1). Outputs:
  *   d_bits  uint32 [sum of m_alpha over the range], set-major: shot j of set first+a lands at
  *           shot_offsets[first+a] - shot_offsets[first] + j. Null states (d_status 1) yield
  *           0xFFFFFFFF. d_bits_capacity = number of uint32 slots available.

@@ -680,7 +680,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             }
         }
         if (n > sample_cluster_max_qubits()) {
-            A.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * sizeof(double));
+            A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
             for (uint32_t a = 0; a < count; ++a) {
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
@@ -779,13 +779,13 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
             PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
             launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream);
         } else {
-            const size_t need = sample_global_scratch_doubles(n) * sizeof(double);
+            const size_t need = sample_global_scratch_doubles(n) * 8;
             if (need > cap)
                 fail(PTSBE_ERR_UNSUPPORTED, std::to_string(n) + "-qubit states need " + std::to_string(need) +
                                                 " bytes of CDF workspace; the fixed scratch holds " + std::to_string(cap) +
                                                 " (at most 21 qubits)");
             ctx->use_device();
-            A.scratch = (double*)noalloc_scratch(ctx->device);
+            A.scratch = (unsigned long long*)noalloc_scratch(ctx->device);
             for (uint32_t a = 0; a < count; ++a) {
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
@@ -977,7 +977,7 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
         SampleArgs R{};
         R.n = n; R.states = A.states; R.status = nullptr; R.seed = seed;
         const bool cluster = n <= sample_cluster_max_qubits();
-        if (!cluster) R.scratch = (double*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * sizeof(double));
+        if (!cluster) R.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
         std::vector<SampleItem> items;
         for (uint64_t b0 = 0; b0 < n_shots; b0 += batch) {
             const uint32_t cnt = (uint32_t)std::min<uint64_t>(batch, n_shots - b0);

@@ -363,8 +363,8 @@ struct SampleArgs {
     const uint8_t* status;
     uint64_t seed;
     uint32_t* bits;
-    double* scratch;                 // n > 17: per-state global CDF workspace
-    double* scratch_tot;             // n > 17: per-block totals / offsets
+    unsigned long long* scratch;     // n > 17: per-state global CDF workspace (2^-62 fixed point)
+    unsigned long long* scratch_tot; // n > 17: per-block totals / offsets
 };
 
 void launch_sample_cluster(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);

@@ -1,20 +1,21 @@
 // Batched shot sampling (Sec. 3: all m_alpha shots of a prepared state are drawn at once).
 //
-// For a state with P_i = |psi_i|^2 and FP64 inclusive prefix C, T = C[last], shot j draws
-// u = U53(Philox(seed; j_lo, j_hi, alpha, 2)) and returns the smallest i with u*T < C[i].
+// For a state with P_i = |psi_i|^2 and inclusive prefix C, T = C[last], shot j draws
+// u = U53(Philox(seed; j_lo, j_hi, alpha, 2)) and returns the smallest i with u*T < C[i]. The
+// prefix is kept in 2^-62 fixed point (64-bit integers): exact sums on the integer pipe, and
+// u*T = floor(m T / 2^53) exactly for u = m / 2^53.
 //
-// n <= 17: the whole FP64 CDF is held on chip. A thread-block cluster of CL = 2^(n-14) CTAs
-// (one CTA when n <= 14) owns one state: CTA r builds the prefix of amplitudes
-// [r*2^sb, (r+1)*2^sb) in its shared memory, the cluster exchanges slice totals over distributed
-// shared memory (DSMEM), and every shot searches the slice it falls in, remote or local, through
-// DSMEM. A guide table per slice (the first index past each of 256 equal-probability cuts of the
-// slice) narrows each search to a few entries; each thread runs four searches interleaved, so
-// their dependent DSMEM loads overlap. Shots are written in order, so the output stream is
-// coalesced. Heavy states are split into several work items (shot ranges), each rebuilding the CDF.
+// n <= 17: the whole CDF is held on chip. A thread-block cluster of CL = 2^(n-14) CTAs (one CTA
+// when n <= 14) owns one state: CTA r builds the prefix of amplitudes [r*2^sb, (r+1)*2^sb) in its
+// shared memory, the cluster exchanges slice totals over distributed shared memory (DSMEM), and
+// every CTA holds a guide table of the whole CDF (the first index past each of 4,096 cuts
+// floor(b T / 4096)). A shot's target lies between the cuts named by the top 12 bits of its
+// uniform, so the guide narrows each search to the entries between two cuts (through DSMEM when
+// remote); each thread runs four searches interleaved. Shots are written in order, so the output
+// stream is coalesced. Heavy states are split into several work items (shot ranges), each
+// rebuilding the CDF.
 //
 // n > 17: the CDF is built in global workspace (block prefixes, block offsets) and searched there.
-//
-// Comparisons of non-negative doubles are done on their bit patterns (same order, integer ALU).
 #include <cooperative_groups.h>
 #include <mutex>
 
@@ -30,8 +31,6 @@ namespace {
 constexpr int kSliceBits = 14;   // per-CTA CDF slice: 2^14 doubles = 128 KiB
 constexpr int kSampleThreads = 1024;
 
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-
 // Padded shared-memory address of CDF entry l when every thread owns K = 2^kb consecutive
 // entries: one pad slot per K entries keeps a warp's accesses on distinct banks.
 __device__ __forceinline__ uint32_t paddr(uint32_t l, int kb) { return l + (l >> kb); }
@@ -43,75 +42,76 @@ __device__ __forceinline__ int entries_log2(int cb) {
     return cb > tl ? cb - tl : 0;
 }
 
-// Exact FP32 -> FP64 of a non-negative finite float by integer operations, keeping the
-// conversion off the FP64 pipe (1/64 of the FP32 rate on GB300).
-__device__ __forceinline__ double f2d_exact(float f) {
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = u >> 23;
-    unsigned long long bits;
-    if (e != 0) {
-        bits = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    } else if (u == 0) {
-        bits = 0ull;
-    } else {                                        // subnormal: value = u * 2^-149
-        const int k = 31 - __clz(u);
-        bits = ((unsigned long long)(k + 874) << 52) | ((unsigned long long)(u ^ (1u << k)) << (52 - k));
-    }
-    return __longlong_as_double((long long)bits);
-}
+// Probabilities in 2^-62 fixed point: P = |psi_i|^2 (FP32 product) becomes floor(P * 2^62) as an
+// unsigned 64-bit integer, so prefix sums are exact integer additions on the integer pipe (the
+// FP64 pipe runs at 1/64 of the FP32 rate on GB300) and carry no rounding at all; the resolution
+// (2.2e-19 absolute) is finer than an FP64 running sum near C = 1 (1.1e-16). A state's total must
+// stay below 4 (normalised states: 1).
+using fx = unsigned long long;
+constexpr int kFxBits = 62;
 
-// Stage 1 of a slice prefix: P_i = |psi_i|^2 (FP32 product, exact FP64 value) into cdf (padded
-// layout); thread t owns entries [t*K, (t+1)*K) and sums them sequentially in FP64; the thread sums
-// are scanned across the CTA in a fixed order. Returns the thread's exclusive offset.
-__device__ double slice_stage1(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
+__device__ __forceinline__ fx fx_of(float p) {          // p >= 0 finite; P >= 2 saturates at 2^63
+    const uint32_t u = __float_as_uint(p);
+    const uint32_t e = u >> 23;
+    const fx m = e ? (fx)((u & 0x7FFFFFu) | 0x800000u) : (fx)(u & 0x7FFFFFu);
+    const int sh = (int)(e ? e : 1u) - 150 + kFxBits;    // P = m 2^(e - 150)
+    if (sh >= 0) return sh > 39 ? (fx)1 << 63 : m << sh;
+    return sh <= -24 ? 0ull : m >> (-sh);
+}
+__device__ __forceinline__ fx fx_prob(float2 a) { return fx_of(fmaf(a.x, a.x, a.y * a.y)); }
+
+// floor(u T) for the uniform u = m / 2^53 (m its 53-bit integer): exact.
+__device__ __forceinline__ fx fx_target(uint64_t m53, fx T) { return __umul64hi(m53 << 11, T); }
+
+// Stage 1 of a slice prefix: P_i in fixed point into cdf (padded layout); thread t owns entries
+// [t*K, (t+1)*K) and sums them; the thread sums are scanned across the CTA. Returns the thread's
+// exclusive offset.
+__device__ fx slice_stage1(const float2* __restrict__ amps, int cb, fx* cdf, fx* red) {
     const uint32_t count = 1u << cb;
     const int kb = entries_log2(cb);
     const uint32_t K = 1u << kb;
     const uint32_t l0 = threadIdx.x * K;
     const bool mine = l0 < count;
-    double tot = 0.0;
+    fx tot = 0;
     if (mine) {
         if (K == 1) {
-            const float2 v = amps[l0];
-            const double p = f2d_exact(fmaf(v.x, v.x, v.y * v.y));
+            const fx p = fx_prob(amps[l0]);
             cdf[paddr(l0, kb)] = p;
             tot = p;
         } else {
             for (uint32_t i = 0; i < K; i += 2) {
                 const float4 v = __ldg(reinterpret_cast<const float4*>(amps + l0 + i));
-                const double p0 = f2d_exact(fmaf(v.x, v.x, v.y * v.y));
-                const double p1 = f2d_exact(fmaf(v.z, v.z, v.w * v.w));
+                const fx p0 = fx_prob(make_float2(v.x, v.y));
+                const fx p1 = fx_prob(make_float2(v.z, v.w));
                 cdf[paddr(l0 + i, kb)] = p0;
                 cdf[paddr(l0 + i + 1, kb)] = p1;
-                tot += p0;
-                tot += p1;
+                tot += p0 + p1;
             }
         }
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    double x = tot;
+    fx x = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        const fx y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    const double prev = __shfl_up_sync(0xffffffffu, x, 1);   // inclusive sum of the lanes before
+    const fx prev = __shfl_up_sync(0xffffffffu, x, 1);   // inclusive sum of the lanes before
     if (lane == 31) red[w] = x;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int i = 0; i < nw; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+        fx acc = 0;
+        for (int i = 0; i < nw; ++i) { const fx t = red[i]; red[i] = acc; acc += t; }
     }
     __syncthreads();
-    return red[w] + (lane == 0 ? 0.0 : prev);
+    return red[w] + (lane == 0 ? 0ull : prev);
 }
 
-// Inclusive FP64 prefix of |psi|^2 over 2^cb amplitudes into cdf: stage 1, then every thread runs
-// the sequential prefix of its own entries from its offset. Returns the last entry.
-__device__ double build_prefix(const float2* __restrict__ amps, int cb, double* cdf, double* red) {
+// Inclusive fixed-point prefix of |psi|^2 over 2^cb amplitudes into cdf. Returns the last entry.
+__device__ fx build_prefix(const float2* __restrict__ amps, int cb, fx* cdf, fx* red) {
     const int kb = entries_log2(cb);
     const uint32_t K = 1u << kb, l0 = threadIdx.x * K;
-    double run = slice_stage1(amps, cb, cdf, red);
+    fx run = slice_stage1(amps, cb, cdf, red);
     if (l0 < (1u << cb))
         for (uint32_t i = 0; i < K; ++i) {
             run += cdf[paddr(l0 + i, kb)];
@@ -126,25 +126,17 @@ constexpr int kGuideBits = 12;
 constexpr int kGuide = 1 << kGuideBits;
 constexpr int kShotIlp = 4;
 
-// Float approximation (truncated mantissa) of a double in [0, 1) by integer operations; values
-// below the float range become 0. Only used to pick a guide bucket.
-__device__ __forceinline__ float d2f_trunc(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)(b >> 52);
-    if (e <= 896) return 0.0f;
-    return __uint_as_float(((uint32_t)(e - 896) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
-}
-
-// Guide threshold b of a CDF with total T: b * T * 2^-kGuideBits (the same value everywhere).
-__device__ __forceinline__ double guide_thr(uint32_t b, double T) { return ((double)b * T) * (1.0 / kGuide); }
+// Guide cut b < kGuide of a CDF with total T: floor(b T / kGuide). A shot whose 53-bit uniform has
+// top bits b has floor(u T) in [cut b, cut b+1], so its answer lies in [guide[b], guide[b+1]].
+__device__ __forceinline__ fx fx_cut(uint32_t b, fx T) { return __umul64hi((fx)b << (64 - kGuideBits), T); }
 
 template <int CL>
 __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs a, const SampleItem* __restrict__ items, int sb) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[33];
-    __shared__ double endv[CL];
-    __shared__ uint32_t guide[kGuide + 1];   // first state index with C > guide_thr(b, T)
-    double* cdf = reinterpret_cast<double*>(smem);
+    __shared__ fx red[33];
+    __shared__ fx endv[CL];
+    __shared__ uint32_t guide[kGuide + 1];   // first state index with C > cut b
+    fx* cdf = reinterpret_cast<fx*>(smem);
     int rank = 0;
     if constexpr (CL > 1) rank = (int)cg::this_cluster().block_rank();
     const SampleItem it = items[blockIdx.x / CL];
@@ -157,16 +149,16 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
         return;
     }
     const float2* amps = a.states + ((size_t)it.state << a.n) + ((size_t)rank << sb);
-    const double local_total = build_prefix(amps, sb, cdf, red);
-    double T;
+    const fx local_total = build_prefix(amps, sb, cdf, red);
+    fx T;
     if constexpr (CL > 1) {
         cg::cluster_group cluster = cg::this_cluster();
         cluster.sync();
         if (threadIdx.x == 0) {
-            double off = 0.0, my_off = 0.0;
+            fx off = 0, my_off = 0;
             for (int r = 0; r < CL; ++r) {
-                const double* rc = cluster.map_shared_rank(cdf, r);
-                const double tot_r = rc[paddr((1u << sb) - 1, kb)];
+                const fx* rc = cluster.map_shared_rank(cdf, r);
+                const fx tot_r = rc[paddr((1u << sb) - 1, kb)];
                 if (r == rank) my_off = off;
                 endv[r] = off + tot_r;     // == the remote last entry after its own offset add
                 off = endv[r];
@@ -174,8 +166,8 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
             red[32] = my_off;
         }
         cluster.sync();                    // everyone has read the raw slice totals
-        const double my_off = red[32];
-        if (my_off != 0.0)
+        const fx my_off = red[32];
+        if (my_off != 0)
             for (uint32_t l = threadIdx.x; l < (1u << sb); l += nth) cdf[paddr(l, kb)] += my_off;
         __syncthreads();
         T = endv[CL - 1];
@@ -184,19 +176,20 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
         if (threadIdx.x == 0) endv[0] = local_total;
         __syncthreads();
     }
-    // Guide over the whole CDF: each CTA resolves the thresholds that fall in its slice (local
-    // search), then copies the others' entries over DSMEM, so every CTA holds the full table.
+    // Guide over the whole CDF: each CTA resolves the cuts that fall in its slice (local search),
+    // then copies the others' entries over DSMEM, so every CTA holds the full table. Every cut
+    // lies in [0, T), so when T > 0 each is resolved by exactly one slice.
     const uint32_t last = (1u << a.n) - 1;
     const uint32_t slast = (1u << sb) - 1;
     {
-        const long long st_b = rank == 0 ? 0ll : dbits(endv[rank - 1]), en_b = dbits(endv[rank]);
-        for (uint32_t b = threadIdx.x; b <= (uint32_t)kGuide; b += nth) {
-            const long long thr = dbits(guide_thr(b, T));
-            if (b == (uint32_t)kGuide || !(thr >= st_b && thr < en_b)) continue;
+        const fx st_b = rank == 0 ? 0ull : endv[rank - 1], en_b = endv[rank];
+        for (uint32_t b = threadIdx.x; b < (uint32_t)kGuide; b += nth) {
+            const fx thr = fx_cut(b, T);
+            if (!(thr >= st_b && thr < en_b)) continue;
             uint32_t lo = 0, hi = slast;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (thr < dbits(cdf[paddr(mid, kb)])) hi = mid; else lo = mid + 1;
+                if (thr < cdf[paddr(mid, kb)]) hi = mid; else lo = mid + 1;
             }
             guide[b] = ((uint32_t)rank << sb) | lo;
         }
@@ -206,38 +199,36 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
         cg::cluster_group cluster = cg::this_cluster();
         cluster.sync();
         for (uint32_t b = threadIdx.x; b < (uint32_t)kGuide; b += nth) {
-            const long long thr = dbits(guide_thr(b, T));
+            const fx thr = fx_cut(b, T);
             int r = 0;
-            while (r < CL - 1 && !(thr < dbits(endv[r]))) ++r;
+            while (r < CL - 1 && !(thr < endv[r])) ++r;
             if (r != rank) guide[b] = cluster.map_shared_rank(guide, r)[b];
         }
     }
     __syncthreads();
-    // Shots k, k + stride, ... : kShotIlp of them per thread at a time. The bucket of u is
-    // estimated in float (error far below one bucket), so the true bucket is b-1, b or b+1 and
-    // the answer lies in [guide[b-1], guide[b+2]]; it is resolved from the local guide when that
-    // range is one index, else by a search of those entries (through DSMEM for remote slices).
+    // Shots k, k + stride, ... : kShotIlp of them per thread at a time. A shot's target floor(u T)
+    // lies between the cuts of the bucket named by the top bits of its uniform, so its answer is in
+    // [guide[b], guide[b+1]]: resolved from the local guide when that range is one index, else by a
+    // search of those entries (through DSMEM for remote slices).
     const uint64_t stride = (uint64_t)CL * nth;
     for (uint64_t k0 = (uint64_t)rank * nth + threadIdx.x; k0 < nshots; k0 += kShotIlp * stride) {
         uint32_t lo[kShotIlp], hi[kShotIlp];
-        long long tb[kShotIlp];
+        fx tq[kShotIlp];
 #pragma unroll
         for (int q = 0; q < kShotIlp; ++q) {
             const uint64_t k = k0 + q * stride;
             lo[q] = hi[q] = last;
-            tb[q] = 0;
+            tq[q] = 0;
             if (k >= nshots) continue;
             const uint64_t j = it.j0 + k;
             const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom,
                                             (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-            const double u = u53(x.x[0], x.x[1]);
-            const double t = u * T;
-            tb[q] = dbits(t);
-            if (!(tb[q] < dbits(T))) continue;          // rounding put t at or above T
-            int b = (int)(d2f_trunc(u) * (float)kGuide);
-            b = b < 0 ? 0 : (b > kGuide - 1 ? kGuide - 1 : b);
-            lo[q] = guide[b > 0 ? b - 1 : 0];
-            hi[q] = guide[b + 2 < kGuide ? b + 2 : kGuide];
+            const uint64_t m = u53_bits(x.x[0], x.x[1]);
+            tq[q] = fx_target(m, T);
+            if (!(tq[q] < T)) continue;                  // only for T = 0
+            const uint32_t b = (uint32_t)(m >> (53 - kGuideBits));
+            lo[q] = guide[b];
+            hi[q] = guide[b + 1];
         }
         while (true) {
             bool any = false;
@@ -247,9 +238,9 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
                     any = true;
                     const uint32_t mid = (lo[q] + hi[q]) >> 1;
                     const int r = (int)(mid >> sb);
-                    const double* rc = cdf;
+                    const fx* rc = cdf;
                     if constexpr (CL > 1) rc = cg::this_cluster().map_shared_rank(cdf, r);
-                    if (tb[q] < dbits(rc[paddr(mid & slast, kb)])) hi[q] = mid; else lo[q] = mid + 1;
+                    if (tq[q] < rc[paddr(mid & slast, kb)]) hi[q] = mid; else lo[q] = mid + 1;
                 }
             }
             if (!any) break;
@@ -265,12 +256,10 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
 
 // ---- light states: one CTA per state, chunk prefixes ----------------------------------------------------
 // For a state with few shots the full CDF is never stored. Pass 1 sums each run of cs = 2^n / 8192
-// consecutive P_i sequentially in FP64 (chunk totals); a fixed-order scan turns them into the FP64
-// prefix at every chunk start, P[c] (P[8192] = T). A shot finds its chunk by binary search on P and
-// then accumulates the chunk's P_i from P[c] in order: C_i = P[c] + p_first + ... + p_i inside the
-// chunk, the chunk's last entry taken as P[c+1] (so C is the chunk-start prefix everywhere). Each
-// shot re-reads one chunk (cs amplitudes, mostly from L2), so FP64 work is one add per amplitude
-// plus at most cs per shot.
+// consecutive P_i (chunk totals, fixed point); a scan turns them into the prefix at every chunk
+// start, P[c] (P[8192] = T). A shot finds its chunk by binary search on P and then accumulates the
+// chunk's P_i from P[c] in order; the sums are exact, so the chunk's last entry equals P[c+1]. Each
+// shot re-reads one chunk (cs amplitudes, mostly from L2).
 constexpr int kLightChunkBits = 13;
 constexpr int kLightChunks = 1 << kLightChunkBits;
 constexpr int kLightThreads = 512;          // one shot per thread at most
@@ -278,12 +267,10 @@ constexpr int kLightPerThread = kLightChunks / kLightThreads;   // chunks scanne
 
 __device__ __forceinline__ uint32_t lpad(uint32_t c) { return c + (c >> 4); }   // bank-distinct rows of 16
 
-__device__ __forceinline__ double prob64(float2 a) { return f2d_exact(fmaf(a.x, a.x, a.y * a.y)); }
-
 __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a, const SampleItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[33];
-    double* P = reinterpret_cast<double*>(smem);       // padded: P[lpad(c)], c = 0 .. kLightChunks
+    __shared__ fx red[33];
+    fx* P = reinterpret_cast<fx*>(smem);               // padded: P[lpad(c)], c = 0 .. kLightChunks
     const SampleItem it = items[blockIdx.x];
     const uint64_t nshots = it.j1 - it.j0;              // <= blockDim.x
     if (a.status && a.status[it.state]) {
@@ -294,63 +281,67 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
     const int csb = n - kLightChunkBits;                // log2 of the chunk size (2 .. 7)
     const uint32_t cs = 1u << csb;
     const float2* amps = a.states + ((size_t)it.state << n);
-    // pass 1: chunk totals, sequential FP64 sums (two amplitudes per 16-byte load)
+    // pass 1: chunk totals (two amplitudes per 16-byte load, the chunk's loads issued together)
     for (uint32_t c = threadIdx.x; c < (uint32_t)kLightChunks; c += blockDim.x) {
         const float4* v = reinterpret_cast<const float4*>(amps + ((size_t)c << csb));
-        double acc = 0.0;
-        for (uint32_t i = 0; i < cs / 2; ++i) {
-            const float4 x = __ldg(v + i);
-            acc += prob64(make_float2(x.x, x.y));
-            acc += prob64(make_float2(x.z, x.w));
+        fx acc = 0;
+        for (uint32_t i0 = 0; i0 < cs / 2; i0 += 8) {
+            float4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < cs / 2) x[u] = __ldg(v + i0 + u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < cs / 2) acc += fx_prob(make_float2(x[u].x, x[u].y)) + fx_prob(make_float2(x[u].z, x[u].w));
         }
         P[lpad(c)] = acc;
     }
     __syncthreads();
-    // scan: thread t owns chunks [16 t, 16 t + 16): sequential sum, fixed-order CTA exclusive scan of
-    // the thread sums, then the chunk-start prefixes
+    // scan: thread t owns chunks [16 t, 16 t + 16): its sum, a CTA exclusive scan of the thread
+    // sums, then the chunk-start prefixes
     const uint32_t c0 = threadIdx.x * kLightPerThread;
-    double tot[kLightPerThread];
-    double mine = 0.0;
+    fx tot[kLightPerThread];
+    fx mine = 0;
 #pragma unroll
     for (int i = 0; i < kLightPerThread; ++i) { tot[i] = P[lpad(c0 + i)]; mine += tot[i]; }
-    double v = mine;
+    fx v = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, v, o);
+        const fx y = __shfl_up_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) >= (uint32_t)o) v += y;
     }
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 31) red[w] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int i = 0; i < nw; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+        fx acc = 0;
+        for (int i = 0; i < nw; ++i) { const fx t = red[i]; red[i] = acc; acc += t; }
         red[32] = acc;                                  // T
     }
     __syncthreads();
-    double run = red[w] + (v - mine);                   // exclusive prefix of this thread's chunks
+    fx run = red[w] + (v - mine);                       // exclusive prefix of this thread's chunks
 #pragma unroll
     for (int i = 0; i < kLightPerThread; ++i) { P[lpad(c0 + i)] = run; run += tot[i]; }
-    const double T = red[32];
+    const fx T = red[32];
     if (threadIdx.x == 0) P[lpad(kLightChunks)] = T;
     __syncthreads();
     if (threadIdx.x >= nshots) return;
     const uint64_t j = it.j0 + threadIdx.x;
     const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const long long tb = dbits(u53(x.x[0], x.x[1]) * T);
-    uint32_t idx = (1u << n) - 1;                       // rounding put t at or above T
-    if (tb < dbits(T)) {
+    const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
+    uint32_t idx = (1u << n) - 1;                       // T = 0
+    if (t < T) {
         uint32_t lo = 0, hi = kLightChunks - 1;         // first chunk c with t < P[c + 1]
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (tb < dbits(P[lpad(mid + 1)])) hi = mid; else lo = mid + 1;
+            if (t < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
         }
-        double acc = P[lpad(lo)];
+        fx acc = P[lpad(lo)];
         const float2* ch = amps + ((size_t)lo << csb);
         idx = (lo << csb) + cs - 1;
         for (uint32_t i = 0; i + 1 < cs; ++i) {
-            acc += prob64(__ldg(ch + i));
-            if (tb < dbits(acc)) { idx = (lo << csb) + i; break; }
+            acc += fx_prob(__ldg(ch + i));
+            if (t < acc) { idx = (lo << csb) + i; break; }
         }
     }
     a.bits[it.out0 + threadIdx.x] = idx;
@@ -359,35 +350,35 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
 // ---- n > 17: global-memory CDF -----------------------------------------------------------------------
 
 // One CTA per block of 2^14 amplitudes: local inclusive prefix (unpadded) and block total.
-__global__ void __launch_bounds__(kSampleThreads) k_block_prefix(const float2* __restrict__ amps, double* cdf, double* btot) {
+__global__ void __launch_bounds__(kSampleThreads) k_block_prefix(const float2* __restrict__ amps, fx* cdf, fx* btot) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[33];
-    double* s = reinterpret_cast<double*>(smem);
+    __shared__ fx red[33];
+    fx* s = reinterpret_cast<fx*>(smem);
     const uint32_t b = blockIdx.x;
     const int kb = entries_log2(kSliceBits);
-    const double tot = build_prefix(amps + ((size_t)b << kSliceBits), kSliceBits, s, red);
+    const fx tot = build_prefix(amps + ((size_t)b << kSliceBits), kSliceBits, s, red);
     for (uint32_t l = threadIdx.x; l < (1u << kSliceBits); l += blockDim.x)
         cdf[((size_t)b << kSliceBits) + l] = s[paddr(l, kb)];
     if (threadIdx.x == 0) btot[b] = tot;
 }
 
-// One CTA: exclusive block offsets (sequential per thread chunk, then across threads); writes
-// the block end values bend[b] = offset[b] + btot[b] and T into bend[nb].
-__global__ void k_block_scan(const double* __restrict__ btot, double* boff, double* bend, uint32_t nb) {
-    __shared__ double red[1024];
+// One CTA: exclusive block offsets (per thread chunk, then across threads); writes the block end
+// values bend[b] = offset[b] + btot[b].
+__global__ void k_block_scan(const fx* __restrict__ btot, fx* boff, fx* bend, uint32_t nb) {
+    __shared__ fx red[1024];
     const uint32_t nth = blockDim.x;
     const uint32_t per = (nb + nth - 1) / nth;
     const uint32_t b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
-    double s = 0.0;
+    fx s = 0;
     for (uint32_t b = b0; b < b1; ++b) s += btot[b];
     red[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (uint32_t i = 0; i < nth; ++i) { const double t = red[i]; red[i] = acc; acc += t; }
+        fx acc = 0;
+        for (uint32_t i = 0; i < nth; ++i) { const fx t = red[i]; red[i] = acc; acc += t; }
     }
     __syncthreads();
-    double run = red[threadIdx.x];
+    fx run = red[threadIdx.x];
     for (uint32_t b = b0; b < b1; ++b) {
         boff[b] = run;
         run += btot[b];
@@ -395,39 +386,39 @@ __global__ void k_block_scan(const double* __restrict__ btot, double* boff, doub
     }
 }
 
-__global__ void k_block_add(double* cdf, const double* __restrict__ boff) {
+__global__ void k_block_add(fx* cdf, const fx* __restrict__ boff) {
     const uint32_t b = blockIdx.x;
-    const double off = boff[b];
-    if (off == 0.0) return;
-    double* c = cdf + ((size_t)b << kSliceBits);
+    const fx off = boff[b];
+    if (off == 0) return;
+    fx* c = cdf + ((size_t)b << kSliceBits);
     for (uint32_t l = threadIdx.x; l < (1u << kSliceBits); l += blockDim.x) c[l] += off;
 }
 
-__global__ void k_search_global(SampleArgs a, const double* __restrict__ cdf, const double* __restrict__ bend,
+__global__ void k_search_global(SampleArgs a, const fx* __restrict__ cdf, const fx* __restrict__ bend,
                                 uint32_t nb, uint32_t state, uint32_t alpha, uint64_t j0, uint64_t j1, uint64_t out0,
                                 uint32_t dom) {
-    const double T = bend[nb - 1];
+    const fx T = bend[nb - 1];
     const bool null = a.status && a.status[state];
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < j1 - j0; k += (uint64_t)gridDim.x * blockDim.x) {
         if (null) { a.bits[out0 + k] = 0xFFFFFFFFu; continue; }
         const uint64_t j = j0 + k;
         const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), alpha, dom,
                                         (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        const long long tb = dbits(u53(x.x[0], x.x[1]) * T);
+        const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
         uint32_t lo = 0, hi = nb - 1;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (tb < dbits(bend[mid])) hi = mid; else lo = mid + 1;
+            if (t < bend[mid]) hi = mid; else lo = mid + 1;
         }
         uint64_t idx;
-        if (!(tb < dbits(bend[lo]))) {
+        if (!(t < bend[lo])) {
             idx = (1ull << a.n) - 1;
         } else {
-            const double* c = cdf + ((size_t)lo << kSliceBits);
+            const fx* c = cdf + ((size_t)lo << kSliceBits);
             uint32_t l = 0, h = (1u << kSliceBits) - 1;
             while (l < h) {
                 const uint32_t mid = (l + h) >> 1;
-                if (tb < dbits(c[mid])) h = mid; else l = mid + 1;
+                if (t < c[mid]) h = mid; else l = mid + 1;
             }
             idx = ((uint64_t)lo << kSliceBits) | l;
         }
@@ -440,7 +431,7 @@ __global__ void k_fill(uint32_t* bits, uint64_t count, uint32_t v) {
         bits[k] = v;
 }
 
-// Padded CDF slice of 2^sb doubles for a CTA of `threads` threads.
+// Padded CDF slice of 2^sb 8-byte entries for a CTA of `threads` threads.
 size_t cdf_smem_bytes(int sb, uint32_t threads) {
     const size_t count = (size_t)1 << sb;
     size_t K = count / threads;
@@ -513,7 +504,7 @@ int sample_light_max_qubits() { return kLightChunkBits + 7; }
 void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
     if (n_items == 0) return;
     static bool configured = false;
-    const size_t smem = ((size_t)kLightChunks + kLightChunks / 16 + 1) * sizeof(double);
+    const size_t smem = ((size_t)kLightChunks + kLightChunks / 16 + 1) * sizeof(fx);
     if (!configured) {
         PTSBE_CUDA(cudaFuncSetAttribute(k_sample_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
@@ -553,10 +544,10 @@ void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, u
     const int n = a.n;
     if (j1 <= j0) return;
     const uint32_t nb = 1u << (n - kSliceBits);
-    double* cdf = a.scratch;
-    double* btot = cdf + ((size_t)1 << n);
-    double* boff = btot + nb;
-    double* bend = boff + nb;
+    fx* cdf = a.scratch;
+    fx* btot = cdf + ((size_t)1 << n);
+    fx* boff = btot + nb;
+    fx* bend = boff + nb;
     static bool configured = false;
     if (!configured) {
         PTSBE_CUDA(cudaFuncSetAttribute(k_block_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
