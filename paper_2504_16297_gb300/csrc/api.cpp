@@ -498,6 +498,15 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         std::vector<uint8_t> fresh(count);
         std::vector<double> wmix(count), qa(count);
         std::unordered_map<std::string, uint32_t> index;
+        // A set can only start later than stage 0 in a plan with more than one stage.
+        const bool trie = reuse && J > 1;
+        // prod over unitary-mixture sites of q_{s,0}; a set's product is this times the ratios at its
+        // entries (the full product when some q_{s,0} is 0)
+        double q0mix = 1.0;
+        for (uint32_t site = 0; site < S; ++site) {
+            const HostChannel& ch = c.ch[c.site_ch[site]];
+            if (ch.mixture) q0mix *= ch.q[0];
+        }
         auto key_of = [&](uint32_t alpha, uint32_t len) {
             std::string k;
             k.resize(len * 5);
@@ -513,7 +522,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             ebeg[a] = s.off[alpha]; eend[a] = s.off[alpha + 1];
             qa[a] = s.q[alpha];
             uint32_t parent = UINT32_MAX;
-            if (reuse) {
+            if (trie) {
                 for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
                     auto it = index.find(key_of(alpha, (uint32_t)p));
                     if (it != index.end()) { parent = it->second; break; }
@@ -529,13 +538,21 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
                 if (j > 0) { sstage[a] = j; src[a] = sstage[parent] == j ? src[parent] : parent; fresh[a] = 0; }
             }
             // prod over unitary-mixture sites of q_{s,k_s}
-            double w = 1.0;
-            uint32_t e = s.off[alpha];
-            for (uint32_t site = 0; site < S; ++site) {
-                uint32_t k = 0;
-                if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
-                const HostChannel& ch = c.ch[c.site_ch[site]];
-                if (ch.mixture) w *= ch.q[k];
+            double w = q0mix;
+            if (q0mix > 0) {
+                for (uint32_t e = s.off[alpha]; e < s.off[alpha + 1]; ++e) {
+                    const HostChannel& ch = c.ch[c.site_ch[s.site[e]]];
+                    if (ch.mixture) w *= ch.q[s.k[e]] / ch.q[0];
+                }
+            } else {
+                w = 1.0;
+                uint32_t e = s.off[alpha];
+                for (uint32_t site = 0; site < S; ++site) {
+                    uint32_t k = 0;
+                    if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
+                    const HostChannel& ch = c.ch[c.site_ch[site]];
+                    if (ch.mixture) w *= ch.q[k];
+                }
             }
             wmix[a] = w;
         }

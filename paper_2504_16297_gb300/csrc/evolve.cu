@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kProgThreads) k_frame_program(EvolveArgs a, in
     P.B = B;
 }
 
+// Copies from global memory (read-only path: the source must not be in shared memory).
 __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t bytes, uint32_t t, uint32_t nt) {
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
     const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
@@ -147,6 +148,7 @@ constexpr int kFrameThreads = 512;   // 128 registers per thread: grouped mixes 
 // the stage in a layout that maps the mixing directions to the low bits); the tile buffer holds
 // only that prefix, so several CTAs share an SM and one CTA's stores overlap another's passes.
 constexpr int kFrameSmallThreads = 128;
+constexpr int kZeroChunk = 4096;      // bytes per bulk zero copy (the state size is a multiple)
 constexpr int kFrameSmallCtas = 3;
 template <bool SMALL>
 __global__ void __launch_bounds__(SMALL ? kFrameSmallThreads : kFrameThreads, SMALL ? kFrameSmallCtas : 1)
@@ -161,6 +163,7 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
     __shared__ Step S[kMaxSteps];
     __shared__ Factor pool[kMaxPool];
     __shared__ uint32_t delta[kMaxTabs * kDeltaSlots];
+    __shared__ __align__(128) float4 zbuf[SMALL ? kZeroChunk / 16 : 1];
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     const uint32_t tid = threadIdx.x, nthr = blockDim.x;
     float2* tile = reinterpret_cast<float2*>(smem);
@@ -221,6 +224,22 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
             }
         }
     }
+    if constexpr (SMALL) {
+        // The state is all zeros outside the support: the copy engine writes those zeros (bulk
+        // copies of a zeroed shared buffer, issued by one thread) while the CTA runs the program;
+        // the sparse final waits for them before it scatters the support.
+        for (uint32_t v = tid; v < (uint32_t)kZeroChunk / 16; v += nthr) zbuf[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t src = (uint32_t)__cvta_generic_to_shared(zbuf);
+            const uint64_t bytes = (uint64_t)8 << n;
+            for (uint64_t off = 0; off < bytes; off += kZeroChunk)
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                             :: "l"(reinterpret_cast<unsigned char*>(g) + off), "r"(src), "n"(kZeroChunk) : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+    }
     __syncthreads();
     if (B.npool <= (uint32_t)kMaxPool) poolp = pool;
     if (B.nsteps <= (uint32_t)kMaxSteps) Sp = S;
@@ -245,8 +264,17 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
                 const double w = a.wmix[node] * part;
                 const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
                 const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
-                float4* g4 = reinterpret_cast<float4*>(g);
-                for (uint32_t v = tid; v < (1u << (n - 1)); v += nthr) g4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (SMALL) {
+                    // the bulk zero copies issued at the start: complete, and ordered before the
+                    // scatter's stores
+                    if (tid == 0) {
+                        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
+                } else {
+                    float4* g4 = reinterpret_cast<float4*>(g);
+                    for (uint32_t v = tid; v < (1u << (n - 1)); v += nthr) g4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 __syncthreads();
                 if (!null) run_sparse_final(sp, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
                 if (tid == 0) {
@@ -285,6 +313,9 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
         poolp = pool;
         __syncthreads();
     }
+    // no bulk copy may still read this CTA's shared memory when it exits
+    if constexpr (SMALL)
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Per node: total squared norm from the tile partials (fixed order), weight, null flag, scale.

@@ -38,7 +38,8 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     // the small-buffer kernel (sparse final stage with a support bound) runs 128 threads
     const bool small = a.fstages[stage].sparse_final && a.fstages[stage].sbits > 0;
-    const uint32_t nthr = small ? 128u : threads_for(tb);
+    const uint32_t nthr = small ? 128u : threads_for(tb);   // the small-buffer kernel: 128 threads
+    const uint32_t nthr_final = nthr;
     const uint32_t tamps = small ? 1u << a.fstages[stage].sbits : 1u << tb;
     std::vector<float2> tile(1u << tb), tabs((size_t)kMaxTabs * kTabSize);
     // past the buffer the kernel would have: a sentinel that must survive the whole CTA, and that
@@ -90,15 +91,15 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
                 for (uint32_t t = 0; t < nthr; ++t) run_diag(sp, tile.data(), tabs.data(), delta, tb, t, nthr);
             } else if (sp.kind == ST_FINAL && fs.sparse_final) {
                 double part = 0;
-                for (uint32_t t = 0; t < nthr; ++t)
-                    part += run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, nullptr, 1.f, 0, t, nthr);
+                for (uint32_t t = 0; t < nthr_final; ++t)
+                    part += run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, nullptr, 1.f, 0, t, nthr_final);
                 const double w = a.wmix[node] * part;
                 const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
                 const float scale = null ? 0.0f : (float)(1.0 / std::sqrt(part));
                 for (size_t i = 0; i < (1ull << n); ++i) g[i] = make_float2(0.f, 0.f);
                 if (!null)
-                    for (uint32_t t = 0; t < nthr; ++t)
-                        run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, g, scale, 1, t, nthr);
+                    for (uint32_t t = 0; t < nthr_final; ++t)
+                        run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, g, scale, 1, t, nthr_final);
                 a.weights[node] = w;
                 a.status[node] = null ? 1 : 0;
             } else if (sp.kind == ST_STORE) {
