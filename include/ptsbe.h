@@ -344,7 +344,11 @@ enum {
      * registers, the tile re-shuffled through shared memory between register groups), 3 deferred
      * frame (permutations and diagonals tracked as an index map and factor tables; only
      * operators that mix amplitudes pass over the tile). */
-    PTSBE_OPT_EVOLVE_KERNEL = 0
+    PTSBE_OPT_EVOLVE_KERNEL = 0,
+    /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
+     * prefixes (one chunk re-read per shot); heavier ones by a thread-block cluster holding the
+     * whole CDF. Both give the same shots; only the speed differs. Default 65,536 (measured).  */
+    PTSBE_OPT_LIGHT_SHOTS = 1
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */

@@ -17,6 +17,7 @@ PTSBE_PTS_PROPORTIONAL, PTSBE_PTS_TOPK, PTSBE_PTS_BAND, PTSBE_PTS_TARGETED, PTSB
 PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVEN = range(4)
 PTSBE_EVOLVE_PREFIX_REUSE = 1
 PTSBE_OPT_EVOLVE_KERNEL = 0
+PTSBE_OPT_LIGHT_SHOTS = 1
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
  PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD) = range(7)
 

@@ -59,6 +59,7 @@ struct ptsbe_ctx {
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
     int evolve_kernel = 0;
+    uint64_t light_shots = kLightShotLimit;   // states with at most this many shots: one-CTA sampler
     int n_sm = 0;                      // streaming multiprocessors of the device
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
@@ -675,7 +676,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             const uint32_t alpha = first + a;
             const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
             if (m == 0) continue;
-            if (light_ok && m <= kLightShotLimit) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
+            if (light_ok && m <= ctx->light_shots) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
             if (n <= sample_cluster_max_qubits())
                 for (uint64_t j0 = 0; j0 < m; j0 += chunk)
                     items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
@@ -701,7 +702,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             for (uint32_t a = 0; a < count; ++a) {
                 const uint32_t alpha = first + a;
                 const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
-                if (m == 0 || (light_ok && m <= kLightShotLimit)) continue;
+                if (m == 0 || (light_ok && m <= ctx->light_shots)) continue;
                 const double sb = 8.0 * (double)(1ull << n);
                 ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
             }
@@ -714,6 +715,9 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         if (option == PTSBE_OPT_EVOLVE_KERNEL) {
             if (value < 0 || value > 3) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0, 1, 2 or 3");
             ctx->evolve_kernel = (int)value;
+        } else if (option == PTSBE_OPT_LIGHT_SHOTS) {
+            if (value < 0) fail(PTSBE_ERR_INVALID, "light-sampler shot limit must be >= 0");
+            ctx->light_shots = (uint64_t)value;
         } else {
             fail(PTSBE_ERR_INVALID, "unknown option");
         }

@@ -434,8 +434,10 @@ void launch_backward(const BwArgs& a, cudaStream_t s);
 
 int sample_cluster_max_qubits();
 int sample_light_max_qubits();
-// States with at most this many shots go to the one-CTA-per-state light sampler (15 <= n <= 20).
-constexpr uint64_t kLightShotLimit = 512;
+// Default shot limit of the one-CTA-per-state light sampler (15 <= n <= 20); heavier states go to
+// the cluster sampler. Both give the same shots (exact integer prefix sums), so the limit only
+// moves work between the kernels (PTSBE_OPT_LIGHT_SHOTS).
+constexpr uint64_t kLightShotLimit = 65536;
 void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);
 
 }  // namespace ptsbe

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
 // shot re-reads one chunk (cs amplitudes, mostly from L2).
 constexpr int kLightChunkBits = 13;
 constexpr int kLightChunks = 1 << kLightChunkBits;
-constexpr int kLightThreads = 512;          // one shot per thread at most
+constexpr int kLightThreads = 512;
 constexpr int kLightPerThread = kLightChunks / kLightThreads;   // chunks scanned by one thread (16)
 
 __device__ __forceinline__ uint32_t lpad(uint32_t c) { return c + (c >> 4); }   // bank-distinct rows of 16
@@ -272,9 +272,9 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
     __shared__ fx red[33];
     fx* P = reinterpret_cast<fx*>(smem);               // padded: P[lpad(c)], c = 0 .. kLightChunks
     const SampleItem it = items[blockIdx.x];
-    const uint64_t nshots = it.j1 - it.j0;              // <= blockDim.x
+    const uint64_t nshots = it.j1 - it.j0;
     if (a.status && a.status[it.state]) {
-        if (threadIdx.x < nshots) a.bits[it.out0 + threadIdx.x] = 0xFFFFFFFFu;
+        for (uint64_t k = threadIdx.x; k < nshots; k += blockDim.x) a.bits[it.out0 + k] = 0xFFFFFFFFu;
         return;
     }
     const int n = a.n;
@@ -325,26 +325,27 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
     const fx T = red[32];
     if (threadIdx.x == 0) P[lpad(kLightChunks)] = T;
     __syncthreads();
-    if (threadIdx.x >= nshots) return;
-    const uint64_t j = it.j0 + threadIdx.x;
-    const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
-    uint32_t idx = (1u << n) - 1;                       // T = 0
-    if (t < T) {
-        uint32_t lo = 0, hi = kLightChunks - 1;         // first chunk c with t < P[c + 1]
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (t < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
+    for (uint64_t k = threadIdx.x; k < nshots; k += blockDim.x) {
+        const uint64_t j = it.j0 + k;
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+        const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
+        uint32_t idx = (1u << n) - 1;                   // T = 0
+        if (t < T) {
+            uint32_t lo = 0, hi = kLightChunks - 1;     // first chunk c with t < P[c + 1]
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (t < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
+            }
+            fx acc = P[lpad(lo)];
+            const float2* ch = amps + ((size_t)lo << csb);
+            idx = (lo << csb) + cs - 1;
+            for (uint32_t i = 0; i + 1 < cs; ++i) {
+                acc += fx_prob(__ldg(ch + i));
+                if (t < acc) { idx = (lo << csb) + i; break; }
+            }
         }
-        fx acc = P[lpad(lo)];
-        const float2* ch = amps + ((size_t)lo << csb);
-        idx = (lo << csb) + cs - 1;
-        for (uint32_t i = 0; i + 1 < cs; ++i) {
-            acc += fx_prob(__ldg(ch + i));
-            if (t < acc) { idx = (lo << csb) + i; break; }
-        }
+        a.bits[it.out0 + k] = idx;
     }
-    a.bits[it.out0 + threadIdx.x] = idx;
 }
 
 // ---- n > 17: global-memory CDF -----------------------------------------------------------------------

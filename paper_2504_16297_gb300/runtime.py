@@ -106,6 +106,10 @@ class Ptsbe:
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL,
                               {"auto": 0, "sweep": 1, "registers": 2, "frame": 3}[kernel])
 
+    def set_light_shots(self, limit: int):
+        """Shot count up to which a state is sampled by the one-CTA light sampler."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_LIGHT_SHOTS, int(limit))
+
     def set_timing(self, enable: bool):
         capi.ptsbe_set_timing(self.ctx, enable)
 
