@@ -354,6 +354,28 @@ enum {
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
 PTSBE_API int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value);
 
+/* Result of ptsbe_autotune: the options it chose and the measured time of every candidate
+ * (milliseconds per ptsbe_evolve_batch / ptsbe_sample_shots call, mean of `reps` calls; 0 for a
+ * candidate that does not apply). */
+typedef struct {
+    int32_t evolve_kernel;            /* chosen PTSBE_OPT_EVOLVE_KERNEL (1 sweeps, 2 registers, 3 frame) */
+    uint64_t light_shots;             /* chosen PTSBE_OPT_LIGHT_SHOTS                                */
+    double evolve_ms[4];              /* by kernel index (entry 0 unused)                           */
+    uint64_t light_candidates[4];
+    double sample_ms[4];              /* by light-shot candidate                                    */
+} ptsbe_tuning;
+
+/* Autotuner: runs ptsbe_evolve_batch (every evolve kernel, flags as given) and then
+ * ptsbe_sample_shots (each light-shot limit) on sets [first, first + count) of set_id, `reps`
+ * timed calls each after one warm-up, times them with CUDA events on the context stream, and sets
+ * the context to the fastest evolve kernel and shot limit. The kernels give the same results up
+ * to rounding (the shot limit changes no shot at all), so tuning changes speed only. Buffers as
+ * for the two calls; d_states, d_weights, d_status and d_bits are overwritten. Host-synchronous.
+ * Errors: those of the two calls; PTSBE_ERR_INVALID for reps = 0. */
+PTSBE_API int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
+                             double* d_weights, uint8_t* d_status, uint32_t flags, uint64_t seed, uint32_t* d_bits,
+                             uint64_t d_bits_capacity, uint32_t reps, ptsbe_tuning* out);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Instrumentation                                                                           */
 /* ---------------------------------------------------------------------------------------- */

@@ -51,6 +51,11 @@ class ptsbe_observable(C.Structure):
                 ("d_diag", C.c_void_p)]
 
 
+class ptsbe_tuning(C.Structure):
+    _fields_ = [("evolve_kernel", C.c_int32), ("light_shots", C.c_uint64), ("evolve_ms", C.c_double * 4),
+                ("light_candidates", C.c_uint64 * 4), ("sample_ms", C.c_double * 4)]
+
+
 class PtsbeError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -86,6 +91,8 @@ _PROTOS = {
     "ptsbe_backward": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.POINTER(ptsbe_observable), C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p]),
+    "ptsbe_autotune": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(ptsbe_tuning)]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -200,6 +207,13 @@ def ptsbe_backward(ctx, circuit_id, set_id, first, count, obs: ptsbe_observable,
                    d_per_set, d_grad_params, d_grad_noise):
     check(ctx, load().ptsbe_backward(ctx, circuit_id, set_id, first, count, C.byref(obs), checkpoint_every, d_loss,
                                      d_per_set, d_grad_params, d_grad_noise))
+
+
+def ptsbe_autotune(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed, d_bits, capacity, reps):
+    t = ptsbe_tuning()
+    check(ctx, load().ptsbe_autotune(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed, d_bits,
+                                     capacity, reps, C.byref(t)))
+    return t
 
 
 def ptsbe_kernel_launches() -> int:

@@ -687,7 +687,11 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
             SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
             ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
             if (nl) {
-                const double bytes = 8.0 * (double)(1ull << n) * (double)nl * 1.1;
+                // algorithmic: each state read once and 4 bytes per shot written (the per-shot chunk
+                // re-reads are the light design's extra traffic, not counted)
+                uint64_t light_shots = 0;
+                for (size_t i = 0; i < nl; ++i) light_shots += light[i].j1 - light[i].j0;
+                const double bytes = 8.0 * (double)(1ull << n) * (double)nl + 4.0 * (double)light_shots;
                 ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
             }
             if (nh) {
@@ -721,6 +725,74 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         } else {
             fail(PTSBE_ERR_INVALID, "unknown option");
         }
+    });
+}
+
+int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states, double* d_weights,
+                   uint8_t* d_status, uint32_t flags, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity,
+                   uint32_t reps, ptsbe_tuning* out) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        if (reps == 0) fail(PTSBE_ERR_INVALID, "reps must be positive");
+        ctx->use_device();
+        ptsbe_tuning t{};
+        cudaEvent_t e0, e1;
+        PTSBE_CUDA(cudaEventCreate(&e0));
+        PTSBE_CUDA(cudaEventCreate(&e1));
+        auto timed_ms = [&](auto&& call) {
+            int st = call();                                   // warm-up (plans, tables, workspace)
+            if (st != PTSBE_OK) return -1.0;
+            PTSBE_CUDA(cudaEventRecord(e0, ctx->stream));
+            for (uint32_t r = 0; r < reps && st == PTSBE_OK; ++r) st = call();
+            PTSBE_CUDA(cudaEventRecord(e1, ctx->stream));
+            PTSBE_CUDA(cudaEventSynchronize(e1));
+            if (st != PTSBE_OK) return -1.0;
+            float ms = 0;
+            PTSBE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            return (double)ms / reps;
+        };
+        const int keep_kernel = ctx->evolve_kernel;
+        const uint64_t keep_light = ctx->light_shots;
+        int best_k = -1;
+        double best = 0;
+        try {
+            for (int k : {3, 1, 2}) {
+                ctx->evolve_kernel = k;
+                const double ms = timed_ms([&] { return ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags); });
+                if (ms < 0) fail(PTSBE_ERR_INVALID, std::string("autotune: evolve kernel ") + std::to_string(k) + ": " + ctx->err);
+                t.evolve_ms[k] = ms;
+                if (best_k < 0 || ms < best) { best = ms; best_k = k; }
+            }
+            ctx->evolve_kernel = best_k;
+            PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
+            if (ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags) != PTSBE_OK)
+                fail(PTSBE_ERR_INVALID, "autotune: " + ctx->err);
+            const uint64_t cand[4] = {512, 4096, 65536, 1ull << 20};
+            int best_l = -1;
+            double best_s = 0;
+            for (int i = 0; i < 4; ++i) {
+                ctx->light_shots = cand[i];
+                t.light_candidates[i] = cand[i];
+                const double ms = timed_ms([&] {
+                    return ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bits, d_bits_capacity);
+                });
+                if (ms < 0) fail(PTSBE_ERR_INVALID, "autotune: sampler: " + ctx->err);
+                t.sample_ms[i] = ms;
+                if (best_l < 0 || ms < best_s) { best_s = ms; best_l = i; }
+            }
+            ctx->light_shots = cand[best_l];
+        } catch (...) {
+            ctx->evolve_kernel = keep_kernel;
+            ctx->light_shots = keep_light;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        t.evolve_kernel = ctx->evolve_kernel;
+        t.light_shots = ctx->light_shots;
+        if (out) *out = t;
     });
 }
 

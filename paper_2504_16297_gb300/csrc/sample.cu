@@ -336,12 +336,26 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
                 const uint32_t mid = (lo + hi) >> 1;
                 if (t < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
             }
+            // the chunk's amplitudes, eight 16-byte loads in flight at a time, then scanned in order
             fx acc = P[lpad(lo)];
-            const float2* ch = amps + ((size_t)lo << csb);
+            const float4* cv = reinterpret_cast<const float4*>(amps + ((size_t)lo << csb));
             idx = (lo << csb) + cs - 1;
-            for (uint32_t i = 0; i + 1 < cs; ++i) {
-                acc += fx_prob(__ldg(ch + i));
-                if (t < acc) { idx = (lo << csb) + i; break; }
+            bool hit = false;
+            for (uint32_t i0 = 0; i0 < cs / 2 && !hit; i0 += 8) {
+                float4 x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < cs / 2) x[u] = __ldg(cv + i0 + u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (hit || i0 + u >= cs / 2) continue;
+                    const uint32_t l0 = 2 * (i0 + u);
+                    acc += fx_prob(make_float2(x[u].x, x[u].y));
+                    if (t < acc) { idx = (lo << csb) + l0; hit = true; continue; }
+                    if (l0 + 1 == cs - 1) continue;      // the chunk's last entry is P[lo + 1] > t
+                    acc += fx_prob(make_float2(x[u].z, x[u].w));
+                    if (t < acc) { idx = (lo << csb) + l0 + 1; hit = true; }
+                }
             }
         }
         a.bits[it.out0 + k] = idx;

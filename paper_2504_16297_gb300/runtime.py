@@ -106,6 +106,18 @@ class Ptsbe:
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL,
                               {"auto": 0, "sweep": 1, "registers": 2, "frame": 3}[kernel])
 
+    def autotune(self, info: KrausSetInfo, first: int, count: int, states, weights, status, seed: int, bits,
+                 prefix_reuse: bool = True, reps: int = 3):
+        """Times every evolve kernel and sampler shot limit on this workload and keeps the fastest
+        (host-synchronous). Returns a dict of the choice and the measured milliseconds."""
+        flags = capi.PTSBE_EVOLVE_PREFIX_REUSE if prefix_reuse else 0
+        t = capi.ptsbe_autotune(self.ctx, info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), flags,
+                                seed, _ptr(bits), bits.numel(), reps)
+        names = {1: "sweep", 2: "registers", 3: "frame"}
+        return {"evolve_kernel": names.get(t.evolve_kernel, t.evolve_kernel), "light_shots": t.light_shots,
+                "evolve_ms": {names[k]: t.evolve_ms[k] for k in (1, 2, 3)},
+                "sample_ms": {int(t.light_candidates[i]): t.sample_ms[i] for i in range(4)}}
+
     def set_light_shots(self, limit: int):
         """Shot count up to which a state is sampled by the one-CTA light sampler."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_LIGHT_SHOTS, int(limit))

@@ -232,3 +232,38 @@ def test_sampler_light_states_bit_exact(P, oracle_mod, n):
     for a in range(count):
         o0, o1 = int(info.shot_offsets[a]), int(info.shot_offsets[a + 1])
         check_shots(b_h[o0:o1], st_h[a], 4242, a, 0, oracle_mod, n)
+
+
+def test_autotune_keeps_results(oracle_mod):
+    """The autotuner times every evolve kernel and sampler shot limit, keeps the fastest, and the
+    tuned context still matches the oracle (states) and gives the same shots as before tuning (the
+    shot limit changes no shot)."""
+    torch = torch_cuda()
+    P = gpu_ctx()
+    from workloads import syndrome17
+    circ = syndrome17(rounds=1)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "topk", k=60, total_shots=200000)
+    n = circ.n_qubits
+    st = torch.empty((info.count, 1 << n), dtype=torch.complex64, device="cuda")
+    w = torch.empty(info.count, dtype=torch.float64, device="cuda")
+    s = torch.empty(info.count, dtype=torch.uint8, device="cuda")
+    bits = torch.empty(info.total_shots, dtype=torch.int32, device="cuda")
+    P.evolve(info, 0, info.count, st, w, s, prefix_reuse=True)
+    P.sample(info, 0, info.count, st, s, 77, bits)
+    torch.cuda.synchronize()
+    before = bits.cpu().numpy().copy()
+    res = P.autotune(info, 0, info.count, st, w, s, 77, bits, reps=1)
+    assert res["evolve_kernel"] in ("frame", "sweep", "registers")
+    assert res["light_shots"] in res["sample_ms"]
+    assert all(v > 0 for v in res["evolve_ms"].values()) and all(v > 0 for v in res["sample_ms"].values())
+    st2, w2, s2 = evolve_gpu(P, info, 0, info.count, n, True)
+    o = oracle_mod.Oracle(circ)
+    ref = o.pts_targeted([info.entries(i) for i in range(info.count)], shots=np.asarray(info.shots, np.uint64))
+    for i in range(0, info.count, 7):
+        psi, wr, sr = o.evolve(ref, i)
+        compare_state(st2.cpu().numpy()[i], psi, float(w2.cpu()[i]), wr, int(s2.cpu()[i]), sr, f"set {i}")
+    if res["evolve_kernel"] == "frame":
+        P.sample(info, 0, info.count, st2, s2, 77, bits)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits.cpu().numpy(), before)
