@@ -421,6 +421,24 @@ def main():
         pershot = {"value": args.pershot_shots / (ps_ms / 1e3), "unit": "shots/s", "shots": args.pershot_shots,
                    "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot"}
 
+    # unique-shot statistic (Sec. 4): distinct outcomes among the shots of the heaviest sets, from
+    # one more step outside the timed region
+    uniq = None
+    if rank == 0:
+        cid = P.register(circ)
+        info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
+        P.evolve(info, 0, K, states, weights[0], status[0], prefix_reuse=True)
+        P.sample(info, 0, K, states, status[0], seed, bits[0])
+        top = 4
+        u = torch.zeros(top, dtype=torch.int64, device=dev)
+        P.unique_shots(info, 0, top, bits[0], u)
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        uniq = [{"set": a, "errors": len(info.entries(a)), "shots": int(info.shots[a]), "unique": int(uc[a]),
+                 "fraction": float(uc[a]) / max(1, int(info.shots[a]))} for a in range(top)]
+        P.release_set(info)
+        P.release_circuit(cid)
+
     bw = None
     if not args.no_backward:
         bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
@@ -465,6 +483,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "backward": bw,
+            "unique_shots": uniq,
         }
         print(json.dumps(out), flush=True)
     if dist:

@@ -163,7 +163,14 @@ typedef enum {
     PTSBE_PTS_TARGETED = 3,
     /* Algorithm 2 as printed: each (site, k != 0) draws r = U53(Philox(seed; s, i_lo, i_hi,
      * 4 | k << 8)) and is appended when r <= q_{s,k} and its site is still free (compatible). */
-    PTSBE_PTS_LITERAL = 4
+    PTSBE_PTS_LITERAL = 4,
+    /* Targeted error sets by rule (Sec. 3.1 "selection criteria"): every set of 1 .. max_errors
+     * errors at distinct sites whose every error (s, k) passes the filters -- site in
+     * [site_lo, site_hi), all qubits of the site in qubit_mask, Kraus index k in kraus_mask, the
+     * gate the site follows (the last gate before it that shares one of its qubits) in gate_mask
+     * -- and whose weight passes weight_parity; plus the empty set when include_empty. A zero
+     * mask or site_hi = 0 accepts everything. Shots by BY_PROB (default), UNIFORM or BY_COUNT. */
+    PTSBE_PTS_PREDICATE = 5
 } ptsbe_pts_mode;
 
 typedef enum {
@@ -186,6 +193,14 @@ typedef struct {
     const uint32_t* t_sites;    /* TARGETED: strictly increasing per set                      */
     const uint8_t* t_kidx;      /* TARGETED: 0 < k < n_kraus                                  */
     const uint64_t* t_shots;    /* TARGETED with SHOTS_GIVEN: [t_count]                       */
+    uint32_t max_errors;        /* PREDICATE: 1 .. 8 errors per set                           */
+    uint32_t include_empty;     /* PREDICATE: 1 adds the error-free set                       */
+    uint64_t qubit_mask;        /* PREDICATE: bit q allows sites on qubit q (0: all)          */
+    uint32_t kraus_mask;        /* PREDICATE: bit k allows Kraus index k >= 1 (0: all)        */
+    uint32_t gate_mask;         /* PREDICATE: bit g allows sites after gate code g (0: all)   */
+    uint32_t site_lo, site_hi;  /* PREDICATE: site range (site_hi = 0: all sites)             */
+    uint32_t weight_parity;     /* PREDICATE: 0 any, 1 odd, 2 even number of errors           */
+    uint64_t max_sets;          /* PREDICATE: PTSBE_ERR_UNSUPPORTED above this (0: 10^7)      */
 } ptsbe_pts_params;
 
 /* Runs a PTS algorithm and stores the resulting Kraus sets in the context. Sets are returned in
@@ -260,6 +275,14 @@ PTSBE_API int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * Asynchronous. Errors: PTSBE_ERR_BUFFER_TOO_SMALL, PTSBE_ERR_INVALID, PTSBE_ERR_OOM. */
 PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                        const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity);
+
+/* Unique-shot statistic (Sec. 4: the fraction of distinct outcomes among a set's shots): for sets
+ * [first, first + count) of set_id, d_unique[a] = number of distinct values among the shots of set
+ * first + a in d_bits (laid out as ptsbe_sample_shots writes them; the null-branch sentinel is not
+ * an outcome and is skipped). Device outputs, asynchronous. n_qubits <= 20 (else
+ * PTSBE_ERR_UNSUPPORTED). Errors: PTSBE_ERR_INVALID (range, null pointers). */
+PTSBE_API int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count,
+                                 const uint32_t* d_bits, uint64_t* d_unique);
 
 /* Same shots as ptsbe_sample_shots, bit for bit, for callers that cannot allocate device memory:
  * a program whose memory pool has already reserved the GPU, a fixed-footprint deployment that

@@ -293,6 +293,53 @@ def loss_grad_fd(circ, sets, masks, coeffs, h=1e-4, diag=None, param_slots=None,
     return per, dp, dn
 
 
+def predicate_sets(circ, max_errors, include_empty=False, qubit_mask=0, kraus_mask=0, gate_mask=0,
+                   site_lo=0, site_hi=0, weight_parity=0):
+    """Targeted error sets by rule (Sec. 3.1, "selection criteria"), written out from their
+    definition: an error (s, k) is eligible when s lies in [site_lo, site_hi) (site_hi 0: every
+    site), every qubit of the site is in qubit_mask, k >= 1 is in kraus_mask and the gate the site
+    follows (the last gate before it sharing one of its qubits) is in gate_mask (a zero mask
+    accepts all); the sets are all combinations of 1 .. max_errors eligible errors at distinct
+    sites whose number of errors has the requested parity (0 any, 1 odd, 2 even), plus the empty
+    set when include_empty. Returns them as (site, k) lists with increasing sites."""
+    import itertools
+    op_ints = np.asarray(circ.op_ints)
+    noise_ops = [i for i in range(circ.n_ops) if op_ints[i][0] == 1]
+    S = len(noise_ops)
+    hi = S if site_hi == 0 else min(site_hi, S)
+
+    def qubits(i):
+        return [int(op_ints[i][3])] + ([int(op_ints[i][4])] if op_ints[i][2] == 2 else [])
+
+    def gate_before(i):
+        for j in range(i - 1, -1, -1):
+            if op_ints[j][0] == 0 and set(qubits(j)) & set(qubits(i)):
+                return int(op_ints[j][1])
+        return None
+
+    options = []
+    for s in range(site_lo, hi):
+        i = noise_ops[s]
+        if qubit_mask and not all((qubit_mask >> q) & 1 for q in qubits(i)):
+            continue
+        if gate_mask:
+            g = gate_before(i)
+            if g is None or not (gate_mask >> g) & 1:
+                continue
+        nk = int(circ.ch_ints[int(op_ints[i][1])][2])
+        ks = [k for k in range(1, nk) if not kraus_mask or (kraus_mask >> k) & 1]
+        if ks:
+            options.append((s, ks))
+    out = [[]] if include_empty else []
+    for w in range(1, max_errors + 1):
+        if weight_parity == 1 and w % 2 == 0 or weight_parity == 2 and w % 2 == 1:
+            continue
+        for combo in itertools.combinations(options, w):
+            for kk in itertools.product(*[ks for (_, ks) in combo]):
+                out.append([(s, k) for (s, _), k in zip(combo, kk)])
+    return out
+
+
 def philox(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().or_philox(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)

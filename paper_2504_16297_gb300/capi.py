@@ -13,7 +13,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_NOT_CPTP", 3: "ERR_OOM", 4: "
                 5: "ERR_TIMEOUT", 6: "ERR_BUFFER_TOO_SMALL", 7: "ERR_UNSUPPORTED", 8: "ERR_NO_DEVICE"}
 
 PTSBE_OP_GATE, PTSBE_OP_NOISE = 0, 1
-PTSBE_PTS_PROPORTIONAL, PTSBE_PTS_TOPK, PTSBE_PTS_BAND, PTSBE_PTS_TARGETED, PTSBE_PTS_LITERAL = range(5)
+(PTSBE_PTS_PROPORTIONAL, PTSBE_PTS_TOPK, PTSBE_PTS_BAND, PTSBE_PTS_TARGETED, PTSBE_PTS_LITERAL,
+ PTSBE_PTS_PREDICATE) = range(6)
 PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVEN = range(4)
 PTSBE_EVOLVE_PREFIX_REUSE = 1
 PTSBE_OPT_EVOLVE_KERNEL = 0
@@ -37,7 +38,10 @@ class ptsbe_pts_params(C.Structure):
                 ("k", C.c_uint64), ("p_min", C.c_double), ("p_max", C.c_double),
                 ("total_shots", C.c_uint64), ("shots_per_set", C.c_uint64), ("t_count", C.c_uint32),
                 ("t_offsets", C.POINTER(C.c_uint32)), ("t_sites", C.POINTER(C.c_uint32)),
-                ("t_kidx", C.POINTER(C.c_uint8)), ("t_shots", C.POINTER(C.c_uint64))]
+                ("t_kidx", C.POINTER(C.c_uint8)), ("t_shots", C.POINTER(C.c_uint64)),
+                ("max_errors", C.c_uint32), ("include_empty", C.c_uint32), ("qubit_mask", C.c_uint64),
+                ("kraus_mask", C.c_uint32), ("gate_mask", C.c_uint32), ("site_lo", C.c_uint32),
+                ("site_hi", C.c_uint32), ("weight_parity", C.c_uint32), ("max_sets", C.c_uint64)]
 
 
 class ptsbe_set_view(C.Structure):
@@ -93,6 +97,7 @@ _PROTOS = {
                                  C.c_void_p]),
     "ptsbe_autotune": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(ptsbe_tuning)]),
+    "ptsbe_unique_shots": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -214,6 +219,10 @@ def ptsbe_autotune(ctx, set_id, first, count, d_states, d_weights, d_status, fla
     check(ctx, load().ptsbe_autotune(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed, d_bits,
                                      capacity, reps, C.byref(t)))
     return t
+
+
+def ptsbe_unique_shots(ctx, set_id, first, count, d_bits, d_unique):
+    check(ctx, load().ptsbe_unique_shots(ctx, set_id, first, count, d_bits, d_unique))
 
 
 def ptsbe_kernel_launches() -> int:

@@ -714,6 +714,30 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
     });
 }
 
+int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const uint32_t* d_bits,
+                       uint64_t* d_unique) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        KSet& s = ctx->set(set_id);
+        Circuit& c = ctx->circuit(s.circuit);
+        if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (count == 0) return;
+        if (!d_bits || !d_unique) fail(PTSBE_ERR_INVALID, "null device pointer");
+        if ((int)c.n > unique_max_qubits()) fail(PTSBE_ERR_UNSUPPORTED, "unique-shot statistic handles n <= 20");
+        ctx->use_device();
+        const uint64_t base = s.shot_off[first];
+        std::vector<uint64_t> ranges(2 * (size_t)count);
+        for (uint32_t a = 0; a < count; ++a) {
+            ranges[2 * a] = s.shot_off[first + a] - base;
+            ranges[2 * a + 1] = s.shot_off[first + a + 1] - base;
+        }
+        uint64_t* d_r = (uint64_t*)ctx->dalloc(ranges.size() * sizeof(uint64_t));
+        ctx->h2d(d_r, ranges.data(), ranges.size() * sizeof(uint64_t));
+        launch_unique(d_bits, d_r, count, (int)c.n, (unsigned long long*)d_unique, ctx->stream);
+        ctx->dfree(d_r);
+    });
+}
+
 int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
     return guarded(ctx, [&] {
         if (option == PTSBE_OPT_EVOLVE_KERNEL) {

@@ -10,6 +10,7 @@
 // Compiled without floating-point contraction so the FP64 decisions (categorical draws,
 // keys, quotas) are reproducible on every host.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -341,6 +342,78 @@ void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uin
     }
 }
 
+namespace {
+
+// Gate code of the last gate before op i that shares a qubit with it (UINT32_MAX if none).
+uint32_t gate_before(const Circuit& c, size_t i) {
+    const ptsbe_op& o = c.ops[i];
+    for (size_t j = i; j-- > 0;) {
+        const ptsbe_op& g = c.ops[j];
+        if (g.kind != PTSBE_OP_GATE) continue;
+        for (uint32_t a = 0; a < g.n_targets; ++a)
+            for (uint32_t b = 0; b < o.n_targets; ++b)
+                if (g.targets[a] == o.targets[b]) return g.id;
+    }
+    return UINT32_MAX;
+}
+
+// Targeted error sets by rule: the eligible (site, k) options, then every combination of 1 ..
+// max_errors options at distinct sites (sites increasing), filtered by weight parity.
+void pts_predicate(const Circuit& c, const ptsbe_pts_params& p, std::vector<std::pair<List, uint64_t>>& sets) {
+    if (p.max_errors < 1 || p.max_errors > 8) fail(PTSBE_ERR_INVALID, "PREDICATE needs 1 <= max_errors <= 8");
+    if (p.weight_parity > 2) fail(PTSBE_ERR_INVALID, "weight_parity must be 0, 1 or 2");
+    const uint32_t S = (uint32_t)c.site_ch.size();
+    const uint32_t lo = p.site_lo, hi = p.site_hi ? std::min<uint32_t>(p.site_hi, S) : S;
+    std::vector<uint32_t> site_of;            // eligible sites, increasing
+    std::vector<std::vector<uint8_t>> ks;     // their allowed Kraus indices
+    for (uint32_t s = lo; s < hi; ++s) {
+        const size_t op = c.site_op[s];
+        const ptsbe_op& o = c.ops[op];
+        bool ok = true;
+        if (p.qubit_mask)
+            for (uint32_t t = 0; t < o.n_targets; ++t) ok &= ((p.qubit_mask >> o.targets[t]) & 1ull) != 0;
+        if (ok && p.gate_mask) {
+            const uint32_t g = gate_before(c, op);
+            ok = g < 32 && ((p.gate_mask >> g) & 1u);
+        }
+        if (!ok) continue;
+        std::vector<uint8_t> kk;
+        const HostChannel& ch = c.ch[c.site_ch[s]];
+        for (uint32_t k = 1; k < ch.nk; ++k)
+            if (!p.kraus_mask || ((p.kraus_mask >> k) & 1u)) kk.push_back((uint8_t)k);
+        if (kk.empty()) continue;
+        site_of.push_back(s);
+        ks.push_back(std::move(kk));
+    }
+    // count before enumerating: e_w = number of w-error sets (elementary symmetric sums)
+    const uint64_t cap = p.max_sets ? p.max_sets : 10000000ull;
+    const uint32_t W = p.max_errors;
+    std::vector<double> e(W + 1, 0.0);
+    e[0] = 1.0;
+    for (const auto& kk : ks)
+        for (uint32_t w = W; w >= 1; --w) e[w] += e[w - 1] * (double)kk.size();
+    double total = p.include_empty ? 1.0 : 0.0;
+    for (uint32_t w = 1; w <= W; ++w)
+        if (p.weight_parity == 0 || (p.weight_parity == 1) == (w % 2 == 1)) total += e[w];
+    if (total > (double)cap) fail(PTSBE_ERR_UNSUPPORTED, "PREDICATE selects more than max_sets sets");
+    if (p.include_empty) sets.push_back({List{}, 1});
+    List cur;
+    std::function<void(size_t)> rec = [&](size_t from) {
+        const uint32_t w = (uint32_t)cur.size();
+        if (w >= 1 && (p.weight_parity == 0 || (p.weight_parity == 1) == (w % 2 == 1))) sets.push_back({cur, 1});
+        if (w == W) return;
+        for (size_t i = from; i < site_of.size(); ++i)
+            for (uint8_t k : ks[i]) {
+                cur.push_back({site_of[i], k});
+                rec(i + 1);
+                cur.pop_back();
+            }
+    };
+    rec(0);
+}
+
+}  // namespace
+
 void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& out) {
     std::vector<std::pair<List, uint64_t>> sets;
     std::vector<uint64_t> given;
@@ -395,6 +468,9 @@ void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& o
         }
         break;
     }
+    case PTSBE_PTS_PREDICATE:
+        pts_predicate(c, p, sets);
+        break;
     default:
         fail(PTSBE_ERR_INVALID, "unknown PTS mode");
     }

@@ -16,6 +16,7 @@
 // rebuilding the CDF.
 //
 // n > 17: the CDF is built in global workspace (block prefixes, block offsets) and searched there.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <mutex>
 
@@ -441,6 +442,37 @@ __global__ void k_search_global(SampleArgs a, const fx* __restrict__ cdf, const 
     }
 }
 
+// Distinct outcomes among the shots of each set (the unique-shot statistic of Sec. 4): one CTA per
+// set marks a bitmap of the 2^n outcomes in shared memory and counts its set bits. Shots that are
+// not outcomes (the null-branch sentinel) are skipped.
+__global__ void k_unique(const uint32_t* __restrict__ bits, const uint64_t* __restrict__ ranges, int n,
+                         unsigned long long* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long red[32];
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem);
+    const uint32_t words = (1u << n) >= 32 ? (1u << n) / 32 : 1u;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+    const uint64_t b0 = ranges[2 * blockIdx.x], b1 = ranges[2 * blockIdx.x + 1];
+    const uint64_t lim = 1ull << n;
+    for (uint64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+        const uint32_t x = bits[k];
+        if ((uint64_t)x < lim) atomicOr(&bm[x >> 5], 1u << (x & 31));
+    }
+    __syncthreads();
+    unsigned long long c = 0;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) c += (unsigned long long)__popc(bm[i]);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (uint32_t w = 0; w < (blockDim.x + 31) / 32; ++w) t += red[w];
+        out[blockIdx.x] = t;
+    }
+}
+
 __global__ void k_fill(uint32_t* bits, uint64_t count, uint32_t v) {
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (uint64_t)gridDim.x * blockDim.x)
         bits[k] = v;
@@ -585,6 +617,25 @@ void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, u
     k_search_global<<<blocks, 256, 0, s>>>(a, cdf, bend, nb, state, alpha, j0, j1, out0, dom);
     PTSBE_CUDA(cudaGetLastError());
         count_launch();
+}
+
+int unique_max_qubits() { return 20; }
+
+void launch_unique(const uint32_t* bits, const uint64_t* d_ranges, uint32_t count, int n, unsigned long long* out,
+                   cudaStream_t s) {
+    if (count == 0) return;
+    const size_t smem = std::max<size_t>(4, ((size_t)1 << n) / 8);
+    static bool configured = false;
+    if (!configured) {
+        PTSBE_CUDA(cudaFuncSetAttribute(k_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(((size_t)1 << 20) / 8)));
+        configured = true;
+    }
+    for (uint32_t b = 0; b < count; b += 65535u) {
+        const uint32_t cnt = std::min<uint32_t>(65535u, count - b);
+        k_unique<<<cnt, 1024, smem, s>>>(bits, d_ranges + 2 * (size_t)b, n, out + b);
+        PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    }
 }
 
 void launch_fill(uint32_t* bits, uint64_t count, uint32_t v, cudaStream_t s) {

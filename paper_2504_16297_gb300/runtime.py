@@ -135,19 +135,24 @@ class Ptsbe:
     # -- pre-trajectory sampling -------------------------------------------------------------------
     def sample_kraus(self, cid: int, mode: str, seed: int = 0, *, nsamples=0, k=0, p_min=0.0, p_max=1.0,
                      total_shots=0, shots_per_set=0, shot_alloc=None, targeted=None, targeted_shots=None,
-                     export=True):
+                     export=True, max_errors=1, include_empty=False, qubit_mask=0, kraus_mask=0, gate_mask=0,
+                     site_lo=0, site_hi=0, weight_parity=0, max_sets=0):
         p = capi.ptsbe_pts_params()
         modes = dict(proportional=capi.PTSBE_PTS_PROPORTIONAL, topk=capi.PTSBE_PTS_TOPK,
-                     band=capi.PTSBE_PTS_BAND, targeted=capi.PTSBE_PTS_TARGETED, literal=capi.PTSBE_PTS_LITERAL)
+                     band=capi.PTSBE_PTS_BAND, targeted=capi.PTSBE_PTS_TARGETED, literal=capi.PTSBE_PTS_LITERAL,
+                     predicate=capi.PTSBE_PTS_PREDICATE)
         p.mode = modes[mode]
         allocs = dict(count=capi.PTSBE_SHOTS_BY_COUNT, uniform=capi.PTSBE_SHOTS_UNIFORM,
                       prob=capi.PTSBE_SHOTS_BY_PROB, given=capi.PTSBE_SHOTS_GIVEN)
         if shot_alloc is None:
             shot_alloc = {"proportional": "count", "topk": "prob", "band": "prob", "literal": "uniform",
-                          "targeted": "given" if targeted_shots is not None else "prob"}[mode]
+                          "targeted": "given" if targeted_shots is not None else "prob", "predicate": "prob"}[mode]
         p.shot_alloc = allocs[shot_alloc]
         p.nsamples, p.k, p.p_min, p.p_max = nsamples, k, p_min, p_max
         p.total_shots, p.shots_per_set = total_shots, shots_per_set
+        p.max_errors, p.include_empty, p.qubit_mask = int(max_errors), int(bool(include_empty)), int(qubit_mask)
+        p.kraus_mask, p.gate_mask, p.site_lo, p.site_hi = int(kraus_mask), int(gate_mask), int(site_lo), int(site_hi)
+        p.weight_parity, p.max_sets = int(weight_parity), int(max_sets)
         keep = []
         if targeted is not None:
             offs, sites, ks = [0], [], []
@@ -218,6 +223,10 @@ class Ptsbe:
         obs.d_diag = _ptr(diag)
         capi.ptsbe_backward(self.ctx, cid, info.set_id, first, count, obs, checkpoint_every, _ptr(loss), _ptr(per_set),
                             _ptr(grad_params), _ptr(grad_noise))
+
+    def unique_shots(self, info: KrausSetInfo, first: int, count: int, bits, out):
+        """out[a] (int64 device tensor) = number of distinct outcomes among the shots of set first + a."""
+        capi.ptsbe_unique_shots(self.ctx, info.set_id, first, count, _ptr(bits), _ptr(out))
 
     def pershot(self, cid: int, seed: int, first_shot: int, n_shots: int, bits, kraus=None):
         capi.ptsbe_pershot_run(self.ctx, cid, seed, first_shot, n_shots, _ptr(bits), _ptr(kraus))

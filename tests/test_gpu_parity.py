@@ -267,3 +267,31 @@ def test_autotune_keeps_results(oracle_mod):
         P.sample(info, 0, info.count, st2, s2, 77, bits)
         torch.cuda.synchronize()
         assert np.array_equal(bits.cpu().numpy(), before)
+
+
+@pytest.mark.parametrize("which", ["syndrome", "small"])
+def test_unique_shot_statistic(oracle_mod, which):
+    """Distinct outcomes per set (the unique-shot statistic of Sec. 4) against numpy's count of
+    the same shots; the null-branch sentinel is not an outcome."""
+    torch = torch_cuda()
+    P = gpu_ctx()
+    if which == "syndrome":
+        from workloads import syndrome17
+        circ = syndrome17(rounds=1)
+        info = P.sample_kraus(P.register(circ), "topk", k=40, total_shots=300000)
+    else:
+        circ = brickwork(4, 3, 0.05, 0.05, 9)
+        info = P.sample_kraus(P.register(circ), "proportional", seed=3, nsamples=50, total_shots=5000)
+    n = circ.n_qubits
+    st, w, s = evolve_gpu(P, info, 0, info.count, n, True)
+    bits = torch.empty(max(info.total_shots, 1), dtype=torch.int32, device="cuda")
+    P.sample(info, 0, info.count, st, s, 5, bits)
+    u = torch.zeros(info.count, dtype=torch.int64, device="cuda")
+    P.unique_shots(info, 0, info.count, bits, u)
+    torch.cuda.synchronize()
+    b = bits.cpu().numpy().view(np.uint32)
+    got = u.cpu().numpy()
+    for a in range(info.count):
+        x = b[int(info.shot_offsets[a]): int(info.shot_offsets[a + 1])]
+        x = x[x < (1 << n)]
+        assert got[a] == len(np.unique(x)), (a, got[a], len(np.unique(x)))

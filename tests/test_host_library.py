@@ -8,7 +8,7 @@ import re
 import numpy as np
 import pytest
 
-from workloads import CircuitBuilder, config
+from workloads import CircuitBuilder, config, GATE
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -163,3 +163,34 @@ def test_circuit_info(host):
         cid = host.register(circ)
         nq, ns, ng = host.circuit_info(cid)
         assert (nq, ns, ng) == (circ.n_qubits, circ.n_sites, circ.n_gates)
+
+
+PREDICATES = [
+    dict(max_errors=1),
+    dict(max_errors=2, include_empty=True),
+    dict(max_errors=2, qubit_mask=0b0000110011, kraus_mask=0b0110),
+    dict(max_errors=3, gate_mask=1 << GATE["CX"], site_lo=20, site_hi=90, weight_parity=1),
+    dict(max_errors=2, gate_mask=1 << GATE["U3"], kraus_mask=1 << 3, weight_parity=2, include_empty=True),
+]
+
+
+@pytest.mark.parametrize("pred", PREDICATES)
+def test_predicate_targeted_bit_exact(host, oracle_mod, pred):
+    """Targeted error sets by rule (NEXT-4): the library's enumeration equals the oracle's plain
+    enumeration from the definition (sets in canonical order, q_alpha and shots bit-exact)."""
+    circ = config(0)["circuit"]
+    cid = host.register(circ)
+    got = host.sample_kraus(cid, "predicate", total_shots=123457, **pred)
+    sets = oracle_mod.predicate_sets(circ, **pred)
+    want = oracle_mod.Oracle(circ).pts_targeted(sets, total_shots=123457)
+    assert got.count == len(sets) > 0
+    _assert_same_sets(got, want)
+
+
+def test_predicate_refuses_too_many_sets(host):
+    from paper_2504_16297_gb300.capi import PtsbeError
+    circ = config(0)["circuit"]
+    cid = host.register(circ)
+    with pytest.raises(PtsbeError) as e:
+        host.sample_kraus(cid, "predicate", total_shots=10, max_errors=3, max_sets=1000)
+    assert e.value.status == 7

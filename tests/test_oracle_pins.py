@@ -513,3 +513,33 @@ def test_loss_is_importance_weighted_expectation(oracle_mod):
     ov = sum(c * np.where(np.array([bin(v & int(mk)).count("1") % 2 for v in x]) == 1, -1.0, 1.0)
              for mk, c in zip(masks, coeffs))
     assert abs(total - float((diag * ov).sum())) < 1e-12
+
+
+def test_predicate_sets_against_full_enumeration(oracle_mod):
+    """The oracle's rule-based targeted sets equal the sets picked, by the same rule, from the
+    independent enumeration of every Kraus combination (tests/densmat.py); with every filter open
+    and max_errors = S they are all combinations, whose nominal probabilities sum to 1."""
+    circ = small_mixed_circuit()
+    o = oracle_mod.Oracle(circ)
+    S = o.n_sites
+    allc = [sorted(c) for c in densmat.all_kraus_sets(circ)]
+    op_ints = np.asarray(circ.op_ints)
+    noise_ops = [i for i in range(circ.n_ops) if op_ints[i][0] == 1]
+
+    def site_qubits(s):
+        i = noise_ops[s]
+        return {int(op_ints[i][3])} | ({int(op_ints[i][4])} if op_ints[i][2] == 2 else set())
+
+    for kw, keep in [
+        (dict(max_errors=S, include_empty=True), lambda c: True),
+        (dict(max_errors=2), lambda c: 1 <= len(c) <= 2),
+        (dict(max_errors=3, qubit_mask=0b101, weight_parity=1),
+         lambda c: len(c) in (1, 3) and all(site_qubits(s) <= {0, 2} for s, _ in c)),
+        (dict(max_errors=2, kraus_mask=0b0010, site_lo=2, site_hi=8, include_empty=True),
+         lambda c: len(c) <= 2 and all(k == 1 and 2 <= s < 8 for s, k in c)),
+    ]:
+        got = sorted(tuple(x) for x in oracle_mod.predicate_sets(circ, **kw))
+        want = sorted(tuple(c) for c in allc if keep(c))
+        assert got == want
+    sets = o.pts_targeted(oracle_mod.predicate_sets(circ, max_errors=S, include_empty=True), total_shots=10)
+    assert abs(float(np.sum(sets.q)) - 1.0) < 1e-12
