@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--backward-only", action="store_true",
                     help="run only the adjoint-backward measurement and print its JSON object")
     ap.add_argument("--backward-samples", type=int, default=4096)
+    ap.add_argument("--uneven", action="store_true",
+                    help="also run the uneven batch (512 brickwork circuits, 12-22 qubits, 64 samples each)")
+    ap.add_argument("--uneven-only", action="store_true", help="run only the uneven batch and print its JSON object")
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
     return ap.parse_args()
@@ -234,6 +237,26 @@ def backward_leg(P, dev, reps: int = 3, cpu: bool = True, nsamples: int = 4096):
     return out
 
 
+def uneven_leg(dev_index: int, streams: int = 4):
+    """The uneven batch: 512 brickwork circuits (n ~ U{12..22}, depth ~ U{10..40}), 64 proportional
+    samples each, shot budgets ~ LogUniform(1e3, 1e6), through UnevenBatch (4 contexts and
+    streams); evolve kernel per size from the autotuner (outside the timed run). Shots stay on the
+    device; the time covers host PTS, registration and all kernels."""
+    from paper_2504_16297_gb300.batch import UnevenBatch
+    from workloads import config
+    cfg = config(2)
+    circs, shots = cfg["circuits"], cfg["shots"]
+    B = UnevenBatch(device=dev_index, streams=streams, max_qubits=max(c.n_qubits for c in circs),
+                    max_sets=cfg["nsamples"], max_shots=int(np.max(shots)))
+    kernels = B.autotune(circs, shots, cfg["nsamples"], cfg["seed"])
+    B.run(circs[:8], shots[:8], cfg["nsamples"], cfg["seed"])       # warm-up
+    secs, total, counts, _ = B.run(circs, shots, cfg["nsamples"], cfg["seed"])
+    return {"workload": cfg["name"], "circuits": len(circs), "sets": int(np.sum(counts)), "shots": int(total),
+            "seconds": secs, "shots_per_s": total / secs, "streams": streams,
+            "evolve_kernel_by_qubits": {str(k): v for k, v in sorted(kernels.items())},
+            "kind": "one context and stream per worker, circuits round-robin; not a single persistent launch"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -296,6 +319,11 @@ def main():
     from paper_2504_16297_gb300.runtime import Ptsbe
     from workloads import config
     build()
+
+    if args.uneven_only:
+        if rank == 0:
+            print(json.dumps({"uneven": uneven_leg(local)}), flush=True)
+        return
 
     if args.backward_only:
         dev = torch.device("cuda", local)
@@ -443,6 +471,8 @@ def main():
     if not args.no_backward:
         bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
+    unev = uneven_leg(local) if (args.uneven and rank == 0) else None
+
     ms_step = ms / args.steps
     value = job_throughput(world, M, ms_step)
     e2e_value = job_throughput(world, M, ms_e2e / steps_e2e)
@@ -484,6 +514,7 @@ def main():
             "clocks": clk,
             "backward": bw,
             "unique_shots": uniq,
+            "uneven": unev,
         }
         print(json.dumps(out), flush=True)
     if dist:

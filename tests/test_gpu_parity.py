@@ -295,3 +295,28 @@ def test_unique_shot_statistic(oracle_mod, which):
         x = b[int(info.shot_offsets[a]): int(info.shot_offsets[a + 1])]
         x = x[x < (1 << n)]
         assert got[a] == len(np.unique(x)), (a, got[a], len(np.unique(x)))
+
+
+def test_uneven_batch_matches_single_context(oracle_mod):
+    """The uneven-batch runner (several contexts, one stream each, circuits of different sizes)
+    gives every circuit the same shots as a direct run of the same calls on one context."""
+    torch = torch_cuda()
+    from paper_2504_16297_gb300.batch import UnevenBatch
+    cfg = config(2, small=True)
+    circs, shots = cfg["circuits"], cfg["shots"]
+    B = UnevenBatch(streams=3, max_qubits=max(c.n_qubits for c in circs), max_sets=cfg["nsamples"],
+                    max_shots=int(np.max(shots)))
+    B.autotune(circs, shots, cfg["nsamples"], cfg["seed"])
+    secs, total, counts, kept = B.run(circs, shots, cfg["nsamples"], cfg["seed"], keep=set(range(len(circs))))
+    assert total == int(np.sum(shots))
+    P = gpu_ctx()
+    for i, c in enumerate(circs):
+        P.set_evolve_kernel(B.kernel_by_n[c.n_qubits])
+        info = P.sample_kraus(P.register(c), "proportional", seed=cfg["seed"] + i, nsamples=cfg["nsamples"],
+                              total_shots=int(shots[i]))
+        st, w, s = evolve_gpu(P, info, 0, info.count, c.n_qubits, True)
+        bits = torch.empty(info.total_shots, dtype=torch.int32, device="cuda")
+        P.sample(info, 0, info.count, st, s, cfg["seed"] + i, bits)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits.cpu().numpy(), kept[i][0].numpy()), f"circuit {i}"
+        assert info.count == counts[i]
