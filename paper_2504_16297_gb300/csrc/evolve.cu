@@ -226,19 +226,74 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
     }
     if constexpr (SMALL) {
         // The state is all zeros outside the support: the copy engine writes those zeros (bulk
-        // copies of a zeroed shared buffer, issued by one thread) while the CTA runs the program;
-        // the sparse final waits for them before it scatters the support.
+        // copies of a zeroed shared buffer) while the CTA runs the program. Warp 0 only issues
+        // the copies (issue stalls while the copy queue is full, so it keeps out of the program's
+        // barriers); warps 2-3 run the program with a 64-thread named barrier (the executors step
+        // through cosets by thread-count bits, so the count is a power of two); everyone meets
+        // for the norm and the scatter once warp 0 has waited for the copies.
+        __shared__ Step fin;
         for (uint32_t v = tid; v < (uint32_t)kZeroChunk / 16; v += nthr) zbuf[v] = make_float4(0.f, 0.f, 0.f, 0.f);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
-            const uint32_t src = (uint32_t)__cvta_generic_to_shared(zbuf);
-            const uint64_t bytes = (uint64_t)8 << n;
-            for (uint64_t off = 0; off < bytes; off += kZeroChunk)
-                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                             :: "l"(reinterpret_cast<unsigned char*>(g) + off), "r"(src), "n"(kZeroChunk) : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        if (B.npool <= (uint32_t)kMaxPool) poolp = pool;
+        if (B.nsteps <= (uint32_t)kMaxSteps) Sp = S;
+        const uint32_t warp = tid >> 5;
+        if (warp == 0) {
+            if (tid == 0) {
+                const uint32_t src = (uint32_t)__cvta_generic_to_shared(zbuf);
+                const uint64_t bytes = (uint64_t)8 << n;
+                for (uint64_t off = 0; off < bytes; off += kZeroChunk)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                                 :: "l"(reinterpret_cast<unsigned char*>(g) + off), "r"(src), "n"(kZeroChunk) : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+        } else if (warp >= 2) {
+            const uint32_t pt = tid - 64, pn = 64;
+            auto pbar = [&]() { asm volatile("bar.sync 1, %0;" :: "r"(pn) : "memory"); };
+            if (pt == 0) { fin.kind = ST_FINAL; fin.ncomp = 0xFF; fin.ntab = 0; }   // scatters nothing unless set
+            pbar();
+            bool found = false;
+            while (!found) {
+                const uint32_t ns = B.nsteps;
+                for (uint32_t si = 0; si < ns; ++si) {
+                    const Step& sp = Sp[si];
+                    if (sp.ntab) {
+                        prepare_tables(sp, fs, poolp, tabs, delta, tb, tau, pt, pn);
+                        pbar();
+                    }
+                    if (sp.kind == ST_MIX1) run_mix1(sp, poolp, tile, tabs, delta, tb, tau, pt, pn);
+                    else if (sp.kind == ST_MIX2) run_mix2(sp, tile, tabs, delta, tb, tau, pt, pn);
+                    else if (sp.kind == ST_DIAG) run_diag(sp, tile, tabs, delta, tb, pt, pn);
+                    else if (sp.kind == ST_FINAL) {
+                        // plain loads: the step is in shared memory when the program fits there
+                        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(&sp);
+                        uint32_t* d32 = reinterpret_cast<uint32_t*>(&fin);
+                        for (uint32_t i = pt; i < (uint32_t)(sizeof(Step) / 4); i += pn) d32[i] = s32[i];
+                        found = true;
+                    }
+                    pbar();
+                    if (found) break;
+                }
+                if (found || B.done) break;
+                if (pt == 0) build_segment(B, S, pool, a, st, kMaxSteps, kMaxPool);
+                pbar();
+                Sp = S;
+                poolp = pool;
+            }
         }
+        __syncthreads();
+        const double part = cta_sum(run_sparse_final(fin, fs, tile, tabs, delta, n, lb, hi, nullptr, 1.0f, 0, tid, nthr), red);
+        const double w = a.wmix[node] * part;
+        const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
+        const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
+        if (!null) run_sparse_final(fin, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
+        if (tid == 0) {
+            if (a.weights) a.weights[node] = w;
+            if (a.status) a.status[node] = null ? 1 : 0;
+        }
+        return;
     }
     __syncthreads();
     if (B.npool <= (uint32_t)kMaxPool) poolp = pool;

@@ -38,8 +38,9 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     // the small-buffer kernel (sparse final stage with a support bound) runs 128 threads
     const bool small = a.fstages[stage].sparse_final && a.fstages[stage].sbits > 0;
-    const uint32_t nthr = small ? 128u : threads_for(tb);   // the small-buffer kernel: 128 threads
-    const uint32_t nthr_final = nthr;
+    // the small-buffer kernel runs the program on warps 2-3 (64 threads) and the final store on 128
+    const uint32_t nthr = small ? 64u : threads_for(tb);
+    const uint32_t nthr_final = small ? 128u : nthr;
     const uint32_t tamps = small ? 1u << a.fstages[stage].sbits : 1u << tb;
     std::vector<float2> tile(1u << tb), tabs((size_t)kMaxTabs * kTabSize);
     // past the buffer the kernel would have: a sentinel that must survive the whole CTA, and that
