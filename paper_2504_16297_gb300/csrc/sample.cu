@@ -264,6 +264,8 @@ __global__ void __launch_bounds__(kSampleThreads, 1) k_sample_cluster(SampleArgs
 constexpr int kLightChunkBits = 13;
 constexpr int kLightChunks = 1 << kLightChunkBits;
 constexpr int kLightThreads = 512;
+constexpr int kLightGuideBits = 8;
+constexpr int kLightGuide = 1 << kLightGuideBits;
 constexpr int kLightPerThread = kLightChunks / kLightThreads;   // chunks scanned by one thread (16)
 
 __device__ __forceinline__ uint32_t lpad(uint32_t c) { return c + (c >> 4); }   // bank-distinct rows of 16
@@ -271,6 +273,7 @@ __device__ __forceinline__ uint32_t lpad(uint32_t c) { return c + (c >> 4); }   
 __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a, const SampleItem* __restrict__ items) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ fx red[33];
+    __shared__ uint16_t lguide[kLightGuide + 1];
     fx* P = reinterpret_cast<fx*>(smem);               // padded: P[lpad(c)], c = 0 .. kLightChunks
     const SampleItem it = items[blockIdx.x];
     const uint64_t nshots = it.j1 - it.j0;
@@ -326,13 +329,29 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
     const fx T = red[32];
     if (threadIdx.x == 0) P[lpad(kLightChunks)] = T;
     __syncthreads();
+    // guide: the first chunk c with cut b < P[c + 1], cut b = floor(b T / 256); a shot whose
+    // uniform has top bits b has floor(u T) between cuts b and b + 1, so its chunk lies between
+    // the two guide entries
+    for (uint32_t b = threadIdx.x; b < (uint32_t)kLightGuide; b += blockDim.x) {
+        const fx cut = __umul64hi((fx)b << (64 - kLightGuideBits), T);
+        uint32_t lo = 0, hi = kLightChunks - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cut < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
+        }
+        lguide[b] = (uint16_t)lo;
+    }
+    if (threadIdx.x == 0) lguide[kLightGuide] = kLightChunks - 1;
+    __syncthreads();
     for (uint64_t k = threadIdx.x; k < nshots; k += blockDim.x) {
         const uint64_t j = it.j0 + k;
         const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, it.dom, (uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-        const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
+        const uint64_t m = u53_bits(x.x[0], x.x[1]);
+        const fx t = fx_target(m, T);
         uint32_t idx = (1u << n) - 1;                   // T = 0
         if (t < T) {
-            uint32_t lo = 0, hi = kLightChunks - 1;     // first chunk c with t < P[c + 1]
+            const uint32_t gb = (uint32_t)(m >> (53 - kLightGuideBits));
+            uint32_t lo = lguide[gb], hi = lguide[gb + 1];   // first chunk c with t < P[c + 1]
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
                 if (t < P[lpad(mid + 1)]) hi = mid; else lo = mid + 1;
