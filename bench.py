@@ -218,7 +218,19 @@ def backward_leg(P, dev, reps: int = 3, cpu: bool = True, nsamples: int = 4096):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # FP32 roofline of the adjoint (state and adjoint stay on chip): useful FLOPs per set, a
+    # complex multiply-add counted as 8 flops. Forward: B phi (one-qubit block 4 cmadd per pair,
+    # two-qubit 16 per quad); reverse: B^-1 phi, the outer product and B^dag mu (3x that).
+    plan = P.backward_plan_info(cid)
+    per_amp = 8 * ((2 * plan["blocks_1q"] + 4 * plan["blocks_2q"]) * 4)      # fwd + 3x rev, per amplitude
+    flops = float(info.count) * float(1 << n) * per_amp
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12              # FP32 FMA lanes x 2 x max clock
     out = {"workload": f"ansatz16_8layers_{nsamples}samples", "sets": info.count, "ms": ms,
+           "plan": plan,
+           "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": flops / (ms / 1e3) / 1e12 / peak,
+                        "peak_kind": "derived: SMs x 128 FP32 FMA lanes x 2 flops x 2.07 GHz (no measured FP32 peak)"},
            "sets_per_s": info.count / (ms / 1e3), "gradient_entries": 256 + 2, "loss": float(loss.cpu()[0]),
            "kernel": "k_backward (cluster of 8 CTAs per set, state and adjoint in DSMEM) + k_backward_finish"}
     if cpu:

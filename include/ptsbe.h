@@ -339,6 +339,12 @@ typedef struct {
  * Asynchronous on the context stream. Errors: PTSBE_ERR_INVALID (range, structure, null
  * observable, a set with q_alpha = 0), PTSBE_ERR_UNSUPPORTED (n > 16, longer sets),
  * PTSBE_ERR_OOM, PTSBE_ERR_CUDA. */
+/* Shape of the backward plan of a circuit (built on first use): fused blocks of one and two
+ * qubits, qubit-position swaps between cluster CTAs, blocks holding a differentiable parameter.
+ * Any pointer may be NULL. Host-only work. Errors: PTSBE_ERR_INVALID, PTSBE_ERR_UNSUPPORTED (n > 16). */
+PTSBE_API int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* blocks_1q, uint32_t* blocks_2q,
+                                       uint32_t* swaps, uint32_t* differentiable_blocks);
+
 PTSBE_API int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
                              const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss,
                              double* d_per_set, double* d_grad_params, double* d_grad_noise);

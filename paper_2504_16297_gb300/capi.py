@@ -98,6 +98,8 @@ _PROTOS = {
     "ptsbe_autotune": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(ptsbe_tuning)]),
     "ptsbe_unique_shots": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
+    "ptsbe_backward_plan_info": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                           C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -223,6 +225,12 @@ def ptsbe_autotune(ctx, set_id, first, count, d_states, d_weights, d_status, fla
 
 def ptsbe_unique_shots(ctx, set_id, first, count, d_bits, d_unique):
     check(ctx, load().ptsbe_unique_shots(ctx, set_id, first, count, d_bits, d_unique))
+
+
+def ptsbe_backward_plan_info(ctx, circuit_id):
+    v = [C.c_uint32() for _ in range(4)]
+    check(ctx, load().ptsbe_backward_plan_info(ctx, circuit_id, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def ptsbe_kernel_launches() -> int:

@@ -912,6 +912,24 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
     });
 }
 
+int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* blocks_1q, uint32_t* blocks_2q,
+                             uint32_t* swaps, uint32_t* differentiable_blocks) {
+    return guarded(ctx, [&] {
+        Circuit& c = ctx->circuit(circuit_id);
+        if (c.n > (uint32_t)kBwMaxQubits) fail(PTSBE_ERR_UNSUPPORTED, "backward handles at most 16 qubits");
+        BwPlan local;
+        const BwPlan* P = &c.bw;
+        if (!c.bw.built) { make_backward_plan(c, local); P = &local; }
+        uint32_t n1 = 0, n2 = 0, ns = 0, nd = 0;
+        for (const BwItem& it : P->items) { (it.nq == 2 ? n2 : n1)++; nd += it.diff ? 1u : 0u; }
+        for (const BwStep& st : P->steps) ns += st.kind == 1 ? 1u : 0u;
+        if (blocks_1q) *blocks_1q = n1;
+        if (blocks_2q) *blocks_2q = n2;
+        if (swaps) *swaps = ns;
+        if (differentiable_blocks) *differentiable_blocks = nd;
+    });
+}
+
 int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
                    const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss, double* d_per_set,
                    double* d_grad_params, double* d_grad_noise) {

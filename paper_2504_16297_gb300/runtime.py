@@ -228,5 +228,10 @@ class Ptsbe:
         """out[a] (int64 device tensor) = number of distinct outcomes among the shots of set first + a."""
         capi.ptsbe_unique_shots(self.ctx, info.set_id, first, count, _ptr(bits), _ptr(out))
 
+    def backward_plan_info(self, cid: int):
+        """(one-qubit blocks, two-qubit blocks, qubit-position swaps, differentiable blocks)."""
+        b1, b2, sw, nd = capi.ptsbe_backward_plan_info(self.ctx, cid)
+        return {"blocks_1q": b1, "blocks_2q": b2, "swaps": sw, "differentiable_blocks": nd}
+
     def pershot(self, cid: int, seed: int, first_shot: int, n_shots: int, bits, kraus=None):
         capi.ptsbe_pershot_run(self.ctx, cid, seed, first_shot, n_shots, _ptr(bits), _ptr(kraus))
