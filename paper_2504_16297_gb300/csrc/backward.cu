@@ -24,9 +24,11 @@ namespace cg = cooperative_groups;
 namespace ptsbe {
 namespace {
 
-constexpr int kBwThreads = 256;
+constexpr int kBwThreads = 256;       // 8 warps of up to 255 registers: 4x4 blocks, inverses and outer products in registers
 constexpr int kBwWarps = kBwThreads / 32;
-constexpr int kSwapPer = (1 << (kBwLocalBits - 1)) / kBwThreads;   // half a slice per thread
+constexpr int kSwapPer = ((1 << (kBwLocalBits - 1)) + kBwThreads - 1) / kBwThreads;   // half a slice per thread
+constexpr int kFinThreads = 256;      // the finishing kernel
+constexpr int kFinWarps = kFinThreads / 32;
 
 struct ErrEnt {
     uint32_t item, member, k;
@@ -495,13 +497,13 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_backward(BwArgs a) {
 
 // Default blocks: sum the per-slot accumulators, contract with the variant-0 derivatives; then add
 // the per-set contractions and the unitary-mixture terms, and scatter to the outputs.
-__global__ void __launch_bounds__(256) k_backward_finish(BwArgs a) {
-    __shared__ double2 sc[kBwWarps][32];
-    __shared__ double Gs[kBwWarps][32];
+__global__ void __launch_bounds__(kFinThreads) k_backward_finish(BwArgs a) {
+    __shared__ double2 sc[kFinWarps][32];
+    __shared__ double Gs[kFinWarps][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t d = tid; d < a.ndslots; d += blockDim.x) a.dtot[d] = 0;
     __syncthreads();
-    for (uint32_t b = warp; b < a.nitems; b += kBwWarps) {
+    for (uint32_t b = warp; b < a.nitems; b += kFinWarps) {
         const BwItem it = a.items[b];
         if (!it.diff) continue;
         double s = 0;
@@ -615,7 +617,7 @@ void launch_backward(const BwArgs& a, cudaStream_t s) {
         default: fail(PTSBE_ERR_UNSUPPORTED, "backward cluster size");
         }
     }
-    k_backward_finish<<<1, 256, 0, s>>>(a);
+    k_backward_finish<<<1, kFinThreads, 0, s>>>(a);
     PTSBE_CUDA(cudaGetLastError());
     count_launch();
 }
