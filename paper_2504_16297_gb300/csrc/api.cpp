@@ -725,16 +725,23 @@ int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         if (!d_bits || !d_unique) fail(PTSBE_ERR_INVALID, "null device pointer");
         if ((int)c.n > unique_max_qubits()) fail(PTSBE_ERR_UNSUPPORTED, "unique-shot statistic handles n <= 20");
         ctx->use_device();
+        // pieces (set, begin, end) of at most 2^18 shots, so heavy sets spread over many CTAs
         const uint64_t base = s.shot_off[first];
-        std::vector<uint64_t> ranges(2 * (size_t)count);
+        const uint64_t piece = 1ull << 18;
+        std::vector<uint64_t> pieces;
         for (uint32_t a = 0; a < count; ++a) {
-            ranges[2 * a] = s.shot_off[first + a] - base;
-            ranges[2 * a + 1] = s.shot_off[first + a + 1] - base;
+            const uint64_t b0 = s.shot_off[first + a] - base, b1 = s.shot_off[first + a + 1] - base;
+            for (uint64_t x = b0; x < b1; x += piece) pieces.insert(pieces.end(), {(uint64_t)a, x, std::min(b1, x + piece)});
         }
-        uint64_t* d_r = (uint64_t*)ctx->dalloc(ranges.size() * sizeof(uint64_t));
-        ctx->h2d(d_r, ranges.data(), ranges.size() * sizeof(uint64_t));
-        launch_unique(d_bits, d_r, count, (int)c.n, (unsigned long long*)d_unique, ctx->stream);
-        ctx->dfree(d_r);
+        const uint32_t np = (uint32_t)(pieces.size() / 3);
+        const size_t bm_bytes = unique_bitmap_bytes((int)c.n) * count;
+        unsigned char* buf = (unsigned char*)ctx->dalloc(((bm_bytes + 255) & ~(size_t)255) + std::max<size_t>(pieces.size(), 1) * 8);
+        uint32_t* d_bm = (uint32_t*)buf;
+        uint64_t* d_p = (uint64_t*)(buf + ((bm_bytes + 255) & ~(size_t)255));
+        PTSBE_CUDA(cudaMemsetAsync(d_bm, 0, bm_bytes, ctx->stream));
+        if (np) ctx->h2d(d_p, pieces.data(), pieces.size() * sizeof(uint64_t));
+        launch_unique(d_bits, d_p, np, count, (int)c.n, d_bm, (unsigned long long*)d_unique, ctx->stream);
+        ctx->dfree(buf);
     });
 }
 

@@ -433,8 +433,9 @@ uint32_t backward_slots(int n, uint32_t count, int n_sm);
 void launch_backward(const BwArgs& a, cudaStream_t s);
 
 int unique_max_qubits();
-void launch_unique(const uint32_t* bits, const uint64_t* d_ranges, uint32_t count, int n, unsigned long long* out,
-                   cudaStream_t s);
+size_t unique_bitmap_bytes(int n);
+void launch_unique(const uint32_t* bits, const uint64_t* d_pieces, uint32_t n_pieces, uint32_t count, int n,
+                   uint32_t* d_bitmaps, unsigned long long* out, cudaStream_t s);
 int sample_cluster_max_qubits();
 int sample_light_max_qubits();
 // Default shot limit of the one-CTA-per-state light sampler (15 <= n <= 20); heavier states go to

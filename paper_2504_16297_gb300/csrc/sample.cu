@@ -461,26 +461,36 @@ __global__ void k_search_global(SampleArgs a, const fx* __restrict__ cdf, const 
     }
 }
 
-// Distinct outcomes among the shots of each set (the unique-shot statistic of Sec. 4): one CTA per
-// set marks a bitmap of the 2^n outcomes in shared memory and counts its set bits. Shots that are
-// not outcomes (the null-branch sentinel) are skipped.
-__global__ void k_unique(const uint32_t* __restrict__ bits, const uint64_t* __restrict__ ranges, int n,
-                         unsigned long long* out) {
+// Distinct outcomes among the shots of each set (the unique-shot statistic of Sec. 4). Each CTA
+// takes one piece of one set's shots (sets are cut into pieces so heavy sets spread over the GPU),
+// marks a bitmap of the 2^n outcomes in shared memory, and ORs its nonzero words into the set's
+// bitmap in global memory; a second kernel counts each set's bits. Shots that are not outcomes
+// (the null-branch sentinel) are skipped.
+__global__ void k_unique_mark(const uint32_t* __restrict__ bits, const uint64_t* __restrict__ pieces, int n,
+                              uint32_t* gbm) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long red[32];
     uint32_t* bm = reinterpret_cast<uint32_t*>(smem);
     const uint32_t words = (1u << n) >= 32 ? (1u << n) / 32 : 1u;
     for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) bm[i] = 0u;
     __syncthreads();
-    const uint64_t b0 = ranges[2 * blockIdx.x], b1 = ranges[2 * blockIdx.x + 1];
+    const uint64_t set = pieces[3 * blockIdx.x], b0 = pieces[3 * blockIdx.x + 1], b1 = pieces[3 * blockIdx.x + 2];
     const uint64_t lim = 1ull << n;
     for (uint64_t k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
         const uint32_t x = bits[k];
         if ((uint64_t)x < lim) atomicOr(&bm[x >> 5], 1u << (x & 31));
     }
     __syncthreads();
+    uint32_t* g = gbm + set * words;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x)
+        if (bm[i]) atomicOr(&g[i], bm[i]);
+}
+
+__global__ void k_unique_count(const uint32_t* __restrict__ gbm, int n, unsigned long long* out) {
+    __shared__ unsigned long long red[32];
+    const uint32_t words = (1u << n) >= 32 ? (1u << n) / 32 : 1u;
+    const uint32_t* g = gbm + (size_t)blockIdx.x * words;
     unsigned long long c = 0;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) c += (unsigned long long)__popc(bm[i]);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) c += (unsigned long long)__popc(g[i]);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
@@ -640,18 +650,26 @@ void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, u
 
 int unique_max_qubits() { return 20; }
 
-void launch_unique(const uint32_t* bits, const uint64_t* d_ranges, uint32_t count, int n, unsigned long long* out,
-                   cudaStream_t s) {
+size_t unique_bitmap_bytes(int n) { return 4 * std::max<size_t>(1, ((size_t)1 << n) / 32); }
+
+void launch_unique(const uint32_t* bits, const uint64_t* d_pieces, uint32_t n_pieces, uint32_t count, int n,
+                   uint32_t* d_bitmaps, unsigned long long* out, cudaStream_t s) {
     if (count == 0) return;
-    const size_t smem = std::max<size_t>(4, ((size_t)1 << n) / 8);
+    const size_t smem = unique_bitmap_bytes(n);
     static bool configured = false;
     if (!configured) {
-        PTSBE_CUDA(cudaFuncSetAttribute(k_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(((size_t)1 << 20) / 8)));
+        PTSBE_CUDA(cudaFuncSetAttribute(k_unique_mark, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)unique_bitmap_bytes(20)));
         configured = true;
+    }
+    for (uint32_t b = 0; b < n_pieces; b += 65535u) {
+        const uint32_t cnt = std::min<uint32_t>(65535u, n_pieces - b);
+        k_unique_mark<<<cnt, 1024, smem, s>>>(bits, d_pieces + 3 * (size_t)b, n, d_bitmaps);
+        PTSBE_CUDA(cudaGetLastError());
+        count_launch();
     }
     for (uint32_t b = 0; b < count; b += 65535u) {
         const uint32_t cnt = std::min<uint32_t>(65535u, count - b);
-        k_unique<<<cnt, 1024, smem, s>>>(bits, d_ranges + 2 * (size_t)b, n, out + b);
+        k_unique_count<<<cnt, 256, 0, s>>>(d_bitmaps + (size_t)b * (unique_bitmap_bytes(n) / 4), n, out + b);
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }
