@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
     ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "frame", "sweep", "registers"])
+    ap.add_argument("--separate", action="store_true",
+                    help="time ptsbe_evolve_batch + ptsbe_sample_shots instead of the one-call ptsbe_evolve_sample")
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the adjoint-backward measurement (16-qubit ansatz, 4,096 samples)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -375,8 +377,11 @@ def main():
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M, export=False)
         assert info.count == K and info.total_shots == M
         stream.wait_event(done[b])                        # buffer b is free again
-        P.evolve(info, 0, K, states, weights[b], status[b], prefix_reuse=True)
-        P.sample(info, 0, K, states, status[b], seed, bits[b])
+        if args.separate:
+            P.evolve(info, 0, K, states, weights[b], status[b], prefix_reuse=True)
+            P.sample(info, 0, K, states, status[b], seed, bits[b])
+        else:
+            P.evolve_sample(info, 0, K, states, weights[b], status[b], seed, bits[b], prefix_reuse=True)
         if e2e:
             copy_stream.wait_stream(stream)
             with torch.cuda.stream(copy_stream):
@@ -467,8 +472,7 @@ def main():
     if rank == 0:
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
-        P.evolve(info, 0, K, states, weights[0], status[0], prefix_reuse=True)
-        P.sample(info, 0, K, states, status[0], seed, bits[0])
+        P.evolve_sample(info, 0, K, states, weights[0], status[0], seed, bits[0], prefix_reuse=True)
         top = 4
         u = torch.zeros(top, dtype=torch.int64, device=dev)
         P.unique_shots(info, 0, top, bits[0], u)
@@ -511,7 +515,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "qubits": n, "kraus_sets": K, "shots": M, "pts": "topk",
-                       "prefix_reuse": True, "amplitudes": "complex64, FP64 norms, CDF in 2^-62 fixed point (exact integer sums)",
+                       "prefix_reuse": True, "call": "evolve_batch + sample_shots" if args.separate else "evolve_sample", "amplitudes": "complex64, FP64 norms, CDF in 2^-62 fixed point (exact integer sums)",
                        "l2": "inputs larger than L2 (10.5 GB of states per step)",
                        "parallelism": f"{world} independent replicas (weak scaling)", "tuning": tuning},
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,

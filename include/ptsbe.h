@@ -78,7 +78,8 @@ PTSBE_API const char* ptsbe_last_error(const ptsbe_ctx* ctx);
 
 /* Blocks until all work enqueued by the context has finished; returns PTSBE_ERR_CUDA (with the
  * CUDA error text) if an asynchronous kernel failed, PTSBE_ERR_TIMEOUT if a bounded device wait
- * gave up. */
+ * gave up, PTSBE_ERR_UNSUPPORTED if a fused sampling launch flagged the context (see
+ * ptsbe_evolve_sample; the flag is cleared). */
 PTSBE_API int ptsbe_synchronize(ptsbe_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------------- */
@@ -276,6 +277,22 @@ PTSBE_API int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
 PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                        const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity);
 
+/* Batched execution in one call (Sec. 3: each unique state prepared once, then all m_alpha of its
+ * shots drawn at once): the outputs of ptsbe_evolve_batch(ctx, set_id, first, count, d_states,
+ * d_weights, d_status, flags) followed by ptsbe_sample_shots(ctx, set_id, first, count, d_states,
+ * d_status, seed, d_bits, d_bits_capacity), bit for bit (states, weights, status and shots).
+ * When the last tile stage prepares each state from its support in one CTA (a sparse final
+ * stage), that CTA also draws the shots of states with at most PTSBE_OPT_LIGHT_SHOTS shots from
+ * the support it holds on chip, so those states are never read back; the CDF of a state over its
+ * support in increasing index order has the same prefix values as over all 2^n entries (the
+ * others are exact zeros). The remaining states go to the sampler kernels. Arguments, layouts and
+ * ownership as for the two calls. Asynchronous. Errors: those of the two calls; a kernel that
+ * finds a support not of the form the plan guarantees flags the context, and the next
+ * ptsbe_synchronize returns PTSBE_ERR_UNSUPPORTED (the affected shots hold 0xFFFFFFFF). */
+PTSBE_API int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
+                                  double* d_weights, uint8_t* d_status, uint32_t flags, uint64_t seed,
+                                  uint32_t* d_bits, uint64_t d_bits_capacity);
+
 /* Unique-shot statistic (Sec. 4: the fraction of distinct outcomes among a set's shots): for sets
  * [first, first + count) of set_id, d_unique[a] = number of distinct values among the shots of set
  * first + a in d_bits (laid out as ptsbe_sample_shots writes them; the null-branch sentinel is not
@@ -377,15 +394,19 @@ enum {
     /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
      * prefixes (one chunk re-read per shot); heavier ones by a thread-block cluster holding the
      * whole CDF. Both give the same shots; only the speed differs. Default 65,536 (measured).  */
-    PTSBE_OPT_LIGHT_SHOTS = 1
+    PTSBE_OPT_LIGHT_SHOTS = 1,
+    /* Kraus sets whose frame programs one warp of the program prepass builds (one thread per set):
+     * 4, 8 or 16 (0 = default, 8: measured). The builders branch on each set's entries, so fewer
+     * sets per warp diverge less and leave more warps per scheduler. Same programs; speed only. */
+    PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
 PTSBE_API int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value);
 
 /* Result of ptsbe_autotune: the options it chose and the measured time of every candidate
- * (milliseconds per ptsbe_evolve_batch / ptsbe_sample_shots call, mean of `reps` calls; 0 for a
- * candidate that does not apply). */
+ * (milliseconds per ptsbe_evolve_batch call for the kernels, per ptsbe_evolve_sample call for the
+ * shot limits; mean of `reps` calls; 0 for a candidate that does not apply). */
 typedef struct {
     int32_t evolve_kernel;            /* chosen PTSBE_OPT_EVOLVE_KERNEL (1 sweeps, 2 registers, 3 frame) */
     uint64_t light_shots;             /* chosen PTSBE_OPT_LIGHT_SHOTS                                */
@@ -395,7 +416,7 @@ typedef struct {
 } ptsbe_tuning;
 
 /* Autotuner: runs ptsbe_evolve_batch (every evolve kernel, flags as given) and then
- * ptsbe_sample_shots (each light-shot limit) on sets [first, first + count) of set_id, `reps`
+ * ptsbe_evolve_sample (each light-shot limit) on sets [first, first + count) of set_id, `reps`
  * timed calls each after one warm-up, times them with CUDA events on the context stream, and sets
  * the context to the fastest evolve kernel and shot limit. The kernels give the same results up
  * to rounding (the shot limit changes no shot at all), so tuning changes speed only. Buffers as

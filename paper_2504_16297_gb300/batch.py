@@ -2,11 +2,11 @@
 budget, through several libptsbe contexts (one CUDA stream each) so that small circuits share the
 GPU while the host runs PTS for the next ones.
 
-Per circuit: register, pre-trajectory sampling (host), ptsbe_evolve_batch and ptsbe_sample_shots
-on the circuit's context (asynchronous), release. Circuits go to the contexts round-robin; each
-context reuses one state, weight, status and shot buffer, ordered by its own stream. The evolve
-kernel for each qubit count is chosen once by the library's autotuner on the first circuit of that
-size. Marshalling only: every step runs in libptsbe.
+Per circuit: register, pre-trajectory sampling (host), ptsbe_evolve_sample (state preparation
+and shots in one call) on the circuit's context (asynchronous), release. Circuits go to the
+contexts round-robin; each context reuses one state, weight, status and shot buffer, ordered by
+its own stream. The evolve kernel for each qubit count is chosen once by the library's autotuner
+on the first circuit of that size. Marshalling only: every step runs in libptsbe.
 """
 from __future__ import annotations
 
@@ -77,8 +77,7 @@ class UnevenBatch:
             if info.count > self.max_sets:
                 raise ValueError("more unique sets than the batch buffers hold")
             st, w, s, b = self._views(j, info.count, n, info.total_shots)
-            P.evolve(info, 0, info.count, st, w, s, prefix_reuse=True)
-            P.sample(info, 0, info.count, st, s, seed + i, b)
+            P.evolve_sample(info, 0, info.count, st, w, s, seed + i, b, prefix_reuse=True)
             if keep is not None and i in keep:
                 with torch.cuda.stream(self.streams[j]):
                     kept[i] = (b[: info.total_shots].cpu(), info)

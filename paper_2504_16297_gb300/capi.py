@@ -19,6 +19,7 @@ PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVE
 PTSBE_EVOLVE_PREFIX_REUSE = 1
 PTSBE_OPT_EVOLVE_KERNEL = 0
 PTSBE_OPT_LIGHT_SHOTS = 1
+PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
  PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD) = range(7)
 
@@ -90,6 +91,8 @@ _PROTOS = {
                                      C.c_void_p, C.c_uint32]),
     "ptsbe_sample_shots": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
                                      C.c_uint64, C.c_void_p, C.c_uint64]),
+    "ptsbe_evolve_sample": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64]),
     "ptsbe_sample_shots_noalloc": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p,
                                              C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64]),
     "ptsbe_backward": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -200,6 +203,11 @@ def ptsbe_release_set(ctx, set_id):
 
 def ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags):
     check(ctx, load().ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags))
+
+
+def ptsbe_evolve_sample(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed, d_bits, capacity):
+    check(ctx, load().ptsbe_evolve_sample(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed,
+                                          d_bits, capacity))
 
 
 def ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bits, capacity):

@@ -54,12 +54,13 @@ struct ptsbe_ctx {
     std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
     uint32_t next_circuit = 1, next_set = 1;
-    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong;
+    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault;
     std::vector<unsigned char> host_blob;
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
     int evolve_kernel = 0;
     uint64_t light_shots = kLightShotLimit;   // states with at most this many shots: one-CTA sampler
+    int prog_sets_per_warp = 8;                // frame program prepass: Kraus sets per warp (measured)
     int n_sm = 0;                      // streaming multiprocessors of the device
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
@@ -178,6 +179,14 @@ struct ptsbe_ctx {
         return p;
     }
     void free_buf(DevBuf& b) { if (b.p) cudaFree(b.p); b.p = nullptr; b.cap = 0; }
+    // Device word that kernels set when they could not do their work (zero when created).
+    uint32_t* fault_word() {
+        if (!fault.p) {
+            void* p = ws(fault, sizeof(uint32_t));
+            PTSBE_CUDA(cudaMemsetAsync(p, 0, sizeof(uint32_t), stream));
+        }
+        return (uint32_t*)fault.p;
+    }
 
     Circuit& circuit(uint32_t id) {
         auto it = circuits.find(id);
@@ -297,6 +306,287 @@ void check_same_structure(const Circuit& a, const Circuit& b) {
 
 }  // namespace
 
+namespace {
+
+// Shots the last evolve launch draws from the support it holds on chip.
+struct FusedShots {
+    uint64_t seed;
+    uint32_t* bits;
+};
+
+// Prepares states [first, first + count) of set s (the work of ptsbe_evolve_batch). With fused,
+// the small sparse final stage also draws the shots of the states it can (drawn[a] = 1).
+void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
+                  double* d_weights, uint8_t* d_status, uint32_t flags, const FusedShots* fused,
+                  std::vector<uint8_t>* drawn) {
+    ctx->use_device();
+    ensure_set_on_device(ctx, s);
+    const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
+    if (frame && !c.frame_planned) {
+        c.plan_frame = make_frame_plan(c, kTileMax);
+        upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
+        c.frame_planned = true;
+    }
+    if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
+    const Plan& P = frame ? c.plan_frame : c.plan;
+    const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
+    const uint32_t S = (uint32_t)c.site_op.size();
+    const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
+
+    // --- node tables ---
+    // With prefix reuse a set whose entries extend those of an earlier set of the range (its
+    // parent: longest such prefix) starts at the stage holding its first extra site, from the
+    // parent's input of that stage; a start in stage 0 is a start from |0...0>.
+    const uint32_t J = (uint32_t)P.stages.size();
+    std::vector<uint32_t> ebeg(count), eend(count), sstage(count), src(count);
+    std::vector<uint8_t> fresh(count);
+    std::vector<double> wmix(count), qa(count);
+    std::unordered_map<std::string, uint32_t> index;
+    // A set can only start later than stage 0 in a plan with more than one stage.
+    const bool trie = reuse && J > 1;
+    // prod over unitary-mixture sites of q_{s,0}; a set's product is this times the ratios at its
+    // entries (the full product when some q_{s,0} is 0)
+    double q0mix = 1.0;
+    for (uint32_t site = 0; site < S; ++site) {
+        const HostChannel& ch = c.ch[c.site_ch[site]];
+        if (ch.mixture) q0mix *= ch.q[0];
+    }
+    auto key_of = [&](uint32_t alpha, uint32_t len) {
+        std::string k;
+        k.resize(len * 5);
+        for (uint32_t i = 0; i < len; ++i) {
+            std::memcpy(&k[5 * i], &s.site[s.off[alpha] + i], 4);
+            k[5 * i + 4] = (char)s.k[s.off[alpha] + i];
+        }
+        return k;
+    };
+    for (uint32_t a = 0; a < count; ++a) {
+        const uint32_t alpha = first + a;
+        const uint32_t len = s.off[alpha + 1] - s.off[alpha];
+        ebeg[a] = s.off[alpha]; eend[a] = s.off[alpha + 1];
+        qa[a] = s.q[alpha];
+        uint32_t parent = UINT32_MAX;
+        if (trie) {
+            for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
+                auto it = index.find(key_of(alpha, (uint32_t)p));
+                if (it != index.end()) { parent = it->second; break; }
+            }
+            index.emplace(key_of(alpha, len), a);
+        }
+        sstage[a] = 0; src[a] = a; fresh[a] = 1;
+        if (parent != UINT32_MAX) {
+            const uint32_t plen = s.off[first + parent + 1] - s.off[first + parent];
+            const uint32_t j = (uint32_t)P.op_stage[c.site_op[s.site[s.off[alpha] + plen]]];
+            // The parent starts no later than the child (its extra sites come first). If it
+            // starts in the same stage, both read the same input: the parent's source.
+            if (j > 0) { sstage[a] = j; src[a] = sstage[parent] == j ? src[parent] : parent; fresh[a] = 0; }
+        }
+        // prod over unitary-mixture sites of q_{s,k_s}
+        double w = q0mix;
+        if (q0mix > 0) {
+            for (uint32_t e = s.off[alpha]; e < s.off[alpha + 1]; ++e) {
+                const HostChannel& ch = c.ch[c.site_ch[s.site[e]]];
+                if (ch.mixture) w *= ch.q[s.k[e]] / ch.q[0];
+            }
+        } else {
+            w = 1.0;
+            uint32_t e = s.off[alpha];
+            for (uint32_t site = 0; site < S; ++site) {
+                uint32_t k = 0;
+                if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
+                const HostChannel& ch = c.ch[c.site_ch[site]];
+                if (ch.mixture) w *= ch.q[k];
+            }
+        }
+        wmix[a] = w;
+    }
+    // one launch per stage: every set whose start stage is at or before it
+    std::vector<uint32_t> lists;
+    std::vector<std::pair<size_t, uint32_t>> launches;  // (offset, count) per stage
+    for (uint32_t j = 0; j < J; ++j) {
+        const size_t off = lists.size();
+        for (uint32_t a = 0; a < count; ++a)
+            if (sstage[a] <= j) lists.push_back(a);
+        launches.push_back({off, (uint32_t)(lists.size() - off)});
+    }
+    Blob blob(ctx->host_blob);
+    const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_sstage = blob.add(sstage);
+    const size_t o_src = blob.add(src), o_fresh = blob.add(fresh);
+    const size_t o_wmix = blob.add(wmix), o_q = blob.add(qa), o_lists = blob.add(lists);
+    // Shots drawn by the last launch: the small sparse final stage holds each state's support
+    // on chip and draws the shots of states with at most light_shots of them (the others are
+    // left to the sampler kernels).
+    int sparse_last = -1, small_last = 0;
+    if (frame)
+        for (uint32_t j = 0; j < J; ++j)
+            if (P.fstages[j].sparse_final) { sparse_last = (int)j; small_last = (int)P.fstages[j].sbits; }
+    const bool fuse = fused && sparse_last == (int)J - 1 && small_last > 0;
+    std::vector<uint32_t> nshots;
+    std::vector<uint64_t> nout;
+    size_t o_nshots = 0, o_nout = 0;
+    uint64_t fused_shots = 0;
+    if (drawn) drawn->assign(count, 0);
+    if (fuse) {
+        nshots.assign(count, 0);
+        nout.assign(count, 0);
+        const uint64_t base = s.shot_off[first];
+        for (uint32_t a = 0; a < count; ++a) {
+            const uint64_t m = s.shots[first + a];
+            nout[a] = s.shot_off[first + a] - base;
+            if (m > 0 && m <= ctx->light_shots && m <= UINT32_MAX) {
+                nshots[a] = (uint32_t)m;
+                fused_shots += m;
+                if (drawn) (*drawn)[a] = 1;
+            }
+        }
+        o_nshots = blob.add(nshots);
+        o_nout = blob.add(nout);
+    }
+    unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
+    ctx->h2d(dblob, ctx->host_blob.data(), ctx->host_blob.size());
+
+    EvolveArgs A{};
+    A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
+    A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi; A.fstages = D.fstages;
+    A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
+    A.ent_site = s.d_site; A.ent_k = s.d_k;
+    A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
+    A.node_sstage = (const uint32_t*)(dblob + o_sstage); A.node_src = (const uint32_t*)(dblob + o_src);
+    A.node_fresh = (const uint8_t*)(dblob + o_fresh);
+    A.wmix = (const double*)(dblob + o_wmix); A.qalpha = (const double*)(dblob + o_q);
+    A.weights = d_weights; A.status = d_status;
+    if (fuse && fused_shots) {
+        A.shot_bits = fused->bits;
+        A.shot_seed = fused->seed;
+        A.shot_alpha0 = first;
+        A.node_shots = (const uint32_t*)(dblob + o_nshots);
+        A.node_shot_out = (const uint64_t*)(dblob + o_nout);
+        A.fault = ctx->fault_word();
+    }
+    const double sbytes = 8.0 * (double)(1ull << c.n);
+    // stage j writes out(j); out(J-1) is the caller's buffer. The per-operator kernels without
+    // reuse read and write the caller's buffer in place (a tile is read whole before it is
+    // written); frame stores move amplitudes between tiles, so they always alternate.
+    float2* const user = (float2*)d_states;
+    float2* const other = (reuse || frame) && J > 1 ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * (size_t)sbytes) : user;
+    auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
+    const int ob = (int)c.n - P.tb;
+    float* d_scale = nullptr;
+    if (ob > 0) {
+        A.part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
+        d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
+    }
+    if (frame) {
+        uint32_t widest = 0;
+        for (const auto& L : launches) widest = std::max(widest, L.second);
+        A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());
+    }
+    const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
+    // When the last frame stage only reorders (no ops), the norm is known after the stage
+    // before it: that stage's stores leave tile norms, a reduce turns them into scales, and
+    // the last stage writes the normalised state (no separate renormalisation pass).
+    const bool early_norm = frame && ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end &&
+                            launches[J - 2].second == count;
+    A.sparse_final_stage = -1;
+    A.small_bits = 0;
+    if (frame)
+        for (uint32_t j = 0; j < J; ++j)
+            if (P.fstages[j].sparse_final) { A.sparse_final_stage = (int)j; A.small_bits = (int)P.fstages[j].sbits; }
+    for (uint32_t j = 0; j < J; ++j) {
+        const auto& L = launches[j];
+        if (L.second == 0) continue;
+        A.states = out_buf(j);
+        A.states_in = j > 0 ? out_buf(j - 1) : out_buf(j);
+        A.store_norm = early_norm && j + 2 == J;
+        A.scale_in = early_norm && j + 1 == J ? d_scale : nullptr;
+        // algorithmic bytes: read (unless started from |0>) and write of each set's state
+        double bytes = 0;
+        for (size_t t = L.first; t < L.first + L.second; ++t)
+            bytes += (fresh[lists[t]] && j == 0) ? sbytes : 2 * sbytes;
+        if (A.shot_bits && j + 1 == J) bytes += 4.0 * (double)fused_shots;
+        if (frame)
+            ctx->timed(PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
+                launch_frame_program(A, (int)j, d_lists + L.first, L.second, ctx->stream, ctx->prog_sets_per_warp);
+            });
+        ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
+            launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
+        });
+        if (A.store_norm)
+            ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 0.0, [&] { launch_evolve_reduce(A, count, d_scale, ctx->stream); });
+    }
+    A.states = user;
+    A.store_norm = 0;
+    A.scale_in = nullptr;
+    if (ob > 0 && !early_norm && A.sparse_final_stage < 0)
+        ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
+}
+
+// Draws the shots of states [first, first + count) (the work of ptsbe_sample_shots), except those
+// of states marked in drawn.
+void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, const void* d_states,
+                  const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, const std::vector<uint8_t>* drawn) {
+    ctx->use_device();
+    SampleArgs A{};
+    A.n = (int)c.n;
+    A.states = (const float2*)d_states;
+    A.status = d_status;
+    A.seed = seed;
+    A.bits = d_bits;
+    const int n = (int)c.n;
+    const bool light_ok = n > 14 && n <= sample_light_max_qubits();
+    std::vector<SampleItem> light, items;
+    // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
+    // state's CDF. About four items per resident cluster over the whole shot budget.
+    const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
+    const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
+    const uint64_t base = s.shot_off[first];
+    uint64_t total = 0;
+    for (uint32_t a = 0; a < count; ++a)
+        if (!(drawn && (*drawn)[a])) total += s.shots[first + a];
+    const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+    for (uint32_t a = 0; a < count; ++a) {
+        const uint32_t alpha = first + a;
+        const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+        if (m == 0 || (drawn && (*drawn)[a])) continue;
+        if (light_ok && m <= ctx->light_shots) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
+        if (n <= sample_cluster_max_qubits())
+            for (uint64_t j0 = 0; j0 < m; j0 += chunk)
+                items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
+    }
+    const size_t nl = light.size(), nh = items.size();
+    if (nl + nh) {
+        light.insert(light.end(), items.begin(), items.end());
+        SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
+        ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
+        if (nl) {
+            // algorithmic: each state read once and 4 bytes per shot written (the per-shot chunk
+            // re-reads are the light design's extra traffic, not counted)
+            uint64_t light_shots = 0;
+            for (size_t i = 0; i < nl; ++i) light_shots += light[i].j1 - light[i].j0;
+            const double bytes = 8.0 * (double)(1ull << n) * (double)nl + 4.0 * (double)light_shots;
+            ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
+        }
+        if (nh) {
+            uint64_t heavy_shots = 0;
+            for (size_t i = nl; i < light.size(); ++i) heavy_shots += light[i].j1 - light[i].j0;
+            const double bytes = 8.0 * (double)(1ull << n) * (double)nh + 4.0 * (double)heavy_shots;
+            ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items + nl, (uint32_t)nh, ctx->stream); });
+        }
+    }
+    if (n > sample_cluster_max_qubits()) {
+        A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
+        for (uint32_t a = 0; a < count; ++a) {
+            const uint32_t alpha = first + a;
+            const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+            if (m == 0 || (light_ok && m <= ctx->light_shots) || (drawn && (*drawn)[a])) continue;
+            const double sb = 8.0 * (double)(1ull << n);
+            ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
+        }
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
@@ -352,7 +642,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
-        ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong);
+        ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault);
         ctx->free_timers();
     }
     delete ctx;
@@ -373,6 +663,14 @@ int ptsbe_synchronize(ptsbe_ctx* ctx) {
         ctx->use_device();
         PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
         PTSBE_CUDA(cudaGetLastError());
+        if (ctx->fault.p) {
+            uint32_t f = 0;
+            PTSBE_CUDA(cudaMemcpy(&f, ctx->fault.p, sizeof(f), cudaMemcpyDeviceToHost));
+            if (f) {
+                PTSBE_CUDA(cudaMemset(ctx->fault.p, 0, sizeof(f)));
+                fail(PTSBE_ERR_UNSUPPORTED, "a fused sampling launch found a support it cannot order (shots left at 0xFFFFFFFF)");
+            }
+        }
     });
 }
 
@@ -476,168 +774,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         if (!d_states) fail(PTSBE_ERR_INVALID, "d_states is NULL");
         if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
         if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
-        ctx->use_device();
-        ensure_set_on_device(ctx, s);
-        const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
-        if (frame && !c.frame_planned) {
-            c.plan_frame = make_frame_plan(c, kTileMax);
-            upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
-            c.frame_planned = true;
-        }
-        if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
-        const Plan& P = frame ? c.plan_frame : c.plan;
-        const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
-        const uint32_t S = (uint32_t)c.site_op.size();
-        const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
-
-        // --- node tables ---
-        // With prefix reuse a set whose entries extend those of an earlier set of the range (its
-        // parent: longest such prefix) starts at the stage holding its first extra site, from the
-        // parent's input of that stage; a start in stage 0 is a start from |0...0>.
-        const uint32_t J = (uint32_t)P.stages.size();
-        std::vector<uint32_t> ebeg(count), eend(count), sstage(count), src(count);
-        std::vector<uint8_t> fresh(count);
-        std::vector<double> wmix(count), qa(count);
-        std::unordered_map<std::string, uint32_t> index;
-        // A set can only start later than stage 0 in a plan with more than one stage.
-        const bool trie = reuse && J > 1;
-        // prod over unitary-mixture sites of q_{s,0}; a set's product is this times the ratios at its
-        // entries (the full product when some q_{s,0} is 0)
-        double q0mix = 1.0;
-        for (uint32_t site = 0; site < S; ++site) {
-            const HostChannel& ch = c.ch[c.site_ch[site]];
-            if (ch.mixture) q0mix *= ch.q[0];
-        }
-        auto key_of = [&](uint32_t alpha, uint32_t len) {
-            std::string k;
-            k.resize(len * 5);
-            for (uint32_t i = 0; i < len; ++i) {
-                std::memcpy(&k[5 * i], &s.site[s.off[alpha] + i], 4);
-                k[5 * i + 4] = (char)s.k[s.off[alpha] + i];
-            }
-            return k;
-        };
-        for (uint32_t a = 0; a < count; ++a) {
-            const uint32_t alpha = first + a;
-            const uint32_t len = s.off[alpha + 1] - s.off[alpha];
-            ebeg[a] = s.off[alpha]; eend[a] = s.off[alpha + 1];
-            qa[a] = s.q[alpha];
-            uint32_t parent = UINT32_MAX;
-            if (trie) {
-                for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
-                    auto it = index.find(key_of(alpha, (uint32_t)p));
-                    if (it != index.end()) { parent = it->second; break; }
-                }
-                index.emplace(key_of(alpha, len), a);
-            }
-            sstage[a] = 0; src[a] = a; fresh[a] = 1;
-            if (parent != UINT32_MAX) {
-                const uint32_t plen = s.off[first + parent + 1] - s.off[first + parent];
-                const uint32_t j = (uint32_t)P.op_stage[c.site_op[s.site[s.off[alpha] + plen]]];
-                // The parent starts no later than the child (its extra sites come first). If it
-                // starts in the same stage, both read the same input: the parent's source.
-                if (j > 0) { sstage[a] = j; src[a] = sstage[parent] == j ? src[parent] : parent; fresh[a] = 0; }
-            }
-            // prod over unitary-mixture sites of q_{s,k_s}
-            double w = q0mix;
-            if (q0mix > 0) {
-                for (uint32_t e = s.off[alpha]; e < s.off[alpha + 1]; ++e) {
-                    const HostChannel& ch = c.ch[c.site_ch[s.site[e]]];
-                    if (ch.mixture) w *= ch.q[s.k[e]] / ch.q[0];
-                }
-            } else {
-                w = 1.0;
-                uint32_t e = s.off[alpha];
-                for (uint32_t site = 0; site < S; ++site) {
-                    uint32_t k = 0;
-                    if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
-                    const HostChannel& ch = c.ch[c.site_ch[site]];
-                    if (ch.mixture) w *= ch.q[k];
-                }
-            }
-            wmix[a] = w;
-        }
-        // one launch per stage: every set whose start stage is at or before it
-        std::vector<uint32_t> lists;
-        std::vector<std::pair<size_t, uint32_t>> launches;  // (offset, count) per stage
-        for (uint32_t j = 0; j < J; ++j) {
-            const size_t off = lists.size();
-            for (uint32_t a = 0; a < count; ++a)
-                if (sstage[a] <= j) lists.push_back(a);
-            launches.push_back({off, (uint32_t)(lists.size() - off)});
-        }
-        Blob blob(ctx->host_blob);
-        const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_sstage = blob.add(sstage);
-        const size_t o_src = blob.add(src), o_fresh = blob.add(fresh);
-        const size_t o_wmix = blob.add(wmix), o_q = blob.add(qa), o_lists = blob.add(lists);
-        unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
-        ctx->h2d(dblob, ctx->host_blob.data(), ctx->host_blob.size());
-
-        EvolveArgs A{};
-        A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
-        A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi; A.fstages = D.fstages;
-        A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
-        A.ent_site = s.d_site; A.ent_k = s.d_k;
-        A.node_ebeg = (const uint32_t*)(dblob + o_ebeg); A.node_eend = (const uint32_t*)(dblob + o_eend);
-        A.node_sstage = (const uint32_t*)(dblob + o_sstage); A.node_src = (const uint32_t*)(dblob + o_src);
-        A.node_fresh = (const uint8_t*)(dblob + o_fresh);
-        A.wmix = (const double*)(dblob + o_wmix); A.qalpha = (const double*)(dblob + o_q);
-        A.weights = d_weights; A.status = d_status;
-        const double sbytes = 8.0 * (double)(1ull << c.n);
-        // stage j writes out(j); out(J-1) is the caller's buffer. The per-operator kernels without
-        // reuse read and write the caller's buffer in place (a tile is read whole before it is
-        // written); frame stores move amplitudes between tiles, so they always alternate.
-        float2* const user = (float2*)d_states;
-        float2* const other = (reuse || frame) && J > 1 ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * (size_t)sbytes) : user;
-        auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
-        const int ob = (int)c.n - P.tb;
-        float* d_scale = nullptr;
-        if (ob > 0) {
-            A.part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
-            d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
-        }
-        if (frame) {
-            uint32_t widest = 0;
-            for (const auto& L : launches) widest = std::max(widest, L.second);
-            A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());
-        }
-        const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
-        // When the last frame stage only reorders (no ops), the norm is known after the stage
-        // before it: that stage's stores leave tile norms, a reduce turns them into scales, and
-        // the last stage writes the normalised state (no separate renormalisation pass).
-        const bool early_norm = frame && ob > 0 && J >= 2 && P.stages[J - 1].op_begin == P.stages[J - 1].op_end &&
-                                launches[J - 2].second == count;
-        A.sparse_final_stage = -1;
-        A.small_bits = 0;
-        if (frame)
-            for (uint32_t j = 0; j < J; ++j)
-                if (P.fstages[j].sparse_final) { A.sparse_final_stage = (int)j; A.small_bits = (int)P.fstages[j].sbits; }
-        for (uint32_t j = 0; j < J; ++j) {
-            const auto& L = launches[j];
-            if (L.second == 0) continue;
-            A.states = out_buf(j);
-            A.states_in = j > 0 ? out_buf(j - 1) : out_buf(j);
-            A.store_norm = early_norm && j + 2 == J;
-            A.scale_in = early_norm && j + 1 == J ? d_scale : nullptr;
-            // algorithmic bytes: read (unless started from |0>) and write of each set's state
-            double bytes = 0;
-            for (size_t t = L.first; t < L.first + L.second; ++t)
-                bytes += (fresh[lists[t]] && j == 0) ? sbytes : 2 * sbytes;
-            if (frame)
-                ctx->timed(PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
-                    launch_frame_program(A, (int)j, d_lists + L.first, L.second, ctx->stream);
-                });
-            ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
-                launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
-            });
-            if (A.store_norm)
-                ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 0.0, [&] { launch_evolve_reduce(A, count, d_scale, ctx->stream); });
-        }
-        A.states = user;
-        A.store_norm = 0;
-        A.scale_in = nullptr;
-        if (ob > 0 && !early_norm && A.sparse_final_stage < 0)
-            ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
+        evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, nullptr, nullptr);
     });
 }
 
@@ -658,59 +795,31 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
                                                                           " shots, the range needs " + std::to_string(total));
         if (c.n > 32) fail(PTSBE_ERR_UNSUPPORTED, "outcomes are 32-bit");
         ctx->use_device();
-        SampleArgs A{};
-        A.n = (int)c.n;
-        A.states = (const float2*)d_states;
-        A.status = d_status;
-        A.seed = seed;
-        A.bits = d_bits;
-        const int n = (int)c.n;
-        const bool light_ok = n > 14 && n <= sample_light_max_qubits();
-        std::vector<SampleItem> light, items;
-        // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
-        // state's CDF. About four items per resident cluster over the whole shot budget.
-        const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
-        const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
-        const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
-        for (uint32_t a = 0; a < count; ++a) {
-            const uint32_t alpha = first + a;
-            const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
-            if (m == 0) continue;
-            if (light_ok && m <= ctx->light_shots) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
-            if (n <= sample_cluster_max_qubits())
-                for (uint64_t j0 = 0; j0 < m; j0 += chunk)
-                    items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
-        }
-        const size_t nl = light.size(), nh = items.size();
-        if (nl + nh) {
-            light.insert(light.end(), items.begin(), items.end());
-            SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
-            ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
-            if (nl) {
-                // algorithmic: each state read once and 4 bytes per shot written (the per-shot chunk
-                // re-reads are the light design's extra traffic, not counted)
-                uint64_t light_shots = 0;
-                for (size_t i = 0; i < nl; ++i) light_shots += light[i].j1 - light[i].j0;
-                const double bytes = 8.0 * (double)(1ull << n) * (double)nl + 4.0 * (double)light_shots;
-                ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
-            }
-            if (nh) {
-                uint64_t heavy_shots = 0;
-                for (size_t i = nl; i < light.size(); ++i) heavy_shots += light[i].j1 - light[i].j0;
-                const double bytes = 8.0 * (double)(1ull << n) * (double)nh + 4.0 * (double)heavy_shots;
-                ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items + nl, (uint32_t)nh, ctx->stream); });
-            }
-        }
-        if (n > sample_cluster_max_qubits()) {
-            A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
-            for (uint32_t a = 0; a < count; ++a) {
-                const uint32_t alpha = first + a;
-                const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
-                if (m == 0 || (light_ok && m <= ctx->light_shots)) continue;
-                const double sb = 8.0 * (double)(1ull << n);
-                ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
-            }
-        }
+        sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, nullptr);
+    });
+}
+
+int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
+                        double* d_weights, uint8_t* d_status, uint32_t flags, uint64_t seed, uint32_t* d_bits,
+                        uint64_t d_bits_capacity) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        KSet& s = ctx->set(set_id);
+        Circuit& c = ctx->circuit(s.circuit);
+        if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
+        if (count == 0) return;
+        if (!d_states) fail(PTSBE_ERR_INVALID, "d_states is NULL");
+        if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
+        if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
+        const uint64_t total = s.shot_off[first + count] - s.shot_off[first];
+        if (total && !d_bits) fail(PTSBE_ERR_INVALID, "null device pointer");
+        if (d_bits_capacity < total) fail(PTSBE_ERR_BUFFER_TOO_SMALL, "d_bits holds " + std::to_string(d_bits_capacity) +
+                                                                          " shots, the range needs " + std::to_string(total));
+        if (total && c.n > 32) fail(PTSBE_ERR_UNSUPPORTED, "outcomes are 32-bit");
+        std::vector<uint8_t> drawn;
+        const FusedShots fs{seed, d_bits};
+        evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, total ? &fs : nullptr, &drawn);
+        if (total) sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, &drawn);
     });
 }
 
@@ -753,6 +862,9 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         } else if (option == PTSBE_OPT_LIGHT_SHOTS) {
             if (value < 0) fail(PTSBE_ERR_INVALID, "light-sampler shot limit must be >= 0");
             ctx->light_shots = (uint64_t)value;
+        } else if (option == PTSBE_OPT_PROGRAM_SETS_PER_WARP) {
+            if (value != 0 && value != 4 && value != 8 && value != 16) fail(PTSBE_ERR_INVALID, "sets per warp must be 0, 4, 8 or 16");
+            ctx->prog_sets_per_warp = value ? (int)value : 8;
         } else {
             fail(PTSBE_ERR_INVALID, "unknown option");
         }
@@ -796,8 +908,8 @@ int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t cou
             }
             ctx->evolve_kernel = best_k;
             PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
-            if (ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags) != PTSBE_OK)
-                fail(PTSBE_ERR_INVALID, "autotune: " + ctx->err);
+            // the shot limit splits states between the sampling fused into the last evolve launch
+            // (or the one-CTA sampler) and the cluster sampler: timed on the one-call path
             const uint64_t cand[4] = {512, 4096, 65536, 1ull << 20};
             int best_l = -1;
             double best_s = 0;
@@ -805,7 +917,8 @@ int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t cou
                 ctx->light_shots = cand[i];
                 t.light_candidates[i] = cand[i];
                 const double ms = timed_ms([&] {
-                    return ptsbe_sample_shots(ctx, set_id, first, count, d_states, d_status, seed, d_bits, d_bits_capacity);
+                    return ptsbe_evolve_sample(ctx, set_id, first, count, d_states, d_weights, d_status, flags, seed, d_bits,
+                                               d_bits_capacity);
                 });
                 if (ms < 0) fail(PTSBE_ERR_INVALID, "autotune: sampler: " + ctx->err);
                 t.sample_ms[i] = ms;

@@ -18,8 +18,10 @@
 // stage is still intact while the stage writes its outputs; one launch per stage covers all sets.
 #include <cstdio>
 
+#include "fixed_point.cuh"
 #include "frame.cuh"
 #include "internal.h"
+#include "philox.h"
 #include "tile_ops.cuh"
 
 namespace ptsbe {
@@ -117,19 +119,27 @@ __host__ __device__ inline size_t frame_tab_offset_amps(uint32_t tamps, int tb, 
 __host__ __device__ inline size_t frame_tab_offset(int tb, int lb) { return frame_tab_offset_amps(1u << tb, tb, lb); }
 
 // One thread per node of a launch builds the node's program for the stage (the first segment, and
-// the builder state a tile CTA needs to continue when the program is longer).
-constexpr int kProgThreads = 16;
-__global__ void __launch_bounds__(kProgThreads) k_frame_program(EvolveArgs a, int stage_idx, const uint32_t* __restrict__ nodes,
-                                                                uint32_t n_nodes, frame::Program* progs) {
+// the builder state a tile CTA needs to continue when the program is longer). A CTA serves 16
+// nodes (builder states in shared memory); SPW of them share a warp, one per group of 32 / SPW
+// lanes. The builders' branches depend on each set's entries, so lanes of one warp diverge: fewer
+// sets per warp run shorter instruction streams, and more warps share each scheduler.
+constexpr int kProgSets = 16;
+template <int SPW>
+__global__ void __launch_bounds__(32 * (kProgSets / SPW), SPW == 4 ? 5 : 1)
+k_frame_program(EvolveArgs a, int stage_idx, const uint32_t* __restrict__ nodes, uint32_t n_nodes, frame::Program* progs) {
     using namespace frame;
-    __shared__ Builder Bs[kProgThreads];
+    __shared__ Builder Bs[kProgSets];
     __shared__ DevStage st;
     if (threadIdx.x == 0) st = a.stages[stage_idx];
     __syncthreads();
-    const uint32_t i = blockIdx.x * kProgThreads + threadIdx.x;
+    constexpr uint32_t stride = 32 / SPW;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane % stride) return;
+    const uint32_t slot = (threadIdx.x >> 5) * SPW + lane / stride;
+    const uint32_t i = blockIdx.x * kProgSets + slot;
     if (i >= n_nodes) return;
     const uint32_t node = nodes[i];
-    Builder& B = Bs[threadIdx.x];
+    Builder& B = Bs[slot];
     Program& P = progs[i];
     builder_init(B, a, st, a.fstages[stage_idx], node, a.node_fresh[node] && stage_idx == 0);
     build_segment(B, P.S, P.pool, a, st, kProgSteps, kProgPool);
@@ -143,13 +153,100 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t 
     for (uint32_t i = t; i < bytes / 4; i += nt) d[i] = __ldg(s + i);
 }
 
+// Sparse final store fused with drawing the state's shots (Sec. 3: all m_alpha shots of a
+// prepared state at once). The CTA holds the state's support on chip, so the outcome CDF is built
+// from it instead of from a read of the stored 2^n amplitudes: every other amplitude is an exact
+// zero and adds nothing to an inclusive prefix, so the smallest index whose prefix exceeds a
+// target is a support entry, and the shots equal those the stand-alone samplers draw from the
+// stored state (same fixed-point probabilities of the same stored values, same Philox counters).
+// Support entries are placed in increasing logical order by their bits at the order mask's
+// positions (frame::sparse_order_mask); cdf and lidx (2^ncomp entries each) live in scratch.
+__device__ void scatter_and_sample(const EvolveArgs& a, const frame::Step& fin, const DevFrameStage& fs,
+                                   const float2* tile, const float2* tabs, const uint32_t* delta, const uint32_t* hi,
+                                   float2* g, float scale, bool null, uint32_t node, uint32_t m, void* scratch,
+                                   double* red, uint32_t tid, uint32_t nthr) {
+    using namespace frame;
+    __shared__ uint32_t order, ok;
+    const int n = a.n;
+    uint32_t* out = a.shot_bits + a.node_shot_out[node];
+    if (tid == 0) {
+        order = sparse_order_mask(fin, fs, n, a.lb, hi);
+        ok = (!null && fin.ncomp != 0xFF && (uint32_t)__popc(order) == fin.ncomp) ? 1u : 0u;
+        if (!null && !ok) atomicOr(a.fault, 1u);
+    }
+    __syncthreads();
+    const uint32_t last = (uint32_t)((1ull << n) - 1ull);
+    if (!ok) {
+        // A null state has no outcome: the all-ones marker when the status is recorded (as the
+        // samplers write), else what they draw from its zeroed amplitudes (T = 0: the last index).
+        // The other case cannot occur for a plan's support (flagged above) and leaves the marker.
+        if (!null) run_sparse_final(fin, fs, tile, tabs, delta, n, a.lb, hi, g, scale, 1, tid, nthr);
+        const uint32_t mark = (null && !a.status) ? last : 0xFFFFFFFFu;
+        for (uint32_t k = tid; k < m; k += nthr) out[k] = mark;
+        return;
+    }
+    const uint32_t H = order, N = 1u << fin.ncomp;
+    fx* cdf = reinterpret_cast<fx*>(scratch);
+    uint32_t* lidx = reinterpret_cast<uint32_t*>(cdf + N);
+    for (uint32_t i = tid; i < N; i += nthr) {
+        const uint32_t p = enum_base(fin, i, nullptr, 0);
+        const float2 v = mul2r(sparse_value(fin, tile, tabs, delta, p), scale);
+        const uint32_t l = sparse_logical(fin, fs, n, a.lb, hi, p);
+        g[l] = v;
+        const uint32_t r = extract_bits(l, H);
+        cdf[r] = fx_prob(v);
+        lidx[r] = l;
+    }
+    __syncthreads();
+    // inclusive prefix in rank order: thread t owns K consecutive entries
+    const uint32_t K = N > nthr ? N / nthr : 1u, c0 = tid * K;
+    fx mine = 0;
+    if (c0 < N)
+        for (uint32_t i = 0; i < K; ++i) mine += cdf[c0 + i];
+    fx v = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const fx y = __shfl_up_sync(0xffffffffu, v, o);
+        if ((tid & 31) >= (uint32_t)o) v += y;
+    }
+    fx* fred = reinterpret_cast<fx*>(red);
+    const uint32_t w = tid >> 5, nw = nthr >> 5;
+    if ((tid & 31) == 31) fred[w] = v;
+    __syncthreads();
+    if (tid == 0) {
+        fx acc = 0;
+        for (uint32_t i = 0; i < nw; ++i) { const fx t = fred[i]; fred[i] = acc; acc += t; }
+    }
+    __syncthreads();
+    fx run = fred[w] + (v - mine);
+    if (c0 < N)
+        for (uint32_t i = 0; i < K; ++i) { run += cdf[c0 + i]; cdf[c0 + i] = run; }
+    __syncthreads();
+    const fx T = cdf[N - 1];
+    const uint32_t alpha = a.shot_alpha0 + node;
+    for (uint32_t k = tid; k < m; k += nthr) {
+        const Philox4 x = philox4x32_10(k, 0u, alpha, kDomShot, (uint32_t)a.shot_seed, (uint32_t)(a.shot_seed >> 32));
+        const fx t = fx_target(u53_bits(x.x[0], x.x[1]), T);
+        uint32_t idx = last;                            // T = 0
+        if (t < T) {
+            uint32_t lo = 0, hi2 = N - 1;               // smallest rank r with t < cdf[r]
+            while (lo < hi2) {
+                const uint32_t mid = (lo + hi2) >> 1;
+                if (t < cdf[mid]) hi2 = mid; else lo = mid + 1;
+            }
+            idx = lidx[lo];
+        }
+        out[k] = idx;
+    }
+}
+
 constexpr int kFrameThreads = 512;   // 128 registers per thread: grouped mixes stay in registers
 // SMALL: a sparse final stage whose support lies below tile address 2^fs.sbits (the plan entered
 // the stage in a layout that maps the mixing directions to the low bits); the tile buffer holds
 // only that prefix, so several CTAs share an SM and one CTA's stores overlap another's passes.
 constexpr int kFrameSmallThreads = 128;
 constexpr int kZeroChunk = 4096;      // bytes per bulk zero copy (the state size is a multiple)
-constexpr int kFrameSmallCtas = 3;
+constexpr int kFrameSmallCtas = 4;
 template <bool SMALL>
 __global__ void __launch_bounds__(SMALL ? kFrameSmallThreads : kFrameThreads, SMALL ? kFrameSmallCtas : 1)
 k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes,
@@ -288,7 +385,14 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
         const double w = a.wmix[node] * part;
         const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
         const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
-        if (!null) run_sparse_final(fin, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
+        const uint32_t m = a.shot_bits ? a.node_shots[node] : 0u;
+        if (m) {
+            // the program's steps and factor pool are dead: their shared memory holds the CDF
+            static_assert((sizeof(fx) + sizeof(uint32_t)) << kSmallSupportBits <= sizeof(S), "CDF scratch");
+            scatter_and_sample(a, fin, fs, tile, tabs, delta, hi, g, scale, null, node, m, S, red, tid, nthr);
+        } else if (!null) {
+            run_sparse_final(fin, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
+        }
         if (tid == 0) {
             if (a.weights) a.weights[node] = w;
             if (a.status) a.status[node] = null ? 1 : 0;
@@ -819,7 +923,8 @@ size_t evolve_frame_smem_bytes(int tb, int lb) {
     return frame_tab_offset(tb, lb) + (size_t)frame::kMaxTabs * frame::kTabSize * sizeof(float2);
 }
 size_t evolve_frame_small_smem_bytes(int sbits, int tb, int lb) {
-    return frame_tab_offset_amps(1u << sbits, tb, lb) + (size_t)frame::kMaxTabs * frame::kTabSize * sizeof(float2);
+    // tables of a small stage index at most sbits tile bits (rows outside the support are dropped)
+    return frame_tab_offset_amps(1u << sbits, tb, lb) + ((size_t)frame::kMaxTabs << sbits) * sizeof(float2);
 }
 size_t evolve_rb_smem_bytes(int tb, int lb) { return ((evolve_smem_bytes(tb, lb) + 15) & ~(size_t)15) + 8 * (size_t)kMaxStream; }
 
@@ -866,11 +971,18 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
     }
 }
 
-void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s) {
+void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,
+                          int sets_per_warp) {
     if (n_nodes == 0) return;
     frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
     if (!progs) fail(PTSBE_ERR_INVALID, "frame program prepass launched without workspace");
-    k_frame_program<<<(n_nodes + kProgThreads - 1) / kProgThreads, kProgThreads, 0, s>>>(a, stage, d_nodes, n_nodes, progs);
+    const uint32_t ctas = (n_nodes + kProgSets - 1) / kProgSets;
+    if (sets_per_warp == 4)
+        k_frame_program<4><<<ctas, 32 * (kProgSets / 4), 0, s>>>(a, stage, d_nodes, n_nodes, progs);
+    else if (sets_per_warp == 8)
+        k_frame_program<8><<<ctas, 32 * (kProgSets / 8), 0, s>>>(a, stage, d_nodes, n_nodes, progs);
+    else
+        k_frame_program<16><<<ctas, 32 * (kProgSets / 16), 0, s>>>(a, stage, d_nodes, n_nodes, progs);
     PTSBE_CUDA(cudaGetLastError());
     count_launch();
 }

@@ -85,7 +85,7 @@ struct Step {
     // Sparse passes (a stage started from |0...0>): the nonzero amplitudes lie in the span of the
     // directions mixed so far, so MIX / DIAG passes visit only the cosets base = sum_i bit_i comp[i]
     // of that span (complemented by the step's own directions); ncomp = 0xFF: the whole tile.
-    uint8_t ncomp, pad3;
+    uint8_t ncomp, tsb;              // tsb: table t starts at entry t << tsb of the table buffer
     uint16_t comp[kTileMax];
     Table tab[kMaxTabs];
     float2 m[16];                    // MIX1: 2x2 of direction i at m[4i..4i+3]; MIX2: 4x4 on 2 l_a + l_b
@@ -99,8 +99,9 @@ struct Builder {
     uint32_t npush, nframe;                      // factor changes and frame changes so far
     uint32_t sparse, sdim;                       // support tracking (stage from |0...0>): basis size
     uint32_t sparse_final;                       // the stage ends with the sparse final store
+    uint32_t tmask;                              // tile bits a table row keeps (the support's, small stages)
     uint16_t sech[kTileMax];                     // echelon basis of the support (tile-local)
-    uint8_t spiv[kTileMax], pad3[2];
+    uint8_t spiv[kTileMax], tsb, pad3;          // tsb: log2 of the table stride of emitted steps
     uint16_t ech[kTabBits], comb[kTabBits];      // echelon rows of the table being filled
     uint8_t piv[kTabBits], pad2[2];
     Factor pend[kMaxPending];
@@ -235,6 +236,7 @@ PTSBE_HD void order_table(Table& T, Factor* pool) {
 // factors that found a table (all of them unless more than kMaxTabs tables would be needed).
 PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor* pool, uint64_t mask) {
     st.ntab = 0;
+    st.tsb = B.tsb;
     uint64_t used = 0, left = mask;
     while (left && st.ntab < kMaxTabs) {
         Table& T = st.tab[st.ntab];
@@ -245,9 +247,9 @@ PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor*
             if (!((left >> j) & 1u)) continue;
             const Factor& f = B.pend[j];
             const int d0 = d;
-            const uint32_t c1 = reduce_or_add(tile_part(stg, f.r1), T, B.ech, B.comb, B.piv, d);
+            const uint32_t c1 = reduce_or_add(tile_part(stg, f.r1) & B.tmask, T, B.ech, B.comb, B.piv, d);
             uint32_t c2 = 0;
-            if (d <= kTabBits) c2 = reduce_or_add(tile_part(stg, f.r2), T, B.ech, B.comb, B.piv, d);
+            if (d <= kTabBits) c2 = reduce_or_add(tile_part(stg, f.r2) & B.tmask, T, B.ech, B.comb, B.piv, d);
             if (d > kTabBits) { d = d0; continue; }
             Factor& g = pool[B.npool++];
             g = f;
@@ -631,6 +633,12 @@ PTSBE_HD_CALL void builder_init(Builder& B, const EvolveArgs& a, const DevStage&
     B.sparse = from_zero ? 1u : 0u;      // the support starts as {0}
     B.sdim = 0;
     B.sparse_final = fs.sparse_final;
+    // A sparse final stage with a support bound keeps every nonzero amplitude below tile address
+    // 2^sbits: parities against the other tile bits never matter, so table rows drop them (at most
+    // sbits index bits per table).
+    const bool small = fs.sparse_final && fs.sbits > 0;
+    B.tmask = small ? (1u << fs.sbits) - 1u : 0xFFFFFFFFu;
+    B.tsb = (uint8_t)(small ? fs.sbits : kTabBits);
 }
 
 // Emits steps until the stage ends (then the end step and done = 1) or the step list or the
@@ -754,14 +762,14 @@ PTSBE_HD void prepare_tables(const Step& st, const DevFrameStage& fs, const Fact
                     const Factor& f = pool[j];
                     v *= f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))].x;
                 }
-                tabs[t * kTabSize + idx] = make_float2(v, 0.f);
+                tabs[((uint32_t)t << st.tsb) + idx] = make_float2(v, 0.f);
             } else {
                 float2 v = make_float2(1.f, 0.f);
                 for (uint32_t j = T.fb; j < T.fe; ++j) {
                     const Factor& f = pool[j];
                     v = fmul(v, f.f[2u * (par(f.c1 & idx) ^ par(f.r1o & tau)) + (par(f.c2 & idx) ^ par(f.r2o & tau))]);
                 }
-                tabs[t * kTabSize + idx] = v;
+                tabs[((uint32_t)t << st.tsb) + idx] = v;
             }
         }
     }
@@ -772,7 +780,7 @@ PTSBE_HD void prepare_tables(const Step& st, const DevFrameStage& fs, const Fact
 
 struct Lookup {
     int ntab, real;                  // real bit t: table t holds real values
-    uint32_t ix[kMaxTabs];
+    uint32_t ix[kMaxTabs];           // entry in the table buffer (table base t << tsb | index)
 };
 
 PTSBE_HD float2 apply_tabs(float2 x, const Lookup& L, const float2* tabs, const uint32_t* delta, int slot) {
@@ -781,9 +789,9 @@ PTSBE_HD float2 apply_tabs(float2 x, const Lookup& L, const float2* tabs, const 
         if (t < L.ntab) {
             const uint32_t i = slot < 0 ? L.ix[t] : (L.ix[t] ^ delta[t * kDeltaSlots + slot]);
             if ((L.real >> t) & 1) {
-                x = mul2r(x, reinterpret_cast<const float*>(tabs + t * kTabSize + i)[0]);
+                x = mul2r(x, reinterpret_cast<const float*>(tabs + i)[0]);
             } else {
-                x = fmul(x, tabs[t * kTabSize + i]);
+                x = fmul(x, tabs[i]);
             }
         }
     return x;
@@ -794,7 +802,7 @@ PTSBE_HD void lookup_init(Lookup& L, const Step& st, uint32_t p) {
     L.real = 0;
     for (int t = 0; t < st.ntab; ++t) L.real |= st.tab[t].real << t;
 #pragma unroll
-    for (int t = 0; t < kMaxTabs; ++t) L.ix[t] = t < L.ntab ? lin_idx(st.tab[t], p) : 0u;
+    for (int t = 0; t < kMaxTabs; ++t) L.ix[t] = t < L.ntab ? (((uint32_t)t << st.tsb) | lin_idx(st.tab[t], p)) : 0u;
 }
 PTSBE_HD void lookup_step(Lookup& L, const uint32_t* delta, int j) {
 #pragma unroll
@@ -1074,6 +1082,24 @@ PTSBE_HD double run_final(const Step& st, const DevFrameStage& fs, const float2*
 // Sparse final store: the support of the state (span of comp, all in this tile) holds every
 // nonzero amplitude. phase 0 returns this thread's part of the squared norm; phase 1 writes
 // D(x) s[x] * scale to logical index R_end x ^ R_end b of dst (the caller zero-filled dst before).
+// Support entry at tile position p of the sparse final store: its amplitude (deferred factors
+// applied, before the normalisation scale) and its logical index.
+PTSBE_HD float2 sparse_value(const Step& st, const float2* s, const float2* tabs, const uint32_t* delta, uint32_t p) {
+    float2 a = s[p];
+    if (st.ntab) {
+        Lookup L;
+        lookup_init(L, st, p);
+        a = apply_tabs(a, L, tabs, delta, -1);
+    }
+    return a;
+}
+PTSBE_HD uint32_t sparse_logical(const Step& st, const DevFrameStage& fs, int n, int lb, const uint32_t* hi, uint32_t p) {
+    const uint64_t x = gaddr(p, lb, hi, 0);
+    uint32_t l = st.lb0;
+    for (int q = 0; q < n; ++q) l ^= par(fs.rowe[q] & (uint32_t)x) << q;
+    return l;
+}
+
 PTSBE_HD double run_sparse_final(const Step& st, const DevFrameStage& fs, const float2* s, const float2* tabs,
                                  const uint32_t* delta, int n, int lb, const uint32_t* hi, float2* dst, float scale,
                                  int phase, uint32_t tid, uint32_t nthr) {
@@ -1081,22 +1107,45 @@ PTSBE_HD double run_sparse_final(const Step& st, const DevFrameStage& fs, const 
     double acc = 0.0;
     for (uint32_t i = tid; i < N; i += nthr) {
         const uint32_t p = enum_base(st, i, nullptr, 0);
-        float2 a = s[p];
-        if (st.ntab) {
-            Lookup L;
-            lookup_init(L, st, p);
-            a = apply_tabs(a, L, tabs, delta, -1);
-        }
-        if (phase == 0) {
-            acc += (double)fmaf(a.x, a.x, a.y * a.y);
-        } else {
-            const uint64_t x = gaddr(p, lb, hi, 0);
-            uint32_t l = st.lb0;
-            for (int q = 0; q < n; ++q) l ^= par(fs.rowe[q] & (uint32_t)x) << q;
-            dst[l] = mul2r(a, scale);
-        }
+        const float2 a = sparse_value(st, s, tabs, delta, p);
+        if (phase == 0) acc += (double)fmaf(a.x, a.x, a.y * a.y);
+        else dst[sparse_logical(st, fs, n, lb, hi, p)] = mul2r(a, scale);
     }
     return acc;
+}
+
+// Order of the support in logical index. The support's logical indices form an affine subspace
+// c + span(v_0 .. v_{k-1}), v_j the image of the coset generator comp[j] (the map from tile
+// position to logical index is affine over GF(2)). Reduce the v_j to an echelon basis with
+// distinct leading bits h_j: two members differ by a nonzero combination whose highest bit is
+// some h_j, so they agree above h_j and the one with bit h_j set is larger, and the bits of a
+// member at the positions h_j, read as a k-bit integer, give its rank in increasing order.
+// Returns the mask of the h_j (k bits set exactly when the images are independent).
+PTSBE_HD uint32_t sparse_order_mask(const Step& st, const DevFrameStage& fs, int n, int lb, const uint32_t* hi) {
+    if (st.ncomp == 0xFF) return 0u;
+    uint32_t basis[32];
+    uint32_t lead = 0;
+    const uint32_t l0 = sparse_logical(st, fs, n, lb, hi, 0u);
+    for (int j = 0; j < st.ncomp; ++j) {
+        uint32_t v = sparse_logical(st, fs, n, lb, hi, st.comp[j]) ^ l0;
+        while (v) {
+            const int h = high_bit(v);
+            if (!((lead >> h) & 1u)) { basis[h] = v; lead |= 1u << h; break; }
+            v ^= basis[h];
+        }
+    }
+    return lead;
+}
+
+// Bits of x at the set positions of mask, packed from bit 0 up.
+PTSBE_HD uint32_t extract_bits(uint32_t x, uint32_t mask) {
+    uint32_t r = 0;
+    for (int k = 0; mask; ++k) {
+        const int b = low_bit(mask);
+        r |= ((x >> b) & 1u) << k;
+        mask &= mask - 1u;
+    }
+    return r;
 }
 
 }  // namespace frame

@@ -336,6 +336,15 @@ struct EvolveArgs {
     int sparse_final_stage;          // frame kernel: stage with the sparse final store (one CTA per state), or -1
     const float* scale_in;           // frame kernel: the last stage writes psi * scale_in[node] (norm known)
     int small_bits;                  // frame kernel: support bits of the sparse final stage (0: tile-sized buffer)
+    // Shots drawn by the small sparse final stage from the support it holds on chip (null
+    // shot_bits: none). Node i draws node_shots[i] shots (0: drawn later by a sampler kernel) into
+    // shot_bits[node_shot_out[i] ...], with Philox counter word 2 = shot_alpha0 + i.
+    uint32_t* shot_bits;
+    const uint32_t* node_shots;
+    const uint64_t* node_shot_out;
+    uint64_t shot_seed;
+    uint32_t shot_alpha0;
+    uint32_t* fault;                 // set nonzero when a launch could not do its work (checked by the host)
 };
 
 // kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame
@@ -343,7 +352,8 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                          cudaStream_t s, int kernel = 0);
 // Frame kernel (kernel 0 or 3): builds the per-node programs of a stage; must precede
 // launch_evolve_stage of the same stage and nodes.
-void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s);
+void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,
+                          int sets_per_warp);
 void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 size_t evolve_frame_program_bytes();   // workspace per node of a frame-kernel launch

@@ -118,6 +118,10 @@ class Ptsbe:
                 "evolve_ms": {names[k]: t.evolve_ms[k] for k in (1, 2, 3)},
                 "sample_ms": {int(t.light_candidates[i]): t.sample_ms[i] for i in range(4)}}
 
+    def set_program_sets_per_warp(self, spw: int):
+        """Kraus sets per warp of the frame program prepass (4, 8 or 16; 0 = default, 8)."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_PROGRAM_SETS_PER_WARP, int(spw))
+
     def set_light_shots(self, limit: int):
         """Shot count up to which a state is sampled by the one-CTA light sampler."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_LIGHT_SHOTS, int(limit))
@@ -205,6 +209,14 @@ class Ptsbe:
     def sample(self, info: KrausSetInfo, first: int, count: int, states, status, seed: int, bits):
         capi.ptsbe_sample_shots(self.ctx, info.set_id, first, count, _ptr(states), _ptr(status), seed, _ptr(bits),
                                 bits.numel())
+
+    def evolve_sample(self, info: KrausSetInfo, first: int, count: int, states, weights, status, seed: int, bits,
+                      prefix_reuse: bool = False):
+        """evolve() then sample() in one call (same outputs); light states' shots are drawn by the last
+        evolve launch from the support it holds on chip."""
+        flags = capi.PTSBE_EVOLVE_PREFIX_REUSE if prefix_reuse else 0
+        capi.ptsbe_evolve_sample(self.ctx, info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), flags,
+                                 seed, _ptr(bits), bits.numel() if bits is not None else 0)
 
     def backward(self, cid: int, info: KrausSetInfo, first: int, count: int, masks=(), coeffs=(), diag=None,
                  checkpoint_every: int = 0, loss=None, per_set=None, grad_params=None, grad_noise=None):

@@ -33,6 +33,26 @@ uint32_t threads_for(int tb) {
 }
 
 int g_guard_violations = 0;   // small-buffer stages: tile entries past 2^sbits that were touched
+int g_order_checks = 0;       // sparse final stores whose support order (fused sampling) was checked
+int g_order_violations = 0;   // ... whose order mask did not rank the support 0 .. N-1 increasingly
+
+// The ranks the fused sampler gives the support entries (bits of the logical index at the order
+// mask) must be a bijection onto 0 .. N-1 that increases with the logical index.
+void check_support_order(const Step& sp, const DevFrameStage& fs, int n, int lb, const uint32_t* hi) {
+    ++g_order_checks;
+    const uint32_t H = sparse_order_mask(sp, fs, n, lb, hi);
+    if (sp.ncomp == 0xFF || __builtin_popcount(H) != sp.ncomp) { ++g_order_violations; return; }
+    const uint32_t N = 1u << sp.ncomp;
+    std::vector<int64_t> at(N, -1);
+    for (uint32_t i = 0; i < N; ++i) {
+        const uint32_t l = sparse_logical(sp, fs, n, lb, hi, enum_base(sp, i, nullptr, 0));
+        const uint32_t r = extract_bits(l, H);
+        if (r >= N || at[r] != -1) { ++g_order_violations; return; }
+        at[r] = l;
+    }
+    for (uint32_t r = 1; r < N; ++r)
+        if (at[r] <= at[r - 1]) { ++g_order_violations; return; }
+}
 
 void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t tau, const float* scale_in) {
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
@@ -49,6 +69,9 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
     float sent;
     std::memcpy(&sent, &kSentinel, 4);
     for (uint32_t v = tamps; v < (1u << tb); ++v) tile[v] = make_float2(sent, sent);
+    // the small kernel's table buffer holds kMaxTabs << sbits entries: the same sentinel past it
+    const size_t tabs_len = small ? ((size_t)kMaxTabs << a.fstages[stage].sbits) : tabs.size();
+    for (size_t v = tabs_len; v < tabs.size(); ++v) tabs[v] = make_float2(sent, sent);
     static Builder B;
     static Step S[kProgSteps];
     static Factor pool[kProgPool];
@@ -98,9 +121,11 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
                 const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
                 const float scale = null ? 0.0f : (float)(1.0 / std::sqrt(part));
                 for (size_t i = 0; i < (1ull << n); ++i) g[i] = make_float2(0.f, 0.f);
-                if (!null)
+                if (!null) {
                     for (uint32_t t = 0; t < nthr_final; ++t)
                         run_sparse_final(sp, fs, tile.data(), tabs.data(), delta, n, lb, hi, g, scale, 1, t, nthr_final);
+                    check_support_order(sp, fs, n, lb, hi);
+                }
                 a.weights[node] = w;
                 a.status[node] = null ? 1 : 0;
             } else if (sp.kind == ST_STORE) {
@@ -143,6 +168,12 @@ void run_cta(const EvolveArgs& a, int stage, bool last, uint32_t node, uint32_t 
         std::memcpy(&by, &tile[v].y, 4);
         if (bx != kSentinel || by != kSentinel) ++g_guard_violations;
     }
+    for (size_t v = tabs_len; v < tabs.size(); ++v) {
+        uint32_t bx, by;
+        std::memcpy(&bx, &tabs[v].x, 4);
+        std::memcpy(&by, &tabs[v].y, 4);
+        if (bx != kSentinel || by != kSentinel) ++g_guard_violations;
+    }
 }
 
 }  // namespace
@@ -168,6 +199,11 @@ int fh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
 // Sets in CSR (off, site, k) with nominal probabilities q; the same schedule as ptsbe_evolve_batch
 // (prefix reuse, alternating buffers, early norm when the last stage has no ops).
 // Support bits of the plan's sparse final stage (0: none, or no support bound).
+void fh_order_stats(int* checks, int* violations) {
+    *checks = g_order_checks;
+    *violations = g_order_violations;
+}
+
 int fh_sparse_bits() {
     for (const DevFrameStage& f : g_plan.fstages)
         if (f.sparse_final) return (int)f.sbits;

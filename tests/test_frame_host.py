@@ -103,6 +103,12 @@ def test_deep_cx_network_restarts_the_frame(fh, oracle_mod):
     assert stages >= 3
 
 
+def _order_stats(fh):
+    c, v = C.c_int(0), C.c_int(0)
+    fh.fh_order_stats(C.byref(c), C.byref(v))
+    return c.value, v.value
+
+
 def test_syndrome_plan_and_states(fh, oracle_mod):
     """One syndrome round on 17 qubits: the CX-heavy circuit fits one frame stage; one CTA per
     state holds every nonzero amplitude and scatters them in logical order (sparse final)."""
@@ -119,9 +125,13 @@ def test_syndrome_support_in_low_bits(fh, oracle_mod):
     with a sentinel and fails if any step touches it."""
     circ = syndrome17(rounds=3)
     sets = oracle_mod.Oracle(circ).pts_topk(300, 3000)
+    c0, v0 = _order_stats(fh)
     stages = _compare(fh, oracle_mod, circ, sets, 14, 1, check=range(0, 300, 23))
     assert stages == 1
     assert fh.fh_sparse_bits() == 8
+    # fused sampling: the order mask ranks every state's 256-entry support increasingly
+    c1, v1 = _order_stats(fh)
+    assert c1 - c0 >= 300 and v1 == v0
 
 
 @pytest.mark.parametrize("n,tile_bits", [(10, 8), (12, 9)])
@@ -140,8 +150,11 @@ def test_one_stage_multi_tile_sparse_final(fh, oracle_mod, n, tile_bits):
         b.gate("H", [2]); b.noise(ad, [2])
     circ = b.build()
     sets = oracle_mod.Oracle(circ).pts_proportional(30, 11, total_shots=300)
+    c0, v0 = _order_stats(fh)
     stages = _compare(fh, oracle_mod, circ, sets, tile_bits, 1)
     assert stages == 1
+    c1, v1 = _order_stats(fh)
+    assert c1 > c0 and v1 == v0
 
 
 def _sink(n, seed):

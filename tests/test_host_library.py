@@ -194,3 +194,19 @@ def test_predicate_refuses_too_many_sets(host):
     with pytest.raises(PtsbeError) as e:
         host.sample_kraus(cid, "predicate", total_shots=10, max_errors=3, max_sets=1000)
     assert e.value.status == 7
+
+
+def test_options_validate_values(host):
+    """Options are host-side state: accepted values take, others are refused with ERR_INVALID."""
+    from paper_2504_16297_gb300 import capi
+    for spw in (0, 4, 8, 16):
+        host.set_program_sets_per_warp(spw)
+    for bad in (1, 2, 5, 32, -4):
+        with pytest.raises(capi.PtsbeError) as e:
+            host.set_program_sets_per_warp(bad)
+        assert e.value.status == 1
+    host.set_light_shots(0)
+    with pytest.raises(capi.PtsbeError):
+        host.set_light_shots(-1)
+    with pytest.raises(capi.PtsbeError):
+        capi.ptsbe_set_option(host.ctx, 99, 0)
