@@ -35,7 +35,7 @@ METRIC = "shots/s & gate-apply HBM GB/s, PTSBE batched vs per-shot trajectories,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k", type=int, default=10_000)
     ap.add_argument("--shots", type=int, default=100_000_000)
     ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "frame", "sweep", "registers"])
+    ap.add_argument("--e2e-copy", default="overlap", choices=["overlap", "serial"],
+                    help="e2e device-to-host copies on a side stream or on the compute stream")
     ap.add_argument("--separate", action="store_true",
                     help="time ptsbe_evolve_batch + ptsbe_sample_shots instead of the one-call ptsbe_evolve_sample")
     ap.add_argument("--no-backward", action="store_true",
@@ -365,7 +367,9 @@ def main():
     host_bits = [torch.empty(M, dtype=torch.int32, pin_memory=True) for _ in range(2)]
     host_w = [torch.empty(K, dtype=torch.float64, pin_memory=True) for _ in range(2)]
     host_s = [torch.empty(K, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-    copy_stream = torch.cuda.Stream(dev)
+    # e2e copies: on their own stream, overlapping the next step's kernels ("overlap"), or on the
+    # compute stream after the step's kernels ("serial")
+    copy_stream = torch.cuda.Stream(dev) if args.e2e_copy == "overlap" else stream
     done = [torch.cuda.Event(), torch.cuda.Event()]      # buffer b's copy finished
     h2d_bytes = [0]
     count = [0]
@@ -525,7 +529,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": h2d_bytes[0],
-                    "d2h_bytes_per_step": M * 4 + K * 9},
+                    "d2h_bytes_per_step": M * 4 + K * 9, "copies": args.e2e_copy},
             "gpu_launches": launches,
             "clocks": clk,
             "backward": bw,
