@@ -148,6 +148,20 @@ def traffic_for(kernel: str):
     return None
 
 
+def inst_for(kernel: str, sets: int):
+    """Warp instructions of one launch over `sets` Kraus sets, from a committed ncu count taken on
+    the current source (None otherwise)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            e = json.load(f).get(kernel)
+        if e and e.get("source_sha") == source_sha(e["sources"]):
+            return float(e["warp_inst_per_set"]) * sets
+    except Exception:
+        pass
+    return None
+
+
 # ----------------------------------------------------------------------------------------------
 # CPU oracle leg
 # ----------------------------------------------------------------------------------------------
@@ -498,14 +512,37 @@ def main():
     e2e_value = job_throughput(world, M, ms_e2e / steps_e2e)
     peak, peak_kind = peaks()
     dom = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
-    roof = None
-    if dom:
-        d = kern[dom]
+
+    def hbm_roof(name):
+        d = kern[name]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": traffic_for(dom), "bytes_per_launch": d["bytes"] / d["launches"],
+                "traffic": traffic_for(name), "bytes_per_launch": d["bytes"] / d["launches"],
                 "ms_per_launch": d["ms"] / d["launches"]}
+
+    roof, roof_hbm = None, None
+    byte_kernels = [k for k, v in kern.items() if v["bytes"] > 0]
+    if byte_kernels:
+        roof_hbm = hbm_roof(max(byte_kernels, key=lambda k: kern[k]["ms"]))
+    if dom and kern[dom]["bytes"] > 0:
+        roof = roof_hbm
+    elif dom:
+        # The program prepass moves almost no data: one serial builder chain per Kraus set, bound
+        # by instruction issue and latency. Its roofline is the warp-instruction issue rate (one
+        # warp instruction per cycle on each of the 4 schedulers of every SM) at the measured SM
+        # clock, against the warp instructions one launch executes (ncu count of this source,
+        # scaled by the sets of the launch).
+        d = kern[dom]
+        inst = inst_for(dom, K)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_issue = 4 * n_sm * mhz * 1e6 / 1e9
+        ms_launch = d["ms"] / d["launches"]
+        achieved = inst / (ms_launch / 1e3) / 1e9 if inst else None
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_issue, "unit": "Gwarp-inst/s",
+                "frac": (achieved / peak_issue) if achieved else None, "peak_kind": "4 schedulers x SMs x measured SM clock",
+                "traffic": None, "warp_inst_per_launch": inst, "ms_per_launch": ms_launch}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -527,6 +564,7 @@ def main():
             "speedup_vs_pershot": (value / world / pershot["value"]) if pershot else None,
             "kernels": kern,
             "roofline": roof,
+            "roofline_hbm": roof_hbm if roof_hbm is not roof else None,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "shots/s", "h2d_bytes_per_step": h2d_bytes[0],
                     "d2h_bytes_per_step": M * 4 + K * 9, "copies": args.e2e_copy},

@@ -285,7 +285,10 @@ PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * stage), that CTA also draws the shots of states with at most PTSBE_OPT_LIGHT_SHOTS shots from
  * the support it holds on chip, so those states are never read back; the CDF of a state over its
  * support in increasing index order has the same prefix values as over all 2^n entries (the
- * others are exact zeros). The remaining states go to the sampler kernels. Arguments, layouts and
+ * others are exact zeros). Heavier states leave that CDF (at most 2^10 entries) in a library
+ * workspace, and a sampler kernel spreads their shots over many CTAs, each holding the CDF in
+ * shared memory. Without a sparse final stage the states go to the sampler kernels of
+ * ptsbe_sample_shots. Arguments, layouts and
  * ownership as for the two calls. Asynchronous. Errors: those of the two calls; a kernel that
  * finds a support not of the form the plan guarantees flags the context, and the next
  * ptsbe_synchronize returns PTSBE_ERR_UNSUPPORTED (the affected shots hold 0xFFFFFFFF). */
@@ -441,7 +444,7 @@ PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
 enum {
     PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
     PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* norm reduction / renormalisation of ptsbe_evolve_batch   */
-    PTSBE_TIMER_SAMPLE = 2,           /* ptsbe_sample_shots: cluster and global samplers          */
+    PTSBE_TIMER_SAMPLE = 2,           /* cluster and global samplers; support-CDF sampler          */
     PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
     PTSBE_TIMER_EVOLVE_PROGRAM = 4,   /* per-set program prepass of the deferred-frame kernel     */
     PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */

@@ -54,7 +54,7 @@ struct ptsbe_ctx {
     std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
     uint32_t next_circuit = 1, next_set = 1;
-    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault;
+    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support;
     std::vector<unsigned char> host_blob;
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
@@ -421,26 +421,38 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         for (uint32_t j = 0; j < J; ++j)
             if (P.fstages[j].sparse_final) { sparse_last = (int)j; small_last = (int)P.fstages[j].sbits; }
     const bool fuse = fused && sparse_last == (int)J - 1 && small_last > 0;
-    std::vector<uint32_t> nshots;
+    // Heavier states leave their support CDF for k_sample_support (drawn[a] = 2).
+    std::vector<uint32_t> nshots, nexport;
     std::vector<uint64_t> nout;
-    size_t o_nshots = 0, o_nout = 0;
+    size_t o_nshots = 0, o_nout = 0, o_nexport = 0;
     uint64_t fused_shots = 0;
+    std::vector<SupportItem> support_items;
+    uint32_t n_export = 0;
     if (drawn) drawn->assign(count, 0);
     if (fuse) {
         nshots.assign(count, 0);
         nout.assign(count, 0);
+        nexport.assign(count, 0xFFFFFFFFu);
         const uint64_t base = s.shot_off[first];
         for (uint32_t a = 0; a < count; ++a) {
             const uint64_t m = s.shots[first + a];
             nout[a] = s.shot_off[first + a] - base;
-            if (m > 0 && m <= ctx->light_shots && m <= UINT32_MAX) {
+            if (m == 0) continue;
+            if (m <= ctx->light_shots && m <= UINT32_MAX) {
                 nshots[a] = (uint32_t)m;
                 fused_shots += m;
                 if (drawn) (*drawn)[a] = 1;
+            } else {
+                nexport[a] = n_export;
+                for (uint64_t j0 = 0; j0 < m; j0 += kSupportChunk)
+                    support_items.push_back({n_export, first + a, j0, std::min(m, j0 + kSupportChunk), nout[a] + j0});
+                ++n_export;
+                if (drawn) (*drawn)[a] = 2;
             }
         }
         o_nshots = blob.add(nshots);
         o_nout = blob.add(nout);
+        if (n_export) o_nexport = blob.add(nexport);
     }
     unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
     ctx->h2d(dblob, ctx->host_blob.data(), ctx->host_blob.size());
@@ -461,8 +473,13 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         A.shot_alpha0 = first;
         A.node_shots = (const uint32_t*)(dblob + o_nshots);
         A.node_shot_out = (const uint64_t*)(dblob + o_nout);
-        A.fault = ctx->fault_word();
     }
+    const size_t slot_bytes = support_slot_bytes(small_last);
+    if (n_export) {
+        A.node_export = (const uint32_t*)(dblob + o_nexport);
+        A.support_out = (unsigned char*)ctx->ws(ctx->support, (size_t)n_export * slot_bytes);
+    }
+    if (fuse && (fused_shots || n_export)) A.fault = ctx->fault_word();
     const double sbytes = 8.0 * (double)(1ull << c.n);
     // stage j writes out(j); out(J-1) is the caller's buffer. The per-operator kernels without
     // reuse read and write the caller's buffer in place (a tile is read whole before it is
@@ -519,6 +536,18 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     A.scale_in = nullptr;
     if (ob > 0 && !early_norm && A.sparse_final_stage < 0)
         ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
+    if (!support_items.empty()) {
+        SupportItem* d_items = (SupportItem*)ctx->ws(ctx->items, support_items.size() * sizeof(SupportItem));
+        ctx->h2d(d_items, support_items.data(), support_items.size() * sizeof(SupportItem));
+        uint64_t heavy = 0;
+        for (const SupportItem& it : support_items) heavy += it.j1 - it.j0;
+        // algorithmic: each exported CDF read once per item + 4 B per shot
+        const double bytes = (double)slot_bytes * (double)support_items.size() + 4.0 * (double)heavy;
+        ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] {
+            launch_sample_support(A.support_out, slot_bytes, d_items, (uint32_t)support_items.size(), fused->seed,
+                                  fused->bits, ctx->stream);
+        });
+    }
 }
 
 // Draws the shots of states [first, first + count) (the work of ptsbe_sample_shots), except those
@@ -642,7 +671,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
-        ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault);
+        ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault); ctx->free_buf(ctx->support);
         ctx->free_timers();
     }
     delete ctx;

@@ -161,14 +161,16 @@ __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t 
 // stored state (same fixed-point probabilities of the same stored values, same Philox counters).
 // Support entries are placed in increasing logical order by their bits at the order mask's
 // positions (frame::sparse_order_mask); cdf and lidx (2^ncomp entries each) live in scratch.
+// A heavy state (exp != null) leaves the CDF in its export slot instead (SupportCdfHeader layout)
+// for k_sample_support, which spreads its shots over many CTAs.
 __device__ void scatter_and_sample(const EvolveArgs& a, const frame::Step& fin, const DevFrameStage& fs,
                                    const float2* tile, const float2* tabs, const uint32_t* delta, const uint32_t* hi,
-                                   float2* g, float scale, bool null, uint32_t node, uint32_t m, void* scratch,
-                                   double* red, uint32_t tid, uint32_t nthr) {
+                                   float2* g, float scale, bool null, uint32_t node, uint32_t m, unsigned char* exp,
+                                   void* scratch, double* red, uint32_t tid, uint32_t nthr) {
     using namespace frame;
     __shared__ uint32_t order, ok;
     const int n = a.n;
-    uint32_t* out = a.shot_bits + a.node_shot_out[node];
+    uint32_t* out = exp ? nullptr : a.shot_bits + a.node_shot_out[node];
     if (tid == 0) {
         order = sparse_order_mask(fin, fs, n, a.lb, hi);
         ok = (!null && fin.ncomp != 0xFF && (uint32_t)__popc(order) == fin.ncomp) ? 1u : 0u;
@@ -182,6 +184,13 @@ __device__ void scatter_and_sample(const EvolveArgs& a, const frame::Step& fin, 
         // The other case cannot occur for a plan's support (flagged above) and leaves the marker.
         if (!null) run_sparse_final(fin, fs, tile, tabs, delta, n, a.lb, hi, g, scale, 1, tid, nthr);
         const uint32_t mark = (null && !a.status) ? last : 0xFFFFFFFFu;
+        if (exp) {
+            if (tid == 0) {
+                SupportCdfHeader* h = reinterpret_cast<SupportCdfHeader*>(exp);
+                h->T = 0; h->n = 0; h->mark_all = 1; h->mark = mark; h->nq = (uint32_t)n;
+            }
+            return;
+        }
         for (uint32_t k = tid; k < m; k += nthr) out[k] = mark;
         return;
     }
@@ -223,6 +232,14 @@ __device__ void scatter_and_sample(const EvolveArgs& a, const frame::Step& fin, 
         for (uint32_t i = 0; i < K; ++i) { run += cdf[c0 + i]; cdf[c0 + i] = run; }
     __syncthreads();
     const fx T = cdf[N - 1];
+    if (exp) {
+        SupportCdfHeader* h = reinterpret_cast<SupportCdfHeader*>(exp);
+        fx* ec = reinterpret_cast<fx*>(exp + sizeof(SupportCdfHeader));
+        uint32_t* el = reinterpret_cast<uint32_t*>(ec + N);
+        for (uint32_t i = tid; i < N; i += nthr) { ec[i] = cdf[i]; el[i] = lidx[i]; }
+        if (tid == 0) { h->T = T; h->n = N; h->mark_all = 0; h->mark = 0; h->nq = (uint32_t)n; }
+        return;
+    }
     const uint32_t alpha = a.shot_alpha0 + node;
     for (uint32_t k = tid; k < m; k += nthr) {
         const Philox4 x = philox4x32_10(k, 0u, alpha, kDomShot, (uint32_t)a.shot_seed, (uint32_t)(a.shot_seed >> 32));
@@ -386,10 +403,12 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
         const bool null = !(part > 0.0) || w < 1e-6 * a.qalpha[node];
         const float scale = null ? 0.0f : (float)(1.0 / sqrt(part));
         const uint32_t m = a.shot_bits ? a.node_shots[node] : 0u;
-        if (m) {
+        const uint32_t e = a.node_export ? a.node_export[node] : 0xFFFFFFFFu;
+        unsigned char* exp = e != 0xFFFFFFFFu ? a.support_out + (size_t)e * support_slot_bytes(fs.sbits) : nullptr;
+        if (m || exp) {
             // the program's steps and factor pool are dead: their shared memory holds the CDF
             static_assert((sizeof(fx) + sizeof(uint32_t)) << kSmallSupportBits <= sizeof(S), "CDF scratch");
-            scatter_and_sample(a, fin, fs, tile, tabs, delta, hi, g, scale, null, node, m, S, red, tid, nthr);
+            scatter_and_sample(a, fin, fs, tile, tabs, delta, hi, g, scale, null, node, m, exp, S, red, tid, nthr);
         } else if (!null) {
             run_sparse_final(fin, fs, tile, tabs, delta, n, lb, hi, g, scale, 1, tid, nthr);
         }

@@ -345,7 +345,33 @@ struct EvolveArgs {
     uint64_t shot_seed;
     uint32_t shot_alpha0;
     uint32_t* fault;                 // set nonzero when a launch could not do its work (checked by the host)
+    // Heavy states of the small sparse final stage: node i with node_export[i] != ~0 leaves its
+    // support CDF in slot node_export[i] of support_out (SupportCdf layout) for k_sample_support.
+    const uint32_t* node_export;
+    unsigned char* support_out;
 };
+
+// A state's outcome CDF over its support, in increasing outcome order (2^-62 fixed point), as the
+// small sparse final stage leaves it for heavy states: header, then cdf[2^sbits], then lidx[2^sbits].
+struct SupportCdfHeader {
+    unsigned long long T;            // total (inclusive prefix of the last entry)
+    uint32_t n;                      // entries (a power of two)
+    uint32_t mark_all;               // 1: every shot is `mark` (null state, or a support not ordered)
+    uint32_t mark;
+    uint32_t nq;                     // qubits: outcome 2^nq - 1 when T = 0 (as the dense samplers)
+    uint32_t pad[2];
+};
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline size_t support_slot_bytes(int sbits) { return sizeof(SupportCdfHeader) + ((size_t)12 << sbits); }
+
+struct SupportItem {                 // a shot range of one exported state
+    uint32_t slot, alpha;
+    uint64_t j0, j1, out0;
+};
+void launch_sample_support(const unsigned char* slots, size_t slot_bytes, const SupportItem* d_items, uint32_t n_items,
+                           uint64_t seed, uint32_t* bits, cudaStream_t s);
 
 // kernel: 0 auto (= 3), 1 shared-memory sweeps, 2 register-blocked, 3 deferred frame
 void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32_t* d_nodes, uint32_t n_nodes,
@@ -452,6 +478,7 @@ int sample_light_max_qubits();
 // the cluster sampler. Both give the same shots (exact integer prefix sums), so the limit only
 // moves work between the kernels (PTSBE_OPT_LIGHT_SHOTS).
 constexpr uint64_t kLightShotLimit = 65536;
+constexpr uint64_t kSupportChunk = 1ull << 16;   // shots per k_sample_support work item
 void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s);
 
 }  // namespace ptsbe

@@ -362,6 +362,71 @@ __global__ void __launch_bounds__(kLightThreads, 2) k_sample_light(SampleArgs a,
     }
 }
 
+// ---- support CDF: heavy states exported by the small sparse final evolve stage -------------------
+// One CTA per shot range of an exported state. The CDF (at most 2^10 entries in increasing outcome
+// order) and its outcome indices go to shared memory with a 256-entry guide over them; each shot
+// is a Philox draw, the guide bucket of its top bits and a short binary search. Same shots as the
+// samplers that read the stored state: only support entries can be the smallest index whose
+// prefix exceeds the target, and their prefix values are the same.
+constexpr int kSupportThreads = 256;
+constexpr int kSupportGuideBits = 8;
+constexpr int kSupportGuide = 1 << kSupportGuideBits;
+
+__global__ void __launch_bounds__(kSupportThreads) k_sample_support(const unsigned char* __restrict__ slots, size_t slot_bytes,
+                                                                    const SupportItem* __restrict__ items, uint64_t seed,
+                                                                    uint32_t* bits) {
+    __shared__ fx cdf[1 << kSmallSupportBits];
+    __shared__ uint32_t lidx[1 << kSmallSupportBits];
+    __shared__ uint16_t guide[kSupportGuide + 1];
+    const SupportItem it = items[blockIdx.x];
+    const unsigned char* slot = slots + (size_t)it.slot * slot_bytes;
+    const SupportCdfHeader h = *reinterpret_cast<const SupportCdfHeader*>(slot);
+    uint32_t* out = bits + it.out0;
+    const uint64_t m = it.j1 - it.j0;
+    if (h.mark_all || h.n == 0 || h.n > (1u << kSmallSupportBits)) {
+        const uint32_t mark = h.mark_all ? h.mark : 0xFFFFFFFFu;
+        for (uint64_t k = threadIdx.x; k < m; k += blockDim.x) out[k] = mark;
+        return;
+    }
+    const uint32_t N = h.n;
+    const fx* gc = reinterpret_cast<const fx*>(slot + sizeof(SupportCdfHeader));
+    const uint32_t* gl = reinterpret_cast<const uint32_t*>(gc + N);
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) { cdf[i] = gc[i]; lidx[i] = gl[i]; }
+    __syncthreads();
+    const fx T = h.T;
+    // guide b: the first entry r with cut b < cdf[r], cut b = floor(b T / 256); a shot whose uniform
+    // has top bits b has floor(u T) between cuts b and b + 1, so its entry lies between guide b and b + 1
+    for (uint32_t b = threadIdx.x; b < (uint32_t)kSupportGuide; b += blockDim.x) {
+        const fx cut = __umul64hi((fx)b << (64 - kSupportGuideBits), T);
+        uint32_t lo = 0, hi = N - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cut < cdf[mid]) hi = mid; else lo = mid + 1;
+        }
+        guide[b] = (uint16_t)lo;
+    }
+    if (threadIdx.x == 0) guide[kSupportGuide] = (uint16_t)(N - 1);
+    __syncthreads();
+    const uint32_t last = (uint32_t)((1ull << h.nq) - 1ull);   // T = 0
+    for (uint64_t k = threadIdx.x; k < m; k += blockDim.x) {
+        const uint64_t j = it.j0 + k;
+        const Philox4 x = philox4x32_10((uint32_t)j, (uint32_t)(j >> 32), it.alpha, kDomShot, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const uint64_t m53 = u53_bits(x.x[0], x.x[1]);
+        const fx t = fx_target(m53, T);
+        uint32_t idx = last;
+        if (t < T) {
+            const uint32_t gb = (uint32_t)(m53 >> (53 - kSupportGuideBits));
+            uint32_t lo = guide[gb], hi = guide[gb + 1];     // smallest r with t < cdf[r]
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (t < cdf[mid]) hi = mid; else lo = mid + 1;
+            }
+            idx = lidx[lo];
+        }
+        out[k] = idx;
+    }
+}
+
 // ---- n > 17: global-memory CDF -----------------------------------------------------------------------
 
 // One CTA per block of 2^14 amplitudes: local inclusive prefix (unpadded) and block total.
@@ -568,6 +633,16 @@ void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_
     for (uint32_t b = 0; b < n_items; b += (1u << 30)) {
         const uint32_t cnt = (n_items - b) < (1u << 30) ? (n_items - b) : (1u << 30);
         k_sample_light<<<cnt, kLightThreads, smem, s>>>(a, d_items + b);
+        PTSBE_CUDA(cudaGetLastError());
+        count_launch();
+    }
+}
+
+void launch_sample_support(const unsigned char* slots, size_t slot_bytes, const SupportItem* d_items, uint32_t n_items,
+                           uint64_t seed, uint32_t* bits, cudaStream_t s) {
+    for (uint32_t b = 0; b < n_items; b += (1u << 30)) {
+        const uint32_t cnt = (n_items - b) < (1u << 30) ? (n_items - b) : (1u << 30);
+        k_sample_support<<<cnt, kSupportThreads, 0, s>>>(slots, slot_bytes, d_items + b, seed, bits);
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }

@@ -61,7 +61,8 @@ def _light_launches(P, info, n, seed, reuse=True):
 def test_syndrome_fused_matches_two_calls_and_oracle(oracle_mod):
     """17-qubit syndrome circuit, the 2,000 most likely sets, 2x10^7 shots: every light state's
     shots come from the evolve launch (no light-sampler launch), the error-free state's from the
-    cluster sampler; everything equals the two-call path, and sampled sets match the oracle."""
+    support sampler over the CDF the evolve launch exported; everything equals the two-call path,
+    and sampled sets match the oracle."""
     P = gpu_ctx()
     circ = syndrome17(rounds=3)
     n = circ.n_qubits
@@ -114,12 +115,14 @@ def _null_circuit():
     return b.build()
 
 
-@pytest.mark.parametrize("status", [True, False])
-def test_null_states_fused(status):
+@pytest.mark.parametrize("status,limit", [(True, 65536), (False, 65536), (True, 0), (False, 0)])
+def test_null_states_fused(status, limit):
     """Null branches: the all-ones marker with a status buffer, the last index without one (what
-    the samplers draw from a zeroed state), in both paths."""
+    the samplers draw from a zeroed state), in both paths; with limit 0 every state leaves its
+    support CDF (or its marker) for the support sampler."""
     torch = torch_cuda()
     P = gpu_ctx()
+    P.set_light_shots(limit)
     circ = _null_circuit()
     n = circ.n_qubits
     cid = P.register(circ)
@@ -130,7 +133,8 @@ def test_null_states_fused(status):
     fused = _run(P, info, n, 3, True, status=status)
     _same(sep, fused)
     if status:
-        assert _light_launches(P, info, n, 3)[1:] == (0, 0)   # every state sampled in the evolve launch
+        light, support = _light_launches(P, info, n, 3)[1:]
+        assert light == 0 and (support == 0) == (limit > 0)   # limit 0: every state exported
     b_h = fused[3].cpu().numpy().view(np.uint32)
     mark = 0xFFFFFFFF if status else (1 << n) - 1
     null = [i for i in range(info.count) if (sites - 1, 1) in [tuple(e) for e in info.entries(i)]]
