@@ -134,15 +134,24 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current source."""
+def traffic_for(kernel: str, bytes_per_launch: float = 0.0, units: int = 0):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current source.
+    A per-state record (a smaller capture of the same launch) is scaled to this launch: reads by the
+    state count; writes by the further states' bytes and the difference between this launch's shot
+    bytes (its algorithmic bytes beyond the states) and the capture's."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(kernel)
-        if e and e.get("source_sha") == source_sha(e["sources"]):
-            return float(e["dram_bytes_per_launch"])
+        if not e or e.get("source_sha") != source_sha(e["sources"]):
+            return None
+        c = e.get("capture")
+        if e.get("model") == "per_state" and c and units:
+            shot_bytes = bytes_per_launch - units * c["state_bytes"]
+            return float(c["dram_bytes_read"] * units / c["states"] + c["dram_bytes_write"]
+                         + (units - c["states"]) * c["state_bytes"] + (shot_bytes - c["shot_bytes"]))
+        return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -518,7 +527,7 @@ def main():
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": traffic_for(name), "bytes_per_launch": d["bytes"] / d["launches"],
+                "traffic": traffic_for(name, d["bytes"] / d["launches"], K), "bytes_per_launch": d["bytes"] / d["launches"],
                 "ms_per_launch": d["ms"] / d["launches"]}
 
     roof, roof_hbm = None, None

@@ -279,7 +279,13 @@ PTSBE_HD uint64_t drop_pending(Builder& B, uint64_t rm, uint64_t keep) {
     for (uint32_t j = 0; j < B.npend; ++j) {
         if ((rm >> j) & 1u) continue;
         if ((keep >> j) & 1u) out |= 1ull << w;
-        if (w != j) B.pend[w] = B.pend[j];
+        if (w != j) {
+            // a pending factor only carries its rows and values (the other fields stay zero)
+            Factor& d = B.pend[w];
+            const Factor& f = B.pend[j];
+            d.r1 = f.r1; d.r2 = f.r2;
+            for (int x = 0; x < 4; ++x) d.f[x] = f.f[x];
+        }
         ++w;
     }
     B.npend = w;
@@ -350,12 +356,22 @@ PTSBE_HD void push_factor(Builder& B, const DevStage& stg, Step* S, Factor* pool
     if (r1 == 0) { g[1] = g[2] = g[3] = g[0]; }
     if (is_one(g[0]) && is_one(g[1]) && is_one(g[2]) && is_one(g[3])) return;
     ++B.npush;
-    for (uint32_t j = 0; j < B.npend; ++j) {
-        Factor& f = B.pend[j];
-        if (f.r1 == r1 && f.r2 == r2) {
-            for (int x = 0; x < 4; ++x) f.f[x] = fmul(f.f[x], g[x]);
-            return;
-        }
+    // at most one pending factor has these rows; four compared per iteration (independent loads)
+    uint32_t hit = B.npend;
+    uint32_t j = 0;
+    for (; j + 4 <= B.npend && hit == B.npend; j += 4) {
+        const bool h0 = B.pend[j].r1 == r1 && B.pend[j].r2 == r2;
+        const bool h1 = B.pend[j + 1].r1 == r1 && B.pend[j + 1].r2 == r2;
+        const bool h2 = B.pend[j + 2].r1 == r1 && B.pend[j + 2].r2 == r2;
+        const bool h3 = B.pend[j + 3].r1 == r1 && B.pend[j + 3].r2 == r2;
+        if (h0 | h1 | h2 | h3) hit = j + (h0 ? 0u : h1 ? 1u : h2 ? 2u : 3u);
+    }
+    for (; j < B.npend && hit == B.npend; ++j)
+        if (B.pend[j].r1 == r1 && B.pend[j].r2 == r2) hit = j;
+    if (hit < B.npend) {
+        Factor& f = B.pend[hit];
+        for (int x = 0; x < 4; ++x) f.f[x] = fmul(f.f[x], g[x]);
+        return;
     }
     if (B.npend == kMaxPending) {
         Step& st = take_tables(B, stg, S, pool, all_pending(B), true);
