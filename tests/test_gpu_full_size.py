@@ -58,3 +58,47 @@ def test_bench_workload_full_size(oracle_mod):
         m = min(int(info.shots[i]), 20000)
         got = bits[off: off + m].cpu().numpy().view(np.uint32)
         check_shots(got, psi_gpu, seed, i, 0, oracle_mod, n)
+
+
+@pytest.mark.parametrize("limit", [65536, 512])
+def test_bench_workload_one_call(oracle_mod, limit):
+    """The call bench.py times (ptsbe_evolve_sample) at full size, at the default light-shot limit
+    and at 512 (the autotuner's choice on some boxes): states, weights, flags and all 10^8 shots
+    bit-identical to ptsbe_evolve_batch + ptsbe_sample_shots; the error-free state's shots (support
+    sampler over its exported CDF) and sampled light states' shots against the oracle."""
+    torch = torch_cuda()
+    P = gpu_ctx()
+    P.set_light_shots(limit)
+    cfg = config(1)
+    circ = cfg["circuit"]
+    n = circ.n_qubits
+    K, M = cfg["k"], cfg["total_shots"]
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
+    seed = cfg["seed"]
+    outs = []
+    for fused in (False, True):
+        states = torch.empty((K, 1 << n), dtype=torch.complex64, device="cuda")
+        w = torch.empty(K, dtype=torch.float64, device="cuda")
+        s = torch.empty(K, dtype=torch.uint8, device="cuda")
+        bits = torch.full((M,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+        if fused:
+            P.evolve_sample(info, 0, K, states, w, s, seed, bits, prefix_reuse=True)
+        else:
+            P.evolve(info, 0, K, states, w, s, prefix_reuse=True)
+            P.sample(info, 0, K, states, s, seed, bits)
+        torch.cuda.synchronize()
+        P.synchronize()
+        outs.append((states, w, s, bits))
+    (s0, w0, f0, b0), (s1, w1, f1, b1) = outs
+    assert torch.equal(torch.view_as_real(s0), torch.view_as_real(s1))
+    assert torch.equal(w0, w1) and torch.equal(f0, f1) and torch.equal(b0, b1)
+    del s0, w0, f0, b0
+    lens = [len(info.entries(i)) for i in range(K)]
+    for i in [0, 1, lens.index(2), K - 1]:
+        if int(info.shots[i]) == 0:
+            continue
+        psi = s1[i].cpu().numpy()
+        off = int(info.shot_offsets[i])
+        m = min(int(info.shots[i]), 20000)
+        check_shots(b1[off: off + m].cpu().numpy().view(np.uint32), psi, seed, i, 0, oracle_mod, n)
