@@ -327,6 +327,10 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
         c.frame_planned = true;
     }
+    if (!frame && !c.op_planned) {
+        c.plan = make_plan(c, kTileMax, false);
+        c.op_planned = true;
+    }
     if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
     const Plan& P = frame ? c.plan_frame : c.plan;
     const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
@@ -717,7 +721,7 @@ int ptsbe_register_circuit(ptsbe_ctx* ctx, uint32_t n_qubits, const ptsbe_op* op
         for (uint32_t j = 0; j < n_channels; ++j) build_channel(channels[j], c->ch[j]);
         register_ops(*c, ops, n_ops, custom_gates, n_custom);
         build_device_ops(*c);
-        c->plan = make_plan(*c, kTileMax, false);   // device tables uploaded by the first call that needs them
+        // plans and device tables are built by the first call that needs them
         const uint32_t id = ctx->next_circuit++;
         ctx->circuits[id] = std::move(c);
         *circuit_id = id;

@@ -262,6 +262,7 @@ struct Circuit {
     BwPlan bw;                       // adjoint backward plan (built on the first backward call)
     bool pershot_planned = false;
     bool frame_planned = false;
+    bool op_planned = false;         // per-operator plan (sweep and register-blocked kernels) built
     DeviceCircuit dev;
     DeviceCircuit dev_pershot;
     DeviceCircuit dev_frame;

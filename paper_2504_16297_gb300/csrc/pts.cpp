@@ -306,10 +306,13 @@ void apportion_counts(const std::vector<uint64_t>& c, uint64_t M, std::vector<ui
             used += out[i];
         }
     }
-    std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
-        return a.first != b.first ? a.first > b.first : a.second < b.second;
-    });
-    for (uint64_t j = 0; j < M - used; ++j) out[rem[j].second] += 1;
+    // the M - used largest remainders (ties: lower index first) get one more shot; only the set
+    // matters, and under this strict total order selection gives the same set as a full sort
+    const uint64_t R = M - used;
+    if (R == 0) return;
+    auto first_r = [](const auto& a, const auto& b) { return a.first != b.first ? a.first > b.first : a.second < b.second; };
+    if (R < n) std::nth_element(rem.begin(), rem.begin() + (ptrdiff_t)(R - 1), rem.end(), first_r);
+    for (uint64_t j = 0; j < R; ++j) out[rem[j].second] += 1;
 }
 
 void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uint64_t>& out) {
@@ -328,10 +331,11 @@ void apportion_weights(const std::vector<double>& w, uint64_t M, std::vector<uin
         used += out[i];
     }
     if (used <= M) {
-        std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
-            return a.first != b.first ? a.first > b.first : a.second < b.second;
-        });
-        for (uint64_t j = 0; j < M - used && j < n; ++j) out[rem[j].second] += 1;
+        // as in apportion_counts: selection of the largest remainders, same set as a full sort
+        const uint64_t R = std::min<uint64_t>(M - used, n);
+        auto first_r = [](const auto& a, const auto& b) { return a.first != b.first ? a.first > b.first : a.second < b.second; };
+        if (R > 0 && R < n) std::nth_element(rem.begin(), rem.begin() + (ptrdiff_t)(R - 1), rem.end(), first_r);
+        for (uint64_t j = 0; j < R; ++j) out[rem[j].second] += 1;
     } else {
         std::sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) {
             return a.first != b.first ? a.first < b.first : a.second > b.second;

@@ -40,6 +40,15 @@ def _ptr(t) -> int | None:
     return int(t.data_ptr())
 
 
+_OP_DTYPE = np.dtype({
+    "names": ["kind", "id", "n_targets", "targets", "params"],
+    "formats": [np.uint32, np.uint32, np.uint32, (np.uint32, 2), (np.float64, 3)],
+    "offsets": [capi.ptsbe_op.kind.offset, capi.ptsbe_op.id.offset, capi.ptsbe_op.n_targets.offset,
+                capi.ptsbe_op.targets.offset, capi.ptsbe_op.params.offset],
+    "itemsize": C.sizeof(capi.ptsbe_op),
+})
+
+
 class Ptsbe:
     """One libptsbe context. device=-1 gives a host-only context (registration and PTS)."""
 
@@ -71,14 +80,15 @@ class Ptsbe:
     # -- registration ----------------------------------------------------------------------------
     def register(self, circ) -> int:
         n_ops = circ.n_ops
-        ops = (capi.ptsbe_op * max(n_ops, 1))()
-        oi = np.asarray(circ.op_ints)
-        op = np.asarray(circ.op_params)
-        for i in range(n_ops):
-            o = ops[i]
-            o.kind, o.id, o.n_targets = int(oi[i, 0]), int(oi[i, 1]), int(oi[i, 2])
-            o.targets[0], o.targets[1] = int(oi[i, 3]), int(oi[i, 4])
-            o.params[0], o.params[1], o.params[2] = float(op[i, 0]), float(op[i, 1]), float(op[i, 2])
+        # ptsbe_op records filled column by column through a numpy view of the same layout
+        arr = np.zeros(max(n_ops, 1), dtype=_OP_DTYPE)
+        if n_ops:
+            oi = np.asarray(circ.op_ints)
+            op = np.asarray(circ.op_params, np.float64)
+            arr["kind"][:n_ops], arr["id"][:n_ops], arr["n_targets"][:n_ops] = oi[:, 0], oi[:, 1], oi[:, 2]
+            arr["targets"][:n_ops] = oi[:, 3:5]
+            arr["params"][:n_ops] = op[:, 0:3]
+        ops = C.cast(arr.ctypes.data, C.POINTER(capi.ptsbe_op))
         n_ch = len(circ.ch_params)
         chans = (capi.ptsbe_channel * max(n_ch, 1))()
         keep = []
@@ -94,8 +104,10 @@ class Ptsbe:
                 c.kraus = arr.ctypes.data_as(C.POINTER(C.c_double))
         cg = np.ascontiguousarray(np.asarray(circ.custom_gates, np.complex128)).view(np.float64).reshape(-1)
         cg_ptr = cg.ctypes.data if cg.size else None
-        return capi.ptsbe_register_circuit(self.ctx, circ.n_qubits, ops, n_ops, chans, n_ch, cg_ptr,
-                                           int(circ.custom_gates.shape[0]))
+        cid = capi.ptsbe_register_circuit(self.ctx, circ.n_qubits, ops, n_ops, chans, n_ch, cg_ptr,
+                                          int(circ.custom_gates.shape[0]))
+        del arr
+        return cid
 
     def release_circuit(self, cid):
         capi.ptsbe_release_circuit(self.ctx, cid)
