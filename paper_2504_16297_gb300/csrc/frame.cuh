@@ -103,6 +103,7 @@ struct Builder {
     uint16_t sech[kTileMax];                     // echelon basis of the support (tile-local)
     uint8_t spiv[kTileMax], tsb, pad3;          // tsb: log2 of the table stride of emitted steps
     uint16_t ech[kTabBits], comb[kTabBits];      // echelon rows of the table being filled
+    uint32_t freal;                              // the factors folded by the last fold_factors are real
     uint8_t piv[kTabBits], pad2[2];
     Factor pend[kMaxPending];
 };
@@ -211,7 +212,10 @@ PTSBE_HD uint32_t reduce_or_add(uint32_t r, Table& T, uint16_t* ech, uint16_t* c
 // Orders the index bits of a finished table by the lowest set bit of their basis rows. The lanes
 // of a warp differ in the low tile-local bits, so their lookups then differ in the low index bits
 // and spread over the shared-memory banks.
-PTSBE_HD void order_table(Table& T, Factor* pool) {
+// The coordinates of pool factors [T.fb, T.fe) in the unordered basis are read from the pending
+// factors they were copied from (pend entries of `took`, in order), so the pool entries, possibly
+// in global memory, are only written.
+PTSBE_HD void order_table(Table& T, Factor* pool, const Factor* pend, uint64_t took) {
     uint8_t ord[kTabBits], at[kTabBits];
     for (int i = 0; i < T.d; ++i) {
         int j = i;
@@ -223,9 +227,12 @@ PTSBE_HD void order_table(Table& T, Factor* pool) {
     for (int i = 0; i < T.d; ++i) T.basis[i] = nb[i];
     for (uint32_t j = T.fb; j < T.fe; ++j) {
         uint32_t c1 = 0, c2 = 0;
+        const int k = (uint32_t)took ? low_bit((uint32_t)took) : 32 + low_bit((uint32_t)(took >> 32));
+        took &= took - 1ull;
+        const uint32_t u1 = pend[k].c1, u2 = pend[k].c2;
         for (int i = 0; i < T.d; ++i) {
-            if ((pool[j].c1 >> i) & 1u) c1 |= 1u << at[i];
-            if ((pool[j].c2 >> i) & 1u) c2 |= 1u << at[i];
+            if ((u1 >> i) & 1u) c1 |= 1u << at[i];
+            if ((u2 >> i) & 1u) c2 |= 1u << at[i];
         }
         pool[j].c1 = (uint16_t)c1;
         pool[j].c2 = (uint16_t)c2;
@@ -243,6 +250,7 @@ PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor*
         int d = 0;
         T.fb = (uint16_t)B.npool;
         uint64_t took = 0;
+        uint8_t real = 1;
         for (uint32_t j = 0; j < B.npend; ++j) {
             if (!((left >> j) & 1u)) continue;
             const Factor& f = B.pend[j];
@@ -251,6 +259,9 @@ PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor*
             uint32_t c2 = 0;
             if (d <= kTabBits) c2 = reduce_or_add(tile_part(stg, f.r2) & B.tmask, T, B.ech, B.comb, B.piv, d);
             if (d > kTabBits) { d = d0; continue; }
+            B.pend[j].c1 = (uint16_t)c1;     // for order_table (a pending factor's c1, c2 are scratch)
+            B.pend[j].c2 = (uint16_t)c2;
+            for (int x = 0; x < 4; ++x) if (f.f[x].y != 0.0f) real = 0;
             Factor& g = pool[B.npool++];
             g = f;
             g.c1 = (uint16_t)c1;
@@ -261,10 +272,8 @@ PTSBE_HD uint64_t fill_tables(Builder& B, const DevStage& stg, Step& st, Factor*
         }
         T.fe = (uint16_t)B.npool;
         T.d = (uint8_t)d;
-        T.real = 1;
-        for (uint32_t j = T.fb; j < T.fe; ++j)
-            for (int x = 0; x < 4; ++x) if (pool[j].f[x].y != 0.0f) T.real = 0;
-        order_table(T, pool);
+        T.real = real;
+        order_table(T, pool, B.pend, took);
         ++st.ntab;
         used |= took;
         left &= ~took;
@@ -280,7 +289,8 @@ PTSBE_HD uint64_t drop_pending(Builder& B, uint64_t rm, uint64_t keep) {
         if ((rm >> j) & 1u) continue;
         if ((keep >> j) & 1u) out |= 1ull << w;
         if (w != j) {
-            // a pending factor only carries its rows and values (the other fields stay zero)
+            // a pending factor only carries its rows and values (r1o, r2o and pad stay zero; c1, c2
+            // are scratch of fill_tables, overwritten in every pool copy)
             Factor& d = B.pend[w];
             const Factor& f = B.pend[j];
             d.r1 = f.r1; d.r2 = f.r2;
@@ -434,8 +444,10 @@ PTSBE_HD void set_pivots(Step& st) {
 PTSBE_HD uint64_t fold_factors(Builder& B, const DevStage& stg, Factor* pool, uint64_t var, uint16_t& fb, uint16_t& fe) {
     fb = (uint16_t)B.npool;
     uint64_t folded = 0;
+    B.freal = 1;
     for (uint32_t j = 0; j < B.npend; ++j) {
         if (!((var >> j) & 1u) || B.pend[j].r2 != 0) continue;
+        if (B.pend[j].f[0].y != 0.f || B.pend[j].f[2].y != 0.f) B.freal = 0;
         Factor& g = pool[B.npool++];
         g = B.pend[j];
         g.c1 = (uint16_t)tile_part(stg, g.r1);
@@ -448,10 +460,9 @@ PTSBE_HD uint64_t fold_factors(Builder& B, const DevStage& stg, Factor* pool, ui
     return folded;
 }
 
-PTSBE_HD bool real_mix(const float2* m, const Factor* pool, uint32_t fb, uint32_t fe) {
-    bool r = m[0].y == 0.f && m[1].y == 0.f && m[2].y == 0.f && m[3].y == 0.f;
-    for (uint32_t j = fb; r && j < fe; ++j) r = pool[j].f[0].y == 0.f && pool[j].f[2].y == 0.f;
-    return r;
+// The 2x2 m and the factors folded into it (freal, from the builder) are real.
+PTSBE_HD bool real_mix(const float2* m, uint32_t freal) {
+    return m[0].y == 0.f && m[1].y == 0.f && m[2].y == 0.f && m[3].y == 0.f && freal;
 }
 
 PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, int q, const float2* m) {
@@ -480,7 +491,7 @@ PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
             const int i = pr.ndir++;
             pr.fold_b[i] = fb;
             pr.fold_e[i] = fe;
-            if (real_mix(m, pool, fb, fe)) pr.mreal |= (uint8_t)(1u << i);
+            if (real_mix(m, B.freal)) pr.mreal |= (uint8_t)(1u << i);
             pr.dir[i] = (uint16_t)ut;
             pr.rin[i] = (uint16_t)tile_part(stg, B.row[q]);
             pr.rout[i] = outer_part(stg, B.row[q]);
@@ -494,7 +505,7 @@ PTSBE_HD void emit_mix1(Builder& B, const DevStage& stg, Step* S, Factor* pool, 
     }
     st.kind = ST_MIX1;
     st.ndir = 1;
-    st.mreal = real_mix(m, pool, fb, fe) ? 1 : 0;
+    st.mreal = real_mix(m, B.freal) ? 1 : 0;
     st.fold_b[0] = fb;
     st.fold_e[0] = fe;
     st.dir[0] = (uint16_t)ut;

@@ -81,14 +81,14 @@ class Ptsbe:
     def register(self, circ) -> int:
         n_ops = circ.n_ops
         # ptsbe_op records filled column by column through a numpy view of the same layout
-        arr = np.zeros(max(n_ops, 1), dtype=_OP_DTYPE)
+        op_rec = np.zeros(max(n_ops, 1), dtype=_OP_DTYPE)   # kept alive until the call returns
         if n_ops:
             oi = np.asarray(circ.op_ints)
             op = np.asarray(circ.op_params, np.float64)
-            arr["kind"][:n_ops], arr["id"][:n_ops], arr["n_targets"][:n_ops] = oi[:, 0], oi[:, 1], oi[:, 2]
-            arr["targets"][:n_ops] = oi[:, 3:5]
-            arr["params"][:n_ops] = op[:, 0:3]
-        ops = C.cast(arr.ctypes.data, C.POINTER(capi.ptsbe_op))
+            op_rec["kind"][:n_ops], op_rec["id"][:n_ops], op_rec["n_targets"][:n_ops] = oi[:, 0], oi[:, 1], oi[:, 2]
+            op_rec["targets"][:n_ops] = oi[:, 3:5]
+            op_rec["params"][:n_ops] = op[:, 0:3]
+        ops = C.cast(op_rec.ctypes.data, C.POINTER(capi.ptsbe_op))
         n_ch = len(circ.ch_params)
         chans = (capi.ptsbe_channel * max(n_ch, 1))()
         keep = []
@@ -106,7 +106,7 @@ class Ptsbe:
         cg_ptr = cg.ctypes.data if cg.size else None
         cid = capi.ptsbe_register_circuit(self.ctx, circ.n_qubits, ops, n_ops, chans, n_ch, cg_ptr,
                                           int(circ.custom_gates.shape[0]))
-        del arr
+        del op_rec, keep
         return cid
 
     def release_circuit(self, cid):

@@ -210,3 +210,24 @@ def test_options_validate_values(host):
         host.set_light_shots(-1)
     with pytest.raises(capi.PtsbeError):
         capi.ptsbe_set_option(host.ctx, 99, 0)
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_register_every_op_and_channel_kind(host, oracle_mod, n):
+    """Every gate kind, custom gates and custom Kraus channels through the binding's op and channel
+    marshalling: the registered circuit has the op and site counts it was given, and proportional
+    PTS on it is bit-identical to the oracle's (the channels' probabilities come from the
+    marshalled Kraus operators)."""
+    import test_gpu_parity
+    circ = test_gpu_parity._kitchen_sink(n, n)
+    cid = host.register(circ)
+    nq, n_sites, n_gates = host.circuit_info(cid)
+    assert (nq, n_sites, n_gates) == (n, circ.n_sites, circ.n_ops - circ.n_sites)
+    info = host.sample_kraus(cid, "proportional", seed=17, nsamples=400, total_shots=4000)
+    ref = oracle_mod.Oracle(circ).pts_proportional(400, 17, total_shots=4000)
+    assert info.count == ref.count
+    for i in range(info.count):
+        assert info.entries(i) == ref.entries(i), i
+    np.testing.assert_array_equal(np.asarray(info.shots, np.uint64), np.asarray(ref.shots, np.uint64))
+    host.release_set(info)
+    host.release_circuit(cid)
