@@ -199,6 +199,56 @@ int fh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
 // Sets in CSR (off, site, k) with nominal probabilities q; the same schedule as ptsbe_evolve_batch
 // (prefix reuse, alternating buffers, early norm when the last stage has no ops).
 // Support bits of the plan's sparse final stage (0: none, or no support bound).
+// Randomised check of the support order used by fused sampling: random supports (coset
+// generators comp[j] of a 14-bit tile) under random invertible index maps (rowe) and offsets;
+// the order mask must rank the 2^ncomp members 0 .. N-1 increasingly when the generators are
+// independent, and show fewer than ncomp bits exactly when they are dependent.
+int fh_order_selftest(uint64_t seed, int trials) {
+    uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto rnd = [&]() { x ^= x << 13; x ^= x >> 7; x ^= x << 17; return x; };
+    int bad = 0;
+    static Step st;
+    static DevFrameStage fs;
+    const uint32_t hi0[1] = {0};
+    for (int t = 0; t < trials; ++t) {
+        const int n = 4 + (int)(rnd() % 17);                 // 4 .. 20 qubits
+        const int tbits = n < 14 ? n : 14;
+        std::memset(&fs, 0, sizeof(fs));
+        std::memset(&st, 0, sizeof(st));
+        for (int q = 0; q < n; ++q) fs.rowe[q] = 1u << q;
+        for (int k = 0; k < 4 * n; ++k) {                     // random invertible rows: row additions
+            const int a = (int)(rnd() % n), b = (int)(rnd() % n);
+            if (a != b) fs.rowe[a] ^= fs.rowe[b];
+        }
+        st.ncomp = (uint8_t)(rnd() % 11);
+        for (int j = 0; j < st.ncomp; ++j) {
+            uint32_t v = 0;
+            while (!v) v = (uint32_t)(rnd() & ((1u << tbits) - 1u));
+            st.comp[j] = (uint16_t)v;
+        }
+        st.lb0 = (uint32_t)(rnd() & ((1u << n) - 1u));
+        const uint32_t H = sparse_order_mask(st, fs, n, 14, hi0);
+        const uint32_t N = 1u << st.ncomp;
+        std::vector<int64_t> at(N, -1);
+        std::vector<uint32_t> seen;
+        bool distinct = true;
+        for (uint32_t i = 0; i < N; ++i) seen.push_back(sparse_logical(st, fs, n, 14, hi0, enum_base(st, i, nullptr, 0)));
+        std::vector<uint32_t> sorted = seen;
+        std::sort(sorted.begin(), sorted.end());
+        for (uint32_t i = 1; i < N; ++i) if (sorted[i] == sorted[i - 1]) distinct = false;
+        if ((__builtin_popcount(H) == st.ncomp) != distinct) { ++bad; continue; }
+        if (!distinct) continue;
+        for (uint32_t i = 0; i < N; ++i) {
+            const uint32_t r = extract_bits(seen[i], H);
+            if (r >= N || at[r] != -1) { ++bad; break; }
+            at[r] = seen[i];
+        }
+        for (uint32_t r = 0; r < N; ++r)
+            if (at[r] != (int64_t)sorted[r]) { ++bad; break; }
+    }
+    return bad;
+}
+
 void fh_order_stats(int* checks, int* violations) {
     *checks = g_order_checks;
     *violations = g_order_violations;

@@ -189,3 +189,13 @@ def test_null_branch_and_single_qubit(fh, oracle_mod):
     circ = b.build()
     sets = oracle_mod.Oracle(circ).pts_targeted([[], [(0, 1)], [(1, 1)]], np.array([50, 60, 70], np.uint64))
     _compare(fh, oracle_mod, circ, sets, 8, 1)
+
+
+def test_support_order_mask_random(fh):
+    """The rank rule of fused sampling on 3,000 random supports: up to 10 coset generators of a
+    14-bit tile under random invertible logical maps and offsets, 4 to 20 qubits. Independent
+    generators: the bits of each member's logical index at the order mask rank the 2^k members
+    0 .. 2^k - 1 in increasing order (brute force: sorted list). Dependent ones: the mask has fewer
+    than k bits, which the kernel treats as a fault."""
+    fh.fh_order_selftest.restype = C.c_int
+    assert fh.fh_order_selftest(C.c_uint64(12345), C.c_int(3000)) == 0
