@@ -396,7 +396,10 @@ enum {
     PTSBE_OPT_EVOLVE_KERNEL = 0,
     /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
      * prefixes (one chunk re-read per shot); heavier ones by a thread-block cluster holding the
-     * whole CDF. Both give the same shots; only the speed differs. Default 65,536 (measured).  */
+     * whole CDF. In ptsbe_evolve_sample with a sparse final stage, states with at most this many
+     * shots are sampled inside the evolve launch and heavier ones from their exported support
+     * CDF. Every choice gives the same shots; only the speed differs. Default 65,536 (measured
+     * for ptsbe_sample_shots; the autotuner times 512 .. 2^20 on the one-call path). */
     PTSBE_OPT_LIGHT_SHOTS = 1,
     /* Kraus sets whose frame programs one warp of the program prepass builds (one thread per set):
      * 4, 8 or 16 (0 = default, 8: measured). The builders branch on each set's entries, so fewer
