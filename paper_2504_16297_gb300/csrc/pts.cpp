@@ -186,21 +186,26 @@ class BestFirst {
         push({1.0, 0});
     }
 
-    // Pops the next set in order; false when exhausted.
-    bool next(double& key, List& canon) {
+    // Pops the next set in order (its node: key and site-sorted packed entries stay readable);
+    // false when exhausted.
+    bool next_node(uint32_t& node) {
         if (heap_.empty()) return false;
         const HeapItem top = heap_.front();
         std::pop_heap(heap_.begin(), heap_.end(), after_);
         heap_.pop_back();
-        const Node nd = nodes_[top.node];
-        key = nd.key;
-        canon.clear();
-        for (uint32_t i = 0; i < nd.len; ++i) {
-            const uint64_t e = ent_[nd.off + i];
-            canon.push_back({(uint32_t)(e >> 8), (uint8_t)(e & 0xFF)});
-        }
+        node = top.node;
         expand(top.node);
         return true;
+    }
+    double key(uint32_t node) const { return nodes_[node].key; }
+    uint32_t len(uint32_t node) const { return nodes_[node].len; }
+    const uint64_t* entries(uint32_t node) const { return ent_.data() + nodes_[node].off; }
+    // canonical order of two popped sets (entries packed site << 8 | k compare as (site, k))
+    bool canon_before(uint32_t a, uint32_t b) const {
+        const Node& na = nodes_[a];
+        const Node& nb = nodes_[b];
+        return std::lexicographical_compare(ent_.begin() + na.off, ent_.begin() + na.off + na.len,
+                                            ent_.begin() + nb.off, ent_.begin() + nb.off + nb.len);
     }
 
   private:
@@ -272,11 +277,14 @@ class BestFirst {
 
 double set_key(const Circuit& c, const uint32_t* sites, const uint8_t* ks, uint32_t len) {
     if (len == 0) return 1.0;
-    std::vector<double> r(len);
+    double buf[16];
+    std::vector<double> big;
+    double* r = buf;
+    if (len > 16) { big.resize(len); r = big.data(); }
     for (uint32_t i = 0; i < len; ++i) r[i] = ratio(c, sites[i], ks[i]);
-    std::sort(r.begin(), r.end(), [](double a, double b) { return a > b; });
+    std::sort(r, r + len, [](double a, double b) { return a > b; });
     double key = 1.0;
-    for (double x : r) key *= x;
+    for (uint32_t i = 0; i < len; ++i) key *= r[i];
     return key;
 }
 
@@ -435,20 +443,42 @@ void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& o
             fail(PTSBE_ERR_UNSUPPORTED, "TOPK/BAND need q_{s,0} to be the strict maximum at every site");
         if (p.mode == PTSBE_PTS_BAND && !(p.p_min > 0) )
             fail(PTSBE_ERR_INVALID, "BAND needs p_min > 0");
+        if (alloc == PTSBE_SHOTS_GIVEN) fail(PTSBE_ERR_INVALID, "SHOTS_GIVEN is for TARGETED");
+        // The search yields distinct sets: they go to the output in canonical order straight from
+        // the search's entry arena (no per-set lists, no merging of duplicates).
         BestFirst bf(c);
-        double key;
-        List canon;
+        std::vector<uint32_t> ids;
+        uint32_t node;
         if (p.mode == PTSBE_PTS_TOPK) {
-            for (uint64_t i = 0; i < p.k && bf.next(key, canon); ++i) sets.push_back({canon, 1});
+            ids.reserve((size_t)std::min<uint64_t>(p.k, 1ull << 24));
+            for (uint64_t i = 0; i < p.k && bf.next_node(node); ++i) ids.push_back(node);
         } else {
-            while (bf.next(key, canon)) {
-                const double q = c.Q0 * key;
+            while (bf.next_node(node)) {
+                const double q = c.Q0 * bf.key(node);
                 if (q < p.p_min) break;
-                if (q <= p.p_max) sets.push_back({canon, 1});
-                if (sets.size() > (1ull << 31)) fail(PTSBE_ERR_UNSUPPORTED, "band selects more than 2^31 sets");
+                if (q <= p.p_max) ids.push_back(node);
+                if (ids.size() > (1ull << 31)) fail(PTSBE_ERR_UNSUPPORTED, "band selects more than 2^31 sets");
             }
         }
-        break;
+        std::sort(ids.begin(), ids.end(), [&](uint32_t a, uint32_t b) { return bf.canon_before(a, b); });
+        out.off.assign(1, 0);
+        out.site.clear(); out.k.clear(); out.mult.clear(); out.q.clear(); out.key.clear(); out.shots.clear();
+        for (uint32_t id : ids) {
+            const uint64_t* e = bf.entries(id);
+            for (uint32_t i = 0; i < bf.len(id); ++i) { out.site.push_back((uint32_t)(e[i] >> 8)); out.k.push_back((uint8_t)(e[i] & 0xFF)); }
+            out.off.push_back((uint32_t)out.site.size());
+        }
+        const uint32_t n = (uint32_t)ids.size();
+        out.mult.assign(n, 1);
+        out.key.resize(n); out.q.resize(n);
+        for (uint32_t i = 0; i < n; ++i) {
+            out.key[i] = set_key(c, out.site.data() + out.off[i], out.k.data() + out.off[i], out.off[i + 1] - out.off[i]);
+            out.q[i] = c.Q0 * out.key[i];
+        }
+        allocate_shots(out, alloc, p.total_shots, p.shots_per_set);
+        out.shot_off.assign(out.count() + 1, 0);
+        for (uint32_t i = 0; i < out.count(); ++i) out.shot_off[i + 1] = out.shot_off[i] + out.shots[i];
+        return;
     }
     case PTSBE_PTS_TARGETED: {
         if (p.t_count && (!p.t_offsets || !p.t_sites || !p.t_kidx)) fail(PTSBE_ERR_INVALID, "targeted set arrays missing");
