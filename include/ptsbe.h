@@ -292,6 +292,15 @@ PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * ownership as for the two calls. Asynchronous. Errors: those of the two calls; a kernel that
  * finds a support not of the form the plan guarantees flags the context, and the next
  * ptsbe_synchronize returns PTSBE_ERR_UNSUPPORTED (the affected shots hold 0xFFFFFFFF). */
+/* d_states may be NULL when n > 12: the states are then not returned and live only in library
+ * buffers (for states too large to keep one per set, e.g. 8 GiB at 30 qubits). The sets of the
+ * range are prepared with dense passes, one branch at a time: at each pass the sets are split by
+ * their Kraus entries inside that pass; a group with entries there branches into a new buffer from
+ * the state all of them share at that pass (prefix reuse) and is finished -- prepared, normalised,
+ * sampled -- before the sets without entries there continue in place. Device memory: one 2^n
+ * complex64 buffer per level of branch nesting plus one (Kraus sets with e entries nest at most
+ * e + 1 deep), plus the sampler's workspace. Weights, status and shots are as above (the same
+ * states up to rounding, bit-identical to evolve kernel 4 with d_states given). */
 PTSBE_API int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
                                   double* d_weights, uint8_t* d_status, uint32_t flags, uint64_t seed,
                                   uint32_t* d_bits, uint64_t d_bits_capacity);
@@ -392,7 +401,11 @@ enum {
      * pass of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
      * registers, the tile re-shuffled through shared memory between register groups), 3 deferred
      * frame (permutations and diagonals tracked as an index map and factor tables; only
-     * operators that mix amplitudes pass over the tile). */
+     * operators that mix amplitudes pass over the tile), 4 dense passes for n > 12 (the state
+     * streams through HBM once per pass over 12-qubit tiles; the operators of a pass are fused into
+     * 1- and 2-qubit blocks applied to amplitudes held in registers; the planner changes the
+     * qubit-to-bit layout between passes so each pass holds the qubits it needs; n <= 12 falls back
+     * to 3). */
     PTSBE_OPT_EVOLVE_KERNEL = 0,
     /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
      * prefixes (one chunk re-read per shot); heavier ones by a thread-block cluster holding the
@@ -414,9 +427,9 @@ PTSBE_API int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value);
  * (milliseconds per ptsbe_evolve_batch call for the kernels, per ptsbe_evolve_sample call for the
  * shot limits; mean of `reps` calls; 0 for a candidate that does not apply). */
 typedef struct {
-    int32_t evolve_kernel;            /* chosen PTSBE_OPT_EVOLVE_KERNEL (1 sweeps, 2 registers, 3 frame) */
+    int32_t evolve_kernel;            /* chosen PTSBE_OPT_EVOLVE_KERNEL (1 sweeps, 2 registers, 3 frame, 4 dense) */
     uint64_t light_shots;             /* chosen PTSBE_OPT_LIGHT_SHOTS                                */
-    double evolve_ms[4];              /* by kernel index (entry 0 unused)                           */
+    double evolve_ms[5];              /* by kernel index (entry 0 unused; 4 only for n > 12)        */
     uint64_t light_candidates[4];
     double sample_ms[4];              /* by light-shot candidate                                    */
 } ptsbe_tuning;
@@ -443,6 +456,13 @@ PTSBE_API int ptsbe_kernel_launches(uint64_t* count);
  * entries, per-call schedules). */
 PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
 
+/* Prefix-reuse accounting of the context's last ptsbe_evolve_batch / ptsbe_evolve_sample call
+ * (Sec. 3 batched execution with shared prefixes): *gates_applied = gates the call's passes applied,
+ * summed over its Kraus sets (a pass run once for a group of sets that share it counts once);
+ * *gates_without_reuse = the circuit's gates times the number of sets. The savings are
+ * 1 - applied / without. Either pointer may be NULL. Host-only. */
+PTSBE_API int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_t* gates_without_reuse);
+
 /* Kernel classes of the timing counters. */
 enum {
     PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
@@ -452,7 +472,8 @@ enum {
     PTSBE_TIMER_EVOLVE_PROGRAM = 4,   /* per-set program prepass of the deferred-frame kernel     */
     PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */
     PTSBE_TIMER_BACKWARD = 6,         /* ptsbe_backward                                           */
-    PTSBE_TIMER_CLASSES = 7
+    PTSBE_TIMER_DENSE = 7,            /* dense tile passes (evolve kernel 4, and states not returned) */
+    PTSBE_TIMER_CLASSES = 8
 };
 
 /* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and

@@ -14,9 +14,9 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libptsbe.so")
 
-CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp", "backward.cpp"]
-CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu", "backward.cu"]
-HEADERS = ["internal.h", "philox.h", "tile_ops.cuh", "frame.cuh"]
+CXX_SOURCES = ["api.cpp", "pts.cpp", "circuit.cpp", "backward.cpp", "dense_plan.cpp"]
+CU_SOURCES = ["evolve.cu", "sample.cu", "pershot.cu", "backward.cu", "dense.cu"]
+HEADERS = ["internal.h", "philox.h", "tile_ops.cuh", "frame.cuh", "dense.cuh", "fixed_point.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -21,7 +21,7 @@ PTSBE_OPT_EVOLVE_KERNEL = 0
 PTSBE_OPT_LIGHT_SHOTS = 1
 PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
- PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD) = range(7)
+ PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE) = range(8)
 
 
 class ptsbe_op(C.Structure):
@@ -57,7 +57,7 @@ class ptsbe_observable(C.Structure):
 
 
 class ptsbe_tuning(C.Structure):
-    _fields_ = [("evolve_kernel", C.c_int32), ("light_shots", C.c_uint64), ("evolve_ms", C.c_double * 4),
+    _fields_ = [("evolve_kernel", C.c_int32), ("light_shots", C.c_uint64), ("evolve_ms", C.c_double * 5),
                 ("light_candidates", C.c_uint64 * 4), ("sample_ms", C.c_double * 4)]
 
 
@@ -105,6 +105,7 @@ _PROTOS = {
                                            C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "ptsbe_reuse_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "ptsbe_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "ptsbe_get_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
@@ -255,6 +256,12 @@ def ptsbe_h2d_bytes() -> int:
     if st != PTSBE_OK:
         raise PtsbeError(st, "ptsbe_h2d_bytes failed")
     return n.value
+
+
+def ptsbe_reuse_stats(ctx):
+    a, f = C.c_uint64(), C.c_uint64()
+    check(ctx, load().ptsbe_reuse_stats(ctx, C.byref(a), C.byref(f)))
+    return a.value, f.value
 
 
 def ptsbe_set_option(ctx, option: int, value: int):

@@ -1,10 +1,12 @@
 // C ABI of libptsbe: contexts, registries, workspace and the host-side scheduling of the kernels.
 #include <algorithm>
+#include <functional>
 #include <atomic>
 #include <cstring>
 #include <memory>
 #include <new>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 
 #include "internal.h"
@@ -55,6 +57,9 @@ struct ptsbe_ctx {
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
     uint32_t next_circuit = 1, next_set = 1;
     DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support;
+    DevBuf dense_tabs, stream_status;          // dense passes: per-call node/override tables; status when the caller passes none
+    std::vector<DevBuf> state_pool;            // dense passes without caller states: branch state buffers
+    uint64_t reuse_gates_run = 0, reuse_gates_full = 0;   // last evolve call: gates applied / without prefix reuse
     std::vector<unsigned char> host_blob;
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
@@ -314,12 +319,51 @@ struct FusedShots {
     uint32_t* bits;
 };
 
+void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
+                        double* d_weights, uint8_t* d_status, uint32_t flags);
+
+// prod over unitary-mixture sites of q_{s,k_s} for set alpha (q0mix: the product of every q_{s,0})
+double mix_weight(const Circuit& c, const KSet& s, uint32_t alpha, double q0mix) {
+    const uint32_t S = (uint32_t)c.site_op.size();
+    double w = q0mix;
+    if (q0mix > 0) {
+        for (uint32_t e = s.off[alpha]; e < s.off[alpha + 1]; ++e) {
+            const HostChannel& ch = c.ch[c.site_ch[s.site[e]]];
+            if (ch.mixture) w *= ch.q[s.k[e]] / ch.q[0];
+        }
+    } else {
+        w = 1.0;
+        uint32_t e = s.off[alpha];
+        for (uint32_t site = 0; site < S; ++site) {
+            uint32_t k = 0;
+            if (e < s.off[alpha + 1] && s.site[e] == site) k = s.k[e++];
+            const HostChannel& ch = c.ch[c.site_ch[site]];
+            if (ch.mixture) w *= ch.q[k];
+        }
+    }
+    return w;
+}
+
+double mix_q0(const Circuit& c) {
+    double q0mix = 1.0;
+    for (uint32_t site = 0; site < c.site_op.size(); ++site) {
+        const HostChannel& ch = c.ch[c.site_ch[site]];
+        if (ch.mixture) q0mix *= ch.q[0];
+    }
+    return q0mix;
+}
+
 // Prepares states [first, first + count) of set s (the work of ptsbe_evolve_batch). With fused,
 // the small sparse final stage also draws the shots of the states it can (drawn[a] = 1).
 void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
                   double* d_weights, uint8_t* d_status, uint32_t flags, const FusedShots* fused,
                   std::vector<uint8_t>* drawn) {
     ctx->use_device();
+    if (ctx->evolve_kernel == 4 && (int)c.n > dense::kT) {
+        if (drawn) drawn->assign(count, 0);
+        evolve_dense_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags);
+        return;
+    }
     ensure_set_on_device(ctx, s);
     const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
     if (frame && !c.frame_planned) {
@@ -412,6 +456,17 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         for (uint32_t a = 0; a < count; ++a)
             if (sstage[a] <= j) lists.push_back(a);
         launches.push_back({off, (uint32_t)(lists.size() - off)});
+    }
+    {   // gates applied with and without prefix reuse
+        std::vector<uint64_t> stage_gates(J + 1, 0);
+        for (uint32_t j = J; j-- > 0;) {
+            uint64_t g = 0;
+            for (uint32_t op = P.stages[j].op_begin; op < P.stages[j].op_end; ++op) g += c.ops[op].kind == PTSBE_OP_GATE;
+            stage_gates[j] = stage_gates[j + 1] + g;
+        }
+        ctx->reuse_gates_run = 0;
+        for (uint32_t a = 0; a < count; ++a) ctx->reuse_gates_run += stage_gates[sstage[a]];
+        ctx->reuse_gates_full = (uint64_t)count * stage_gates[0];
     }
     Blob blob(ctx->host_blob);
     const size_t o_ebeg = blob.add(ebeg), o_eend = blob.add(eend), o_sstage = blob.add(sstage);
@@ -618,6 +673,331 @@ void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     }
 }
 
+// ---- dense tile passes -------------------------------------------------------------------------
+
+void ensure_dense_plan(ptsbe_ctx* ctx, Circuit& c) {
+    DensePlan& P = c.dense;
+    if (!P.built) make_dense_plan(c, P);
+    if (P.dev) return;
+    std::vector<unsigned char> buf;
+    Blob b(buf);
+    const size_t o_p = b.add(P.passes), o_g = b.add(P.groups), o_b = b.add(P.blocks), o_h = b.add(P.hi);
+    const size_t o_o = b.add(P.omap), o_m = b.add(P.mats);
+    unsigned char* base = (unsigned char*)ctx->dalloc(buf.size());
+    ctx->h2d(base, buf.data(), buf.size());
+    P.dev = base;
+    P.d_passes = (const dense::Pass*)(base + o_p);
+    P.d_groups = (const dense::Group*)(base + o_g);
+    P.d_blocks = (const dense::Block*)(base + o_b);
+    P.d_hi = (const uint32_t*)(base + o_h);
+    P.d_omap = (const uint16_t*)(base + o_o);
+    P.d_mats = (const float2*)(base + o_m);
+}
+
+// Override blocks of set alpha: every block holding one of its entries, with the set's Kraus
+// operators in it, sorted by block id. Appends to ovr / pool; returns [begin, end).
+std::pair<uint32_t, uint32_t> dense_overrides(const Circuit& c, const DensePlan& P, const KSet& s, uint32_t alpha,
+                                              std::vector<dense::Override>& ovr, std::vector<float2>& pool) {
+    const uint32_t e0 = s.off[alpha], e1 = s.off[alpha + 1];
+    std::vector<std::pair<uint32_t, uint32_t>> eb;   // (block, entry)
+    for (uint32_t e = e0; e < e1; ++e) eb.push_back({P.site_block[s.site[e]], e});
+    std::sort(eb.begin(), eb.end());
+    const uint32_t begin = (uint32_t)ovr.size();
+    std::vector<uint32_t> sites;
+    std::vector<uint8_t> ks;
+    for (size_t i = 0; i < eb.size();) {
+        const uint32_t blk = eb[i].first;
+        sites.clear();
+        ks.clear();
+        for (; i < eb.size() && eb[i].first == blk; ++i) { sites.push_back(s.site[eb[i].second]); ks.push_back(s.k[eb[i].second]); }
+        const uint32_t cnt = P.blk_nq[blk] == 1 ? 4 : 16;
+        const uint32_t off = (uint32_t)pool.size();
+        pool.resize(pool.size() + cnt);
+        dense_block_matrix(c, P, blk, sites.data(), ks.data(), (uint32_t)sites.size(), &pool[off]);
+        ovr.push_back({blk, off});
+    }
+    return {begin, (uint32_t)ovr.size()};
+}
+
+DenseArgs dense_args(const DensePlan& P, int n) {
+    DenseArgs A{};
+    A.passes = P.d_passes; A.groups = P.d_groups; A.blocks = P.d_blocks;
+    A.hi = P.d_hi; A.omap = P.d_omap; A.mats = P.d_mats;
+    A.n = n;
+    return A;
+}
+
+// Algorithmic bytes of one dense pass launch over `nodes` states (read unless started from
+// |0...0>, then write; 8 bytes per amplitude each way).
+double dense_bytes(int n, uint32_t nodes, uint32_t fresh) {
+    const double sb = 8.0 * (double)(1ull << n);
+    return (2.0 * (nodes - fresh) + (double)fresh) * sb;
+}
+
+// ptsbe_evolve_batch with the dense kernel: one launch per pass for every set of the range, each
+// set's override blocks inserted. Prefix reuse: a set starts at the first pass that holds a block
+// with one of its entries beyond those of an earlier set of the range (its parent: the longest
+// such prefix that has computed its state at that pass), reading the parent's input of that pass.
+void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
+                        double* d_weights, uint8_t* d_status, uint32_t flags) {
+    ensure_dense_plan(ctx, c);
+    const DensePlan& P = c.dense;
+    const int n = (int)c.n;
+    const uint32_t J = (uint32_t)P.passes.size();
+    const bool reuse = (flags & PTSBE_EVOLVE_PREFIX_REUSE) && J > 1;
+    std::vector<dense::Override> ovr;
+    std::vector<float2> pool;
+    std::vector<uint32_t> ovb(count), ove(count), sstage(count, 0), src(count);
+    std::vector<double> wmix(count), qa(count);
+    const double q0mix = mix_q0(c);
+    std::unordered_map<std::string, uint32_t> index;
+    auto key_of = [&](uint32_t alpha, uint32_t len) {
+        std::string k;
+        k.resize(len * 5);
+        for (uint32_t i = 0; i < len; ++i) {
+            std::memcpy(&k[5 * i], &s.site[s.off[alpha] + i], 4);
+            k[5 * i + 4] = (char)s.k[s.off[alpha] + i];
+        }
+        return k;
+    };
+    for (uint32_t a = 0; a < count; ++a) {
+        const uint32_t alpha = first + a;
+        const uint32_t len = s.off[alpha + 1] - s.off[alpha];
+        auto r = dense_overrides(c, P, s, alpha, ovr, pool);
+        ovb[a] = r.first;
+        ove[a] = r.second;
+        wmix[a] = mix_weight(c, s, alpha, q0mix);
+        qa[a] = s.q[alpha];
+        src[a] = a;
+        if (reuse) {
+            for (int64_t p = (int64_t)len - 1; p >= 0; --p) {
+                auto it = index.find(key_of(alpha, (uint32_t)p));
+                if (it == index.end()) continue;
+                const uint32_t par = it->second;
+                uint32_t j = J;
+                for (uint32_t e = s.off[alpha] + (uint32_t)p; e < s.off[alpha + 1]; ++e)
+                    j = std::min(j, P.blk_pass[P.site_block[s.site[e]]]);
+                if (j == 0 || sstage[par] > j) continue;
+                sstage[a] = j;
+                src[a] = sstage[par] == j ? src[par] : par;
+                break;
+            }
+            index.emplace(key_of(alpha, len), a);
+        }
+    }
+    ctx->reuse_gates_run = 0;
+    uint64_t total_gates = 0;
+    std::vector<uint64_t> suffix(J + 1, 0);
+    for (uint32_t j = J; j-- > 0;) suffix[j] = suffix[j + 1] + P.pass_gates[j];
+    total_gates = suffix[0];
+    for (uint32_t a = 0; a < count; ++a) ctx->reuse_gates_run += suffix[sstage[a]];
+    ctx->reuse_gates_full = (uint64_t)count * total_gates;
+
+    const size_t sb = (size_t)8 << n;
+    float2* const user = (float2*)d_states;
+    float2* const other = reuse ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * sb) : user;
+    auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
+    auto slot = [&](float2* b, uint32_t a) { return b + ((size_t)a << n); };
+    std::vector<dense::Node> nodes;
+    std::vector<std::pair<size_t, uint32_t>> launches;
+    std::vector<uint32_t> fresh_cnt;
+    for (uint32_t j = 0; j < J; ++j) {
+        const size_t off = nodes.size();
+        uint32_t fr = 0;
+        for (uint32_t a = 0; a < count; ++a) {
+            if (sstage[a] > j) continue;
+            dense::Node nd{};
+            if (j == sstage[a] && j == 0) { nd.src = nullptr; ++fr; }
+            else nd.src = slot(j == 0 ? user : out_buf(j - 1), j == sstage[a] ? src[a] : a);
+            nd.dst = slot(out_buf(j), a);
+            nd.ov_begin = ovb[a];
+            nd.ov_end = ove[a];
+            nd.part = a;
+            nodes.push_back(nd);
+        }
+        launches.push_back({off, (uint32_t)(nodes.size() - off)});
+        fresh_cnt.push_back(fr);
+    }
+    std::vector<unsigned char> buf;
+    Blob b(buf);
+    const size_t o_n = b.add(nodes), o_o = b.add(ovr), o_p = b.add(pool), o_w = b.add(wmix), o_q = b.add(qa);
+    unsigned char* d = (unsigned char*)ctx->ws(ctx->dense_tabs, buf.size());
+    ctx->h2d(d, buf.data(), buf.size());
+    const int ob = n - dense::kT;
+    double* part = (double*)ctx->ws(ctx->part, ((size_t)count << ob) * sizeof(double));
+    float* d_scale = (float*)ctx->ws(ctx->scale, (size_t)count * sizeof(float));
+    DenseArgs A = dense_args(P, n);
+    A.ovr = (const dense::Override*)(d + o_o);
+    A.opool = (const float2*)(d + o_p);
+    A.part = part;
+    for (uint32_t j = 0; j < J; ++j) {
+        if (launches[j].second == 0) continue;
+        A.nodes = (const dense::Node*)(d + o_n) + launches[j].first;
+        A.n_nodes = launches[j].second;
+        A.pass = (int)j;
+        A.last = j + 1 == J ? 1 : 0;
+        ctx->timed(PTSBE_TIMER_DENSE, dense_bytes(n, A.n_nodes, fresh_cnt[j]), [&] { launch_dense_pass(A, ctx->n_sm, ctx->stream); });
+    }
+    EvolveArgs E{};
+    E.n = n;
+    E.tb = dense::kT;
+    E.part = part;
+    E.wmix = (const double*)(d + o_w);
+    E.qalpha = (const double*)(d + o_q);
+    E.weights = d_weights;
+    E.status = d_status;
+    E.states = user;
+    ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb * count, [&] { launch_evolve_finalize(E, count, d_scale, ctx->stream); });
+}
+
+// ptsbe_evolve_sample without caller states: the states live in library buffers, one branch at
+// a time. The sets of the range are split, pass by pass, by their entries in that pass: every
+// group with entries there branches into a new buffer (reading the shared input of the pass) and
+// runs to the end first; then the sets with none continue in place. A branch that reaches the end
+// holds exactly one set's state: it is normalised (weight, status) and sampled, and its buffer is
+// released. Live buffers never exceed the nesting depth of the branches plus one.
+void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, double* d_weights,
+                          uint8_t* d_status, uint64_t seed, uint32_t* d_bits) {
+    ensure_dense_plan(ctx, c);
+    const DensePlan& P = c.dense;
+    const int n = (int)c.n;
+    const uint32_t J = (uint32_t)P.passes.size();
+    std::vector<dense::Override> ovr;
+    std::vector<float2> pool;
+    std::vector<uint32_t> ovb(count), ove(count);
+    std::vector<double> wmix(count), qa(count);
+    const double q0mix = mix_q0(c);
+    // entries of each set as (pass, site, k), sorted
+    std::vector<std::vector<std::tuple<uint32_t, uint32_t, uint8_t>>> byp(count);
+    for (uint32_t a = 0; a < count; ++a) {
+        const uint32_t alpha = first + a;
+        auto r = dense_overrides(c, P, s, alpha, ovr, pool);
+        ovb[a] = r.first;
+        ove[a] = r.second;
+        wmix[a] = mix_weight(c, s, alpha, q0mix);
+        qa[a] = s.q[alpha];
+        for (uint32_t e = s.off[alpha]; e < s.off[alpha + 1]; ++e)
+            byp[a].emplace_back(P.blk_pass[P.site_block[s.site[e]]], s.site[e], s.k[e]);
+        std::sort(byp[a].begin(), byp[a].end());
+    }
+    struct Act {
+        uint32_t pass;                 // J: leaf -- normalise and sample set `rep`
+        int src, dst;                  // buffer indices (-1: |0...0>)
+        uint32_t rep;                  // a set of the group (its overrides serve the whole group)
+    };
+    std::vector<Act> acts;
+    int nbuf = 0;
+    std::vector<int> freeb;
+    auto alloc = [&]() {
+        if (!freeb.empty()) { const int x = freeb.back(); freeb.pop_back(); return x; }
+        return nbuf++;
+    };
+    std::vector<size_t> cur(count, 0);
+    uint64_t gates_run = 0;
+    std::function<void(uint32_t, int, std::vector<uint32_t>&)> rec = [&](uint32_t j, int X, std::vector<uint32_t>& sets) {
+        if (j == J) {
+            for (uint32_t a : sets) acts.push_back({J, X, X, a});
+            freeb.push_back(X);
+            return;
+        }
+        std::vector<std::vector<uint32_t>> groups;
+        std::unordered_map<std::string, size_t> gi;
+        std::vector<uint32_t> main;
+        for (uint32_t a : sets) {
+            std::string key;
+            while (cur[a] < byp[a].size() && std::get<0>(byp[a][cur[a]]) == j) {
+                const uint32_t site = std::get<1>(byp[a][cur[a]]);
+                key.append((const char*)&site, 4);
+                key.push_back((char)std::get<2>(byp[a][cur[a]]));
+                ++cur[a];
+            }
+            if (key.empty()) { main.push_back(a); continue; }
+            auto it = gi.find(key);
+            if (it == gi.end()) { gi.emplace(key, groups.size()); groups.push_back({a}); }
+            else groups[it->second].push_back(a);
+        }
+        for (auto& g : groups) {
+            const int Y = alloc();
+            acts.push_back({j, X, Y, g[0]});
+            gates_run += P.pass_gates[j];
+            rec(j + 1, Y, g);
+        }
+        if (main.empty()) {
+            if (X >= 0) freeb.push_back(X);
+            return;
+        }
+        const int D = X >= 0 ? X : alloc();
+        acts.push_back({j, X, D, main[0]});
+        gates_run += P.pass_gates[j];
+        rec(j + 1, D, main);
+    };
+    {
+        std::vector<uint32_t> all(count);
+        for (uint32_t a = 0; a < count; ++a) all[a] = a;
+        rec(0, -1, all);
+    }
+    uint64_t total_gates = 0;
+    for (uint32_t g : P.pass_gates) total_gates += g;
+    ctx->reuse_gates_run = gates_run;
+    ctx->reuse_gates_full = (uint64_t)count * total_gates;
+
+    const size_t sb = (size_t)8 << n;
+    if (ctx->state_pool.size() < (size_t)nbuf) ctx->state_pool.resize(nbuf);
+    std::vector<float2*> bufs(nbuf);
+    for (int i = 0; i < nbuf; ++i) bufs[i] = (float2*)ctx->ws(ctx->state_pool[i], sb);
+    std::vector<dense::Node> nodes;
+    std::vector<uint32_t> fresh;
+    for (const Act& x : acts) {
+        if (x.pass == J) continue;
+        dense::Node nd{};
+        nd.src = x.src >= 0 ? bufs[x.src] : nullptr;
+        nd.dst = bufs[x.dst];
+        nd.ov_begin = ovb[x.rep];
+        nd.ov_end = ove[x.rep];
+        nd.part = 0;
+        nodes.push_back(nd);
+    }
+    std::vector<unsigned char> buf;
+    Blob b(buf);
+    const size_t o_n = b.add(nodes), o_o = b.add(ovr), o_p = b.add(pool), o_w = b.add(wmix), o_q = b.add(qa);
+    unsigned char* d = (unsigned char*)ctx->ws(ctx->dense_tabs, buf.size());
+    ctx->h2d(d, buf.data(), buf.size());
+    if (!d_status) d_status = (uint8_t*)ctx->ws(ctx->stream_status, count);
+    const int ob = n - dense::kT;
+    double* part = (double*)ctx->ws(ctx->part, ((size_t)1 << ob) * sizeof(double));
+    float* d_scale = (float*)ctx->ws(ctx->scale, sizeof(float));
+    DenseArgs A = dense_args(P, n);
+    A.ovr = (const dense::Override*)(d + o_o);
+    A.opool = (const float2*)(d + o_p);
+    A.part = part;
+    A.n_nodes = 1;
+    const dense::Node* dn = (const dense::Node*)(d + o_n);
+    const uint64_t base = s.shot_off[first];
+    size_t ni = 0;
+    for (const Act& x : acts) {
+        if (x.pass < J) {
+            A.nodes = dn + ni++;
+            A.pass = (int)x.pass;
+            A.last = x.pass + 1 == J ? 1 : 0;
+            ctx->timed(PTSBE_TIMER_DENSE, dense_bytes(n, 1, x.src < 0 ? 1 : 0), [&] { launch_dense_pass(A, ctx->n_sm, ctx->stream); });
+            continue;
+        }
+        const uint32_t a = x.rep;
+        EvolveArgs E{};
+        E.n = n;
+        E.tb = dense::kT;
+        E.part = part;
+        E.wmix = (const double*)(d + o_w) + a;
+        E.qalpha = (const double*)(d + o_q) + a;
+        E.weights = d_weights ? d_weights + a : nullptr;
+        E.status = d_status + a;
+        E.states = bufs[x.src];
+        ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb, [&] { launch_evolve_finalize(E, 1, d_scale, ctx->stream); });
+        if (s.shots[first + a])
+            sample_range(ctx, s, c, first + a, 1, bufs[x.src], d_status + a, seed, d_bits + (s.shot_off[first + a] - base), nullptr);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -668,6 +1048,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
             free_device_circuit(ctx, kv.second->dev); free_device_circuit(ctx, kv.second->dev_pershot);
             free_device_circuit(ctx, kv.second->dev_frame);
             ctx->dfree(kv.second->bw.dev);
+            ctx->dfree(kv.second->dense.dev);
         }
         for (auto& kv : ctx->sets) ctx->dfree(kv.second->d_site);   // d_k shares the allocation
         cudaStreamSynchronize(ctx->stream);
@@ -676,6 +1057,8 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
         ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault); ctx->free_buf(ctx->support);
+        ctx->free_buf(ctx->dense_tabs); ctx->free_buf(ctx->stream_status);
+        for (DevBuf& b : ctx->state_pool) ctx->free_buf(b);
         ctx->free_timers();
     }
     delete ctx;
@@ -747,6 +1130,8 @@ int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
             free_device_circuit(ctx, c.dev_frame);
             ctx->dfree(c.bw.dev);
             c.bw.dev = nullptr;
+            ctx->dfree(c.dense.dev);
+            c.dense.dev = nullptr;
         }
         ctx->circuits.erase(circuit_id);
     });
@@ -841,7 +1226,6 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
         Circuit& c = ctx->circuit(s.circuit);
         if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
         if (count == 0) return;
-        if (!d_states) fail(PTSBE_ERR_INVALID, "d_states is NULL");
         if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
         if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
         const uint64_t total = s.shot_off[first + count] - s.shot_off[first];
@@ -849,6 +1233,13 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
         if (d_bits_capacity < total) fail(PTSBE_ERR_BUFFER_TOO_SMALL, "d_bits holds " + std::to_string(d_bits_capacity) +
                                                                           " shots, the range needs " + std::to_string(total));
         if (total && c.n > 32) fail(PTSBE_ERR_UNSUPPORTED, "outcomes are 32-bit");
+        if (!d_states) {
+            if ((int)c.n <= dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "d_states may be NULL only for n > 12 (dense passes)");
+            ctx->use_device();
+            ensure_set_on_device(ctx, s);
+            stream_evolve_sample(ctx, s, c, first, count, d_weights, d_status, seed, d_bits);
+            return;
+        }
         std::vector<uint8_t> drawn;
         const FusedShots fs{seed, d_bits};
         evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, total ? &fs : nullptr, &drawn);
@@ -890,7 +1281,7 @@ int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
 int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
     return guarded(ctx, [&] {
         if (option == PTSBE_OPT_EVOLVE_KERNEL) {
-            if (value < 0 || value > 3) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0, 1, 2 or 3");
+            if (value < 0 || value > 4) fail(PTSBE_ERR_INVALID, "evolve kernel must be 0 .. 4");
             ctx->evolve_kernel = (int)value;
         } else if (option == PTSBE_OPT_LIGHT_SHOTS) {
             if (value < 0) fail(PTSBE_ERR_INVALID, "light-sampler shot limit must be >= 0");
@@ -932,7 +1323,9 @@ int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t cou
         int best_k = -1;
         double best = 0;
         try {
-            for (int k : {3, 1, 2}) {
+            const bool dense_ok = (int)ctx->circuit(ctx->set(set_id).circuit).n > dense::kT;
+            for (int k : {3, 1, 2, 4}) {
+                if (k == 4 && !dense_ok) continue;
                 ctx->evolve_kernel = k;
                 const double ms = timed_ms([&] { return ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags); });
                 if (ms < 0) fail(PTSBE_ERR_INVALID, std::string("autotune: evolve kernel ") + std::to_string(k) + ": " + ctx->err);
@@ -1004,6 +1397,13 @@ int ptsbe_h2d_bytes(uint64_t* bytes) {
     if (!bytes) return PTSBE_ERR_INVALID;
     *bytes = g_h2d.load(std::memory_order_relaxed);
     return PTSBE_OK;
+}
+
+int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_t* gates_without_reuse) {
+    return guarded(ctx, [&] {
+        if (gates_applied) *gates_applied = ctx->reuse_gates_run;
+        if (gates_without_reuse) *gates_without_reuse = ctx->reuse_gates_full;
+    });
 }
 
 int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,

@@ -1,0 +1,180 @@
+// Dense tile passes for large states (Sec. 3, batched execution: one O(2^n) preparation per Kraus
+// set, the dominant cost of PTSBE). Shared by the CUDA kernel (dense.cu), the host planner
+// (dense_plan.cpp) and the CPU harness of the tests, which runs the same per-thread code.
+//
+// A pass streams a state through HBM once: the 2^n amplitudes are cut into 2^(n-T) tiles of 2^T
+// amplitudes (T = kT tile bits); the tile bits are a set of physical index bits that always
+// contains the kC lowest ones, so a tile is made of contiguous 2^kC-amplitude (128-byte) runs.
+// Inside the tile, the pass applies every operator of its part of the circuit -- gates, and at each
+// noise site the Kraus operator the set selects -- fused into 1- and 2-qubit blocks. The blocks
+// run in register groups: each of the 2^(T-kR) threads holds 2^kR amplitudes whose tile index
+// varies in the group's kR register bits, applies the group's blocks in registers and hands the
+// tile on through shared memory (XOR-swizzled so that a warp's accesses spread over the banks).
+// Between passes the logical-to-physical qubit map may change: a pass writes its tile bits back
+// in another order, which is how qubits that the next pass needs reach the low bits.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#ifdef __CUDACC__
+#define PTSBE_HD __host__ __device__ __forceinline__
+#else
+#define PTSBE_HD inline
+#endif
+
+namespace ptsbe {
+namespace dense {
+
+constexpr int kT = 12;                          // tile bits: 2^12 complex64 = 32 KiB of shared memory
+constexpr int kC = 4;                           // contiguous low bits of every tile (16 amplitudes)
+constexpr int kR = 4;                           // register bits per thread (16 amplitudes)
+constexpr int kTB = kT - kR;                    // thread-index bits
+constexpr int kThreads = 1 << kTB;              // 256 threads per CTA
+constexpr int kAmps = 1 << kR;                  // amplitudes per thread
+constexpr int kHi = 1 << (kT - kC);             // entries of a pass's high-offset table
+constexpr int kMaxQ = 32;
+
+// One fused operator of a pass. code 0..3: 2x2 on register bit `code`; code 4..9: 4x4 on the
+// register pair kPairs[code - 4] = (lo, hi), local index bit(lo) + 2 bit(hi).
+struct Block {
+    uint8_t code;
+    uint8_t pad[3];
+    uint32_t mat;                               // default matrix: float2 pool offset (4 or 16 entries)
+    uint32_t id;                                // plan-wide index, increasing in execution order
+};
+
+// Consecutive blocks of a pass that act on the same kR tile bits. Thread t holds the amplitudes at
+// tile addresses base(t) ^ roff[j], j = 0 .. 15, with base(t) the XOR of toff[k] over the set bits k
+// of t; both tables hold swizzled addresses (the swizzle is linear over GF(2)).
+struct Group {
+    uint16_t toff[kTB];
+    uint16_t roff[kAmps];
+    uint32_t blk_begin, blk_end;                // blocks (indices into the plan's block array)
+};
+
+// One pass. Tile bit i is physical index bit pos[i] (pos ascending, pos[i] = i for i < kC) on the
+// way in; on the way out the tile is written in another order: the amplitude at output-local index
+// L (whose bit j is physical bit pos[j] again) comes from tile address omap[L >> kC] ^ olow[L & 15].
+struct Pass {
+    uint32_t group_begin, group_end;
+    uint32_t blk_begin, blk_end;                // plan-wide block ids of this pass
+    uint32_t hi_off;                            // hi pool: kHi amplitude offsets of tile bits [kC, kT)
+    uint32_t omap_off;                          // omap pool: kHi tile addresses
+    uint16_t olow[1 << kC];
+    uint8_t opos[kMaxQ];                        // outer bit k -> physical position (ascending)
+    uint32_t nouter;
+    uint32_t nops;                              // circuit operations this pass applies
+};
+
+// A (set, pass) launch entry: where the tile comes from and goes to, and the set's override blocks.
+struct Node {
+    const float2* src;                          // nullptr: the state starts from |0...0> in this pass
+    float2* dst;
+    uint32_t ov_begin, ov_end;                  // overrides (sorted by block id) of this set
+    uint32_t part;                              // row of the norm partials (last pass)
+    uint32_t pad;
+};
+
+struct Override {
+    uint32_t block;                             // plan-wide block id
+    uint32_t mat;                               // float2 offset into the override pool (4 or 16 entries)
+};
+
+// Register pairs of the 4x4 codes.
+PTSBE_HD int pair_lo(int p) { return p < 3 ? 0 : (p < 5 ? 1 : 2); }
+PTSBE_HD int pair_hi(int p) { return p < 3 ? p + 1 : (p < 5 ? p - 1 : 3); }
+
+// XOR swizzle of a tile address (kT = 12): the float2 bank pair of address t is bits 0..3 of the
+// result, and tile bit p contributes unit vector p mod 4 to them.
+PTSBE_HD uint32_t swz(uint32_t t) { return t ^ ((t >> 4) & 15u) ^ ((t >> 8) & 15u); }
+
+#ifdef __CUDA_ARCH__
+PTSBE_HD float4 ldm(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+#else
+PTSBE_HD float4 ldm(const float2* p) { return *reinterpret_cast<const float4*>(p); }
+#endif
+
+// out = a * x + b * y (complex)
+PTSBE_HD float2 cmac2(float2 a, float2 x, float2 b, float2 y) {
+    float2 r;
+    r.x = a.x * x.x - a.y * x.y + b.x * y.x - b.y * y.y;
+    r.y = a.x * x.y + a.y * x.x + b.x * y.y + b.y * y.x;
+    return r;
+}
+
+// 2x2 matrix m (row-major, 4 float2, 16-byte aligned) on register bit A of v[16].
+template <int A>
+PTSBE_HD void apply1(float2* v, const float2* m) {
+    const float4 r0 = ldm(m), r1 = ldm(m + 2);
+    const float2 m00 = make_float2(r0.x, r0.y), m01 = make_float2(r0.z, r0.w);
+    const float2 m10 = make_float2(r1.x, r1.y), m11 = make_float2(r1.z, r1.w);
+#pragma unroll
+    for (int j = 0; j < kAmps; ++j) {
+        if (j & (1 << A)) continue;
+        const float2 x = v[j], y = v[j | (1 << A)];
+        v[j] = cmac2(m00, x, m01, y);
+        v[j | (1 << A)] = cmac2(m10, x, m11, y);
+    }
+}
+
+// 4x4 matrix m (row-major, 16 float2) on register bits (L, H), local index bit(L) + 2 bit(H).
+template <int L, int H>
+PTSBE_HD void apply2(float2* v, const float2* m) {
+    float2 M[16];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 r = ldm(m + 2 * i);
+        M[2 * i] = make_float2(r.x, r.y);
+        M[2 * i + 1] = make_float2(r.z, r.w);
+    }
+#pragma unroll
+    for (int j = 0; j < kAmps; ++j) {
+        if (j & ((1 << L) | (1 << H))) continue;
+        const int i1 = j | (1 << L), i2 = j | (1 << H), i3 = j | (1 << L) | (1 << H);
+        const float2 x0 = v[j], x1 = v[i1], x2 = v[i2], x3 = v[i3];
+        float2 o[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float2 a = cmac2(M[4 * r], x0, M[4 * r + 1], x1);
+            const float2 b = cmac2(M[4 * r + 2], x2, M[4 * r + 3], x3);
+            o[r] = make_float2(a.x + b.x, a.y + b.y);
+        }
+        v[j] = o[0]; v[i1] = o[1]; v[i2] = o[2]; v[i3] = o[3];
+    }
+}
+
+PTSBE_HD void apply_block(float2* v, int code, const float2* m) {
+    switch (code) {
+    case 0: apply1<0>(v, m); break;
+    case 1: apply1<1>(v, m); break;
+    case 2: apply1<2>(v, m); break;
+    case 3: apply1<3>(v, m); break;
+    case 4: apply2<0, 1>(v, m); break;
+    case 5: apply2<0, 2>(v, m); break;
+    case 6: apply2<0, 3>(v, m); break;
+    case 7: apply2<1, 2>(v, m); break;
+    case 8: apply2<1, 3>(v, m); break;
+    default: apply2<2, 3>(v, m); break;
+    }
+}
+
+// Swizzled tile address of thread t's register base in group g.
+PTSBE_HD uint32_t group_base(const Group& g, uint32_t t) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int k = 0; k < kTB; ++k)
+        if ((t >> k) & 1u) b ^= g.toff[k];
+    return b;
+}
+
+// Amplitude offset of outer index tau (bits -> physical positions opos).
+PTSBE_HD uint64_t outer_offset(const Pass& p, uint64_t tau) {
+    uint64_t o = 0;
+    for (uint32_t k = 0; k < p.nouter; ++k)
+        if ((tau >> k) & 1u) o |= 1ull << p.opos[k];
+    return o;
+}
+
+}  // namespace dense
+}  // namespace ptsbe

@@ -1,0 +1,496 @@
+// Planner of the dense tile passes (dense.cuh).
+//
+// The circuit (gates and noise sites in order) is cut into passes. A pass holds kT logical qubits
+// -- always the kC qubits currently at physical bits 0 .. kC-1, so tiles are made of contiguous
+// runs -- and applies every not yet applied operation that acts only on those qubits and whose
+// predecessors on its qubits are applied. The qubit set of a pass is the best of a few candidates
+// (contiguous windows of qubit indices, the qubits of the next pending operations, a greedy
+// one-qubit-at-a-time growth), scored by how many operations it applies. A pass then rewrites its
+// tile bits in a new order that puts, at the low physical bits, qubits the next pass will want;
+// trailing passes without operations restore logical order (qubit q = bit q) at the end.
+//
+// Within a pass, operations become blocks: consecutive operations on one qubit, or on one pair,
+// multiplied together (a gate, then the Kraus operator of each noise site after it: operator 0 by
+// default, the set's operator where the set has an entry -- an "override" block). Blocks are then
+// packed into register groups of kR tile bits, taking later blocks forward past ones they commute
+// with (disjoint qubits).
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace ptsbe {
+
+namespace {
+
+using namespace dense;
+
+struct OpQ {
+    uint32_t q0, q1;
+    uint8_t nq;
+};
+
+uint64_t qmask(const OpQ& o) { return (1ull << o.q0) | (o.nq == 2 ? (1ull << o.q1) : 0ull); }
+int pop(uint64_t m) { return __builtin_popcountll(m); }
+
+struct PassRec {
+    uint64_t S;                          // logical qubits of the tile
+    std::vector<uint32_t> ops;           // operations applied, circuit order
+    std::vector<int> phys_in, phys_out;  // logical -> physical before / after the pass
+};
+
+struct Planner {
+    int n = 0, T = 0;
+    std::vector<OpQ> ops;
+    std::vector<uint8_t> done;
+    size_t first = 0;
+    std::vector<int> phys, at;           // logical -> physical, physical -> logical
+
+    uint32_t exec(uint64_t S, std::vector<uint32_t>* out) const {
+        uint64_t blocked = 0;
+        uint32_t cnt = 0;
+        for (size_t i = first; i < ops.size(); ++i) {
+            if (done[i]) continue;
+            const uint64_t m = qmask(ops[i]);
+            if ((m & ~S) || (m & blocked)) {
+                blocked |= m;
+                if ((blocked & S) == S) break;
+                continue;
+            }
+            ++cnt;
+            if (out) out->push_back((uint32_t)i);
+        }
+        return cnt;
+    }
+
+    uint64_t low_set() const {
+        uint64_t m = 0;
+        for (int p = 0; p < kC; ++p) m |= 1ull << at[p];
+        return m;
+    }
+
+    uint64_t choose(uint64_t must, uint32_t* best_cnt) const {
+        uint64_t best = 0;
+        uint32_t bc = 0;
+        bool have = false;
+        auto consider = [&](uint64_t S) {
+            if (pop(S) != T) return;
+            const uint32_t k = exec(S, nullptr);
+            if (!have || k > bc) { best = S; bc = k; have = true; }
+        };
+        for (int a = 0; a < n; ++a) {
+            uint64_t S = must;
+            for (int q = a; q < n && pop(S) < T; ++q) S |= 1ull << q;
+            for (int q = a - 1; q >= 0 && pop(S) < T; --q) S |= 1ull << q;
+            consider(S);
+        }
+        {   // the qubits of the next pending operations, in order
+            uint64_t S = must;
+            for (size_t i = first; i < ops.size() && pop(S) < T; ++i) {
+                if (done[i]) continue;
+                const uint64_t m = qmask(ops[i]);
+                if (pop(S | m) <= T) S |= m;
+            }
+            for (int q = 0; q < n && pop(S) < T; ++q) S |= 1ull << q;
+            consider(S);
+        }
+        {   // greedy growth
+            uint64_t S = must;
+            while (pop(S) < T) {
+                int bq = -1;
+                uint32_t bk = 0;
+                for (int q = 0; q < n; ++q) {
+                    if ((S >> q) & 1u) continue;
+                    const uint32_t k = exec(S | (1ull << q), nullptr);
+                    if (bq < 0 || k > bk) { bq = q; bk = k; }
+                }
+                S |= 1ull << bq;
+            }
+            consider(S);
+        }
+        *best_cnt = bc;
+        return best;
+    }
+
+    // first pending operation index of every qubit (ops.size() when none)
+    std::vector<size_t> next_pending() const {
+        std::vector<size_t> nx(n, ops.size());
+        int left = n;
+        for (size_t i = first; i < ops.size() && left > 0; ++i) {
+            if (done[i]) continue;
+            const OpQ& o = ops[i];
+            if (nx[o.q0] == ops.size()) { nx[o.q0] = i; --left; }
+            if (o.nq == 2 && nx[o.q1] == ops.size()) { nx[o.q1] = i; --left; }
+        }
+        return nx;
+    }
+
+    // Moves the qubits `low` (kC of them, all in S) to physical bits 0 .. kC-1; the qubits they
+    // displace take the positions they leave.
+    void set_low(const std::vector<int>& low) {
+        std::vector<int> leaving;
+        for (int p = 0; p < kC; ++p)
+            if (std::find(low.begin(), low.end(), at[p]) == low.end()) leaving.push_back(at[p]);
+        std::vector<int> arriving;
+        for (int q : low)
+            if (phys[q] >= kC) arriving.push_back(q);
+        for (size_t i = 0; i < arriving.size(); ++i) {
+            const int a = arriving[i], b = leaving[i];
+            std::swap(phys[a], phys[b]);
+            at[phys[a]] = a;
+            at[phys[b]] = b;
+        }
+    }
+};
+
+// Tile bit of each logical qubit of S (rank of its physical position) and the positions.
+void tile_positions(uint64_t S, const std::vector<int>& phys, std::vector<int>& P, std::vector<int>& tbit, int n) {
+    P.clear();
+    for (int q = 0; q < n; ++q)
+        if ((S >> q) & 1u) P.push_back(phys[q]);
+    std::sort(P.begin(), P.end());
+    tbit.assign(n, -1);
+    for (int q = 0; q < n; ++q)
+        if ((S >> q) & 1u) tbit[q] = (int)(std::lower_bound(P.begin(), P.end(), phys[q]) - P.begin());
+}
+
+void op_matrix(const Circuit& c, uint32_t op, uint32_t k, cd* m, int& dim) {
+    const ptsbe_op& o = c.ops[op];
+    if (o.kind == PTSBE_OP_GATE) {
+        const double* custom = nullptr;
+        if (o.id == PTSBE_G_U1 || o.id == PTSBE_G_U2) custom = c.custom.data() + 32 * (size_t)o.params[0];
+        gate_matrix_of(o.id, o.params, custom, m, dim);
+        return;
+    }
+    const HostChannel& ch = c.ch[o.id];
+    const uint32_t dd = ch.dim * ch.dim;
+    const cd* src = ch.mixture ? &ch.U[(size_t)k * dd] : &ch.K[(size_t)k * dd];
+    for (uint32_t i = 0; i < dd; ++i) m[i] = src[i];
+    dim = (int)ch.dim;
+}
+
+int pair_index(int lo, int hi) {
+    static const int idx[4][4] = {{-1, 0, 1, 2}, {-1, -1, 3, 4}, {-1, -1, -1, 5}, {-1, -1, -1, -1}};
+    return idx[lo][hi];
+}
+
+}  // namespace
+
+void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
+                        uint32_t len, float2* out) {
+    const int nq = P.blk_nq[b];
+    const int d = nq == 1 ? 2 : 4;
+    cd M[16], E[16], m[16], t[16];
+    for (int i = 0; i < d * d; ++i) M[i] = (i % (d + 1) == 0) ? cd(1.0) : cd(0.0);
+    uint32_t e = 0;
+    const uint32_t qs2[2] = {P.blk_qa[b], P.blk_qb[b]};
+    for (uint32_t i = P.blk_op_off[b]; i < P.blk_op_off[b + 1]; ++i) {
+        const uint32_t op = P.blk_ops[i];
+        const ptsbe_op& o = c.ops[op];
+        uint32_t k = 0;
+        if (o.kind == PTSBE_OP_NOISE) {
+            // site index of this op: entries are sorted by site, and so are the block's sites
+            while (e < len && c.site_op[sites[e]] < op) ++e;
+            if (e < len && c.site_op[sites[e]] == op) k = ks[e];
+        }
+        int dim = 2;
+        op_matrix(c, op, k, m, dim);
+        const cd* A = m;
+        if (nq == 2) {
+            embed_pair(m, dim, o.targets, qs2[0], qs2[1], E);
+            A = E;
+        }
+        for (int r = 0; r < d; ++r)
+            for (int col = 0; col < d; ++col) {
+                cd s = 0;
+                for (int x = 0; x < d; ++x) s += A[r * d + x] * M[x * d + col];
+                t[r * d + col] = s;
+            }
+        for (int i2 = 0; i2 < d * d; ++i2) M[i2] = t[i2];
+    }
+    if (nq == 2 && P.blk_swap[b]) {
+        auto p = [](int l) { return ((l & 1) << 1) | (l >> 1); };
+        for (int r = 0; r < 4; ++r)
+            for (int col = 0; col < 4; ++col) t[p(r) * 4 + p(col)] = M[r * 4 + col];
+        for (int i = 0; i < 16; ++i) M[i] = t[i];
+    }
+    for (int i = 0; i < d * d; ++i) out[i] = make_float2((float)M[i].real(), (float)M[i].imag());
+}
+
+void make_dense_plan(const Circuit& c, DensePlan& P) {
+    const int n = (int)c.n;
+    if (n <= kT || n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 12 < n <= 32");
+    P = DensePlan{};
+    P.n = n;
+    Planner pl;
+    pl.n = n;
+    pl.T = kT;
+    pl.ops.resize(c.ops.size());
+    for (size_t i = 0; i < c.ops.size(); ++i) {
+        const ptsbe_op& o = c.ops[i];
+        pl.ops[i] = OpQ{o.targets[0], o.n_targets == 2 ? o.targets[1] : o.targets[0], (uint8_t)o.n_targets};
+    }
+    pl.done.assign(c.ops.size(), 0);
+    pl.phys.resize(n);
+    pl.at.resize(n);
+    for (int q = 0; q < n; ++q) { pl.phys[q] = q; pl.at[q] = q; }
+
+    std::vector<PassRec> recs;
+    while (pl.first < pl.ops.size()) {
+        uint32_t cnt = 0;
+        const uint64_t S = pl.choose(pl.low_set(), &cnt);
+        if (cnt == 0) fail(PTSBE_ERR_INVALID, "dense planner made no progress");
+        PassRec r;
+        r.S = S;
+        r.phys_in = pl.phys;
+        pl.exec(S, &r.ops);
+        for (uint32_t i : r.ops) pl.done[i] = 1;
+        while (pl.first < pl.ops.size() && pl.done[pl.first]) ++pl.first;
+        if (pl.first < pl.ops.size()) {
+            // qubits the next pass will likely hold go to the low bits
+            uint32_t c2 = 0;
+            const uint64_t S2 = pl.choose(0, &c2);
+            const std::vector<size_t> nx = pl.next_pending();
+            std::vector<int> cand;
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1u) cand.push_back(q);
+            std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+                const bool ia = (S2 >> a) & 1u, ib = (S2 >> b) & 1u;
+                if (ia != ib) return ia;
+                return nx[a] < nx[b];
+            });
+            std::vector<int> low(cand.begin(), cand.begin() + kC);
+            pl.set_low(low);
+        }
+        r.phys_out = pl.phys;
+        recs.push_back(std::move(r));
+    }
+    // restore logical order: passes without operations, each fixing the qubits whose home lies
+    // in its tile (tiles grown along permutation cycles, so every pass makes progress)
+    for (int guard = 0; guard < 4 * n; ++guard) {
+        std::vector<int> disp;
+        for (int p = 0; p < n; ++p)
+            if (pl.at[p] != p) disp.push_back(p);
+        if (disp.empty()) break;
+        std::vector<int> Pp;
+        for (int p = 0; p < kC; ++p) Pp.push_back(p);
+        auto has = [&](int p) { return std::find(Pp.begin(), Pp.end(), p) != Pp.end(); };
+        for (int p0 : disp) {
+            int p = p0;
+            while ((int)Pp.size() < kT && !has(p)) {
+                Pp.push_back(p);
+                p = pl.at[p];   // the home of the qubit at p is position at[p]
+            }
+            if ((int)Pp.size() >= kT) break;
+        }
+        for (int p = 0; p < n && (int)Pp.size() < kT; ++p)
+            if (!has(p)) Pp.push_back(p);
+        PassRec r;
+        r.S = 0;
+        for (int p : Pp) r.S |= 1ull << pl.at[p];
+        r.phys_in = pl.phys;
+        // qubits whose home is in the tile go home; the others take the free tile positions
+        std::vector<int> qs;
+        for (int p : Pp) qs.push_back(pl.at[p]);
+        std::vector<int> freep;
+        std::vector<uint8_t> taken(n, 0);
+        for (int q : qs)
+            if (has(q)) taken[q] = 1;
+        for (int p : Pp)
+            if (!taken[p]) freep.push_back(p);
+        size_t fi = 0;
+        for (int q : qs) pl.phys[q] = has(q) ? q : freep[fi++];
+        for (int q : qs) pl.at[pl.phys[q]] = q;
+        r.phys_out = pl.phys;
+        recs.push_back(std::move(r));
+        ++P.fixup_passes;
+    }
+    for (int p = 0; p < n; ++p)
+        if (pl.at[p] != p) fail(PTSBE_ERR_INVALID, "dense planner could not restore logical order");
+
+    // --- blocks, groups and tables of every pass ---
+    std::vector<uint32_t> op_site(c.ops.size(), UINT32_MAX);
+    for (uint32_t s = 0; s < c.site_op.size(); ++s) op_site[c.site_op[s]] = s;
+    P.site_block.assign(c.site_op.size(), UINT32_MAX);
+    P.blk_op_off.push_back(0);
+    for (size_t j = 0; j < recs.size(); ++j) {
+        const PassRec& r = recs[j];
+        std::vector<int> pos, tbit;
+        tile_positions(r.S, r.phys_in, pos, tbit, n);
+        // fuse
+        struct TB {
+            int nq;
+            uint32_t qa, qb;
+            std::vector<uint32_t> ops;
+            bool alive;
+        };
+        std::vector<TB> bl;
+        std::vector<int> open(n, -1);
+        for (uint32_t i : r.ops) {
+            const OpQ& o = pl.ops[i];
+            if (o.nq == 1) {
+                const int b = open[o.q0];
+                if (b >= 0) bl[b].ops.push_back(i);
+                else { bl.push_back(TB{1, o.q0, o.q0, {i}, true}); open[o.q0] = (int)bl.size() - 1; }
+                continue;
+            }
+            const int bx = open[o.q0], by = open[o.q1];
+            if (bx >= 0 && bx == by) { bl[bx].ops.push_back(i); continue; }
+            TB nb{2, o.q0, o.q1, {}, true};
+            if (bx >= 0 && bl[bx].nq == 1) { nb.ops = bl[bx].ops; bl[bx].alive = false; }
+            if (by >= 0 && bl[by].nq == 1) {
+                nb.ops.insert(nb.ops.end(), bl[by].ops.begin(), bl[by].ops.end());
+                bl[by].alive = false;
+            }
+            nb.ops.push_back(i);
+            bl.push_back(std::move(nb));
+            open[o.q0] = open[o.q1] = (int)bl.size() - 1;
+        }
+        std::vector<int> order;
+        for (size_t b = 0; b < bl.size(); ++b)
+            if (bl[b].alive) {
+                // an absorbed block's operations were appended out of circuit order; circuit order
+                // restricted to a block's operations is a valid order for its product
+                std::sort(bl[b].ops.begin(), bl[b].ops.end());
+                order.push_back((int)b);
+            }
+        auto tmask = [&](const TB& b) {
+            uint32_t m = 1u << tbit[b.qa];
+            if (b.nq == 2) m |= 1u << tbit[b.qb];
+            return m;
+        };
+        Pass ps{};
+        ps.group_begin = (uint32_t)P.groups.size();
+        ps.blk_begin = (uint32_t)P.blocks.size();
+        ps.nops = (uint32_t)r.ops.size();
+        std::vector<uint8_t> used(order.size(), 0);
+        size_t left = order.size();
+        while (left > 0) {
+            uint32_t G = 0, blocked = 0;
+            std::vector<int> chosen;
+            for (size_t x = 0; x < order.size(); ++x) {
+                if (used[x]) continue;
+                const uint32_t m = tmask(bl[order[x]]);
+                if (m & blocked) { blocked |= m; continue; }
+                if (pop(G | m) <= kR) { G |= m; chosen.push_back((int)x); }
+                else blocked |= m;
+            }
+            for (int x : chosen) used[x] = 1;
+            left -= chosen.size();
+            // register bits: G, padded with the tile bits of the most common residue mod 4
+            std::vector<int> R;
+            for (int t = 0; t < kT; ++t)
+                if ((G >> t) & 1u) R.push_back(t);
+            while ((int)R.size() < kR) {
+                int cntres[4] = {0, 0, 0, 0};
+                for (int t = 0; t < kT; ++t)
+                    if (std::find(R.begin(), R.end(), t) == R.end()) ++cntres[t & 3];
+                int pick = -1;
+                for (int t = kT - 1; t >= 0; --t) {
+                    if (std::find(R.begin(), R.end(), t) != R.end()) continue;
+                    if (pick < 0 || cntres[t & 3] > cntres[pick & 3]) pick = t;
+                }
+                R.push_back(pick);
+            }
+            std::sort(R.begin(), R.end());
+            // thread bits: lanes 0..3 on tile bits of distinct residues mod 4 (distinct banks)
+            std::vector<int> rest;
+            for (int t = 0; t < kT; ++t)
+                if (std::find(R.begin(), R.end(), t) == R.end()) rest.push_back(t);
+            std::vector<int> tb;
+            bool res_used[4] = {false, false, false, false};
+            for (int t : rest)
+                if ((int)tb.size() < 4 && !res_used[t & 3]) { tb.push_back(t); res_used[t & 3] = true; }
+            for (int t : rest)
+                if (std::find(tb.begin(), tb.end(), t) == tb.end()) tb.push_back(t);
+            Group g{};
+            for (int k = 0; k < kTB; ++k) g.toff[k] = (uint16_t)swz(1u << tb[k]);
+            for (int jj = 0; jj < kAmps; ++jj) {
+                uint32_t t = 0;
+                for (int mbit = 0; mbit < kR; ++mbit)
+                    if ((jj >> mbit) & 1) t |= 1u << R[mbit];
+                g.roff[jj] = (uint16_t)swz(t);
+            }
+            g.blk_begin = (uint32_t)P.blocks.size();
+            for (int x : chosen) {
+                const TB& b = bl[order[x]];
+                const uint32_t id = (uint32_t)P.blocks.size();
+                Block B{};
+                B.id = id;
+                const int ia = (int)(std::find(R.begin(), R.end(), tbit[b.qa]) - R.begin());
+                uint8_t swap = 0;
+                if (b.nq == 1) {
+                    B.code = (uint8_t)ia;
+                } else {
+                    const int ib = (int)(std::find(R.begin(), R.end(), tbit[b.qb]) - R.begin());
+                    B.code = (uint8_t)(4 + pair_index(std::min(ia, ib), std::max(ia, ib)));
+                    swap = ia < ib ? 1 : 0;
+                }
+                P.blocks.push_back(B);
+                P.blk_nq.push_back((uint8_t)b.nq);
+                P.blk_qa.push_back(b.qa);
+                P.blk_qb.push_back(b.qb);
+                P.blk_swap.push_back(swap);
+                P.blk_pass.push_back((uint32_t)j);
+                for (uint32_t op : b.ops) {
+                    P.blk_ops.push_back(op);
+                    if (op_site[op] != UINT32_MAX) P.site_block[op_site[op]] = id;
+                }
+                P.blk_op_off.push_back((uint32_t)P.blk_ops.size());
+            }
+            g.blk_end = (uint32_t)P.blocks.size();
+            P.groups.push_back(g);
+        }
+        ps.group_end = (uint32_t)P.groups.size();
+        ps.blk_end = (uint32_t)P.blocks.size();
+        // tables: input offsets of tile bits [kC, kT); output order
+        ps.hi_off = (uint32_t)P.hi.size();
+        for (int h = 0; h < kHi; ++h) {
+            uint32_t o = 0;
+            for (int b = 0; b < kT - kC; ++b)
+                if ((h >> b) & 1) o |= 1u << pos[kC + b];
+            P.hi.push_back(o);
+        }
+        std::vector<int> rho(kT);   // output rank -> tile bit
+        for (int q = 0; q < n; ++q) {
+            if (!((r.S >> q) & 1u)) continue;
+            const int rank = (int)(std::lower_bound(pos.begin(), pos.end(), r.phys_out[q]) - pos.begin());
+            if (rank >= kT || pos[rank] != r.phys_out[q]) fail(PTSBE_ERR_INVALID, "dense planner moved a qubit out of its tile");
+            rho[rank] = tbit[q];
+        }
+        ps.omap_off = (uint32_t)P.omap.size();
+        for (int h = 0; h < kHi; ++h) {
+            uint32_t t = 0;
+            for (int b = 0; b < kT - kC; ++b)
+                if ((h >> b) & 1) t |= 1u << rho[kC + b];
+            P.omap.push_back((uint16_t)t);
+        }
+        for (int x = 0; x < (1 << kC); ++x) {
+            uint32_t t = 0;
+            for (int b = 0; b < kC; ++b)
+                if ((x >> b) & 1) t |= 1u << rho[b];
+            ps.olow[x] = (uint16_t)t;
+        }
+        ps.nouter = 0;
+        for (int p = 0; p < n; ++p)
+            if (!std::binary_search(pos.begin(), pos.end(), p)) ps.opos[ps.nouter++] = (uint8_t)p;
+        P.passes.push_back(ps);
+    }
+    // default matrices
+    for (uint32_t b = 0; b < P.blocks.size(); ++b) {
+        const int cnt = P.blk_nq[b] == 1 ? 4 : 16;
+        P.blocks[b].mat = (uint32_t)P.mats.size();
+        P.mats.resize(P.mats.size() + cnt);
+        dense_block_matrix(c, P, b, nullptr, nullptr, 0, &P.mats[P.blocks[b].mat]);
+    }
+    // gates applied per pass (prefix-reuse accounting)
+    P.pass_gates.assign(P.passes.size(), 0);
+    for (size_t j = 0; j < recs.size(); ++j)
+        for (uint32_t i : recs[j].ops)
+            if (c.ops[i].kind == PTSBE_OP_GATE) ++P.pass_gates[j];
+    for (uint32_t s = 0; s < c.site_op.size(); ++s)
+        if (P.site_block[s] == UINT32_MAX) fail(PTSBE_ERR_INVALID, "dense planner left a noise site out");
+    P.built = true;
+}
+
+}  // namespace ptsbe

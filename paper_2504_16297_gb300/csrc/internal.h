@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ptsbe.h"
+#include "dense.cuh"
 
 namespace ptsbe {
 
@@ -211,6 +212,38 @@ struct BwPlan {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Dense tile passes (dense.cuh): the circuit cut into passes over kT-bit tiles, each pass's
+// operators fused into 1- and 2-qubit blocks and grouped by register bits. Built on first use.
+// ---------------------------------------------------------------------------------------------
+struct DensePlan {
+    bool built = false;
+    int n = 0;
+    std::vector<dense::Pass> passes;
+    std::vector<dense::Group> groups;
+    std::vector<dense::Block> blocks;         // execution order; blocks[i].id == i
+    std::vector<uint32_t> hi;
+    std::vector<uint16_t> omap;
+    std::vector<float2> mats;                 // default block matrices (every site at Kraus operator 0)
+    // host records for the per-set override blocks
+    std::vector<uint32_t> site_block;         // noise site -> block id
+    std::vector<uint32_t> blk_pass;           // block id -> pass
+    std::vector<uint32_t> blk_op_off;         // block id -> its ops [blk_op_off[b], blk_op_off[b+1]) in blk_ops
+    std::vector<uint32_t> blk_ops;
+    std::vector<uint8_t> blk_nq;              // 1 or 2
+    std::vector<uint32_t> blk_qa, blk_qb;     // logical qubits; block basis index 2 bit(qa) + bit(qb)
+    std::vector<uint8_t> blk_swap;            // kernel local index = bit(qa) + 2 bit(qb) (else 2 bit(qa) + bit(qb))
+    std::vector<uint32_t> pass_gates;         // gates applied by each pass (prefix-reuse accounting)
+    uint32_t fixup_passes = 0;                // trailing passes that only restore logical order
+    void* dev = nullptr;                      // device copy (one allocation)
+    const dense::Pass* d_passes = nullptr;
+    const dense::Group* d_groups = nullptr;
+    const dense::Block* d_blocks = nullptr;
+    const uint32_t* d_hi = nullptr;
+    const uint16_t* d_omap = nullptr;
+    const float2* d_mats = nullptr;
+};
+
+// ---------------------------------------------------------------------------------------------
 // Host-side circuit and Kraus-set records.
 // ---------------------------------------------------------------------------------------------
 using cd = std::complex<double>;
@@ -260,6 +293,7 @@ struct Circuit {
     Plan plan_pershot;               // Algorithm 1 plan (stage break before every general site)
     Plan plan_frame;                 // deferred-frame plan (mixing directions inside each tile)
     BwPlan bw;                       // adjoint backward plan (built on the first backward call)
+    DensePlan dense;                 // dense tile passes (built on first use)
     bool pershot_planned = false;
     bool frame_planned = false;
     bool op_planned = false;         // per-operator plan (sweep and register-blocked kernels) built
@@ -296,6 +330,11 @@ void register_ops(Circuit& c, const ptsbe_op* ops, uint64_t n_ops, const double*
 void build_device_ops(Circuit& c);
 Plan make_plan(const Circuit& c, int tile_bits, bool pershot);
 Plan make_frame_plan(const Circuit& c, int tile_bits);
+void make_dense_plan(const Circuit& c, DensePlan& P);
+// Matrix of block b (kernel layout, complex64) with Kraus operator ks[i] at site sites[i] (sites
+// inside the block, increasing) and operator 0 at its other sites.
+void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
+                        uint32_t len, float2* out);
 
 // ---------------------------------------------------------------------------------------------
 // Kernel launch interface (evolve.cu / sample.cu / pershot.cu).
@@ -468,6 +507,23 @@ struct BwArgs {
 };
 uint32_t backward_slots(int n, uint32_t count, int n_sm);
 void launch_backward(const BwArgs& a, cudaStream_t s);
+
+struct DenseArgs {
+    const dense::Pass* passes;
+    const dense::Group* groups;
+    const dense::Block* blocks;
+    const uint32_t* hi;
+    const uint16_t* omap;
+    const float2* mats;
+    const dense::Node* nodes;
+    uint32_t n_nodes;
+    const dense::Override* ovr;
+    const float2* opool;
+    int n, pass, last;
+    double* part;                    // last pass: [rows][2^(n - kT)] tile squared norms
+};
+void launch_dense_pass(const DenseArgs& a, int n_sm, cudaStream_t s);
+int dense_ctas_per_sm();
 
 int unique_max_qubits();
 size_t unique_bitmap_bytes(int n);

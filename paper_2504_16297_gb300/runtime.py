@@ -114,9 +114,10 @@ class Ptsbe:
 
     def set_evolve_kernel(self, kernel: str):
         """'auto' (= 'frame'), 'frame' (permutations and diagonals deferred; tile passes only for
-        operators that mix amplitudes), 'sweep' (one shared-memory pass per operator) or 'registers'."""
+        operators that mix amplitudes), 'sweep' (one shared-memory pass per operator), 'registers' or
+        'dense' (n > 12: register-blocked fused 1-/2-qubit blocks, one HBM pass per planned pass)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL,
-                              {"auto": 0, "sweep": 1, "registers": 2, "frame": 3}[kernel])
+                              {"auto": 0, "sweep": 1, "registers": 2, "frame": 3, "dense": 4}[kernel])
 
     def autotune(self, info: KrausSetInfo, first: int, count: int, states, weights, status, seed: int, bits,
                  prefix_reuse: bool = True, reps: int = 3):
@@ -125,9 +126,9 @@ class Ptsbe:
         flags = capi.PTSBE_EVOLVE_PREFIX_REUSE if prefix_reuse else 0
         t = capi.ptsbe_autotune(self.ctx, info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), flags,
                                 seed, _ptr(bits), bits.numel(), reps)
-        names = {1: "sweep", 2: "registers", 3: "frame"}
+        names = {1: "sweep", 2: "registers", 3: "frame", 4: "dense"}
         return {"evolve_kernel": names.get(t.evolve_kernel, t.evolve_kernel), "light_shots": t.light_shots,
-                "evolve_ms": {names[k]: t.evolve_ms[k] for k in (1, 2, 3)},
+                "evolve_ms": {names[k]: t.evolve_ms[k] for k in (1, 2, 3, 4) if t.evolve_ms[k] > 0},
                 "sample_ms": {int(t.light_candidates[i]): t.sample_ms[i] for i in range(4)}}
 
     def set_program_sets_per_warp(self, spw: int):
@@ -144,6 +145,10 @@ class Ptsbe:
     def timing(self, kernel_class: int, reset: bool = False):
         """(milliseconds, launches, algorithmic bytes) accumulated for one kernel class."""
         return capi.ptsbe_get_timing(self.ctx, kernel_class, reset)
+
+    def reuse_stats(self):
+        """(gates applied, gates without prefix reuse) of the last evolve call."""
+        return capi.ptsbe_reuse_stats(self.ctx)
 
     def circuit_info(self, cid):
         return capi.ptsbe_circuit_info(self.ctx, cid)
@@ -225,7 +230,8 @@ class Ptsbe:
     def evolve_sample(self, info: KrausSetInfo, first: int, count: int, states, weights, status, seed: int, bits,
                       prefix_reuse: bool = False):
         """evolve() then sample() in one call (same outputs); light states' shots are drawn by the last
-        evolve launch from the support it holds on chip."""
+        evolve launch from the support it holds on chip. states=None (n > 12): the states stay in
+        library buffers, prepared one branch at a time with dense passes (see ptsbe_evolve_sample)."""
         flags = capi.PTSBE_EVOLVE_PREFIX_REUSE if prefix_reuse else 0
         capi.ptsbe_evolve_sample(self.ctx, info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), flags,
                                  seed, _ptr(bits), bits.numel() if bits is not None else 0)

@@ -63,3 +63,28 @@ def check_shots(bits, psi, seed, alpha, first_shot, oracle_mod, n):
             assert dist <= BOUNDARY_TOL, f"shot {j}: gpu {got[j]} oracle {want[j]} |C/T-u| {dist:.2e}"
     assert len(bad) <= max(2, m // 1000), f"{len(bad)} boundary mismatches out of {m}"
     return len(bad)
+
+
+def _oracle_evolve_worker(args):
+    """Oracle state of one Kraus set given by its entries (run in a spawned worker process)."""
+    circ, entries, i = args
+    from oracle import oracle as o
+    O = o.Oracle(circ)
+    sets = O.pts_targeted([entries], shots=np.zeros(1, np.uint64))
+    psi, w, st = O.evolve(sets, 0)
+    return i, psi, w, st
+
+
+def oracle_states_parallel(circ, entries, idxs, workers=None):
+    """{i: (psi, w, status)} from the oracle for the sets `entries[i]`, i in idxs, evaluated in
+    parallel in processes started with spawn (safe after CUDA is initialised)."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    idxs = list(idxs)
+    workers = workers or max(1, min(len(idxs), (os.cpu_count() or 2)))
+    out = {}
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for i, psi, w, st in ex.map(_oracle_evolve_worker, [(circ, list(entries[i]), i) for i in idxs]):
+            out[i] = (psi, w, st)
+    return out
