@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "syndrome17_3rounds_top1e4_1e8shots"
+DENSE30_SETS = 96
 METRIC = "shots/s & gate-apply HBM GB/s, PTSBE batched vs per-shot trajectories, 1 GB300"
 
 
@@ -59,6 +60,10 @@ def parse():
     ap.add_argument("--uneven-only", action="store_true", help="run only the uneven batch and print its JSON object")
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
+    ap.add_argument("--dense30-sets", type=int, default=DENSE30_SETS,
+                    help="Kraus sets of the 30-qubit workload timed in the dense leg, a prefix of the trie "
+                         "(canonical) order (0 = skip the leg, -1 = the whole job)")
+    ap.add_argument("--dense30-only", action="store_true", help="run only the 30-qubit dense leg and print it")
     return ap.parse_args()
 
 
@@ -174,7 +179,7 @@ def inst_for(kernel: str, sets: int):
 # ----------------------------------------------------------------------------------------------
 # CPU oracle leg
 # ----------------------------------------------------------------------------------------------
-def oracle_estimate(budget_s: float, k: int, shots: int, seed: int):
+def oracle_estimate(budget_s: float, k: int, shots: int, seed: int, parts: dict | None = None):
     """Times the oracle on a bounded sample of the workload and extrapolates the whole job:
     top-K PTS once, state preparation of a few sets (each costs a full 17-qubit evolution), CDF
     construction and per-shot inverse-CDF draws. Returns (shots/s, description)."""
@@ -214,7 +219,123 @@ def oracle_estimate(budget_s: float, k: int, shots: int, seed: int):
     desc = (f"complex128 C oracle, 1 thread: top-{k} PTS once ({t_pts:.1f}s), {n_ev} of {sets.count} state "
             f"preparations ({t_ev / n_ev:.3f}s each), CDF build {t_cdf * 1e3:.1f} ms, {m} shots "
             f"({t_shot * 1e9:.0f} ns each); extrapolated to {sets.count} states + {shots} shots = {total:.0f}s")
+    if parts is not None:
+        parts.update(pts=t_pts, evolve=t_ev / n_ev, cdf=t_cdf, shot=t_shot)
     return shots / total, desc
+
+
+_ORC = {}
+
+
+def _orc_init(k, shots):
+    """Worker of the all-cores oracle timing: the oracle and its top-K sets, built once per process."""
+    from oracle import oracle as orc
+    from workloads import config
+    circ = config(1)["circuit"]
+    o = orc.Oracle(circ)
+    _ORC["o"] = o
+    _ORC["sets"] = o.pts_topk(k, shots)
+
+
+def _orc_evolve(i):
+    o, sets = _ORC["o"], _ORC["sets"]
+    o.evolve(sets, i % sets.count)
+    return i
+
+
+def oracle_all_cores(k: int, shots: int, budget_s: float, t_single: dict):
+    """The oracle as it stands, one process per host core (spawned), each preparing its share of
+    the Kraus sets of the same workload: measured state preparations per second over all cores,
+    extrapolated to the whole job like the one-thread estimate. Returns (shots/s, cores, desc)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    cores = os.cpu_count() or 1
+    with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"), initializer=_orc_init,
+                             initargs=(k, shots)) as ex:
+        list(ex.map(_orc_evolve, range(cores)))              # every worker initialised and warm
+        n = max(cores, int(budget_s / max(t_single["evolve"], 1e-3)) * cores // 2)
+        n = min(n, 16 * cores)
+        t0 = time.perf_counter()
+        list(ex.map(_orc_evolve, [(j * 7919) % k for j in range(n)], chunksize=1))
+        el = time.perf_counter() - t0
+    per_state = el / n
+    total = t_single["pts"] + k * (per_state + t_single["cdf"] / cores) + shots * t_single["shot"] / cores
+    desc = (f"complex128 C oracle, {cores} processes (one per host core, spawned): {n} state preparations in "
+            f"{el:.1f}s ({per_state * 1e3:.1f} ms per state over all cores); PTS once on one core "
+            f"({t_single['pts']:.1f}s); CDF and shot draws divided over the cores; extrapolated to {k} states + "
+            f"{shots} shots = {total:.0f}s")
+    return shots / total, cores, desc
+
+
+def result_errors(P, dev, info, states, weights, status, bits, seed, picks):
+    """Error of the GPU results against the FP64 oracle for sampled Kraus sets (outside the timed
+    region): relative 2-norm of the state, the largest relative error of any amplitude with
+    |psi|^2 >= 1e-6 and of its probability, the weight, and the shots that differ from the oracle
+    fed the GPU's own state (allowed only within 1e-6 of a CDF boundary)."""
+    from oracle import oracle as orc
+    from workloads import config
+    circ = config(1)["circuit"]
+    n = circ.n_qubits
+    o = orc.Oracle(circ)
+    out = []
+    w_h, s_h = weights.cpu().numpy(), status.cpu().numpy()
+    b_h = bits.cpu().numpy().view(np.uint32)
+    for i in picks:
+        ref = o.pts_targeted([info.entries(i)], shots=np.zeros(1, np.uint64))
+        psi, wr, sr = o.evolve(ref, 0)
+        g = states[i].cpu().numpy().astype(np.complex128)
+        e = {"set": int(i), "errors": len(info.entries(i)), "status": int(s_h[i]), "oracle_status": int(sr)}
+        if sr == 0:
+            e["state_rel_2norm"] = float(np.linalg.norm(g - psi) / np.linalg.norm(psi))
+            big = np.abs(psi) ** 2 >= 1e-6
+            e["amp_max_rel"] = float((np.abs(g[big] - psi[big]) / np.abs(psi[big])).max())
+            pg, pr = np.abs(g[big]) ** 2, np.abs(psi[big]) ** 2
+            e["prob_max_rel"] = float((np.abs(pg - pr) / pr).max())
+            e["weight_rel"] = float(abs(w_h[i] - wr) / wr)
+            o0, o1 = int(info.shot_offsets[i]), int(info.shot_offsets[i + 1])
+            m = min(o1 - o0, 200_000)
+            want = orc.sample(n, g, m, seed, int(i))
+            e["shots_checked"] = m
+            e["shots_differing"] = int(np.count_nonzero(want != b_h[o0:o0 + m]))
+        out.append(e)
+    return out
+
+
+def config0_ratio(P, dev, seed: int = 2000):
+    """Workload 0 (10-qubit brickwork, 20 layers, 1,000 proportional samples, 10^5 shots): PTSBE
+    (one call, prefix reuse) against the per-shot path (Algorithm 1) on the same GPU, same shots."""
+    import torch
+    from workloads import config
+    c = config(0)
+    circ = c["circuit"]
+    n = circ.n_qubits
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=c["seed"], nsamples=c["nsamples"], total_shots=c["total_shots"])
+    st = torch.empty((info.count, 1 << n), dtype=torch.complex64, device=dev)
+    w = torch.empty(info.count, dtype=torch.float64, device=dev)
+    s = torch.empty(info.count, dtype=torch.uint8, device=dev)
+    bits = torch.empty(info.total_shots, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    pt_ms = timed(lambda: P.evolve_sample(info, 0, info.count, st, w, s, seed, bits, prefix_reuse=True), 10)
+    m = info.total_shots
+    ps_bits = torch.empty(m, dtype=torch.int32, device=dev)
+    ps_ms = timed(lambda: P.pershot(cid, seed, 0, m, ps_bits), 2)
+    P.release_set(info)
+    P.release_circuit(cid)
+    return {"workload": c["name"], "sets": info.count, "shots": m, "ptsbe_ms": pt_ms, "pershot_ms": ps_ms,
+            "ptsbe_shots_per_s": m / (pt_ms / 1e3), "pershot_shots_per_s": m / (ps_ms / 1e3),
+            "ratio": ps_ms / pt_ms}
 
 
 def backward_leg(P, dev, reps: int = 3, cpu: bool = True, nsamples: int = 4096):
@@ -296,6 +417,114 @@ def uneven_leg(dev_index: int, streams: int = 4):
             "kind": "one context and stream per worker, circuits round-robin; not a single persistent launch"}
 
 
+def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
+    """The 30-qubit workload: brickwork, 60 layers (1,800 U3 + 870 CX), DEPOL1 after every U3 and
+    DEPOL2 after every CX at p = 5e-4, 2,000 proportional samples, 10^9 shots. States (8 GiB each)
+    are not returned: ptsbe_evolve_sample prepares the sets branch by branch with dense passes
+    (prefix reuse: sets share the state up to the pass of their first entry) and samples each from
+    its global-memory CDF. Timed with CUDA events on the launch stream: a prefix of the sets in
+    canonical (trie) order -- the error-free set, then the sets by first error site -- or the whole
+    job. The full job's schedule is planned (no device work) for its prefix-reuse savings."""
+    import torch
+    from workloads import config
+    from paper_2504_16297_gb300 import capi
+    c = config(3)
+    circ = c["circuit"]
+    n = circ.n_qubits
+    cid = P.register(circ)
+    t0 = time.perf_counter()
+    info = P.sample_kraus(cid, "proportional", seed=c["seed"], nsamples=c["nsamples"], total_shots=c["total_shots"])
+    t_pts = time.perf_counter() - t0
+    plan = P.dense_plan_info(cid)
+    full_applied, full_nominal = P.plan(info, 0, info.count)
+    count = info.count if max_sets < 0 else min(max_sets, info.count)
+    shots = int(info.shot_offsets[count])
+    w = torch.empty(count, dtype=torch.float64, device=dev)
+    s = torch.empty(count, dtype=torch.uint8, device=dev)
+    bits = torch.empty(max(shots, 1), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # warm-up: uploads, workspace, library buffers (one set)
+    P.evolve_sample(info, 0, 1, None, w, s, seed, bits)
+    torch.cuda.synchronize()
+    P.set_timing(True)
+    for k in range(8):
+        P.timing(k, reset=True)
+    clk = Clocks(clocks_index)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.evolve_sample(info, 0, count, None, w, s, seed, bits)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    applied, nominal = P.reuse_stats()
+    launches, fma = P.dense_work()
+    kern = {}
+    for cls, name in [(capi.PTSBE_TIMER_DENSE, "dense_pass"), (capi.PTSBE_TIMER_EVOLVE_FINALIZE, "finalize"),
+                      (capi.PTSBE_TIMER_SAMPLE, "sample"), (capi.PTSBE_TIMER_SAMPLE_LIGHT, "sample_light")]:
+        kms, kl, kb = P.timing(cls, reset=True)
+        if kl:
+            kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
+    P.set_timing(False)
+    null = int(s.sum().item())
+    # the traditional per-shot path on this workload: one trajectory prepared from |0...0> for one
+    # shot (for these unitary-mixture channels Algorithm 1's Kraus draws do not depend on the state,
+    # so a shot costs one full preparation); timed on the error-free trajectory
+    one = P.sample_kraus(cid, "targeted", targeted=[[]], targeted_shots=np.array([1], np.uint64))
+    b1 = torch.empty(1, dtype=torch.int32, device=dev)
+    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ps_ms = f0.elapsed_time(f1)
+    P.release_set(one)
+    hbm_peak, hbm_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12             # FP32 TFLOP/s: SMs x 128 FMA lanes x 2 x clock
+    d = kern.get("dense_pass")
+    dense = None
+    if d:
+        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        tfl = 2 * fma / (d["ms"] / 1e3) / 1e12
+        dense = {"ms": d["ms"], "launches": d["launches"], "algorithmic_bytes": d["bytes"],
+                 "gate_apply_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind,
+                 "fma": fma, "fp32_tflops": tfl, "alu_frac": tfl / alu_peak, "alu_peak_tflops": alu_peak,
+                 "alu_peak_kind": "derived: SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
+                 "ms_per_pass_launch": d["ms"] / d["launches"]}
+    est_s = None
+    if applied:
+        est_s = (ms / 1e3) * full_applied / applied
+    out = {"workload": c["name"], "qubits": n, "layers": 60, "gates": circ.n_gates, "noise_sites": circ.n_sites,
+           "sets_total": info.count, "sets_timed": count, "shots_total": info.total_shots, "shots_timed": shots,
+           "timed": "whole job" if count == info.count else f"first {count} of {info.count} sets in canonical (trie) order",
+           "ms": ms, "shots_per_s": shots / (ms / 1e3), "null_sets": null, "host_pts_s": t_pts,
+           "trajectory_gates_per_s": {"applied": applied / (ms / 1e3), "logical": count * circ.n_gates / (ms / 1e3)},
+           "prefix_reuse": {"timed_sets": {"gates_applied": applied, "gates_without_reuse": nominal,
+                                           "savings": 1 - applied / nominal if nominal else None},
+                            "full_job": {"gates_applied": full_applied, "gates_without_reuse": full_nominal,
+                                         "savings": 1 - full_applied / full_nominal if full_nominal else None}},
+           "plan": plan, "kernels": kern, "dense": dense,
+           "roofline": ({"bound": "alu", "kernel": "k_dense_pass", "achieved": dense["fp32_tflops"], "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": dense["alu_frac"]} if dense else None),
+           "roofline_hbm": ({"bound": "hbm", "kernel": "k_dense_pass", "achieved": dense["gate_apply_gbs"],
+                             "peak": hbm_peak, "unit": "GB/s", "frac": dense["hbm_frac"]} if dense else None),
+           "full_job_estimate_s": est_s,
+           "pershot": {"value": 1.0 / (ps_ms / 1e3), "unit": "shots/s", "ms_per_shot": ps_ms,
+                       "kind": "one full 30-qubit trajectory prepared per shot (dense passes, no reuse)"},
+           "speedup_vs_pershot": (shots / (ms / 1e3)) / (1.0 / (ps_ms / 1e3)),
+           "clocks": clocks}
+    P.release_set(info)
+    P.release_circuit(cid)
+    del bits, w, s
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -362,6 +591,14 @@ def main():
     if args.uneven_only:
         if rank == 0:
             print(json.dumps({"uneven": uneven_leg(local)}), flush=True)
+        return
+
+    if args.dense30_only:
+        dev = torch.device("cuda", local)
+        P = Ptsbe(device=local, stream=torch.cuda.current_stream(dev).cuda_stream)
+        d30 = dense30_leg(P, dev, args.dense30_sets, local)
+        if rank == 0:
+            print(json.dumps({"dense30": d30}), flush=True)
         return
 
     if args.backward_only:
@@ -510,11 +747,28 @@ def main():
         P.release_set(info)
         P.release_circuit(cid)
 
+    errors = None
+    c0 = None
+    if rank == 0:
+        cid = P.register(circ)
+        info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
+        P.evolve_sample(info, 0, K, states, weights[0], status[0], seed, bits[0], prefix_reuse=True)
+        torch.cuda.synchronize()
+        errors = result_errors(P, dev, info, states, weights[0], status[0], bits[0], seed,
+                               [0, 1, 2, K // 2, K - 1])
+        P.release_set(info)
+        P.release_circuit(cid)
+        c0 = config0_ratio(P, dev)
+
     bw = None
     if not args.no_backward:
         bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     unev = uneven_leg(local) if (args.uneven and rank == 0) else None
+
+    d30 = None
+    if args.dense30_sets != 0 and rank == 0:
+        d30 = dense30_leg(P, dev, args.dense30_sets, local)
 
     ms_step = ms / args.steps
     value = job_throughput(world, M, ms_step)
@@ -555,8 +809,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc = oracle_estimate(args.cpu_budget, K, M, seed)
-        cpu = {"value": v, "unit": "shots/s", "cores": 1, "kind": "oracle", "sample": desc}
+        parts = {}
+        v1, desc1 = oracle_estimate(args.cpu_budget, K, M, seed, parts)
+        try:
+            va, cores, desca = oracle_all_cores(K, M, args.cpu_budget, parts)
+        except Exception as e:          # no process pool on this host: the one-thread figure stands
+            va, cores, desca = v1, 1, f"all-cores run unavailable ({e}); {desc1}"
+        cpu = {"value": va, "unit": "shots/s", "cores": cores, "kind": "oracle", "sample": desca,
+               "single_thread": {"value": v1, "unit": "shots/s", "cores": 1, "sample": desc1}}
 
     if rank == 0:
         gate_ms = kern.get("evolve_stage", {}).get("ms")
@@ -581,7 +841,10 @@ def main():
             "clocks": clk,
             "backward": bw,
             "unique_shots": uniq,
+            "errors_vs_oracle": errors,
+            "config0_vs_pershot": c0,
             "uneven": unev,
+            "dense30": d30,
         }
         print(json.dumps(out), flush=True)
     if dist:

@@ -49,7 +49,8 @@ typedef enum {
     PTSBE_OK = 0,
     PTSBE_ERR_INVALID = 1,          /* malformed argument (bad id, qubit >= n, unsorted set ...) */
     PTSBE_ERR_NOT_CPTP = 2,         /* a channel violates sum_k K_k^dag K_k = I (Sec. 2.2)      */
-    PTSBE_ERR_OOM = 3,              /* host or device allocation failed; nothing was written     */
+    PTSBE_ERR_OOM = 3,              /* host or device allocation failed (before any kernel of the
+                                       call was enqueued: no output was written)                  */
     PTSBE_ERR_CUDA = 4,             /* a CUDA runtime call failed                                */
     PTSBE_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up                        */
     PTSBE_ERR_BUFFER_TOO_SMALL = 6, /* a caller buffer is smaller than the result                */
@@ -242,7 +243,12 @@ enum {
      * tile stages before the one holding its first extra site, starting there from the other
      * set's input of that stage instead of from |0...0>. Stages alternate between d_states and a
      * library workspace of the same size. */
-    PTSBE_EVOLVE_PREFIX_REUSE = 1u
+    PTSBE_EVOLVE_PREFIX_REUSE = 1u,
+    /* Plan only (dense passes: evolve kernel 4, or d_states NULL in ptsbe_evolve_sample): build the
+     * call's schedule (prefix reuse, branches) and set the counters of ptsbe_reuse_stats, but
+     * enqueue no device work and write no output; output pointers may be NULL. For sizing a job
+     * before running it. With another evolve kernel: PTSBE_ERR_UNSUPPORTED. */
+    PTSBE_EVOLVE_PLAN_ONLY = 2u
 };
 
 /* Prepares the states of sets [first, first + count) of set_id (each once, Sec. 3):
@@ -318,15 +324,18 @@ PTSBE_API int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * plans every byte up front, or a latency-critical loop that must not hit the device-wide
  * synchronisation a cudaFree implies. (The paper has no counterpart; this is an interface choice
  * of the library.) The call's scratch -- the work-item list for n <= 17, the CDF workspace for
- * 18 <= n <= 21 -- lives in a fixed 32 MiB device array compiled into the library, which every
+ * 18 <= n <= 21 -- lives in a fixed 40 MiB device array compiled into the library, which every
  * GPU that loads the library holds until the process exits; no cudaMalloc, cudaFree or other
- * allocating routine is called. Requests that need more (more than 2^20 work items, or n > 21)
- * return PTSBE_ERR_UNSUPPORTED with the sizes in the message. The first call on a device looks up
- * the array's device address (a one-time driver query): make that first call before any stream
- * capture. Every call shares the one array and overwrites what the previous call left there
- * (nothing is read before this call writes it); calls whose work can overlap on the GPU -- on
- * different streams or contexts of the same device -- race on it and must be serialised by the
- * caller. Arguments, layout and other errors as for ptsbe_sample_shots. */
+ * allocating routine is called. Requests that need more (more than 2^20 = 1,048,576 work items --
+ * a work item is a set, or a range of at least 65,536 of its shots -- or n > 21) return
+ * PTSBE_ERR_UNSUPPORTED with the sizes in the message. The first call on a device looks up the
+ * array's device address (a one-time driver query): make that first call before any stream
+ * capture. For n <= 17 the work items are copied from pageable host memory, so the call waits
+ * for the work already queued on the context stream before it returns. Every call shares the one
+ * array and overwrites what the previous call left there (nothing is read before this call writes
+ * it); calls whose work can overlap on the GPU -- on different streams or contexts of the same
+ * device -- race on it and must be serialised by the caller. Arguments, layout and other errors
+ * as for ptsbe_sample_shots. */
 PTSBE_API int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count,
                                          const void* d_states, const uint8_t* d_status, uint64_t seed,
                                          uint32_t* d_bits, uint64_t d_bits_capacity);
@@ -417,7 +426,14 @@ enum {
     /* Kraus sets whose frame programs one warp of the program prepass builds (one thread per set):
      * 4, 8 or 16 (0 = default, 8: measured). The builders branch on each set's entries, so fewer
      * sets per warp diverge less and leave more warps per scheduler. Same programs; speed only. */
-    PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
+    PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2,
+    /* Fault injection for tests (no GPU fault: the failure is made on the host): value k >= 0 makes
+     * the k-th allocation (0-based: device tables, workspace, pinned staging) the context attempts
+     * from now on fail as if memory ran out, so the call making it returns PTSBE_ERR_OOM; -1
+     * (default) turns it off. Every entry point but ptsbe_autotune (a series of calls) allocates
+     * before its first kernel launch, so a call that fails this way has written none of its
+     * outputs, and the context stays usable. */
+    PTSBE_OPT_FAIL_ALLOC = 3
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
@@ -462,6 +478,19 @@ PTSBE_API int ptsbe_h2d_bytes(uint64_t* bytes);
  * *gates_without_reuse = the circuit's gates times the number of sets. The savings are
  * 1 - applied / without. Either pointer may be NULL. Host-only. */
 PTSBE_API int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_t* gates_without_reuse);
+
+/* Work of the context's last call that ran dense passes (evolve kernel 4, or ptsbe_evolve_sample
+ * without states): *pass_launches = passes run summed over the states they ran for; *fma = the
+ * FP32 multiply-adds of those passes' fused blocks (a 2x2 complex block 8 per amplitude, a 4x4
+ * block 16 per amplitude), the algorithmic arithmetic for an ALU roofline. Host-only. */
+PTSBE_API int ptsbe_dense_work(ptsbe_ctx* ctx, uint64_t* pass_launches, double* fma);
+
+/* The dense-pass plan of a circuit (built if needed; n > 12, else PTSBE_ERR_UNSUPPORTED): passes
+ * (of which fixup_passes only restore logical qubit order at the end), fused 1- and 2-qubit
+ * blocks, and FP32 multiply-adds per amplitude of one full preparation. Any pointer may be NULL.
+ * Host-only. */
+PTSBE_API int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes, uint32_t* fixup_passes,
+                                    uint64_t* blocks_1q, uint64_t* blocks_2q, double* fma_per_amplitude);
 
 /* Kernel classes of the timing counters. */
 enum {

@@ -17,9 +17,11 @@ PTSBE_OP_GATE, PTSBE_OP_NOISE = 0, 1
  PTSBE_PTS_PREDICATE) = range(6)
 PTSBE_SHOTS_BY_COUNT, PTSBE_SHOTS_UNIFORM, PTSBE_SHOTS_BY_PROB, PTSBE_SHOTS_GIVEN = range(4)
 PTSBE_EVOLVE_PREFIX_REUSE = 1
+PTSBE_EVOLVE_PLAN_ONLY = 2
 PTSBE_OPT_EVOLVE_KERNEL = 0
 PTSBE_OPT_LIGHT_SHOTS = 1
 PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
+PTSBE_OPT_FAIL_ALLOC = 3
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
  PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE) = range(8)
 
@@ -106,6 +108,9 @@ _PROTOS = {
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_reuse_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "ptsbe_dense_work": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
+    "ptsbe_dense_plan_info": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                        C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
     "ptsbe_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "ptsbe_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "ptsbe_get_timing": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64),
@@ -262,6 +267,19 @@ def ptsbe_reuse_stats(ctx):
     a, f = C.c_uint64(), C.c_uint64()
     check(ctx, load().ptsbe_reuse_stats(ctx, C.byref(a), C.byref(f)))
     return a.value, f.value
+
+
+def ptsbe_dense_work(ctx):
+    n, f = C.c_uint64(), C.c_double()
+    check(ctx, load().ptsbe_dense_work(ctx, C.byref(n), C.byref(f)))
+    return n.value, f.value
+
+
+def ptsbe_dense_plan_info(ctx, circuit_id):
+    p, fx, b1, b2, f = C.c_uint32(), C.c_uint32(), C.c_uint64(), C.c_uint64(), C.c_double()
+    check(ctx, load().ptsbe_dense_plan_info(ctx, circuit_id, C.byref(p), C.byref(fx), C.byref(b1), C.byref(b2),
+                                            C.byref(f)))
+    return p.value, fx.value, b1.value, b2.value, f.value
 
 
 def ptsbe_set_option(ctx, option: int, value: int):

@@ -22,6 +22,8 @@ void cuda_check(cudaError_t e, const char* what) {
 
 size_t sample_global_scratch_doubles(int n);
 size_t noalloc_scratch_bytes();
+size_t noalloc_max_items();
+int noalloc_max_qubits();
 void* noalloc_scratch(int device);
 
 static std::atomic<uint64_t> g_launches{0};
@@ -56,10 +58,12 @@ struct ptsbe_ctx {
     std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
     uint32_t next_circuit = 1, next_set = 1;
-    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support;
+    DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support, sitems;
     DevBuf dense_tabs, stream_status;          // dense passes: per-call node/override tables; status when the caller passes none
     std::vector<DevBuf> state_pool;            // dense passes without caller states: branch state buffers
     uint64_t reuse_gates_run = 0, reuse_gates_full = 0;   // last evolve call: gates applied / without prefix reuse
+    uint64_t dense_launches = 0;               // last evolve call with dense passes: pass launches (set x pass)
+    double dense_fma = 0;                      // ... and the FP32 multiply-adds their blocks perform
     std::vector<unsigned char> host_blob;
     std::vector<SampleItem> noalloc_items;
     bool timing = false;
@@ -125,7 +129,17 @@ struct ptsbe_ctx {
     Slot slots[kSlots];
     size_t next_slot = 0;
 
+    // Test hook (PTSBE_OPT_FAIL_ALLOC): the allocation with index fail_alloc_at, counted from when
+    // the option was set, fails as if the device or host were out of memory.
+    int64_t fail_alloc_at = -1;
+    uint64_t alloc_count = 0;
+    void inject(const char* what) {
+        if (fail_alloc_at >= 0 && alloc_count++ == (uint64_t)fail_alloc_at)
+            fail(PTSBE_ERR_OOM, std::string("injected allocation failure: ") + what);
+    }
+
     void* dalloc(size_t bytes) {
+        inject("device table");
         void* p = nullptr;
         const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
         if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "device table allocation failed"); }
@@ -136,20 +150,31 @@ struct ptsbe_ctx {
     }
     // Stream-ordered copy of `bytes` host bytes to dst through the oldest staging slot (its
     // previous copy was issued kSlots copies ago; waiting for it is normally immediate).
+    // Grows staging slot `sl` to hold `bytes` (pinned host memory).
+    void grow_slot(Slot& sl, size_t bytes) {
+        if (sl.cap >= bytes) return;
+        if (sl.used) PTSBE_CUDA(cudaEventSynchronize(sl.ev));
+        inject("pinned staging");
+        if (sl.p) PTSBE_CUDA(cudaFreeHost(sl.p));   // synchronises the device: rare (large uploads)
+        sl.p = nullptr;
+        sl.cap = 0;
+        size_t cap = kSlotMin;
+        while (cap < bytes) cap *= 2;
+        const cudaError_t e = cudaHostAlloc((void**)&sl.p, cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); sl.p = nullptr; sl.cap = 0; fail(PTSBE_ERR_OOM, "pinned staging allocation failed"); }
+        sl.cap = cap;
+    }
+    // The next k copies through h2d find slots of at least `bytes`, so a call that reserves before
+    // its first launch allocates nothing after it.
+    void reserve_staging(size_t bytes, size_t k) {
+        for (size_t i = 0; i < k && i < kSlots; ++i) grow_slot(slots[(next_slot + i) % kSlots], bytes);
+    }
     void h2d(void* dst, const void* src, size_t bytes) {
         if (!bytes) return;
         Slot& sl = slots[next_slot];
         next_slot = (next_slot + 1) % kSlots;
         if (sl.used) PTSBE_CUDA(cudaEventSynchronize(sl.ev));
-        if (sl.cap < bytes) {
-            if (sl.p) PTSBE_CUDA(cudaFreeHost(sl.p));   // synchronises the device: rare (large uploads)
-            sl.p = nullptr;
-            size_t cap = kSlotMin;
-            while (cap < bytes) cap *= 2;
-            const cudaError_t e = cudaHostAlloc((void**)&sl.p, cap, cudaHostAllocDefault);
-            if (e != cudaSuccess) { (void)cudaGetLastError(); sl.p = nullptr; sl.cap = 0; fail(PTSBE_ERR_OOM, "pinned staging allocation failed"); }
-            sl.cap = cap;
-        }
+        grow_slot(sl, bytes);
         if (!sl.ev) PTSBE_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
         std::memcpy(sl.p, src, bytes);
         PTSBE_CUDA(cudaMemcpyAsync(dst, sl.p, bytes, cudaMemcpyHostToDevice, stream));
@@ -174,6 +199,7 @@ struct ptsbe_ctx {
     // Grows a workspace buffer; waits for in-flight work that may still use the old one.
     void* ws(DevBuf& b, size_t bytes) {
         if (bytes <= b.cap && b.p) return b.p;
+        inject("workspace");
         PTSBE_CUDA(cudaStreamSynchronize(stream));
         if (b.p) { PTSBE_CUDA(cudaFree(b.p)); b.p = nullptr; b.cap = 0; }
         const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
@@ -364,6 +390,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         evolve_dense_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags);
         return;
     }
+    if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel (n > 12)");
     ensure_set_on_device(ctx, s);
     const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
     if (frame && !c.frame_planned) {
@@ -539,6 +566,13 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         A.support_out = (unsigned char*)ctx->ws(ctx->support, (size_t)n_export * slot_bytes);
     }
     if (fuse && (fused_shots || n_export)) A.fault = ctx->fault_word();
+    // the support sampler's work items go up before the first launch (every allocation of the
+    // call precedes its kernels)
+    SupportItem* d_sitems = nullptr;
+    if (!support_items.empty()) {
+        d_sitems = (SupportItem*)ctx->ws(ctx->sitems, support_items.size() * sizeof(SupportItem));
+        ctx->h2d(d_sitems, support_items.data(), support_items.size() * sizeof(SupportItem));
+    }
     const double sbytes = 8.0 * (double)(1ull << c.n);
     // stage j writes out(j); out(J-1) is the caller's buffer. The per-operator kernels without
     // reuse read and write the caller's buffer in place (a tile is read whole before it is
@@ -596,8 +630,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     if (ob > 0 && !early_norm && A.sparse_final_stage < 0)
         ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2 * sbytes * count, [&] { launch_evolve_finalize(A, count, d_scale, ctx->stream); });
     if (!support_items.empty()) {
-        SupportItem* d_items = (SupportItem*)ctx->ws(ctx->items, support_items.size() * sizeof(SupportItem));
-        ctx->h2d(d_items, support_items.data(), support_items.size() * sizeof(SupportItem));
+        SupportItem* d_items = d_sitems;
         uint64_t heavy = 0;
         for (const SupportItem& it : support_items) heavy += it.j1 - it.j0;
         // algorithmic: each exported CDF read once per item + 4 B per shot
@@ -607,6 +640,17 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
                                   fused->bits, ctx->stream);
         });
     }
+}
+
+// Reserves what sample_range will allocate for `count` states (work items: at most one light
+// item per state plus chunks; at most 2 count + 4 SMs + 16 of them), so that a call that prepares
+// and samples allocates nothing after its first launch.
+void reserve_sampler(ptsbe_ctx* ctx, const Circuit& c, uint32_t count) {
+    const size_t items = 2 * (size_t)count + 4 * (size_t)std::max(ctx->n_sm, 1) + 16;
+    ctx->ws(ctx->items, items * sizeof(SampleItem));
+    if ((int)c.n > sample_cluster_max_qubits()) ctx->ws(ctx->scratch, sample_global_scratch_doubles((int)c.n) * 8);
+    // every staging slot: later copies of the call may land on any of them
+    ctx->reserve_staging(std::max(items * sizeof(SampleItem), ptsbe_ctx::kSlotMin), ptsbe_ctx::kSlots);
 }
 
 // Draws the shots of states [first, first + count) (the work of ptsbe_sample_shots), except those
@@ -642,6 +686,8 @@ void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
                 items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
     }
     const size_t nl = light.size(), nh = items.size();
+    if (n > sample_cluster_max_qubits())   // reserved before any launch of this call
+        A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
     if (nl + nh) {
         light.insert(light.end(), items.begin(), items.end());
         SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
@@ -662,7 +708,6 @@ void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         }
     }
     if (n > sample_cluster_max_qubits()) {
-        A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
         for (uint32_t a = 0; a < count; ++a) {
             const uint32_t alpha = first + a;
             const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
@@ -740,7 +785,11 @@ double dense_bytes(int n, uint32_t nodes, uint32_t fresh) {
 // such prefix that has computed its state at that pass), reading the parent's input of that pass.
 void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
                         double* d_weights, uint8_t* d_status, uint32_t flags) {
-    ensure_dense_plan(ctx, c);
+    if (flags & PTSBE_EVOLVE_PLAN_ONLY) {
+        if (!c.dense.built) make_dense_plan(c, c.dense);
+    } else {
+        ensure_dense_plan(ctx, c);
+    }
     const DensePlan& P = c.dense;
     const int n = (int)c.n;
     const uint32_t J = (uint32_t)P.passes.size();
@@ -792,6 +841,7 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
     total_gates = suffix[0];
     for (uint32_t a = 0; a < count; ++a) ctx->reuse_gates_run += suffix[sstage[a]];
     ctx->reuse_gates_full = (uint64_t)count * total_gates;
+    if (flags & PTSBE_EVOLVE_PLAN_ONLY) return;
 
     const size_t sb = (size_t)8 << n;
     float2* const user = (float2*)d_states;
@@ -830,12 +880,17 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
     A.ovr = (const dense::Override*)(d + o_o);
     A.opool = (const float2*)(d + o_p);
     A.part = part;
+    ctx->dense_launches = 0;
+    ctx->dense_fma = 0;
     for (uint32_t j = 0; j < J; ++j) {
         if (launches[j].second == 0) continue;
+        ctx->dense_launches += launches[j].second;
+        ctx->dense_fma += (double)P.pass_fma[j] * (double)(1ull << n) * launches[j].second;
         A.nodes = (const dense::Node*)(d + o_n) + launches[j].first;
         A.n_nodes = launches[j].second;
         A.pass = (int)j;
         A.last = j + 1 == J ? 1 : 0;
+        A.stage_bytes = P.passes[j].stage_bytes;
         ctx->timed(PTSBE_TIMER_DENSE, dense_bytes(n, A.n_nodes, fresh_cnt[j]), [&] { launch_dense_pass(A, ctx->n_sm, ctx->stream); });
     }
     EvolveArgs E{};
@@ -857,8 +912,12 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
 // holds exactly one set's state: it is normalised (weight, status) and sampled, and its buffer is
 // released. Live buffers never exceed the nesting depth of the branches plus one.
 void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, double* d_weights,
-                          uint8_t* d_status, uint64_t seed, uint32_t* d_bits) {
-    ensure_dense_plan(ctx, c);
+                          uint8_t* d_status, uint64_t seed, uint32_t* d_bits, bool plan_only) {
+    if (plan_only) {
+        if (!c.dense.built) make_dense_plan(c, c.dense);
+    } else {
+        ensure_dense_plan(ctx, c);
+    }
     const DensePlan& P = c.dense;
     const int n = (int)c.n;
     const uint32_t J = (uint32_t)P.passes.size();
@@ -940,6 +999,7 @@ void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, u
     for (uint32_t g : P.pass_gates) total_gates += g;
     ctx->reuse_gates_run = gates_run;
     ctx->reuse_gates_full = (uint64_t)count * total_gates;
+    if (plan_only) return;
 
     const size_t sb = (size_t)8 << n;
     if (ctx->state_pool.size() < (size_t)nbuf) ctx->state_pool.resize(nbuf);
@@ -966,6 +1026,7 @@ void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, u
     const int ob = n - dense::kT;
     double* part = (double*)ctx->ws(ctx->part, ((size_t)1 << ob) * sizeof(double));
     float* d_scale = (float*)ctx->ws(ctx->scale, sizeof(float));
+    reserve_sampler(ctx, c, 1);
     DenseArgs A = dense_args(P, n);
     A.ovr = (const dense::Override*)(d + o_o);
     A.opool = (const float2*)(d + o_p);
@@ -974,11 +1035,16 @@ void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, u
     const dense::Node* dn = (const dense::Node*)(d + o_n);
     const uint64_t base = s.shot_off[first];
     size_t ni = 0;
+    ctx->dense_launches = 0;
+    ctx->dense_fma = 0;
     for (const Act& x : acts) {
         if (x.pass < J) {
+            ctx->dense_launches += 1;
+            ctx->dense_fma += (double)P.pass_fma[x.pass] * (double)(1ull << n);
             A.nodes = dn + ni++;
             A.pass = (int)x.pass;
             A.last = x.pass + 1 == J ? 1 : 0;
+            A.stage_bytes = P.passes[x.pass].stage_bytes;
             ctx->timed(PTSBE_TIMER_DENSE, dense_bytes(n, 1, x.src < 0 ? 1 : 0), [&] { launch_dense_pass(A, ctx->n_sm, ctx->stream); });
             continue;
         }
@@ -1041,28 +1107,36 @@ int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
 
 int ptsbe_destroy(ptsbe_ctx* ctx) {
     if (!ctx) return PTSBE_ERR_INVALID;
-    if (ctx->has_device()) {
+    int status = PTSBE_OK;
+    // Every free is attempted even after a failed one (a device error left by an earlier kernel
+    // makes them all fail); nothing throws out of this call.
+    if (ctx->has_device()) try {
+        auto qfree = [&](void* p) {
+            if (p && cudaFreeAsync(p, ctx->stream) != cudaSuccess) status = PTSBE_ERR_CUDA;
+        };
         cudaSetDevice(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) status = PTSBE_ERR_CUDA;
         for (auto& kv : ctx->circuits) {
-            free_device_circuit(ctx, kv.second->dev); free_device_circuit(ctx, kv.second->dev_pershot);
-            free_device_circuit(ctx, kv.second->dev_frame);
-            ctx->dfree(kv.second->bw.dev);
-            ctx->dfree(kv.second->dense.dev);
+            qfree(kv.second->dev.base); qfree(kv.second->dev_pershot.base); qfree(kv.second->dev_frame.base);
+            qfree(kv.second->bw.dev); qfree(kv.second->dense.dev);
         }
-        for (auto& kv : ctx->sets) ctx->dfree(kv.second->d_site);   // d_k shares the allocation
+        for (auto& kv : ctx->sets) qfree(kv.second->d_site);   // d_k shares the allocation
         cudaStreamSynchronize(ctx->stream);
         ctx->free_staging();
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
         ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault); ctx->free_buf(ctx->support);
-        ctx->free_buf(ctx->dense_tabs); ctx->free_buf(ctx->stream_status);
+        ctx->free_buf(ctx->dense_tabs); ctx->free_buf(ctx->stream_status); ctx->free_buf(ctx->sitems);
         for (DevBuf& b : ctx->state_pool) ctx->free_buf(b);
         ctx->free_timers();
+    } catch (const Error& e) {
+        status = e.status;
+    } catch (...) {
+        status = PTSBE_ERR_CUDA;
     }
     delete ctx;
-    return PTSBE_OK;
+    return status;
 }
 
 int ptsbe_set_stream(ptsbe_ctx* ctx, void* cuda_stream) {
@@ -1189,9 +1263,10 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
         Circuit& c = ctx->circuit(s.circuit);
         if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
         if (count == 0) return;
-        if (!d_states) fail(PTSBE_ERR_INVALID, "d_states is NULL");
+        if (flags & ~(uint32_t)(PTSBE_EVOLVE_PREFIX_REUSE | PTSBE_EVOLVE_PLAN_ONLY)) fail(PTSBE_ERR_INVALID, "unknown flags");
+        const bool plan_only = flags & PTSBE_EVOLVE_PLAN_ONLY;
+        if (!d_states && !plan_only) fail(PTSBE_ERR_INVALID, "d_states is NULL");
         if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
-        if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
         evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, nullptr, nullptr);
     });
 }
@@ -1227,8 +1302,14 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
         if ((uint64_t)first + count > s.count()) fail(PTSBE_ERR_INVALID, "set range out of bounds");
         if (count == 0) return;
         if ((uintptr_t)d_states % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
-        if (flags & ~(uint32_t)PTSBE_EVOLVE_PREFIX_REUSE) fail(PTSBE_ERR_INVALID, "unknown flags");
+        if (flags & ~(uint32_t)(PTSBE_EVOLVE_PREFIX_REUSE | PTSBE_EVOLVE_PLAN_ONLY)) fail(PTSBE_ERR_INVALID, "unknown flags");
+        const bool plan_only = flags & PTSBE_EVOLVE_PLAN_ONLY;
         const uint64_t total = s.shot_off[first + count] - s.shot_off[first];
+        if (plan_only) {
+            if (!d_states && (int)c.n > dense::kT) stream_evolve_sample(ctx, s, c, first, count, nullptr, nullptr, seed, nullptr, true);
+            else evolve_range(ctx, s, c, first, count, d_states, nullptr, nullptr, flags, nullptr, nullptr);
+            return;
+        }
         if (total && !d_bits) fail(PTSBE_ERR_INVALID, "null device pointer");
         if (d_bits_capacity < total) fail(PTSBE_ERR_BUFFER_TOO_SMALL, "d_bits holds " + std::to_string(d_bits_capacity) +
                                                                           " shots, the range needs " + std::to_string(total));
@@ -1237,11 +1318,13 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
             if ((int)c.n <= dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "d_states may be NULL only for n > 12 (dense passes)");
             ctx->use_device();
             ensure_set_on_device(ctx, s);
-            stream_evolve_sample(ctx, s, c, first, count, d_weights, d_status, seed, d_bits);
+            stream_evolve_sample(ctx, s, c, first, count, d_weights, d_status, seed, d_bits, false);
             return;
         }
         std::vector<uint8_t> drawn;
         const FusedShots fs{seed, d_bits};
+        ctx->use_device();
+        if (total) reserve_sampler(ctx, c, count);
         evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, total ? &fs : nullptr, &drawn);
         if (total) sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, &drawn);
     });
@@ -1286,6 +1369,10 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         } else if (option == PTSBE_OPT_LIGHT_SHOTS) {
             if (value < 0) fail(PTSBE_ERR_INVALID, "light-sampler shot limit must be >= 0");
             ctx->light_shots = (uint64_t)value;
+        } else if (option == PTSBE_OPT_FAIL_ALLOC) {
+            if (value < -1) fail(PTSBE_ERR_INVALID, "allocation failure index must be >= -1");
+            ctx->fail_alloc_at = value;
+            ctx->alloc_count = 0;
         } else if (option == PTSBE_OPT_PROGRAM_SETS_PER_WARP) {
             if (value != 0 && value != 4 && value != 8 && value != 16) fail(PTSBE_ERR_INVALID, "sets per warp must be 0, 4, 8 or 16");
             ctx->prog_sets_per_warp = value ? (int)value : 8;
@@ -1406,6 +1493,32 @@ int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_t* gates_w
     });
 }
 
+int ptsbe_dense_work(ptsbe_ctx* ctx, uint64_t* pass_launches, double* fma) {
+    return guarded(ctx, [&] {
+        if (pass_launches) *pass_launches = ctx->dense_launches;
+        if (fma) *fma = ctx->dense_fma;
+    });
+}
+
+int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes, uint32_t* fixup_passes,
+                          uint64_t* blocks_1q, uint64_t* blocks_2q, double* fma_per_amplitude) {
+    return guarded(ctx, [&] {
+        Circuit& c = ctx->circuit(circuit_id);
+        if ((int)c.n <= dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need n > 12");
+        if (!c.dense.built) make_dense_plan(c, c.dense);
+        const DensePlan& P = c.dense;
+        uint64_t b1 = 0, b2 = 0;
+        for (uint8_t q : P.blk_nq) (q == 1 ? b1 : b2) += 1;
+        double f = 0;
+        for (uint32_t x : P.pass_fma) f += x;
+        if (passes) *passes = (uint32_t)P.passes.size();
+        if (fixup_passes) *fixup_passes = P.fixup_passes;
+        if (blocks_1q) *blocks_1q = b1;
+        if (blocks_2q) *blocks_2q = b2;
+        if (fma_per_amplitude) *fma_per_amplitude = f;
+    });
+}
+
 int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                                const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity) {
     return guarded(ctx, [&] {
@@ -1441,16 +1554,18 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
                 for (uint64_t j0 = 0; j0 < m; j0 += chunk)
                     items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
             }
-            if (items.size() * sizeof(SampleItem) > cap)
+            if (items.size() > noalloc_max_items() || items.size() * sizeof(SampleItem) > cap)
                 fail(PTSBE_ERR_UNSUPPORTED, "range needs " + std::to_string(items.size()) + " work items; the fixed scratch holds " +
-                                                std::to_string(cap / sizeof(SampleItem)));
+                                                std::to_string(noalloc_max_items()));
             ctx->use_device();
             SampleItem* d_items = (SampleItem*)noalloc_scratch(ctx->device);
+            // A copy from pageable host memory: no allocation, but the driver first waits for the
+            // work already queued on the stream (documented in the header).
             PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
             launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream);
         } else {
             const size_t need = sample_global_scratch_doubles(n) * 8;
-            if (need > cap)
+            if (n > noalloc_max_qubits() || need > cap)
                 fail(PTSBE_ERR_UNSUPPORTED, std::to_string(n) + "-qubit states need " + std::to_string(need) +
                                                 " bytes of CDF workspace; the fixed scratch holds " + std::to_string(cap) +
                                                 " (at most 21 qubits)");
@@ -1666,6 +1781,10 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
         R.n = n; R.states = A.states; R.status = nullptr; R.seed = seed;
         const bool cluster = n <= sample_cluster_max_qubits();
         if (!cluster) R.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
+        if (cluster) {   // the readout work items of every batch: allocated before the first launch
+            ctx->ws(ctx->items, (size_t)batch * sizeof(SampleItem));
+            ctx->reserve_staging((size_t)batch * sizeof(SampleItem), (size_t)((n_shots + batch - 1) / batch));
+        }
         std::vector<SampleItem> items;
         for (uint64_t b0 = 0; b0 < n_shots; b0 += batch) {
             const uint32_t cnt = (uint32_t)std::min<uint64_t>(batch, n_shots - b0);

@@ -32,11 +32,15 @@ constexpr int kR = 4;                           // register bits per thread (16 
 constexpr int kTB = kT - kR;                    // thread-index bits
 constexpr int kThreads = 1 << kTB;              // 256 threads per CTA
 constexpr int kAmps = 1 << kR;                  // amplitudes per thread
+constexpr int kCodes1 = kR;                     // block codes 0 .. kR-1: 2x2 on one register bit
+constexpr int kStageMax = 24 * 1024;            // a pass's descriptors + matrices staged in shared memory
+                                                // when they fit in this many bytes
 constexpr int kHi = 1 << (kT - kC);             // entries of a pass's high-offset table
 constexpr int kMaxQ = 32;
 
 // One fused operator of a pass. code 0..3: 2x2 on register bit `code`; code 4..9: 4x4 on the
-// register pair kPairs[code - 4] = (lo, hi), local index bit(lo) + 2 bit(hi).
+// register pair number code - 4 = (lo, hi) of (0,1) (0,2) (0,3) (1,2) (1,3) (2,3), local index
+// bit(lo) + 2 bit(hi).
 struct Block {
     uint8_t code;
     uint8_t pad[3];
@@ -65,6 +69,8 @@ struct Pass {
     uint8_t opos[kMaxQ];                        // outer bit k -> physical position (ascending)
     uint32_t nouter;
     uint32_t nops;                              // circuit operations this pass applies
+    uint32_t mat_begin, mat_end;                // the pass's default matrices (float2 pool range)
+    uint32_t stage_bytes;                       // groups + blocks + matrices, 0 when above kStageMax
 };
 
 // A (set, pass) launch entry: where the tile comes from and goes to, and the set's override blocks.
@@ -81,19 +87,25 @@ struct Override {
     uint32_t mat;                               // float2 offset into the override pool (4 or 16 entries)
 };
 
-// Register pairs of the 4x4 codes.
-PTSBE_HD int pair_lo(int p) { return p < 3 ? 0 : (p < 5 ? 1 : 2); }
-PTSBE_HD int pair_hi(int p) { return p < 3 ? p + 1 : (p < 5 ? p - 1 : 3); }
+
+// Shared-memory staging of a pass (groups, then blocks, then default matrices, each 16-byte aligned).
+PTSBE_HD uint32_t dense_align16(uint32_t x) { return (x + 15u) & ~15u; }
+PTSBE_HD uint32_t dense_stage_blocks_off(const Pass& p) { return dense_align16((p.group_end - p.group_begin) * (uint32_t)sizeof(Group)); }
+PTSBE_HD uint32_t dense_stage_mats_off(const Pass& p) {
+    return dense_stage_blocks_off(p) + dense_align16((p.blk_end - p.blk_begin) * (uint32_t)sizeof(Block));
+}
+PTSBE_HD uint32_t dense_stage_bytes(const Pass& p) {
+    return dense_stage_mats_off(p) + (p.mat_end - p.mat_begin) * (uint32_t)sizeof(float2);
+}
 
 // XOR swizzle of a tile address (kT = 12): the float2 bank pair of address t is bits 0..3 of the
 // result, and tile bit p contributes unit vector p mod 4 to them.
 PTSBE_HD uint32_t swz(uint32_t t) { return t ^ ((t >> 4) & 15u) ^ ((t >> 8) & 15u); }
 
-#ifdef __CUDA_ARCH__
-PTSBE_HD float4 ldm(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-#else
+// Block matrices come from shared memory (a staged pass) or from global memory (override blocks,
+// unstaged passes): a plain generic load serves both (the read-only global path must not be used
+// on a shared-memory address).
 PTSBE_HD float4 ldm(const float2* p) { return *reinterpret_cast<const float4*>(p); }
-#endif
 
 // out = a * x + b * y (complex)
 PTSBE_HD float2 cmac2(float2 a, float2 x, float2 b, float2 y) {
@@ -132,13 +144,22 @@ PTSBE_HD void apply2(float2* v, const float2* m) {
     for (int j = 0; j < kAmps; ++j) {
         if (j & ((1 << L) | (1 << H))) continue;
         const int i1 = j | (1 << L), i2 = j | (1 << H), i3 = j | (1 << L) | (1 << H);
-        const float2 x0 = v[j], x1 = v[i1], x2 = v[i2], x3 = v[i3];
+        const float2 x[4] = {v[j], v[i1], v[i2], v[i3]};
         float2 o[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const float2 a = cmac2(M[4 * r], x0, M[4 * r + 1], x1);
-            const float2 b = cmac2(M[4 * r + 2], x2, M[4 * r + 3], x3);
-            o[r] = make_float2(a.x + b.x, a.y + b.y);
+            // one multiply-add chain per component: 16 operations per output
+            float re = M[4 * r].x * x[0].x, im = M[4 * r].x * x[0].y;
+            re -= M[4 * r].y * x[0].y;
+            im += M[4 * r].y * x[0].x;
+#pragma unroll
+            for (int l = 1; l < 4; ++l) {
+                re += M[4 * r + l].x * x[l].x;
+                im += M[4 * r + l].x * x[l].y;
+                re -= M[4 * r + l].y * x[l].y;
+                im += M[4 * r + l].y * x[l].x;
+            }
+            o[r] = make_float2(re, im);
         }
         v[j] = o[0]; v[i1] = o[1]; v[i2] = o[2]; v[i3] = o[3];
     }

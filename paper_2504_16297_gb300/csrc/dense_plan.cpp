@@ -169,9 +169,15 @@ void op_matrix(const Circuit& c, uint32_t op, uint32_t k, cd* m, int& dim) {
     dim = (int)ch.dim;
 }
 
+// Number of the register pair (lo, hi), lo < hi < kR, in the order (0,1) (0,2) .. (0,kR-1) (1,2) ..
 int pair_index(int lo, int hi) {
-    static const int idx[4][4] = {{-1, 0, 1, 2}, {-1, -1, 3, 4}, {-1, -1, -1, 5}, {-1, -1, -1, -1}};
-    return idx[lo][hi];
+    int k = 0;
+    for (int a = 0; a < kR; ++a)
+        for (int b = a + 1; b < kR; ++b) {
+            if (a == lo && b == hi) return k;
+            ++k;
+        }
+    fail(PTSBE_ERR_INVALID, "bad register pair");
 }
 
 }  // namespace
@@ -423,7 +429,7 @@ void make_dense_plan(const Circuit& c, DensePlan& P) {
                     B.code = (uint8_t)ia;
                 } else {
                     const int ib = (int)(std::find(R.begin(), R.end(), tbit[b.qb]) - R.begin());
-                    B.code = (uint8_t)(4 + pair_index(std::min(ia, ib), std::max(ia, ib)));
+                    B.code = (uint8_t)(kCodes1 + pair_index(std::min(ia, ib), std::max(ia, ib)));
                     swap = ia < ib ? 1 : 0;
                 }
                 P.blocks.push_back(B);
@@ -476,14 +482,22 @@ void make_dense_plan(const Circuit& c, DensePlan& P) {
             if (!std::binary_search(pos.begin(), pos.end(), p)) ps.opos[ps.nouter++] = (uint8_t)p;
         P.passes.push_back(ps);
     }
-    // default matrices
+    // default matrices, in block order: each pass's matrices are one contiguous range
     for (uint32_t b = 0; b < P.blocks.size(); ++b) {
         const int cnt = P.blk_nq[b] == 1 ? 4 : 16;
         P.blocks[b].mat = (uint32_t)P.mats.size();
         P.mats.resize(P.mats.size() + cnt);
         dense_block_matrix(c, P, b, nullptr, nullptr, 0, &P.mats[P.blocks[b].mat]);
     }
+    for (Pass& ps : P.passes) {
+        ps.mat_begin = ps.blk_begin < ps.blk_end ? P.blocks[ps.blk_begin].mat : 0;
+        ps.mat_end = ps.blk_begin < ps.blk_end ? P.blocks[ps.blk_end - 1].mat + (P.blk_nq[ps.blk_end - 1] == 1 ? 4 : 16) : 0;
+        const size_t bytes = dense_stage_bytes(ps);
+        ps.stage_bytes = bytes <= (size_t)kStageMax ? (uint32_t)bytes : 0u;
+    }
     // gates applied per pass (prefix-reuse accounting)
+    P.pass_fma.assign(P.passes.size(), 0);
+    for (uint32_t b = 0; b < P.blocks.size(); ++b) P.pass_fma[P.blk_pass[b]] += P.blk_nq[b] == 1 ? 8 : 16;
     P.pass_gates.assign(P.passes.size(), 0);
     for (size_t j = 0; j < recs.size(); ++j)
         for (uint32_t i : recs[j].ops)

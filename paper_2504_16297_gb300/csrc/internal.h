@@ -233,6 +233,8 @@ struct DensePlan {
     std::vector<uint32_t> blk_qa, blk_qb;     // logical qubits; block basis index 2 bit(qa) + bit(qb)
     std::vector<uint8_t> blk_swap;            // kernel local index = bit(qa) + 2 bit(qb) (else 2 bit(qa) + bit(qb))
     std::vector<uint32_t> pass_gates;         // gates applied by each pass (prefix-reuse accounting)
+    std::vector<uint32_t> pass_fma;           // FP32 multiply-adds per amplitude of each pass's blocks
+                                              // (a 2x2 block 8, a 4x4 block 16: complex products of 4)
     uint32_t fixup_passes = 0;                // trailing passes that only restore logical order
     void* dev = nullptr;                      // device copy (one allocation)
     const dense::Pass* d_passes = nullptr;
@@ -521,6 +523,7 @@ struct DenseArgs {
     const float2* opool;
     int n, pass, last;
     double* part;                    // last pass: [rows][2^(n - kT)] tile squared norms
+    uint32_t stage_bytes;            // dynamic shared memory: the pass's staged tables (0: read from global)
 };
 void launch_dense_pass(const DenseArgs& a, int n_sm, cudaStream_t s);
 int dense_ctas_per_sm();

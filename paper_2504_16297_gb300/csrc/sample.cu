@@ -594,7 +594,17 @@ void launch_cluster(const SampleArgs& a, const SampleItem* items, uint32_t n_ite
 // Fixed scratch for ptsbe_sample_shots_noalloc: every GPU that loads the library holds these
 // bytes until the process exits. In host code the name is only a stand-in for the symbol; the
 // device address comes from cudaGetSymbolAddress, looked up once per device below.
-constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+// Sized for its two uses: 2^20 work items of the cluster sampler (n <= 17), or the global-memory
+// CDF workspace of one 21-qubit state (n = 18 .. 21).
+constexpr size_t kNoAllocMaxItems = (size_t)1 << 20;
+constexpr int kNoAllocMaxQubits = 21;
+constexpr size_t kNoAllocCdfBytes =
+    (((size_t)1 << kNoAllocMaxQubits) + 3 * ((size_t)1 << (kNoAllocMaxQubits - kSliceBits)) + 8) * 8;
+constexpr size_t kNoAllocScratchBytes =
+    ((kNoAllocMaxItems * sizeof(SampleItem) > kNoAllocCdfBytes ? kNoAllocMaxItems * sizeof(SampleItem) : kNoAllocCdfBytes)
+     + 255) & ~(size_t)255;
+static_assert(kNoAllocScratchBytes >= kNoAllocMaxItems * sizeof(SampleItem) && kNoAllocScratchBytes >= kNoAllocCdfBytes,
+              "the fixed scratch holds 2^20 work items and a 21-qubit CDF");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -604,6 +614,8 @@ void* g_noalloc_ptr[kMaxDevices] = {};
 }  // namespace
 
 size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+size_t noalloc_max_items() { return kNoAllocMaxItems; }
+int noalloc_max_qubits() { return kNoAllocMaxQubits; }
 
 // Device address of the fixed scratch on `device`, which must be the current device. The first
 // call on a device resolves the symbol (a driver call that is not a stream operation, so it has to

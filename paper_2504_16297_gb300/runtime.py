@@ -150,6 +150,21 @@ class Ptsbe:
         """(gates applied, gates without prefix reuse) of the last evolve call."""
         return capi.ptsbe_reuse_stats(self.ctx)
 
+    def dense_work(self):
+        """(pass launches, FP32 multiply-adds) of the last call that ran dense passes."""
+        return capi.ptsbe_dense_work(self.ctx)
+
+    def dense_plan_info(self, cid):
+        p, fx, b1, b2, f = capi.ptsbe_dense_plan_info(self.ctx, cid)
+        return {"passes": p, "fixup_passes": fx, "blocks_1q": b1, "blocks_2q": b2, "fma_per_amplitude": f}
+
+    def plan(self, info: KrausSetInfo, first: int, count: int):
+        """Schedule of ptsbe_evolve_sample without states for the range, without running it; returns
+        (gates applied, gates without prefix reuse)."""
+        capi.ptsbe_evolve_sample(self.ctx, info.set_id, first, count, None, None, None, capi.PTSBE_EVOLVE_PLAN_ONLY,
+                                 0, None, 0)
+        return capi.ptsbe_reuse_stats(self.ctx)
+
     def circuit_info(self, cid):
         return capi.ptsbe_circuit_info(self.ctx, cid)
 

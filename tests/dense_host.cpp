@@ -23,6 +23,7 @@ namespace {
 
 Circuit g_circ;
 DensePlan g_plan;
+int g_stage_errors = 0;     // staged passes whose size disagrees with the staging offsets
 
 // One pass of one state, in place (a tile is read whole before it is written).
 void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>& ovr, const std::vector<float2>& opool) {
@@ -32,6 +33,22 @@ void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>&
     std::vector<float2> tile(1u << kT);
     const uint32_t* hi = &P.hi[ps.hi_off];
     const uint16_t* omap = &P.omap[ps.omap_off];
+    // the kernel's shared-memory staging of the pass (same offsets), or the plan's arrays
+    std::vector<unsigned char> stage(ps.stage_bytes + 16);
+    const Group* groups = &P.groups[ps.group_begin];
+    const Block* blocks = &P.blocks[ps.blk_begin];
+    const float2* mats = &P.mats[ps.mat_begin];
+    if (ps.stage_bytes) {
+        unsigned char* base = stage.data();
+        while ((uintptr_t)base % 16) ++base;
+        std::memcpy(base, groups, (ps.group_end - ps.group_begin) * sizeof(Group));
+        std::memcpy(base + dense_stage_blocks_off(ps), blocks, (ps.blk_end - ps.blk_begin) * sizeof(Block));
+        std::memcpy(base + dense_stage_mats_off(ps), mats, (ps.mat_end - ps.mat_begin) * sizeof(float2));
+        if (dense_stage_mats_off(ps) + (ps.mat_end - ps.mat_begin) * sizeof(float2) != ps.stage_bytes) ++g_stage_errors;
+        groups = reinterpret_cast<const Group*>(base);
+        blocks = reinterpret_cast<const Block*>(base + dense_stage_blocks_off(ps));
+        mats = reinterpret_cast<const float2*>(base + dense_stage_mats_off(ps));
+    }
     for (uint64_t tau = 0; tau < (1ull << ob); ++tau) {
         const uint64_t outer = outer_offset(ps, tau);
         for (uint32_t tid = 0; tid < (uint32_t)kThreads; ++tid)
@@ -44,8 +61,8 @@ void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>&
             }
         size_t ov = 0;
         while (ov < ovr.size() && ovr[ov].block < ps.blk_begin) ++ov;
-        for (uint32_t gi = ps.group_begin; gi < ps.group_end; ++gi) {
-            const Group& G = P.groups[gi];
+        for (uint32_t gi = 0; gi < ps.group_end - ps.group_begin; ++gi) {
+            const Group& G = groups[gi];
             // the override cursor is uniform over the CTA: every thread sees the same blocks
             const size_t ov0 = ov;
             for (uint32_t tid = 0; tid < (uint32_t)kThreads; ++tid) {
@@ -53,9 +70,9 @@ void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>&
                 const uint32_t base = group_base(G, tid);
                 alignas(16) float2 v[kAmps];
                 for (int jj = 0; jj < kAmps; ++jj) v[jj] = tile[base ^ G.roff[jj]];
-                for (uint32_t b = G.blk_begin; b < G.blk_end; ++b) {
-                    const Block& B = P.blocks[b];
-                    const float2* m = &P.mats[B.mat];
+                for (uint32_t b = G.blk_begin - ps.blk_begin; b < G.blk_end - ps.blk_begin; ++b) {
+                    const Block& B = blocks[b];
+                    const float2* m = mats + (B.mat - ps.mat_begin);
                     if (ov < ovr.size() && ovr[ov].block == B.id) { m = &opool[ovr[ov].mat]; ++ov; }
                     apply_block(v, B.code, m);
                 }
@@ -94,8 +111,8 @@ int dh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
     }
 }
 
-// out[0..7]: passes, fix-up passes, groups, blocks, operations placed, operations placed more than
-// once or never, 2-qubit blocks, gates
+// out[0..9]: passes, fix-up passes, groups, blocks, operations placed, operations placed more than
+// once or never, 2-qubit blocks, gates, passes staged in shared memory, staging size mismatches
 void dh_stats(uint64_t* out) {
     const DensePlan& P = g_plan;
     std::vector<int> seen(g_circ.ops.size(), 0);
@@ -114,6 +131,10 @@ void dh_stats(uint64_t* out) {
     out[5] = bad;
     out[6] = two;
     out[7] = gates;
+    uint64_t staged = 0;
+    for (const Pass& ps : P.passes) staged += ps.stage_bytes != 0;
+    out[8] = staged;
+    out[9] = (uint64_t)g_stage_errors;
 }
 
 // Prepares the state of one Kraus set (entries sorted by site) from |0...0> through every pass, as

@@ -67,9 +67,9 @@ def register(dh, circ):
 
 
 def stats(dh):
-    out = (C.c_uint64 * 8)()
+    out = (C.c_uint64 * 10)()
     dh.dh_stats(out)
-    keys = ["passes", "fixup", "groups", "blocks", "placed", "misplaced", "blocks2", "gates"]
+    keys = ["passes", "fixup", "groups", "blocks", "placed", "misplaced", "blocks2", "gates", "staged", "stage_errors"]
     return dict(zip(keys, [int(x) for x in out]))
 
 
@@ -110,6 +110,8 @@ def test_brickwork_sets_match_oracle(dh, oracle_mod, n, layers):
     assert passes >= 2
     sets = oracle_mod.Oracle(circ).pts_proportional(30, 11, total_shots=300)
     compare(dh, oracle_mod, circ, sets, range(min(sets.count, 8)))
+    st = stats(dh)
+    assert st["staged"] > 0 and st["stage_errors"] == 0
 
 
 def test_deep_brickwork_many_passes(dh, oracle_mod):
@@ -176,6 +178,7 @@ def test_thirty_qubit_plan(dh):
     assert st["misplaced"] == 0 and st["placed"] == circ.n_ops
     assert st["gates"] == circ.n_gates
     assert passes <= 40
+    assert st["staged"] == passes - st["fixup"] and st["stage_errors"] == 0
     mean = C.c_double()
     bad = dh.dh_bank_stats(C.byref(mean))
     assert mean.value >= 14.0, (bad, mean.value)

@@ -254,7 +254,7 @@ def test_autotune_keeps_results(oracle_mod):
     torch.cuda.synchronize()
     before = bits.cpu().numpy().copy()
     res = P.autotune(info, 0, info.count, st, w, s, 77, bits, reps=1)
-    assert res["evolve_kernel"] in ("frame", "sweep", "registers")
+    assert res["evolve_kernel"] in ("frame", "sweep", "registers", "dense")
     assert res["light_shots"] in res["sample_ms"]
     assert all(v > 0 for v in res["evolve_ms"].values()) and all(v > 0 for v in res["sample_ms"].values())
     st2, w2, s2 = evolve_gpu(P, info, 0, info.count, n, True)

@@ -3,8 +3,8 @@
 Unitary-mixture channels: the Kraus choice of every site depends only on (seed, site, shot), so
 the labels are bit-identical to the oracle and outcomes differ only at CDF boundaries. General
 channels (amplitude damping): the branch probabilities come from the complex64 state, so a
-choice may flip where u sits within ~1e-6 of a cumulative boundary; almost all shots agree and
-the outcome distribution matches the density matrix."""
+choice may flip only where u sits within 1e-6 of a cumulative boundary of the oracle's branch
+probabilities (checked shot by shot), and the outcome distribution matches the density matrix."""
 import numpy as np
 import pytest
 from scipy import stats
@@ -63,14 +63,76 @@ def _damping_circuit(n, layers, seed):
     return b.build()
 
 
+def _uniform(oracle_mod, seed, c0, c1, c2, c3):
+    x = oracle_mod.philox([c0, c1, c2, c3], [seed & 0xFFFFFFFF, seed >> 32])
+    return oracle_mod.u53(int(x[0]), int(x[1]))
+
+
+def _prefix_state(oracle_mod, circ, upto_op, entries):
+    """Oracle state (normalised) of the circuit's first `upto_op` operations with the Kraus choices
+    `entries` at their sites."""
+    from workloads import Circuit
+    t = Circuit(circ.n_qubits, circ.op_ints[:upto_op], circ.op_params[:upto_op], circ.ch_ints, circ.ch_params,
+                circ.ch_kraus, circ.ch_kraus_off, circ.custom_gates)
+    o = oracle_mod.Oracle(t)
+    sets = o.pts_targeted([entries], shots=np.zeros(1, np.uint64))
+    psi, w, st = o.evolve(sets, 0)
+    return psi
+
+
+def _boundary_ok(C, u, a, b):
+    """u lies within BOUNDARY_TOL of every cumulative boundary between outcomes a and b."""
+    from gpu_common import BOUNDARY_TOL
+    lo, hi = sorted((int(a), int(b)))
+    return bool(np.all(np.abs(C[lo:hi] - u) <= BOUNDARY_TOL))
+
+
+def _damping_kraus(gamma):
+    return [np.array([[1, 0], [0, np.sqrt(1 - gamma)]]), np.array([[0, np.sqrt(gamma)], [0, 0]])]
+
+
 @pytest.mark.parametrize("n,layers,m", [(5, 3, 400), (15, 2, 80)])
 def test_general_channels_agree_with_oracle(P, oracle_mod, n, layers, m):
+    """Every shot agrees with the oracle except where a uniform sits within 1e-6 of a cumulative
+    boundary: at the first site whose Kraus choice differs (branch probabilities <psi|K_k^dag K_k|psi>
+    of the oracle's state before that site, Algorithm 1), or, with identical choices, at the
+    readout CDF of the final state."""
     circ = _damping_circuit(n, layers, seed=n)
-    got, gk = _run(P, circ, 23, 0, m)
-    want, wk = _oracle(oracle_mod, circ, 23, 0, m)
-    same_labels = np.all(gk == wk, axis=1)
-    assert same_labels.mean() >= 0.98
-    assert (got[same_labels] == want[same_labels]).mean() >= 0.98
+    seed = 23
+    got, gk = _run(P, circ, seed, 0, m)
+    want, wk = _oracle(oracle_mod, circ, seed, 0, m)
+    op_ints = np.asarray(circ.op_ints)
+    noise_ops = [i for i in range(circ.n_ops) if op_ints[i][0] == 1]
+    K = _damping_kraus(0.15)
+    flips = 0
+    for j in range(m):
+        diff = np.nonzero(gk[j] != wk[j])[0]
+        if len(diff):
+            s = int(diff[0])
+            op = noise_ops[s]
+            ch = int(op_ints[op][1])
+            assert int(circ.ch_ints[ch][0]) == 2, f"shot {j}: mixture site {s} chose differently"
+            q = int(op_ints[op][3])
+            entries = [(t, int(k)) for t, k in enumerate(wk[j][:s]) if k]
+            psi = _prefix_state(oracle_mod, circ, op, entries).reshape([2] * n)
+            ax = n - 1 - q
+            p = []
+            for Kk in K:
+                v = np.tensordot(Kk, psi, axes=([1], [ax]))
+                p.append(float(np.sum(np.abs(v) ** 2)))
+            C = np.cumsum(p) / np.sum(p)
+            u = _uniform(oracle_mod, seed, s, j & 0xFFFFFFFF, j >> 32, 3)
+            assert _boundary_ok(C, u, gk[j][s], wk[j][s]), f"shot {j}: site {s} u={u} C={C}"
+            flips += 1
+        elif got[j] != want[j]:
+            entries = [(t, int(k)) for t, k in enumerate(wk[j]) if k]
+            psi = _prefix_state(oracle_mod, circ, circ.n_ops, entries)
+            C = np.cumsum(np.abs(psi) ** 2)
+            C = C / C[-1]
+            u = _uniform(oracle_mod, seed, j & 0xFFFFFFFF, j >> 32, 0, 5)
+            assert _boundary_ok(C, u, got[j], want[j]), f"shot {j}: readout u={u}"
+            flips += 1
+    assert flips <= max(2, m // 50)
 
 
 def test_damping_histogram_matches_density_matrix(P):

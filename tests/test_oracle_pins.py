@@ -335,6 +335,59 @@ def test_literal_algorithm2(oracle_mod):
         assert len(sites) == len(set(sites))   # compatible(): one operator per site
 
 
+def _literal_law(circ):
+    """Exact law of Algorithm 2 as printed (Sec. 3.1): at each site every operator k >= 1 draws its
+    own uniform and succeeds with probability q_k, and compatible() keeps the first success in
+    listed order, so P(k) = q_k * prod_{1 <= j < k} (1 - q_j) and P(0) = prod_{j >= 1} (1 - q_j);
+    sites are independent. Exact rationals."""
+    import itertools
+    per_site = []
+    for i in range(circ.n_ops):
+        if circ.op_ints[i][0] != 1:
+            continue
+        ch = int(circ.op_ints[i][1])
+        q = densmat.exact_q(int(circ.ch_ints[ch][0]), Fraction(str(float(circ.ch_params[ch]))))
+        law, miss = [], Fraction(1)
+        for k in range(1, len(q)):
+            law.append(q[k] * miss)
+            miss *= 1 - q[k]
+        per_site.append([miss] + law)
+    out = {}
+    for combo in itertools.product(*[range(len(c)) for c in per_site]):
+        pr = Fraction(1)
+        for s, k in enumerate(combo):
+            pr *= per_site[s][k]
+        out[tuple((s, k) for s, k in enumerate(combo) if k)] = pr
+    return out
+
+
+def test_literal_algorithm2_outcome_law(oracle_mod):
+    """Frequencies of the printed Algorithm 2 against its exact law (chi-square). The law differs
+    from the channel's (DEPOL1 p = 0.3: P(1), P(2), P(3) = 0.1, 0.09, 0.081, not 0.1 each), so keeping
+    the last success instead of the first, or drawing one categorical per site, fails."""
+    from scipy import stats
+    circ = _few_site_circuit()
+    o = oracle_mod.Oracle(circ)
+    ns = 60000
+    sets = o.pts_literal(ns, 31, nshots=1)
+    law = _literal_law(circ)
+    assert sum(law.values()) == 1
+    got = {tuple(sets.entries(i)): int(sets.mult[i]) for i in range(sets.count)}
+    assert sum(got.values()) == ns and set(got) <= set(law)
+    big = [a for a, p in law.items() if p * ns >= 10]
+    obs = np.array([got.get(a, 0) for a in big] + [ns - sum(got.get(a, 0) for a in big)], float)
+    exp = np.array([float(law[a]) * ns for a in big] + [ns - sum(float(law[a]) * ns for a in big)])
+    keep = exp > 0
+    chi = float(((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum())
+    pval = stats.chi2.sf(chi, int(keep.sum()) - 1)
+    assert pval > 1e-3, f"chi-square p = {pval:.2e}"
+    # the channel's own law is rejected by the same data (the test has power)
+    chan = _exact_probabilities(circ)
+    exp2 = np.array([float(chan[a]) * ns for a in big] + [ns - sum(float(chan[a]) * ns for a in big)])
+    chi2 = float(((obs - exp2) ** 2 / np.maximum(exp2, 1e-9)).sum())
+    assert stats.chi2.sf(chi2, len(big)) < 1e-6
+
+
 _ORDER_CACHE = {}
 
 
@@ -543,3 +596,21 @@ def test_predicate_sets_against_full_enumeration(oracle_mod):
         assert got == want
     sets = o.pts_targeted(oracle_mod.predicate_sets(circ, max_errors=S, include_empty=True), total_shots=10)
     assert abs(float(np.sum(sets.q)) - 1.0) < 1e-12
+
+
+def test_predicate_sets_gate_filter_against_hand_table(oracle_mod):
+    """The gate_mask rule ("the gate a site follows" = the last gate before the site that shares one
+    of its qubits) against a table read off small_mixed_circuit by hand: site 7 (DEPOL1 on qubit 2)
+    comes right after SWAP(1, 0) but follows CZ(2, 1), the last gate on qubit 2."""
+    from workloads import GATE
+    circ = small_mixed_circuit()
+    follows = {0: "U3", 1: "U3", 2: "CX", 3: "RZ", 4: "H", 5: "CZ", 6: "RX", 7: "CZ"}
+    allc = [sorted(c) for c in densmat.all_kraus_sets(circ)]
+    for names, max_err in [(("CZ", "U3"), 2), (("SWAP", "H"), 3), (("CX", "RX", "RZ"), 1)]:
+        mask = 0
+        for g in names:
+            mask |= 1 << GATE[g]
+        eligible = {s for s, g in follows.items() if g in names}
+        got = sorted(tuple(x) for x in oracle_mod.predicate_sets(circ, max_errors=max_err, gate_mask=mask))
+        want = sorted(tuple(c) for c in allc if 1 <= len(c) <= max_err and all(s in eligible for s, _ in c))
+        assert got == want, names

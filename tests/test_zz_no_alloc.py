@@ -55,8 +55,82 @@ def test_noalloc_rejects_states_beyond_the_fixed_scratch():
     circ = brickwork(22, 1, 0.0, 0.0, seed=1)
     cid = P.register(circ)
     info = P.sample_kraus(cid, "targeted", targeted=[[]], targeted_shots=np.array([16], np.uint64))
-    states = torch.zeros(16, dtype=torch.complex64, device="cuda")     # never read: refused first
+    # a full-size state (32 MiB), so that even a refusal that regressed could only read valid memory
+    states = torch.zeros(1 << 22, dtype=torch.complex64, device="cuda")
     bits = torch.zeros(16, dtype=torch.int32, device="cuda")
     with pytest.raises(PtsbeError) as e:
         capi.ptsbe_sample_shots_noalloc(P.ctx, info.set_id, 0, 1, states.data_ptr(), None, 1, bits.data_ptr(), 16)
     assert e.value.status == 7 and "fixed scratch" in str(e.value)
+
+
+def test_noalloc_21_qubits_accepted():
+    """The largest state the fixed CDF workspace holds (21 qubits): accepted, same shots."""
+    from paper_2504_16297_gb300 import capi
+    P = gpu_ctx()
+    circ = brickwork(21, 1, 0.05, 0.05, seed=21)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=3, nsamples=8, total_shots=50_000)
+    count = min(info.count, 2)
+    states, w, status = evolve_gpu(P, info, 0, count, 21)
+    total = int(info.shot_offsets[count])
+    want = _shots(P, capi.ptsbe_sample_shots, info, count, states, status, 5, total)
+    got = _shots(P, capi.ptsbe_sample_shots_noalloc, info, count, states, status, 5, total)
+    assert np.array_equal(got, want)
+
+
+def test_noalloc_rejects_more_work_items_than_the_fixed_scratch():
+    """n <= 17 with more than 2^20 work items (one per set here): refused on the host before any
+    device work, and the message gives the real limit. One qubit with 40 depolarising sites at
+    p = 0.5 gives over a million distinct Kraus sets; their states (2 amplitudes each, 16 MiB in
+    all) are allocated in full, so a regressed refusal could only read valid memory."""
+    from paper_2504_16297_gb300 import capi
+    from paper_2504_16297_gb300.capi import PtsbeError
+    from workloads import CircuitBuilder
+    torch = torch_cuda()
+    P = gpu_ctx()
+    b = CircuitBuilder(1)
+    d1 = b.channel("DEPOL1", 0.5)
+    for _ in range(40):
+        b.gate("H", [0])
+        b.noise(d1, [0])
+    cid = P.register(b.build())
+    n_sets = (1 << 20) + 100
+    info = P.sample_kraus(cid, "proportional", seed=4, nsamples=n_sets + 4096, total_shots=n_sets + 4096,
+                          export=False)
+    assert info.count > (1 << 20)
+    states = torch.zeros((info.count, 2), dtype=torch.complex64, device="cuda")
+    bits = torch.zeros(info.total_shots, dtype=torch.int32, device="cuda")
+    with pytest.raises(PtsbeError) as e:
+        capi.ptsbe_sample_shots_noalloc(P.ctx, info.set_id, 0, info.count, states.data_ptr(), None, 1,
+                                        bits.data_ptr(), info.total_shots)
+    assert e.value.status == 7 and "1048576" in str(e.value)
+
+
+def test_noalloc_allocates_nothing():
+    """Repeated calls leave the device's free memory and the caching allocator's counters unchanged
+    (after one warm-up call, which may load the library's module and resolve the array address)."""
+    from paper_2504_16297_gb300 import capi
+    torch = torch_cuda()
+    P = gpu_ctx()
+    n = 19
+    circ = brickwork(n, 2, 0.02, 0.02, seed=319)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=5, nsamples=20, total_shots=100_000)
+    count = min(info.count, 4)
+    states, w, status = evolve_gpu(P, info, 0, count, n)
+    total = int(info.shot_offsets[count])
+    bits = torch.zeros(total, dtype=torch.int32, device="cuda")
+    call = lambda: capi.ptsbe_sample_shots_noalloc(P.ctx, info.set_id, 0, count, states.data_ptr(),
+                                                   status.data_ptr(), 9, bits.data_ptr(), total)
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    P.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    alloc1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0, (free0, free1)
+    assert alloc1 == alloc0
