@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "syndrome17_3rounds_top1e4_1e8shots"
-DENSE30_SETS = 96
+DENSE30_SETS = 48
 METRIC = "shots/s & gate-apply HBM GB/s, PTSBE batched vs per-shot trajectories, 1 GB300"
 
 
@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--backward-only", action="store_true",
                     help="run only the adjoint-backward measurement and print its JSON object")
     ap.add_argument("--backward-samples", type=int, default=4096)
-    ap.add_argument("--uneven", action="store_true",
-                    help="also run the uneven batch (512 brickwork circuits, 12-22 qubits, 64 samples each)")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the uneven batch (512 brickwork circuits, 12-22 qubits, 64 samples each)")
     ap.add_argument("--uneven-only", action="store_true", help="run only the uneven batch and print its JSON object")
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
@@ -316,6 +316,9 @@ def config0_ratio(P, dev, seed: int = 2000):
     s = torch.empty(info.count, dtype=torch.uint8, device=dev)
     bits = torch.empty(info.total_shots, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # the evolve kernel and sampler shot limit tuned on this workload (outside the timing), as for
+    # the main workload
+    tuning = P.autotune(info, 0, info.count, st, w, s, seed, bits, prefix_reuse=True, reps=2)
 
     def timed(fn, reps):
         fn()
@@ -333,7 +336,7 @@ def config0_ratio(P, dev, seed: int = 2000):
     ps_ms = timed(lambda: P.pershot(cid, seed, 0, m, ps_bits), 2)
     P.release_set(info)
     P.release_circuit(cid)
-    return {"workload": c["name"], "sets": info.count, "shots": m, "ptsbe_ms": pt_ms, "pershot_ms": ps_ms,
+    return {"workload": c["name"], "sets": info.count, "shots": m, "tuning": tuning, "ptsbe_ms": pt_ms, "pershot_ms": ps_ms,
             "ptsbe_shots_per_s": m / (pt_ms / 1e3), "pershot_shots_per_s": m / (ps_ms / 1e3),
             "ratio": ps_ms / pt_ms}
 
@@ -397,132 +400,101 @@ def backward_leg(P, dev, reps: int = 3, cpu: bool = True, nsamples: int = 4096):
     return out
 
 
-def uneven_leg(dev_index: int, streams: int = 4):
-    """The uneven batch: 512 brickwork circuits (n ~ U{12..22}, depth ~ U{10..40}), 64 proportional
-    samples each, shot budgets ~ LogUniform(1e3, 1e6), through UnevenBatch (4 contexts and
-    streams); evolve kernel per size from the autotuner (outside the timed run). Shots stay on the
-    device; the time covers host PTS, registration and all kernels."""
-    from paper_2504_16297_gb300.batch import UnevenBatch
+def uneven_leg(dev, reps: int = 2, margin_gb: float = 24.0):
+    """The uneven batch: 512 brickwork circuits (n ~ U{12..22}, depth ~ U{10..40}, DEPOL1 1e-3 after
+    every U3, DEPOL2 1e-2 after every CX), 64 proportional samples each, shot budgets
+    ~ LogUniform(1e3, 1e6). Registration, PTS and the batch plan run on the host once (timed
+    apart); every run is ONE persistent cooperative launch (a device work queue) that prepares all
+    28,769 states (181 GB of complex64) with dense passes, then the samplers draw the 7.08x10^7
+    shots. The run is captured as a CUDA graph and replayed; the timed region is `reps` replays,
+    CUDA events on the launch stream. If the device cannot hold every state at once, the circuits
+    are split into chunks, one launch (and graph) each, and the line says so."""
+    import torch
+    from paper_2504_16297_gb300.runtime import Ptsbe
     from workloads import config
     cfg = config(2)
     circs, shots = cfg["circuits"], cfg["shots"]
-    B = UnevenBatch(device=dev_index, streams=streams, max_qubits=max(c.n_qubits for c in circs),
-                    max_sets=cfg["nsamples"], max_shots=int(np.max(shots)))
-    kernels = B.autotune(circs, shots, cfg["nsamples"], cfg["seed"])
-    B.run(circs[:8], shots[:8], cfg["nsamples"], cfg["seed"])       # warm-up
-    secs, total, counts, _ = B.run(circs, shots, cfg["nsamples"], cfg["seed"])
-    return {"workload": cfg["name"], "circuits": len(circs), "sets": int(np.sum(counts)), "shots": int(total),
-            "seconds": secs, "shots_per_s": total / secs, "streams": streams,
-            "evolve_kernel_by_qubits": {str(k): v for k, v in sorted(kernels.items())},
-            "kind": "one context and stream per worker, circuits round-robin; not a single persistent launch"}
-
-
-def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
-    """The 30-qubit workload: brickwork, 60 layers (1,800 U3 + 870 CX), DEPOL1 after every U3 and
-    DEPOL2 after every CX at p = 5e-4, 2,000 proportional samples, 10^9 shots. States (8 GiB each)
-    are not returned: ptsbe_evolve_sample prepares the sets branch by branch with dense passes
-    (prefix reuse: sets share the state up to the pass of their first entry) and samples each from
-    its global-memory CDF. Timed with CUDA events on the launch stream: a prefix of the sets in
-    canonical (trie) order -- the error-free set, then the sets by first error site -- or the whole
-    job. The full job's schedule is planned (no device work) for its prefix-reuse savings."""
-    import torch
-    from workloads import config
-    from paper_2504_16297_gb300 import capi
-    c = config(3)
-    circ = c["circuit"]
-    n = circ.n_qubits
-    cid = P.register(circ)
-    t0 = time.perf_counter()
-    info = P.sample_kraus(cid, "proportional", seed=c["seed"], nsamples=c["nsamples"], total_shots=c["total_shots"])
-    t_pts = time.perf_counter() - t0
-    plan = P.dense_plan_info(cid)
-    full_applied, full_nominal = P.plan(info, 0, info.count)
-    count = info.count if max_sets < 0 else min(max_sets, info.count)
-    shots = int(info.shot_offsets[count])
-    w = torch.empty(count, dtype=torch.float64, device=dev)
-    s = torch.empty(count, dtype=torch.uint8, device=dev)
-    bits = torch.empty(max(shots, 1), dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    # warm-up: uploads, workspace, library buffers (one set)
-    P.evolve_sample(info, 0, 1, None, w, s, seed, bits)
+    # a stream of its own: the legacy default stream cannot be captured into a graph
+    side = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
-    P.set_timing(True)
-    for k in range(8):
-        P.timing(k, reset=True)
-    clk = Clocks(clocks_index)
+    P = Ptsbe(device=dev.index if dev.index is not None else 0, stream=side.cuda_stream)
+    t0 = time.perf_counter()
+    infos = []
+    for i, circ in enumerate(circs):
+        cid = P.register(circ)
+        infos.append((circ, cid, P.sample_kraus(cid, "proportional", seed=cfg["seed"] + i, nsamples=cfg["nsamples"],
+                                                 total_shots=int(shots[i]))))
+    t_pts = time.perf_counter() - t0
+    need = sum(info.count * (8 << circ.n_qubits) for circ, _, info in infos)
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = max(1.0, free - margin_gb * 2 ** 30)
+    chunks, cur, cur_b = [], [], 0
+    for k, (circ, cid, info) in enumerate(infos):
+        b = info.count * (8 << circ.n_qubits)
+        if cur and cur_b + b > budget:
+            chunks.append(cur)
+            cur, cur_b = [], 0
+        cur.append(k)
+        cur_b += b
+    if cur:
+        chunks.append(cur)
+    # the states of a chunk are views into one flat buffer; chunks run one after another on the
+    # stream, each reusing the same memory (one chunk: every state at once)
+    chunk_amps = [sum(infos[k][2].count << infos[k][0].n_qubits for k in ch) for ch in chunks]
+    flat = torch.empty(max(chunk_amps), dtype=torch.complex64, device=dev)
+    bufs = []
+    for circ, cid, info in infos:
+        bufs.append([None, torch.empty(info.count, dtype=torch.float64, device=dev),
+                     torch.empty(info.count, dtype=torch.uint8, device=dev),
+                     torch.empty(max(info.total_shots, 1), dtype=torch.int32, device=dev)])
+    for ch in chunks:
+        off = 0
+        for k in ch:
+            circ, _, info = infos[k]
+            m = info.count << circ.n_qubits
+            bufs[k][0] = flat[off:off + m].view(info.count, 1 << circ.n_qubits)
+            off += m
+    t0 = time.perf_counter()
+    batches = []
+    for ch in chunks:
+        jobs = [(infos[k][2], 0, infos[k][2].count, bufs[k][0], bufs[k][1], bufs[k][2], 7000 + k, bufs[k][3]) for k in ch]
+        batches.append(P.batch_plan(jobs))
+    t_plan = time.perf_counter() - t0
+    info0 = [P.batch_info(b) for b in batches]
+    torch.cuda.synchronize()                 # the buffers were made on the default stream
+    stream = side
+    for b in batches:
+        P.batch_run(b)                  # warm-up (plain launches)
+    for b in batches:
+        P.batch_run(b, graph=True)      # captures each chunk's graph and launches it
+    P.synchronize()
+    torch.cuda.synchronize()
+    clk = Clocks(dev.index if dev.index is not None else 0)
     clk.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    P.evolve_sample(info, 0, count, None, w, s, seed, bits)
+    for _ in range(reps):
+        for b in batches:
+            P.batch_run(b, graph=True)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    applied, nominal = P.reuse_stats()
-    launches, fma = P.dense_work()
-    kern = {}
-    for cls, name in [(capi.PTSBE_TIMER_DENSE, "dense_pass"), (capi.PTSBE_TIMER_EVOLVE_FINALIZE, "finalize"),
-                      (capi.PTSBE_TIMER_SAMPLE, "sample"), (capi.PTSBE_TIMER_SAMPLE_LIGHT, "sample_light")]:
-        kms, kl, kb = P.timing(cls, reset=True)
-        if kl:
-            kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
-    P.set_timing(False)
-    null = int(s.sum().item())
-    # the traditional per-shot path on this workload: one trajectory prepared from |0...0> for one
-    # shot (for these unitary-mixture channels Algorithm 1's Kraus draws do not depend on the state,
-    # so a shot costs one full preparation); timed on the error-free trajectory
-    one = P.sample_kraus(cid, "targeted", targeted=[[]], targeted_shots=np.array([1], np.uint64))
-    b1 = torch.empty(1, dtype=torch.int32, device=dev)
-    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
-    torch.cuda.synchronize()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    ps_ms = f0.elapsed_time(f1)
-    P.release_set(one)
-    hbm_peak, hbm_kind = peaks()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    alu_peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12             # FP32 TFLOP/s: SMs x 128 FMA lanes x 2 x clock
-    d = kern.get("dense_pass")
-    dense = None
-    if d:
-        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        tfl = 2 * fma / (d["ms"] / 1e3) / 1e12
-        dense = {"ms": d["ms"], "launches": d["launches"], "algorithmic_bytes": d["bytes"],
-                 "gate_apply_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind,
-                 "fma": fma, "fp32_tflops": tfl, "alu_frac": tfl / alu_peak, "alu_peak_tflops": alu_peak,
-                 "alu_peak_kind": "derived: SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
-                 "ms_per_pass_launch": d["ms"] / d["launches"]}
-    est_s = None
-    if applied:
-        est_s = (ms / 1e3) * full_applied / applied
-    out = {"workload": c["name"], "qubits": n, "layers": 60, "gates": circ.n_gates, "noise_sites": circ.n_sites,
-           "sets_total": info.count, "sets_timed": count, "shots_total": info.total_shots, "shots_timed": shots,
-           "timed": "whole job" if count == info.count else f"first {count} of {info.count} sets in canonical (trie) order",
-           "ms": ms, "shots_per_s": shots / (ms / 1e3), "null_sets": null, "host_pts_s": t_pts,
-           "trajectory_gates_per_s": {"applied": applied / (ms / 1e3), "logical": count * circ.n_gates / (ms / 1e3)},
-           "prefix_reuse": {"timed_sets": {"gates_applied": applied, "gates_without_reuse": nominal,
-                                           "savings": 1 - applied / nominal if nominal else None},
-                            "full_job": {"gates_applied": full_applied, "gates_without_reuse": full_nominal,
-                                         "savings": 1 - full_applied / full_nominal if full_nominal else None}},
-           "plan": plan, "kernels": kern, "dense": dense,
-           "roofline": ({"bound": "alu", "kernel": "k_dense_pass", "achieved": dense["fp32_tflops"], "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": dense["alu_frac"]} if dense else None),
-           "roofline_hbm": ({"bound": "hbm", "kernel": "k_dense_pass", "achieved": dense["gate_apply_gbs"],
-                             "peak": hbm_peak, "unit": "GB/s", "frac": dense["hbm_frac"]} if dense else None),
-           "full_job_estimate_s": est_s,
-           "pershot": {"value": 1.0 / (ps_ms / 1e3), "unit": "shots/s", "ms_per_shot": ps_ms,
-                       "kind": "one full 30-qubit trajectory prepared per shot (dense passes, no reuse)"},
-           "speedup_vs_pershot": (shots / (ms / 1e3)) / (1.0 / (ps_ms / 1e3)),
-           "clocks": clocks}
-    P.release_set(info)
-    P.release_circuit(cid)
-    del bits, w, s
-    torch.cuda.empty_cache()
-    return out
+    P.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    total_shots = int(sum(int(info.total_shots) for _, _, info in infos))
+    sets = int(sum(info.count for _, _, info in infos))
+    logical_gates = float(sum(info.count * circ.n_gates for circ, _, info in infos))
+    null = int(sum(int(b[2].sum().item()) for b in bufs))
+    for b in batches:
+        P.batch_release(b)
+    P.close()
+    del flat, bufs
+    return {"workload": cfg["name"], "circuits": len(circs), "sets": sets, "shots": total_shots,
+            "state_bytes": need, "launch_chunks": len(chunks), "ms_per_run": ms, "shots_per_s": total_shots / (ms / 1e3),
+            "trajectory_gates_per_s": logical_gates / (ms / 1e3), "null_sets": null,
+            "queue": info0, "host_pts_s": t_pts, "host_plan_s": t_plan, "reps": reps, "clocks": clocks,
+            "kind": ("one persistent cooperative launch (device work queue, bounded waits) per run over all circuits, "
+                     "then the samplers; replayed as a CUDA graph")}
 
 
 def run_reference(args):
@@ -590,7 +562,7 @@ def main():
 
     if args.uneven_only:
         if rank == 0:
-            print(json.dumps({"uneven": uneven_leg(local)}), flush=True)
+            print(json.dumps({"uneven": uneven_leg(torch.device("cuda", local))}), flush=True)
         return
 
     if args.dense30_only:
@@ -758,17 +730,25 @@ def main():
                                [0, 1, 2, K // 2, K - 1])
         P.release_set(info)
         P.release_circuit(cid)
-        c0 = config0_ratio(P, dev)
+        P0 = Ptsbe(device=local, stream=stream.cuda_stream)
+        c0 = config0_ratio(P0, dev)
+        P0.close()
 
     bw = None
     if not args.no_backward:
         bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
-    unev = uneven_leg(local) if (args.uneven and rank == 0) else None
+    unev = None
 
     d30 = None
     if args.dense30_sets != 0 and rank == 0:
-        d30 = dense30_leg(P, dev, args.dense30_sets, local)
+        P30 = Ptsbe(device=local, stream=stream.cuda_stream)
+        d30 = dense30_leg(P30, dev, args.dense30_sets, local)
+        P30.close()
+        torch.cuda.empty_cache()
+    if not args.no_uneven and rank == 0:
+        unev = uneven_leg(dev)
+        torch.cuda.empty_cache()
 
     ms_step = ms / args.steps
     value = job_throughput(world, M, ms_step)

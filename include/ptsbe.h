@@ -244,7 +244,7 @@ enum {
      * set's input of that stage instead of from |0...0>. Stages alternate between d_states and a
      * library workspace of the same size. */
     PTSBE_EVOLVE_PREFIX_REUSE = 1u,
-    /* Plan only (dense passes: evolve kernel 4, or d_states NULL in ptsbe_evolve_sample): build the
+    /* Plan only (dense passes, n >= 12: evolve kernel 4, or d_states NULL in ptsbe_evolve_sample): build the
      * call's schedule (prefix reuse, branches) and set the counters of ptsbe_reuse_stats, but
      * enqueue no device work and write no output; output pointers may be NULL. For sizing a job
      * before running it. With another evolve kernel: PTSBE_ERR_UNSUPPORTED. */
@@ -298,7 +298,7 @@ PTSBE_API int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * ownership as for the two calls. Asynchronous. Errors: those of the two calls; a kernel that
  * finds a support not of the form the plan guarantees flags the context, and the next
  * ptsbe_synchronize returns PTSBE_ERR_UNSUPPORTED (the affected shots hold 0xFFFFFFFF). */
-/* d_states may be NULL when n > 12: the states are then not returned and live only in library
+/* d_states may be NULL when n >= 12: the states are then not returned and live only in library
  * buffers (for states too large to keep one per set, e.g. 8 GiB at 30 qubits). The sets of the
  * range are prepared with dense passes, one branch at a time: at each pass the sets are split by
  * their Kraus entries inside that pass; a group with entries there branches into a new buffer from
@@ -339,6 +339,57 @@ PTSBE_API int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
 PTSBE_API int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count,
                                          const void* d_states, const uint8_t* d_status, uint64_t seed,
                                          uint32_t* d_bits, uint64_t d_bits_capacity);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Many circuits in one persistent launch (Sec. 3 batched execution over uneven circuits)        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* One job of a batch: sets [first, first + count) of set_id, prepared in place in d_states
+ * (complex64 [count][2^n], 16-byte aligned, n >= 12) with dense passes, normalised (d_weights
+ * float64 [count] and d_status uint8 [count] as for ptsbe_evolve_batch; either may be NULL), and
+ * sampled into d_bits as ptsbe_sample_shots would (NULL: no shots). All buffers caller-owned, on
+ * the context's device, and valid while the batch lives. */
+typedef struct {
+    uint32_t set_id, first, count;
+    void* d_states;
+    double* d_weights;
+    uint8_t* d_status;
+    uint64_t seed;
+    uint32_t* d_bits;
+    uint64_t d_bits_capacity;
+} ptsbe_job;
+
+enum {
+    /* ptsbe_batch_run: capture the run into a CUDA graph on the first such call (the context's
+     * stream must not be the legacy default stream) and launch that graph on this and later calls. */
+    PTSBE_BATCH_GRAPH = 1u
+};
+
+/* Plans a batch: every job's dense-pass plan, Kraus-set overrides, weights, the work queue's tasks
+ * and the sampler launches, copied to the device now (the jobs' sets and circuits may be released
+ * afterwards). The tasks are (set, level) of every job, level by level: each dense pass of a set
+ * (one work item per 2^12-amplitude tile), then its normalisation and its scaling; a task waits for
+ * the same set's previous level. Host-synchronous planning, one stream-ordered upload.
+ * Errors: PTSBE_ERR_INVALID, PTSBE_ERR_UNSUPPORTED (n < 12), PTSBE_ERR_BUFFER_TOO_SMALL, PTSBE_ERR_OOM. */
+PTSBE_API int ptsbe_batch_plan(ptsbe_ctx* ctx, const ptsbe_job* jobs, uint32_t n_jobs, uint32_t* batch_id);
+
+/* Runs a planned batch on the context stream: one persistent cooperative launch prepares every
+ * job's states (all CTAs resident; each takes the next tile from one global counter and waits,
+ * bounded by PTSBE_OPT_QUEUE_SPIN_CYCLES, for the tiles it depends on), then the samplers draw the
+ * shots. Enqueues device work only (memsets and kernels), so it can be replayed as a CUDA graph
+ * (PTSBE_BATCH_GRAPH). Results: the outputs of ptsbe_evolve_batch (kernel 4) and
+ * ptsbe_sample_shots for every job, bit for bit. A wait that ran out makes the next
+ * ptsbe_synchronize return PTSBE_ERR_TIMEOUT (the outputs are then incomplete); the context and
+ * the batch stay usable. Asynchronous. */
+PTSBE_API int ptsbe_batch_run(ptsbe_ctx* ctx, uint32_t batch_id, uint32_t flags);
+
+/* Size of a planned batch: queue tasks, work items, CTAs of the persistent launch, kernels per run
+ * (any pointer may be NULL). Host-only. */
+PTSBE_API int ptsbe_batch_info(ptsbe_ctx* ctx, uint32_t batch_id, uint64_t* tasks, uint64_t* items, uint32_t* grid,
+                               uint64_t* kernels_per_run);
+
+/* Frees a batch's device tables, workspace and graph (stream-ordered after its runs). */
+PTSBE_API int ptsbe_batch_release(ptsbe_ctx* ctx, uint32_t batch_id);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Adjoint gradients of the fixed-set estimator (Sec. 3 with the Kraus sets held fixed)        */
@@ -410,10 +461,10 @@ enum {
      * pass of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
      * registers, the tile re-shuffled through shared memory between register groups), 3 deferred
      * frame (permutations and diagonals tracked as an index map and factor tables; only
-     * operators that mix amplitudes pass over the tile), 4 dense passes for n > 12 (the state
+     * operators that mix amplitudes pass over the tile), 4 dense passes for n >= 12 (the state
      * streams through HBM once per pass over 12-qubit tiles; the operators of a pass are fused into
      * 1- and 2-qubit blocks applied to amplitudes held in registers; the planner changes the
-     * qubit-to-bit layout between passes so each pass holds the qubits it needs; n <= 12 falls back
+     * qubit-to-bit layout between passes so each pass holds the qubits it needs; n < 12 falls back
      * to 3). */
     PTSBE_OPT_EVOLVE_KERNEL = 0,
     /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
@@ -433,7 +484,15 @@ enum {
      * (default) turns it off. Every entry point but ptsbe_autotune (a series of calls) allocates
      * before its first kernel launch, so a call that fails this way has written none of its
      * outputs, and the context stays usable. */
-    PTSBE_OPT_FAIL_ALLOC = 3
+    PTSBE_OPT_FAIL_ALLOC = 3,
+    /* Wait budget of the batch work queue (ptsbe_batch_run), in GPU clock cycles (clock64): a CTA
+     * waiting for another task's tiles gives up after this long, records the task, and every CTA
+     * leaves; the next ptsbe_synchronize returns PTSBE_ERR_TIMEOUT. Default 2e10 (~10 s). */
+    PTSBE_OPT_QUEUE_SPIN_CYCLES = 4,
+    /* Test hook of the work queue: the task with this index waits for one tile more than its
+     * predecessor has, so its wait always runs out (no GPU fault: the wait is bounded and the
+     * kernel returns); -1 (default) turns it off. */
+    PTSBE_OPT_QUEUE_STALL_TASK = 5
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
@@ -445,7 +504,7 @@ PTSBE_API int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value);
 typedef struct {
     int32_t evolve_kernel;            /* chosen PTSBE_OPT_EVOLVE_KERNEL (1 sweeps, 2 registers, 3 frame, 4 dense) */
     uint64_t light_shots;             /* chosen PTSBE_OPT_LIGHT_SHOTS                                */
-    double evolve_ms[5];              /* by kernel index (entry 0 unused; 4 only for n > 12)        */
+    double evolve_ms[5];              /* by kernel index (entry 0 unused; 4 only for n >= 12)       */
     uint64_t light_candidates[4];
     double sample_ms[4];              /* by light-shot candidate                                    */
 } ptsbe_tuning;
@@ -485,7 +544,7 @@ PTSBE_API int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_
  * block 16 per amplitude), the algorithmic arithmetic for an ALU roofline. Host-only. */
 PTSBE_API int ptsbe_dense_work(ptsbe_ctx* ctx, uint64_t* pass_launches, double* fma);
 
-/* The dense-pass plan of a circuit (built if needed; n > 12, else PTSBE_ERR_UNSUPPORTED): passes
+/* The dense-pass plan of a circuit (built if needed; n >= 12, else PTSBE_ERR_UNSUPPORTED): passes
  * (of which fixup_passes only restore logical qubit order at the end), fused 1- and 2-qubit
  * blocks, and FP32 multiply-adds per amplitude of one full preparation. Any pointer may be NULL.
  * Host-only. */

@@ -22,6 +22,9 @@ PTSBE_OPT_EVOLVE_KERNEL = 0
 PTSBE_OPT_LIGHT_SHOTS = 1
 PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
 PTSBE_OPT_FAIL_ALLOC = 3
+PTSBE_OPT_QUEUE_SPIN_CYCLES = 4
+PTSBE_OPT_QUEUE_STALL_TASK = 5
+PTSBE_BATCH_GRAPH = 1
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
  PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE) = range(8)
 
@@ -61,6 +64,12 @@ class ptsbe_observable(C.Structure):
 class ptsbe_tuning(C.Structure):
     _fields_ = [("evolve_kernel", C.c_int32), ("light_shots", C.c_uint64), ("evolve_ms", C.c_double * 5),
                 ("light_candidates", C.c_uint64 * 4), ("sample_ms", C.c_double * 4)]
+
+
+class ptsbe_job(C.Structure):
+    _fields_ = [("set_id", C.c_uint32), ("first", C.c_uint32), ("count", C.c_uint32), ("d_states", C.c_void_p),
+                ("d_weights", C.c_void_p), ("d_status", C.c_void_p), ("seed", C.c_uint64), ("d_bits", C.c_void_p),
+                ("d_bits_capacity", C.c_uint64)]
 
 
 class PtsbeError(RuntimeError):
@@ -108,6 +117,11 @@ _PROTOS = {
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_reuse_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "ptsbe_batch_plan": (C.c_int, [C.c_void_p, C.POINTER(ptsbe_job), C.c_uint32, C.POINTER(C.c_uint32)]),
+    "ptsbe_batch_run": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32]),
+    "ptsbe_batch_info": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                   C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
+    "ptsbe_batch_release": (C.c_int, [C.c_void_p, C.c_uint32]),
     "ptsbe_dense_work": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
     "ptsbe_dense_plan_info": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_double)]),
@@ -280,6 +294,27 @@ def ptsbe_dense_plan_info(ctx, circuit_id):
     check(ctx, load().ptsbe_dense_plan_info(ctx, circuit_id, C.byref(p), C.byref(fx), C.byref(b1), C.byref(b2),
                                             C.byref(f)))
     return p.value, fx.value, b1.value, b2.value, f.value
+
+
+def ptsbe_batch_plan(ctx, jobs) -> int:
+    arr = (ptsbe_job * max(len(jobs), 1))(*jobs)
+    bid = C.c_uint32()
+    check(ctx, load().ptsbe_batch_plan(ctx, arr, len(jobs), C.byref(bid)))
+    return bid.value
+
+
+def ptsbe_batch_run(ctx, batch_id, flags=0):
+    check(ctx, load().ptsbe_batch_run(ctx, batch_id, flags))
+
+
+def ptsbe_batch_info(ctx, batch_id):
+    t, i, g, k = C.c_uint64(), C.c_uint64(), C.c_uint32(), C.c_uint64()
+    check(ctx, load().ptsbe_batch_info(ctx, batch_id, C.byref(t), C.byref(i), C.byref(g), C.byref(k)))
+    return t.value, i.value, g.value, k.value
+
+
+def ptsbe_batch_release(ctx, batch_id):
+    check(ctx, load().ptsbe_batch_release(ctx, batch_id))
 
 
 def ptsbe_set_option(ctx, option: int, value: int):

@@ -47,6 +47,28 @@ struct ClassTimer {
     double bytes = 0;
 };
 
+// A planned batch of jobs for one persistent launch (ptsbe_batch_plan).
+struct PlannedSample {
+    int kind;                        // 0 light, 1 cluster, 2 global
+    SampleArgs A;
+    size_t item_off;                 // into the batch's item array (kinds 0, 1)
+    const SampleItem* items;         // device address of the first item, set after the upload
+    uint32_t n_items;
+    uint32_t state, alpha;           // kind 2
+    uint64_t m, out0;
+};
+
+struct Batch {
+    void* dtab = nullptr;            // tables (one device allocation, uploaded at plan time)
+    void* dws = nullptr;             // counters, tile norms, scales, status, sampler scratch
+    QueueArgs qa{};
+    std::vector<PlannedSample> samples;
+    uint64_t kernels_per_run = 0;
+    uint32_t* d_err = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    size_t counter_bytes = 0;
+};
+
 }  // namespace ptsbe
 
 using namespace ptsbe;
@@ -57,6 +79,10 @@ struct ptsbe_ctx {
     std::string err = "no error";
     std::unordered_map<uint32_t, std::unique_ptr<Circuit>> circuits;
     std::unordered_map<uint32_t, std::unique_ptr<KSet>> sets;
+    std::unordered_map<uint32_t, std::unique_ptr<Batch>> batches;
+    uint32_t next_batch = 1;
+    long long queue_spin_cycles = 20000000000ll;   // ~10 s at 2 GHz: a wait of the work queue gives up after this
+    int64_t queue_stall_task = -1;                  // test hook (PTSBE_OPT_QUEUE_STALL_TASK)
     uint32_t next_circuit = 1, next_set = 1;
     DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support, sitems;
     DevBuf dense_tabs, stream_status;          // dense passes: per-call node/override tables; status when the caller passes none
@@ -385,12 +411,12 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
                   double* d_weights, uint8_t* d_status, uint32_t flags, const FusedShots* fused,
                   std::vector<uint8_t>* drawn) {
     ctx->use_device();
-    if (ctx->evolve_kernel == 4 && (int)c.n > dense::kT) {
+    if (ctx->evolve_kernel == 4 && (int)c.n >= dense::kT) {
         if (drawn) drawn->assign(count, 0);
         evolve_dense_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags);
         return;
     }
-    if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel (n > 12)");
+    if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel (n >= 12)");
     ensure_set_on_device(ctx, s);
     const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
     if (frame && !c.frame_planned) {
@@ -758,8 +784,9 @@ std::pair<uint32_t, uint32_t> dense_overrides(const Circuit& c, const DensePlan&
         const uint32_t cnt = P.blk_nq[blk] == 1 ? 4 : 16;
         const uint32_t off = (uint32_t)pool.size();
         pool.resize(pool.size() + cnt);
-        dense_block_matrix(c, P, blk, sites.data(), ks.data(), (uint32_t)sites.size(), &pool[off]);
-        ovr.push_back({blk, off});
+        uint32_t code = 0;
+        dense_block_matrix(c, P, blk, sites.data(), ks.data(), (uint32_t)sites.size(), &pool[off], &code);
+        ovr.push_back({blk, off, code});
     }
     return {begin, (uint32_t)ovr.size()};
 }
@@ -1064,6 +1091,65 @@ void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, u
     }
 }
 
+// ---- one persistent launch over many jobs (ptsbe_batch_*) --------------------------------------
+
+// The sampler launches of ptsbe_sample_shots for a range, planned up front (same kernels, items and
+// counters as sample_range), so that a run enqueues kernels only.
+void plan_samples(const ptsbe_ctx* ctx, const KSet& s, const Circuit& c, uint32_t first, uint32_t count,
+                  const float2* states, const uint8_t* status, uint64_t seed, uint32_t* bits,
+                  std::vector<SampleItem>& items, std::vector<PlannedSample>& out) {
+    const int n = (int)c.n;
+    SampleArgs A{};
+    A.n = n; A.states = states; A.status = status; A.seed = seed; A.bits = bits;
+    const bool light_ok = n > 14 && n <= sample_light_max_qubits();
+    const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
+    const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
+    const uint64_t base = s.shot_off[first];
+    uint64_t total = 0;
+    for (uint32_t a = 0; a < count; ++a) total += s.shots[first + a];
+    const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+    std::vector<SampleItem> light, heavy;
+    for (uint32_t a = 0; a < count; ++a) {
+        const uint32_t alpha = first + a;
+        const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
+        if (m == 0) continue;
+        if (light_ok && m <= ctx->light_shots) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
+        if (n <= sample_cluster_max_qubits()) {
+            for (uint64_t j0 = 0; j0 < m; j0 += chunk) heavy.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
+        } else {
+            PlannedSample g{};
+            g.kind = 2; g.A = A; g.state = a; g.alpha = alpha; g.m = m; g.out0 = o;
+            out.push_back(g);
+        }
+    }
+    if (!light.empty()) {
+        PlannedSample p{};
+        p.kind = 0; p.A = A; p.item_off = items.size(); p.n_items = (uint32_t)light.size();
+        items.insert(items.end(), light.begin(), light.end());
+        out.push_back(p);
+    }
+    if (!heavy.empty()) {
+        PlannedSample p{};
+        p.kind = 1; p.A = A; p.item_off = items.size(); p.n_items = (uint32_t)heavy.size();
+        items.insert(items.end(), heavy.begin(), heavy.end());
+        out.push_back(p);
+    }
+}
+
+// Enqueues one run of a batch: counters cleared, the persistent queue launch, the samplers.
+void batch_enqueue(ptsbe_ctx* ctx, Batch& B) {
+    QueueArgs qa = B.qa;
+    qa.spin_cycles = ctx->queue_spin_cycles;
+    qa.stall_task = ctx->queue_stall_task < 0 ? 0xFFFFFFFFu : (uint32_t)ctx->queue_stall_task;
+    PTSBE_CUDA(cudaMemsetAsync(B.dws, 0, B.counter_bytes, ctx->stream));
+    launch_dense_queue(qa, ctx->n_sm, ctx->stream);
+    for (const PlannedSample& p : B.samples) {
+        if (p.kind == 0) launch_sample_light(p.A, p.items, p.n_items, ctx->stream);
+        else if (p.kind == 1) launch_sample_cluster(p.A, p.items, p.n_items, ctx->stream);
+        else launch_sample_global(p.A, p.state, p.alpha, 0, p.m, p.out0, ctx->stream);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1121,6 +1207,11 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
             qfree(kv.second->bw.dev); qfree(kv.second->dense.dev);
         }
         for (auto& kv : ctx->sets) qfree(kv.second->d_site);   // d_k shares the allocation
+        for (auto& kv : ctx->batches) {
+            qfree(kv.second->dtab);
+            qfree(kv.second->dws);
+            if (kv.second->graph) cudaGraphExecDestroy(kv.second->graph);
+        }
         cudaStreamSynchronize(ctx->stream);
         ctx->free_staging();
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -1153,6 +1244,15 @@ int ptsbe_synchronize(ptsbe_ctx* ctx) {
         ctx->use_device();
         PTSBE_CUDA(cudaStreamSynchronize(ctx->stream));
         PTSBE_CUDA(cudaGetLastError());
+        for (auto& kv : ctx->batches) {
+            uint32_t e = 0;
+            PTSBE_CUDA(cudaMemcpy(&e, kv.second->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+            if (e) {
+                PTSBE_CUDA(cudaMemset(kv.second->d_err, 0, sizeof(e)));
+                fail(PTSBE_ERR_TIMEOUT, "batch " + std::to_string(kv.first) + ": the work queue's wait for task " +
+                                            std::to_string(e - 1) + " ran out; the batch's outputs are incomplete");
+            }
+        }
         if (ctx->fault.p) {
             uint32_t f = 0;
             PTSBE_CUDA(cudaMemcpy(&f, ctx->fault.p, sizeof(f), cudaMemcpyDeviceToHost));
@@ -1306,7 +1406,7 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
         const bool plan_only = flags & PTSBE_EVOLVE_PLAN_ONLY;
         const uint64_t total = s.shot_off[first + count] - s.shot_off[first];
         if (plan_only) {
-            if (!d_states && (int)c.n > dense::kT) stream_evolve_sample(ctx, s, c, first, count, nullptr, nullptr, seed, nullptr, true);
+            if (!d_states && (int)c.n >= dense::kT) stream_evolve_sample(ctx, s, c, first, count, nullptr, nullptr, seed, nullptr, true);
             else evolve_range(ctx, s, c, first, count, d_states, nullptr, nullptr, flags, nullptr, nullptr);
             return;
         }
@@ -1315,7 +1415,7 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
                                                                           " shots, the range needs " + std::to_string(total));
         if (total && c.n > 32) fail(PTSBE_ERR_UNSUPPORTED, "outcomes are 32-bit");
         if (!d_states) {
-            if ((int)c.n <= dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "d_states may be NULL only for n > 12 (dense passes)");
+            if ((int)c.n < dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "d_states may be NULL only for n >= 12 (dense passes)");
             ctx->use_device();
             ensure_set_on_device(ctx, s);
             stream_evolve_sample(ctx, s, c, first, count, d_weights, d_status, seed, d_bits, false);
@@ -1369,6 +1469,12 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         } else if (option == PTSBE_OPT_LIGHT_SHOTS) {
             if (value < 0) fail(PTSBE_ERR_INVALID, "light-sampler shot limit must be >= 0");
             ctx->light_shots = (uint64_t)value;
+        } else if (option == PTSBE_OPT_QUEUE_SPIN_CYCLES) {
+            if (value <= 0) fail(PTSBE_ERR_INVALID, "queue wait budget must be positive");
+            ctx->queue_spin_cycles = value;
+        } else if (option == PTSBE_OPT_QUEUE_STALL_TASK) {
+            if (value < -1) fail(PTSBE_ERR_INVALID, "stall task must be >= -1");
+            ctx->queue_stall_task = value;
         } else if (option == PTSBE_OPT_FAIL_ALLOC) {
             if (value < -1) fail(PTSBE_ERR_INVALID, "allocation failure index must be >= -1");
             ctx->fail_alloc_at = value;
@@ -1410,7 +1516,7 @@ int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t cou
         int best_k = -1;
         double best = 0;
         try {
-            const bool dense_ok = (int)ctx->circuit(ctx->set(set_id).circuit).n > dense::kT;
+            const bool dense_ok = (int)ctx->circuit(ctx->set(set_id).circuit).n >= dense::kT;
             for (int k : {3, 1, 2, 4}) {
                 if (k == 4 && !dense_ok) continue;
                 ctx->evolve_kernel = k;
@@ -1504,7 +1610,7 @@ int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes,
                           uint64_t* blocks_1q, uint64_t* blocks_2q, double* fma_per_amplitude) {
     return guarded(ctx, [&] {
         Circuit& c = ctx->circuit(circuit_id);
-        if ((int)c.n <= dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need n > 12");
+        if ((int)c.n < dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need n >= 12");
         if (!c.dense.built) make_dense_plan(c, c.dense);
         const DensePlan& P = c.dense;
         uint64_t b1 = 0, b2 = 0;
@@ -1812,6 +1918,221 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
                 }
             }
         }
+    });
+}
+
+int ptsbe_batch_plan(ptsbe_ctx* ctx, const ptsbe_job* jobs, uint32_t n_jobs, uint32_t* batch_id) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        if (!batch_id) fail(PTSBE_ERR_INVALID, "batch_id is NULL");
+        if (n_jobs && !jobs) fail(PTSBE_ERR_INVALID, "jobs is NULL");
+        ctx->use_device();
+        struct JobHost {
+            KSet* s;
+            Circuit* c;
+            int n, J;
+            std::vector<dense::Override> ovr;
+            std::vector<float2> pool;
+            std::vector<uint32_t> ovb, ove;
+            std::vector<double> wmix, qa;
+        };
+        std::vector<JobHost> H(n_jobs);
+        int maxJ = 0;
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            const ptsbe_job& jb = jobs[j];
+            KSet& s = ctx->set(jb.set_id);
+            Circuit& c = ctx->circuit(s.circuit);
+            if ((uint64_t)jb.first + jb.count > s.count()) fail(PTSBE_ERR_INVALID, "job " + std::to_string(j) + ": set range out of bounds");
+            if ((int)c.n < dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "job " + std::to_string(j) + ": batches need n >= 12");
+            if (jb.count && !jb.d_states) fail(PTSBE_ERR_INVALID, "job " + std::to_string(j) + ": d_states is NULL");
+            if ((uintptr_t)jb.d_states % 16) fail(PTSBE_ERR_INVALID, "job " + std::to_string(j) + ": d_states must be 16-byte aligned");
+            const uint64_t total = s.shot_off[jb.first + jb.count] - s.shot_off[jb.first];
+            if (jb.d_bits && jb.d_bits_capacity < total)
+                fail(PTSBE_ERR_BUFFER_TOO_SMALL, "job " + std::to_string(j) + ": d_bits holds " + std::to_string(jb.d_bits_capacity) +
+                                                     " shots, the range needs " + std::to_string(total));
+            if (!c.dense.built) make_dense_plan(c, c.dense);
+            JobHost& h = H[j];
+            h.s = &s; h.c = &c; h.n = (int)c.n; h.J = (int)c.dense.passes.size();
+            maxJ = std::max(maxJ, h.J);
+            const double q0mix = mix_q0(c);
+            h.ovb.resize(jb.count); h.ove.resize(jb.count); h.wmix.resize(jb.count); h.qa.resize(jb.count);
+            for (uint32_t a = 0; a < jb.count; ++a) {
+                auto r = dense_overrides(c, c.dense, s, jb.first + a, h.ovr, h.pool);
+                h.ovb[a] = r.first; h.ove[a] = r.second;
+                h.wmix[a] = mix_weight(c, s, jb.first + a, q0mix);
+                h.qa[a] = s.q[jb.first + a];
+            }
+        }
+        // tasks, level by level: dense passes 0 .. J-1, finalisation J, scaling J + 1
+        std::vector<QTask> tasks;
+        std::vector<std::vector<uint32_t>> last(n_jobs);
+        for (uint32_t j = 0; j < n_jobs; ++j) last[j].assign(jobs[j].count, 0xFFFFFFFFu);
+        uint64_t item = 0;
+        for (int lvl = 0; lvl < maxJ + 2; ++lvl)
+            for (uint32_t j = 0; j < n_jobs; ++j) {
+                const int J = H[j].J, ob = H[j].n - dense::kT;
+                if (lvl > J + 1) continue;
+                for (uint32_t a = 0; a < jobs[j].count; ++a) {
+                    QTask t{};
+                    t.item0 = item; t.job = j; t.set = a; t.level = (uint32_t)lvl;
+                    t.items = lvl == J ? 1u : (1u << ob);
+                    t.pred = last[j][a];
+                    t.pred_items = t.pred == 0xFFFFFFFFu ? 0u : tasks[t.pred].items;
+                    last[j][a] = (uint32_t)tasks.size();
+                    tasks.push_back(t);
+                    item += t.items;
+                }
+            }
+        if (tasks.size() >= 0xFFFFFFF0u) fail(PTSBE_ERR_UNSUPPORTED, "too many tasks in one batch");
+        // device workspace: [next][err][done per task] then per job tile norms, scales, status; sampler scratch
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        size_t off = 0;
+        const size_t o_next = off; off += 8;
+        const size_t o_err = off; off += 8;
+        const size_t o_done = off; off += 4 * tasks.size();
+        const size_t counter_bytes = off;
+        off = al(off);
+        std::vector<size_t> o_part(n_jobs), o_scale(n_jobs), o_stat(n_jobs, SIZE_MAX);
+        int max_global_n = 0;
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            const int ob = H[j].n - dense::kT;
+            o_part[j] = off; off = al(off + ((size_t)jobs[j].count << ob) * sizeof(double));
+            o_scale[j] = off; off = al(off + (size_t)jobs[j].count * sizeof(float));
+            if (!jobs[j].d_status) { o_stat[j] = off; off = al(off + jobs[j].count); }
+            if (jobs[j].d_bits && H[j].n > sample_cluster_max_qubits()) max_global_n = std::max(max_global_n, H[j].n);
+        }
+        size_t o_scr = SIZE_MAX;
+        if (max_global_n) { o_scr = off; off = al(off + sample_global_scratch_doubles(max_global_n) * 8); }
+        auto B = std::make_unique<Batch>();
+        unsigned char* dws = (unsigned char*)ctx->dalloc(off);
+        B->dws = dws;
+        B->counter_bytes = counter_bytes;
+        // tables: the plans of every job, the sets' overrides and weights, jobs, tasks, sampler items
+        std::vector<unsigned char> buf;
+        Blob b(buf);
+        struct Offs { size_t p, g, bl, h, o, m, ov, pl, ob, oe, w, q; };
+        std::vector<Offs> O(n_jobs);
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            const DensePlan& P = H[j].c->dense;
+            O[j] = {b.add(P.passes), b.add(P.groups), b.add(P.blocks), b.add(P.hi), b.add(P.omap), b.add(P.mats),
+                    b.add(H[j].ovr), b.add(H[j].pool), b.add(H[j].ovb), b.add(H[j].ove), b.add(H[j].wmix), b.add(H[j].qa)};
+        }
+        std::vector<QJob> qj(n_jobs);
+        const size_t o_jobs = b.add(qj), o_tasks = b.add(tasks);
+        std::vector<SampleItem> items;
+        std::vector<PlannedSample> samples;
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            if (!jobs[j].d_bits) continue;
+            const uint8_t* st = jobs[j].d_status ? jobs[j].d_status : dws + o_stat[j];
+            const size_t before = samples.size();
+            plan_samples(ctx, *H[j].s, *H[j].c, jobs[j].first, jobs[j].count, (const float2*)jobs[j].d_states, st,
+                         jobs[j].seed, jobs[j].d_bits, items, samples);
+            for (size_t i = before; i < samples.size(); ++i)
+                if (o_scr != SIZE_MAX) samples[i].A.scratch = (unsigned long long*)(dws + o_scr);
+        }
+        const size_t o_items = b.add(items);
+        unsigned char* dt = (unsigned char*)ctx->dalloc(buf.size());
+        B->dtab = dt;
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            QJob& q = qj[j];
+            q.passes = (const dense::Pass*)(dt + O[j].p); q.groups = (const dense::Group*)(dt + O[j].g);
+            q.blocks = (const dense::Block*)(dt + O[j].bl); q.hi = (const uint32_t*)(dt + O[j].h);
+            q.omap = (const uint16_t*)(dt + O[j].o); q.mats = (const float2*)(dt + O[j].m);
+            q.ovr = (const dense::Override*)(dt + O[j].ov); q.opool = (const float2*)(dt + O[j].pl);
+            q.ov_begin = (const uint32_t*)(dt + O[j].ob); q.ov_end = (const uint32_t*)(dt + O[j].oe);
+            q.wmix = (const double*)(dt + O[j].w); q.qalpha = (const double*)(dt + O[j].q);
+            q.states = (float2*)jobs[j].d_states;
+            q.part = (double*)(dws + o_part[j]);
+            q.weights = jobs[j].d_weights;
+            q.status = jobs[j].d_status ? jobs[j].d_status : dws + o_stat[j];
+            q.scale = (float*)(dws + o_scale[j]);
+            q.n = (uint32_t)H[j].n; q.J = (uint32_t)H[j].J; q.count = jobs[j].count;
+        }
+        std::memcpy(buf.data() + o_jobs, qj.data(), qj.size() * sizeof(QJob));
+        ctx->h2d(dt, buf.data(), buf.size());
+        for (PlannedSample& p : samples) p.items = (const SampleItem*)(dt + o_items) + p.item_off;
+        B->qa.jobs = (const QJob*)(dt + o_jobs);
+        B->qa.tasks = (const QTask*)(dt + o_tasks);
+        B->qa.n_tasks = (uint32_t)tasks.size();
+        B->qa.n_items = item;
+        B->qa.next = (unsigned long long*)(dws + o_next);
+        B->qa.err = (uint32_t*)(dws + o_err);
+        B->qa.done = (uint32_t*)(dws + o_done);
+        B->d_err = B->qa.err;
+        B->samples = std::move(samples);
+        B->kernels_per_run = item ? 1 : 0;
+        for (const PlannedSample& p : B->samples) B->kernels_per_run += p.kind == 2 ? 4 : 1;
+        PTSBE_CUDA(cudaMemsetAsync(B->d_err, 0, 4, ctx->stream));
+        dense_queue_grid(ctx->n_sm);      // kernel attributes set now, not during a capture
+        configure_samplers();
+        const uint32_t id = ctx->next_batch++;
+        ctx->batches[id] = std::move(B);
+        *batch_id = id;
+    });
+}
+
+int ptsbe_batch_run(ptsbe_ctx* ctx, uint32_t batch_id, uint32_t flags) {
+    return guarded(ctx, [&] {
+        ctx->need_device();
+        auto it = ctx->batches.find(batch_id);
+        if (it == ctx->batches.end()) fail(PTSBE_ERR_INVALID, "unknown batch id " + std::to_string(batch_id));
+        if (flags & ~(uint32_t)PTSBE_BATCH_GRAPH) fail(PTSBE_ERR_INVALID, "unknown flags");
+        Batch& B = *it->second;
+        ctx->use_device();
+        if (!(flags & PTSBE_BATCH_GRAPH)) {
+            batch_enqueue(ctx, B);
+            return;
+        }
+        if (!B.graph) {
+            if (!ctx->stream) fail(PTSBE_ERR_UNSUPPORTED, "graph capture needs a stream other than the legacy default stream");
+            const uint64_t l0 = launches_so_far();
+            PTSBE_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                batch_enqueue(ctx, B);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(ctx->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                (void)cudaGetLastError();
+                throw;
+            }
+            cudaGraph_t g = nullptr;
+            PTSBE_CUDA(cudaStreamEndCapture(ctx->stream, &g));
+            const cudaError_t e = cudaGraphInstantiate(&B.graph, g, 0);
+            cudaGraphDestroy(g);
+            PTSBE_CUDA(e);
+            count_launch((uint64_t)0 - (launches_so_far() - l0));   // nothing ran yet: the launches count at replay
+        }
+        PTSBE_CUDA(cudaGraphLaunch(B.graph, ctx->stream));
+        count_launch(B.kernels_per_run);
+    });
+}
+
+int ptsbe_batch_info(ptsbe_ctx* ctx, uint32_t batch_id, uint64_t* tasks, uint64_t* items, uint32_t* grid,
+                     uint64_t* kernels_per_run) {
+    return guarded(ctx, [&] {
+        auto it = ctx->batches.find(batch_id);
+        if (it == ctx->batches.end()) fail(PTSBE_ERR_INVALID, "unknown batch id " + std::to_string(batch_id));
+        const Batch& B = *it->second;
+        if (tasks) *tasks = B.qa.n_tasks;
+        if (items) *items = B.qa.n_items;
+        if (grid) *grid = (uint32_t)std::min<uint64_t>(B.qa.n_items, (uint64_t)dense_queue_grid(ctx->n_sm));
+        if (kernels_per_run) *kernels_per_run = B.kernels_per_run;
+    });
+}
+
+int ptsbe_batch_release(ptsbe_ctx* ctx, uint32_t batch_id) {
+    return guarded(ctx, [&] {
+        auto it = ctx->batches.find(batch_id);
+        if (it == ctx->batches.end()) fail(PTSBE_ERR_INVALID, "unknown batch id " + std::to_string(batch_id));
+        Batch& B = *it->second;
+        if (ctx->has_device()) {
+            ctx->use_device();
+            ctx->dfree(B.dtab);
+            ctx->dfree(B.dws);
+            if (B.graph) PTSBE_CUDA(cudaGraphExecDestroy(B.graph));
+        }
+        ctx->batches.erase(it);
     });
 }
 

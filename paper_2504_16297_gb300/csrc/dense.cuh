@@ -33,14 +33,17 @@ constexpr int kTB = kT - kR;                    // thread-index bits
 constexpr int kThreads = 1 << kTB;              // 256 threads per CTA
 constexpr int kAmps = 1 << kR;                  // amplitudes per thread
 constexpr int kCodes1 = kR;                     // block codes 0 .. kR-1: 2x2 on one register bit
-constexpr int kStageMax = 24 * 1024;            // a pass's descriptors + matrices staged in shared memory
-                                                // when they fit in this many bytes
+constexpr int kCodeDR = 10;                     // offset of the diagonal-times-real variant of a code
+constexpr int kStageMax = 24 * 1024;            // shared memory for a pass's groups, blocks and matrices
+                                                // (the planner keeps every pass within it)
 constexpr int kHi = 1 << (kT - kC);             // entries of a pass's high-offset table
 constexpr int kMaxQ = 32;
 
 // One fused operator of a pass. code 0..3: 2x2 on register bit `code`; code 4..9: 4x4 on the
 // register pair number code - 4 = (lo, hi) of (0,1) (0,2) (0,3) (1,2) (1,3) (2,3), local index
-// bit(lo) + 2 bit(hi).
+// bit(lo) + 2 bit(hi). Codes kCodeDR + 0..9: the same operator in diagonal-times-real form, M = R D
+// with D diagonal (its entry 0 is 1) and R real: the amplitudes are multiplied by D, then by R
+// (matrix layout: D entries 1.. as float2, padded to an even count, then R row-major as floats).
 struct Block {
     uint8_t code;
     uint8_t pad[3];
@@ -70,7 +73,7 @@ struct Pass {
     uint32_t nouter;
     uint32_t nops;                              // circuit operations this pass applies
     uint32_t mat_begin, mat_end;                // the pass's default matrices (float2 pool range)
-    uint32_t stage_bytes;                       // groups + blocks + matrices, 0 when above kStageMax
+    uint32_t stage_bytes;                       // groups + blocks + matrices staged in shared memory
 };
 
 // A (set, pass) launch entry: where the tile comes from and goes to, and the set's override blocks.
@@ -85,6 +88,7 @@ struct Node {
 struct Override {
     uint32_t block;                             // plan-wide block id
     uint32_t mat;                               // float2 offset into the override pool (4 or 16 entries)
+    uint32_t code;                              // its block code (a general 2x2 or 4x4)
 };
 
 
@@ -165,6 +169,59 @@ PTSBE_HD void apply2(float2* v, const float2* m) {
     }
 }
 
+PTSBE_HD float2 cmul(float2 a, float2 d) {
+    float2 r;
+    r.x = a.x * d.x - a.y * d.y;
+    r.y = a.x * d.y + a.y * d.x;
+    return r;
+}
+
+// Diagonal-times-real 2x2 on register bit A: amplitude 1 of each pair times d1, then R.
+template <int A>
+PTSBE_HD void apply1dr(float2* v, const float2* m) {
+    const float4 a = ldm(m), r = ldm(m + 2);
+    const float2 d1 = make_float2(a.x, a.y);
+#pragma unroll
+    for (int j = 0; j < kAmps; ++j) {
+        if (j & (1 << A)) continue;
+        const float2 x = v[j], y = cmul(v[j | (1 << A)], d1);
+        v[j] = make_float2(r.x * x.x + r.y * y.x, r.x * x.y + r.y * y.y);
+        v[j | (1 << A)] = make_float2(r.z * x.x + r.w * y.x, r.z * x.y + r.w * y.y);
+    }
+}
+
+// Diagonal-times-real 4x4 on register bits (L, H): amplitudes 1, 2, 3 of each quad times d1, d2, d3,
+// then the real matrix R (12 multiply-adds of the diagonal and 32 of R per quad, against 64).
+template <int L, int H>
+PTSBE_HD void apply2dr(float2* v, const float2* m) {
+    const float4 a = ldm(m), b = ldm(m + 2);
+    const float2 d1 = make_float2(a.x, a.y), d2 = make_float2(a.z, a.w), d3 = make_float2(b.x, b.y);
+    float R[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 r = ldm(m + 4 + 2 * i);
+        R[4 * i] = r.x; R[4 * i + 1] = r.y; R[4 * i + 2] = r.z; R[4 * i + 3] = r.w;
+    }
+#pragma unroll
+    for (int j = 0; j < kAmps; ++j) {
+        if (j & ((1 << L) | (1 << H))) continue;
+        const int i1 = j | (1 << L), i2 = j | (1 << H), i3 = j | (1 << L) | (1 << H);
+        const float2 x[4] = {v[j], cmul(v[i1], d1), cmul(v[i2], d2), cmul(v[i3], d3)};
+        float2 o[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float re = R[4 * r] * x[0].x, im = R[4 * r] * x[0].y;
+#pragma unroll
+            for (int l = 1; l < 4; ++l) {
+                re += R[4 * r + l] * x[l].x;
+                im += R[4 * r + l] * x[l].y;
+            }
+            o[r] = make_float2(re, im);
+        }
+        v[j] = o[0]; v[i1] = o[1]; v[i2] = o[2]; v[i3] = o[3];
+    }
+}
+
 PTSBE_HD void apply_block(float2* v, int code, const float2* m) {
     switch (code) {
     case 0: apply1<0>(v, m); break;
@@ -176,8 +233,24 @@ PTSBE_HD void apply_block(float2* v, int code, const float2* m) {
     case 6: apply2<0, 3>(v, m); break;
     case 7: apply2<1, 2>(v, m); break;
     case 8: apply2<1, 3>(v, m); break;
-    default: apply2<2, 3>(v, m); break;
+    case 9: apply2<2, 3>(v, m); break;
+    case kCodeDR + 0: apply1dr<0>(v, m); break;
+    case kCodeDR + 1: apply1dr<1>(v, m); break;
+    case kCodeDR + 2: apply1dr<2>(v, m); break;
+    case kCodeDR + 3: apply1dr<3>(v, m); break;
+    case kCodeDR + 4: apply2dr<0, 1>(v, m); break;
+    case kCodeDR + 5: apply2dr<0, 2>(v, m); break;
+    case kCodeDR + 6: apply2dr<0, 3>(v, m); break;
+    case kCodeDR + 7: apply2dr<1, 2>(v, m); break;
+    case kCodeDR + 8: apply2dr<1, 3>(v, m); break;
+    default: apply2dr<2, 3>(v, m); break;
     }
+}
+
+// float2 entries of a block matrix in the pool: general 2x2 4, 4x4 16; diagonal-times-real 2x2 4,
+// 4x4 12 (all even, so matrices stay 16-byte aligned).
+PTSBE_HD uint32_t code_mat_count(int code) {
+    return code < kCodes1 ? 4u : code < kCodeDR ? 16u : code < kCodeDR + kCodes1 ? 4u : 12u;
 }
 
 // Swizzled tile address of thread t's register base in group g.

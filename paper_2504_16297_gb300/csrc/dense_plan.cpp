@@ -15,6 +15,7 @@
 // packed into register groups of kR tile bits, taking later blocks forward past ones they commute
 // with (disjoint qubits).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "internal.h"
@@ -46,18 +47,24 @@ struct Planner {
     size_t first = 0;
     std::vector<int> phys, at;           // logical -> physical, physical -> logical
 
+    // A pass holds at most kMaxPass2q two-qubit operations: its blocks (at most one 1-qubit block
+    // per tile qubit, plus one per two-qubit operation), groups and matrices then always fit the
+    // kernel's shared-memory staging (kStageMax).
+    static constexpr uint32_t kMaxPass2q = 112;
+
     uint32_t exec(uint64_t S, std::vector<uint32_t>* out) const {
         uint64_t blocked = 0;
-        uint32_t cnt = 0;
+        uint32_t cnt = 0, cnt2 = 0;
         for (size_t i = first; i < ops.size(); ++i) {
             if (done[i]) continue;
             const uint64_t m = qmask(ops[i]);
-            if ((m & ~S) || (m & blocked)) {
+            if ((m & ~S) || (m & blocked) || (ops[i].nq == 2 && cnt2 >= kMaxPass2q)) {
                 blocked |= m;
                 if ((blocked & S) == S) break;
                 continue;
             }
             ++cnt;
+            cnt2 += ops[i].nq == 2;
             if (out) out->push_back((uint32_t)i);
         }
         return cnt;
@@ -182,11 +189,15 @@ int pair_index(int lo, int hi) {
 
 }  // namespace
 
-void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
-                        uint32_t len, float2* out) {
+namespace {
+
+// Product of block b's operators in its logical basis (2 bit(qa) + bit(qb)), Kraus operator ks[i]
+// at site sites[i] and operator 0 at the block's other sites.
+void block_product(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
+                   uint32_t len, cd* M) {
     const int nq = P.blk_nq[b];
     const int d = nq == 1 ? 2 : 4;
-    cd M[16], E[16], m[16], t[16];
+    cd E[16], m[16], t[16];
     for (int i = 0; i < d * d; ++i) M[i] = (i % (d + 1) == 0) ? cd(1.0) : cd(0.0);
     uint32_t e = 0;
     const uint32_t qs2[2] = {P.blk_qa[b], P.blk_qb[b]};
@@ -195,7 +206,7 @@ void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const 
         const ptsbe_op& o = c.ops[op];
         uint32_t k = 0;
         if (o.kind == PTSBE_OP_NOISE) {
-            // site index of this op: entries are sorted by site, and so are the block's sites
+            // entries are sorted by site, and so are the block's sites
             while (e < len && c.site_op[sites[e]] < op) ++e;
             if (e < len && c.site_op[sites[e]] == op) k = ks[e];
         }
@@ -208,24 +219,111 @@ void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const 
         }
         for (int r = 0; r < d; ++r)
             for (int col = 0; col < d; ++col) {
-                cd s = 0;
-                for (int x = 0; x < d; ++x) s += A[r * d + x] * M[x * d + col];
-                t[r * d + col] = s;
+                cd sum = 0;
+                for (int x = 0; x < d; ++x) sum += A[r * d + x] * M[x * d + col];
+                t[r * d + col] = sum;
             }
         for (int i2 = 0; i2 < d * d; ++i2) M[i2] = t[i2];
     }
-    if (nq == 2 && P.blk_swap[b]) {
-        auto p = [](int l) { return ((l & 1) << 1) | (l >> 1); };
-        for (int r = 0; r < 4; ++r)
-            for (int col = 0; col < 4; ++col) t[p(r) * 4 + p(col)] = M[r * 4 + col];
-        for (int i = 0; i < 16; ++i) M[i] = t[i];
+}
+
+// Entry l of a per-qubit diagonal pair product: 2 qubits l = 2 a + b -> x[a] y[b]; 1 qubit x[l].
+cd diag_entry(const std::array<cd, 4>& D, int nq, int l) { return nq == 1 ? D[l] : D[l >> 1] * D[2 + (l & 1)]; }
+
+// Logical -> kernel index of a block's local basis.
+int kernel_index(const DensePlan& P, uint32_t b, int l) {
+    return (P.blk_nq[b] == 2 && P.blk_swap[b]) ? (((l & 1) << 1) | (l >> 1)) : l;
+}
+
+// A = D_out R D_in with R real, D_in diagonal (entry 0 = 1) and D_out a product of one diagonal per
+// qubit (x on qa, y on qb): phases phi_r + theta_c = arg A_rc (mod pi) over the nonzero entries,
+// propagated from row 0, then checked on every entry. false when A has no such form.
+bool factor_dr(const cd* A, int nq, cd* din, double* R, std::array<cd, 4>& dout) {
+    const int d = nq == 1 ? 2 : 4;
+    double amax = 0;
+    for (int i = 0; i < d * d; ++i) amax = std::max(amax, std::abs(A[i]));
+    if (!(amax > 0)) return false;
+    const double eps = 1e-12 * amax;
+    double phr[4], phc[4];
+    bool kr[4] = {false, false, false, false}, kc[4] = {false, false, false, false};
+    int r0 = -1;
+    for (int r = 0; r < d && r0 < 0; ++r)
+        for (int c2 = 0; c2 < d; ++c2)
+            if (std::abs(A[r * d + c2]) > eps) { r0 = r; break; }
+    phr[r0] = 0;
+    kr[r0] = true;
+    for (int it = 0; it < 2 * d; ++it)
+        for (int r = 0; r < d; ++r)
+            for (int c2 = 0; c2 < d; ++c2) {
+                if (std::abs(A[r * d + c2]) <= eps) continue;
+                const double ph = std::arg(A[r * d + c2]);
+                if (kr[r] && !kc[c2]) { phc[c2] = ph - phr[r]; kc[c2] = true; }
+                else if (kc[c2] && !kr[r]) { phr[r] = ph - phc[c2]; kr[r] = true; }
+            }
+    for (int i = 0; i < d; ++i) {
+        if (!kr[i]) { if (nq == 2) return false; phr[i] = 0; }
+        if (!kc[i]) { if (nq == 2) return false; phc[i] = 0; }
     }
-    for (int i = 0; i < d * d; ++i) out[i] = make_float2((float)M[i].real(), (float)M[i].imag());
+    // every row and column is reached from row 0 (one component): the phases are fixed up to
+    // multiples of pi per row (absorbed as signs of R); make the row phases separable over qubits
+    if (nq == 2) {
+        const double delta = phr[0] + phr[3] - phr[1] - phr[2];
+        const double k = std::nearbyint(delta / M_PI);
+        if (std::abs(delta - k * M_PI) > 1e-9) return false;
+        if (((long long)k) & 1) phr[3] += M_PI;
+    }
+    // D_in entry 0 = 1: its phase moves to D_out (a common phase, separable)
+    const double t0 = phc[0];
+    for (int c2 = 0; c2 < d; ++c2) phc[c2] -= t0;
+    for (int r = 0; r < d; ++r) phr[r] += t0;
+    for (int r = 0; r < d; ++r)
+        for (int c2 = 0; c2 < d; ++c2) {
+            const cd x = A[r * d + c2] * std::polar(1.0, -(phr[r] + phc[c2]));
+            if (std::abs(x.imag()) > 1e-10 * amax) return false;
+            R[r * d + c2] = x.real();
+        }
+    for (int c2 = 0; c2 < d; ++c2) din[c2] = std::polar(1.0, phc[c2]);
+    if (nq == 1) {
+        dout = {std::polar(1.0, phr[0]), std::polar(1.0, phr[1]), cd(1.0), cd(1.0)};
+    } else {
+        // phr[2a + b] = alpha_a + beta_b with alpha_0 = 0
+        dout = {cd(1.0), std::polar(1.0, phr[2] - phr[0]), std::polar(1.0, phr[0]), std::polar(1.0, phr[1])};
+        for (int l = 0; l < 4; ++l)
+            if (std::abs(diag_entry(dout, 2, l) - std::polar(1.0, phr[l])) > 1e-9) return false;
+    }
+    return true;
+}
+
+// Kernel-layout general matrix of K (logical basis) into out (complex64).
+void store_general(const DensePlan& P, uint32_t b, const cd* K, float2* out) {
+    const int d = P.blk_nq[b] == 1 ? 2 : 4;
+    for (int r = 0; r < d; ++r)
+        for (int c2 = 0; c2 < d; ++c2) {
+            const cd x = K[r * d + c2];
+            out[kernel_index(P, b, r) * d + kernel_index(P, b, c2)] = make_float2((float)x.real(), (float)x.imag());
+        }
+}
+
+}  // namespace
+
+void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
+                        uint32_t len, float2* out, uint32_t* code) {
+    const int nq = P.blk_nq[b];
+    const int d = nq == 1 ? 2 : 4;
+    cd M[16], K[16];
+    block_product(c, P, b, sites, ks, len, M);
+    // the kernel holds D_out^-1 (state) on the block's output and takes D_in-phased input
+    for (int r = 0; r < d; ++r)
+        for (int c2 = 0; c2 < d; ++c2)
+            K[r * d + c2] = M[r * d + c2] * diag_entry(P.blk_pin[b], nq, c2) / diag_entry(P.blk_pout[b], nq, r);
+    store_general(P, b, K, out);
+    const int gcode = P.blocks[b].code >= kCodeDR ? P.blocks[b].code - kCodeDR : P.blocks[b].code;
+    if (code) *code = (uint32_t)gcode;
 }
 
 void make_dense_plan(const Circuit& c, DensePlan& P) {
     const int n = (int)c.n;
-    if (n <= kT || n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 12 < n <= 32");
+    if (n < kT || n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 12 <= n <= 32");
     P = DensePlan{};
     P.n = n;
     Planner pl;
@@ -482,22 +580,74 @@ void make_dense_plan(const Circuit& c, DensePlan& P) {
             if (!std::binary_search(pos.begin(), pos.end(), p)) ps.opos[ps.nouter++] = (uint8_t)p;
         P.passes.push_back(ps);
     }
-    // default matrices, in block order: each pass's matrices are one contiguous range
-    for (uint32_t b = 0; b < P.blocks.size(); ++b) {
-        const int cnt = P.blk_nq[b] == 1 ? 4 : 16;
+    // default matrices, in block order (each pass's matrices one contiguous range). A block whose
+    // qubits all have a later block takes the diagonal-times-real form: with the phases P_in it
+    // inherits, M P_in = D_out R D_in; it applies D_in then R, and D_out (one diagonal per qubit)
+    // passes on to the next blocks of those qubits. A qubit's last block is general and absorbs
+    // what is left, so the final state carries no pending phase.
+    const uint32_t NB = (uint32_t)P.blocks.size();
+    std::vector<uint32_t> last_blk(n, UINT32_MAX);
+    for (uint32_t b = 0; b < NB; ++b) {
+        last_blk[P.blk_qa[b]] = b;
+        if (P.blk_nq[b] == 2) last_blk[P.blk_qb[b]] = b;
+    }
+    std::vector<std::array<cd, 2>> pend(n, {cd(1.0), cd(1.0)});
+    P.blk_pin.resize(NB);
+    P.blk_pout.resize(NB);
+    for (uint32_t b = 0; b < NB; ++b) {
+        const int nq = P.blk_nq[b];
+        const int d = nq == 1 ? 2 : 4;
+        const uint32_t qa = P.blk_qa[b], qb = P.blk_qb[b];
+        P.blk_pin[b] = {pend[qa][0], pend[qa][1], nq == 2 ? pend[qb][0] : cd(1.0), nq == 2 ? pend[qb][1] : cd(1.0)};
+        cd M[16], A[16], din[4];
+        double R[16];
+        block_product(c, P, b, nullptr, nullptr, 0, M);
+        for (int r = 0; r < d; ++r)
+            for (int c2 = 0; c2 < d; ++c2) A[r * d + c2] = M[r * d + c2] * diag_entry(P.blk_pin[b], nq, c2);
+        std::array<cd, 4> dout{};
+        const bool later = last_blk[qa] != b && (nq == 1 || last_blk[qb] != b);
         P.blocks[b].mat = (uint32_t)P.mats.size();
-        P.mats.resize(P.mats.size() + cnt);
-        dense_block_matrix(c, P, b, nullptr, nullptr, 0, &P.mats[P.blocks[b].mat]);
+        if (later && factor_dr(A, nq, din, R, dout)) {
+            P.blk_pout[b] = dout;
+            pend[qa] = {dout[0], dout[1]};
+            if (nq == 2) pend[qb] = {dout[2], dout[3]};
+            P.blocks[b].code = (uint8_t)(P.blocks[b].code + kCodeDR);
+            const uint32_t cnt = code_mat_count(P.blocks[b].code);
+            P.mats.resize(P.mats.size() + cnt, make_float2(0.f, 0.f));
+            float2* m = &P.mats[P.blocks[b].mat];
+            float dk[4][2], Rk[16];
+            for (int c2 = 0; c2 < d; ++c2) {
+                const int kc = kernel_index(P, b, c2);
+                dk[kc][0] = (float)din[c2].real();
+                dk[kc][1] = (float)din[c2].imag();
+                for (int r = 0; r < d; ++r) Rk[kernel_index(P, b, r) * d + kc] = (float)R[r * d + c2];
+            }
+            for (int i = 1; i < d; ++i) m[i - 1] = make_float2(dk[i][0], dk[i][1]);
+            float* rf = reinterpret_cast<float*>(m + (nq == 1 ? 2 : 4));
+            for (int i = 0; i < d * d; ++i) rf[i] = Rk[i];
+        } else {
+            P.blk_pout[b] = {cd(1.0), cd(1.0), cd(1.0), cd(1.0)};
+            pend[qa] = {cd(1.0), cd(1.0)};
+            if (nq == 2) pend[qb] = {cd(1.0), cd(1.0)};
+            const uint32_t cnt = code_mat_count(P.blocks[b].code);
+            P.mats.resize(P.mats.size() + cnt);
+            store_general(P, b, A, &P.mats[P.blocks[b].mat]);
+        }
     }
     for (Pass& ps : P.passes) {
         ps.mat_begin = ps.blk_begin < ps.blk_end ? P.blocks[ps.blk_begin].mat : 0;
-        ps.mat_end = ps.blk_begin < ps.blk_end ? P.blocks[ps.blk_end - 1].mat + (P.blk_nq[ps.blk_end - 1] == 1 ? 4 : 16) : 0;
+        ps.mat_end = ps.blk_begin < ps.blk_end ? P.blocks[ps.blk_end - 1].mat + code_mat_count(P.blocks[ps.blk_end - 1].code) : 0;
         const size_t bytes = dense_stage_bytes(ps);
-        ps.stage_bytes = bytes <= (size_t)kStageMax ? (uint32_t)bytes : 0u;
+        if (bytes > (size_t)kStageMax) fail(PTSBE_ERR_INVALID, "dense planner: a pass's tables exceed the shared-memory stage");
+        ps.stage_bytes = (uint32_t)bytes;
     }
     // gates applied per pass (prefix-reuse accounting)
     P.pass_fma.assign(P.passes.size(), 0);
-    for (uint32_t b = 0; b < P.blocks.size(); ++b) P.pass_fma[P.blk_pass[b]] += P.blk_nq[b] == 1 ? 8 : 16;
+    for (uint32_t b = 0; b < P.blocks.size(); ++b) {
+        const int code = P.blocks[b].code;
+        // per amplitude: general 2x2 8, 4x4 16; diagonal-times-real 2x2 6 (2 + 4), 4x4 11 (3 + 8)
+        P.pass_fma[P.blk_pass[b]] += code < kCodes1 ? 8 : code < kCodeDR ? 16 : code < kCodeDR + kCodes1 ? 6 : 11;
+    }
     P.pass_gates.assign(P.passes.size(), 0);
     for (size_t j = 0; j < recs.size(); ++j)
         for (uint32_t i : recs[j].ops)

@@ -6,6 +6,7 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
+#include <array>
 
 #include <cuda_runtime.h>
 
@@ -232,6 +233,11 @@ struct DensePlan {
     std::vector<uint8_t> blk_nq;              // 1 or 2
     std::vector<uint32_t> blk_qa, blk_qb;     // logical qubits; block basis index 2 bit(qa) + bit(qb)
     std::vector<uint8_t> blk_swap;            // kernel local index = bit(qa) + 2 bit(qb) (else 2 bit(qa) + bit(qb))
+    // Phases carried between blocks (diagonal-times-real form): the state after block b is
+    // D_out(b) times what the kernel holds, D_out a product of one diagonal per qubit. blk_pin: the
+    // per-qubit diagonals (qa entries 0, 1; qb entries 2, 3) the block absorbs on its input;
+    // blk_pout: those it leaves (identity for a general block).
+    std::vector<std::array<std::complex<double>, 4>> blk_pin, blk_pout;
     std::vector<uint32_t> pass_gates;         // gates applied by each pass (prefix-reuse accounting)
     std::vector<uint32_t> pass_fma;           // FP32 multiply-adds per amplitude of each pass's blocks
                                               // (a 2x2 block 8, a 4x4 block 16: complex products of 4)
@@ -333,10 +339,11 @@ void build_device_ops(Circuit& c);
 Plan make_plan(const Circuit& c, int tile_bits, bool pershot);
 Plan make_frame_plan(const Circuit& c, int tile_bits);
 void make_dense_plan(const Circuit& c, DensePlan& P);
-// Matrix of block b (kernel layout, complex64) with Kraus operator ks[i] at site sites[i] (sites
-// inside the block, increasing) and operator 0 at its other sites.
+// Override matrix of block b (kernel layout, complex64, a general 2x2 or 4x4; *code its block code)
+// with Kraus operator ks[i] at site sites[i] (sites inside the block, increasing) and operator 0 at
+// its other sites, including the phases the block takes in and leaves (blk_pin, blk_pout).
 void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const uint32_t* sites, const uint8_t* ks,
-                        uint32_t len, float2* out);
+                        uint32_t len, float2* out, uint32_t* code);
 
 // ---------------------------------------------------------------------------------------------
 // Kernel launch interface (evolve.cu / sample.cu / pershot.cu).
@@ -528,11 +535,55 @@ struct DenseArgs {
 void launch_dense_pass(const DenseArgs& a, int n_sm, cudaStream_t s);
 int dense_ctas_per_sm();
 
+// One persistent launch over many circuits' dense passes (a device work queue, dense.cu).
+struct QJob {                        // one circuit's range of Kraus sets, prepared in place
+    const dense::Pass* passes;
+    const dense::Group* groups;
+    const dense::Block* blocks;
+    const uint32_t* hi;
+    const uint16_t* omap;
+    const float2* mats;
+    const dense::Override* ovr;
+    const float2* opool;
+    const uint32_t* ov_begin;        // [count] override range of each set
+    const uint32_t* ov_end;
+    float2* states;                  // [count][2^n]
+    double* part;                    // [count][2^(n - kT)] tile norms of the last pass
+    const double* wmix;              // [count] prod of unitary-mixture q
+    const double* qalpha;            // [count]
+    double* weights;                 // [count] or null
+    uint8_t* status;                 // [count] or null
+    float* scale;                    // [count]
+    uint32_t n, J, count, pad;
+};
+struct QTask {
+    uint64_t item0;                  // first global work item
+    uint32_t job, set;               // set: job-local index
+    uint32_t level;                  // pass j < J; J: finalisation; J + 1: scaling
+    uint32_t items;                  // work items of this task
+    uint32_t pred;                   // task that must finish first (~0: none)
+    uint32_t pred_items;             // its work items
+};
+struct QueueArgs {
+    const QJob* jobs;
+    const QTask* tasks;
+    uint32_t n_tasks;
+    uint64_t n_items;
+    unsigned long long* next;        // global item counter (zero before the launch)
+    uint32_t* done;                  // [n_tasks] finished items (zero before the launch)
+    uint32_t* err;                   // nonzero: a wait ran out (the task index + 1)
+    long long spin_cycles;           // wait budget in clock64 cycles
+    uint32_t stall_task;             // test hook: this task waits for one item more than its predecessor has
+};
+void launch_dense_queue(const QueueArgs& a, int n_sm, cudaStream_t s);
+int dense_queue_grid(int n_sm);
+
 int unique_max_qubits();
 size_t unique_bitmap_bytes(int n);
 void launch_unique(const uint32_t* bits, const uint64_t* d_pieces, uint32_t n_pieces, uint32_t count, int n,
                    uint32_t* d_bitmaps, unsigned long long* out, cudaStream_t s);
 int sample_cluster_max_qubits();
+void configure_samplers();
 int sample_light_max_qubits();
 // Default shot limit of the one-CTA-per-state light sampler (15 <= n <= 20); heavier states go to
 // the cluster sampler. Both give the same shots (exact integer prefix sums), so the limit only

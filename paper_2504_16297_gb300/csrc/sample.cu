@@ -631,6 +631,23 @@ void* noalloc_scratch(int device) {
     return g_noalloc_ptr[device];
 }
 
+// Sets the dynamic shared-memory limits of every sampler kernel (the launchers do the same lazily);
+// called before a launch sequence that may be captured into a CUDA graph.
+void configure_samplers() {
+    PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+    PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+    PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+    PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+    const size_t lsmem = ((size_t)kLightChunks + kLightChunks / 16 + 1) * sizeof(fx);
+    PTSBE_CUDA(cudaFuncSetAttribute(k_sample_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+    PTSBE_CUDA(cudaFuncSetAttribute(k_block_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
+}
+
 int sample_cluster_max_qubits() { return kSliceBits + 3; }
 int sample_light_max_qubits() { return kLightChunkBits + 7; }
 

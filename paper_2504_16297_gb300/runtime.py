@@ -146,6 +146,31 @@ class Ptsbe:
         """(milliseconds, launches, algorithmic bytes) accumulated for one kernel class."""
         return capi.ptsbe_get_timing(self.ctx, kernel_class, reset)
 
+    def batch_plan(self, jobs):
+        """Plans one persistent launch over many jobs: each job is (info, first, count, states, weights,
+        status, seed, bits) with device tensors (weights, status, bits may be None). Returns a batch id."""
+        recs = []
+        for (info, first, count, states, weights, status, seed, bits) in jobs:
+            recs.append(capi.ptsbe_job(info.set_id, first, count, _ptr(states), _ptr(weights), _ptr(status), seed,
+                                       _ptr(bits), bits.numel() if bits is not None else 0))
+        return capi.ptsbe_batch_plan(self.ctx, recs)
+
+    def batch_run(self, batch_id, graph: bool = False):
+        capi.ptsbe_batch_run(self.ctx, batch_id, capi.PTSBE_BATCH_GRAPH if graph else 0)
+
+    def batch_info(self, batch_id):
+        t, i, g, k = capi.ptsbe_batch_info(self.ctx, batch_id)
+        return {"tasks": t, "items": i, "grid": g, "kernels_per_run": k}
+
+    def batch_release(self, batch_id):
+        capi.ptsbe_batch_release(self.ctx, batch_id)
+
+    def set_queue_wait(self, cycles: int):
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_QUEUE_SPIN_CYCLES, int(cycles))
+
+    def set_queue_stall_task(self, task: int):
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_QUEUE_STALL_TASK, int(task))
+
     def reuse_stats(self):
         """(gates applied, gates without prefix reuse) of the last evolve call."""
         return capi.ptsbe_reuse_stats(self.ctx)

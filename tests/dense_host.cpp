@@ -73,8 +73,9 @@ void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>&
                 for (uint32_t b = G.blk_begin - ps.blk_begin; b < G.blk_end - ps.blk_begin; ++b) {
                     const Block& B = blocks[b];
                     const float2* m = mats + (B.mat - ps.mat_begin);
-                    if (ov < ovr.size() && ovr[ov].block == B.id) { m = &opool[ovr[ov].mat]; ++ov; }
-                    apply_block(v, B.code, m);
+                    int code = B.code;
+                    if (ov < ovr.size() && ovr[ov].block == B.id) { m = &opool[ovr[ov].mat]; code = (int)ovr[ov].code; ++ov; }
+                    apply_block(v, code, m);
                 }
                 for (int jj = 0; jj < kAmps; ++jj) tile[base ^ G.roff[jj]] = v[jj];
             }
@@ -111,8 +112,9 @@ int dh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
     }
 }
 
-// out[0..9]: passes, fix-up passes, groups, blocks, operations placed, operations placed more than
-// once or never, 2-qubit blocks, gates, passes staged in shared memory, staging size mismatches
+// out[0..10]: passes, fix-up passes, groups, blocks, operations placed, operations placed more than
+// once or never, 2-qubit blocks, gates, passes staged in shared memory, staging size mismatches,
+// blocks in diagonal-times-real form
 void dh_stats(uint64_t* out) {
     const DensePlan& P = g_plan;
     std::vector<int> seen(g_circ.ops.size(), 0);
@@ -135,6 +137,9 @@ void dh_stats(uint64_t* out) {
     for (const Pass& ps : P.passes) staged += ps.stage_bytes != 0;
     out[8] = staged;
     out[9] = (uint64_t)g_stage_errors;
+    uint64_t dr = 0;
+    for (const Block& B : P.blocks) dr += B.code >= kCodeDR;
+    out[10] = dr;
 }
 
 // Prepares the state of one Kraus set (entries sorted by site) from |0...0> through every pass, as
@@ -158,8 +163,9 @@ double dh_evolve(const uint32_t* sites, const uint8_t* ks, uint32_t len, float* 
         for (; i < eb.size() && eb[i].first == blk; ++i) { ss.push_back(sites[eb[i].second]); kk.push_back(ks[eb[i].second]); }
         const uint32_t off = (uint32_t)opool.size();
         opool.resize(off + (P.blk_nq[blk] == 1 ? 4 : 16));
-        dense_block_matrix(g_circ, P, blk, ss.data(), kk.data(), (uint32_t)ss.size(), &opool[off]);
-        ovr.push_back({blk, off});
+        uint32_t code = 0;
+        dense_block_matrix(g_circ, P, blk, ss.data(), kk.data(), (uint32_t)ss.size(), &opool[off], &code);
+        ovr.push_back({blk, off, code});
     }
     for (uint32_t j = 0; j < P.passes.size(); ++j) run_pass(j, psi, ovr, opool);
     double nrm = 0;

@@ -67,9 +67,10 @@ def register(dh, circ):
 
 
 def stats(dh):
-    out = (C.c_uint64 * 10)()
+    out = (C.c_uint64 * 11)()
     dh.dh_stats(out)
-    keys = ["passes", "fixup", "groups", "blocks", "placed", "misplaced", "blocks2", "gates", "staged", "stage_errors"]
+    keys = ["passes", "fixup", "groups", "blocks", "placed", "misplaced", "blocks2", "gates", "staged", "stage_errors",
+            "dr"]
     return dict(zip(keys, [int(x) for x in out]))
 
 
@@ -179,6 +180,8 @@ def test_thirty_qubit_plan(dh):
     assert st["gates"] == circ.n_gates
     assert passes <= 40
     assert st["staged"] == passes - st["fixup"] and st["stage_errors"] == 0
+    # every block but the last on each qubit takes the diagonal-times-real form (U3 = P R_y P)
+    assert st["dr"] >= 0.95 * st["blocks"]
     mean = C.c_double()
     bad = dh.dh_bank_stats(C.byref(mean))
     assert mean.value >= 14.0, (bad, mean.value)
