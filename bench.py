@@ -64,6 +64,9 @@ def parse():
                     help="Kraus sets of the 30-qubit workload timed in the dense leg, a prefix of the trie "
                          "(canonical) order (0 = skip the leg, -1 = the whole job)")
     ap.add_argument("--dense30-only", action="store_true", help="run only the 30-qubit dense leg and print it")
+    ap.add_argument("--dense-probe", type=int, default=0, metavar="QUBITS",
+                    help="prepare and sample one error-free brickwork set (16 layers) of QUBITS qubits with the "
+                         "dense passes, states not returned, and print its timing (the profiling case)")
     return ap.parse_args()
 
 
@@ -152,6 +155,8 @@ def traffic_for(kernel: str, bytes_per_launch: float = 0.0, units: int = 0):
         if not e or e.get("source_sha") != source_sha(e["sources"]):
             return None
         c = e.get("capture")
+        if e.get("model") == "per_amplitude" and c and units:
+            return float((c["dram_bytes_read"] + c["dram_bytes_write"]) * units / c["amplitudes"])
         if e.get("model") == "per_state" and c and units:
             shot_bytes = bytes_per_launch - units * c["state_bytes"]
             return float(c["dram_bytes_read"] * units / c["states"] + c["dram_bytes_write"]
@@ -497,6 +502,149 @@ def uneven_leg(dev, reps: int = 2, margin_gb: float = 24.0):
                      "then the samplers; replayed as a CUDA graph")}
 
 
+def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
+    """The 30-qubit workload: brickwork, 60 layers (1,800 U3 + 870 CX), DEPOL1 after every U3 and
+    DEPOL2 after every CX at p = 5e-4, 2,000 proportional samples, 10^9 shots. States (8 GiB each)
+    are not returned: ptsbe_evolve_sample prepares the sets branch by branch with dense passes
+    (prefix reuse: sets share the state up to the pass of their first entry) and samples each from
+    its global-memory CDF. Timed with CUDA events on the launch stream: a prefix of the sets in
+    canonical (trie) order -- the error-free set, then the sets by first error site -- or the whole
+    job. The full job's schedule is planned (no device work) for its prefix-reuse savings."""
+    import torch
+    from workloads import config
+    from paper_2504_16297_gb300 import capi
+    c = config(3)
+    circ = c["circuit"]
+    n = circ.n_qubits
+    cid = P.register(circ)
+    t0 = time.perf_counter()
+    info = P.sample_kraus(cid, "proportional", seed=c["seed"], nsamples=c["nsamples"], total_shots=c["total_shots"])
+    t_pts = time.perf_counter() - t0
+    plan = P.dense_plan_info(cid)
+    full_applied, full_nominal = P.plan(info, 0, info.count)
+    count = info.count if max_sets < 0 else min(max_sets, info.count)
+    shots = int(info.shot_offsets[count])
+    w = torch.empty(count, dtype=torch.float64, device=dev)
+    s = torch.empty(count, dtype=torch.uint8, device=dev)
+    bits = torch.empty(max(shots, 1), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # warm-up: uploads, workspace, library buffers (one set)
+    P.evolve_sample(info, 0, 1, None, w, s, seed, bits)
+    torch.cuda.synchronize()
+    P.set_timing(True)
+    for k in range(8):
+        P.timing(k, reset=True)
+    clk = Clocks(clocks_index)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.evolve_sample(info, 0, count, None, w, s, seed, bits)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    applied, nominal = P.reuse_stats()
+    launches, fma = P.dense_work()
+    kern = {}
+    for cls, name in [(capi.PTSBE_TIMER_DENSE, "dense_pass"), (capi.PTSBE_TIMER_EVOLVE_FINALIZE, "finalize"),
+                      (capi.PTSBE_TIMER_SAMPLE, "sample"), (capi.PTSBE_TIMER_SAMPLE_LIGHT, "sample_light")]:
+        kms, kl, kb = P.timing(cls, reset=True)
+        if kl:
+            kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
+    P.set_timing(False)
+    null = int(s.sum().item())
+    # the traditional per-shot path on this workload: one trajectory prepared from |0...0> for one
+    # shot (for these unitary-mixture channels Algorithm 1's Kraus draws do not depend on the state,
+    # so a shot costs one full preparation); timed on the error-free trajectory
+    one = P.sample_kraus(cid, "targeted", targeted=[[]], targeted_shots=np.array([1], np.uint64))
+    b1 = torch.empty(1, dtype=torch.int32, device=dev)
+    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    P.evolve_sample(one, 0, 1, None, w, s, seed, b1)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ps_ms = f0.elapsed_time(f1)
+    P.release_set(one)
+    hbm_peak, hbm_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12             # FP32 TFLOP/s: SMs x 128 FMA lanes x 2 x clock
+    d = kern.get("dense_pass")
+    dense = None
+    if d:
+        gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        tfl = 2 * fma / (d["ms"] / 1e3) / 1e12
+        dense = {"ms": d["ms"], "launches": d["launches"], "algorithmic_bytes": d["bytes"],
+                 "gate_apply_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": hbm_kind,
+                 "fma": fma, "fp32_tflops": tfl, "alu_frac": tfl / alu_peak, "alu_peak_tflops": alu_peak,
+                 "alu_peak_kind": "derived: SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
+                 "ms_per_pass_launch": d["ms"] / d["launches"]}
+    est_s = None
+    if applied:
+        est_s = (ms / 1e3) * full_applied / applied
+    out = {"workload": c["name"], "qubits": n, "layers": 60, "gates": circ.n_gates, "noise_sites": circ.n_sites,
+           "sets_total": info.count, "sets_timed": count, "shots_total": info.total_shots, "shots_timed": shots,
+           "timed": "whole job" if count == info.count else f"first {count} of {info.count} sets in canonical (trie) order",
+           "ms": ms, "shots_per_s": shots / (ms / 1e3), "null_sets": null, "host_pts_s": t_pts,
+           "trajectory_gates_per_s": {"applied": applied / (ms / 1e3), "logical": count * circ.n_gates / (ms / 1e3)},
+           "prefix_reuse": {"timed_sets": {"gates_applied": applied, "gates_without_reuse": nominal,
+                                           "savings": 1 - applied / nominal if nominal else None},
+                            "full_job": {"gates_applied": full_applied, "gates_without_reuse": full_nominal,
+                                         "savings": 1 - full_applied / full_nominal if full_nominal else None}},
+           "plan": plan, "kernels": kern, "dense": dense,
+           "roofline": ({"bound": "alu", "kernel": "k_dense_pass", "achieved": dense["fp32_tflops"], "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": dense["alu_frac"],
+                         "traffic": traffic_for("dense_pass", units=1 << n)} if dense else None),
+           "roofline_hbm": ({"bound": "hbm", "kernel": "k_dense_pass", "achieved": dense["gate_apply_gbs"],
+                             "peak": hbm_peak, "unit": "GB/s", "frac": dense["hbm_frac"],
+                             "traffic": traffic_for("dense_pass", units=1 << n)} if dense else None),
+           "full_job_estimate_s": est_s,
+           "pershot": {"value": 1.0 / (ps_ms / 1e3), "unit": "shots/s", "ms_per_shot": ps_ms,
+                       "kind": "one full 30-qubit trajectory prepared per shot (dense passes, no reuse)"},
+           "speedup_vs_pershot": (shots / (ms / 1e3)) / (1.0 / (ps_ms / 1e3)),
+           "clocks": clocks}
+    P.release_set(info)
+    P.release_circuit(cid)
+    del bits, w, s
+    torch.cuda.empty_cache()
+    return out
+
+
+def dense_probe(dev, n: int, layers: int = 16, seed: int = 1003):
+    """One error-free set of an n-qubit brickwork (U3 layer + CX brickwork, `layers` times) prepared
+    by the dense passes and sampled (1,000 shots), states not returned: the small case the dense
+    pass kernel is profiled on. Three runs; the last is timed with CUDA events."""
+    import torch
+    from workloads import brickwork
+    from paper_2504_16297_gb300 import capi
+    from paper_2504_16297_gb300.runtime import Ptsbe
+    P = Ptsbe(device=dev.index or 0, stream=torch.cuda.current_stream(dev).cuda_stream)
+    circ = brickwork(n, layers, 5e-4, 5e-4, seed)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "targeted", targeted=[[]], targeted_shots=np.array([1000], np.uint64))
+    w = torch.empty(1, dtype=torch.float64, device=dev)
+    s = torch.empty(1, dtype=torch.uint8, device=dev)
+    bits = torch.empty(1000, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        P.evolve_sample(info, 0, 1, None, w, s, 7, bits)
+    torch.cuda.synchronize()
+    P.set_timing(True)
+    P.timing(capi.PTSBE_TIMER_DENSE, reset=True)
+    P.evolve_sample(info, 0, 1, None, w, s, 7, bits)
+    P.synchronize()
+    dms, dl, db = P.timing(capi.PTSBE_TIMER_DENSE, reset=True)
+    P.set_timing(False)
+    out = {"qubits": n, "layers": layers, "passes": dl, "dense_ms": dms, "ms_per_pass": dms / max(dl, 1),
+           "gate_apply_gbs": db / (dms / 1e3) / 1e9 if dms else None, "weight": float(w.item()),
+           "status": int(s.item())}
+    P.release_set(info)
+    P.release_circuit(cid)
+    P.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -563,6 +711,11 @@ def main():
     if args.uneven_only:
         if rank == 0:
             print(json.dumps({"uneven": uneven_leg(torch.device("cuda", local))}), flush=True)
+        return
+
+    if args.dense_probe:
+        if rank == 0:
+            print(json.dumps({"dense_probe": dense_probe(torch.device("cuda", local), args.dense_probe)}), flush=True)
         return
 
     if args.dense30_only:

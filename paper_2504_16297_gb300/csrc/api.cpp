@@ -929,7 +929,7 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
     E.weights = d_weights;
     E.status = d_status;
     E.states = user;
-    ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb * count, [&] { launch_evolve_finalize(E, count, d_scale, ctx->stream); });
+    ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb * count, [&] { launch_evolve_finalize(E, count, d_scale, ctx->stream, true); });
 }
 
 // ptsbe_evolve_sample without caller states: the states live in library buffers, one branch at
@@ -1085,7 +1085,7 @@ void stream_evolve_sample(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, u
         E.weights = d_weights ? d_weights + a : nullptr;
         E.status = d_status + a;
         E.states = bufs[x.src];
-        ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb, [&] { launch_evolve_finalize(E, 1, d_scale, ctx->stream); });
+        ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb, [&] { launch_evolve_finalize(E, 1, d_scale, ctx->stream, true); });
         if (s.shots[first + a])
             sample_range(ctx, s, c, first + a, 1, bufs[x.src], d_status + a, seed, d_bits + (s.shot_off[first + a] - base), nullptr);
     }

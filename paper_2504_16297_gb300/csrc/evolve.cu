@@ -1013,8 +1013,9 @@ void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, c
     count_launch();
 }
 
-void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s) {
-    if (a.n == a.tb || count == 0) return;
+void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s, bool one_tile_too) {
+    // a one-tile state's norm is fused into the tile kernels of the other evolve kernels
+    if ((a.n == a.tb && !one_tile_too) || count == 0) return;
     k_evolve_reduce<<<count, 256, 0, s>>>(a, d_scale);
     PTSBE_CUDA(cudaGetLastError());
         count_launch();

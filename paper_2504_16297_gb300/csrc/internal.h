@@ -429,7 +429,10 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
 // launch_evolve_stage of the same stage and nodes.
 void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,
                           int sets_per_warp);
-void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
+// Reduce (weights, flags, scales) and scale; for n == tb only with one_tile_too (the dense passes:
+// the other kernels normalise a one-tile state themselves).
+void launch_evolve_finalize(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s,
+                            bool one_tile_too = false);
 void launch_evolve_reduce(const EvolveArgs& a, uint32_t count, float* d_scale, cudaStream_t s);
 size_t evolve_frame_program_bytes();   // workspace per node of a frame-kernel launch
 

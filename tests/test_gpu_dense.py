@@ -63,7 +63,7 @@ def compare_sets(P, oracle_mod, circ, info, idxs, reuse, shots=True, parallel=Fa
     return st, w, s
 
 
-@pytest.mark.parametrize("n,layers", [(13, 8), (15, 6), (18, 4)])
+@pytest.mark.parametrize("n,layers", [(12, 10), (13, 8), (15, 6), (18, 4)])
 @pytest.mark.parametrize("reuse", [False, True])
 def test_dense_brickwork_matches_oracle(P, oracle_mod, n, layers, reuse):
     circ = brickwork(n, layers, 0.02, 0.03, seed=70 + n)
@@ -131,7 +131,7 @@ def _stream_vs_batch(P, info, n, reuse=True):
     return w2, s2, bits_b
 
 
-@pytest.mark.parametrize("n,layers", [(15, 10), (18, 8), (22, 6)])
+@pytest.mark.parametrize("n,layers", [(12, 12), (15, 10), (18, 8), (22, 6)])
 def test_stream_matches_batch(P, oracle_mod, n, layers):
     circ = brickwork(n, layers, 4e-3, 8e-3, seed=40 + n)
     cid = P.register(circ)
