@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--evolve-kernel", default="auto", choices=["auto", "frame", "sweep", "registers"])
     ap.add_argument("--e2e-copy", default="overlap", choices=["overlap", "serial"],
                     help="e2e device-to-host copies on a side stream or on the compute stream")
+    ap.add_argument("--split-fill", type=int, default=0, metavar="PERCENT",
+                    help="percentage of each state's zero fill run beside the program prepass (0: all in the evolve launch)")
     ap.add_argument("--separate", action="store_true",
                     help="time ptsbe_evolve_batch + ptsbe_sample_shots instead of the one-call ptsbe_evolve_sample")
     ap.add_argument("--no-backward", action="store_true",
@@ -532,7 +534,7 @@ def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
     P.evolve_sample(info, 0, 1, None, w, s, seed, bits)
     torch.cuda.synchronize()
     P.set_timing(True)
-    for k in range(8):
+    for k in range(capi.PTSBE_TIMER_CLASSES):
         P.timing(k, reset=True)
     clk = Clocks(clocks_index)
     clk.start()
@@ -743,6 +745,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     P = Ptsbe(device=local, stream=stream.cuda_stream)
     P.set_evolve_kernel(args.evolve_kernel)
+    P.set_split_fill(args.split_fill)
     states = torch.empty((K, 1 << n), dtype=torch.complex64, device=dev)
     # Results of consecutive steps alternate between two buffers, so the copy of step i's shots,
     # weights and flags to the host (its own stream) overlaps step i+1's kernels.
@@ -791,7 +794,7 @@ def main():
         barrier()
         if instrument:
             P.set_timing(True)
-            for cls in range(6):
+            for cls in range(capi.PTSBE_TIMER_CLASSES):
                 P.timing(cls, reset=True)
         l0 = capi.ptsbe_kernel_launches()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -805,7 +808,10 @@ def main():
         launches = capi.ptsbe_kernel_launches() - l0
         kern = {}
         if instrument:
-            for cls, name in enumerate(["evolve_stage", "evolve_finalize", "sample", "pershot", "evolve_program", "sample_light"]):
+            for cls, name in [(capi.PTSBE_TIMER_EVOLVE_STAGE, "evolve_stage"), (capi.PTSBE_TIMER_EVOLVE_FINALIZE, "evolve_finalize"),
+                              (capi.PTSBE_TIMER_SAMPLE, "sample"), (capi.PTSBE_TIMER_PERSHOT, "pershot"),
+                              (capi.PTSBE_TIMER_EVOLVE_PROGRAM, "evolve_program"), (capi.PTSBE_TIMER_SAMPLE_LIGHT, "sample_light"),
+                              (capi.PTSBE_TIMER_ZERO_FILL, "zero_fill")]:
                 kms, kl, kb = P.timing(cls, reset=True)
                 if kl:
                     kern[name] = {"ms": kms, "launches": kl, "bytes": kb}
@@ -960,6 +966,8 @@ def main():
             "config": {"workload": WORKLOAD, "qubits": n, "kraus_sets": K, "shots": M, "pts": "topk",
                        "prefix_reuse": True, "call": "evolve_batch + sample_shots" if args.separate else "evolve_sample", "amplitudes": "complex64, FP64 norms, CDF in 2^-62 fixed point (exact integer sums)",
                        "l2": "inputs larger than L2 (10.5 GB of states per step)",
+                       "zero_fill": (f"{args.split_fill}% of each state on a second stream beside the program prepass, the rest in the evolve launch"
+                                     if args.split_fill else "in the evolve launch"),
                        "parallelism": f"{world} independent replicas (weak scaling)", "tuning": tuning},
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,
             "pershot": pershot,

@@ -492,7 +492,16 @@ enum {
     /* Test hook of the work queue: the task with this index waits for one tile more than its
      * predecessor has, so its wait always runs out (no GPU fault: the wait is bounded and the
      * kernel returns); -1 (default) turns it off. */
-    PTSBE_OPT_QUEUE_STALL_TASK = 5
+    PTSBE_OPT_QUEUE_STALL_TASK = 5,
+    /* Percentage p (0..100, default 0) of each state's bytes zeroed apart from the evolve launch,
+     * when a call's plan is one stage ending in the small sparse final store (each state's nonzero
+     * amplitudes held on chip, as for the syndrome workload): that part of the zero fill runs as
+     * its own kernel on a second stream of the context, concurrently with the program prepass, and
+     * the evolve launch zeroes the rest (rounded to whole 4 KB chunks). Same outputs; speed only.
+     * The second stream starts after the work the call found on the context stream and the
+     * context stream waits for it, so the call stays ordered on the context stream (and a capture
+     * of that stream into a CUDA graph takes both). */
+    PTSBE_OPT_SPLIT_FILL = 6
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
@@ -561,7 +570,9 @@ enum {
     PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */
     PTSBE_TIMER_BACKWARD = 6,         /* ptsbe_backward                                           */
     PTSBE_TIMER_DENSE = 7,            /* dense tile passes (evolve kernel 4, and states not returned) */
-    PTSBE_TIMER_CLASSES = 8
+    PTSBE_TIMER_ZERO_FILL = 8,        /* zero fill of the states of a small sparse final stage, run on
+                                         the context's second stream beside the program prepass      */
+    PTSBE_TIMER_CLASSES = 9
 };
 
 /* enable != 0: every later launch is bracketed by CUDA events recorded on the context stream and

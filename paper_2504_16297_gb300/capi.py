@@ -24,9 +24,12 @@ PTSBE_OPT_PROGRAM_SETS_PER_WARP = 2
 PTSBE_OPT_FAIL_ALLOC = 3
 PTSBE_OPT_QUEUE_SPIN_CYCLES = 4
 PTSBE_OPT_QUEUE_STALL_TASK = 5
+PTSBE_OPT_SPLIT_FILL = 6
 PTSBE_BATCH_GRAPH = 1
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
- PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE) = range(8)
+ PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE,
+ PTSBE_TIMER_ZERO_FILL) = range(9)
+PTSBE_TIMER_CLASSES = 9
 
 
 class ptsbe_op(C.Structure):

@@ -96,6 +96,9 @@ struct ptsbe_ctx {
     int evolve_kernel = 0;
     uint64_t light_shots = kLightShotLimit;   // states with at most this many shots: one-CTA sampler
     int prog_sets_per_warp = 8;                // frame program prepass: Kraus sets per warp (measured)
+    int split_fill = 0;                        // small sparse final stage: percent of each state zeroed beside the program prepass
+    cudaStream_t aux = nullptr;                // second stream of the context (the zero fill), joined by events
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int n_sm = 0;                      // streaming multiprocessors of the device
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
@@ -105,18 +108,30 @@ struct ptsbe_ctx {
         PTSBE_CUDA(cudaEventCreate(&e));
         return e;
     }
-    // Brackets a launch of kernel class `cls` (no-op when timing is off).
+    // Brackets a launch of kernel class `cls` on stream `s` (no-op when timing is off).
     template <class F>
-    void timed(int cls, double bytes, F&& launch) {
+    void timed_on(cudaStream_t s, int cls, double bytes, F&& launch) {
         if (!timing) { launch(); return; }
         ClassTimer& t = timers[cls];
         cudaEvent_t a = take_event(t), b = take_event(t);
-        PTSBE_CUDA(cudaEventRecord(a, stream));
+        PTSBE_CUDA(cudaEventRecord(a, s));
         launch();
-        PTSBE_CUDA(cudaEventRecord(b, stream));
+        PTSBE_CUDA(cudaEventRecord(b, s));
         t.pending.push_back({a, b});
         t.launches += 1;
         t.bytes += bytes;
+    }
+    template <class F>
+    void timed(int cls, double bytes, F&& launch) { timed_on(stream, cls, bytes, static_cast<F&&>(launch)); }
+    // Work on the auxiliary stream starts after everything enqueued on the context stream so far
+    // (fork) and the context stream waits for it before its next launch (join).
+    void fork_aux() {
+        PTSBE_CUDA(cudaEventRecord(ev_fork, stream));
+        PTSBE_CUDA(cudaStreamWaitEvent(aux, ev_fork, 0));
+    }
+    void join_aux() {
+        PTSBE_CUDA(cudaEventRecord(ev_join, aux));
+        PTSBE_CUDA(cudaStreamWaitEvent(stream, ev_join, 0));
     }
     void collect_timers() {
         for (ClassTimer& t : timers) {
@@ -628,6 +643,14 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     if (frame)
         for (uint32_t j = 0; j < J; ++j)
             if (P.fstages[j].sparse_final) { A.sparse_final_stage = (int)j; A.small_bits = (int)P.fstages[j].sbits; }
+    // A one-stage plan ending in the small sparse final store writes only each state's support
+    // (at most 2^small_bits amplitudes); every other amplitude is zero. That zero fill needs no
+    // program, so it runs as its own HBM-bound kernel on the auxiliary stream while the
+    // latency-bound program prepass runs, and the evolve launch waits for it.
+    // prefix of each state zeroed beside the prepass: whole 4 KB chunks (the in-launch fill's unit)
+    const uint64_t prefill = (uint64_t)((double)sbytes * ctx->split_fill / 100.0) / 4096u * 4096u;
+    const bool split_fill = frame && prefill && ctx->aux && J == 1 && A.sparse_final_stage == 0 &&
+                            A.small_bits > 0 && launches[0].second == count && (uint64_t)sbytes % 4096u == 0;
     for (uint32_t j = 0; j < J; ++j) {
         const auto& L = launches[j];
         if (L.second == 0) continue;
@@ -639,11 +662,20 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         double bytes = 0;
         for (size_t t = L.first; t < L.first + L.second; ++t)
             bytes += (fresh[lists[t]] && j == 0) ? sbytes : 2 * sbytes;
+        if (split_fill) bytes -= (double)L.second * (double)prefill;   // zeros stored by the prepass-side fill
         if (A.shot_bits && j + 1 == J) bytes += 4.0 * (double)fused_shots;
+        if (split_fill) ctx->fork_aux();
         if (frame)
             ctx->timed(PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
                 launch_frame_program(A, (int)j, d_lists + L.first, L.second, ctx->stream, ctx->prog_sets_per_warp);
             });
+        A.prefill_bytes = 0;
+        if (split_fill) {
+            ctx->timed_on(ctx->aux, PTSBE_TIMER_ZERO_FILL, (double)count * (double)prefill,
+                          [&] { launch_zero_states(user, (uint64_t)sbytes, prefill, count, ctx->n_sm, ctx->aux); });
+            ctx->join_aux();
+            A.prefill_bytes = prefill;
+        }
         ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
             launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
         });
@@ -1186,6 +1218,15 @@ int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
             (void)cudaGetLastError();
             return PTSBE_ERR_CUDA;
         }
+        if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (ctx->aux) cudaStreamDestroy(ctx->aux);
+            if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+            cudaMemPoolDestroy(ctx->pool);
+            return PTSBE_ERR_CUDA;
+        }
     }
     *out = ctx.release();
     return PTSBE_OK;
@@ -1213,6 +1254,12 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
             if (kv.second->graph) cudaGraphExecDestroy(kv.second->graph);
         }
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->aux) {
+            if (cudaStreamSynchronize(ctx->aux) != cudaSuccess) status = PTSBE_ERR_CUDA;
+            cudaStreamDestroy(ctx->aux);
+        }
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
         ctx->free_staging();
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
@@ -1479,6 +1526,9 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
             if (value < -1) fail(PTSBE_ERR_INVALID, "allocation failure index must be >= -1");
             ctx->fail_alloc_at = value;
             ctx->alloc_count = 0;
+        } else if (option == PTSBE_OPT_SPLIT_FILL) {
+            if (value < 0 || value > 100) fail(PTSBE_ERR_INVALID, "split fill must be a percentage, 0 to 100");
+            ctx->split_fill = (int)value;
         } else if (option == PTSBE_OPT_PROGRAM_SETS_PER_WARP) {
             if (value != 0 && value != 4 && value != 8 && value != 16) fail(PTSBE_ERR_INVALID, "sets per warp must be 0, 4, 8 or 16");
             ctx->prog_sets_per_warp = value ? (int)value : 8;

@@ -146,6 +146,31 @@ k_frame_program(EvolveArgs a, int stage_idx, const uint32_t* __restrict__ nodes,
     P.B = B;
 }
 
+// Zero fill apart from the evolve launch (the small sparse final stage writes only each state's
+// support, so every other amplitude of its output is a zero that can be stored before the programs
+// exist): the first `prefix` bytes of each of the states at base + i * state_bytes, by bulk copies
+// (TMA) of a zeroed shared buffer. Lane l of CTA c copies chunks 32 c + l, 32 (c + G) + l, ... of
+// the count * prefix / kFillChunk chunks (G CTAs); prefix is a multiple of kFillChunk.
+constexpr uint32_t kFillChunk = 4096;
+__global__ void __launch_bounds__(32) k_zero_states(unsigned char* __restrict__ base, uint64_t state_bytes,
+                                                    uint64_t prefix, uint64_t chunks) {
+    __shared__ __align__(128) float4 z[kFillChunk / 16];
+    for (uint32_t v = threadIdx.x; v < kFillChunk / 16; v += 32) z[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(z);
+    const uint64_t per_state = prefix / kFillChunk;
+    const uint64_t lanes = (uint64_t)gridDim.x * 32u;
+    for (uint64_t c = (uint64_t)blockIdx.x * 32u + threadIdx.x; c < chunks; c += lanes) {
+        const uint64_t st = c / per_state, off = st * state_bytes + (c - st * per_state) * kFillChunk;
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                     :: "l"(base + off), "r"(src), "n"(kFillChunk) : "memory");
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Copies from global memory (read-only path: the source must not be in shared memory).
 __device__ __forceinline__ void copy_words(void* dst, const void* src, uint32_t bytes, uint32_t t, uint32_t nt) {
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
@@ -346,17 +371,19 @@ k_evolve_frame(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict
         // through cosets by thread-count bits, so the count is a power of two); everyone meets
         // for the norm and the scatter once warp 0 has waited for the copies.
         __shared__ Step fin;
-        for (uint32_t v = tid; v < (uint32_t)kZeroChunk / 16; v += nthr) zbuf[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint64_t zbytes = (uint64_t)8 << n;
+        if (a.prefill_bytes < zbytes) {
+            for (uint32_t v = tid; v < (uint32_t)kZeroChunk / 16; v += nthr) zbuf[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
         __syncthreads();
         if (B.npool <= (uint32_t)kMaxPool) poolp = pool;
         if (B.nsteps <= (uint32_t)kMaxSteps) Sp = S;
         const uint32_t warp = tid >> 5;
         if (warp == 0) {
-            if (tid == 0) {
+            if (tid == 0 && a.prefill_bytes < zbytes) {
                 const uint32_t src = (uint32_t)__cvta_generic_to_shared(zbuf);
-                const uint64_t bytes = (uint64_t)8 << n;
-                for (uint64_t off = 0; off < bytes; off += kZeroChunk)
+                for (uint64_t off = a.prefill_bytes; off < zbytes; off += kZeroChunk)
                     asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
                                  :: "l"(reinterpret_cast<unsigned char*>(g) + off), "r"(src), "n"(kZeroChunk) : "memory");
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -988,6 +1015,17 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }
+}
+
+void launch_zero_states(void* base, uint64_t state_bytes, uint64_t prefix, uint32_t count, int n_sm, cudaStream_t s) {
+    if (prefix == 0 || count == 0) return;
+    if ((uintptr_t)base % 16 || state_bytes % 16 || prefix % kFillChunk || prefix > state_bytes)
+        fail(PTSBE_ERR_INVALID, "zero fill: unaligned base, or a prefix that is not whole 4 KB chunks of the state");
+    const uint64_t chunks = (uint64_t)count * (prefix / kFillChunk);
+    const uint64_t grid = std::min<uint64_t>((chunks + 31) / 32, (uint64_t)std::max(n_sm, 1));
+    k_zero_states<<<(uint32_t)grid, 32, 0, s>>>(reinterpret_cast<unsigned char*>(base), state_bytes, prefix, chunks);
+    PTSBE_CUDA(cudaGetLastError());
+    count_launch();
 }
 
 void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,

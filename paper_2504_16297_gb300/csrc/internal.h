@@ -398,6 +398,9 @@ struct EvolveArgs {
     // support CDF in slot node_export[i] of support_out (SupportCdf layout) for k_sample_support.
     const uint32_t* node_export;
     unsigned char* support_out;
+    // Small sparse final stage: the first prefill_bytes of every state were zeroed by
+    // k_zero_states before the launch; the launch's bulk copies zero the rest.
+    uint64_t prefill_bytes;
 };
 
 // A state's outcome CDF over its support, in increasing outcome order (2^-62 fixed point), as the
@@ -427,6 +430,10 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                          cudaStream_t s, int kernel = 0);
 // Frame kernel (kernel 0 or 3): builds the per-node programs of a stage; must precede
 // launch_evolve_stage of the same stage and nodes.
+// Zero fill of the first `prefix` bytes (a multiple of 4096) of each of `count` states of
+// `state_bytes` from the 16-byte aligned `base`: bulk copies of a zeroed shared buffer, at most one
+// one-warp CTA per SM (it shares the SMs with a running program prepass).
+void launch_zero_states(void* base, uint64_t state_bytes, uint64_t prefix, uint32_t count, int n_sm, cudaStream_t s);
 void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,
                           int sets_per_warp);
 // Reduce (weights, flags, scales) and scale; for n == tb only with one_tile_too (the dense passes:

@@ -135,6 +135,11 @@ class Ptsbe:
         """Kraus sets per warp of the frame program prepass (4, 8 or 16; 0 = default, 8)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_PROGRAM_SETS_PER_WARP, int(spw))
 
+    def set_split_fill(self, percent: int):
+        """Percentage of each state of a small sparse final stage zeroed on the context's second
+        stream beside the program prepass (default 0: all of it inside the evolve launch)."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_SPLIT_FILL, int(percent))
+
     def set_light_shots(self, limit: int):
         """Shot count up to which a state is sampled by the one-CTA light sampler."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_LIGHT_SHOTS, int(limit))

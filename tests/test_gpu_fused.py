@@ -162,6 +162,34 @@ def test_dense_states_fall_back_to_samplers(kernel):
     _same(_run(P, info, 12, 21, False), _run(P, info, 12, 21, True))
 
 
+@pytest.mark.parametrize("fused,percent", [(True, 100), (True, 37), (False, 100), (False, 50)])
+def test_zero_fill_beside_program_prepass(fused, percent):
+    """Part (or all) of the states' zero fill of a one-stage sparse final plan runs on the context's
+    second stream beside the program prepass, the rest inside the evolve launch: the outputs equal
+    those of the fill inside the evolve launch, and the split fill is one launch of its own over
+    that share of every state (whole 4 KB chunks)."""
+    from paper_2504_16297_gb300 import capi
+    P = gpu_ctx()
+    circ = syndrome17(rounds=2)
+    n = circ.n_qubits
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "topk", k=1500, total_shots=3_000_000)
+    try:
+        P.set_split_fill(0)
+        off = _run(P, info, n, 29, fused)
+        P.set_split_fill(percent)
+        P.set_timing(True)
+        P.timing(capi.PTSBE_TIMER_ZERO_FILL, reset=True)
+        on = _run(P, info, n, 29, fused)
+        _, launches, nbytes = P.timing(capi.PTSBE_TIMER_ZERO_FILL, reset=True)
+    finally:
+        P.set_timing(False)
+        P.set_split_fill(0)
+    _same(off, on)
+    state = 8 << n
+    assert launches == 1 and nbytes == info.count * (state * percent // 100 // 4096 * 4096)
+
+
 def test_evolve_sample_errors():
     """Capacity and pointer checks before any launch."""
     torch = torch_cuda()

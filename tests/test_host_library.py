@@ -210,6 +210,11 @@ def test_options_validate_values(host):
         host.set_light_shots(-1)
     with pytest.raises(capi.PtsbeError):
         capi.ptsbe_set_option(host.ctx, 99, 0)
+    for pct in (0, 50, 100):
+        host.set_split_fill(pct)
+    for bad in (101, -1):
+        with pytest.raises(capi.PtsbeError):
+            capi.ptsbe_set_option(host.ctx, capi.PTSBE_OPT_SPLIT_FILL, bad)
 
 
 @pytest.mark.parametrize("n", [2, 5, 9])
