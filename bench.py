@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the uneven batch (512 brickwork circuits, 12-22 qubits, 64 samples each)")
     ap.add_argument("--uneven-only", action="store_true", help="run only the uneven batch and print its JSON object")
+    ap.add_argument("--pershot-tile-bits", type=int, default=0, help="tile bits of the per-shot plan (0: default)")
     ap.add_argument("--pershot-shots", type=int, default=2048,
                     help="shots of the traditional per-shot path timed for comparison (0 = skip)")
     ap.add_argument("--dense30-sets", type=int, default=DENSE30_SETS,
@@ -847,19 +848,31 @@ def main():
     pershot = None
     if args.pershot_shots > 0:
         cid = P.register(circ)
+        P.set_pershot_tile_bits(args.pershot_tile_bits)
         ps_bits = torch.empty(args.pershot_shots, dtype=torch.int32, device=dev)
         P.pershot(cid, seed, 0, min(64, args.pershot_shots), ps_bits)      # warm-up
         barrier()
+        P.set_timing(True)
+        P.timing(capi.PTSBE_TIMER_PERSHOT, reset=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         P.pershot(cid, seed, 0, args.pershot_shots, ps_bits)
         e1.record(stream)
         barrier()
         ps_ms = e0.elapsed_time(e1)
+        k_ms, k_launches, k_bytes = P.timing(capi.PTSBE_TIMER_PERSHOT, reset=True)
+        P.set_timing(False)
         P.release_circuit(cid)
         del ps_bits
+        # its own roofline: every stage reads and writes each state once (16 B per amplitude), the
+        # readout reads it once more; its kernels run back to back, so their event time is its time
+        ps_gbs = k_bytes / (k_ms / 1e3) / 1e9 if k_ms else None
+        hbm_peak, hbm_kind = peaks()
         pershot = {"value": args.pershot_shots / (ps_ms / 1e3), "unit": "shots/s", "shots": args.pershot_shots,
-                   "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot"}
+                   "ms": ps_ms, "kind": "Algorithm 1 on the same GPU, same tile kernels, one state per shot",
+                   "tile_bits": args.pershot_tile_bits or "default", "launches": k_launches, "algorithmic_bytes": k_bytes,
+                   "roofline": {"bound": "hbm", "achieved": ps_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": ps_gbs / hbm_peak if ps_gbs else None, "peak_kind": hbm_kind}}
 
     # unique-shot statistic (Sec. 4): distinct outcomes among the shots of the heaviest sets, from
     # one more step outside the timed region

@@ -501,7 +501,11 @@ enum {
      * The second stream starts after the work the call found on the context stream and the
      * context stream waits for it, so the call stays ordered on the context stream (and a capture
      * of that stream into a CUDA graph takes both). */
-    PTSBE_OPT_SPLIT_FILL = 6
+    PTSBE_OPT_SPLIT_FILL = 6,
+    /* Tile bits (9..14; 0 = default) of the plan ptsbe_pershot_run uses: its stages end at every
+     * general noise site whatever the tile, so the tile only sets how many CTAs share an SM and
+     * how many tiles a state spans. Same shots; speed only. */
+    PTSBE_OPT_PERSHOT_TILE_BITS = 7
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */
@@ -565,7 +569,7 @@ enum {
     PTSBE_TIMER_EVOLVE_STAGE = 0,     /* tile passes of ptsbe_evolve_batch                        */
     PTSBE_TIMER_EVOLVE_FINALIZE = 1,  /* norm reduction / renormalisation of ptsbe_evolve_batch   */
     PTSBE_TIMER_SAMPLE = 2,           /* cluster and global samplers; support-CDF sampler          */
-    PTSBE_TIMER_PERSHOT = 3,          /* ptsbe_pershot_run                                        */
+    PTSBE_TIMER_PERSHOT = 3,          /* stage kernels of ptsbe_pershot_run (its readout: SAMPLE)   */
     PTSBE_TIMER_EVOLVE_PROGRAM = 4,   /* per-set program prepass of the deferred-frame kernel     */
     PTSBE_TIMER_SAMPLE_LIGHT = 5,     /* ptsbe_sample_shots: one-CTA-per-state light sampler      */
     PTSBE_TIMER_BACKWARD = 6,         /* ptsbe_backward                                           */

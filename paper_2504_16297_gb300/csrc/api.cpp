@@ -96,6 +96,7 @@ struct ptsbe_ctx {
     int evolve_kernel = 0;
     uint64_t light_shots = kLightShotLimit;   // states with at most this many shots: one-CTA sampler
     int prog_sets_per_warp = 8;                // frame program prepass: Kraus sets per warp (measured)
+    int pershot_tile_bits = 0;                 // Algorithm 1 path: tile bits of its plan (0: kPershotTileBits)
     int split_fill = 0;                        // small sparse final stage: percent of each state zeroed beside the program prepass
     cudaStream_t aux = nullptr;                // second stream of the context (the zero fill), joined by events
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1526,6 +1527,9 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
             if (value < -1) fail(PTSBE_ERR_INVALID, "allocation failure index must be >= -1");
             ctx->fail_alloc_at = value;
             ctx->alloc_count = 0;
+        } else if (option == PTSBE_OPT_PERSHOT_TILE_BITS) {
+            if (value != 0 && (value < 9 || value > kTileMax)) fail(PTSBE_ERR_INVALID, "per-shot tile bits must be 0 or 9 to 14");
+            ctx->pershot_tile_bits = (int)value;
         } else if (option == PTSBE_OPT_SPLIT_FILL) {
             if (value < 0 || value > 100) fail(PTSBE_ERR_INVALID, "split fill must be a percentage, 0 to 100");
             ctx->split_fill = (int)value;
@@ -1917,10 +1921,16 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
         if (n_shots == 0) return;
         if (!d_bits) fail(PTSBE_ERR_INVALID, "d_bits is NULL");
         ctx->use_device();
-        if (!c.pershot_planned) {
-            c.plan_pershot = make_plan(c, kTileMax, true);
+        // Its stages break at every general noise site whatever the tile size, and a stage holds a
+        // few operators, so small tiles (many CTAs per SM) stream the states best (measured).
+        const int tb = ctx->pershot_tile_bits ? ctx->pershot_tile_bits : kPershotTileBits;
+        if (!c.pershot_planned || c.pershot_tb != tb) {
+            if (c.pershot_planned) free_device_circuit(ctx, c.dev_pershot);
+            c.pershot_planned = false;
+            c.plan_pershot = make_plan(c, tb, true);
             upload_circuit(ctx, c, c.plan_pershot, c.dev_pershot);
             c.pershot_planned = true;
+            c.pershot_tb = tb;
         }
         const Plan& P = c.plan_pershot;
         const int n = (int)c.n, ob = n - P.tb;
@@ -1946,7 +1956,9 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
             const uint32_t cnt = (uint32_t)std::min<uint64_t>(batch, n_shots - b0);
             A.first_shot = first_shot + b0;
             A.kraus = d_kraus ? d_kraus + b0 * A.n_sites : nullptr;
-            ctx->timed(PTSBE_TIMER_PERSHOT, 2.0 * sbytes * cnt * P.stages.size(), [&] {
+            // algorithmic bytes: each stage reads and writes every state once, the first one only
+            // writes (it starts from |0...0>)
+            ctx->timed(PTSBE_TIMER_PERSHOT, (double)sbytes * cnt * (2.0 * (double)P.stages.size() - 1.0), [&] {
                 for (size_t j = 0; j < P.stages.size(); ++j) launch_pershot_stage(A, (int)j, cnt, ctx->stream);
             });
             // read every state out once with its own uniform (the sampler with the per-shot domain)
@@ -1959,11 +1971,12 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
                 }
                 SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, items.size() * sizeof(SampleItem));
                 ctx->h2d(d_items, items.data(), items.size() * sizeof(SampleItem));
-                ctx->timed(PTSBE_TIMER_PERSHOT, 8.0 * sbytes * cnt, [&] { launch_sample_cluster(R, d_items, cnt, ctx->stream); });
+                ctx->timed(PTSBE_TIMER_SAMPLE, (double)sbytes * cnt + 4.0 * cnt,
+                           [&] { launch_sample_cluster(R, d_items, cnt, ctx->stream); });
             } else {
                 for (uint32_t i = 0; i < cnt; ++i) {
                     const uint64_t jj = first_shot + b0 + i;
-                    ctx->timed(PTSBE_TIMER_PERSHOT, 5.0 * sbytes,
+                    ctx->timed(PTSBE_TIMER_SAMPLE, 5.0 * sbytes,
                                [&] { launch_sample_global(R, i, 0u, jj, jj + 1, (uint64_t)i, ctx->stream, kDomPershotRead); });
                 }
             }

@@ -18,6 +18,7 @@ namespace ptsbe {
 constexpr int kMaxKraus = 16;
 constexpr int kMaxQubits = 32;
 constexpr int kTileMax = 14;      // largest tile: 2^14 complex64 = 128 KiB of shared memory
+constexpr int kPershotTileBits = 12;   // tile of the Algorithm 1 path's plan (PTSBE_OPT_PERSHOT_TILE_BITS; measured)
 constexpr int kLowBits = 4;       // low qubits every tile keeps contiguous (16 amplitudes = 128 B)
 constexpr int kSmallSupportBits = 10;   // sparse final stages with a support of at most 2^10 amplitudes
                                         // run the small-buffer frame kernel
@@ -303,6 +304,7 @@ struct Circuit {
     BwPlan bw;                       // adjoint backward plan (built on the first backward call)
     DensePlan dense;                 // dense tile passes (built on first use)
     bool pershot_planned = false;
+    int pershot_tb = 0;              // tile bits plan_pershot was made for
     bool frame_planned = false;
     bool op_planned = false;         // per-operator plan (sweep and register-blocked kernels) built
     DeviceCircuit dev;

@@ -140,6 +140,10 @@ class Ptsbe:
         stream beside the program prepass (default 0: all of it inside the evolve launch)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_SPLIT_FILL, int(percent))
 
+    def set_pershot_tile_bits(self, bits: int):
+        """Tile bits of the per-shot (Algorithm 1) plan (9..14; 0 = default)."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_PERSHOT_TILE_BITS, int(bits))
+
     def set_light_shots(self, limit: int):
         """Shot count up to which a state is sampled by the one-CTA light sampler."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_LIGHT_SHOTS, int(limit))

@@ -17,7 +17,7 @@ from workloads import brickwork
 
 pytestmark = pytest.mark.gpu
 
-MEMBERS = [(12, 9), (13, 14), (15, 11), (17, 20), (19, 8), (21, 12)]
+MEMBERS = [(12, 9), (13, 14), (15, 11), (17, 20), (19, 8), (21, 12), (22, 6)]
 
 
 def _members(P, nsamples=16):
@@ -120,7 +120,7 @@ def test_batch_members_against_oracle(oracle_mod):
     bid = _plan(P, members, bufs)
     P.batch_run(bid)
     P.synchronize()
-    for m in (0, 3, 5):
+    for m in (0, 3, 5, 6):
         circ, info = members[m]
         st, w, s, b = bufs[m]
         o = oracle_mod.Oracle(circ)

@@ -40,6 +40,21 @@ def _oracle(oracle_mod, circ, seed, first, m):
     return np.array(out, np.int64), np.array(labels, np.uint8)
 
 
+@pytest.mark.parametrize("bits", [9, 12])
+def test_tile_size_does_not_change_mixture_shots(P, bits):
+    """With unitary mixtures only, the Kraus labels depend on (seed, site, shot) alone and every
+    amplitude sees the same operations in the same order whatever the tile: shots and labels are
+    bit-identical across the plan's tile sizes."""
+    circ = brickwork(16, 4, 0.05, 0.08, seed=77)
+    ref = _run(P, circ, 5, 0, 96)
+    P.set_pershot_tile_bits(bits)
+    try:
+        got = _run(P, circ, 5, 0, 96)
+    finally:
+        P.set_pershot_tile_bits(0)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+
+
 @pytest.mark.parametrize("n", [6, 10, 15])
 def test_mixture_channels_bit_exact_labels(P, oracle_mod, n):
     circ = brickwork(n, 3, 0.05, 0.08, seed=40 + n)
@@ -91,15 +106,20 @@ def _damping_kraus(gamma):
     return [np.array([[1, 0], [0, np.sqrt(1 - gamma)]]), np.array([[0, np.sqrt(gamma)], [0, 0]])]
 
 
-@pytest.mark.parametrize("n,layers,m", [(5, 3, 400), (15, 2, 80)])
-def test_general_channels_agree_with_oracle(P, oracle_mod, n, layers, m):
+@pytest.mark.parametrize("n,layers,m,tile_bits", [(5, 3, 400, 0), (15, 2, 80, 0), (15, 2, 80, 9), (15, 2, 80, 14)])
+def test_general_channels_agree_with_oracle(P, oracle_mod, n, layers, m, tile_bits):
     """Every shot agrees with the oracle except where a uniform sits within 1e-6 of a cumulative
     boundary: at the first site whose Kraus choice differs (branch probabilities <psi|K_k^dag K_k|psi>
     of the oracle's state before that site, Algorithm 1), or, with identical choices, at the
-    readout CDF of the final state."""
+    readout CDF of the final state. The default tile (2^12 amplitudes), 2^9 and 2^14 split the
+    15-qubit state over 8, 64 and 2 CTAs whose branch-probability partials every tile sums."""
     circ = _damping_circuit(n, layers, seed=n)
     seed = 23
-    got, gk = _run(P, circ, seed, 0, m)
+    P.set_pershot_tile_bits(tile_bits)
+    try:
+        got, gk = _run(P, circ, seed, 0, m)
+    finally:
+        P.set_pershot_tile_bits(0)
     want, wk = _oracle(oracle_mod, circ, seed, 0, m)
     op_ints = np.asarray(circ.op_ints)
     noise_ops = [i for i in range(circ.n_ops) if op_ints[i][0] == 1]

@@ -215,6 +215,11 @@ def test_options_validate_values(host):
     for bad in (101, -1):
         with pytest.raises(capi.PtsbeError):
             capi.ptsbe_set_option(host.ctx, capi.PTSBE_OPT_SPLIT_FILL, bad)
+    for bits in (0, 9, 14):
+        host.set_pershot_tile_bits(bits)
+    for bad in (8, 15, -1):
+        with pytest.raises(capi.PtsbeError):
+            host.set_pershot_tile_bits(bad)
 
 
 @pytest.mark.parametrize("n", [2, 5, 9])
