@@ -423,16 +423,20 @@ typedef struct {
  *                 lambda; 0 for every other operation and parameter)
  *   d_grad_noise  float64 [n_channels]: dL / d channels[c].param (the named kinds; 0 for CUSTOM)
  * checkpoint_every: 0 stores a set's state only before operators it cannot invert (a damping
- * jump); c > 0 also every c fused blocks (the un-computed state is replaced by the stored one
- * there). n_qubits <= 16, at most 64 (site, k) entries per set.
+ * jump) and where the plan's conditioning rule asks for it (un-computing through the blocks since
+ * the last stored copy would multiply FP32 rounding by more than 2^6: the product of their
+ * condition numbers, e.g. 1 / sqrt(1 - gamma) per damping site); c > 0 also every c fused blocks
+ * (the un-computed state is replaced by the stored one there). n_qubits <= 16, at most 64 (site, k) entries per set.
  * Asynchronous on the context stream. Errors: PTSBE_ERR_INVALID (range, structure, null
  * observable, a set with q_alpha = 0), PTSBE_ERR_UNSUPPORTED (n > 16, longer sets),
  * PTSBE_ERR_OOM, PTSBE_ERR_CUDA. */
 /* Shape of the backward plan of a circuit (built on first use): fused blocks of one and two
- * qubits, qubit-position swaps between cluster CTAs, blocks holding a differentiable parameter.
+ * qubits, qubit-position swaps between cluster CTAs, blocks holding a differentiable parameter,
+ * blocks before which the state is stored by the conditioning rule (see ptsbe_backward).
  * Any pointer may be NULL. Host-only work. Errors: PTSBE_ERR_INVALID, PTSBE_ERR_UNSUPPORTED (n > 16). */
 PTSBE_API int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* blocks_1q, uint32_t* blocks_2q,
-                                       uint32_t* swaps, uint32_t* differentiable_blocks);
+                                       uint32_t* swaps, uint32_t* differentiable_blocks,
+                                       uint32_t* conditioning_checkpoints);
 
 PTSBE_API int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
                              const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss,

@@ -117,7 +117,7 @@ _PROTOS = {
                                  C.c_uint32, C.c_uint64, C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(ptsbe_tuning)]),
     "ptsbe_unique_shots": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p]),
     "ptsbe_backward_plan_info": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
-                                           C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
+                                           C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "ptsbe_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_h2d_bytes": (C.c_int, [C.POINTER(C.c_uint64)]),
     "ptsbe_reuse_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
@@ -260,7 +260,7 @@ def ptsbe_unique_shots(ctx, set_id, first, count, d_bits, d_unique):
 
 
 def ptsbe_backward_plan_info(ctx, circuit_id):
-    v = [C.c_uint32() for _ in range(4)]
+    v = [C.c_uint32() for _ in range(5)]
     check(ctx, load().ptsbe_backward_plan_info(ctx, circuit_id, *[C.byref(x) for x in v]))
     return tuple(x.value for x in v)
 

@@ -1741,7 +1741,7 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
 }
 
 int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* blocks_1q, uint32_t* blocks_2q,
-                             uint32_t* swaps, uint32_t* differentiable_blocks) {
+                             uint32_t* swaps, uint32_t* differentiable_blocks, uint32_t* conditioning_checkpoints) {
     return guarded(ctx, [&] {
         Circuit& c = ctx->circuit(circuit_id);
         if (c.n > (uint32_t)kBwMaxQubits) fail(PTSBE_ERR_UNSUPPORTED, "backward handles at most 16 qubits");
@@ -1755,6 +1755,7 @@ int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* bloc
         if (blocks_2q) *blocks_2q = n2;
         if (swaps) *swaps = ns;
         if (differentiable_blocks) *differentiable_blocks = nd;
+        if (conditioning_checkpoints) *conditioning_checkpoints = P->cond_ckpts;
     });
 }
 
@@ -1788,7 +1789,7 @@ int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_
         double Nmult = 0;
         for (uint32_t a = 0; a < count; ++a) Nmult += (double)S.mult[first + a];
         if (count && !(Nmult > 0)) fail(PTSBE_ERR_INVALID, "sets with zero total multiplicity");
-        uint32_t base_ck = (uint32_t)P.defsing_items.size();
+        uint32_t base_ck = (uint32_t)P.defsing_items.size() + P.cond_ckpts;
         if (checkpoint_every) base_ck += (uint32_t)((P.items.size() + checkpoint_every - 1) / checkpoint_every);
         uint32_t extra_ck = 0;
         std::vector<uint32_t> seen_items;
@@ -1821,8 +1822,16 @@ int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_
                     if (bw_unit_channel(H)) s2 *= H.q[k];
                 }
             }
-            W[a] = (double)S.mult[g] * s2 / (Nmult * S.q[g]);
-            s2q[a] = s2 / S.q[g];
+            // the kernel's general-channel variants are scaled to norm 1: divide their product out
+            double logC = P.logc_default;
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t m = P.site_mem[S.site[e]];
+                if (m < P.logc_off.size() && P.logc_off[m] != kBwNone)
+                    logC += P.logc[P.logc_off[m] + S.k[e]] - P.logc[P.logc_off[m]];
+            }
+            const double invC = std::exp(-logC);
+            W[a] = (double)S.mult[g] * s2 / (Nmult * S.q[g]) * invC;
+            s2q[a] = s2 / S.q[g] * invC;
             for (uint32_t ch = 0; ch < nch; ++ch) {
                 const HostChannel& H = c.ch[ch];
                 const bool pauli_kind = H.kind == PTSBE_CH_DEPOL1 || H.kind == PTSBE_CH_DEPOL2 ||

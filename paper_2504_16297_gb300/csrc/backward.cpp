@@ -92,6 +92,34 @@ bool invert(const cd* a, int d, cd* out) {
     return big <= 1e4;
 }
 
+// Largest eigenvalue of A^dag A, the squared spectral norm of the d x d matrix A (power iteration;
+// d <= 4, a bound for a planning threshold, not a result).
+double norm2_sq(const cd* A, int d) {
+    cd v[4];
+    for (int i = 0; i < d; ++i) v[i] = cd(1.0 + 0.17 * i, 0.05 * i);
+    double lam = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        double nv = 0.0;
+        for (int i = 0; i < d; ++i) nv += std::norm(v[i]);
+        nv = std::sqrt(nv);
+        if (!(nv > 0.0)) return 0.0;
+        for (int i = 0; i < d; ++i) v[i] /= nv;
+        cd t[4], w[4];
+        for (int r = 0; r < d; ++r) {
+            t[r] = 0.0;
+            for (int c = 0; c < d; ++c) t[r] += A[r * d + c] * v[c];
+        }
+        for (int c = 0; c < d; ++c) {
+            w[c] = 0.0;
+            for (int r = 0; r < d; ++r) w[c] += std::conj(A[r * d + c]) * t[r];
+        }
+        double nw = 0.0;
+        for (int i = 0; i < d; ++i) { nw += std::norm(w[i]); v[i] = w[i]; }
+        lam = std::sqrt(nw);
+    }
+    return lam;
+}
+
 void mul(const cd* A, const cd* B, cd* out, int d) {   // out = A B
     cd t[16];
     for (int r = 0; r < d; ++r)
@@ -232,6 +260,11 @@ void make_backward_plan(const Circuit& c, BwPlan& P) {
         const HostChannel& ch = c.ch[c.site_ch[s]];
         if (bw_unit_channel(ch)) P.P0mix *= ch.q[0];
     }
+    double cond_run = 0.0;   // log2 of the product of kappa since the last stored copy
+    P.cond_ckpts = 0;
+    P.logc.clear();
+    P.logc_off.clear();
+    P.logc_default = 0.0;
     for (size_t t = 0; t < done.size(); ++t) {
         const Work& it = done[t];
         BwItem& bi = P.items[t];
@@ -287,6 +320,19 @@ void make_backward_plan(const Circuit& c, BwPlan& P) {
                     m.nd = 1;
                     diff = true;
                 }
+                if (!unit) {
+                    // variants (and their derivatives, same constant) scaled to spectral norm 1
+                    P.logc_off.resize(P.members.size() + 1, kBwNone);
+                    P.logc_off[P.members.size()] = (uint32_t)P.logc.size();
+                    for (uint32_t k = 0; k < ch.nk; ++k) {
+                        const double n2 = norm2_sq(&ch.K[k * dd], (int)ch.dim);
+                        const double c = n2 > 0.0 ? 1.0 / std::sqrt(n2) : 1.0;
+                        for (cd& x : var[k]) x *= c;
+                        if (k < der.size()) for (cd& x : der[k]) x *= c;
+                        P.logc.push_back(2.0 * std::log(c));
+                    }
+                    P.logc_default += P.logc[P.logc_off[P.members.size()]];
+                }
                 m.noise = 1; m.nk = (uint8_t)ch.nk;
                 P.site_item[s] = (uint32_t)t;
                 P.site_mem[s] = (uint32_t)P.members.size();
@@ -315,6 +361,7 @@ void make_backward_plan(const Circuit& c, BwPlan& P) {
             P.members.push_back(m);
         }
         bi.mend = (uint32_t)P.members.size();
+        P.logc_off.resize(P.members.size(), kBwNone);
         bi.def = push32(B.data(), d);
         if (dsing) Bi.fill(0.0);
         bi.definv = push32(Bi.data(), d);
@@ -322,6 +369,20 @@ void make_backward_plan(const Circuit& c, BwPlan& P) {
         bi.diff = diff ? 1 : 0;
         bi.gslot = diff ? P.ngs++ : kBwNone;
         if (dsing) P.defsing_items.push_back((uint32_t)t);
+        // items are in forward order: a stored copy before block t ends the run of un-computed
+        // blocks at t (a block whose default cannot be inverted is stored anyway)
+        if (dsing) {
+            cond_run = 0.0;
+        } else {
+            const double l2k = 0.5 * std::log2(std::max(1.0, norm2_sq(B.data(), d) * norm2_sq(Bi.data(), d)));
+            if (cond_run + l2k > kBwCondLog2) {
+                bi.ckpt = 1;
+                ++P.cond_ckpts;
+                cond_run = 0.0;
+            } else {
+                cond_run += l2k;
+            }
+        }
     }
     P.first_diff_step = (uint32_t)P.steps.size();
     for (size_t j = 0; j < P.steps.size(); ++j)

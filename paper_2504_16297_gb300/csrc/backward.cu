@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_backward(BwArgs a) {
                 sing = s_sing != 0;
             }
             ep = e1;
-            if (sing || (a.ckpt_every && b % a.ckpt_every == 0)) {
+            if (sing || it.ckpt || (a.ckpt_every && b % a.ckpt_every == 0)) {
                 if (ck < a.maxck) {   // the host sizes maxck for every set; the test only guards memory
                     float2* dst = a.ckpt + ((((size_t)slot * a.maxck + ck) << a.n) | slice);
                     for (uint32_t l = tid; l < L; l += kBwThreads) dst[l] = phi[l];
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_backward(BwArgs a) {
             }
             ep = e0;
             const float2* ckp = nullptr;
-            if (sing || (a.ckpt_every && b % a.ckpt_every == 0)) {
+            if (sing || it.ckpt || (a.ckpt_every && b % a.ckpt_every == 0)) {
                 --ck;   // forward counted every block, backward visits a suffix: ck stays >= 0
                 if (ck < a.maxck) ckp = a.ckpt + ((((size_t)slot * a.maxck + ck) << a.n) | slice);
             }

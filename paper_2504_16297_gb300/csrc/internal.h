@@ -180,6 +180,8 @@ struct BwItem {
     uint32_t def, definv;       // FP32 pool blocks of the default product (every variant 0) and inverse
     uint32_t defsing;           // the default product cannot be inverted
     uint32_t gslot;             // slot of its outer-product accumulator (differentiable items)
+    uint32_t ckpt;              // store phi before this block: un-computing through the blocks since
+                                // the last stored copy would amplify rounding too much (see kBwCondLog2)
 };
 
 struct BwStep {
@@ -187,9 +189,27 @@ struct BwStep {
     uint32_t a, g, item;
 };
 
+// Un-computing phi_{t-1} = B_t^-1 phi_t multiplies the rounding error of phi_t by up to the
+// condition number kappa(B_t) (relative to the state's norm); through a run of blocks the factors
+// multiply. The plan stores phi before a block once the product of kappa over the blocks that would
+// be un-computed since the last stored copy would exceed 2^kBwCondLog2 (damping K0 = diag(1,
+// sqrt(1 - gamma)) has kappa = 1 / sqrt(1 - gamma); unitary blocks have kappa = 1).
+constexpr double kBwCondLog2 = 6.0;
+
 struct BwPlan {
     bool built = false;
     int nl = 0;
+    uint32_t cond_ckpts = 0;             // blocks marked ckpt
+    // Kraus variants of general channels are stored scaled to spectral norm 1 (a damping jump
+    // K1 = [[0, sqrt g], [0, 0]] would otherwise shrink the FP32 state by sqrt g per jump, and a
+    // set with tens of jumps underflows into subnormals); their derivative matrices carry the same
+    // constant. A set's state, loss and gradients are then all multiplied by C = prod over its
+    // general sites of c_k^2, which the host divides out of its weight in FP64. logc[logc_off[m] + k]
+    // = ln c_k^2 of member m's variant k (kBwNone: a gate or a unitary mixture, c = 1);
+    // logc_default = sum over every general site of its variant-0 term.
+    std::vector<double> logc;
+    std::vector<uint32_t> logc_off;
+    double logc_default = 0.0;
     std::vector<BwStep> steps;
     std::vector<BwItem> items;
     std::vector<BwMember> members;

@@ -308,9 +308,11 @@ class Ptsbe:
         capi.ptsbe_unique_shots(self.ctx, info.set_id, first, count, _ptr(bits), _ptr(out))
 
     def backward_plan_info(self, cid: int):
-        """(one-qubit blocks, two-qubit blocks, qubit-position swaps, differentiable blocks)."""
-        b1, b2, sw, nd = capi.ptsbe_backward_plan_info(self.ctx, cid)
-        return {"blocks_1q": b1, "blocks_2q": b2, "swaps": sw, "differentiable_blocks": nd}
+        """One- and two-qubit blocks, qubit-position swaps, differentiable blocks, and blocks before
+        which the state is stored by the conditioning rule."""
+        b1, b2, sw, nd, ck = capi.ptsbe_backward_plan_info(self.ctx, cid)
+        return {"blocks_1q": b1, "blocks_2q": b2, "swaps": sw, "differentiable_blocks": nd,
+                "conditioning_checkpoints": ck}
 
     def pershot(self, cid: int, seed: int, first_shot: int, n_shots: int, bits, kraus=None):
         capi.ptsbe_pershot_run(self.ctx, cid, seed, first_shot, n_shots, _ptr(bits), _ptr(kraus))

@@ -198,6 +198,34 @@ def test_cluster_sizes(P, oracle_mod, n):
             param_slots=pick)
 
 
+@pytest.mark.parametrize("layers", [8, 16, 32])
+def test_gradient_error_with_depth(P, oracle_mod, layers):
+    """Deep damped circuits: the 10-qubit ansatz at 8, 16 and 32 layers (up to 928 gates, sets with
+    up to 40 Kraus entries, 20+ damping jumps). Two things grow with depth: the amplification of
+    rounding when phi is un-computed through damping inverses (the plan stores phi where it would
+    pass 2^6: 0, 1 and 2 copies here), and the shrinking of an unnormalised FP32 state by sqrt(gamma)
+    per jump (the kernel's general-channel variants are scaled to norm 1 and the scale is divided
+    out of the set weight in FP64; unscaled, sets with ~17+ jumps reached FP32 subnormals and an
+    angle with zero gradient read 1.7e-4). The first angle (un-computed through every later block),
+    the second, a middle one and the last (zero gradient: a diagonal rotation before diagonal
+    operators and a ZZ observable) meet the 1e-3 bound against the oracle's FP64 finite
+    differences."""
+    circ = ansatz(n=10, layers=layers, gamma=0.02, p=0.02, seed=300 + layers)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=layers, nsamples=16, total_shots=1600)
+    slots = oracle_mod.gate_param_slots(circ)
+    pick = [slots[0], slots[1], slots[len(slots) // 2], slots[-1]]
+    L, per, gp, gn = run_gpu(P, circ, info, 0, info.count, zz(10), np.asarray(circ.meta["zz_coeffs"]))
+    Lr, perr, gpr, gnr, scale, w = run_ref(oracle_mod, circ, info, 0, info.count, zz(10),
+                                           np.asarray(circ.meta["zz_coeffs"]), param_slots=pick, noise_slots=[0, 1])
+    idx = tuple(np.array(pick).T)
+    bound = GRAD_RTOL * np.abs(gpr[idx]) + 1e-4 * max(np.abs(gpr[idx]).max(), 1e-12)
+    used = np.abs(gp[idx] - gpr[idx]) / bound
+    print(f"depth {layers}: gates {circ.n_gates}, angle-gradient error at most {used.max():.3f} of the bound")
+    assert_grad(gp[idx], gpr[idx], f"angles at depth {layers}")
+    assert_grad(gn[[0, 1]], gnr[[0, 1]], f"channel strengths at depth {layers}")
+
+
 def test_full_size_ansatz(P, oracle_mod):
     """The 16-qubit, 8-layer ansatz with 4,096 proportional samples: the whole range runs, and
     single sets of it match the oracle's finite differences."""

@@ -241,3 +241,21 @@ def test_register_every_op_and_channel_kind(host, oracle_mod, n):
     np.testing.assert_array_equal(np.asarray(info.shots, np.uint64), np.asarray(ref.shots, np.uint64))
     host.release_set(info)
     host.release_circuit(cid)
+
+
+def test_backward_conditioning_checkpoints(host):
+    """The backward plan stores the state where un-computing through the blocks since the last
+    stored copy would multiply rounding by more than 2^6 (the product of the blocks' condition
+    numbers): none for unitary circuits or the 16-qubit ansatz with gamma = 1e-3 (product about
+    2^0.37), and about one per 2^6 for a deep damped circuit (32 layers, gamma = 0.02: 1,216
+    damping sites of 2^0.0146 each, about 2^17.7 in all)."""
+    import math
+    from workloads import ansatz, brickwork
+    uni = host.register(brickwork(10, 8, 0.0, 0.0, seed=3))
+    assert host.backward_plan_info(uni)["conditioning_checkpoints"] == 0
+    assert host.backward_plan_info(host.register(ansatz()))["conditioning_checkpoints"] == 0
+    deep = ansatz(n=10, layers=32, gamma=0.02, p=0.02, seed=332)
+    total = 1216 * 0.5 * math.log2(1.0 / 0.98)
+    ck = host.backward_plan_info(host.register(deep))["conditioning_checkpoints"]
+    assert math.floor(total / 6.0) - 1 <= ck <= math.floor(total / 6.0)
+
