@@ -325,7 +325,60 @@ def result_errors(P, dev, info, states, weights, status, bits, seed, picks):
     return out
 
 
-def config0_ratio(P, dev, seed: int = 2000):
+def oracle_config0(seed: int = 2000):
+    """The oracle on workload 0, the whole job on one core: PTS, every set's state, and every set's
+    shots (its CDF and inverse-CDF draws). Returns (seconds, description)."""
+    from oracle import oracle as orc
+    from workloads import config
+    c = config(0)
+    circ = c["circuit"]
+    n = circ.n_qubits
+    t0 = time.perf_counter()
+    o = orc.Oracle(circ)
+    sets = o.pts_proportional(c["nsamples"], c["seed"], total_shots=c["total_shots"])
+    for i in range(sets.count):
+        psi, w, st = o.evolve(sets, i)
+        m = int(sets.shots[i])
+        if m and st == 0:
+            orc.sample(n, psi, m, seed, i)
+    el = time.perf_counter() - t0
+    return el, (f"complex128 C oracle, 1 thread, the whole job: PTS, {sets.count} state preparations, "
+                f"{int(np.sum(sets.shots))} shots in {el:.2f}s")
+
+
+def oracle_dense30_estimate(ops30: int, sets: int, shots: int, n_small: int = 24):
+    """The oracle on the 30-qubit workload, extrapolated: one error-free trajectory of a one-layer
+    brickwork at n_small qubits (a state far larger than the host caches) is timed per operation
+    and scaled by 2^(30 - n_small) per operation (each operation streams the whole state) to the
+    30-qubit circuit's operations and sets; CDF and shot costs likewise. Returns (shots/s, desc)."""
+    from oracle import oracle as orc
+    from workloads import brickwork
+    small = brickwork(n_small, 1, 5e-4, 5e-4, seed=1003)
+    o = orc.Oracle(small)
+    ks = o.pts_targeted([[]], shots=np.zeros(1, np.uint64))
+    t0 = time.perf_counter()
+    psi, w, st = o.evolve(ks, 0)
+    t_ev = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.cdf(n_small, psi)
+    t_cdf = time.perf_counter() - t0
+    # each sample call builds the CDF once: the per-shot cost is the difference of two sizes
+    t0 = time.perf_counter()
+    orc.sample(n_small, psi, 100_000, 1, 0)
+    t1 = time.perf_counter()
+    orc.sample(n_small, psi, 2_100_000, 1, 0)
+    t2 = time.perf_counter()
+    t_shot = max((t2 - t1) - (t1 - t0), 0.0) / 2_000_000
+    scale = float(1 << (30 - n_small))
+    per_op = t_ev / small.n_ops
+    total = sets * (per_op * scale * ops30 + t_cdf * scale) + shots * t_shot * 30.0 / n_small
+    return shots / total, (f"complex128 C oracle, 1 thread: one {n_small}-qubit trajectory ({small.n_ops} operations, "
+                           f"{per_op * 1e3:.1f} ms each, CDF {t_cdf:.2f}s, {t_shot * 1e9:.0f} ns per shot) scaled "
+                           f"by 2^{30 - n_small} per operation to {ops30} operations x {sets} sets + {shots} shots "
+                           f"= {total / 3600:.0f} h")
+
+
+def config0_ratio(P, dev, seed: int = 2000, cpu: bool = False):
     """Workload 0 (10-qubit brickwork, 20 layers, 1,000 proportional samples, 10^5 shots): PTSBE
     (one call, prefix reuse) against the per-shot path (Algorithm 1) on the same GPU, same shots."""
     import torch
@@ -360,9 +413,13 @@ def config0_ratio(P, dev, seed: int = 2000):
     ps_ms = timed(lambda: P.pershot(cid, seed, 0, m, ps_bits), 2)
     P.release_set(info)
     P.release_circuit(cid)
-    return {"workload": c["name"], "sets": info.count, "shots": m, "tuning": tuning, "ptsbe_ms": pt_ms, "pershot_ms": ps_ms,
-            "ptsbe_shots_per_s": m / (pt_ms / 1e3), "pershot_shots_per_s": m / (ps_ms / 1e3),
-            "ratio": ps_ms / pt_ms}
+    out = {"workload": c["name"], "sets": info.count, "shots": m, "tuning": tuning, "ptsbe_ms": pt_ms, "pershot_ms": ps_ms,
+           "ptsbe_shots_per_s": m / (pt_ms / 1e3), "pershot_shots_per_s": m / (ps_ms / 1e3),
+           "ratio": ps_ms / pt_ms}
+    if cpu:
+        s_cpu, desc = oracle_config0(seed)
+        out["cpu_oracle"] = {"value": m / s_cpu, "unit": "shots/s", "cores": 1, "kind": "oracle", "sample": desc}
+    return out
 
 
 def backward_leg(P, dev, reps: int = 3, cpu: bool = True, nsamples: int = 4096):
@@ -521,7 +578,7 @@ def uneven_leg(dev, reps: int = 2, margin_gb: float = 24.0):
                      "then the samplers; replayed as a CUDA graph")}
 
 
-def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
+def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003, cpu: bool = False):
     """The 30-qubit workload: brickwork, 60 layers (1,800 U3 + 870 CX), DEPOL1 after every U3 and
     DEPOL2 after every CX at p = 5e-4, 2,000 proportional samples, 10^9 shots. States (8 GiB each)
     are not returned: ptsbe_evolve_sample prepares the sets branch by branch with dense passes
@@ -624,6 +681,9 @@ def dense30_leg(P, dev, max_sets: int, clocks_index: int, seed: int = 2003):
                        "kind": "one full 30-qubit trajectory prepared per shot (dense passes, no reuse)"},
            "speedup_vs_pershot": (shots / (ms / 1e3)) / (1.0 / (ps_ms / 1e3)),
            "clocks": clocks}
+    if cpu:
+        v, desc = oracle_dense30_estimate(circ.n_ops, info.count, info.total_shots)
+        out["cpu_oracle"] = {"value": v, "unit": "shots/s", "cores": 1, "kind": "oracle", "sample": desc}
     P.release_set(info)
     P.release_circuit(cid)
     del bits, w, s
@@ -944,7 +1004,7 @@ def main():
         P.release_set(info)
         P.release_circuit(cid)
         P0 = Ptsbe(device=local, stream=stream.cuda_stream)
-        c0 = config0_ratio(P0, dev)
+        c0 = config0_ratio(P0, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
         P0.close()
 
     bw = None
@@ -956,7 +1016,7 @@ def main():
     d30 = None
     if args.dense30_sets != 0 and rank == 0:
         P30 = Ptsbe(device=local, stream=stream.cuda_stream)
-        d30 = dense30_leg(P30, dev, args.dense30_sets, local)
+        d30 = dense30_leg(P30, dev, args.dense30_sets, local, cpu=(world == 1 and not args.no_cpu_baseline))
         P30.close()
         torch.cuda.empty_cache()
     if not args.no_uneven and rank == 0:

@@ -60,8 +60,10 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
     while (e < ee && a.site_op[a.ent_site[e]] < start) ++e;
     __syncthreads();
 
+    __shared__ DevOp sops[kOpChunk];
+    OpWindow win{sops};
     for (uint32_t op = start; op < st.op_end; ++op) {
-        const DevOp o = a.ops[op];
+        const DevOp o = win.at(a.ops, op, st.op_end);
         if (o.kind == DOP_NOISE) {
             uint32_t k = 0;
             if (e < ee && a.ent_site[e] == o.site) { k = a.ent_k[e]; ++e; }

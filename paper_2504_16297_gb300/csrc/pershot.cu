@@ -83,8 +83,10 @@ __global__ void __launch_bounds__(1024) k_pershot_stage(PershotArgs a, int stage
     }
     __syncthreads();
 
+    __shared__ DevOp sops[kOpChunk];
+    OpWindow win{sops};
     for (uint32_t op = st.op_begin; op < st.op_end; ++op) {
-        const DevOp o = a.ops[op];
+        const DevOp o = win.at(a.ops, op, st.op_end);
         if (o.kind != DOP_NOISE) {
             if (o.kind != DOP_NOP) {
                 apply_micro(tile, tb, o.kind, st.pos[o.q0], st.pos[o.q1], a.mats + o.mat);

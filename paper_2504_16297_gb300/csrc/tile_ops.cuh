@@ -152,6 +152,31 @@ __device__ __forceinline__ void apply_micro(float2* s, int tb, uint8_t kind, int
     }
 }
 
+// --- staged operator lists -------------------------------------------------------------------------
+// The per-operator kernels walk a stage's op list one op at a time; read from global memory each op
+// costs a chain of dependent loads (descriptor, then its tables) for every CTA. OpWindow keeps a
+// chunk of the list in shared memory and restages it when the walk leaves the chunk. Every thread
+// must call at() with the same op (the walk is uniform over the CTA): restaging is a barrier.
+constexpr uint32_t kOpChunk = 128;   // 32-byte descriptors: 4 KB of shared memory
+struct OpWindow {
+    DevOp* buf;
+    uint32_t c0 = 1u, c1 = 0u;       // staged ops [c0, c1)
+    __device__ DevOp at(const DevOp* __restrict__ ops, uint32_t op, uint32_t end) {
+        if (op < c0 || op >= c1) {
+            __syncthreads();
+            c0 = op;
+            c1 = op + kOpChunk < end ? op + kOpChunk : end;
+            const uint32_t words = (c1 - c0) * (uint32_t)(sizeof(DevOp) / 4);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(ops + c0);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(buf);
+            for (uint32_t w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldg(src + w);
+            __syncthreads();
+        }
+        return buf[op - c0];
+    }
+};
+static_assert(sizeof(DevOp) % 4 == 0, "op descriptors are staged as 4-byte words");
+
 // --- tile movement ------------------------------------------------------------------------------------
 
 __device__ __forceinline__ uint64_t gidx(uint32_t l, int lb, const uint32_t* hi, uint64_t outer) {
