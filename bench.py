@@ -944,10 +944,14 @@ def main():
     ms_e2e, _, _ = timed(True, steps_e2e, False)
     h2d_bytes[0] = (capi.ptsbe_h2d_bytes() - hb0) // steps_e2e
 
+    # The legs below (comparator, oracle checks, the other workloads) run on one GPU only: under
+    # torchrun they would hold every rank's GPU while rank 0 measures them.
+    single = world == 1
+
     # Traditional trajectories (Algorithm 1) on the same GPU and workload: one prepared state per
     # shot, Kraus operators drawn during the evolution. Timed on a bounded number of shots.
     pershot = None
-    if args.pershot_shots > 0:
+    if args.pershot_shots > 0 and single:
         cid = P.register(circ)
         P.set_pershot_tile_bits(args.pershot_tile_bits)
         ps_bits = torch.empty(args.pershot_shots, dtype=torch.int32, device=dev)
@@ -994,7 +998,7 @@ def main():
 
     errors = None
     c0 = None
-    if rank == 0:
+    if rank == 0 and single:
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
         P.evolve_sample(info, 0, K, states, weights[0], status[0], seed, bits[0], prefix_reuse=True)
@@ -1008,18 +1012,18 @@ def main():
         P0.close()
 
     bw = None
-    if not args.no_backward:
+    if not args.no_backward and single:
         bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
 
     unev = None
 
     d30 = None
-    if args.dense30_sets != 0 and rank == 0:
+    if args.dense30_sets != 0 and rank == 0 and single:
         P30 = Ptsbe(device=local, stream=stream.cuda_stream)
         d30 = dense30_leg(P30, dev, args.dense30_sets, local, cpu=(world == 1 and not args.no_cpu_baseline))
         P30.close()
         torch.cuda.empty_cache()
-    if not args.no_uneven and rank == 0:
+    if not args.no_uneven and rank == 0 and single:
         unev = uneven_leg(dev)
         torch.cuda.empty_cache()
 
@@ -1096,6 +1100,7 @@ def main():
             "config0_vs_pershot": c0,
             "uneven": unev,
             "dense30": d30,
+            "other_legs": None if single else "measured at N = 1 only (comparator, oracle checks, 30-qubit, uneven, backward)",
         }
         print(json.dumps(out), flush=True)
     if dist:
