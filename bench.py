@@ -67,6 +67,9 @@ def parse():
                     help="Kraus sets of the 30-qubit workload timed in the dense leg, a prefix of the trie "
                          "(canonical) order (0 = skip the leg, -1 = the whole job)")
     ap.add_argument("--dense30-only", action="store_true", help="run only the 30-qubit dense leg and print it")
+    ap.add_argument("--config0-only", action="store_true",
+                    help="run only the 10-qubit PTSBE-against-per-shot comparison (a few MB on the device: the "
+                         "profiling case of the per-operator kernels) and print it")
     ap.add_argument("--dense-probe", type=int, default=0, metavar="QUBITS",
                     help="prepare and sample one error-free brickwork set (16 layers) of QUBITS qubits with the "
                          "dense passes, states not returned, and print its timing (the profiling case)")
@@ -99,8 +102,12 @@ class Clocks:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the sampler is running (its first line written) before the timed region starts
+            t0 = time.perf_counter()
+            while os.path.getsize(self.path) == 0 and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -815,6 +822,14 @@ def main():
     if args.uneven_only:
         if rank == 0:
             print(json.dumps({"uneven": uneven_leg(torch.device("cuda", local))}), flush=True)
+        return
+
+    if args.config0_only:
+        dev = torch.device("cuda", local)
+        if rank == 0:
+            P0 = Ptsbe(device=local, stream=torch.cuda.current_stream(dev).cuda_stream)
+            print(json.dumps({"config0_vs_pershot": config0_ratio(P0, dev)}), flush=True)
+            P0.close()
         return
 
     if args.dense_probe:
