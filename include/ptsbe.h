@@ -465,11 +465,12 @@ enum {
      * pass of the tile per operator), 2 register-blocked (operators applied to amplitudes held in
      * registers, the tile re-shuffled through shared memory between register groups), 3 deferred
      * frame (permutations and diagonals tracked as an index map and factor tables; only
-     * operators that mix amplitudes pass over the tile), 4 dense passes for n >= 12 (the state
-     * streams through HBM once per pass over 12-qubit tiles; the operators of a pass are fused into
-     * 1- and 2-qubit blocks applied to amplitudes held in registers; the planner changes the
-     * qubit-to-bit layout between passes so each pass holds the qubits it needs; n < 12 falls back
-     * to 3). */
+     * operators that mix amplitudes pass over the tile), 4 dense passes (the state streams
+     * through HBM once per pass over 12-qubit tiles; the operators of a pass are fused into 1- and
+     * 2-qubit blocks applied to amplitudes held in registers; the planner changes the
+     * qubit-to-bit layout between passes so each pass holds the qubits it needs; a state of
+     * n < 12 qubits is prepared zero-padded to 12 in a library buffer, the added qubits untouched,
+     * and its 2^n amplitudes copied to d_states). */
     PTSBE_OPT_EVOLVE_KERNEL = 0,
     /* States (15 <= n <= 20) with at most this many shots are sampled by one CTA each from chunk
      * prefixes (one chunk re-read per shot); heavier ones by a thread-block cluster holding the
@@ -561,10 +562,10 @@ PTSBE_API int ptsbe_reuse_stats(ptsbe_ctx* ctx, uint64_t* gates_applied, uint64_
  * block 16 per amplitude), the algorithmic arithmetic for an ALU roofline. Host-only. */
 PTSBE_API int ptsbe_dense_work(ptsbe_ctx* ctx, uint64_t* pass_launches, double* fma);
 
-/* The dense-pass plan of a circuit (built if needed; n >= 12, else PTSBE_ERR_UNSUPPORTED): passes
- * (of which fixup_passes only restore logical qubit order at the end), fused 1- and 2-qubit
- * blocks, and FP32 multiply-adds per amplitude of one full preparation. Any pointer may be NULL.
- * Host-only. */
+/* The dense-pass plan of a circuit (built if needed; n < 12 is planned zero-padded to 12 qubits):
+ * passes (of which fixup_passes only restore logical qubit order at the end), fused 1- and 2-qubit
+ * blocks, and FP32 multiply-adds per amplitude (of the plan's state) of one full preparation. Any
+ * pointer may be NULL. Host-only. */
 PTSBE_API int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes, uint32_t* fixup_passes,
                                     uint64_t* blocks_1q, uint64_t* blocks_2q, double* fma_per_amplitude);
 

@@ -85,7 +85,7 @@ struct ptsbe_ctx {
     int64_t queue_stall_task = -1;                  // test hook (PTSBE_OPT_QUEUE_STALL_TASK)
     uint32_t next_circuit = 1, next_set = 1;
     DevBuf nodes, part, scale, items, scratch, pershot, progs, pingpong, fault, support, sitems;
-    DevBuf dense_tabs, stream_status;          // dense passes: per-call node/override tables; status when the caller passes none
+    DevBuf dense_tabs, stream_status, dense_pad;          // dense passes: per-call node/override tables; status when the caller passes none
     std::vector<DevBuf> state_pool;            // dense passes without caller states: branch state buffers
     uint64_t reuse_gates_run = 0, reuse_gates_full = 0;   // last evolve call: gates applied / without prefix reuse
     uint64_t dense_launches = 0;               // last evolve call with dense passes: pass launches (set x pass)
@@ -427,12 +427,12 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
                   double* d_weights, uint8_t* d_status, uint32_t flags, const FusedShots* fused,
                   std::vector<uint8_t>* drawn) {
     ctx->use_device();
-    if (ctx->evolve_kernel == 4 && (int)c.n >= dense::kT) {
+    if (ctx->evolve_kernel == 4) {
         if (drawn) drawn->assign(count, 0);
         evolve_dense_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags);
         return;
     }
-    if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel (n >= 12)");
+    if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel");
     ensure_set_on_device(ctx, s);
     const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
     if (frame && !c.frame_planned) {
@@ -851,7 +851,7 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
         ensure_dense_plan(ctx, c);
     }
     const DensePlan& P = c.dense;
-    const int n = (int)c.n;
+    const int n = P.n;                   // >= kT: a smaller state runs zero-padded to kT qubits
     const uint32_t J = (uint32_t)P.passes.size();
     const bool reuse = (flags & PTSBE_EVOLVE_PREFIX_REUSE) && J > 1;
     std::vector<dense::Override> ovr;
@@ -904,7 +904,9 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
     if (flags & PTSBE_EVOLVE_PLAN_ONLY) return;
 
     const size_t sb = (size_t)8 << n;
-    float2* const user = (float2*)d_states;
+    // padded states go through a library buffer; the caller's states are copied out at the end
+    const bool padded = n > (int)c.n;
+    float2* const user = padded ? (float2*)ctx->ws(ctx->dense_pad, (size_t)count * sb) : (float2*)d_states;
     float2* const other = reuse ? (float2*)ctx->ws(ctx->pingpong, (size_t)count * sb) : user;
     auto out_buf = [&](uint32_t j) { return ((J - 1 - j) & 1u) ? other : user; };
     auto slot = [&](float2* b, uint32_t a) { return b + ((size_t)a << n); };
@@ -963,6 +965,9 @@ void evolve_dense_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uin
     E.status = d_status;
     E.states = user;
     ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)sb * count, [&] { launch_evolve_finalize(E, count, d_scale, ctx->stream, true); });
+    if (padded)
+        ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 2.0 * (double)((size_t)8 << c.n) * count,
+                   [&] { launch_dense_unpad(user, n, (float2*)d_states, (int)c.n, count, ctx->n_sm, ctx->stream); });
 }
 
 // ptsbe_evolve_sample without caller states: the states live in library buffers, one branch at
@@ -1267,6 +1272,7 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         ctx->free_buf(ctx->items); ctx->free_buf(ctx->scratch); ctx->free_buf(ctx->pershot);
         ctx->free_buf(ctx->progs); ctx->free_buf(ctx->pingpong); ctx->free_buf(ctx->fault); ctx->free_buf(ctx->support);
         ctx->free_buf(ctx->dense_tabs); ctx->free_buf(ctx->stream_status); ctx->free_buf(ctx->sitems);
+        ctx->free_buf(ctx->dense_pad);
         for (DevBuf& b : ctx->state_pool) ctx->free_buf(b);
         ctx->free_timers();
     } catch (const Error& e) {
@@ -1570,9 +1576,7 @@ int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t cou
         int best_k = -1;
         double best = 0;
         try {
-            const bool dense_ok = (int)ctx->circuit(ctx->set(set_id).circuit).n >= dense::kT;
             for (int k : {3, 1, 2, 4}) {
-                if (k == 4 && !dense_ok) continue;
                 ctx->evolve_kernel = k;
                 const double ms = timed_ms([&] { return ptsbe_evolve_batch(ctx, set_id, first, count, d_states, d_weights, d_status, flags); });
                 if (ms < 0) fail(PTSBE_ERR_INVALID, std::string("autotune: evolve kernel ") + std::to_string(k) + ": " + ctx->err);
@@ -1664,7 +1668,6 @@ int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes,
                           uint64_t* blocks_1q, uint64_t* blocks_2q, double* fma_per_amplitude) {
     return guarded(ctx, [&] {
         Circuit& c = ctx->circuit(circuit_id);
-        if ((int)c.n < dense::kT) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need n >= 12");
         if (!c.dense.built) make_dense_plan(c, c.dense);
         const DensePlan& P = c.dense;
         uint64_t b1 = 0, b2 = 0;

@@ -310,6 +310,28 @@ __global__ void __launch_bounds__(kThreads, kDenseCtasPerSm) k_dense_queue(Queue
 
 int dense_ctas_per_sm() { return kDenseCtasPerSm; }
 
+// Zero-padded dense states back to their own size: thread-strided copy of float4 pairs.
+__global__ void __launch_bounds__(256) k_dense_unpad(const float4* __restrict__ src, int n_in, float4* __restrict__ dst,
+                                                     int n_out, uint64_t total) {
+    const int shift = n_out - 1;                       // float4 per output state: 2^(n_out - 1)
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t st = i >> shift, k = i & ((1ull << shift) - 1ull);
+        dst[i] = __ldcs(src + (st << (n_in - 1)) + k);
+    }
+}
+
+void launch_dense_unpad(const float2* src, int n_in, float2* dst, int n_out, uint32_t count, int n_sm, cudaStream_t s) {
+    if (count == 0) return;
+    if (n_out < 1 || n_out > n_in) fail(PTSBE_ERR_INVALID, "dense unpad: bad sizes");
+    if ((uintptr_t)dst % 16) fail(PTSBE_ERR_INVALID, "d_states must be 16-byte aligned");
+    const uint64_t total = (uint64_t)count << (n_out - 1);
+    const uint64_t grid = std::min<uint64_t>((total + 255) / 256, (uint64_t)std::max(n_sm, 1) * 8);
+    k_dense_unpad<<<(uint32_t)grid, 256, 0, s>>>(reinterpret_cast<const float4*>(src), n_in, reinterpret_cast<float4*>(dst),
+                                                  n_out, total);
+    PTSBE_CUDA(cudaGetLastError());
+    count_launch();
+}
+
 void launch_dense_pass(const DenseArgs& a, int n_sm, cudaStream_t s) {
     if (a.n_nodes == 0) return;
     if (a.n < kT || a.n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 12 <= n <= 32");

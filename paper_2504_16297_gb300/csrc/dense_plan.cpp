@@ -322,8 +322,10 @@ void dense_block_matrix(const Circuit& c, const DensePlan& P, uint32_t b, const 
 }
 
 void make_dense_plan(const Circuit& c, DensePlan& P) {
-    const int n = (int)c.n;
-    if (n < kT || n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 12 <= n <= 32");
+    // a state of fewer than kT qubits is planned as a kT-qubit one: the extra qubits carry no
+    // operation and stay |0>, so the circuit's state is the first 2^n amplitudes of the plan's
+    const int n = std::max((int)c.n, kT);
+    if (c.n < 1 || n > kMaxQ) fail(PTSBE_ERR_UNSUPPORTED, "dense passes need 1 <= n <= 32");
     P = DensePlan{};
     P.n = n;
     Planner pl;

@@ -455,6 +455,9 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
 // Zero fill of the first `prefix` bytes (a multiple of 4096) of each of `count` states of
 // `state_bytes` from the 16-byte aligned `base`: bulk copies of a zeroed shared buffer, at most one
 // one-warp CTA per SM (it shares the SMs with a running program prepass).
+// Copies the first 2^n_out amplitudes of each of `count` states of 2^n_in amplitudes (a dense
+// plan zero-padded to kT qubits) to the caller's buffer of 2^n_out-amplitude states.
+void launch_dense_unpad(const float2* src, int n_in, float2* dst, int n_out, uint32_t count, int n_sm, cudaStream_t s);
 void launch_zero_states(void* base, uint64_t state_bytes, uint64_t prefix, uint32_t count, int n_sm, cudaStream_t s);
 void launch_frame_program(const EvolveArgs& a, int stage, const uint32_t* d_nodes, uint32_t n_nodes, cudaStream_t s,
                           int sets_per_warp);

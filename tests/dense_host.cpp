@@ -24,6 +24,7 @@ namespace {
 Circuit g_circ;
 DensePlan g_plan;
 int g_stage_errors = 0;     // staged passes whose size disagrees with the staging offsets
+int g_pad_errors = 0;       // nonzero amplitudes on the padding qubits of a plan padded to kT qubits
 
 // One pass of one state, in place (a tile is read whole before it is written).
 void run_pass(uint32_t j, std::vector<float2>& psi, const std::vector<Override>& ovr, const std::vector<float2>& opool) {
@@ -112,6 +113,9 @@ int dh_register(uint32_t n, const ptsbe_op* ops, uint64_t n_ops, const ptsbe_cha
     }
 }
 
+// Nonzero amplitudes found on padding qubits by dh_evolve so far (0 when the plan is not padded).
+int dh_pad_errors() { return g_pad_errors; }
+
 // out[0..10]: passes, fix-up passes, groups, blocks, operations placed, operations placed more than
 // once or never, 2-qubit blocks, gates, passes staged in shared memory, staging size mismatches,
 // blocks in diagonal-times-real form
@@ -168,8 +172,12 @@ double dh_evolve(const uint32_t* sites, const uint8_t* ks, uint32_t len, float* 
         ovr.push_back({blk, off, code});
     }
     for (uint32_t j = 0; j < P.passes.size(); ++j) run_pass(j, psi, ovr, opool);
+    // a plan padded to kT qubits: the circuit's state is the first 2^n amplitudes, the rest zero
+    const size_t amps = (size_t)1 << g_circ.n;
+    for (size_t i = amps; i < psi.size(); ++i)
+        if (psi[i].x != 0.f || psi[i].y != 0.f) ++g_pad_errors;
     double nrm = 0;
-    for (size_t i = 0; i < psi.size(); ++i) {
+    for (size_t i = 0; i < amps; ++i) {
         out[2 * i] = psi[i].x;
         out[2 * i + 1] = psi[i].y;
         nrm += (double)psi[i].x * psi[i].x + (double)psi[i].y * psi[i].y;

@@ -115,6 +115,30 @@ def test_brickwork_sets_match_oracle(dh, oracle_mod, n, layers):
     assert st["staged"] > 0 and st["stage_errors"] == 0
 
 
+@pytest.mark.parametrize("n,layers", [(1, 4), (5, 8), (10, 20), (11, 6)])
+def test_small_states_run_zero_padded(dh, oracle_mod, n, layers):
+    """A state of fewer than 12 qubits is planned as a 12-qubit one whose added qubits carry no
+    operation: its amplitudes are the first 2^n of the plan's state, every other amplitude stays an
+    exact zero, and sets match the oracle (the 10-qubit, 20-layer case is the 10-qubit workload's
+    shape)."""
+    dh.dh_pad_errors.restype = C.c_int
+    before = dh.dh_pad_errors()
+    if n == 1:
+        b = CircuitBuilder(1, "one")
+        dp = b.channel("DEPOL1", 0.1)
+        for _ in range(layers):
+            b.gate("U3", [0], (0.3, 0.7, 1.1)); b.noise(dp, [0])
+        circ = b.build()
+    else:
+        circ = brickwork(n, layers, 0.02, 0.03, seed=700 + n)
+    register(dh, circ)
+    st = stats(dh)
+    assert st["misplaced"] == 0 and st["placed"] == circ.n_ops
+    sets = oracle_mod.Oracle(circ).pts_proportional(30, 17, total_shots=300)
+    compare(dh, oracle_mod, circ, sets, range(min(sets.count, 6)))
+    assert dh.dh_pad_errors() == before
+
+
 def test_deep_brickwork_many_passes(dh, oracle_mod):
     """16 qubits, 30 layers: many passes, the low bits hand over between passes, and the plan ends
     with passes that restore logical order."""

@@ -63,14 +63,38 @@ def compare_sets(P, oracle_mod, circ, info, idxs, reuse, shots=True, parallel=Fa
     return st, w, s
 
 
-@pytest.mark.parametrize("n,layers", [(12, 10), (13, 8), (15, 6), (18, 4)])
+@pytest.mark.parametrize("n,layers", [(3, 6), (10, 20), (11, 8), (12, 10), (13, 8), (15, 6), (18, 4)])
 @pytest.mark.parametrize("reuse", [False, True])
 def test_dense_brickwork_matches_oracle(P, oracle_mod, n, layers, reuse):
+    """n < 12 runs zero-padded to 12 qubits in a library buffer and is copied out to the caller's
+    buffer of 2^n amplitudes per state."""
     circ = brickwork(n, layers, 0.02, 0.03, seed=70 + n)
     cid = P.register(circ)
     info = P.sample_kraus(cid, "proportional", seed=9, nsamples=60, total_shots=6000)
     idxs = sorted(set([0, 1, 2, info.count // 2, info.count - 1]))
     compare_sets(P, oracle_mod, circ, info, idxs, reuse)
+
+
+def test_dense_padded_writes_only_the_callers_states(P):
+    """The copy out of the padded buffer writes exactly count x 2^n amplitudes: a guard region past
+    the caller's states keeps its fill, and the states are normalised."""
+    torch = torch_cuda()
+    circ = brickwork(9, 6, 0.02, 0.03, seed=77)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=3, nsamples=40, total_shots=400)
+    n, cnt = 9, info.count
+    buf = torch.full(((cnt + 1) << n,), 5.0 + 7.0j, dtype=torch.complex64, device="cuda")
+    st = buf[: cnt << n].view(cnt, 1 << n)
+    w = torch.empty(cnt, dtype=torch.float64, device="cuda")
+    s = torch.empty(cnt, dtype=torch.uint8, device="cuda")
+    P.evolve(info, 0, cnt, st, w, s)
+    torch.cuda.synchronize()
+    P.synchronize()
+    guard = buf[cnt << n:].cpu().numpy()
+    assert np.all(guard == np.complex64(5.0 + 7.0j))
+    norms = (st.abs() ** 2).sum(dim=1).cpu().numpy()
+    ok = s.cpu().numpy() == 0
+    assert np.allclose(norms[ok], 1.0, atol=1e-5)
 
 
 @pytest.mark.parametrize("n", [13, 16])
