@@ -10,7 +10,7 @@ with prefix reuse (10.5 GB of complex64 states, larger than L2), draw the 10^8 s
 Output: one JSON line (rank 0) with shots/s, the roofline of the dominant kernel (algorithmic
 bytes per launch over CUDA-event time, against the measured HBM copy peak), the end-to-end figure
 through host buffers, the CPU oracle timed on a bounded sample, and the clocks seen meanwhile.
-`--impl reference` times the CPU oracle (the reference arm of this build) on the same workload.
+`--impl reference` times the CPU oracle (the reference arm) on the same workload.
 """
 from __future__ import annotations
 
