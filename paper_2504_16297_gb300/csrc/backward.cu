@@ -546,11 +546,12 @@ size_t bw_smem(int nl) { return 2 * sizeof(float2) * ((size_t)1 << nl); }
 
 template <int CL>
 void configure() {
-    static bool done = false;
-    if (!done) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool done = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_backward<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bw_smem(kBwLocalBits)));
-        done = true;
-    }
+        return true;
+    }();
+    (void)done;
 }
 
 template <int CL>

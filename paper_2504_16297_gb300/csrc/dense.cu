@@ -338,22 +338,24 @@ void launch_dense_pass(const DenseArgs& a, int n_sm, cudaStream_t s) {
     const uint64_t items = (uint64_t)a.n_nodes << (a.n - kT);
     const uint64_t cap = (uint64_t)std::max(1, n_sm) * kDenseCtasPerSm;
     const uint32_t grid = (uint32_t)std::min<uint64_t>(items, cap);
-    static bool configured = false;
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_dense_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageMax));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     k_dense_pass<<<grid, kThreads, a.stage_bytes, s>>>(a);
     PTSBE_CUDA(cudaGetLastError());
     count_launch();
 }
 
 int dense_queue_grid(int n_sm) {
-    static int per_sm = -1;
-    if (per_sm < 0) {
+    static const int per_sm = [] {    // thread-safe once
+        int v = 0;
         PTSBE_CUDA(cudaFuncSetAttribute(k_dense_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageMax));
-        PTSBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_queue, kThreads, kStageMax));
-    }
+        PTSBE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_dense_queue, kThreads, kStageMax));
+        return v;
+    }();
     return std::max(1, per_sm) * std::max(1, n_sm);
 }
 

@@ -981,8 +981,8 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
     if (n_nodes == 0) return;
     static_assert(sizeof(frame::Builder) % 4 == 0 && sizeof(frame::Step) % 4 == 0 && sizeof(frame::Factor) % 4 == 0,
                   "program copies move 4-byte words");
-    static bool configured = false;
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_stage, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_smem_bytes(kTileMax, 1)));
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_rb, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -991,8 +991,9 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                                         (int)evolve_frame_smem_bytes(kTileMax, 1)));
         PTSBE_CUDA(cudaFuncSetAttribute(k_evolve_frame<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)evolve_frame_small_smem_bytes(kSmallSupportBits, kTileMax, 1)));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     const bool regs = a.tb >= kRegBits && kernel == 2;
     const bool frm = kernel == 0 || kernel == 3;
     const bool small = frm && stage == a.sparse_final_stage && a.small_bits > 0;

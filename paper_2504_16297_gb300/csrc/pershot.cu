@@ -156,12 +156,13 @@ __global__ void __launch_bounds__(1024) k_pershot_stage(PershotArgs a, int stage
 
 void launch_pershot_stage(const PershotArgs& a, int stage, uint32_t batch, cudaStream_t s) {
     if (batch == 0) return;
-    static bool configured = false;
     const size_t smem_max = ((size_t)8 << kTileMax) + ((size_t)4 << (kTileMax - 1));
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_pershot_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     const size_t smem = ((size_t)8 << a.tb) + ((size_t)4 << (a.tb - a.lb));
     int threads = (1 << a.tb) / 16;
     if (threads < 64) threads = 64;

@@ -566,12 +566,13 @@ void launch_cluster(const SampleArgs& a, const SampleItem* items, uint32_t n_ite
     if (threads < 32) threads = 32;
     if (threads > kSampleThreads) threads = kSampleThreads;
     const size_t smem = cdf_smem_bytes(sb, threads);
-    static bool configured = false;
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_sample_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     for (uint32_t b = 0; b < n_items; b += (1u << 20)) {
         const uint32_t cnt = (n_items - b) < (1u << 20) ? (n_items - b) : (1u << 20);
         cudaLaunchConfig_t cfg = {};
@@ -653,12 +654,13 @@ int sample_light_max_qubits() { return kLightChunkBits + 7; }
 
 void launch_sample_light(const SampleArgs& a, const SampleItem* d_items, uint32_t n_items, cudaStream_t s) {
     if (n_items == 0) return;
-    static bool configured = false;
     const size_t smem = ((size_t)kLightChunks + kLightChunks / 16 + 1) * sizeof(fx);
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_sample_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     for (uint32_t b = 0; b < n_items; b += (1u << 30)) {
         const uint32_t cnt = (n_items - b) < (1u << 30) ? (n_items - b) : (1u << 30);
         k_sample_light<<<cnt, kLightThreads, smem, s>>>(a, d_items + b);
@@ -708,12 +710,13 @@ void launch_sample_global(const SampleArgs& a, uint32_t state, uint32_t alpha, u
     fx* btot = cdf + ((size_t)1 << n);
     fx* boff = btot + nb;
     fx* bend = boff + nb;
-    static bool configured = false;
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_block_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)cdf_smem_bytes(kSliceBits, kSampleThreads)));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     const float2* amps = a.states + ((size_t)state << n);
     k_block_prefix<<<nb, kSampleThreads, cdf_smem_bytes(kSliceBits, kSampleThreads), s>>>(amps, cdf, btot);
     PTSBE_CUDA(cudaGetLastError());
@@ -740,11 +743,12 @@ void launch_unique(const uint32_t* bits, const uint64_t* d_pieces, uint32_t n_pi
                    uint32_t* d_bitmaps, unsigned long long* out, cudaStream_t s) {
     if (count == 0) return;
     const size_t smem = unique_bitmap_bytes(n);
-    static bool configured = false;
-    if (!configured) {
+    // thread-safe once: two contexts may be driven from two host threads
+    static const bool configured = [&] {
         PTSBE_CUDA(cudaFuncSetAttribute(k_unique_mark, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)unique_bitmap_bytes(20)));
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     for (uint32_t b = 0; b < n_pieces; b += 65535u) {
         const uint32_t cnt = std::min<uint32_t>(65535u, n_pieces - b);
         k_unique_mark<<<cnt, 1024, smem, s>>>(bits, d_pieces + 3 * (size_t)b, n, d_bitmaps);

@@ -115,7 +115,8 @@ class Ptsbe:
     def set_evolve_kernel(self, kernel: str):
         """'auto' (= 'frame'), 'frame' (permutations and diagonals deferred; tile passes only for
         operators that mix amplitudes), 'sweep' (one shared-memory pass per operator), 'registers' or
-        'dense' (n > 12: register-blocked fused 1-/2-qubit blocks, one HBM pass per planned pass)."""
+        'dense' (register-blocked fused 1-/2-qubit blocks, one HBM pass per planned pass; a state of
+        fewer than 12 qubits runs zero-padded to 12)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_EVOLVE_KERNEL,
                               {"auto": 0, "sweep": 1, "registers": 2, "frame": 3, "dense": 4}[kernel])
 
