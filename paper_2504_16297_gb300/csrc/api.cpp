@@ -1,4 +1,6 @@
 // C ABI of libptsbe: contexts, registries, workspace and the host-side scheduling of the kernels.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <functional>
 #include <atomic>
@@ -25,6 +27,15 @@ size_t noalloc_scratch_bytes();
 size_t noalloc_max_items();
 int noalloc_max_qubits();
 void* noalloc_scratch(int device);
+
+// A named range around an entry point for a timeline profiler (NVTX; nothing is recorded unless a
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_h2d{0};
@@ -1321,6 +1332,7 @@ int ptsbe_synchronize(ptsbe_ctx* ctx) {
 int ptsbe_register_circuit(ptsbe_ctx* ctx, uint32_t n_qubits, const ptsbe_op* ops, uint64_t n_ops,
                            const ptsbe_channel* channels, uint32_t n_channels, const double* custom_gates,
                            uint32_t n_custom, uint32_t* circuit_id) {
+    const NvtxRange nvtx("ptsbe_register_circuit");
     return guarded(ctx, [&] {
         if (!circuit_id) fail(PTSBE_ERR_INVALID, "circuit_id is NULL");
         if (n_qubits < 1 || n_qubits > (uint32_t)kMaxQubits) fail(PTSBE_ERR_INVALID, "n_qubits must be in [1, 32]");
@@ -1367,6 +1379,7 @@ int ptsbe_release_circuit(ptsbe_ctx* ctx, uint32_t circuit_id) {
 
 int ptsbe_sample_kraus(ptsbe_ctx* ctx, uint32_t circuit_id, const ptsbe_pts_params* params, uint64_t seed,
                        uint32_t* set_id, uint32_t* count, uint64_t* n_entries, uint64_t* total_shots) {
+    const NvtxRange nvtx("ptsbe_sample_kraus");
     return guarded(ctx, [&] {
         if (!params) fail(PTSBE_ERR_INVALID, "params is NULL");
         Circuit& c = ctx->circuit(circuit_id);
@@ -1411,6 +1424,7 @@ int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id) {
 
 int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
                        double* d_weights, uint8_t* d_status, uint32_t flags) {
+    const NvtxRange nvtx("ptsbe_evolve_batch");
     return guarded(ctx, [&] {
         ctx->need_device();
         KSet& s = ctx->set(set_id);
@@ -1427,6 +1441,7 @@ int ptsbe_evolve_batch(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
 
 int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                        const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity) {
+    const NvtxRange nvtx("ptsbe_sample_shots");
     return guarded(ctx, [&] {
         ctx->need_device();
         KSet& s = ctx->set(set_id);
@@ -1449,6 +1464,7 @@ int ptsbe_sample_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t
 int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states,
                         double* d_weights, uint8_t* d_status, uint32_t flags, uint64_t seed, uint32_t* d_bits,
                         uint64_t d_bits_capacity) {
+    const NvtxRange nvtx("ptsbe_evolve_sample");
     return guarded(ctx, [&] {
         ctx->need_device();
         KSet& s = ctx->set(set_id);
@@ -1486,6 +1502,7 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
 
 int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const uint32_t* d_bits,
                        uint64_t* d_unique) {
+    const NvtxRange nvtx("ptsbe_unique_shots");
     return guarded(ctx, [&] {
         ctx->need_device();
         KSet& s = ctx->set(set_id);
@@ -1551,6 +1568,7 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
 int ptsbe_autotune(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, void* d_states, double* d_weights,
                    uint8_t* d_status, uint32_t flags, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity,
                    uint32_t reps, ptsbe_tuning* out) {
+    const NvtxRange nvtx("ptsbe_autotune");
     return guarded(ctx, [&] {
         ctx->need_device();
         if (reps == 0) fail(PTSBE_ERR_INVALID, "reps must be positive");
@@ -1684,6 +1702,7 @@ int ptsbe_dense_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* passes,
 
 int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_t count, const void* d_states,
                                const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, uint64_t d_bits_capacity) {
+    const NvtxRange nvtx("ptsbe_sample_shots_noalloc");
     return guarded(ctx, [&] {
         ctx->need_device();
         KSet& s = ctx->set(set_id);
@@ -1765,6 +1784,7 @@ int ptsbe_backward_plan_info(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t* bloc
 int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_t first, uint32_t count,
                    const ptsbe_observable* obs, uint32_t checkpoint_every, double* d_loss, double* d_per_set,
                    double* d_grad_params, double* d_grad_noise) {
+    const NvtxRange nvtx("ptsbe_backward");
     return guarded(ctx, [&] {
         ctx->need_device();
         ctx->use_device();
@@ -1927,6 +1947,7 @@ int ptsbe_backward(ptsbe_ctx* ctx, uint32_t circuit_id, uint32_t set_id, uint32_
 
 int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64_t first_shot, uint64_t n_shots,
                       uint32_t* d_bits, uint8_t* d_kraus) {
+    const NvtxRange nvtx("ptsbe_pershot_run");
     return guarded(ctx, [&] {
         ctx->need_device();
         Circuit& c = ctx->circuit(circuit_id);
@@ -1997,6 +2018,7 @@ int ptsbe_pershot_run(ptsbe_ctx* ctx, uint32_t circuit_id, uint64_t seed, uint64
 }
 
 int ptsbe_batch_plan(ptsbe_ctx* ctx, const ptsbe_job* jobs, uint32_t n_jobs, uint32_t* batch_id) {
+    const NvtxRange nvtx("ptsbe_batch_plan");
     return guarded(ctx, [&] {
         ctx->need_device();
         if (!batch_id) fail(PTSBE_ERR_INVALID, "batch_id is NULL");
@@ -2147,6 +2169,7 @@ int ptsbe_batch_plan(ptsbe_ctx* ctx, const ptsbe_job* jobs, uint32_t n_jobs, uin
 }
 
 int ptsbe_batch_run(ptsbe_ctx* ctx, uint32_t batch_id, uint32_t flags) {
+    const NvtxRange nvtx("ptsbe_batch_run");
     return guarded(ctx, [&] {
         ctx->need_device();
         auto it = ctx->batches.find(batch_id);
