@@ -1012,10 +1012,19 @@ def main():
     # torchrun they would hold every rank's GPU while rank 0 measures them.
     single = world == 1
 
+    # Each leg below is measured outside the timed region; one that fails reports its error in its
+    # key instead of taking the headline line with it.
+    def leg(fn):
+        try:
+            return fn()
+        except Exception as e:                       # noqa: BLE001 (reported, not hidden)
+            torch.cuda.empty_cache()
+            return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
     # Traditional trajectories (Algorithm 1) on the same GPU and workload: one prepared state per
     # shot, Kraus operators drawn during the evolution. Timed on a bounded number of shots.
-    pershot = None
-    if args.pershot_shots > 0 and single:
+    def pershot_leg():
         cid = P.register(circ)
         P.set_pershot_tile_bits(args.pershot_tile_bits)
         ps_bits = torch.empty(args.pershot_shots, dtype=torch.int32, device=dev)
@@ -1033,8 +1042,8 @@ def main():
         P.set_timing(False)
         P.release_circuit(cid)
         del ps_bits
-        # its own roofline: every stage reads and writes each state once (16 B per amplitude), the
-        # readout reads it once more; its kernels run back to back, so their event time is its time
+        # its own roofline: every stage reads and writes each state once (16 B per amplitude); its
+        # stage kernels run back to back (the readout is timed with the samplers)
         ps_gbs = k_bytes / (k_ms / 1e3) / 1e9 if k_ms else None
         hbm_peak, hbm_kind = peaks()
         pershot = {"value": args.pershot_shots / (ps_ms / 1e3), "unit": "shots/s", "shots": args.pershot_shots,
@@ -1042,11 +1051,17 @@ def main():
                    "tile_bits": args.pershot_tile_bits or "default", "launches": k_launches, "algorithmic_bytes": k_bytes,
                    "roofline": {"bound": "hbm", "achieved": ps_gbs, "peak": hbm_peak, "unit": "GB/s",
                                 "frac": ps_gbs / hbm_peak if ps_gbs else None, "peak_kind": hbm_kind}}
+        return pershot
+
+    pershot = leg(pershot_leg) if (args.pershot_shots > 0 and single) else None
+    if pershot is not None and "error" in pershot:
+        pershot_error, pershot = pershot, None
+    else:
+        pershot_error = None
 
     # unique-shot statistic (Sec. 4): distinct outcomes among the shots of the heaviest sets, from
     # one more step outside the timed region
-    uniq = None
-    if rank == 0:
+    def unique_leg():
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
         P.evolve_sample(info, 0, K, states, weights[0], status[0], seed, bits[0], prefix_reuse=True)
@@ -1055,44 +1070,50 @@ def main():
         P.unique_shots(info, 0, top, bits[0], u)
         torch.cuda.synchronize()
         uc = u.cpu().numpy()
-        uniq = [{"set": a, "errors": len(info.entries(a)), "shots": int(info.shots[a]), "unique": int(uc[a]),
-                 "fraction": float(uc[a]) / max(1, int(info.shots[a]))} for a in range(top)]
+        out = [{"set": a, "errors": len(info.entries(a)), "shots": int(info.shots[a]), "unique": int(uc[a]),
+                "fraction": float(uc[a]) / max(1, int(info.shots[a]))} for a in range(top)]
         P.release_set(info)
         P.release_circuit(cid)
+        return out
 
-    errors = None
-    c0 = None
-    if rank == 0 and single:
+    uniq = leg(unique_leg) if rank == 0 else None
+
+    def errors_leg():
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
         P.evolve_sample(info, 0, K, states, weights[0], status[0], seed, bits[0], prefix_reuse=True)
         torch.cuda.synchronize()
-        errors = result_errors(P, dev, info, states, weights[0], status[0], bits[0], seed,
-                               [0, 1, 2, K // 2, K - 1])
+        out = result_errors(P, dev, info, states, weights[0], status[0], bits[0], seed, [0, 1, 2, K // 2, K - 1])
         P.release_set(info)
         P.release_circuit(cid)
+        return out
+
+    def config0_leg():
         P0 = Ptsbe(device=local, stream=stream.cuda_stream)
-        c0 = config0_ratio(P0, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
-        P0.close()
+        try:
+            return config0_ratio(P0, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
+        finally:
+            P0.close()
 
-    overlap = None
-    if rank == 0 and single:
-        overlap = two_in_flight(P, circ, dev, K, M, seed, tuning, args.split_fill)
-
-    bw = None
-    if not args.no_backward and single:
-        bw = backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
-
-    unev = None
-
-    d30 = None
-    if args.dense30_sets != 0 and rank == 0 and single:
+    def dense30_leg_own():
         P30 = Ptsbe(device=local, stream=stream.cuda_stream)
-        d30 = dense30_leg(P30, dev, args.dense30_sets, local, cpu=(world == 1 and not args.no_cpu_baseline))
-        P30.close()
-        torch.cuda.empty_cache()
+        try:
+            return dense30_leg(P30, dev, args.dense30_sets, local, cpu=(world == 1 and not args.no_cpu_baseline))
+        finally:
+            P30.close()
+            torch.cuda.empty_cache()
+
+    errors = c0 = overlap = bw = unev = d30 = None
+    if rank == 0 and single:
+        errors = leg(errors_leg)
+        c0 = leg(config0_leg)
+        overlap = leg(lambda: two_in_flight(P, circ, dev, K, M, seed, tuning, args.split_fill))
+    if not args.no_backward and single:
+        bw = leg(lambda: backward_leg(P, dev, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline)))
+    if args.dense30_sets != 0 and rank == 0 and single:
+        d30 = leg(dense30_leg_own)
     if not args.no_uneven and rank == 0 and single:
-        unev = uneven_leg(dev)
+        unev = leg(lambda: uneven_leg(dev))
         torch.cuda.empty_cache()
 
     ms_step = ms / args.steps
@@ -1132,16 +1153,17 @@ def main():
                 "frac": (achieved / peak_issue) if achieved else None, "peak_kind": "4 schedulers x SMs x measured SM clock",
                 "traffic": None, "warp_inst_per_launch": inst, "ms_per_launch": ms_launch}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    def cpu_leg():
         parts = {}
         v1, desc1 = oracle_estimate(args.cpu_budget, K, M, seed, parts)
         try:
             va, cores, desca = oracle_all_cores(K, M, args.cpu_budget, parts)
         except Exception as e:          # no process pool on this host: the one-thread figure stands
             va, cores, desca = v1, 1, f"all-cores run unavailable ({e}); {desc1}"
-        cpu = {"value": va, "unit": "shots/s", "cores": cores, "kind": "oracle", "sample": desca,
-               "single_thread": {"value": v1, "unit": "shots/s", "cores": 1, "sample": desc1}}
+        return {"value": va, "unit": "shots/s", "cores": cores, "kind": "oracle", "sample": desca,
+                "single_thread": {"value": v1, "unit": "shots/s", "cores": 1, "sample": desc1}}
+
+    cpu = leg(cpu_leg) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
 
     if rank == 0:
         gate_ms = kern.get("evolve_stage", {}).get("ms")
@@ -1152,7 +1174,7 @@ def main():
             "config": workload_config(args, world),
             "tuning": tuning,
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,
-            "pershot": pershot,
+            "pershot": pershot if pershot is not None else pershot_error,
             "speedup_vs_pershot": (value / world / pershot["value"]) if pershot else None,
             "kernels": kern,
             "roofline": roof,
