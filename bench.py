@@ -1078,6 +1078,28 @@ def main():
 
     uniq = leg(unique_leg) if rank == 0 else None
 
+    def sampler_leg(reps: int = 5):
+        """The samplers alone on the step's prepared states (ptsbe_sample_shots over the 10^4 sets
+        and 10^8 shots, the states already in HBM), timed with CUDA events."""
+        cid = P.register(circ)
+        info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
+        P.evolve(info, 0, K, states, weights[0], status[0], prefix_reuse=True)
+        P.sample(info, 0, K, states, status[0], seed, bits[0])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            P.sample(info, 0, K, states, status[0], seed, bits[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / reps
+        P.release_set(info)
+        P.release_circuit(cid)
+        return {"value": M / (ms_s / 1e3), "unit": "shots/s", "ms_per_call": ms_s,
+                "kind": "ptsbe_sample_shots alone over the prepared states (support, light and cluster samplers)"}
+
+    sampler = leg(sampler_leg) if (rank == 0 and single) else None
+
     def errors_leg():
         cid = P.register(circ)
         info = P.sample_kraus(cid, "topk", k=K, total_shots=M)
@@ -1174,6 +1196,10 @@ def main():
             "config": workload_config(args, world),
             "tuning": tuning,
             "gate_apply_gbs": (kern["evolve_stage"]["bytes"] / (gate_ms / 1e3) / 1e9) if gate_ms else None,
+            # logical gates x sets per second of preparation (program prepass + evolve launches)
+            "trajectory_gates_per_s": (circ.n_gates * K / ((gate_ms + kern.get("evolve_program", {}).get("ms", 0.0))
+                                                           / args.steps / 1e3)) if gate_ms else None,
+            "sampler_alone": sampler,
             "pershot": pershot if pershot is not None else pershot_error,
             "speedup_vs_pershot": (value / world / pershot["value"]) if pershot else None,
             "kernels": kern,
