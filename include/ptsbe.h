@@ -510,7 +510,18 @@ enum {
     /* Tile bits (9..14; 0 = default) of the plan ptsbe_pershot_run uses: its stages end at every
      * general noise site whatever the tile, so the tile only sets how many CTAs share an SM and
      * how many tiles a state spans. Same shots; speed only. */
-    PTSBE_OPT_PERSHOT_TILE_BITS = 7
+    PTSBE_OPT_PERSHOT_TILE_BITS = 7,
+    /* 1 (default) or 0. With 1, a frame-kernel call whose plan is one stage (every state prepared
+     * in one tile pass, as for the syndrome workload) puts its table uploads and its program
+     * prepass on the context's second stream without waiting for the context stream: the
+     * programs depend only on the circuit and the Kraus sets, so the latency-bound prepass of
+     * this call runs while the context stream still executes earlier calls (their HBM-bound
+     * evolve launches). The evolve launch waits for it on the context stream, so every output is
+     * still written in the context stream's order, and the caller's buffers are touched only
+     * there. The library keeps two copies of the node tables and programs and reuses one only
+     * after the context stream has run the launches that read it. Off while the context stream
+     * is being captured into a CUDA graph, and with a split zero fill. Same outputs; speed only. */
+    PTSBE_OPT_PREPASS_AHEAD = 8
 };
 
 /* Sets a context option; PTSBE_ERR_INVALID for an unknown option or value. */

@@ -26,6 +26,7 @@ PTSBE_OPT_QUEUE_SPIN_CYCLES = 4
 PTSBE_OPT_QUEUE_STALL_TASK = 5
 PTSBE_OPT_SPLIT_FILL = 6
 PTSBE_OPT_PERSHOT_TILE_BITS = 7
+PTSBE_OPT_PREPASS_AHEAD = 8
 PTSBE_BATCH_GRAPH = 1
 (PTSBE_TIMER_EVOLVE_STAGE, PTSBE_TIMER_EVOLVE_FINALIZE, PTSBE_TIMER_SAMPLE, PTSBE_TIMER_PERSHOT,
  PTSBE_TIMER_EVOLVE_PROGRAM, PTSBE_TIMER_SAMPLE_LIGHT, PTSBE_TIMER_BACKWARD, PTSBE_TIMER_DENSE,

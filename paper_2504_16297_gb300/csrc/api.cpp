@@ -109,8 +109,19 @@ struct ptsbe_ctx {
     int prog_sets_per_warp = 8;                // frame program prepass: Kraus sets per warp (measured)
     int pershot_tile_bits = 0;                 // Algorithm 1 path: tile bits of its plan (0: kPershotTileBits)
     int split_fill = 0;                        // small sparse final stage: percent of each state zeroed beside the program prepass
-    cudaStream_t aux = nullptr;                // second stream of the context (the zero fill), joined by events
+    int prepass_ahead = 1;                     // one-stage frame plans: program prepass on the auxiliary stream, ahead of the context stream
+    cudaStream_t aux = nullptr;                // second stream of the context (prepass ahead, zero fill), joined by events
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // Prepass ahead: uploads and the prepass of a call go to the auxiliary stream, which does not
+    // wait for the context stream, so they overlap the previous call's launches. The node tables
+    // and programs alternate between two lanes; a lane is rewritten only after the context stream
+    // has run the evolve launch that read it (ev_used).
+    cudaStream_t up = nullptr;                 // stream of uploads and table allocations (nullptr: the context stream)
+    DevBuf ahead_nodes[2], ahead_progs[2];
+    cudaEvent_t ev_used[2] = {nullptr, nullptr};
+    bool used_recorded[2] = {false, false};
+    uint32_t lane = 0;
+    cudaStream_t ustream() const { return up ? up : stream; }
     int n_sm = 0;                      // streaming multiprocessors of the device
     ClassTimer timers[PTSBE_TIMER_CLASSES];
 
@@ -194,7 +205,7 @@ struct ptsbe_ctx {
     void* dalloc(size_t bytes) {
         inject("device table");
         void* p = nullptr;
-        const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+        const cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, ustream());
         if (e != cudaSuccess) { (void)cudaGetLastError(); fail(PTSBE_ERR_OOM, "device table allocation failed"); }
         return p;
     }
@@ -230,8 +241,8 @@ struct ptsbe_ctx {
         grow_slot(sl, bytes);
         if (!sl.ev) PTSBE_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
         std::memcpy(sl.p, src, bytes);
-        PTSBE_CUDA(cudaMemcpyAsync(dst, sl.p, bytes, cudaMemcpyHostToDevice, stream));
-        PTSBE_CUDA(cudaEventRecord(sl.ev, stream));
+        PTSBE_CUDA(cudaMemcpyAsync(dst, sl.p, bytes, cudaMemcpyHostToDevice, ustream()));
+        PTSBE_CUDA(cudaEventRecord(sl.ev, ustream()));
         sl.used = true;
         count_h2d(bytes);
     }
@@ -254,6 +265,7 @@ struct ptsbe_ctx {
         if (bytes <= b.cap && b.p) return b.p;
         inject("workspace");
         PTSBE_CUDA(cudaStreamSynchronize(stream));
+        if (aux) PTSBE_CUDA(cudaStreamSynchronize(aux));
         if (b.p) { PTSBE_CUDA(cudaFree(b.p)); b.p = nullptr; b.cap = 0; }
         const size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
         void* p = nullptr;
@@ -306,7 +318,14 @@ int guarded(ptsbe_ctx* ctx, F&& f) {
 
 void free_device_circuit(ptsbe_ctx* ctx, DeviceCircuit& d) {
     ctx->dfree(d.base);
+    if (d.ready) cudaEventDestroy(d.ready);
     d = DeviceCircuit{};
+}
+
+// Marks the end of an upload on the stream that made it (the prepass ahead waits for it).
+void mark_ready(ptsbe_ctx* ctx, cudaEvent_t& ev) {
+    if (!ev) PTSBE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    PTSBE_CUDA(cudaEventRecord(ev, ctx->ustream()));
 }
 
 // All tables of a circuit plan in one allocation and one staged copy.
@@ -324,6 +343,7 @@ void upload_circuit(ptsbe_ctx* ctx, const Circuit& c, const Plan& P, DeviceCircu
     const size_t o_fst = add(P.fstages);
     unsigned char* base = (unsigned char*)ctx->dalloc(blob.size());
     ctx->h2d(base, blob.data(), blob.size());
+    mark_ready(ctx, d.ready);
     auto at = [&](size_t off) { return off == SIZE_MAX ? nullptr : (void*)(base + off); };
     d.base = base;
     d.ops = (DevOp*)at(o_ops); d.micro = (DevMicro*)at(o_micro); d.mats = (float2*)at(o_mats);
@@ -353,6 +373,7 @@ void ensure_set_on_device(ptsbe_ctx* ctx, KSet& s) {
     std::memcpy(blob.data() + sb, s.k.data(), kb);
     unsigned char* base = (unsigned char*)ctx->dalloc(blob.size());
     ctx->h2d(base, blob.data(), blob.size());
+    mark_ready(ctx, s.ready);
     s.d_site = (uint32_t*)base;
     s.d_k = base + sb;
 }
@@ -444,22 +465,64 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         return;
     }
     if (flags & PTSBE_EVOLVE_PLAN_ONLY) fail(PTSBE_ERR_UNSUPPORTED, "plan-only calls need the dense kernel");
-    ensure_set_on_device(ctx, s);
     const bool frame = ctx->evolve_kernel == 0 || ctx->evolve_kernel == 3;
     if (frame && !c.frame_planned) {
         c.plan_frame = make_frame_plan(c, kTileMax);
-        upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
         c.frame_planned = true;
     }
     if (!frame && !c.op_planned) {
         c.plan = make_plan(c, kTileMax, false);
         c.op_planned = true;
     }
-    if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
     const Plan& P = frame ? c.plan_frame : c.plan;
     const DeviceCircuit& D = frame ? c.dev_frame : c.dev;
     const uint32_t S = (uint32_t)c.site_op.size();
     const bool reuse = flags & PTSBE_EVOLVE_PREFIX_REUSE;
+    // Prepass ahead (one-stage frame plans): the programs depend only on the circuit and the sets,
+    // not on any state, so this call's uploads and prepass go to the auxiliary stream without
+    // waiting for the context stream, and run while the context stream still executes earlier
+    // calls. The evolve launch waits for them. Not while the context stream is being captured
+    // (the auxiliary stream would not join the capture) and not with a split zero fill.
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    PTSBE_CUDA(cudaStreamIsCapturing(ctx->stream, &capturing));
+    const bool ahead = frame && ctx->prepass_ahead && ctx->aux && P.stages.size() == 1 && ctx->split_fill == 0 &&
+                       capturing == cudaStreamCaptureStatusNone;
+    // Uploads go to the auxiliary stream while the scope is open; on every exit the context
+    // stream joins the auxiliary stream, and the lane is marked as used by everything the context
+    // stream has been given up to then.
+    struct AheadScope {
+        ptsbe_ctx* ctx;
+        bool on, pending;
+        uint32_t lane;
+        AheadScope(ptsbe_ctx* c, bool a) : ctx(c), on(a), pending(a), lane(c->lane) {
+            if (on) { ctx->up = ctx->aux; ctx->lane ^= 1u; }
+        }
+        void uploads_done() { ctx->up = nullptr; }
+        void join() {
+            ctx->up = nullptr;
+            if (!pending) return;
+            pending = false;
+            PTSBE_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+            PTSBE_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+        }
+        ~AheadScope() {
+            ctx->up = nullptr;
+            if (!on) return;
+            if (pending) {
+                (void)cudaEventRecord(ctx->ev_join, ctx->aux);
+                (void)cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+            }
+            if (cudaEventRecord(ctx->ev_used[lane], ctx->stream) == cudaSuccess) ctx->used_recorded[lane] = true;
+        }
+    } AS(ctx, ahead);
+    const uint32_t lane = AS.lane;
+    ensure_set_on_device(ctx, s);
+    if (frame && !c.dev_frame.base) upload_circuit(ctx, c, c.plan_frame, c.dev_frame);
+    if (!frame && !c.dev.ops) upload_circuit(ctx, c, c.plan, c.dev);
+    if (ahead) {              // tables uploaded by earlier calls, possibly on the context stream
+        if (s.ready) PTSBE_CUDA(cudaStreamWaitEvent(ctx->aux, s.ready, 0));
+        if (c.dev_frame.ready) PTSBE_CUDA(cudaStreamWaitEvent(ctx->aux, c.dev_frame.ready, 0));
+    }
 
     // --- node tables ---
     // With prefix reuse a set whose entries extend those of an earlier set of the range (its
@@ -593,8 +656,10 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         o_nout = blob.add(nout);
         if (n_export) o_nexport = blob.add(nexport);
     }
-    unsigned char* dblob = (unsigned char*)ctx->ws(ctx->nodes, ctx->host_blob.size());
+    unsigned char* dblob = (unsigned char*)ctx->ws(ahead ? ctx->ahead_nodes[lane] : ctx->nodes, ctx->host_blob.size());
+    if (ahead && ctx->used_recorded[lane]) PTSBE_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_used[lane], 0));
     ctx->h2d(dblob, ctx->host_blob.data(), ctx->host_blob.size());
+    AS.uploads_done();        // what follows goes up on the context stream
 
     EvolveArgs A{};
     A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
@@ -642,7 +707,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     if (frame) {
         uint32_t widest = 0;
         for (const auto& L : launches) widest = std::max(widest, L.second);
-        A.frame_progs = ctx->ws(ctx->progs, (size_t)widest * evolve_frame_program_bytes());
+        A.frame_progs = ctx->ws(ahead ? ctx->ahead_progs[lane] : ctx->progs, (size_t)widest * evolve_frame_program_bytes());
     }
     const uint32_t* d_lists = (const uint32_t*)(dblob + o_lists);
     // When the last frame stage only reorders (no ops), the norm is known after the stage
@@ -677,10 +742,13 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         if (split_fill) bytes -= (double)L.second * (double)prefill;   // zeros stored by the prepass-side fill
         if (A.shot_bits && j + 1 == J) bytes += 4.0 * (double)fused_shots;
         if (split_fill) ctx->fork_aux();
-        if (frame)
-            ctx->timed(PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
-                launch_frame_program(A, (int)j, d_lists + L.first, L.second, ctx->stream, ctx->prog_sets_per_warp);
+        if (frame) {
+            cudaStream_t ps = ahead ? ctx->aux : ctx->stream;
+            ctx->timed_on(ps, PTSBE_TIMER_EVOLVE_PROGRAM, 0.0, [&] {
+                launch_frame_program(A, (int)j, d_lists + L.first, L.second, ps, ctx->prog_sets_per_warp);
             });
+            AS.join();
+        }
         A.prefill_bytes = 0;
         if (split_fill) {
             ctx->timed_on(ctx->aux, PTSBE_TIMER_ZERO_FILL, (double)count * (double)prefill,
@@ -691,6 +759,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
         ctx->timed(PTSBE_TIMER_EVOLVE_STAGE, bytes, [&] {
             launch_evolve_stage(A, (int)j, j + 1 == J, d_lists + L.first, L.second, ctx->stream, ctx->evolve_kernel);
         });
+
         if (A.store_norm)
             ctx->timed(PTSBE_TIMER_EVOLVE_FINALIZE, 0.0, [&] { launch_evolve_reduce(A, count, d_scale, ctx->stream); });
     }
@@ -1235,12 +1304,23 @@ int ptsbe_create(ptsbe_ctx** out, int device, void* cuda_stream) {
             (void)cudaGetLastError();
             return PTSBE_ERR_CUDA;
         }
-        if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        // The auxiliary stream runs the prepass ahead of the context stream: at the highest
+        // priority its CTAs are dispatched before the remaining CTAs of launches already running,
+        // so the prepass starts as soon as SM slots free up.
+        int prio_least = 0, prio_greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+            (void)cudaGetLastError();
+            prio_greatest = 0;
+        }
+        if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_used[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_used[1], cudaEventDisableTiming) != cudaSuccess) {
             (void)cudaGetLastError();
             if (ctx->aux) cudaStreamDestroy(ctx->aux);
-            if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+            for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_join, ctx->ev_used[0], ctx->ev_used[1]})
+                if (e) cudaEventDestroy(e);
             cudaMemPoolDestroy(ctx->pool);
             return PTSBE_ERR_CUDA;
         }
@@ -1260,11 +1340,17 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         };
         cudaSetDevice(ctx->device);
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) status = PTSBE_ERR_CUDA;
+        if (ctx->aux && cudaStreamSynchronize(ctx->aux) != cudaSuccess) status = PTSBE_ERR_CUDA;
         for (auto& kv : ctx->circuits) {
             qfree(kv.second->dev.base); qfree(kv.second->dev_pershot.base); qfree(kv.second->dev_frame.base);
             qfree(kv.second->bw.dev); qfree(kv.second->dense.dev);
+            for (DeviceCircuit* d : {&kv.second->dev, &kv.second->dev_pershot, &kv.second->dev_frame})
+                if (d->ready) cudaEventDestroy(d->ready);
         }
-        for (auto& kv : ctx->sets) qfree(kv.second->d_site);   // d_k shares the allocation
+        for (auto& kv : ctx->sets) {
+            qfree(kv.second->d_site);   // d_k shares the allocation
+            if (kv.second->ready) cudaEventDestroy(kv.second->ready);
+        }
         for (auto& kv : ctx->batches) {
             qfree(kv.second->dtab);
             qfree(kv.second->dws);
@@ -1277,6 +1363,11 @@ int ptsbe_destroy(ptsbe_ctx* ctx) {
         }
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+        for (int l = 0; l < 2; ++l) {
+            if (ctx->ev_used[l]) cudaEventDestroy(ctx->ev_used[l]);
+            ctx->free_buf(ctx->ahead_nodes[l]);
+            ctx->free_buf(ctx->ahead_progs[l]);
+        }
         ctx->free_staging();
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         ctx->free_buf(ctx->nodes); ctx->free_buf(ctx->part); ctx->free_buf(ctx->scale);
@@ -1418,6 +1509,7 @@ int ptsbe_release_set(ptsbe_ctx* ctx, uint32_t set_id) {
             ctx->use_device();
             ctx->dfree(s.d_site);                        // stream-ordered (d_k shares the allocation)
         }
+        if (s.ready) cudaEventDestroy(s.ready);
         ctx->sets.erase(set_id);
     });
 }
@@ -1556,6 +1648,9 @@ int ptsbe_set_option(ptsbe_ctx* ctx, int option, int64_t value) {
         } else if (option == PTSBE_OPT_SPLIT_FILL) {
             if (value < 0 || value > 100) fail(PTSBE_ERR_INVALID, "split fill must be a percentage, 0 to 100");
             ctx->split_fill = (int)value;
+        } else if (option == PTSBE_OPT_PREPASS_AHEAD) {
+            if (value != 0 && value != 1) fail(PTSBE_ERR_INVALID, "prepass ahead must be 0 or 1");
+            ctx->prepass_ahead = (int)value;
         } else if (option == PTSBE_OPT_PROGRAM_SETS_PER_WARP) {
             if (value != 0 && value != 4 && value != 8 && value != 16) fail(PTSBE_ERR_INVALID, "sets per warp must be 0, 4, 8 or 16");
             ctx->prog_sets_per_warp = value ? (int)value : 8;

@@ -302,6 +302,7 @@ struct DeviceCircuit {
     uint32_t* hi = nullptr;
     DevFrameStage* fstages = nullptr;
     size_t bytes = 0;
+    cudaEvent_t ready = nullptr;     // recorded after the upload, on the stream that made it
 };
 
 struct Circuit {
@@ -342,6 +343,7 @@ struct KSet {
     // device copies of the entries (uploaded on first use)
     uint32_t* d_site = nullptr;
     uint8_t* d_k = nullptr;
+    cudaEvent_t ready = nullptr;     // recorded after the upload, on the stream that made it
     uint32_t count() const { return (uint32_t)(off.size() - 1); }
 };
 

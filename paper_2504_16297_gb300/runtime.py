@@ -141,6 +141,11 @@ class Ptsbe:
         stream beside the program prepass (default 0: all of it inside the evolve launch)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_SPLIT_FILL, int(percent))
 
+    def set_prepass_ahead(self, on: bool):
+        """One-stage frame plans: uploads and program prepass on the context's second stream,
+        overlapping earlier calls (default on)."""
+        capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_PREPASS_AHEAD, 1 if on else 0)
+
     def set_pershot_tile_bits(self, bits: int):
         """Tile bits of the per-shot (Algorithm 1) plan (9..14; 0 = default)."""
         capi.ptsbe_set_option(self.ctx, capi.PTSBE_OPT_PERSHOT_TILE_BITS, int(bits))

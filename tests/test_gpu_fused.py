@@ -190,6 +190,75 @@ def test_zero_fill_beside_program_prepass(fused, percent):
     assert launches == 1 and nbytes == info.count * (state * percent // 100 // 4096 * 4096)
 
 
+def test_prepass_ahead_back_to_back():
+    """Calls issued back to back with no synchronisation between them, each registering its own
+    circuit and Kraus set and releasing both right after (the bench's step), one-call and two-call
+    paths mixed, two calls writing the same state buffer: with the prepass ahead (uploads and
+    program prepass on the second stream, overlapping the previous call) every output equals the
+    same sequence run with the prepass on the context stream. Also the prepass ahead of a circuit
+    and a set uploaded by an earlier call on the context stream."""
+    torch = torch_cuda()
+    from paper_2504_16297_gb300.runtime import Ptsbe
+    gpu_ctx()
+    jobs = [(2, 5e-4, 1e-3, 1200, True), (3, 1e-3, 1e-3, 2000, False), (2, 2e-3, 5e-4, 900, True),
+            (3, 5e-4, 2e-3, 2500, True), (1, 1e-3, 1e-3, 400, False)]
+
+    def run(ahead):
+        P = Ptsbe(device=0)
+        P.set_prepass_ahead(ahead)
+        shared = torch.full((2500, 1 << 17), 5.0 + 1.0j, dtype=torch.complex64, device="cuda")
+        outs = []
+        torch.cuda.synchronize()
+        for i, (rounds, gamma, p, k, fused) in enumerate(jobs):
+            circ = syndrome17(rounds=rounds, gamma=gamma, p=p, seed=1100 + i)
+            cid = P.register(circ)
+            info = P.sample_kraus(cid, "topk", k=k, total_shots=400_000 * (i + 1), export=False)
+            total = int(info.total_shots)
+            st = shared[:info.count] if i in (2, 3) else torch.full((info.count, 1 << 17), 7.0 + 3.0j,
+                                                                    dtype=torch.complex64, device="cuda")
+            w = torch.full((info.count,), -1.0, dtype=torch.float64, device="cuda")
+            s = torch.full((info.count,), 9, dtype=torch.uint8, device="cuda")
+            b = torch.full((total,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")
+            if fused:
+                P.evolve_sample(info, 0, info.count, st, w, s, 40 + i, b, prefix_reuse=True)
+            else:
+                P.evolve(info, 0, info.count, st, w, s, prefix_reuse=True)
+                P.sample(info, 0, info.count, st, s, 40 + i, b)
+            # the shared buffer is overwritten by the next call: keep a copy made in stream order
+            outs.append((st.clone() if i == 2 else st, w, s, b))
+            P.release_set(info)
+            P.release_circuit(cid)
+        # a circuit and set uploaded on the context stream, then prepared with the prepass ahead
+        circ = syndrome17(rounds=2, seed=1200)
+        cid = P.register(circ)
+        info = P.sample_kraus(cid, "topk", k=700, total_shots=100_000, export=False)
+        P.set_prepass_ahead(False)
+        first = [torch.empty((info.count, 1 << 17), dtype=torch.complex64, device="cuda"),
+                 torch.empty(info.count, dtype=torch.float64, device="cuda"),
+                 torch.empty(info.count, dtype=torch.uint8, device="cuda"),
+                 torch.empty(100_000, dtype=torch.int32, device="cuda")]
+        P.evolve_sample(info, 0, info.count, *first[:3], 3, first[3], prefix_reuse=True)
+        P.set_prepass_ahead(ahead)
+        again = [torch.full_like(x, 0) for x in first]
+        P.evolve_sample(info, 0, info.count, *again[:3], 3, again[3], prefix_reuse=True)
+        outs.append(tuple(first))
+        outs.append(tuple(again))
+        P.synchronize()
+        torch.cuda.synchronize()
+        P.close()
+        return outs
+
+    ref = run(False)
+    got = run(True)
+    assert len(ref) == len(got)
+    for i, (a, b) in enumerate(zip(ref, got)):
+        for x, y, name in zip(a, b, ("states", "weights", "status", "shots")):
+            if x.dtype == torch.complex64:
+                x, y = torch.view_as_real(x), torch.view_as_real(y)
+            assert torch.equal(x, y), f"call {i}: {name} differ"
+    _same(ref[-2], ref[-1])
+
+
 def test_evolve_sample_errors():
     """Capacity and pointer checks before any launch."""
     torch = torch_cuda()

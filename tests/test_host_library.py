@@ -220,6 +220,11 @@ def test_options_validate_values(host):
     for bad in (8, 15, -1):
         with pytest.raises(capi.PtsbeError):
             host.set_pershot_tile_bits(bad)
+    host.set_prepass_ahead(False)
+    host.set_prepass_ahead(True)
+    for bad in (2, -1):
+        with pytest.raises(capi.PtsbeError):
+            capi.ptsbe_set_option(host.ctx, capi.PTSBE_OPT_PREPASS_AHEAD, bad)
 
 
 @pytest.mark.parametrize("n", [2, 5, 9])
