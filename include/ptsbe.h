@@ -330,8 +330,10 @@ PTSBE_API int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * a work item is a set, or a range of at least 65,536 of its shots -- or n > 21) return
  * PTSBE_ERR_UNSUPPORTED with the sizes in the message. The first call on a device looks up the
  * array's device address (a one-time driver query): make that first call before any stream
- * capture. For n <= 17 the work items are copied from pageable host memory, so the call waits
- * for the work already queued on the context stream before it returns. Every call shares the one
+ * capture. For n <= 17 the work items go up through one of the context's pinned staging slots
+ * (asynchronous) when that slot, allocated by earlier calls, already has room for them (up to
+ * 2 MiB: 52,428 items); a larger list is copied from pageable host memory, and the call then
+ * waits for the work already queued on the context stream before it returns. Every call shares the one
  * array and overwrites what the previous call left there (nothing is read before this call writes
  * it); calls whose work can overlap on the GPU -- on different streams or contexts of the same
  * device -- race on it and must be serialised by the caller. Arguments, layout and other errors

@@ -246,6 +246,26 @@ struct ptsbe_ctx {
         sl.used = true;
         count_h2d(bytes);
     }
+    // h2d through a staging slot that already holds `bytes` (the first such slot from the next one
+    // on; no allocation of any kind); false when there is none, and nothing is copied.
+    bool h2d_no_growth(void* dst, const void* src, size_t bytes) {
+        size_t k = 0;
+        while (k < kSlots) {
+            const Slot& c = slots[(next_slot + k) % kSlots];
+            if (c.p && c.cap >= bytes && c.ev) break;
+            ++k;
+        }
+        if (k == kSlots) return false;
+        Slot& sl = slots[(next_slot + k) % kSlots];
+        next_slot = (next_slot + k + 1) % kSlots;
+        if (sl.used) PTSBE_CUDA(cudaEventSynchronize(sl.ev));
+        std::memcpy(sl.p, src, bytes);
+        PTSBE_CUDA(cudaMemcpyAsync(dst, sl.p, bytes, cudaMemcpyHostToDevice, ustream()));
+        PTSBE_CUDA(cudaEventRecord(sl.ev, ustream()));
+        sl.used = true;
+        count_h2d(bytes);
+        return true;
+    }
     void free_staging() {
         for (Slot& sl : slots) {
             if (sl.ev) cudaEventDestroy(sl.ev);
@@ -1836,9 +1856,12 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
                                                 std::to_string(noalloc_max_items()));
             ctx->use_device();
             SampleItem* d_items = (SampleItem*)noalloc_scratch(ctx->device);
-            // A copy from pageable host memory: no allocation, but the driver first waits for the
-            // work already queued on the stream (documented in the header).
-            PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(SampleItem), cudaMemcpyHostToDevice, ctx->stream));
+            // Through a pinned staging slot that already has room (asynchronous); otherwise from
+            // pageable host memory, which allocates nothing either but first waits for the work
+            // already queued on the stream (documented in the header).
+            const size_t ib = items.size() * sizeof(SampleItem);
+            if (!ctx->h2d_no_growth(d_items, items.data(), ib))
+                PTSBE_CUDA(cudaMemcpyAsync(d_items, items.data(), ib, cudaMemcpyHostToDevice, ctx->stream));
             launch_sample_cluster(A, d_items, (uint32_t)items.size(), ctx->stream);
         } else {
             const size_t need = sample_global_scratch_doubles(n) * 8;

@@ -47,6 +47,48 @@ def test_noalloc_matches_sample_shots_twice(n):
     assert not np.array_equal(other, want)
 
 
+@pytest.mark.parametrize("n", [17, 19])
+def test_noalloc_allocates_no_device_memory(n):
+    """Five calls in a row leave the device's free memory (cudaMemGetInfo) where it was after a
+    first call (which loads the kernels and looks up the fixed array's address), and give the
+    same shots each time. At 17 qubits the work items go up through a pinned staging slot that
+    already had room: the library's count of staged host-to-device bytes grows by exactly the
+    items' bytes per call (a pageable copy is not counted there)."""
+    torch = torch_cuda()
+    from paper_2504_16297_gb300 import capi
+    P = gpu_ctx()
+    circ = brickwork(n, 2, 0.02, 0.02, seed=400 + n)
+    cid = P.register(circ)
+    info = P.sample_kraus(cid, "proportional", seed=6, nsamples=30, total_shots=300_000)
+    count = min(info.count, 8)
+    states, w, status = evolve_gpu(P, info, 0, count, n)
+    total = int(info.shot_offsets[count])
+    bits = torch.full((total,), -7, dtype=torch.int32, device="cuda")
+
+    def call():
+        capi.ptsbe_sample_shots_noalloc(P.ctx, info.set_id, 0, count, states.data_ptr(), status.data_ptr(), 91,
+                                        bits.data_ptr(), total)
+
+    call()
+    torch.cuda.synchronize()
+    P.synchronize()
+    first = bits.cpu().numpy().copy()
+    free0, _ = torch.cuda.mem_get_info()
+    h0 = capi.ptsbe_h2d_bytes()
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    P.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    staged = capi.ptsbe_h2d_bytes() - h0
+    assert free1 == free0
+    assert np.array_equal(bits.cpu().numpy(), first)
+    if n <= 17:
+        assert staged > 0 and staged % 5 == 0 and (staged // 5) % 40 == 0   # 40-byte work items
+    else:
+        assert staged == 0                                                  # no work items above 17 qubits
+
+
 def test_noalloc_rejects_states_beyond_the_fixed_scratch():
     from paper_2504_16297_gb300 import capi
     from paper_2504_16297_gb300.capi import PtsbeError
