@@ -327,7 +327,8 @@ PTSBE_API int ptsbe_unique_shots(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first
  * 18 <= n <= 21 -- lives in a fixed 40 MiB device array compiled into the library, which every
  * GPU that loads the library holds until the process exits; no cudaMalloc, cudaFree or other
  * allocating routine is called. Requests that need more (more than 2^20 = 1,048,576 work items --
- * a work item is a set, or a range of at least 65,536 of its shots -- or n > 21) return
+ * a work item is a set, or a range of at least 65,536 of its shots above 14 qubits and of at
+ * least 2^n (1,024 at the least) up to 14 -- or n > 21) return
  * PTSBE_ERR_UNSUPPORTED with the sizes in the message. The first call on a device looks up the
  * array's device address (a one-time driver query): make that first call before any stream
  * capture. For n <= 17 the work items go up through one of the context's pinned staging slots

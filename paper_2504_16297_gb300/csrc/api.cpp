@@ -475,12 +475,16 @@ double mix_q0(const Circuit& c) {
 
 // Prepares states [first, first + count) of set s (the work of ptsbe_evolve_batch). With fused,
 // the small sparse final stage also draws the shots of the states it can (drawn[a] = 1).
+// before_launch runs after the call's own uploads and before its first kernel launch (the one-call
+// entry point puts the samplers' work items up there, so the sampler launch follows the evolve
+// launches with no copy between them); `drawn` is final when it runs.
 void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, void* d_states,
                   double* d_weights, uint8_t* d_status, uint32_t flags, const FusedShots* fused,
-                  std::vector<uint8_t>* drawn) {
+                  std::vector<uint8_t>* drawn, const std::function<void()>& before_launch = {}) {
     ctx->use_device();
     if (ctx->evolve_kernel == 4) {
         if (drawn) drawn->assign(count, 0);
+        if (before_launch) before_launch();
         evolve_dense_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags);
         return;
     }
@@ -748,6 +752,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     const uint64_t prefill = (uint64_t)((double)sbytes * ctx->split_fill / 100.0) / 4096u * 4096u;
     const bool split_fill = frame && prefill && ctx->aux && J == 1 && A.sparse_final_stage == 0 &&
                             A.small_bits > 0 && launches[0].second == count && (uint64_t)sbytes % 4096u == 0;
+    if (before_launch) before_launch();
     for (uint32_t j = 0; j < J; ++j) {
         const auto& L = launches[j];
         if (L.second == 0) continue;
@@ -804,6 +809,17 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
 // Reserves what sample_range will allocate for `count` states (work items: at most one light
 // item per state plus chunks; at most 2 count + 4 SMs + 16 of them), so that a call that prepares
 // and samples allocates nothing after its first launch.
+// Shots per sampler work item. An item rebuilds its state's CDF, so a state is split no finer
+// than that work repays: at least 2^16 shots above 14 qubits (a thread-block cluster per item),
+// and up to 14 qubits (one CTA per item) as many shots as the CDF has entries, 2^n (at least
+// 1,024). Above that floor, about four items per resident cluster over the whole shot budget. The
+// split never changes a shot: shot j of a set draws from the Philox counter of j whichever item
+// holds it.
+uint64_t sample_chunk(int n, uint64_t total, uint64_t clusters) {
+    const uint64_t floor_shots = n <= 14 ? std::max<uint64_t>(1024, 1ull << n) : (1ull << 16);
+    return std::max<uint64_t>(floor_shots, (total + 4 * clusters - 1) / (4 * clusters));
+}
+
 void reserve_sampler(ptsbe_ctx* ctx, const Circuit& c, uint32_t count) {
     const size_t items = 2 * (size_t)count + 4 * (size_t)std::max(ctx->n_sm, 1) + 16;
     ctx->ws(ctx->items, items * sizeof(SampleItem));
@@ -814,10 +830,23 @@ void reserve_sampler(ptsbe_ctx* ctx, const Circuit& c, uint32_t count) {
 
 // Draws the shots of states [first, first + count) (the work of ptsbe_sample_shots), except those
 // of states marked in drawn.
-void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, const void* d_states,
-                  const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, const std::vector<uint8_t>* drawn) {
-    ctx->use_device();
+// The work of sample_range in two halves: the host plan and its upload (work items, scratch), and
+// the launches, so that a caller can put the upload before earlier launches of the same call.
+struct SampleRun {
     SampleArgs A{};
+    SampleItem* d_items = nullptr;
+    size_t nl = 0, nh = 0;
+    double light_bytes = 0, heavy_bytes = 0;
+    std::vector<std::pair<uint32_t, uint64_t>> global;   // (range-local state, shots) for the global CDF
+    std::vector<uint32_t> global_alpha;
+    std::vector<uint64_t> global_out;
+};
+
+SampleRun plan_sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, const void* d_states,
+                            const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, const std::vector<uint8_t>* drawn) {
+    ctx->use_device();
+    SampleRun R;
+    SampleArgs& A = R.A;
     A.n = (int)c.n;
     A.states = (const float2*)d_states;
     A.status = d_status;
@@ -826,55 +855,64 @@ void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
     const int n = (int)c.n;
     const bool light_ok = n > 14 && n <= sample_light_max_qubits();
     std::vector<SampleItem> light, items;
-    // Split heavy states so every cluster gets work, but no finer: each item rebuilds its
-    // state's CDF. About four items per resident cluster over the whole shot budget.
     const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
     const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
     const uint64_t base = s.shot_off[first];
     uint64_t total = 0;
     for (uint32_t a = 0; a < count; ++a)
         if (!(drawn && (*drawn)[a])) total += s.shots[first + a];
-    const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+    const uint64_t chunk = sample_chunk(n, total, clusters);
     for (uint32_t a = 0; a < count; ++a) {
         const uint32_t alpha = first + a;
         const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
         if (m == 0 || (drawn && (*drawn)[a])) continue;
         if (light_ok && m <= ctx->light_shots) { light.push_back({a, alpha, 0, m, o, kDomShot, 0}); continue; }
-        if (n <= sample_cluster_max_qubits())
+        if (n <= sample_cluster_max_qubits()) {
             for (uint64_t j0 = 0; j0 < m; j0 += chunk)
                 items.push_back({a, alpha, j0, std::min(m, j0 + chunk), o + j0, kDomShot, 0});
+        } else {
+            R.global.push_back({a, m});
+            R.global_alpha.push_back(alpha);
+            R.global_out.push_back(o);
+        }
     }
-    const size_t nl = light.size(), nh = items.size();
+    R.nl = light.size();
+    R.nh = items.size();
     if (n > sample_cluster_max_qubits())   // reserved before any launch of this call
         A.scratch = (unsigned long long*)ctx->ws(ctx->scratch, sample_global_scratch_doubles(n) * 8);
-    if (nl + nh) {
+    if (R.nl + R.nh) {
+        // algorithmic: each state read once and 4 bytes per shot written (the light sampler's
+        // per-shot chunk re-reads are its design's extra traffic, not counted)
+        uint64_t light_shots = 0, heavy_shots = 0;
+        for (const SampleItem& it : light) light_shots += it.j1 - it.j0;
+        for (const SampleItem& it : items) heavy_shots += it.j1 - it.j0;
+        R.light_bytes = 8.0 * (double)(1ull << n) * (double)R.nl + 4.0 * (double)light_shots;
+        R.heavy_bytes = 8.0 * (double)(1ull << n) * (double)R.nh + 4.0 * (double)heavy_shots;
         light.insert(light.end(), items.begin(), items.end());
-        SampleItem* d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
-        ctx->h2d(d_items, light.data(), light.size() * sizeof(SampleItem));
-        if (nl) {
-            // algorithmic: each state read once and 4 bytes per shot written (the per-shot chunk
-            // re-reads are the light design's extra traffic, not counted)
-            uint64_t light_shots = 0;
-            for (size_t i = 0; i < nl; ++i) light_shots += light[i].j1 - light[i].j0;
-            const double bytes = 8.0 * (double)(1ull << n) * (double)nl + 4.0 * (double)light_shots;
-            ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, bytes, [&] { launch_sample_light(A, d_items, (uint32_t)nl, ctx->stream); });
-        }
-        if (nh) {
-            uint64_t heavy_shots = 0;
-            for (size_t i = nl; i < light.size(); ++i) heavy_shots += light[i].j1 - light[i].j0;
-            const double bytes = 8.0 * (double)(1ull << n) * (double)nh + 4.0 * (double)heavy_shots;
-            ctx->timed(PTSBE_TIMER_SAMPLE, bytes, [&] { launch_sample_cluster(A, d_items + nl, (uint32_t)nh, ctx->stream); });
-        }
+        R.d_items = (SampleItem*)ctx->ws(ctx->items, light.size() * sizeof(SampleItem));
+        ctx->h2d(R.d_items, light.data(), light.size() * sizeof(SampleItem));
     }
-    if (n > sample_cluster_max_qubits()) {
-        for (uint32_t a = 0; a < count; ++a) {
-            const uint32_t alpha = first + a;
-            const uint64_t m = s.shots[alpha], o = s.shot_off[alpha] - base;
-            if (m == 0 || (light_ok && m <= ctx->light_shots) || (drawn && (*drawn)[a])) continue;
-            const double sb = 8.0 * (double)(1ull << n);
-            ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] { launch_sample_global(A, a, alpha, 0, m, o, ctx->stream); });
-        }
+    return R;
+}
+
+void launch_sample_range(ptsbe_ctx* ctx, const SampleRun& R) {
+    const SampleArgs& A = R.A;
+    if (R.nl)
+        ctx->timed(PTSBE_TIMER_SAMPLE_LIGHT, R.light_bytes, [&] { launch_sample_light(A, R.d_items, (uint32_t)R.nl, ctx->stream); });
+    if (R.nh)
+        ctx->timed(PTSBE_TIMER_SAMPLE, R.heavy_bytes, [&] { launch_sample_cluster(A, R.d_items + R.nl, (uint32_t)R.nh, ctx->stream); });
+    const double sb = 8.0 * (double)(1ull << A.n);
+    for (size_t i = 0; i < R.global.size(); ++i) {
+        const uint64_t m = R.global[i].second;
+        ctx->timed(PTSBE_TIMER_SAMPLE, 5 * sb + 4.0 * m, [&] {
+            launch_sample_global(A, R.global[i].first, R.global_alpha[i], 0, m, R.global_out[i], ctx->stream);
+        });
     }
+}
+
+void sample_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t count, const void* d_states,
+                  const uint8_t* d_status, uint64_t seed, uint32_t* d_bits, const std::vector<uint8_t>* drawn) {
+    launch_sample_range(ctx, plan_sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, drawn));
 }
 
 // ---- dense tile passes -------------------------------------------------------------------------
@@ -1245,7 +1283,7 @@ void plan_samples(const ptsbe_ctx* ctx, const KSet& s, const Circuit& c, uint32_
     const uint64_t base = s.shot_off[first];
     uint64_t total = 0;
     for (uint32_t a = 0; a < count; ++a) total += s.shots[first + a];
-    const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+    const uint64_t chunk = sample_chunk(n, total, clusters);
     std::vector<SampleItem> light, heavy;
     for (uint32_t a = 0; a < count; ++a) {
         const uint32_t alpha = first + a;
@@ -1607,8 +1645,11 @@ int ptsbe_evolve_sample(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, uint32_
         const FusedShots fs{seed, d_bits};
         ctx->use_device();
         if (total) reserve_sampler(ctx, c, count);
-        evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, total ? &fs : nullptr, &drawn);
-        if (total) sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, &drawn);
+        SampleRun run;
+        evolve_range(ctx, s, c, first, count, d_states, d_weights, d_status, flags, total ? &fs : nullptr, &drawn, [&] {
+            if (total) run = plan_sample_range(ctx, s, c, first, count, d_states, d_status, seed, d_bits, &drawn);
+        });
+        if (total) launch_sample_range(ctx, run);
     });
 }
 
@@ -1842,7 +1883,7 @@ int ptsbe_sample_shots_noalloc(ptsbe_ctx* ctx, uint32_t set_id, uint32_t first, 
         if (n <= sample_cluster_max_qubits()) {
             const uint64_t cl = n <= 14 ? 1 : (1ull << (n - 14));
             const uint64_t clusters = std::max<uint64_t>(1, (uint64_t)ctx->n_sm / cl);
-            const uint64_t chunk = std::max<uint64_t>(1u << 16, (total + 4 * clusters - 1) / (4 * clusters));
+            const uint64_t chunk = sample_chunk(n, total, clusters);
             std::vector<SampleItem>& items = ctx->noalloc_items;
             items.clear();
             for (uint32_t a = 0; a < count; ++a) {
