@@ -163,8 +163,12 @@ struct Node {
     uint32_t off, len;
 };
 
+// Heap entries carry the key and the set's first two packed entries plus one (0: absent), which
+// order two sets lexicographically at those positions (a shorter list first); the arenas are read
+// only when the key and both words tie.
 struct HeapItem {
     double key;
+    uint64_t w0, w1;
     uint32_t node;
 };
 
@@ -183,7 +187,7 @@ class BestFirst {
             return a.k < b.k;
         });
         nodes_.push_back({1.0, 1.0, 0, 0});
-        push({1.0, 0});
+        push({1.0, 0, 0, 0});
     }
 
     // Pops the next set in order (its node: key and site-sorted packed entries stay readable);
@@ -207,12 +211,27 @@ class BestFirst {
         return std::lexicographical_compare(ent_.begin() + na.off, ent_.begin() + na.off + na.len,
                                             ent_.begin() + nb.off, ent_.begin() + nb.off + nb.len);
     }
+    // packed entry i of node plus one, 0 past its end
+    uint64_t word(uint32_t node, uint32_t i) const {
+        const Node& nd = nodes_[node];
+        return i < nd.len ? ent_[nd.off + i] + 1 : 0;
+    }
+    // Room for k pops (each pushes at most two children).
+    void reserve(uint64_t k) {
+        const size_t n = (size_t)std::min<uint64_t>(k, 1ull << 24);
+        nodes_.reserve(2 * n + 1);
+        heap_.reserve(2 * n + 1);
+        opt_.reserve(8 * n + 8);
+        ent_.reserve(8 * n + 8);
+    }
 
   private:
     struct After {   // true if a comes after b (max-heap on key, then canonical ascending)
         const BestFirst* bf;
         bool operator()(const HeapItem& a, const HeapItem& b) const {
             if (a.key != b.key) return a.key < b.key;
+            if (a.w0 != b.w0) return b.w0 < a.w0;
+            if (a.w1 != b.w1) return b.w1 < a.w1;
             const Node& na = bf->nodes_[a.node];
             const Node& nb = bf->nodes_[b.node];
             return std::lexicographical_compare(bf->ent_.begin() + nb.off, bf->ent_.begin() + nb.off + nb.len,
@@ -250,7 +269,7 @@ class BestFirst {
         std::sort(ent_.begin() + off, ent_.begin() + off + keep + 1);
         const uint32_t id = (uint32_t)nodes_.size();
         nodes_.push_back({prefix * opts_[j].r, prefix, off, (uint32_t)(keep + 1)});
-        push({nodes_[id].key, id});
+        push({nodes_[id].key, word(id, 0), word(id, 1), id});
     }
     void expand(uint32_t node) {
         const uint32_t len = nodes_[node].len;
@@ -450,6 +469,7 @@ void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& o
         std::vector<uint32_t> ids;
         uint32_t node;
         if (p.mode == PTSBE_PTS_TOPK) {
+            bf.reserve(p.k);
             ids.reserve((size_t)std::min<uint64_t>(p.k, 1ull << 24));
             for (uint64_t i = 0; i < p.k && bf.next_node(node); ++i) ids.push_back(node);
         } else {
@@ -460,7 +480,17 @@ void pts_run(const Circuit& c, const ptsbe_pts_params& p, uint64_t seed, KSet& o
                 if (ids.size() > (1ull << 31)) fail(PTSBE_ERR_UNSUPPORTED, "band selects more than 2^31 sets");
             }
         }
-        std::sort(ids.begin(), ids.end(), [&](uint32_t a, uint32_t b) { return bf.canon_before(a, b); });
+        {   // canonical order, by the first two entry words and the arenas on their ties
+            struct Keyed { uint64_t w0, w1; uint32_t id; };
+            std::vector<Keyed> kv(ids.size());
+            for (size_t i = 0; i < ids.size(); ++i) kv[i] = {bf.word(ids[i], 0), bf.word(ids[i], 1), ids[i]};
+            std::sort(kv.begin(), kv.end(), [&](const Keyed& a, const Keyed& b) {
+                if (a.w0 != b.w0) return a.w0 < b.w0;
+                if (a.w1 != b.w1) return a.w1 < b.w1;
+                return bf.canon_before(a.id, b.id);
+            });
+            for (size_t i = 0; i < ids.size(); ++i) ids[i] = kv[i].id;
+        }
         out.off.assign(1, 0);
         out.site.clear(); out.k.clear(); out.mult.clear(); out.q.clear(); out.key.clear(); out.shots.clear();
         for (uint32_t id : ids) {
