@@ -687,6 +687,7 @@ void evolve_range(ptsbe_ctx* ctx, KSet& s, Circuit& c, uint32_t first, uint32_t 
 
     EvolveArgs A{};
     A.ops = D.ops; A.micro = D.micro; A.mats = D.mats; A.chans = D.chans;
+    A.n_mats = (uint32_t)c.dmats.size();
     A.site_op = D.site_op; A.stages = D.stages; A.groups = D.groups; A.hi = D.hi; A.fstages = D.fstages;
     A.n = (int)c.n; A.tb = P.tb; A.lb = P.lb;
     A.ent_site = s.d_site; A.ent_k = s.d_k;

@@ -29,6 +29,12 @@ namespace ptsbe {
 namespace {
 using namespace tile;
 
+// Shared memory of the per-operator kernel: tile (2^tb complex64), hi table (2^(tb-lb) words),
+// then, 16-byte aligned, the staged matrices.
+__host__ __device__ inline size_t evolve_stage_mats_offset(int tb, int lb) {
+    return (((size_t)8 << tb) + ((size_t)4 << (tb - lb)) + 15) & ~(size_t)15;
+}
+
 __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_idx, int last, const uint32_t* __restrict__ nodes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevStage st;
@@ -36,6 +42,11 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
     const int tb = a.tb, lb = a.lb, n = a.n, ob = n - tb;
     float2* tile = reinterpret_cast<float2*>(smem);
     uint32_t* hi = reinterpret_cast<uint32_t*>(tile + (1u << tb));
+    // The circuit's matrices, when the launch stages them: every operator reads its matrix from
+    // shared memory instead of a global load on the CTA's serial chain of operators.
+    float2* smats = reinterpret_cast<float2*>(smem + evolve_stage_mats_offset(tb, lb));
+    const float2* mats = a.stage_mats ? smats : a.mats;
+    for (uint32_t i = threadIdx.x; i < a.stage_mats; i += blockDim.x) smats[i] = __ldg(a.mats + i);
     if (threadIdx.x == 0) st = a.stages[stage_idx];
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < (1u << (tb - lb)); i += blockDim.x) hi[i] = a.hi[st.hi_off + i];
@@ -72,21 +83,21 @@ __global__ void __launch_bounds__(1024) k_evolve_stage(EvolveArgs a, int stage_i
                 const DevMicro mi = a.micro[u];
                 const int pa = st.pos[mi.operand == 1 ? o.q1 : o.q0];
                 const int pb = st.pos[o.q1];
-                apply_micro(tile, tb, mi.kind, pa, pb, a.mats + mi.mat);
+                apply_micro(tile, tb, mi.kind, pa, pb, mats + mi.mat);
                 __syncthreads();
             }
         } else {
             if (o.fend != 0 && (e >= ee || a.ent_site[e] >= o.fsite1)) {
                 // no error inside the fused block: gate and no-error operators at once
                 if (o.fkind != DOP_NOP) {
-                    apply_micro(tile, tb, o.fkind, st.pos[o.q0], st.pos[o.q1], a.mats + o.fmat, o.fperm);
+                    apply_micro(tile, tb, o.fkind, st.pos[o.q0], st.pos[o.q1], mats + o.fmat, o.fperm);
                     __syncthreads();
                 }
                 op = o.fend - 1;
                 continue;
             }
             if (o.kind != DOP_NOP) {
-                apply_micro(tile, tb, o.kind, st.pos[o.q0], st.pos[o.q1], a.mats + o.mat);
+                apply_micro(tile, tb, o.kind, st.pos[o.q0], st.pos[o.q1], mats + o.mat);
                 __syncthreads();
             }
         }
@@ -1004,6 +1015,13 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
                       : frm ? evolve_frame_smem_bytes(a.tb, a.lb) : evolve_smem_bytes(a.tb, a.lb);
     const uint32_t tiles = (frm && stage == a.sparse_final_stage) ? 1u : 1u << (a.n - a.tb);
     frame::Program* progs = reinterpret_cast<frame::Program*>(a.frame_progs);
+    // The per-operator kernel stages the circuit's matrices when they fit beside its tile within
+    // the shared memory it was configured for (at most 32 KB of them).
+    EvolveArgs ks = a;
+    ks.stage_mats = 0;
+    if (!regs && !frm && a.n_mats <= 4096u &&
+        evolve_stage_mats_offset(a.tb, a.lb) + (size_t)a.n_mats * sizeof(float2) <= evolve_smem_bytes(kTileMax, 1))
+        ks.stage_mats = a.n_mats;
     if (frm && !progs) fail(PTSBE_ERR_INVALID, "frame kernel launched without program workspace");
     for (uint32_t b = 0; b < n_nodes; b += 65535) {
         const uint32_t cnt = (n_nodes - b) < 65535u ? (n_nodes - b) : 65535u;
@@ -1014,7 +1032,9 @@ void launch_evolve_stage(const EvolveArgs& a, int stage, bool last, const uint32
         else if (frm)
             k_evolve_frame<false><<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b, progs + b);
         else
-            k_evolve_stage<<<dim3(tiles, cnt), threads, smem, s>>>(a, stage, last ? 1 : 0, d_nodes + b);
+            k_evolve_stage<<<dim3(tiles, cnt), threads,
+                             ks.stage_mats ? evolve_stage_mats_offset(a.tb, a.lb) + (size_t)ks.stage_mats * sizeof(float2) : smem,
+                             s>>>(ks, stage, last ? 1 : 0, d_nodes + b);
         PTSBE_CUDA(cudaGetLastError());
         count_launch();
     }

@@ -377,6 +377,8 @@ struct EvolveArgs {
     const DevOp* ops;
     const DevMicro* micro;
     const float2* mats;
+    uint32_t n_mats;                 // entries of mats
+    uint32_t stage_mats;             // per-operator kernel: entries of mats staged in shared memory (0: none)
     const DevChannel* chans;
     const uint32_t* site_op;
     const DevStage* stages;
